@@ -1,0 +1,232 @@
+"""Python front end of the FP64 oracle (``rom_oracle.c``).
+
+TEST INFRASTRUCTURE.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
+CPU-baseline leg of ``bench.py`` may import this module.  It is independent
+of the CUDA library: it neither imports the package's binding nor links any
+of its code.
+
+All arrays are logical numpy arrays: ``Avs`` (Kv, Ks), ``Asv`` (Ks, Kv),
+``C`` (R, Kv), states ``V`` (Kv, M) and ``S`` (Ks, M), forcing tables
+(nsteps, M), trace records (nrec, R, M).  They are widened to float64 and
+handed to C in column-major order.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "rom_oracle.c")
+_OUT_DIR = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_OUT_DIR, "liborc.so")
+_lock = threading.Lock()
+_lib = None
+
+_dp = ctypes.POINTER(ctypes.c_double)
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (plain C, OpenMP over realizations,
+    no FMA contraction so every product and sum rounds on its own)."""
+    os.makedirs(_OUT_DIR, exist_ok=True)
+    if (not force and os.path.exists(_LIB_PATH)
+            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
+        return _LIB_PATH
+    tmp = _LIB_PATH + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp",
+           "-ffp-contract=off", "-fno-fast-math", _SRC, "-o", tmp, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            lib = ctypes.CDLL(build())
+            lib.orc_forward.restype = ctypes.c_int
+            lib.orc_forward.argtypes = [_dp, _dp, _dp, _dp, ctypes.c_int, ctypes.c_int,
+                                        ctypes.c_int, ctypes.c_double, _dp, _dp, _dp, _dp,
+                                        ctypes.c_int, ctypes.c_int, ctypes.c_long,
+                                        ctypes.c_int, _dp, ctypes.c_int]
+            lib.orc_inverse.restype = ctypes.c_int
+            lib.orc_inverse.argtypes = [_dp, _dp, _dp, ctypes.c_int, ctypes.c_int,
+                                        ctypes.c_double, _dp, _dp, _dp, _dp, ctypes.c_int,
+                                        ctypes.c_int, ctypes.c_long, ctypes.c_int]
+            lib.orc_energy.restype = ctypes.c_double
+            lib.orc_energy.argtypes = [_dp, ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                       _dp, _dp, ctypes.c_int]
+            lib.orc_spectral_radius.restype = ctypes.c_int
+            lib.orc_spectral_radius.argtypes = [_dp, _dp, ctypes.c_int, ctypes.c_int,
+                                                ctypes.c_int, ctypes.c_double, _dp]
+            lib.orc_adjoint.restype = ctypes.c_int
+            lib.orc_adjoint.argtypes = [_dp, _dp, _dp, _dp, ctypes.c_int, ctypes.c_int,
+                                        ctypes.c_int, ctypes.c_double, _dp, _dp, _dp,
+                                        ctypes.c_int, ctypes.c_int, ctypes.c_long, _dp,
+                                        _dp, _dp, _dp, _dp, ctypes.c_int]
+            lib.orc_ricker.restype = None
+            lib.orc_ricker.argtypes = [_dp, _dp, ctypes.c_int, _dp, _dp]
+            lib.orc_max_threads.restype = ctypes.c_int
+            _lib = lib
+    return _lib
+
+
+def max_threads() -> int:
+    return int(_load().orc_max_threads())
+
+
+def _cm(a) -> np.ndarray:
+    """float64 column-major copy (Fortran order) of a logical 2-D array."""
+    return np.asfortranarray(np.asarray(a, dtype=np.float64))
+
+
+def _ptr(a):
+    if a is None:
+        return None
+    return a.ctypes.data_as(_dp)
+
+
+def _check(rc: int, what: str):
+    if rc < 0:
+        raise RuntimeError(f"oracle {what} failed with code {rc}")
+
+
+def ricker(t, T):
+    """Ricker wavelet f(t; T) and its T-derivative, elementwise (float64)."""
+    t = np.asarray(t, np.float64)
+    T = np.asarray(T, np.float64)
+    shape = np.broadcast(t, T).shape
+    tb = np.ascontiguousarray(np.broadcast_to(t, shape)).ravel()
+    Tb = np.ascontiguousarray(np.broadcast_to(T, shape)).ravel()
+    f = np.empty_like(tb)
+    d = np.empty_like(tb)
+    _load().orc_ricker(_ptr(tb), _ptr(Tb), tb.size, _ptr(f), _ptr(d))
+    return f.reshape(shape), d.reshape(shape)
+
+
+def forward(Avs, Asv, g, C, dt, V0, S0, nsteps, T=None, ftab=None, n0=0, r=0,
+            threads=0):
+    """Leapfrog forward run.  Returns (V, S, traces) as float64 arrays;
+    traces is (nsteps // r, R, M) or None when r == 0 or C has no rows."""
+    Avs = _cm(Avs)
+    Asv = _cm(Asv)
+    Kv, Ks = Avs.shape
+    g = np.ascontiguousarray(np.asarray(g, np.float64))
+    Cm = _cm(C) if C is not None else np.zeros((0, Kv), order="F")
+    R = Cm.shape[0]
+    V = _cm(V0).copy(order="F")
+    S = _cm(S0).copy(order="F")
+    M = V.shape[1]
+    assert V.shape == (Kv, M) and S.shape == (Ks, M)
+    Tc = None if T is None else np.ascontiguousarray(np.asarray(T, np.float64))
+    Fc = None if ftab is None else np.ascontiguousarray(np.asarray(ftab, np.float64))
+    if Fc is not None:
+        assert Fc.shape == (nsteps, M)
+    nrec = nsteps // r if (r > 0 and R > 0) else 0
+    # records are [rec][m][j] in C: allocate (nrec, M, R) C-order
+    tr = np.zeros((nrec, M, R), np.float64) if nrec > 0 else None
+    rc = _load().orc_forward(_ptr(Avs), _ptr(Asv), _ptr(g), _ptr(Cm) if R > 0 else None,
+                             Kv, Ks, R, float(dt), _ptr(V), _ptr(S), _ptr(Tc), _ptr(Fc),
+                             M, int(nsteps), int(n0), int(r) if nrec > 0 else 0,
+                             _ptr(tr), int(threads))
+    _check(rc, "forward")
+    traces = None if tr is None else np.ascontiguousarray(tr.transpose(0, 2, 1))
+    return np.ascontiguousarray(V), np.ascontiguousarray(S), traces
+
+
+def inverse(Avs, Asv, g, dt, V, S, nsteps, T=None, ftab=None, n0=0, threads=0):
+    """Undo ``nsteps`` leapfrog steps (time reversal).  Returns (V0, S0)."""
+    Avs = _cm(Avs)
+    Asv = _cm(Asv)
+    Kv, Ks = Avs.shape
+    g = np.ascontiguousarray(np.asarray(g, np.float64))
+    V = _cm(V).copy(order="F")
+    S = _cm(S).copy(order="F")
+    M = V.shape[1]
+    Tc = None if T is None else np.ascontiguousarray(np.asarray(T, np.float64))
+    Fc = None if ftab is None else np.ascontiguousarray(np.asarray(ftab, np.float64))
+    rc = _load().orc_inverse(_ptr(Avs), _ptr(Asv), _ptr(g), Kv, Ks, float(dt), _ptr(V),
+                             _ptr(S), _ptr(Tc), _ptr(Fc), M, int(nsteps), int(n0),
+                             int(threads))
+    _check(rc, "inverse")
+    return np.ascontiguousarray(V), np.ascontiguousarray(S)
+
+
+def energy(Asv, dt, V, S) -> float:
+    """Discrete leapfrog energy ||V||^2 + ||S||^2 - dt <S, Asv V> (skew case)."""
+    Asv = _cm(Asv)
+    Ks, Kv = Asv.shape
+    V = _cm(V)
+    S = _cm(S)
+    return float(_load().orc_energy(_ptr(Asv), Kv, Ks, float(dt), _ptr(V), _ptr(S),
+                                    V.shape[1]))
+
+
+def spectral_radius(Avs, Asv, max_iter=5000, tol=1e-13):
+    """rho([[0, Avs], [Asv, 0]]) by FP64 power iteration on Avs Asv.
+    Returns (rho, iterations)."""
+    Avs = _cm(Avs)
+    Asv = _cm(Asv)
+    Kv, Ks = Avs.shape
+    out = ctypes.c_double(0.0)
+    it = _load().orc_spectral_radius(_ptr(Avs), _ptr(Asv), Kv, Ks, int(max_iter),
+                                     float(tol), ctypes.byref(out))
+    _check(it, "spectral_radius")
+    return float(out.value), int(it)
+
+
+def adjoint(Avs, Asv, g, C, dt, V0, S0, T, nsteps, ystar, n0=0, threads=0):
+    """Loss and gradients of sum_n sum_m ||C V_m^n - ystar_m^n||^2.
+    ystar is (nsteps, R, M).  Returns (loss, gV0, gS0, gT)."""
+    Avs = _cm(Avs)
+    Asv = _cm(Asv)
+    Kv, Ks = Avs.shape
+    g = np.ascontiguousarray(np.asarray(g, np.float64))
+    Cm = _cm(C)
+    R = Cm.shape[0]
+    V0 = _cm(V0)
+    S0 = _cm(S0)
+    M = V0.shape[1]
+    Tc = np.ascontiguousarray(np.asarray(T, np.float64))
+    ys = np.ascontiguousarray(np.asarray(ystar, np.float64).transpose(0, 2, 1))  # (n, M, R)
+    assert ys.shape == (nsteps, M, R)
+    gV = np.zeros((Kv, M), order="F")
+    gS = np.zeros((Ks, M), order="F")
+    gT = np.zeros(M)
+    loss = ctypes.c_double(0.0)
+    rc = _load().orc_adjoint(_ptr(Avs), _ptr(Asv), _ptr(g), _ptr(Cm), Kv, Ks, R,
+                             float(dt), _ptr(V0), _ptr(S0), _ptr(Tc), M, int(nsteps),
+                             int(n0), _ptr(ys), _ptr(gV), _ptr(gS), _ptr(gT),
+                             ctypes.byref(loss), int(threads))
+    _check(rc, "adjoint")
+    return float(loss.value), np.ascontiguousarray(gV), np.ascontiguousarray(gS), gT
+
+
+def problem_forward(p, V0=None, S0=None, nsteps=None, r=None, n0=0, T=None,
+                    threads=0, columns=None):
+    """Convenience: run a ``RomProblem``-like object (fields Avs, Asv, g, C, dt, T).
+    ``columns`` restricts the run to a subset of realizations (columns are
+    independent, so a subset gives exactly those columns of the full run)."""
+    Kv, Ks = p.Avs.shape
+    Tm = np.asarray(p.T if T is None else T, np.float64)
+    M = Tm.shape[0]
+    if V0 is None:
+        V0 = np.zeros((Kv, M))
+    if S0 is None:
+        S0 = np.zeros((Ks, M))
+    V0 = np.asarray(V0, np.float64)
+    S0 = np.asarray(S0, np.float64)
+    if columns is not None:
+        columns = np.asarray(columns)
+        Tm = Tm[columns]
+        V0 = V0[:, columns]
+        S0 = S0[:, columns]
+    steps = p.meta.get("steps") if nsteps is None else nsteps
+    rr = p.meta.get("r", 0) if r is None else r
+    return forward(p.Avs, p.Asv, p.g, p.C if p.C.shape[0] > 0 else None, p.dt, V0, S0,
+                   steps, T=Tm, n0=n0, r=rr, threads=threads)
