@@ -1,0 +1,393 @@
+"""Benchmark of the rank-2 Galerkin ROM leapfrog on GB300.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl {gb300,reference}]
+
+Workload (one bench "step" = one full rom_run_rank2 call over it): K = Kv = Ks
+= 512 reduced operators (Asv ~ N(0, 1/K), Avs = -Asv^T), M = 256 Ricker
+realizations (T_m = u_m dt, u_m ~ U[30, 60)), 10000 leapfrog steps, R = 64
+receiver rows recorded every r = 10 steps, FP32 with Kahan-compensated
+state.  Each timed step starts from zero state with L2 flushed (a 256 MB
+write between steps, outside the timed events).
+
+Metric: sample-steps/s = M * nsteps / t (one sample-step advances one
+realization by one full leapfrog step), whole job over all ranks.  Useful
+FLOP/s = (4 Kv Ks M + 2 R Kv M / r) per leapfrog step.
+
+Multi-GPU: every rank integrates its own M realizations (replicas by
+realization, no data-path collective); `value` sums over ranks and the time is
+the max over ranks.  Rank 0 prints one JSON line.
+
+`--impl reference` times the FP64 CPU oracle (the reference arm of this
+build) on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = dict(name="rank2-fp32-K512-M256-N10000-R64-r10", K=512, M=256, nsteps=10000, R=64,
+                r=10, prec="fp32", seed=0)
+FP32_LANES_PER_SM = 128  # FP32 FMA lanes per SM (Blackwell)
+
+
+def useful_flops(K, M, N, R, r):
+    return (4.0 * K * K * M + (2.0 * R * K * M / r if r else 0.0)) * N
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+                "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during a region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self.t = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-i", str(self.gpu), "-lms", "100"], stdout=subprocess.PIPE,
+                stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.t = threading.Thread(target=self._read, daemon=True)
+        self.t.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.t.join(timeout=5)
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# --------------------------------------------------------------- reference --
+def run_reference(args):
+    """The FP64 CPU oracle on a bounded sample of the workload."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import oracle
+    from paper_2009_11742_gb300 import inputs
+    p = inputs.make_problem(WORKLOAD["K"], WORKLOAD["K"], WORKLOAD["M"], WORKLOAD["R"],
+                            seed=WORKLOAD["seed"])
+    cores = oracle.max_threads()
+    ncol = min(WORKLOAD["M"], 2 * cores)
+    cols = np.linspace(0, WORKLOAD["M"] - 1, ncol).astype(int)
+    # calibrate so that each step is a few seconds of CPU work
+    t0 = time.perf_counter()
+    oracle.problem_forward(p, nsteps=50, r=WORKLOAD["r"], columns=cols)
+    per_step = (time.perf_counter() - t0) / 50
+    nst = int(max(100, min(WORKLOAD["nsteps"], 3.0 / max(per_step, 1e-9))))
+    nst -= nst % WORKLOAD["r"]
+    for _ in range(args.warmup):
+        oracle.problem_forward(p, nsteps=max(WORKLOAD["r"], nst // 10), r=WORKLOAD["r"],
+                               columns=cols)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        oracle.problem_forward(p, nsteps=nst, r=WORKLOAD["r"], columns=cols)
+        times.append(time.perf_counter() - t0)
+    tot = sum(times)
+    value = ncol * nst * args.steps / tot
+    sample = f"{ncol} of {WORKLOAD['M']} columns x {nst} of {WORKLOAD['nsteps']} steps per step"
+    line = {
+        "impl": "reference", "metric": "rank-2 ROM sample-steps/s (FP64 CPU oracle)",
+        "value": value, "unit": "sample-steps/s", "n_gpus": args.gpus, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": WORKLOAD["name"], "K": WORKLOAD["K"],
+                                        "M": WORKLOAD["M"], "nsteps": WORKLOAD["nsteps"],
+                                        "R": WORKLOAD["R"], "r": WORKLOAD["r"]},
+        "cpu_baseline": {"value": value, "unit": "sample-steps/s", "cores": cores,
+                         "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "sample-steps/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+        "gpu_launches": 0,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def cpu_baseline_sample(p, target_s=12.0):
+    """Oracle throughput on a bounded sample (all host cores)."""
+    import oracle
+    cores = oracle.max_threads()
+    ncol = min(WORKLOAD["M"], 2 * cores)
+    cols = np.linspace(0, WORKLOAD["M"] - 1, ncol).astype(int)
+    t0 = time.perf_counter()
+    oracle.problem_forward(p, nsteps=50, r=WORKLOAD["r"], columns=cols)
+    per_step = (time.perf_counter() - t0) / 50
+    nst = int(max(100, min(WORKLOAD["nsteps"], target_s / max(per_step, 1e-9))))
+    nst -= nst % WORKLOAD["r"]
+    t0 = time.perf_counter()
+    oracle.problem_forward(p, nsteps=nst, r=WORKLOAD["r"], columns=cols)
+    dt = time.perf_counter() - t0
+    return {"value": ncol * nst / dt, "unit": "sample-steps/s", "cores": cores, "kind": "oracle",
+            "sample": f"{ncol} of {WORKLOAD['M']} columns x {nst} of {WORKLOAD['nsteps']} "
+                      f"steps ({dt:.1f} s, OpenMP over columns)"}
+
+
+# ------------------------------------------------------------------- gb300 --
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-check", action="store_true", help="skip the sampled oracle error check")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl != "reference":
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    from paper_2009_11742_gb300 import build as rbuild
+    rbuild.build()
+    from paper_2009_11742_gb300 import inputs, rom
+
+    W = WORKLOAD
+    K, M, N, R, r = W["K"], W["M"], W["nsteps"], W["R"], W["r"]
+    p = inputs.make_problem(K, K, M, R, seed=W["seed"])
+    h = rom.Rom.from_problem(p)
+    V = rom.Rom.new_state(K, M, "fp32", device=dev)
+    S = rom.Rom.new_state(K, M, "fp32", device=dev)
+    T = torch.as_tensor(p.T, dtype=torch.float32, device=dev)
+    nrec = N // r
+    tr = torch.zeros((nrec, M, R), dtype=torch.float32, device=dev)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MB > L2
+    stream = torch.cuda.Stream(device=dev)
+
+    def one_run():
+        h.run_rank2(V, S, T, N, r=r, traces=tr, prec="fp32", stream=stream)
+
+    def reset():
+        V.zero_()
+        S.zero_()
+        flush.fill_(1.0)
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            reset()
+            one_run()
+    torch.cuda.synchronize()
+
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps)]
+    sampler = ClockSampler(local) if rank == 0 else None
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    if sampler:
+        sampler.start()
+    wall0 = time.perf_counter()
+    with torch.cuda.stream(stream):
+        for i in range(args.steps):
+            reset()
+            evs[i][0].record(stream)
+            one_run()
+            evs[i][1].record(stream)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    if dist is not None:
+        dist.barrier()
+    clocks = sampler.stop() if sampler else None
+    st = h.sync_status()
+    if st != 0:
+        raise RuntimeError(f"device status {rom.status_string(st)}")
+    per = [a.elapsed_time(b) * 1e-3 for a, b in evs]
+    t_dev = sum(per)
+    if dist is not None:
+        tt = torch.tensor([t_dev], dtype=torch.float64, device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_dev = float(tt.item())
+    value = world * M * N * args.steps / t_dev
+    ms_per_step = 1e3 * t_dev / args.steps
+    flops = useful_flops(K, M, N, R, r)
+
+    # ---- end-to-end through the C ABI with pinned host buffers
+    Vh = torch.zeros((M, K), dtype=torch.float32).pin_memory().numpy().T
+    Sh = torch.zeros((M, K), dtype=torch.float32).pin_memory().numpy().T
+    Th = torch.as_tensor(p.T, dtype=torch.float32).pin_memory().numpy()
+    trh = torch.zeros((nrec, M, R), dtype=torch.float32).pin_memory().numpy()
+    h.run_rank2(Vh, Sh, Th, N, r=r, traces=trh, prec="fp32")  # warm the staging buffers
+    e2e_times = []
+    for _ in range(max(3, args.steps // 2)):
+        Vh[...] = 0
+        Sh[...] = 0
+        t0 = time.perf_counter()
+        h.run_rank2(Vh, Sh, Th, N, r=r, traces=trh, prec="fp32")
+        e2e_times.append(time.perf_counter() - t0)
+    e2e_t = sum(e2e_times) / len(e2e_times)
+    if dist is not None:
+        tt = torch.tensor([e2e_t], dtype=torch.float64, device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        e2e_t = float(tt.item())
+
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return 0
+
+    # ---- rank-1 baselines on the same operator (fewer steps; throughput is per sample-step)
+    N1 = 2000
+    v1 = torch.zeros(K, dtype=torch.float32, device=dev)
+    s1 = torch.zeros(K, dtype=torch.float32, device=dev)
+    for _ in range(2):
+        h.run_rank1(v1, s1, float(p.T[0]), N1, prec="fp32", stream=stream)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    h.run_rank1(v1, s1, float(p.T[0]), N1, prec="fp32", stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    r1_single = N1 / (e0.elapsed_time(e1) * 1e-3)
+    Ve = rom.Rom.new_state(K, M, "fp32", device=dev)
+    Se = rom.Rom.new_state(K, M, "fp32", device=dev)
+    h.run_rank1_ensemble(Ve, Se, T, N1 // 10, prec="fp32", stream=stream)
+    e0.record(stream)
+    h.run_rank1_ensemble(Ve, Se, T, N1, prec="fp32", stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    r1_ens = M * N1 / (e0.elapsed_time(e1) * 1e-3)
+    rank1_best = max(r1_single, r1_ens)
+
+    # ---- accuracy on sampled columns against the FP64 oracle (full 10000 steps)
+    err = None
+    if not args.no_check:
+        import oracle
+        V.zero_()
+        S.zero_()
+        one_run()
+        torch.cuda.synchronize()
+        cols = np.array([0, 85, 170, 255])
+        Vo, So, tro = oracle.problem_forward(p, nsteps=N, r=r, columns=cols)
+        Vg = V.cpu().numpy()[:, cols]
+        Sg = S.cpu().numpy()[:, cols]
+        tg = tr.transpose(1, 2).cpu().numpy()[:, :, cols]
+
+        def rel(a, b):
+            return float(np.linalg.norm(a.astype(np.float64) - b) / np.linalg.norm(b))
+
+        err = {"V": rel(Vg, Vo), "S": rel(Sg, So), "traces": rel(tg, tro),
+               "columns": cols.tolist()}
+
+    cpu = None
+    if not args.no_cpu_baseline and world == 1:
+        cpu = cpu_baseline_sample(p)
+
+    pk, pk_kind = peaks()
+    sm_clock_max = float(pk.get("sm_max_mhz", 2070.0))
+    nsm = torch.cuda.get_device_properties(dev).multi_processor_count
+    fp32_peak = nsm * FP32_LANES_PER_SM * 2 * sm_clock_max * 1e6 / 1e12  # TFLOP/s
+    achieved = flops / (t_dev / args.steps) / 1e12
+    traffic = None
+    prof = os.path.join(ROOT, "profiles", "rank2_simt_f32_K512_M256.traffic.json")
+    if os.path.exists(prof):
+        try:
+            traffic = json.load(open(prof)).get("dram_bytes_per_launch")
+        except (OSError, ValueError):
+            traffic = None
+    roof = {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
+            "frac": achieved / fp32_peak, "traffic": traffic,
+            "kernel": "rank2_simt_kernel<float,8,8,true>",
+            "peak_basis": f"{nsm} SMs x {FP32_LANES_PER_SM} FP32 FMA lanes x 2 x "
+                          f"{sm_clock_max:.0f} MHz (max SM clock, {pk_kind})"}
+    if clocks and clocks.get("sm_mhz"):
+        roof["frac_at_measured_clock"] = achieved / (fp32_peak * clocks["sm_mhz"] / sm_clock_max)
+
+    es = 4
+    h2d = (2 * K * M + M) * es
+    d2h = (2 * K * M + nrec * R * M) * es
+    line = {
+        "metric": "rank-2 ROM sample-steps/s (FP32 leapfrog, rel err <= 1e-4)",
+        "value": value, "unit": "sample-steps/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": W["name"], "K": K, "M": M, "nsteps": N, "R": R, "r": r,
+                   "prec": "fp32", "parallelism": f"replicas-by-realization x{world}",
+                   "l2": "flushed (256 MB write) before every timed step"},
+        "tflops_useful": world * flops * args.steps / t_dev / 1e12,
+        "roofline": roof,
+        "cpu_baseline": cpu,
+        "e2e": {"value": world * M * N / e2e_t, "unit": "sample-steps/s",
+                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": args.steps,
+        "clocks": clocks,
+        "wall_s_timed_region": wall,
+        "rank1": {"single_sample_steps_s": r1_single, "ensemble_sample_steps_s": r1_ens,
+                  "rank2_speedup_vs_best_rank1": value / world / rank1_best},
+        "rel_err_vs_oracle": err,
+    }
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    h.close()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

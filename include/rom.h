@@ -1,0 +1,188 @@
+/*
+ * rom.h -- C ABI of librom.so, a GB300 (sm_103a) library that integrates
+ * rank-2 Galerkin reduced-order models of linear time-invariant systems.
+ *
+ * The model (Eq. (shwave_rom_ode_tensor), Sec. 3.1) is the velocity/stress
+ * pair of reduced ODEs
+ *
+ *     dV/dt = Avs S + g f(t; T_m)^T,      dS/dt = Asv V,
+ *
+ * with M realizations stacked as the columns of V (Kv x M) and S (Ks x M)
+ * (the rank-2 formulation, Eq. (rom_ode_tensor), Sec. 2.4).  Time stepping is
+ * the leapfrog of Sec. 3.1, velocity first, then stress with the new velocity:
+ *
+ *     V^{n+1} = V^n + dt (Avs S^n + g f_n^T),   S^{n+1} = S^n + dt Asv V^{n+1},
+ *
+ * with f_n[m] = f(t_n; T_m), t_n = (n0 + n) dt, and the point-source Ricker
+ * wavelet of Sec. 3.2 (sparse reduced forcing, Sec. 2.2):
+ *
+ *     f(t; T) = (1 - 2u) exp(-u),  u = pi^2 (t - 1.5 T)^2 / T^2.
+ *
+ * Receiver traces (seismograms from basis rows, Sec. 4.5.2) are y = C V^{n+1}
+ * after every step with (n + 1) mod r == 0.
+ *
+ * Conventions shared by every entry point
+ *  - Every call returns a rom_status.  Nothing aborts, traps or throws across
+ *    the ABI.
+ *  - Matrices are column-major.  Avs is Kv x Ks, Asv is Ks x Kv, C is R x Kv,
+ *    V is Kv x M (ld Kv), S is Ks x M (ld Ks).  A trace buffer holds
+ *    floor(nsteps / r) records; record k is R x M column-major at offset
+ *    k * R * M (element (j, m) at k*R*M + m*R + j).
+ *  - Element type of states, periods, forcing tables and traces: double for
+ *    ROM_FP64, float for every other precision.
+ *  - Pointers may be device pointers or host pointers (pageable or pinned);
+ *    the library tells them apart with cudaPointerGetAttributes.  Device
+ *    buffers are used in place and the call is asynchronous on `stream`.
+ *    Host buffers are staged through library-owned device memory and the
+ *    call returns after the results are copied back (synchronous).
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default).
+ *  - A handle is not re-entrant: do not run two calls on one handle
+ *    concurrently on different streams.
+ *  - Device-side failures (non-finite final state) are recorded in a
+ *    per-handle status word read by rom_sync_status().
+ */
+#ifndef ROM_H
+#define ROM_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct rom_s* rom_t;
+
+typedef enum {
+    ROM_OK = 0,
+    ROM_E_INVAL = 1,       /* bad argument: NULL pointer, size <= 0, misaligned buffer */
+    ROM_E_NOMEM = 2,       /* a device or host allocation failed */
+    ROM_E_CUDA = 3,        /* a CUDA runtime call failed (see rom_last_error) */
+    ROM_E_UNSTABLE = 4,    /* dt * rho >= 2 at rom_create: leapfrog would blow up */
+    ROM_E_TIMEOUT = 5,     /* a bounded device wait ran out */
+    ROM_E_NONFINITE = 6,   /* the final state holds NaN or Inf */
+    ROM_E_UNSUPPORTED = 7  /* shape/precision combination not provided */
+} rom_status;
+
+typedef enum {
+    ROM_FP64 = 0,   /* FP64 check path: FP64 state, FP64 arithmetic */
+    ROM_FP32 = 1,   /* FP32 SIMT products, Kahan-compensated state update */
+    ROM_TF32X3 = 2, /* tensor cores, tf32 hi/lo split, 3 products, Kahan update */
+    ROM_BF16X3 = 3, /* tensor cores, bf16 3-term operator / 2-term state split */
+    ROM_BF16 = 4    /* tensor cores, plain bf16 products (reported, not accepted) */
+} rom_prec;
+
+typedef enum { ROM_IN_F64 = 0, ROM_IN_F32 = 1 } rom_dtype;
+
+/* ------------------------------------------------------------------ handle */
+
+/*
+ * rom_create -- copy a reduced model into library-owned device memory.
+ *
+ * The reduced operators of Eq. (shwave_rom_ode_tensor) (Sec. 3.1): Avs
+ * (Kv x Ks, the paper's velocity operator), Asv (Ks x Kv, the stress
+ * operator), the source row g (Kv) of the velocity basis (Sec. 2.2, 3.2) and
+ * the receiver rows C (R x Kv; R may be 0 and C NULL) of Sec. 4.5.2.  Inputs
+ * are column-major, element type `in_dtype`, host or device; the caller may
+ * free them on return.  The library keeps FP64 and FP32 copies (row- and
+ * column-major, zero-padded) and the split copies the tensor-core paths use.
+ *
+ * dt-stability check (stable step, Sec. 4.4 and App. A): rho, the spectral
+ * radius of the coupled operator [[0, Avs], [Asv, 0]], equals
+ * sqrt(rho(Avs Asv)) and is computed by FP64 power iteration on the GPU.  If
+ * dt * rho >= 2 the handle is not created and ROM_E_UNSTABLE is returned.
+ * *rho_out (may be NULL) receives rho in either case.
+ * Limits: 1 <= Kv, Ks <= 1024, 0 <= R <= 1024.  Runs on the current device.
+ */
+rom_status rom_create(const void* Avs, const void* Asv, const void* g, const void* C,
+                      int Kv, int Ks, int R, double dt, int in_dtype, rom_t* out,
+                      double* rho_out);
+
+/* Free a handle and everything it owns (synchronizes its work first). */
+rom_status rom_destroy(rom_t h);
+
+/* The spectral radius computed by rom_create (FP64 power iteration). */
+rom_status rom_spectral_radius(rom_t h, double* rho);
+
+/* Read and clear the handle's device status word (synchronizes the device). */
+rom_status rom_sync_status(rom_t h, rom_status* device_status);
+
+/* Model dimensions of a handle (any output may be NULL). */
+rom_status rom_get_dims(rom_t h, int* Kv, int* Ks, int* R, double* dt);
+
+/* ------------------------------------------------------------- integrate */
+
+/*
+ * rom_run_rank2 -- the rank-2 Galerkin leapfrog (Eq. (rom_ode_tensor) with the
+ * split of Eq. (shwave_rom_ode_tensor), leapfrog of Sec. 3.1): advance all M
+ * realizations sharing the handle's operators by nsteps steps, IN PLACE on V
+ * (Kv x M) and S (Ks x M).  T (M) holds each realization's Ricker period in
+ * time units.  Steps n = 0 .. nsteps-1 use t_n = (n0 + n) dt.  traces (may be
+ * NULL; r must then be 0) receives floor(nsteps / r) records of C V.
+ * nsteps == 0 is a no-op.  Errors: ROM_E_INVAL (bad pointer/size, r < 0, or
+ * traces without receiver rows), ROM_E_UNSUPPORTED (precision not provided
+ * for this shape), ROM_E_CUDA.
+ */
+rom_status rom_run_rank2(rom_t h, void* V, void* S, const void* T, int M, int nsteps,
+                         long n0, int r, void* traces, int prec, void* stream);
+
+/*
+ * rom_run_rank2_ex -- rom_run_rank2 with the optional inputs spelled out.
+ *  ftab : if non-NULL, an nsteps x M forcing table (element [n * M + m]) used
+ *         in place of the Ricker wavelet; T is then ignored (may be NULL).
+ *         This is the dense reduced-forcing mode of Sec. 2.2 (precomputed
+ *         Phi^T f(t) at every target time).
+ *  compV, compS : optional FP32 Kahan compensation carries (Kv x M, Ks x M,
+ *         float, device).  When given they are read at the start and written
+ *         at the end, so that a run split into chunks (n0 advanced by each
+ *         chunk's nsteps) is bit-identical to one long run.  Ignored by
+ *         ROM_FP64.
+ */
+rom_status rom_run_rank2_ex(rom_t h, void* V, void* S, const void* T, const void* ftab,
+                            void* compV, void* compS, int M, int nsteps, long n0, int r,
+                            void* traces, int prec, void* stream);
+
+/*
+ * rom_run_rank1 -- the rank-1 Galerkin ROM (Eq. (rom_ode), Sec. 2.2): one
+ * realization (v: Kv, s: Ks, period T) advanced by the same leapfrog, two
+ * matrix-vector products per step (the memory-bound GEMV of Sec. 2.3).  It is
+ * the in-house baseline the rank-2 path is compared against.
+ */
+rom_status rom_run_rank1(rom_t h, void* v, void* s, double T, int nsteps, long n0, int r,
+                         void* trace, int prec, void* stream);
+
+/*
+ * rom_run_rank1_ensemble -- M independent rank-1 runs in one launch, one
+ * realization per thread block, with no reuse of operator reads across
+ * realizations: every realization streams both operators from memory every
+ * step.  This is the GPU counterpart of running many single-threaded rank-1
+ * ROMs side by side (Sec. 4.3, 4.5.2).  Arguments as rom_run_rank2.
+ */
+rom_status rom_run_rank1_ensemble(rom_t h, void* V, void* S, const void* T, int M,
+                                  int nsteps, long n0, int r, void* traces, int prec,
+                                  void* stream);
+
+/* ------------------------------------------------------------- utilities */
+
+/*
+ * rom_rel_l2 -- FP64 relative L2 error ||x - ref||_2 / ||ref||_2 (the error
+ * measure of Eq. (errors), Sec. 4.4) of two device vectors of n elements,
+ * element types x_dtype / ref_dtype (rom_dtype).  Synchronous; *out gets the
+ * ratio (or ||x - ref|| when ||ref|| == 0).
+ */
+rom_status rom_rel_l2(const void* x, int x_dtype, const void* ref, int ref_dtype, size_t n,
+                      double* out, void* stream);
+
+/* Human-readable name of a status code (static storage). */
+const char* rom_status_string(rom_status s);
+
+/* Text of the last CUDA error seen by this thread (static per thread). */
+const char* rom_last_error(void);
+
+/* Library version as major * 10000 + minor * 100 + patch. */
+int rom_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ROM_H */

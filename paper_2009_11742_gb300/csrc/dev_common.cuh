@@ -1,0 +1,72 @@
+// Device helpers shared by the librom kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace romk {
+
+// Ricker wavelet of Sec. 3.2 with delay t0 = 1.5 T, sampled at t = step * dt:
+//   f = (1 - 2u) exp(-u),  u = pi^2 (t - t0)^2 / T^2.
+// The time offset tau = t - t0 is formed in FP64 (step * dt reaches ~1e4 and
+// would lose the pulse's position in FP32); the wavelet itself is evaluated
+// in the path's precision with CUDA's expf / exp.
+__device__ __forceinline__ float ricker_eval(long long step, double dt, float T) {
+    const double tau = (double)step * dt - 1.5 * (double)T;
+    const float a = (float)(3.14159265358979323846 * tau / (double)T);
+    const float u = a * a;
+    return (1.0f - 2.0f * u) * expf(-u);
+}
+
+__device__ __forceinline__ double ricker_eval(long long step, double dt, double T) {
+    const double tau = (double)step * dt - 1.5 * T;
+    const double a = 3.14159265358979323846 * tau / T;
+    const double u = a * a;
+    return (1.0 - 2.0 * u) * exp(-u);
+}
+
+// d f / d T at fixed t (t0 = 1.5 T moves with T):
+//   df/du = (2u - 3) e^{-u},  du/dT = -pi^2 tau (3T + 2 tau) / T^3.
+__device__ __forceinline__ float ricker_dT_eval(long long step, double dt, float T) {
+    const double tau = (double)step * dt - 1.5 * (double)T;
+    const float a = (float)(3.14159265358979323846 * tau / (double)T);
+    const float u = a * a;
+    const float dudT = (float)(-9.8696044010893586188 * tau * (3.0 * (double)T + 2.0 * tau) /
+                               ((double)T * (double)T * (double)T));
+    return (2.0f * u - 3.0f) * expf(-u) * dudT;
+}
+
+// Four consecutive elements from shared or global memory (16-byte aligned).
+__device__ __forceinline__ void load4(const float* p, float (&x)[4]) {
+    const float4 v = *reinterpret_cast<const float4*>(p);
+    x[0] = v.x; x[1] = v.y; x[2] = v.z; x[3] = v.w;
+}
+__device__ __forceinline__ void load4(const double* p, double (&x)[4]) {
+    const double2 a = reinterpret_cast<const double2*>(p)[0];
+    const double2 b = reinterpret_cast<const double2*>(p)[1];
+    x[0] = a.x; x[1] = a.y; x[2] = b.x; x[3] = b.y;
+}
+__device__ __forceinline__ void load4_ro(const float* p, float (&x)[4]) {
+    const float4 v = __ldg(reinterpret_cast<const float4*>(p));
+    x[0] = v.x; x[1] = v.y; x[2] = v.z; x[3] = v.w;
+}
+__device__ __forceinline__ void load4_ro(const double* p, double (&x)[4]) {
+    const double2 a = __ldg(reinterpret_cast<const double2*>(p));
+    const double2 b = __ldg(reinterpret_cast<const double2*>(p) + 1);
+    x[0] = a.x; x[1] = a.y; x[2] = b.x; x[3] = b.y;
+}
+
+__device__ __forceinline__ bool is_finite(float x) { return isfinite(x); }
+__device__ __forceinline__ bool is_finite(double x) { return isfinite(x); }
+
+// Compensated (Kahan) accumulation v += inc with carry c.  The explicit
+// round-to-nearest intrinsics keep the compiler from contracting or
+// reassociating the compensation away.
+__device__ __forceinline__ float kahan_add(float v, float inc, float& c) {
+    const float y = __fsub_rn(inc, c);
+    const float t = __fadd_rn(v, y);
+    c = __fsub_rn(__fsub_rn(t, v), y);
+    return t;
+}
+
+}  // namespace romk

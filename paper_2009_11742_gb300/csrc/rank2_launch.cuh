@@ -1,0 +1,135 @@
+// Host-side planning and launch of the cluster-persistent SIMT rank-2 kernel.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <mutex>
+
+#include "rank2_simt.cuh"
+
+namespace romk {
+
+template <typename T, int KI, int CB, bool RES>
+struct Rank2Kernel {
+    static void* fn() { return (void*)&rank2_simt_kernel<T, KI, CB, RES>; }
+};
+
+// Kernel entry for (KI, CB) with the residency rule of the element type:
+// FP32 keeps both operators in registers up to KI = 8 (K <= 512); FP64 up to
+// KI = 4 (K <= 256) and re-reads its 32-row operator slab from L2 each
+// half-step beyond that.
+template <typename T, int CB>
+static void* rank2_kernel_for(int KI, bool* resident) {
+    constexpr bool f64 = sizeof(T) == 8;
+    *resident = !(f64 && KI > 4);
+    switch (KI) {
+        case 1: return Rank2Kernel<T, 1, CB, true>::fn();
+        case 2: return Rank2Kernel<T, 2, CB, true>::fn();
+        case 3: return Rank2Kernel<T, 3, CB, true>::fn();
+        case 4: return Rank2Kernel<T, 4, CB, true>::fn();
+        case 5: return Rank2Kernel<T, 5, CB, !f64>::fn();
+        case 6: return Rank2Kernel<T, 6, CB, !f64>::fn();
+        case 7: return Rank2Kernel<T, 7, CB, !f64>::fn();
+        case 8: return Rank2Kernel<T, 8, CB, !f64>::fn();
+        default: return nullptr;
+    }
+}
+
+template <typename T>
+static void* rank2_kernel(int KI, int cb, bool* resident) {
+    constexpr int CBW = sizeof(T) == 4 ? 8 : 4;  // wide column group
+    if (cb == 1) return rank2_kernel_for<T, 1>(KI, resident);
+    if (cb == CBW) return rank2_kernel_for<T, CBW>(KI, resident);
+    return nullptr;
+}
+
+static int device_smem_optin() {
+    int dev = 0, v = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    return v;
+}
+
+template <typename T>
+static cudaError_t prepare_kernel(void* fn, size_t smem) {
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+}
+
+template <typename T>
+static bool plan_rank2(int Kp, int M, int R, bool rank1, Rank2Plan* p) {
+    if (Kp <= 0 || Kp % 64 != 0 || Kp > 512 || M <= 0) return false;
+    constexpr int CBW = sizeof(T) == 4 ? 8 : 4;
+    p->KI = Kp / 64;
+    p->cs = Kp / 32;
+    p->cb = rank1 ? 1 : CBW;
+    const int rpc = (R + p->cs - 1) / p->cs;
+    const int smax = device_smem_optin();
+    // widest allocation that fits shared memory
+    int wcap = 0;
+    for (int w = p->cb; w <= 4096; w += p->cb) {
+        if (rank2_smem_layout<T>(w, Kp, rpc).total > (size_t)smax) break;
+        wcap = w;
+    }
+    if (wcap == 0) return false;
+    void* fn = rank2_kernel<T>(p->KI, p->cb, &p->resident);
+    if (!fn) return false;
+    const int wprobe = rank1 ? 1 : wcap;
+    const size_t smem_probe = rank2_smem_layout<T>(wprobe, Kp, rpc).total;
+    if (prepare_kernel<T>(fn, smem_probe) != cudaSuccess) return false;
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = p->cs;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3(p->cs, 1, 1);
+    cfg.blockDim = dim3(kThreads, 1, 1);
+    cfg.dynamicSmemBytes = smem_probe;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int nact = 0;
+    if (cudaOccupancyMaxActiveClusters(&nact, fn, &cfg) != cudaSuccess || nact <= 0) {
+        cudaGetLastError();
+        return false;
+    }
+    p->max_active_clusters = nact;
+    int wv = (M + nact - 1) / nact;
+    wv = ((wv + p->cb - 1) / p->cb) * p->cb;
+    if (wv > wcap) wv = wcap;
+    p->Wv = wv;
+    p->Wa = wv;
+    p->nclusters = (M + wv - 1) / wv;
+    p->smem = rank2_smem_layout<T>(p->Wa, Kp, rpc).total;
+    return true;
+}
+
+template <typename T>
+static cudaError_t launch_rank2(const Rank2Args& a_in, const Rank2Plan& p, cudaStream_t st) {
+    Rank2Args a = a_in;
+    a.Wv = p.Wv;
+    a.Wa = p.Wa;
+    a.rpc = (a.R + p.cs - 1) / p.cs;
+    bool res = false;
+    void* fn = rank2_kernel<T>(p.KI, p.cb, &res);
+    if (!fn) return cudaErrorInvalidValue;
+    cudaError_t e = prepare_kernel<T>(fn, p.smem);
+    if (e != cudaSuccess) return e;
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = p.cs;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3(p.cs * p.nclusters, 1, 1);
+    cfg.blockDim = dim3(kThreads, 1, 1);
+    cfg.dynamicSmemBytes = p.smem;
+    cfg.stream = st;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    void* args[] = {(void*)&a};
+    return cudaLaunchKernelExC(&cfg, fn, args);
+}
+
+}  // namespace romk

@@ -1,0 +1,322 @@
+// Cluster-persistent SIMT kernel for the rank-2 Galerkin leapfrog.
+//
+// One launch integrates all nsteps steps.  Work split (GB300 layout):
+//  * A thread-block cluster of CS = Kp / 32 CTAs owns one block of Wv state
+//    columns (realizations) for the whole run.  Columns are independent
+//    (Sec. 2.4: the rank-2 system is M rank-1 systems sharing the operator),
+//    so clusters never talk to each other.
+//  * CTA `rank` of a cluster owns rows [32 rank, 32 rank + 32) of both V and S
+//    and keeps the matching 32 rows of Avs and Asv in REGISTERS for the whole
+//    run (thread (row pair p, chunk j) holds rows 2p, 2p+1 at k = 64 i + 4 j + q).
+//  * Every CTA keeps a full copy of its column block of V and S in shared
+//    memory.  A half-step reads the whole operand (S for the velocity update,
+//    the new V for the stress update, Sec. 3.1 "velocity first"), updates its
+//    own 32 rows, and pushes those rows into the peer CTAs' copies through
+//    distributed shared memory; one cluster barrier per half-step publishes
+//    them.
+//  * The epilogue fuses the point-source forcing g f_n^T (Sec. 2.2, 3.2), the
+//    Kahan-compensated FP32 state update, and every r steps the receiver traces
+//    y = C V (Sec. 4.5.2, rows of C split across the cluster).
+#pragma once
+
+#include <cooperative_groups.h>
+#include <cuda_runtime.h>
+
+#include "dev_common.cuh"
+#include "rom_internal.h"
+
+namespace romk {
+
+namespace cg = cooperative_groups;
+
+constexpr int kThreads = 256;     // 16 row pairs x 16 k-chunks
+constexpr int kRowsPerCta = 32;
+
+__host__ __device__ constexpr size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
+
+// Shared-memory carve-up of one CTA (byte offsets).
+struct Rank2Smem {
+    size_t Vf, Sf, C, f, T, g, cV, cS, total;
+};
+
+template <typename T>
+__host__ __device__ inline Rank2Smem rank2_smem_layout(int Wa, int Kp, int rpc) {
+    Rank2Smem s{};
+    size_t o = 0;
+    s.Vf = o; o += align16((size_t)Wa * Kp * sizeof(T));
+    s.Sf = o; o += align16((size_t)Wa * Kp * sizeof(T));
+    s.C = o;  o += align16((size_t)rpc * Kp * sizeof(T));
+    s.f = o;  o += align16((size_t)Wa * sizeof(T));
+    s.T = o;  o += align16((size_t)Wa * sizeof(T));
+    s.g = o;  o += align16((size_t)kRowsPerCta * sizeof(T));
+    s.cV = o; o += align16((size_t)Wa * kRowsPerCta * sizeof(float));
+    s.cS = o; o += align16((size_t)Wa * kRowsPerCta * sizeof(float));
+    s.total = o;
+    return s;
+}
+
+__device__ __forceinline__ float fmadd(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double fmadd(double a, double b, double c) { return __fma_rn(a, b, c); }
+
+// Butterfly reduce-scatter of NV partial sums over the 16 lanes of a
+// half-warp (lane bits 0..3).  Afterwards the lane holds the full sum of
+// value index `vi`; when NV < 16 the lowest bits are all-reduced, and only
+// lanes with those bits clear report `active`.
+template <typename T, int NV>
+__device__ __forceinline__ T reduce_scatter16(T (&v)[NV], int j, int& vi, bool& active) {
+    static_assert(NV >= 1 && NV <= 16 && (NV & (NV - 1)) == 0, "NV must be a power of 2 <= 16");
+    int base = 0;
+#pragma unroll
+    for (int s = 0; s < 4; ++s) {
+        const int o = 8 >> s;
+        const int n = NV >> s;  // values still held before this stage
+        if (n > 1) {
+            const int half = n / 2;
+            const bool up = (j & o) != 0;
+#pragma unroll
+            for (int k = 0; k < half; ++k) {
+                const T send = up ? v[k] : v[k + half];
+                const T keep = up ? v[k + half] : v[k];
+                v[k] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+            }
+            base += up ? half : 0;
+        } else {
+            v[0] += __shfl_xor_sync(0xffffffffu, v[0], o);
+        }
+    }
+    vi = base;
+    constexpr int allred_bits = (NV >= 16) ? 0 : (NV == 8 ? 1 : (NV == 4 ? 2 : (NV == 2 ? 3 : 4)));
+    active = (j & ((1 << allred_bits) - 1)) == 0;
+    return v[0];
+}
+
+// One half-step on the CTA's own 32 rows:  Y_own += dt (op . X [+ g f^T]).
+template <typename T, int KI, int CB, bool FORCED>
+__device__ __forceinline__ void half_step(const T (&op)[2][4 * KI], const T* __restrict__ X,
+                                          T* __restrict__ Y, float* __restrict__ comp,
+                                          const T* __restrict__ gown, const T* __restrict__ fcol,
+                                          const T dt, const int Wa, const int Kp, const int row0,
+                                          const int rp, const int j) {
+    for (int c0 = 0; c0 < Wa; c0 += CB) {
+        T acc[2][CB];
+#pragma unroll
+        for (int cc = 0; cc < CB; ++cc) { acc[0][cc] = T(0); acc[1][cc] = T(0); }
+#pragma unroll
+        for (int i = 0; i < KI; ++i) {
+            T x[CB][4];
+#pragma unroll
+            for (int cc = 0; cc < CB; ++cc) load4(X + (size_t)(c0 + cc) * Kp + 64 * i + 4 * j, x[cc]);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+#pragma unroll
+                for (int cc = 0; cc < CB; ++cc) {
+                    acc[0][cc] = fmadd(op[0][4 * i + q], x[cc][q], acc[0][cc]);
+                    acc[1][cc] = fmadd(op[1][4 * i + q], x[cc][q], acc[1][cc]);
+                }
+            }
+        }
+        T v[2 * CB];
+#pragma unroll
+        for (int cc = 0; cc < CB; ++cc) { v[cc] = acc[0][cc]; v[CB + cc] = acc[1][cc]; }
+        int vi;
+        bool active;
+        const T tot = reduce_scatter16<T, 2 * CB>(v, j, vi, active);
+        if (active) {
+            const int rl = 2 * rp + vi / CB;
+            const int c = c0 + vi % CB;
+            T* yp = Y + (size_t)c * Kp + row0 + rl;
+            T inc = tot;
+            if (FORCED) inc = fmadd(gown[rl], fcol[c], inc);
+            inc = inc * dt;
+            if constexpr (sizeof(T) == 4) {
+                *yp = kahan_add(*yp, inc, comp[c * kRowsPerCta + rl]);
+            } else {
+                *yp = *yp + inc;
+            }
+        }
+    }
+}
+
+// Copy the CTA's own 32 rows of every column of buffer Y into the same place
+// of every other CTA of the cluster (distributed shared memory stores).
+template <typename T>
+__device__ __forceinline__ void push_own_rows(cg::cluster_group& cluster, T* Y, int Wa, int Kp,
+                                              int row0, int cs, int crank) {
+    constexpr int VPC = kRowsPerCta * (int)sizeof(T) / 16;  // 16-byte vectors per column
+    const int nvec = Wa * VPC;
+    for (int idx = threadIdx.x; idx < nvec; idx += kThreads) {
+        const int c = idx / VPC, part = idx % VPC;
+        float4* src = reinterpret_cast<float4*>(Y + (size_t)c * Kp + row0) + part;
+        const float4 val = *src;
+        for (int k = 1; k < cs; ++k) {
+            int d = crank + k;
+            if (d >= cs) d -= cs;
+            float4* dst = cluster.map_shared_rank(src, d);
+            *dst = val;
+        }
+    }
+}
+
+template <typename T, int KI>
+__device__ __forceinline__ void load_op_rows(T (&op)[2][4 * KI], const T* __restrict__ A, int Kp,
+                                             int row, int j) {
+#pragma unroll
+    for (int rr = 0; rr < 2; ++rr) {
+#pragma unroll
+        for (int i = 0; i < KI; ++i) {
+            T x[4];
+            load4_ro(A + (size_t)(row + rr) * Kp + 64 * i + 4 * j, x);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) op[rr][4 * i + q] = x[q];
+        }
+    }
+}
+
+// Forcing value f_n of local column c (global column gc0 + c).
+template <typename T>
+__device__ __forceinline__ T forcing_at(const Rank2Args& a, const T* Tcol, int c, int ncol,
+                                        int gc0, int n) {
+    if (c >= ncol) return T(0);
+    if (a.ftab) return static_cast<const T*>(a.ftab)[(size_t)n * a.Mtot + gc0 + c];
+    return (T)ricker_eval((long long)a.n0 + n, a.dt, Tcol[c]);
+}
+
+template <typename T, int KI, int CB, bool RESIDENT>
+__global__ void __launch_bounds__(kThreads, 1) rank2_simt_kernel(const Rank2Args a) {
+    cg::cluster_group cluster = cg::this_cluster();
+    const int cs = (int)cluster.num_blocks();
+    const int crank = (int)cluster.block_rank();
+    const int blk = blockIdx.x / cs;
+    const int col0 = blk * a.Wv;                 // first column of this block (within the job)
+    const int ncol = min(a.Wv, a.M - col0);      // valid columns
+    const int Wa = a.Wa;
+    const int Kp = a.Kp;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int j = lane & 15;
+    const int rp = warp * 2 + (lane >> 4);
+    const int row0 = crank * kRowsPerCta;
+    const T dt = (T)a.dt;
+
+    extern __shared__ __align__(16) unsigned char smem[];
+    const Rank2Smem L = rank2_smem_layout<T>(Wa, Kp, a.rpc);
+    T* Vf = reinterpret_cast<T*>(smem + L.Vf);
+    T* Sf = reinterpret_cast<T*>(smem + L.Sf);
+    T* Cown = reinterpret_cast<T*>(smem + L.C);
+    T* fcol = reinterpret_cast<T*>(smem + L.f);
+    T* Tcol = reinterpret_cast<T*>(smem + L.T);
+    T* gown = reinterpret_cast<T*>(smem + L.g);
+    float* cV = reinterpret_cast<float*>(smem + L.cV);
+    float* cS = reinterpret_cast<float*>(smem + L.cS);
+
+    const T* __restrict__ Vin = static_cast<const T*>(a.V);
+    const T* __restrict__ Sin = static_cast<const T*>(a.S);
+    const int gc0 = a.col_base + col0;  // first column in the caller's arrays
+
+    // ---- load the column block (all rows) and the per-CTA constants
+    for (int idx = tid; idx < Wa * Kp; idx += kThreads) {
+        const int c = idx / Kp, k = idx - (idx / Kp) * Kp;
+        Vf[idx] = (c < ncol && k < a.Kv) ? Vin[(size_t)(gc0 + c) * a.Kv + k] : T(0);
+        Sf[idx] = (c < ncol && k < a.Ks) ? Sin[(size_t)(gc0 + c) * a.Ks + k] : T(0);
+    }
+    for (int idx = tid; idx < Wa * kRowsPerCta; idx += kThreads) {
+        const int c = idx / kRowsPerCta, rl = idx % kRowsPerCta, row = row0 + rl;
+        const float* cvin = static_cast<const float*>(a.compV);
+        const float* csin = static_cast<const float*>(a.compS);
+        cV[idx] = (cvin && c < ncol && row < a.Kv) ? cvin[(size_t)(gc0 + c) * a.Kv + row] : 0.f;
+        cS[idx] = (csin && c < ncol && row < a.Ks) ? csin[(size_t)(gc0 + c) * a.Ks + row] : 0.f;
+    }
+    const T* Cp = static_cast<const T*>(a.C_p);
+    for (int idx = tid; idx < a.rpc * Kp; idx += kThreads) {
+        const int jj = idx / Kp, k = idx % Kp, jr = crank * a.rpc + jj;
+        Cown[idx] = (Cp && jr < a.R) ? Cp[(size_t)jr * Kp + k] : T(0);
+    }
+    if (tid < kRowsPerCta) gown[tid] = static_cast<const T*>(a.g_p)[row0 + tid];
+    for (int c = tid; c < Wa; c += kThreads) {
+        Tcol[c] = (a.Tper && c < ncol) ? static_cast<const T*>(a.Tper)[gc0 + c] : T(1);
+    }
+    __syncthreads();
+    for (int c = tid; c < Wa; c += kThreads) {
+        fcol[c] = (a.Tper || a.ftab) ? forcing_at<T>(a, Tcol, c, ncol, gc0, 0) : T(0);
+    }
+
+    T opA[2][4 * KI];
+    T opB[2][4 * KI];
+    const T* __restrict__ Avs = static_cast<const T*>(a.Avs_rm);
+    const T* __restrict__ Asv = static_cast<const T*>(a.Asv_rm);
+    if (RESIDENT) {
+        load_op_rows<T, KI>(opA, Avs, Kp, row0 + 2 * rp, j);
+        load_op_rows<T, KI>(opB, Asv, Kp, row0 + 2 * rp, j);
+    }
+    // every CTA's copies must be initialised before any peer pushes into them
+    cluster.sync();
+
+    T* traces = static_cast<T*>(a.traces);
+    for (int n = 0; n < a.nsteps; ++n) {
+        // ---- velocity half-step: V_own += dt (Avs_own S + g f_n^T)
+        if (!RESIDENT) load_op_rows<T, KI>(opA, Avs, Kp, row0 + 2 * rp, j);
+        half_step<T, KI, CB, true>(opA, Sf, Vf, cV, gown, fcol, dt, Wa, Kp, row0, rp, j);
+        __syncthreads();
+        push_own_rows<T>(cluster, Vf, Wa, Kp, row0, cs, crank);
+        cluster.sync();
+
+        // ---- stress half-step with the new velocity: S_own += dt Asv_own V
+        if (!RESIDENT) load_op_rows<T, KI>(opB, Asv, Kp, row0 + 2 * rp, j);
+        half_step<T, KI, CB, false>(opB, Vf, Sf, cS, gown, fcol, dt, Wa, Kp, row0, rp, j);
+
+        // ---- receiver traces y = C V^{n+1} (this CTA's rows of C)
+        if (traces && ((n + 1) % a.r) == 0) {
+            const int rec = (n + 1) / a.r - 1;
+            const int npair = a.rpc * ncol;
+            for (int pr = warp; pr < npair; pr += kThreads / 32) {
+                const int jj = pr / ncol, c = pr % ncol, jr = crank * a.rpc + jj;
+                if (jr >= a.R) continue;
+                T acc = T(0);
+                for (int k = 4 * lane; k < Kp; k += 128) {
+                    T cx[4], vx[4];
+                    load4(Cown + (size_t)jj * Kp + k, cx);
+                    load4(Vf + (size_t)c * Kp + k, vx);
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) acc = fmadd(cx[q], vx[q], acc);
+                }
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+                if (lane == 0) traces[((size_t)rec * a.Mtot + gc0 + c) * a.R + jr] = acc;
+            }
+        }
+        // ---- forcing of the next step (read by the next velocity epilogue)
+        if (n + 1 < a.nsteps) {
+            for (int c = tid; c < Wa; c += kThreads) {
+                fcol[c] = (a.Tper || a.ftab) ? forcing_at<T>(a, Tcol, c, ncol, gc0, n + 1) : T(0);
+            }
+        }
+        __syncthreads();
+        push_own_rows<T>(cluster, Sf, Wa, Kp, row0, cs, crank);
+        cluster.sync();
+    }
+
+    // ---- write back this CTA's rows (and the Kahan carries)
+    T* Vout = static_cast<T*>(a.V);
+    T* Sout = static_cast<T*>(a.S);
+    float* cvout = static_cast<float*>(a.compV);
+    float* csout = static_cast<float*>(a.compS);
+    int bad = 0;
+    for (int idx = tid; idx < ncol * kRowsPerCta; idx += kThreads) {
+        const int c = idx / kRowsPerCta, rl = idx % kRowsPerCta, row = row0 + rl;
+        if (row < a.Kv) {
+            const T x = Vf[(size_t)c * Kp + row];
+            Vout[(size_t)(gc0 + c) * a.Kv + row] = x;
+            if (cvout) cvout[(size_t)(gc0 + c) * a.Kv + row] = cV[c * kRowsPerCta + rl];
+            bad |= !is_finite(x);
+        }
+        if (row < a.Ks) {
+            const T x = Sf[(size_t)c * Kp + row];
+            Sout[(size_t)(gc0 + c) * a.Ks + row] = x;
+            if (csout) csout[(size_t)(gc0 + c) * a.Ks + row] = cS[c * kRowsPerCta + rl];
+            bad |= !is_finite(x);
+        }
+    }
+    bad = __syncthreads_or(bad);
+    if (bad && tid == 0 && a.status) atomicCAS(a.status, 0, (int)6 /* ROM_E_NONFINITE */);
+}
+
+}  // namespace romk

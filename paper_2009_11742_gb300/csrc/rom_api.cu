@@ -1,0 +1,515 @@
+// C ABI of librom: handles, argument checking, staging of host buffers and
+// dispatch to the kernels.  Declarations and contracts: include/rom.h.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <map>
+#include <mutex>
+#include <tuple>
+#include <vector>
+
+#include "rom_internal.h"
+
+using namespace romk;
+
+namespace {
+
+thread_local char g_last_error[256] = "";
+
+rom_status cuda_fail(cudaError_t e, const char* where) {
+    snprintf(g_last_error, sizeof(g_last_error), "%s: %s", where, cudaGetErrorString(e));
+    return e == cudaErrorMemoryAllocation ? ROM_E_NOMEM : ROM_E_CUDA;
+}
+
+#define ROM_CUDA(call)                                      \
+    do {                                                    \
+        cudaError_t e_ = (call);                            \
+        if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
+    } while (0)
+
+bool is_device_ptr(const void* p) {
+    if (!p) return false;
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+int pad64(int k) { return ((k + 63) / 64) * 64; }
+
+struct DevBuf {
+    void* p = nullptr;
+    size_t bytes = 0;
+    ~DevBuf() {
+        if (p) cudaFree(p);
+    }
+    cudaError_t ensure(size_t n) {
+        if (n <= bytes) return cudaSuccess;
+        if (p) cudaFree(p);
+        p = nullptr;
+        bytes = 0;
+        cudaError_t e = cudaMalloc(&p, n);
+        if (e == cudaSuccess) bytes = n;
+        return e;
+    }
+};
+
+}  // namespace
+
+struct rom_s {
+    int device = 0;
+    int Kv = 0, Ks = 0, R = 0, Kp = 0;
+    double dt = 0.0, rho = 0.0;
+    // Operator copies, zero padded to Kp x Kp.  rm: row-major, cm: column-major.
+    void* Avs_rm[2] = {nullptr, nullptr};  // [0] = f64, [1] = f32
+    void* Asv_rm[2] = {nullptr, nullptr};
+    void* Avs_cm[2] = {nullptr, nullptr};
+    void* Asv_cm[2] = {nullptr, nullptr};
+    void* g_p[2] = {nullptr, nullptr};
+    void* C_rm[2] = {nullptr, nullptr};  // R x Kp row-major
+    void* C_cm[2] = {nullptr, nullptr};  // Kp x R  (column j = row j of C)
+    int* status = nullptr;
+    double* scalar = nullptr;  // small device scratch (rank-1 period)
+    DevBuf stage;              // staging of host buffers
+    std::map<std::tuple<int, int, int, int>, Rank2Plan> plans;
+    std::mutex mu;
+};
+
+namespace {
+
+void free_handle(rom_s* h) {
+    if (!h) return;
+    for (int t = 0; t < 2; ++t) {
+        cudaFree(h->Avs_rm[t]);
+        cudaFree(h->Asv_rm[t]);
+        cudaFree(h->Avs_cm[t]);
+        cudaFree(h->Asv_cm[t]);
+        cudaFree(h->g_p[t]);
+        cudaFree(h->C_rm[t]);
+        cudaFree(h->C_cm[t]);
+    }
+    cudaFree(h->status);
+    cudaFree(h->scalar);
+    delete h;
+}
+
+// FP64 power iteration for rho(Avs Asv) on the GPU.
+rom_status power_iteration(rom_s* h, double* rho_out) {
+    const int Kv = h->Kv, Ks = h->Ks, Kp = h->Kp;
+    const int max_iter = 20000, chunk = 64;
+    const double tol = 1e-14;
+    double *x = nullptr, *z = nullptr, *y = nullptr, *lam = nullptr;
+    cudaError_t e = cudaMalloc(&x, sizeof(double) * Kp);
+    if (e == cudaSuccess) e = cudaMalloc(&z, sizeof(double) * Kp);
+    if (e == cudaSuccess) e = cudaMalloc(&y, sizeof(double) * Kp);
+    if (e == cudaSuccess) e = cudaMalloc(&lam, sizeof(double) * (max_iter + 1));
+    if (e != cudaSuccess) {
+        cudaFree(x); cudaFree(z); cudaFree(y); cudaFree(lam);
+        return cuda_fail(e, "power_iteration alloc");
+    }
+    std::vector<double> hx(Kv, 1.0 / sqrt((double)Kv));
+    std::vector<double> hl(chunk);
+    rom_status st = ROM_OK;
+    double cur = 0.0, prev = -1.0;
+    e = cudaMemcpy(x, hx.data(), sizeof(double) * Kv, cudaMemcpyHostToDevice);
+    for (int it0 = 1; e == cudaSuccess && it0 <= max_iter; it0 += chunk) {
+        const int it1 = it0 + chunk - 1 <= max_iter ? it0 + chunk - 1 : max_iter;
+        for (int it = it0; it <= it1 && e == cudaSuccess; ++it) {
+            e = launch_matvec_f64(static_cast<const double*>(h->Asv_rm[0]), Ks, Kv, Kp, x, z, 0);
+            if (e == cudaSuccess)
+                e = launch_matvec_f64(static_cast<const double*>(h->Avs_rm[0]), Kv, Ks, Kp, z, y, 0);
+            if (e == cudaSuccess) e = launch_power_step(y, x, Kv, lam, it, 0);
+        }
+        if (e != cudaSuccess) break;
+        const int cnt = it1 - it0 + 1;
+        e = cudaMemcpy(hl.data(), lam + it0, sizeof(double) * cnt, cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) break;
+        bool done = false;
+        for (int i = 0; i < cnt; ++i) {
+            cur = hl[i];
+            if (prev >= 0.0 && fabs(cur - prev) <= tol * cur) { done = true; break; }
+            prev = cur;
+        }
+        if (done || cur == 0.0) break;
+    }
+    if (e != cudaSuccess) st = cuda_fail(e, "power_iteration");
+    cudaFree(x); cudaFree(z); cudaFree(y); cudaFree(lam);
+    *rho_out = sqrt(cur);
+    return st;
+}
+
+bool valid_prec(int prec) { return prec >= ROM_FP64 && prec <= ROM_BF16; }
+
+}  // namespace
+
+extern "C" {
+
+int rom_version(void) { return 100; }
+
+const char* rom_last_error(void) { return g_last_error; }
+
+const char* rom_status_string(rom_status s) {
+    switch (s) {
+        case ROM_OK: return "ROM_OK";
+        case ROM_E_INVAL: return "ROM_E_INVAL: invalid argument";
+        case ROM_E_NOMEM: return "ROM_E_NOMEM: allocation failed";
+        case ROM_E_CUDA: return "ROM_E_CUDA: CUDA runtime error";
+        case ROM_E_UNSTABLE: return "ROM_E_UNSTABLE: dt * rho >= 2";
+        case ROM_E_TIMEOUT: return "ROM_E_TIMEOUT: device wait ran out";
+        case ROM_E_NONFINITE: return "ROM_E_NONFINITE: non-finite state";
+        case ROM_E_UNSUPPORTED: return "ROM_E_UNSUPPORTED: shape/precision not provided";
+    }
+    return "unknown rom_status";
+}
+
+rom_status rom_create(const void* Avs, const void* Asv, const void* g, const void* C, int Kv,
+                      int Ks, int R, double dt, int in_dtype, rom_t* out, double* rho_out) {
+    if (!out) return ROM_E_INVAL;
+    *out = nullptr;
+    if (!Avs || !Asv || !g || Kv < 1 || Ks < 1 || Kv > 1024 || Ks > 1024 || R < 0 || R > 1024 ||
+        (R > 0 && !C) || !(dt > 0.0) || !isfinite(dt) ||
+        (in_dtype != ROM_IN_F64 && in_dtype != ROM_IN_F32))
+        return ROM_E_INVAL;
+    rom_s* h = new (std::nothrow) rom_s();
+    if (!h) return ROM_E_NOMEM;
+    cudaGetDevice(&h->device);
+    h->Kv = Kv;
+    h->Ks = Ks;
+    h->R = R;
+    h->dt = dt;
+    h->Kp = pad64(Kv > Ks ? Kv : Ks);
+    const int Kp = h->Kp;
+    const size_t es = in_dtype == ROM_IN_F64 ? 8 : 4;
+    // bring the inputs to the device (temporary copies when they are host data)
+    const void* src[4] = {Avs, Asv, g, C};
+    const size_t cnt[4] = {(size_t)Kv * Ks, (size_t)Ks * Kv, (size_t)Kv, (size_t)R * Kv};
+    void* tmp[4] = {nullptr, nullptr, nullptr, nullptr};
+    const void* dsrc[4] = {nullptr, nullptr, nullptr, nullptr};
+    rom_status st = ROM_OK;
+    cudaError_t e = cudaSuccess;
+    for (int i = 0; i < 4 && e == cudaSuccess; ++i) {
+        if (!src[i] || cnt[i] == 0) continue;
+        if (is_device_ptr(src[i])) {
+            dsrc[i] = src[i];
+        } else {
+            e = cudaMalloc(&tmp[i], cnt[i] * es);
+            if (e == cudaSuccess) e = cudaMemcpy(tmp[i], src[i], cnt[i] * es, cudaMemcpyHostToDevice);
+            dsrc[i] = tmp[i];
+        }
+    }
+    const size_t kk = (size_t)Kp * Kp;
+    for (int t = 0; t < 2 && e == cudaSuccess; ++t) {
+        const size_t el = t == 0 ? 8 : 4;
+        e = cudaMalloc(&h->Avs_rm[t], kk * el);
+        if (e == cudaSuccess) e = cudaMalloc(&h->Asv_rm[t], kk * el);
+        if (e == cudaSuccess) e = cudaMalloc(&h->Avs_cm[t], kk * el);
+        if (e == cudaSuccess) e = cudaMalloc(&h->Asv_cm[t], kk * el);
+        if (e == cudaSuccess) e = cudaMalloc(&h->g_p[t], (size_t)Kp * el);
+        if (e == cudaSuccess && R > 0) e = cudaMalloc(&h->C_rm[t], (size_t)R * Kp * el);
+        if (e == cudaSuccess && R > 0) e = cudaMalloc(&h->C_cm[t], (size_t)R * Kp * el);
+        const int sd = in_dtype == ROM_IN_F64 ? 0 : 1;
+        if (e == cudaSuccess) e = launch_pad_copy(dsrc[0], sd, Kv, Ks, Kp, Kp, true, h->Avs_rm[t], t, 0);
+        if (e == cudaSuccess) e = launch_pad_copy(dsrc[1], sd, Ks, Kv, Kp, Kp, true, h->Asv_rm[t], t, 0);
+        if (e == cudaSuccess) e = launch_pad_copy(dsrc[0], sd, Kv, Ks, Kp, Kp, false, h->Avs_cm[t], t, 0);
+        if (e == cudaSuccess) e = launch_pad_copy(dsrc[1], sd, Ks, Kv, Kp, Kp, false, h->Asv_cm[t], t, 0);
+        if (e == cudaSuccess) e = launch_pad_copy(dsrc[2], sd, Kv, 1, Kp, 1, false, h->g_p[t], t, 0);
+        if (e == cudaSuccess && R > 0) e = launch_pad_copy(dsrc[3], sd, R, Kv, R, Kp, true, h->C_rm[t], t, 0);
+        if (e == cudaSuccess && R > 0) e = launch_pad_copy(dsrc[3], sd, R, Kv, R, Kp, false, h->C_cm[t], t, 0);
+    }
+    if (e == cudaSuccess) e = cudaMalloc(&h->status, sizeof(int) * 4);
+    if (e == cudaSuccess) e = cudaMemset(h->status, 0, sizeof(int) * 4);
+    if (e == cudaSuccess) e = cudaMalloc(&h->scalar, 64);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    for (int i = 0; i < 4; ++i) cudaFree(tmp[i]);
+    if (e != cudaSuccess) {
+        st = cuda_fail(e, "rom_create");
+        free_handle(h);
+        return st;
+    }
+    double rho = 0.0;
+    st = power_iteration(h, &rho);
+    if (st != ROM_OK) {
+        free_handle(h);
+        return st;
+    }
+    h->rho = rho;
+    if (rho_out) *rho_out = rho;
+    if (!(dt * rho < 2.0)) {
+        free_handle(h);
+        return ROM_E_UNSTABLE;
+    }
+    *out = h;
+    return ROM_OK;
+}
+
+rom_status rom_destroy(rom_t h) {
+    if (!h) return ROM_E_INVAL;
+    cudaDeviceSynchronize();
+    free_handle(h);
+    return ROM_OK;
+}
+
+rom_status rom_spectral_radius(rom_t h, double* rho) {
+    if (!h || !rho) return ROM_E_INVAL;
+    *rho = h->rho;
+    return ROM_OK;
+}
+
+rom_status rom_get_dims(rom_t h, int* Kv, int* Ks, int* R, double* dt) {
+    if (!h) return ROM_E_INVAL;
+    if (Kv) *Kv = h->Kv;
+    if (Ks) *Ks = h->Ks;
+    if (R) *R = h->R;
+    if (dt) *dt = h->dt;
+    return ROM_OK;
+}
+
+rom_status rom_sync_status(rom_t h, rom_status* device_status) {
+    if (!h || !device_status) return ROM_E_INVAL;
+    ROM_CUDA(cudaDeviceSynchronize());
+    int v = 0;
+    ROM_CUDA(cudaMemcpy(&v, h->status, sizeof(int), cudaMemcpyDeviceToHost));
+    ROM_CUDA(cudaMemset(h->status, 0, sizeof(int)));
+    *device_status = (rom_status)v;
+    return ROM_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+// Device buffers of one integration call (caller's or staged).
+struct RunBufs {
+    void *V, *S, *T, *ftab, *compV, *compS, *traces;
+};
+
+rom_status get_plan(rom_s* h, int prec, int M, bool rank1, Rank2Plan* plan) {
+    std::lock_guard<std::mutex> lk(h->mu);
+    const auto key = std::make_tuple(prec == ROM_FP64 ? 0 : 1, M, rank1 ? 1 : 0, h->R);
+    auto it = h->plans.find(key);
+    if (it != h->plans.end()) {
+        *plan = it->second;
+        return ROM_OK;
+    }
+    const bool ok = prec == ROM_FP64 ? plan_rank2_simt_f64(h->Kp, M, h->R, rank1, plan)
+                                     : plan_rank2_simt_f32(h->Kp, M, h->R, rank1, plan);
+    if (!ok) {
+        snprintf(g_last_error, sizeof(g_last_error),
+                 "no SIMT rank-2 plan for Kp=%d M=%d (prec %d)", h->Kp, M, prec);
+        return ROM_E_UNSUPPORTED;
+    }
+    h->plans[key] = *plan;
+    return ROM_OK;
+}
+
+rom_status run_rank2_device(rom_s* h, const RunBufs& b, int M, int nsteps, long n0, int r,
+                            int prec, bool rank1, cudaStream_t st) {
+    if (prec != ROM_FP64 && prec != ROM_FP32) {
+        snprintf(g_last_error, sizeof(g_last_error), "precision %d has no kernel in this build", prec);
+        return ROM_E_UNSUPPORTED;
+    }
+    Rank2Plan plan;
+    rom_status s = get_plan(h, prec, M, rank1, &plan);
+    if (s != ROM_OK) return s;
+    const int t = prec == ROM_FP64 ? 0 : 1;
+    Rank2Args a = {};
+    a.Avs_rm = h->Avs_rm[t];
+    a.Asv_rm = h->Asv_rm[t];
+    a.g_p = h->g_p[t];
+    a.C_p = h->C_rm[t];
+    a.V = b.V;
+    a.S = b.S;
+    a.compV = prec == ROM_FP64 ? nullptr : b.compV;
+    a.compS = prec == ROM_FP64 ? nullptr : b.compS;
+    a.Tper = b.ftab ? nullptr : b.T;
+    a.ftab = b.ftab;
+    a.traces = b.traces;
+    a.status = h->status;
+    a.dt = h->dt;
+    a.n0 = n0;
+    a.Kv = h->Kv;
+    a.Ks = h->Ks;
+    a.Kp = h->Kp;
+    a.R = h->R;
+    a.M = M;
+    a.Mtot = M;
+    a.col_base = 0;
+    a.nsteps = nsteps;
+    a.r = b.traces ? r : 1;
+    cudaError_t e = prec == ROM_FP64 ? launch_rank2_simt_f64(a, plan, st)
+                                     : launch_rank2_simt_f32(a, plan, st);
+    if (e != cudaSuccess) return cuda_fail(e, "rank2 launch");
+    return ROM_OK;
+}
+
+// Validates and runs a rank-2 style call; stages host buffers when V is host memory.
+rom_status run_common(rom_s* h, void* V, void* S, const void* T, const void* ftab, void* compV,
+                      void* compS, int M, int nsteps, long n0, int r, void* traces, int prec,
+                      void* stream, bool ensemble) {
+    if (!h || !V || !S || M < 1 || nsteps < 0 || r < 0 || !valid_prec(prec)) return ROM_E_INVAL;
+    if (traces && (r < 1 || h->R < 1)) return ROM_E_INVAL;
+    if (nsteps == 0) return ROM_OK;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const size_t es = prec == ROM_FP64 ? 8 : 4;
+    const int nrec = traces ? nsteps / r : 0;
+    const bool host = !is_device_ptr(V);
+    if (!host) {
+        RunBufs b = {V, S, const_cast<void*>(T), const_cast<void*>(ftab), compV, compS,
+                     nrec > 0 ? traces : nullptr};
+        if (ensemble) {
+            if (ftab || compV || compS) return ROM_E_UNSUPPORTED;
+            const int t = prec == ROM_FP64 ? 0 : 1;
+            Rank1EnsArgs a = {};
+            a.Avs_cm = h->Avs_cm[t];
+            a.Asv_cm = h->Asv_cm[t];
+            a.g_p = h->g_p[t];
+            a.C_cm = h->C_cm[t];
+            a.V = V;
+            a.S = S;
+            a.Tper = T;
+            a.traces = b.traces;
+            a.status = h->status;
+            a.dt = h->dt;
+            a.n0 = n0;
+            a.Kv = h->Kv;
+            a.Ks = h->Ks;
+            a.Kp = h->Kp;
+            a.R = h->R;
+            a.M = M;
+            a.nsteps = nsteps;
+            a.r = b.traces ? r : 1;
+            if (prec != ROM_FP64 && prec != ROM_FP32) return ROM_E_UNSUPPORTED;
+            cudaError_t e = prec == ROM_FP64 ? launch_rank1_ensemble_f64(a, st)
+                                             : launch_rank1_ensemble_f32(a, st);
+            if (e != cudaSuccess) return cuda_fail(e, "rank1 ensemble launch");
+            return ROM_OK;
+        }
+        return run_rank2_device(h, b, M, nsteps, n0, r, prec, false, st);
+    }
+    // host buffers: stage through library-owned device memory, synchronous
+    const size_t nV = (size_t)h->Kv * M, nS = (size_t)h->Ks * M;
+    const size_t nT = T ? (size_t)M : 0, nF = ftab ? (size_t)nsteps * M : 0;
+    const size_t nC = compV ? nV + nS : 0;
+    const size_t nTr = (size_t)nrec * h->R * M;
+    auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
+    const size_t bytes = al(nV * es) + al(nS * es) + al(nT * es) + al(nF * es) + al(nC * 4) +
+                         al(nTr * es);
+    ROM_CUDA(h->stage.ensure(bytes));
+    char* base = static_cast<char*>(h->stage.p);
+    size_t o = 0;
+    RunBufs b = {};
+    b.V = base + o; o += al(nV * es);
+    b.S = base + o; o += al(nS * es);
+    b.T = nT ? base + o : nullptr; o += al(nT * es);
+    b.ftab = nF ? base + o : nullptr; o += al(nF * es);
+    b.compV = nC ? base + o : nullptr;
+    b.compS = nC ? base + o + nV * 4 : nullptr; o += al(nC * 4);
+    b.traces = nTr ? base + o : nullptr;
+    ROM_CUDA(cudaMemcpyAsync(b.V, V, nV * es, cudaMemcpyHostToDevice, st));
+    ROM_CUDA(cudaMemcpyAsync(b.S, S, nS * es, cudaMemcpyHostToDevice, st));
+    if (nT) ROM_CUDA(cudaMemcpyAsync(b.T, T, nT * es, cudaMemcpyHostToDevice, st));
+    if (nF) ROM_CUDA(cudaMemcpyAsync(b.ftab, ftab, nF * es, cudaMemcpyHostToDevice, st));
+    if (nC) {
+        ROM_CUDA(cudaMemcpyAsync(b.compV, compV, nV * 4, cudaMemcpyHostToDevice, st));
+        ROM_CUDA(cudaMemcpyAsync(b.compS, compS, nS * 4, cudaMemcpyHostToDevice, st));
+    }
+    rom_status s = run_common(h, b.V, b.S, b.T, b.ftab, b.compV, b.compS, M, nsteps, n0, r,
+                              b.traces, prec, stream, ensemble);
+    if (s != ROM_OK) return s;
+    ROM_CUDA(cudaMemcpyAsync(V, b.V, nV * es, cudaMemcpyDeviceToHost, st));
+    ROM_CUDA(cudaMemcpyAsync(S, b.S, nS * es, cudaMemcpyDeviceToHost, st));
+    if (nC) {
+        ROM_CUDA(cudaMemcpyAsync(compV, b.compV, nV * 4, cudaMemcpyDeviceToHost, st));
+        ROM_CUDA(cudaMemcpyAsync(compS, b.compS, nS * 4, cudaMemcpyDeviceToHost, st));
+    }
+    if (nTr) ROM_CUDA(cudaMemcpyAsync(traces, b.traces, nTr * es, cudaMemcpyDeviceToHost, st));
+    ROM_CUDA(cudaStreamSynchronize(st));
+    return ROM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+rom_status rom_run_rank2(rom_t h, void* V, void* S, const void* T, int M, int nsteps, long n0,
+                         int r, void* traces, int prec, void* stream) {
+    return run_common(h, V, S, T, nullptr, nullptr, nullptr, M, nsteps, n0, r, traces, prec,
+                      stream, false);
+}
+
+rom_status rom_run_rank2_ex(rom_t h, void* V, void* S, const void* T, const void* ftab,
+                            void* compV, void* compS, int M, int nsteps, long n0, int r,
+                            void* traces, int prec, void* stream) {
+    if ((compV == nullptr) != (compS == nullptr)) return ROM_E_INVAL;
+    return run_common(h, V, S, T, ftab, compV, compS, M, nsteps, n0, r, traces, prec, stream,
+                      false);
+}
+
+rom_status rom_run_rank1_ensemble(rom_t h, void* V, void* S, const void* T, int M, int nsteps,
+                                  long n0, int r, void* traces, int prec, void* stream) {
+    return run_common(h, V, S, T, nullptr, nullptr, nullptr, M, nsteps, n0, r, traces, prec,
+                      stream, true);
+}
+
+rom_status rom_run_rank1(rom_t h, void* v, void* s, double T, int nsteps, long n0, int r,
+                         void* trace, int prec, void* stream) {
+    if (!h || !v || !s || nsteps < 0 || r < 0 || !valid_prec(prec) || !(T > 0.0)) return ROM_E_INVAL;
+    if (trace && (r < 1 || h->R < 1)) return ROM_E_INVAL;
+    if (nsteps == 0) return ROM_OK;
+    if (prec != ROM_FP64 && prec != ROM_FP32) return ROM_E_UNSUPPORTED;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const size_t es = prec == ROM_FP64 ? 8 : 4;
+    // the period goes to a small device scratch in the state's element type
+    if (prec == ROM_FP64) {
+        ROM_CUDA(cudaMemcpyAsync(h->scalar, &T, 8, cudaMemcpyHostToDevice, st));
+    } else {
+        const float Tf = (float)T;
+        ROM_CUDA(cudaMemcpyAsync(h->scalar, &Tf, 4, cudaMemcpyHostToDevice, st));
+    }
+    const bool host = !is_device_ptr(v);
+    const int nrec = trace ? nsteps / r : 0;
+    if (!host) {
+        RunBufs b = {v, s, h->scalar, nullptr, nullptr, nullptr, nrec > 0 ? trace : nullptr};
+        return run_rank2_device(h, b, 1, nsteps, n0, r, prec, true, st);
+    }
+    const size_t nV = h->Kv, nS = h->Ks, nTr = (size_t)nrec * h->R;
+    ROM_CUDA(h->stage.ensure((nV + nS + nTr) * es + 512));
+    char* base = static_cast<char*>(h->stage.p);
+    RunBufs b = {base, base + ((nV * es + 255) & ~size_t(255)), h->scalar, nullptr, nullptr,
+                 nullptr, nullptr};
+    b.traces = nTr ? static_cast<char*>(b.S) + ((nS * es + 255) & ~size_t(255)) : nullptr;
+    ROM_CUDA(cudaMemcpyAsync(b.V, v, nV * es, cudaMemcpyHostToDevice, st));
+    ROM_CUDA(cudaMemcpyAsync(b.S, s, nS * es, cudaMemcpyHostToDevice, st));
+    rom_status rs = run_rank2_device(h, b, 1, nsteps, n0, r, prec, true, st);
+    if (rs != ROM_OK) return rs;
+    ROM_CUDA(cudaMemcpyAsync(v, b.V, nV * es, cudaMemcpyDeviceToHost, st));
+    ROM_CUDA(cudaMemcpyAsync(s, b.S, nS * es, cudaMemcpyDeviceToHost, st));
+    if (nTr) ROM_CUDA(cudaMemcpyAsync(trace, b.traces, nTr * es, cudaMemcpyDeviceToHost, st));
+    ROM_CUDA(cudaStreamSynchronize(st));
+    return ROM_OK;
+}
+
+rom_status rom_rel_l2(const void* x, int x_dtype, const void* ref, int ref_dtype, size_t n,
+                      double* out, void* stream) {
+    if (!x || !ref || !out || n == 0 || (x_dtype != 0 && x_dtype != 1) ||
+        (ref_dtype != 0 && ref_dtype != 1))
+        return ROM_E_INVAL;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    double* acc = nullptr;
+    ROM_CUDA(cudaMalloc(&acc, 2 * sizeof(double)));
+    cudaError_t e = cudaMemsetAsync(acc, 0, 2 * sizeof(double), st);
+    if (e == cudaSuccess) e = launch_rel_l2(x, x_dtype, ref, ref_dtype, n, acc, st);
+    double hacc[2] = {0.0, 0.0};
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hacc, acc, sizeof(hacc), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    cudaFree(acc);
+    if (e != cudaSuccess) return cuda_fail(e, "rom_rel_l2");
+    *out = hacc[1] > 0.0 ? sqrt(hacc[0] / hacc[1]) : sqrt(hacc[0]);
+    return ROM_OK;
+}
+
+}  // extern "C"

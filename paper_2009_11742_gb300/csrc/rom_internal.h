@@ -1,0 +1,90 @@
+// Internal declarations of librom (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+
+#include "../../include/rom.h"
+
+namespace romk {
+
+// Arguments of one rank-2 launch (all device pointers).  Element type T of
+// the state-like buffers is double for ROM_FP64 and float otherwise.
+struct Rank2Args {
+    const void* Avs_rm;  // Kp x Kp row-major, zero padded (T)
+    const void* Asv_rm;  // Kp x Kp row-major, zero padded (T)
+    const void* g_p;     // Kp (T)
+    const void* C_p;     // R x Kp row-major (T); may be null when R == 0
+    void* V;             // Kv x Mtot column-major (T)
+    void* S;             // Ks x Mtot column-major (T)
+    void* compV;         // optional Kahan carry, Kv x Mtot float
+    void* compS;         // optional Kahan carry, Ks x Mtot float
+    const void* Tper;    // Mtot Ricker periods (T) or null
+    const void* ftab;    // nsteps x Mtot forcing table (T) or null
+    void* traces;        // nrec x Mtot x R (T) or null
+    int* status;         // device status word
+    double dt;
+    long long n0;
+    int Kv, Ks, Kp, R;
+    int M;         // columns covered by this launch
+    int Mtot;      // columns of the caller's arrays (leading extent of ftab rows)
+    int col_base;  // first caller column covered by this launch
+    int Wv;        // valid columns per cluster
+    int Wa;        // allocated columns per cluster (multiple of the column group)
+    int nsteps;
+    int r;         // trace interval (> 0 when traces != null)
+    int rpc;       // trace rows of C per CTA
+};
+
+// Launch plan chosen by the host for a rank-2 call.
+struct Rank2Plan {
+    int cs;        // cluster size (CTAs)
+    int KI;        // 64-wide k groups per thread
+    int cb;        // columns per register group
+    int Wv, Wa;    // valid / allocated columns per cluster
+    int nclusters; // clusters launched
+    int max_active_clusters;
+    size_t smem;
+    bool resident; // operators kept in registers for the whole run
+};
+
+// Host launchers (defined in the kernel translation units).  Return a CUDA
+// error code; `plan` must come from plan_rank2_simt.
+cudaError_t launch_rank2_simt_f32(const Rank2Args& a, const Rank2Plan& plan, cudaStream_t st);
+cudaError_t launch_rank2_simt_f64(const Rank2Args& a, const Rank2Plan& plan, cudaStream_t st);
+// Fill `plan` for M columns; returns false if the shape is not supported.
+bool plan_rank2_simt_f32(int Kp, int M, int R, bool rank1, Rank2Plan* plan);
+bool plan_rank2_simt_f64(int Kp, int M, int R, bool rank1, Rank2Plan* plan);
+
+// Rank-1 ensemble (one realization per CTA, operators streamed every step).
+struct Rank1EnsArgs {
+    const void* Avs_cm;  // Kp x Kp column-major, zero padded (T)
+    const void* Asv_cm;
+    const void* g_p;
+    const void* C_cm;    // Kp x R: column j is row j of C (T), may be null
+    void* V;
+    void* S;
+    const void* Tper;
+    void* traces;
+    int* status;
+    double dt;
+    long long n0;
+    int Kv, Ks, Kp, R, M, nsteps, r;
+};
+cudaError_t launch_rank1_ensemble_f32(const Rank1EnsArgs& a, cudaStream_t st);
+cudaError_t launch_rank1_ensemble_f64(const Rank1EnsArgs& a, cudaStream_t st);
+
+// FP64 utilities.
+cudaError_t launch_matvec_f64(const double* A_rm, int rows, int cols, int ld, const double* x,
+                              double* y, cudaStream_t st);
+cudaError_t launch_power_step(const double* y, double* x, int n, double* lam_out, int it,
+                              cudaStream_t st);
+cudaError_t launch_rel_l2(const void* x, int xd, const void* ref, int rd, size_t n,
+                          double* acc2, cudaStream_t st);
+// Padded / transposed copies: dst (Kp x Kp, row-major when rm) from a column-major
+// rows x cols source of element type src_dtype (0 = f64, 1 = f32).
+cudaError_t launch_pad_copy(const void* src, int src_dtype, int rows, int cols, int Kp_rows,
+                            int Kp_cols, bool row_major_out, void* dst, int dst_dtype,
+                            cudaStream_t st);
+
+}  // namespace romk

@@ -1,0 +1,362 @@
+"""ctypes binding of librom.so (C ABI in include/rom.h).
+
+Argument marshalling only: every step of the integration runs in the CUDA
+library.  If the library has not been built, every call raises; there is no
+CPU fallback.
+
+The low-level functions keep the C names (``rom_create``, ``rom_run_rank2``,
+...) and take raw pointers.  ``Rom`` wraps a handle and accepts torch tensors
+(device or host) or numpy arrays, checking shapes, dtypes and the
+column-major layout the ABI wants:
+
+* states are logical (K, M) tensors stored column-major, i.e. the transpose of
+  a contiguous (M, K) tensor -- ``Rom.new_state`` makes one;
+* trace buffers are contiguous (nrec, M, R) tensors (record k is R x M
+  column-major); ``Rom.trace_view`` gives the logical (nrec, R, M) view.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "librom.so")
+
+ROM_OK, ROM_E_INVAL, ROM_E_NOMEM, ROM_E_CUDA, ROM_E_UNSTABLE, ROM_E_TIMEOUT, \
+    ROM_E_NONFINITE, ROM_E_UNSUPPORTED = range(8)
+ROM_FP64, ROM_FP32, ROM_TF32X3, ROM_BF16X3, ROM_BF16 = range(5)
+ROM_IN_F64, ROM_IN_F32 = 0, 1
+PRECISIONS = {"fp64": ROM_FP64, "fp32": ROM_FP32, "tf32x3": ROM_TF32X3,
+              "bf16x3": ROM_BF16X3, "bf16": ROM_BF16}
+
+EXPORTED = ["rom_create", "rom_destroy", "rom_spectral_radius", "rom_sync_status",
+            "rom_get_dims", "rom_run_rank2", "rom_run_rank2_ex", "rom_run_rank1",
+            "rom_run_rank1_ensemble", "rom_rel_l2", "rom_status_string", "rom_last_error",
+            "rom_version"]
+
+_lock = threading.Lock()
+_lib = None
+_vp = ctypes.c_void_p
+_i = ctypes.c_int
+_l = ctypes.c_long
+_d = ctypes.c_double
+
+
+class RomError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        self.status = status
+        super().__init__(f"{what}: {status_string(status)} ({last_error()})")
+
+
+def _signatures(lib):
+    sig = {
+        "rom_create": (_i, [_vp, _vp, _vp, _vp, _i, _i, _i, _d, _i, ctypes.POINTER(_vp),
+                            ctypes.POINTER(_d)]),
+        "rom_destroy": (_i, [_vp]),
+        "rom_spectral_radius": (_i, [_vp, ctypes.POINTER(_d)]),
+        "rom_sync_status": (_i, [_vp, ctypes.POINTER(_i)]),
+        "rom_get_dims": (_i, [_vp, ctypes.POINTER(_i), ctypes.POINTER(_i), ctypes.POINTER(_i),
+                              ctypes.POINTER(_d)]),
+        "rom_run_rank2": (_i, [_vp, _vp, _vp, _vp, _i, _i, _l, _i, _vp, _i, _vp]),
+        "rom_run_rank2_ex": (_i, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _i, _i, _l, _i, _vp, _i,
+                                  _vp]),
+        "rom_run_rank1": (_i, [_vp, _vp, _vp, _d, _i, _l, _i, _vp, _i, _vp]),
+        "rom_run_rank1_ensemble": (_i, [_vp, _vp, _vp, _vp, _i, _i, _l, _i, _vp, _i, _vp]),
+        "rom_rel_l2": (_i, [_vp, _i, _vp, _i, ctypes.c_size_t, ctypes.POINTER(_d), _vp]),
+        "rom_status_string": (ctypes.c_char_p, [_i]),
+        "rom_last_error": (ctypes.c_char_p, []),
+        "rom_version": (_i, []),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+
+
+def load(path: str | None = None):
+    """Load librom.so (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            p = path or LIB_PATH
+            if not os.path.exists(p):
+                raise RuntimeError(
+                    f"librom.so not found at {p}: build it with "
+                    "`python -m paper_2009_11742_gb300.build` (no CPU fallback exists)")
+            lib = ctypes.CDLL(p)
+            _signatures(lib)
+            _lib = lib
+    return _lib
+
+
+def status_string(s: int) -> str:
+    return load().rom_status_string(int(s)).decode()
+
+
+def last_error() -> str:
+    return load().rom_last_error().decode()
+
+
+def _chk(st: int, what: str):
+    if st != ROM_OK:
+        raise RomError(st, what)
+
+
+# ------------------------------------------------------------ raw C calls --
+def rom_create(Avs, Asv, g, C, Kv, Ks, R, dt, in_dtype):
+    h = _vp()
+    rho = _d(0.0)
+    st = load().rom_create(Avs, Asv, g, C, Kv, Ks, R, dt, in_dtype, ctypes.byref(h),
+                           ctypes.byref(rho))
+    return st, h.value, rho.value
+
+
+def rom_destroy(h):
+    return load().rom_destroy(h)
+
+
+def rom_spectral_radius(h):
+    rho = _d(0.0)
+    st = load().rom_spectral_radius(h, ctypes.byref(rho))
+    return st, rho.value
+
+
+def rom_sync_status(h):
+    s = _i(0)
+    st = load().rom_sync_status(h, ctypes.byref(s))
+    return st, s.value
+
+
+def rom_get_dims(h):
+    Kv, Ks, R, dt = _i(0), _i(0), _i(0), _d(0.0)
+    st = load().rom_get_dims(h, ctypes.byref(Kv), ctypes.byref(Ks), ctypes.byref(R),
+                             ctypes.byref(dt))
+    return st, Kv.value, Ks.value, R.value, dt.value
+
+
+def rom_status_string(s):
+    return load().rom_status_string(int(s))
+
+
+def rom_last_error():
+    return load().rom_last_error()
+
+
+def rom_version():
+    return load().rom_version()
+
+
+def rom_run_rank2(h, V, S, T, M, nsteps, n0, r, traces, prec, stream):
+    return load().rom_run_rank2(h, V, S, T, M, nsteps, n0, r, traces, prec, stream)
+
+
+def rom_run_rank2_ex(h, V, S, T, ftab, compV, compS, M, nsteps, n0, r, traces, prec, stream):
+    return load().rom_run_rank2_ex(h, V, S, T, ftab, compV, compS, M, nsteps, n0, r, traces,
+                                   prec, stream)
+
+
+def rom_run_rank1(h, v, s, T, nsteps, n0, r, trace, prec, stream):
+    return load().rom_run_rank1(h, v, s, T, nsteps, n0, r, trace, prec, stream)
+
+
+def rom_run_rank1_ensemble(h, V, S, T, M, nsteps, n0, r, traces, prec, stream):
+    return load().rom_run_rank1_ensemble(h, V, S, T, M, nsteps, n0, r, traces, prec, stream)
+
+
+def rom_rel_l2(x, x_dtype, ref, ref_dtype, n, stream=None):
+    out = _d(0.0)
+    st = load().rom_rel_l2(x, x_dtype, ref, ref_dtype, n, ctypes.byref(out), stream)
+    return st, out.value
+
+
+# ------------------------------------------------------------ tensor glue --
+def _torch():
+    import torch
+    return torch
+
+
+def _ptr(x):
+    """Address of a torch tensor / numpy array (None passes through)."""
+    if x is None:
+        return None
+    if isinstance(x, np.ndarray):
+        return x.ctypes.data
+    return x.data_ptr()
+
+
+def _stream_handle(stream):
+    if stream is None:
+        torch = _torch()
+        if torch.cuda.is_available():
+            return torch.cuda.current_stream().cuda_stream
+        return None
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _check_colmajor(x, K, M, name, dtype):
+    torch = _torch()
+    if isinstance(x, np.ndarray):
+        if x.dtype != dtype or x.shape != (K, M) or not x.flags["F_CONTIGUOUS"]:
+            raise ValueError(f"{name}: need a Fortran-ordered {dtype} array of shape {(K, M)}")
+        return
+    tdt = torch.float64 if dtype == np.float64 else torch.float32
+    if x.dtype != tdt or tuple(x.shape) != (K, M):
+        raise ValueError(f"{name}: need {tdt} of shape {(K, M)}, got {x.dtype} {tuple(x.shape)}")
+    if M > 1 and K > 1 and tuple(x.stride()) != (1, K):
+        raise ValueError(f"{name}: must be column-major (strides (1, {K})); use Rom.new_state")
+
+
+def _check_vec(x, n, name, dtype):
+    torch = _torch()
+    if isinstance(x, np.ndarray):
+        if x.dtype != dtype or x.size != n or not x.flags["C_CONTIGUOUS"]:
+            raise ValueError(f"{name}: need a contiguous {dtype} array with {n} elements")
+        return
+    tdt = torch.float64 if dtype == np.float64 else torch.float32
+    if x.dtype != tdt or x.numel() != n or not x.is_contiguous():
+        raise ValueError(f"{name}: need a contiguous {tdt} tensor with {n} elements")
+
+
+class Rom:
+    """A reduced model resident on the current CUDA device."""
+
+    def __init__(self, Avs, Asv, g, C=None, dt=None):
+        Avs = np.asfortranarray(np.asarray(Avs, dtype=np.float64))
+        Asv = np.asfortranarray(np.asarray(Asv, dtype=np.float64))
+        g = np.ascontiguousarray(np.asarray(g, dtype=np.float64))
+        self.Kv, self.Ks = Avs.shape
+        if Asv.shape != (self.Ks, self.Kv) or g.shape != (self.Kv,):
+            raise ValueError("shape mismatch: Avs (Kv,Ks), Asv (Ks,Kv), g (Kv,)")
+        if C is None or np.asarray(C).size == 0:
+            Cm, self.R = None, 0
+        else:
+            Cm = np.asfortranarray(np.asarray(C, dtype=np.float64))
+            self.R = Cm.shape[0]
+            if Cm.shape[1] != self.Kv:
+                raise ValueError("C must be (R, Kv)")
+        if dt is None:
+            raise ValueError("dt is required")
+        self.dt = float(dt)
+        st, h, rho = rom_create(_ptr(Avs), _ptr(Asv), _ptr(g), _ptr(Cm), self.Kv, self.Ks,
+                                self.R, self.dt, ROM_IN_F64)
+        self.rho = rho
+        _chk(st, "rom_create")
+        self.h = h
+
+    @classmethod
+    def from_problem(cls, p):
+        return cls(p.Avs, p.Asv, p.g, p.C if p.C.shape[0] else None, p.dt)
+
+    def close(self):
+        if getattr(self, "h", None):
+            rom_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ------------------------------------------------------------ helpers
+    @staticmethod
+    def dtype_of(prec):
+        return np.float64 if PRECISIONS.get(prec, prec) == ROM_FP64 else np.float32
+
+    @staticmethod
+    def new_state(K, M, prec="fp32", device="cuda", fill=None):
+        """A column-major (K, M) state tensor (transpose of a contiguous (M, K))."""
+        torch = _torch()
+        dt = torch.float64 if Rom.dtype_of(prec) == np.float64 else torch.float32
+        x = torch.zeros((M, K), dtype=dt, device=device)
+        if fill is not None:
+            x.copy_(torch.as_tensor(np.asarray(fill).T, dtype=dt))
+        return x.t()
+
+    @staticmethod
+    def trace_view(traces):
+        """Logical (nrec, R, M) view of a (nrec, M, R) trace buffer."""
+        return traces.transpose(1, 2) if hasattr(traces, "transpose") and not isinstance(
+            traces, np.ndarray) else np.transpose(traces, (0, 2, 1))
+
+    def spectral_radius(self):
+        st, rho = rom_spectral_radius(self.h)
+        _chk(st, "rom_spectral_radius")
+        return rho
+
+    def sync_status(self):
+        st, dev = rom_sync_status(self.h)
+        _chk(st, "rom_sync_status")
+        return dev
+
+    # ------------------------------------------------------------ integrate
+    def run_rank2(self, V, S, T, nsteps, n0=0, r=0, traces=None, prec="fp32", stream=None,
+                  ftab=None, compV=None, compS=None):
+        p = PRECISIONS.get(prec, prec)
+        dt = self.dtype_of(p)
+        M = V.shape[1]
+        _check_colmajor(V, self.Kv, M, "V", dt)
+        _check_colmajor(S, self.Ks, M, "S", dt)
+        if T is not None:
+            _check_vec(T, M, "T", dt)
+        if ftab is not None:
+            _check_vec(ftab, nsteps * M, "ftab", dt)
+        if traces is not None:
+            nrec = nsteps // r if r > 0 else 0
+            _check_vec(traces, nrec * M * self.R, "traces", dt)
+        if compV is not None:
+            _check_colmajor(compV, self.Kv, M, "compV", np.float32)
+            _check_colmajor(compS, self.Ks, M, "compS", np.float32)
+        sh = _stream_handle(stream)
+        if ftab is None and compV is None:
+            st = rom_run_rank2(self.h, _ptr(V), _ptr(S), _ptr(T), M, int(nsteps), int(n0),
+                               int(r), _ptr(traces), p, sh)
+        else:
+            st = rom_run_rank2_ex(self.h, _ptr(V), _ptr(S), _ptr(T), _ptr(ftab), _ptr(compV),
+                                  _ptr(compS), M, int(nsteps), int(n0), int(r), _ptr(traces),
+                                  p, sh)
+        _chk(st, "rom_run_rank2")
+
+    def run_rank1(self, v, s, T, nsteps, n0=0, r=0, trace=None, prec="fp32", stream=None):
+        p = PRECISIONS.get(prec, prec)
+        dt = self.dtype_of(p)
+        _check_vec(v, self.Kv, "v", dt)
+        _check_vec(s, self.Ks, "s", dt)
+        if trace is not None:
+            _check_vec(trace, (nsteps // r) * self.R, "trace", dt)
+        st = rom_run_rank1(self.h, _ptr(v), _ptr(s), float(T), int(nsteps), int(n0), int(r),
+                           _ptr(trace), p, _stream_handle(stream))
+        _chk(st, "rom_run_rank1")
+
+    def run_rank1_ensemble(self, V, S, T, nsteps, n0=0, r=0, traces=None, prec="fp32",
+                           stream=None):
+        p = PRECISIONS.get(prec, prec)
+        dt = self.dtype_of(p)
+        M = V.shape[1]
+        _check_colmajor(V, self.Kv, M, "V", dt)
+        _check_colmajor(S, self.Ks, M, "S", dt)
+        _check_vec(T, M, "T", dt)
+        if traces is not None:
+            _check_vec(traces, (nsteps // r) * M * self.R, "traces", dt)
+        st = rom_run_rank1_ensemble(self.h, _ptr(V), _ptr(S), _ptr(T), M, int(nsteps), int(n0),
+                                    int(r), _ptr(traces), p, _stream_handle(stream))
+        _chk(st, "rom_run_rank1_ensemble")
+
+
+def rel_l2(x, ref, stream=None) -> float:
+    """FP64 relative L2 error of two device tensors, computed on the GPU."""
+    torch = _torch()
+    dmap = {torch.float64: ROM_IN_F64, torch.float32: ROM_IN_F32}
+    if x.numel() != ref.numel():
+        raise ValueError("size mismatch")
+    xc = x.contiguous()
+    rc = ref.contiguous()
+    st, v = rom_rel_l2(xc.data_ptr(), dmap[xc.dtype], rc.data_ptr(), dmap[rc.dtype],
+                       xc.numel(), _stream_handle(stream))
+    _chk(st, "rom_rel_l2")
+    return v

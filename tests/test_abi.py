@@ -1,0 +1,69 @@
+"""Host-side checks of the C ABI (no GPU needed): the library builds for
+sm_103a, loads, and exports every entry point include/rom.h declares."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_symbols():
+    src = open(os.path.join(ROOT, "include", "rom.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(rom_[a-z0-9_]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2009_11742_gb300 import build
+    path = build.build()
+    return ctypes.CDLL(path)
+
+
+def test_header_declares_the_boundary():
+    syms = declared_symbols()
+    for name in ["rom_create", "rom_destroy", "rom_run_rank1", "rom_run_rank2",
+                 "rom_spectral_radius", "rom_status_string"]:
+        assert name in syms
+
+
+def test_library_exports_every_declared_symbol(lib):
+    missing = [s for s in declared_symbols() if not hasattr(lib, s)]
+    assert not missing, missing
+
+
+def test_binding_names_match_header():
+    from paper_2009_11742_gb300 import rom
+    assert sorted(rom.EXPORTED) == declared_symbols()
+    for s in rom.EXPORTED:
+        assert callable(getattr(rom, s, None)), s
+
+
+def test_status_strings_without_gpu(lib):
+    lib.rom_status_string.restype = ctypes.c_char_p
+    assert lib.rom_status_string(0) == b"ROM_OK"
+    assert b"UNSTABLE" in lib.rom_status_string(4)
+    assert lib.rom_version() >= 100
+
+
+def test_null_arguments_rejected_without_gpu(lib):
+    """Argument checks happen before any CUDA call."""
+    h = ctypes.c_void_p()
+    rc = lib.rom_create(None, None, None, None, 4, 4, 0, ctypes.c_double(0.1), 0,
+                        ctypes.byref(h), None)
+    assert rc == 1  # ROM_E_INVAL
+    rc = lib.rom_run_rank2(None, None, None, None, 1, 1, ctypes.c_long(0), 0, None, 1, None)
+    assert rc == 1
+
+
+def test_missing_library_fails_loudly(tmp_path):
+    from paper_2009_11742_gb300 import rom
+    with pytest.raises(RuntimeError, match="not found"):
+        old = rom._lib
+        rom._lib = None
+        try:
+            rom.load(str(tmp_path / "nope.so"))
+        finally:
+            rom._lib = old

@@ -1,0 +1,258 @@
+"""GPU parity of the rank-2 / rank-1 leapfrog against the FP64 oracle, through
+the C ABI (librom.so).  Tolerances: relative L2 (Eq. (errors), Sec. 4.4) of
+final V, final S and the traces; <= 1e-12 for the FP64 path, <= 1e-4 for the
+FP32 path."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2009_11742_gb300 import inputs
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp64": 1e-12, "fp32": 1e-4}
+
+
+def rel(a, b):
+    a = np.asarray(a, np.float64)
+    b = np.asarray(b, np.float64)
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+@pytest.fixture(scope="module")
+def rom():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2009_11742_gb300 import build
+    build.build()
+    from paper_2009_11742_gb300 import rom as R
+    return R
+
+
+def tdt(prec):
+    return torch.float64 if prec == "fp64" else torch.float32
+
+
+def gpu_run(R, h, p, V0, S0, nsteps, prec, r=0, n0=0, T=None, ftab=None, comp=False):
+    """Run rank-2 on the GPU; returns numpy (V, S, traces (nrec, R, M))."""
+    M = V0.shape[1]
+    V = R.Rom.new_state(p.Kv, M, prec, fill=V0)
+    S = R.Rom.new_state(p.Ks, M, prec, fill=S0)
+    Tt = None
+    if ftab is None:
+        Tt = torch.as_tensor(np.asarray(p.T if T is None else T), dtype=tdt(prec), device="cuda")
+    ft = None if ftab is None else torch.as_tensor(ftab, dtype=tdt(prec), device="cuda").contiguous()
+    nrec = nsteps // r if (r and p.R) else 0
+    tr = torch.zeros((nrec, M, p.R), dtype=tdt(prec), device="cuda") if nrec else None
+    h.run_rank2(V, S, Tt, nsteps, n0=n0, r=r if nrec else 0, traces=tr, prec=prec, ftab=ft)
+    torch.cuda.synchronize()
+    assert h.sync_status() == 0
+    trn = None if tr is None else tr.transpose(1, 2).cpu().numpy()
+    return V.cpu().numpy(), S.cpu().numpy(), trn
+
+
+def test_spectral_radius_matches_numpy(rom):
+    for K in (8, 128, 300, 512):
+        p = inputs.make_problem(K, K, 1, 0, seed=K)
+        h = rom.Rom.from_problem(p)
+        ref = np.linalg.norm(p.Asv.astype(np.float64), 2)
+        assert abs(h.spectral_radius() - ref) / ref < 1e-8
+        h.close()
+
+
+def test_unstable_dt_refused(rom):
+    p = inputs.make_problem(64, 64, 1, 0, seed=3)
+    with pytest.raises(rom.RomError) as ei:
+        rom.Rom(p.Avs, p.Asv, p.g, None, dt=4.1 / np.linalg.norm(p.Asv.astype(np.float64), 2))
+    assert ei.value.status == rom.ROM_E_UNSTABLE
+
+
+def test_config0_fp64(rom):
+    """Workload 0: K = 128, M = 16, 1000 steps, FP64 check path, zero X0."""
+    p = inputs.config(0)
+    h = rom.Rom.from_problem(p)
+    Z = np.zeros((128, 16))
+    V, S, _ = gpu_run(rom, h, p, Z, Z, 1000, "fp64")
+    Vo, So, _ = oracle.problem_forward(p, nsteps=1000, r=0)
+    assert rel(V, Vo) <= TOL["fp64"] and rel(S, So) <= TOL["fp64"]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("Kv,Ks,M,R,N,r", [(100, 90, 37, 5, 300, 7),   # ragged rows and columns
+                                           (64, 64, 8, 3, 200, 10),    # one 64-row tile
+                                           (1, 1, 3, 1, 150, 1),       # K = 1
+                                           (200, 256, 20, 64, 120, 4), # Ks > Kv, many receivers
+                                           (512, 512, 19, 16, 80, 8)]) # full 16-CTA cluster
+def test_rank2_vs_oracle_small(rom, prec, Kv, Ks, M, R, N, r):
+    p = inputs.make_problem(Kv, Ks, M, R, seed=Kv + M)
+    h = rom.Rom.from_problem(p)
+    V0 = inputs.random_state(Kv, M, seed=1, scale=0.1)
+    S0 = inputs.random_state(Ks, M, seed=2, scale=0.1)
+    V, S, tr = gpu_run(rom, h, p, V0, S0, N, prec, r=r, n0=3)
+    Vo, So, tro = oracle.forward(p.Avs, p.Asv, p.g, p.C, p.dt, V0, S0, N, T=p.T, n0=3, r=r)
+    tol = TOL[prec]
+    assert rel(V, Vo) <= tol and rel(S, So) <= tol
+    assert rel(tr, tro) <= tol
+
+
+def test_config1_fp32_sampled_columns(rom):
+    """Workload 1 at full size on the GPU (K = 512, M = 256, 10000 steps,
+    R = 64, r = 10) in the bench's launch configuration; the oracle recomputes
+    a sample of columns (columns are independent, Sec. 2.4)."""
+    p = inputs.config(1)
+    h = rom.Rom.from_problem(p)
+    Z = np.zeros((512, 256))
+    V, S, tr = gpu_run(rom, h, p, Z, Z, 10000, "fp32", r=10)
+    cols = np.array([0, 31, 32, 100, 159, 200, 254, 255])
+    Vo, So, tro = oracle.problem_forward(p, nsteps=10000, r=10, columns=cols)
+    assert rel(V[:, cols], Vo) <= 1e-4
+    assert rel(S[:, cols], So) <= 1e-4
+    assert rel(tr[:, :, cols], tro) <= 1e-4
+    # every column is finite and non-trivial
+    assert np.all(np.isfinite(V)) and np.all(np.linalg.norm(V, axis=0) > 0)
+
+
+def test_rank1_equals_rank2_columns(rom):
+    """Rank-2 column m == rank-1 run m (Sec. 2.4, 4.4), both against the oracle."""
+    p = inputs.make_problem(256, 256, 6, 8, seed=12)
+    h = rom.Rom.from_problem(p)
+    Z = np.zeros((256, 6))
+    N, r = 400, 5
+    V2, S2, tr2 = gpu_run(rom, h, p, Z, Z, N, "fp32", r=r)
+    Vo, So, tro = oracle.forward(p.Avs, p.Asv, p.g, p.C, p.dt, Z, Z, N, T=p.T, r=r)
+    for m in (0, 3, 5):
+        for prec in ("fp32", "fp64"):
+            v = torch.zeros(256, dtype=tdt(prec), device="cuda")
+            s = torch.zeros(256, dtype=tdt(prec), device="cuda")
+            tr = torch.zeros((N // r) * 8, dtype=tdt(prec), device="cuda")
+            h.run_rank1(v, s, float(p.T[m]), N, r=r, trace=tr, prec=prec)
+            torch.cuda.synchronize()
+            tol = TOL[prec]
+            assert rel(v.cpu().numpy(), Vo[:, m]) <= tol
+            assert rel(s.cpu().numpy(), So[:, m]) <= tol
+            assert rel(tr.cpu().numpy().reshape(N // r, 8), tro[:, :, m]) <= tol
+        assert rel(V2[:, m], Vo[:, m]) <= 1e-4
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_rank1_ensemble_vs_oracle(rom, prec):
+    p = inputs.make_problem(192, 160, 11, 4, seed=13)
+    h = rom.Rom.from_problem(p)
+    V0 = inputs.random_state(192, 11, seed=3, scale=0.1)
+    S0 = inputs.random_state(160, 11, seed=4, scale=0.1)
+    N, r = 300, 6
+    V = rom.Rom.new_state(192, 11, prec, fill=V0)
+    S = rom.Rom.new_state(160, 11, prec, fill=S0)
+    T = torch.as_tensor(p.T, dtype=tdt(prec), device="cuda")
+    tr = torch.zeros((N // r, 11, 4), dtype=tdt(prec), device="cuda")
+    h.run_rank1_ensemble(V, S, T, N, n0=2, r=r, traces=tr, prec=prec)
+    torch.cuda.synchronize()
+    Vo, So, tro = oracle.forward(p.Avs, p.Asv, p.g, p.C, p.dt, V0, S0, N, T=p.T, n0=2, r=r)
+    tol = TOL[prec]
+    assert rel(V.cpu().numpy(), Vo) <= tol and rel(S.cpu().numpy(), So) <= tol
+    assert rel(tr.transpose(1, 2).cpu().numpy(), tro) <= tol
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_zero_in_zero_out_bitwise(rom, prec):
+    p = inputs.make_problem(128, 96, 9, 4, seed=14)
+    h = rom.Rom.from_problem(p)
+    Z1, Z2 = np.zeros((128, 9)), np.zeros((96, 9))
+    V, S, tr = gpu_run(rom, h, p, Z1, Z2, 100, prec, r=10, ftab=np.zeros((100, 9)))
+    assert not V.any() and not S.any() and not tr.any()
+
+
+def test_superposition_gpu(rom):
+    """LTI superposition with tabulated forcing: Run(X0, f1 + f2) ==
+    Run(X0, f1) + Run(0, f2) (FP64 path, to roundoff)."""
+    p = inputs.make_problem(96, 96, 5, 3, seed=15)
+    h = rom.Rom.from_problem(p)
+    rng = np.random.default_rng(2)
+    V0 = rng.standard_normal((96, 5))
+    S0 = rng.standard_normal((96, 5))
+    f1 = rng.standard_normal((200, 5))
+    f2 = rng.standard_normal((200, 5))
+    Z = np.zeros((96, 5))
+    Va, Sa, ta = gpu_run(rom, h, p, V0, S0, 200, "fp64", r=5, ftab=f1 + f2)
+    Vb, Sb, tb = gpu_run(rom, h, p, V0, S0, 200, "fp64", r=5, ftab=f1)
+    Vc, Sc, tc = gpu_run(rom, h, p, Z, Z, 200, "fp64", r=5, ftab=f2)
+    assert rel(Va, Vb + Vc) < 1e-12 and rel(Sa, Sb + Sc) < 1e-12 and rel(ta, tb + tc) < 1e-12
+    Vo, So, _ = oracle.forward(p.Avs, p.Asv, p.g, p.C, p.dt, V0, S0, 200, ftab=f1 + f2, r=5)
+    assert rel(Va, Vo) < 1e-12
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_chunked_run_is_bitwise_equal(rom, prec):
+    """n0 + the Kahan carries make a run in chunks identical to one long run."""
+    p = inputs.make_problem(160, 160, 10, 4, seed=16)
+    h = rom.Rom.from_problem(p)
+    M, N1, N2, r = 10, 130, 170, 10
+    T = torch.as_tensor(p.T, dtype=tdt(prec), device="cuda")
+
+    def st():
+        return (rom.Rom.new_state(160, M, prec), rom.Rom.new_state(160, M, prec),
+                rom.Rom.new_state(160, M, "fp32"), rom.Rom.new_state(160, M, "fp32"))
+    V, S, cV, cS = st()
+    tr = torch.zeros(((N1 + N2) // r, M, 4), dtype=tdt(prec), device="cuda")
+    h.run_rank2(V, S, T, N1 + N2, r=r, traces=tr, prec=prec, compV=cV, compS=cS)
+    V2, S2, cV2, cS2 = st()
+    t1 = torch.zeros((N1 // r, M, 4), dtype=tdt(prec), device="cuda")
+    t2 = torch.zeros((N2 // r, M, 4), dtype=tdt(prec), device="cuda")
+    h.run_rank2(V2, S2, T, N1, n0=0, r=r, traces=t1, prec=prec, compV=cV2, compS=cS2)
+    h.run_rank2(V2, S2, T, N2, n0=N1, r=r, traces=t2, prec=prec, compV=cV2, compS=cS2)
+    torch.cuda.synchronize()
+    assert torch.equal(V, V2) and torch.equal(S, S2)
+    assert torch.equal(tr, torch.cat([t1, t2]))
+
+
+def test_host_buffers_match_device_buffers(rom):
+    """The synchronous host-buffer path (staged by the library) gives the same
+    bits as the device path."""
+    p = inputs.make_problem(128, 128, 12, 4, seed=17)
+    h = rom.Rom.from_problem(p)
+    N, r = 120, 6
+    Vd, Sd, trd = gpu_run(rom, h, p, np.zeros((128, 12)), np.zeros((128, 12)), N, "fp32", r=r)
+    Vh = np.zeros((128, 12), np.float32, order="F")
+    Sh = np.zeros((128, 12), np.float32, order="F")
+    Th = np.ascontiguousarray(p.T.astype(np.float32))
+    trh = np.zeros((N // r, 12, 4), np.float32)
+    h.run_rank2(Vh, Sh, Th, N, r=r, traces=trh, prec="fp32")
+    np.testing.assert_array_equal(Vh, Vd)
+    np.testing.assert_array_equal(Sh, Sd)
+    np.testing.assert_array_equal(np.transpose(trh, (0, 2, 1)), trd)
+
+
+def test_energy_conserved_fp64_gpu(rom):
+    """Unforced skew system: the discrete energy stays at its initial value."""
+    p = inputs.config(0)
+    h = rom.Rom.from_problem(p)
+    V0 = inputs.random_state(128, 4, seed=1).astype(np.float64)
+    S0 = inputs.random_state(128, 4, seed=2).astype(np.float64)
+    V, S, _ = gpu_run(rom, h, p, V0, S0, 1000, "fp64", ftab=np.zeros((1000, 4)))
+    E0 = oracle.energy(p.Asv, p.dt, V0, S0)
+    E1 = oracle.energy(p.Asv, p.dt, V, S)
+    assert abs(E1 - E0) / E0 < 1e-12
+
+
+def test_nsteps_zero_and_bad_args(rom):
+    p = inputs.make_problem(64, 64, 2, 0, seed=18)
+    h = rom.Rom.from_problem(p)
+    V = rom.Rom.new_state(64, 2, "fp32", fill=np.ones((64, 2)))
+    S = rom.Rom.new_state(64, 2, "fp32")
+    T = torch.as_tensor(p.T, device="cuda")
+    h.run_rank2(V, S, T, 0, prec="fp32")
+    assert torch.all(V == 1)
+    st = rom.rom_run_rank2(h.h, V.data_ptr(), S.data_ptr(), T.data_ptr(), 2, 10, 0, 5,
+                           V.data_ptr(), rom.ROM_FP32, None)
+    assert st == rom.ROM_E_INVAL  # traces without receiver rows
+    st = rom.rom_run_rank2(h.h, V.data_ptr(), S.data_ptr(), T.data_ptr(), 0, 10, 0, 0, None,
+                           rom.ROM_FP32, None)
+    assert st == rom.ROM_E_INVAL
+
+
+def test_rel_l2_gpu(rom):
+    x = torch.randn(1000, dtype=torch.float64, device="cuda")
+    y = x + 1e-3 * torch.randn(1000, dtype=torch.float64, device="cuda")
+    ref = float(torch.linalg.norm(x - y) / torch.linalg.norm(y))
+    assert abs(rom.rel_l2(x, y) - ref) < 1e-12 * 10 + 1e-9 * ref
