@@ -188,6 +188,10 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-check", action="store_true", help="skip the sampled oracle error check")
+    ap.add_argument("--nsteps", type=int, default=None,
+                    help="leapfrog steps per run (default: the workload's 10000; profiling only)")
+    ap.add_argument("--only-rank2", action="store_true",
+                    help="time the rank-2 runs only (no e2e, rank-1, oracle legs; profiling only)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl != "reference":
         args.warmup = 3
@@ -210,7 +214,9 @@ def main():
     rbuild.build()
     from paper_2009_11742_gb300 import inputs, rom
 
-    W = WORKLOAD
+    W = dict(WORKLOAD)
+    if args.nsteps:
+        W["nsteps"] = args.nsteps
     K, M, N, R, r = W["K"], W["M"], W["nsteps"], W["R"], W["r"]
     p = inputs.make_problem(K, K, M, R, seed=W["seed"])
     h = rom.Rom.from_problem(p)
@@ -268,6 +274,14 @@ def main():
     value = world * M * N * args.steps / t_dev
     ms_per_step = 1e3 * t_dev / args.steps
     flops = useful_flops(K, M, N, R, r)
+
+    if args.only_rank2:
+        if rank == 0:
+            print(json.dumps({"only_rank2": True, "value": value, "ms_per_step": ms_per_step,
+                              "nsteps": N, "clocks": clocks}), flush=True)
+        if dist is not None:
+            dist.destroy_process_group()
+        return 0
 
     # ---- end-to-end through the C ABI with pinned host buffers
     Vh = torch.zeros((M, K), dtype=torch.float32).pin_memory().numpy().T
@@ -351,9 +365,12 @@ def main():
             traffic = json.load(open(prof)).get("dram_bytes_per_launch")
         except (OSError, ValueError):
             traffic = None
+    plan = h.plan(M, "fp32")
+    kname = ("rank2_split_kernel<8>" if plan["variant"] == 2
+             else "rank2_simt_kernel<float,8,8,true>")
     roof = {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
             "frac": achieved / fp32_peak, "traffic": traffic,
-            "kernel": "rank2_simt_kernel<float,8,8,true>",
+            "kernel": kname, "plan": plan,
             "peak_basis": f"{nsm} SMs x {FP32_LANES_PER_SM} FP32 FMA lanes x 2 x "
                           f"{sm_clock_max:.0f} MHz (max SM clock, {pk_kind})"}
     if clocks and clocks.get("sm_mhz"):

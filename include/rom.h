@@ -109,6 +109,45 @@ rom_status rom_sync_status(rom_t h, rom_status* device_status);
 /* Model dimensions of a handle (any output may be NULL). */
 rom_status rom_get_dims(rom_t h, int* Kv, int* Ks, int* R, double* dt);
 
+/* Kernel selection for the rank-2 FP32 path (the FP64 path always uses the
+ * one-block kernel):
+ *  ROM_KERNEL_AUTO      planner's choice (default: two-block);
+ *  ROM_KERNEL_ONE_BLOCK one column block per cluster, every CTA owns 32 rows
+ *                       of both V and S;
+ *  ROM_KERNEL_TWO_BLOCK two column blocks per cluster half a step apart,
+ *                       velocity rows and stress rows on different CTAs, one
+ *                       cluster barrier per half-step phase;
+ *  ROM_KERNEL_DATAFLOW  the two-block schedule synchronised by per-block
+ *                       mbarriers fed with asynchronous remote stores; its
+ *                       waits are bounded (rom_set_wait_limit).
+ * All compute the same leapfrog (Sec. 3.1) with the same summation order. */
+enum { ROM_KERNEL_AUTO = 0, ROM_KERNEL_ONE_BLOCK = 1, ROM_KERNEL_TWO_BLOCK = 2,
+       ROM_KERNEL_DATAFLOW = 3 };
+rom_status rom_set_kernel(rom_t h, int kernel);
+
+/* The launch plan the handle would use for M realizations at precision prec:
+ * kernel variant (1 or 2), cluster size, columns per column block and number
+ * of clusters (outputs may be NULL).  ROM_E_UNSUPPORTED if no kernel fits. */
+rom_status rom_get_plan(rom_t h, int prec, int M, int* variant, int* cluster_size,
+                        int* cols_per_block, int* nclusters);
+
+/*
+ * rom_set_wait_limit -- bound, in SM clock cycles, on every device-side wait
+ * of the dataflow kernel (a consumer waiting for a producer's rows).  A wait
+ * that runs out makes the kernel stop, leave cleanly, and record
+ * ROM_E_TIMEOUT in the handle's status word (rom_sync_status).  Default
+ * 4e9 cycles (about 2 s), far above any legitimate wait.
+ */
+rom_status rom_set_wait_limit(rom_t h, long long cycles);
+
+/*
+ * rom_debug_inject_stall -- failure injection for tests of the timeout path:
+ * when on, one CTA of every cluster of ROM_KERNEL_DATAFLOW never publishes
+ * its rows, so its peers' waits run out (set a small wait limit first).  The
+ * kernel then ends with ROM_E_TIMEOUT instead of hanging.  Off by default.
+ */
+rom_status rom_debug_inject_stall(rom_t h, int on);
+
 /* ------------------------------------------------------------- integrate */
 
 /*

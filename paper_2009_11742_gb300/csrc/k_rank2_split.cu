@@ -1,0 +1,110 @@
+// Host planning / launch of the two-block split-role FP32 rank-2 kernels:
+// variant 2 (one cluster barrier per phase) and variant 3 (dataflow).
+#include <cuda_runtime.h>
+
+#include "rank2_dataflow.cuh"
+#include "rank2_launch.cuh"
+#include "rank2_split.cuh"
+
+namespace romk {
+
+template <bool DF>
+static void* two_block_kernel(int KI) {
+#define ROM_TB_CASE(k) \
+    case k: return DF ? (void*)&rank2_dataflow_kernel<k> : (void*)&rank2_split_kernel<k>;
+    switch (KI) {
+        ROM_TB_CASE(1) ROM_TB_CASE(2) ROM_TB_CASE(3) ROM_TB_CASE(4)
+        ROM_TB_CASE(5) ROM_TB_CASE(6) ROM_TB_CASE(7) ROM_TB_CASE(8)
+        default: return nullptr;
+    }
+#undef ROM_TB_CASE
+}
+
+template <bool DF>
+static size_t two_block_smem(int Wa, int Kp, int rpc) {
+    return DF ? dataflow_smem_layout(Wa, Kp, rpc).total : split_smem_layout(Wa, Kp, rpc).total;
+}
+
+template <bool DF>
+static bool plan_two_block(int Kp, int M, int R, Rank2Plan* p) {
+    if (Kp <= 0 || Kp % 64 != 0 || Kp > 512 || M <= 0) return false;
+    p->KI = Kp / 64;
+    p->cs = Kp / 32;  // H = Kp / 64 CTAs per role
+    p->cb = kSplitCB;
+    p->resident = true;
+    p->variant = DF ? 3 : 2;
+    const int H = p->cs / 2;
+    const int rpc = (R + H - 1) / H;
+    const int smax = device_smem_optin();
+    int wcap = 0;
+    for (int w = kSplitCB; w <= 2048; w += kSplitCB) {
+        if (two_block_smem<DF>(w, Kp, rpc) > (size_t)smax) break;
+        wcap = w;
+    }
+    if (wcap == 0) return false;
+    void* fn = two_block_kernel<DF>(p->KI);
+    if (!fn) return false;
+    const size_t smem_probe = two_block_smem<DF>(wcap, Kp, rpc);
+    if (prepare_kernel<float>(fn, smem_probe) != cudaSuccess) return false;
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = p->cs;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3(p->cs, 1, 1);
+    cfg.blockDim = dim3(kThreads, 1, 1);
+    cfg.dynamicSmemBytes = smem_probe;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int nact = 0;
+    if (cudaOccupancyMaxActiveClusters(&nact, fn, &cfg) != cudaSuccess || nact <= 0) {
+        cudaGetLastError();
+        return false;
+    }
+    p->max_active_clusters = nact;
+    int wv = (M + 2 * nact - 1) / (2 * nact);
+    wv = ((wv + kSplitCB - 1) / kSplitCB) * kSplitCB;
+    if (wv > wcap) wv = wcap;
+    p->Wv = wv;
+    p->Wa = wv;
+    const int nblocks = (M + wv - 1) / wv;
+    p->nclusters = (nblocks + 1) / 2;
+    p->smem = two_block_smem<DF>(p->Wa, Kp, rpc);
+    return true;
+}
+
+template <bool DF>
+static cudaError_t launch_two_block(const Rank2Args& a_in, const Rank2Plan& p, cudaStream_t st) {
+    Rank2Args a = a_in;
+    a.Wv = p.Wv;
+    a.Wa = p.Wa;
+    const int H = p.cs / 2;
+    a.rpc = (a.R + H - 1) / H;
+    void* fn = two_block_kernel<DF>(p.KI);
+    if (!fn) return cudaErrorInvalidValue;
+    cudaError_t e = prepare_kernel<float>(fn, p.smem);
+    if (e != cudaSuccess) return e;
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = p.cs;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3(p.cs * p.nclusters, 1, 1);
+    cfg.blockDim = dim3(kThreads, 1, 1);
+    cfg.dynamicSmemBytes = p.smem;
+    cfg.stream = st;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    void* args[] = {(void*)&a};
+    return cudaLaunchKernelExC(&cfg, fn, args);
+}
+
+bool plan_rank2_split_f32(int Kp, int M, int R, Rank2Plan* p) { return plan_two_block<false>(Kp, M, R, p); }
+bool plan_rank2_dataflow_f32(int Kp, int M, int R, Rank2Plan* p) { return plan_two_block<true>(Kp, M, R, p); }
+cudaError_t launch_rank2_split_f32(const Rank2Args& a, const Rank2Plan& p, cudaStream_t st) {
+    return p.variant == 3 ? launch_two_block<true>(a, p, st) : launch_two_block<false>(a, p, st);
+}
+
+}  // namespace romk

@@ -75,8 +75,11 @@ struct rom_s {
     int* status = nullptr;
     double* scalar = nullptr;  // small device scratch (rank-1 period)
     DevBuf stage;              // staging of host buffers
-    std::map<std::tuple<int, int, int, int>, Rank2Plan> plans;
+    std::map<std::tuple<int, int, int, int, int>, Rank2Plan> plans;
     std::mutex mu;
+    int kernel_choice = 0;  // ROM_KERNEL_AUTO
+    long long wait_limit = 4000000000LL;  // device wait bound in SM clock cycles (~2 s)
+    int inject_stall = 0;
 };
 
 namespace {
@@ -289,14 +292,27 @@ struct RunBufs {
 
 rom_status get_plan(rom_s* h, int prec, int M, bool rank1, Rank2Plan* plan) {
     std::lock_guard<std::mutex> lk(h->mu);
-    const auto key = std::make_tuple(prec == ROM_FP64 ? 0 : 1, M, rank1 ? 1 : 0, h->R);
+    const auto key = std::make_tuple(prec == ROM_FP64 ? 0 : 1, M, rank1 ? 1 : 0, h->R,
+                                     h->kernel_choice);
     auto it = h->plans.find(key);
     if (it != h->plans.end()) {
         *plan = it->second;
         return ROM_OK;
     }
-    const bool ok = prec == ROM_FP64 ? plan_rank2_simt_f64(h->Kp, M, h->R, rank1, plan)
-                                     : plan_rank2_simt_f32(h->Kp, M, h->R, rank1, plan);
+    bool ok = false;
+    // FP32 with more than one realization: the two-block split-role kernel,
+    // unless the caller pinned the one-block kernel.
+    const bool two_block = prec != ROM_FP64 && !rank1 && h->kernel_choice != ROM_KERNEL_ONE_BLOCK;
+    if (two_block && h->kernel_choice == ROM_KERNEL_DATAFLOW) {
+        ok = plan_rank2_dataflow_f32(h->Kp, M, h->R, plan);
+    } else if (two_block) {
+        ok = plan_rank2_split_f32(h->Kp, M, h->R, plan);
+    }
+    if (!ok && h->kernel_choice != ROM_KERNEL_TWO_BLOCK && h->kernel_choice != ROM_KERNEL_DATAFLOW) {
+        ok = prec == ROM_FP64 ? plan_rank2_simt_f64(h->Kp, M, h->R, rank1, plan)
+                              : plan_rank2_simt_f32(h->Kp, M, h->R, rank1, plan);
+        if (ok) plan->variant = 1;
+    }
     if (!ok) {
         snprintf(g_last_error, sizeof(g_last_error),
                  "no SIMT rank-2 plan for Kp=%d M=%d (prec %d)", h->Kp, M, prec);
@@ -340,8 +356,11 @@ rom_status run_rank2_device(rom_s* h, const RunBufs& b, int M, int nsteps, long 
     a.col_base = 0;
     a.nsteps = nsteps;
     a.r = b.traces ? r : 1;
-    cudaError_t e = prec == ROM_FP64 ? launch_rank2_simt_f64(a, plan, st)
-                                     : launch_rank2_simt_f32(a, plan, st);
+    a.spin_limit = h->wait_limit;
+    a.debug_skip_push = h->inject_stall;
+    cudaError_t e = prec == ROM_FP64   ? launch_rank2_simt_f64(a, plan, st)
+                    : plan.variant >= 2 ? launch_rank2_split_f32(a, plan, st)
+                                        : launch_rank2_simt_f32(a, plan, st);
     if (e != cudaSuccess) return cuda_fail(e, "rank2 launch");
     return ROM_OK;
 }
@@ -434,6 +453,39 @@ rom_status run_common(rom_s* h, void* V, void* S, const void* T, const void* fta
 }  // namespace
 
 extern "C" {
+
+rom_status rom_set_wait_limit(rom_t h, long long cycles) {
+    if (!h || cycles < 1) return ROM_E_INVAL;
+    h->wait_limit = cycles;
+    return ROM_OK;
+}
+
+rom_status rom_debug_inject_stall(rom_t h, int on) {
+    if (!h) return ROM_E_INVAL;
+    h->inject_stall = on ? 1 : 0;
+    return ROM_OK;
+}
+
+rom_status rom_set_kernel(rom_t h, int kernel) {
+    if (!h || kernel < ROM_KERNEL_AUTO || kernel > ROM_KERNEL_DATAFLOW) return ROM_E_INVAL;
+    std::lock_guard<std::mutex> lk(h->mu);
+    h->kernel_choice = kernel;
+    return ROM_OK;
+}
+
+rom_status rom_get_plan(rom_t h, int prec, int M, int* variant, int* cluster_size,
+                        int* cols_per_block, int* nclusters) {
+    if (!h || M < 1 || !valid_prec(prec)) return ROM_E_INVAL;
+    if (prec != ROM_FP64 && prec != ROM_FP32) return ROM_E_UNSUPPORTED;
+    Rank2Plan p;
+    rom_status s = get_plan(h, prec, M, false, &p);
+    if (s != ROM_OK) return s;
+    if (variant) *variant = p.variant;
+    if (cluster_size) *cluster_size = p.cs;
+    if (cols_per_block) *cols_per_block = p.Wv;
+    if (nclusters) *nclusters = p.nclusters;
+    return ROM_OK;
+}
 
 rom_status rom_run_rank2(rom_t h, void* V, void* S, const void* T, int M, int nsteps, long n0,
                          int r, void* traces, int prec, void* stream) {

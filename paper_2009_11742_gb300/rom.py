@@ -29,11 +29,13 @@ ROM_OK, ROM_E_INVAL, ROM_E_NOMEM, ROM_E_CUDA, ROM_E_UNSTABLE, ROM_E_TIMEOUT, \
     ROM_E_NONFINITE, ROM_E_UNSUPPORTED = range(8)
 ROM_FP64, ROM_FP32, ROM_TF32X3, ROM_BF16X3, ROM_BF16 = range(5)
 ROM_IN_F64, ROM_IN_F32 = 0, 1
+ROM_KERNEL_AUTO, ROM_KERNEL_ONE_BLOCK, ROM_KERNEL_TWO_BLOCK, ROM_KERNEL_DATAFLOW = 0, 1, 2, 3
 PRECISIONS = {"fp64": ROM_FP64, "fp32": ROM_FP32, "tf32x3": ROM_TF32X3,
               "bf16x3": ROM_BF16X3, "bf16": ROM_BF16}
 
 EXPORTED = ["rom_create", "rom_destroy", "rom_spectral_radius", "rom_sync_status",
-            "rom_get_dims", "rom_run_rank2", "rom_run_rank2_ex", "rom_run_rank1",
+            "rom_get_dims", "rom_set_kernel", "rom_get_plan", "rom_set_wait_limit",
+            "rom_debug_inject_stall", "rom_run_rank2", "rom_run_rank2_ex", "rom_run_rank1",
             "rom_run_rank1_ensemble", "rom_rel_l2", "rom_status_string", "rom_last_error",
             "rom_version"]
 
@@ -60,6 +62,11 @@ def _signatures(lib):
         "rom_sync_status": (_i, [_vp, ctypes.POINTER(_i)]),
         "rom_get_dims": (_i, [_vp, ctypes.POINTER(_i), ctypes.POINTER(_i), ctypes.POINTER(_i),
                               ctypes.POINTER(_d)]),
+        "rom_set_kernel": (_i, [_vp, _i]),
+        "rom_set_wait_limit": (_i, [_vp, ctypes.c_longlong]),
+        "rom_debug_inject_stall": (_i, [_vp, _i]),
+        "rom_get_plan": (_i, [_vp, _i, _i, ctypes.POINTER(_i), ctypes.POINTER(_i),
+                              ctypes.POINTER(_i), ctypes.POINTER(_i)]),
         "rom_run_rank2": (_i, [_vp, _vp, _vp, _vp, _i, _i, _l, _i, _vp, _i, _vp]),
         "rom_run_rank2_ex": (_i, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _i, _i, _l, _i, _vp, _i,
                                   _vp]),
@@ -135,6 +142,25 @@ def rom_get_dims(h):
     st = load().rom_get_dims(h, ctypes.byref(Kv), ctypes.byref(Ks), ctypes.byref(R),
                              ctypes.byref(dt))
     return st, Kv.value, Ks.value, R.value, dt.value
+
+
+def rom_set_kernel(h, kernel):
+    return load().rom_set_kernel(h, kernel)
+
+
+def rom_set_wait_limit(h, cycles):
+    return load().rom_set_wait_limit(h, int(cycles))
+
+
+def rom_debug_inject_stall(h, on):
+    return load().rom_debug_inject_stall(h, 1 if on else 0)
+
+
+def rom_get_plan(h, prec, M):
+    v, cs, w, nc = _i(0), _i(0), _i(0), _i(0)
+    st = load().rom_get_plan(h, prec, M, ctypes.byref(v), ctypes.byref(cs), ctypes.byref(w),
+                             ctypes.byref(nc))
+    return st, v.value, cs.value, w.value, nc.value
 
 
 def rom_status_string(s):
@@ -288,6 +314,14 @@ class Rom:
         st, rho = rom_spectral_radius(self.h)
         _chk(st, "rom_spectral_radius")
         return rho
+
+    def set_kernel(self, kernel):
+        _chk(rom_set_kernel(self.h, int(kernel)), "rom_set_kernel")
+
+    def plan(self, M, prec="fp32"):
+        st, v, cs, w, nc = rom_get_plan(self.h, PRECISIONS.get(prec, prec), int(M))
+        _chk(st, "rom_get_plan")
+        return {"variant": v, "cluster_size": cs, "cols_per_block": w, "nclusters": nc}
 
     def sync_status(self):
         st, dev = rom_sync_status(self.h)

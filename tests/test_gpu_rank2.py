@@ -34,8 +34,9 @@ def tdt(prec):
     return torch.float64 if prec == "fp64" else torch.float32
 
 
-def gpu_run(R, h, p, V0, S0, nsteps, prec, r=0, n0=0, T=None, ftab=None, comp=False):
+def gpu_run(R, h, p, V0, S0, nsteps, prec, r=0, n0=0, T=None, ftab=None, comp=False, kernel=0):
     """Run rank-2 on the GPU; returns numpy (V, S, traces (nrec, R, M))."""
+    h.set_kernel(kernel)
     M = V0.shape[1]
     V = R.Rom.new_state(p.Kv, M, prec, fill=V0)
     S = R.Rom.new_state(p.Ks, M, prec, fill=S0)
@@ -78,18 +79,20 @@ def test_config0_fp64(rom):
     assert rel(V, Vo) <= TOL["fp64"] and rel(S, So) <= TOL["fp64"]
 
 
-@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("prec,kernel", [("fp64", 0), ("fp32", 1), ("fp32", 2), ("fp32", 3)])
 @pytest.mark.parametrize("Kv,Ks,M,R,N,r", [(100, 90, 37, 5, 300, 7),   # ragged rows and columns
                                            (64, 64, 8, 3, 200, 10),    # one 64-row tile
                                            (1, 1, 3, 1, 150, 1),       # K = 1
                                            (200, 256, 20, 64, 120, 4), # Ks > Kv, many receivers
                                            (512, 512, 19, 16, 80, 8)]) # full 16-CTA cluster
-def test_rank2_vs_oracle_small(rom, prec, Kv, Ks, M, R, N, r):
+def test_rank2_vs_oracle_small(rom, prec, kernel, Kv, Ks, M, R, N, r):
     p = inputs.make_problem(Kv, Ks, M, R, seed=Kv + M)
     h = rom.Rom.from_problem(p)
     V0 = inputs.random_state(Kv, M, seed=1, scale=0.1)
     S0 = inputs.random_state(Ks, M, seed=2, scale=0.1)
-    V, S, tr = gpu_run(rom, h, p, V0, S0, N, prec, r=r, n0=3)
+    V, S, tr = gpu_run(rom, h, p, V0, S0, N, prec, r=r, n0=3, kernel=kernel)
+    if kernel:
+        assert h.plan(M, prec)["variant"] == (1 if prec == "fp64" else kernel)
     Vo, So, tro = oracle.forward(p.Avs, p.Asv, p.g, p.C, p.dt, V0, S0, N, T=p.T, n0=3, r=r)
     tol = TOL[prec]
     assert rel(V, Vo) <= tol and rel(S, So) <= tol
@@ -111,6 +114,20 @@ def test_config1_fp32_sampled_columns(rom):
     assert rel(tr[:, :, cols], tro) <= 1e-4
     # every column is finite and non-trivial
     assert np.all(np.isfinite(V)) and np.all(np.linalg.norm(V, axis=0) > 0)
+
+
+def test_one_block_and_two_block_kernels_agree(rom):
+    """Both FP32 schedules at workload-1 width (K = 512) agree to FP32 rounding
+    and the two-block kernel is what the planner picks."""
+    p = inputs.make_problem(512, 512, 256, 64, seed=0)
+    h = rom.Rom.from_problem(p)
+    Z = np.zeros((512, 256))
+    assert h.plan(256)["variant"] == 2
+    V1, S1, t1 = gpu_run(rom, h, p, Z, Z, 1000, "fp32", r=10, kernel=1)
+    V2, S2, t2 = gpu_run(rom, h, p, Z, Z, 1000, "fp32", r=10, kernel=2)
+    V3, S3, t3 = gpu_run(rom, h, p, Z, Z, 1000, "fp32", r=10, kernel=3)
+    assert rel(V1, V2) < 1e-5 and rel(S1, S2) < 1e-5 and rel(t1, t2) < 1e-5
+    assert rel(V3, V2) < 1e-5 and rel(S3, S2) < 1e-5 and rel(t3, t2) < 1e-5
 
 
 def test_rank1_equals_rank2_columns(rom):
@@ -182,11 +199,12 @@ def test_superposition_gpu(rom):
     assert rel(Va, Vo) < 1e-12
 
 
-@pytest.mark.parametrize("prec", ["fp32", "fp64"])
-def test_chunked_run_is_bitwise_equal(rom, prec):
+@pytest.mark.parametrize("prec,kernel", [("fp32", 1), ("fp32", 2), ("fp32", 3), ("fp64", 0)])
+def test_chunked_run_is_bitwise_equal(rom, prec, kernel):
     """n0 + the Kahan carries make a run in chunks identical to one long run."""
     p = inputs.make_problem(160, 160, 10, 4, seed=16)
     h = rom.Rom.from_problem(p)
+    h.set_kernel(kernel)
     M, N1, N2, r = 10, 130, 170, 10
     T = torch.as_tensor(p.T, dtype=tdt(prec), device="cuda")
 
@@ -256,3 +274,28 @@ def test_rel_l2_gpu(rom):
     y = x + 1e-3 * torch.randn(1000, dtype=torch.float64, device="cuda")
     ref = float(torch.linalg.norm(x - y) / torch.linalg.norm(y))
     assert abs(rom.rel_l2(x, y) - ref) < 1e-12 * 10 + 1e-9 * ref
+
+
+def test_wait_timeout_is_reported_not_hung(rom):
+    """Failure detection without a GPU fault: with stall injection on, one CTA
+    of each cluster never publishes its rows, so its peers' bounded waits run
+    out.  The kernel must leave cleanly, report ROM_E_TIMEOUT through the
+    handle's status word, and leave the context usable."""
+    p = inputs.make_problem(128, 128, 16, 0, seed=20)
+    h = rom.Rom.from_problem(p)
+    h.set_kernel(rom.ROM_KERNEL_DATAFLOW)
+    assert rom.rom_set_wait_limit(h.h, 2_000_000) == rom.ROM_OK  # ~1 ms of SM clock
+    assert rom.rom_debug_inject_stall(h.h, 1) == rom.ROM_OK
+    V = rom.Rom.new_state(128, 16, "fp32")
+    S = rom.Rom.new_state(128, 16, "fp32")
+    T = torch.as_tensor(p.T, device="cuda")
+    h.run_rank2(V, S, T, 50, prec="fp32")
+    torch.cuda.synchronize()
+    assert h.sync_status() == rom.ROM_E_TIMEOUT
+    # injection off, default limit: a normal run on the same handle is correct
+    assert rom.rom_debug_inject_stall(h.h, 0) == rom.ROM_OK
+    assert rom.rom_set_wait_limit(h.h, 4_000_000_000) == rom.ROM_OK
+    Z = np.zeros((128, 16))
+    Vg, Sg, _ = gpu_run(rom, h, p, Z, Z, 200, "fp32", kernel=rom.ROM_KERNEL_DATAFLOW)
+    Vo, So, _ = oracle.forward(p.Avs, p.Asv, p.g, None, p.dt, Z, Z, 200, T=p.T)
+    assert rel(Vg, Vo) <= 1e-4 and rel(Sg, So) <= 1e-4
