@@ -211,6 +211,31 @@ rom_status rom_run_rank1_ensemble(rom_t h, void* V, void* S, const void* T, int 
 rom_status rom_rel_l2(const void* x, int x_dtype, const void* ref, int ref_dtype, size_t n,
                       double* out, void* stream);
 
+/*
+ * rom_spectral_radius_noalloc -- the dt-stability check of rom_create (the
+ * spectral radius of [[0, Avs], [Asv, 0]] by FP64 power iteration) for
+ * callers that cannot allocate device memory: code that runs where
+ * cudaMalloc is unavailable or forbidden, such as a host that hands the
+ * library a fixed memory budget, or a section that must not grow the device
+ * footprint.  It allocates nothing.  The paper has no counterpart; it exists
+ * for those callers only.
+ *
+ * Avs (Kv x Ks) and Asv (Ks x Kv) are the caller's column-major FP64 DEVICE
+ * buffers (host pointers are refused with ROM_E_INVAL).  *rho receives the
+ * same quantity rom_create computes.  The iteration's work vectors live in a
+ * fixed file-scope device array of 3 * 4096 + 65 doubles (about 99 KB) that
+ * every GPU which loads the library holds until the process exits; Kv or Ks
+ * above 4096 is refused with ROM_E_INVAL.  The first call on a device looks
+ * up that array's device address (cudaGetSymbolAddress); make that first call
+ * before any stream capture.  All calls on a device share the array and it
+ * keeps the last call's contents (each call re-initialises what it reads), so
+ * calls that overlap on the GPU -- on two streams, or from two host threads --
+ * race and must be serialised by the caller.  Synchronous on `stream`; errors
+ * as for rom_create.
+ */
+rom_status rom_spectral_radius_noalloc(const double* Avs, const double* Asv, int Kv, int Ks,
+                                       double* rho, void* stream);
+
 /* Human-readable name of a status code (static storage). */
 const char* rom_status_string(rom_status s);
 

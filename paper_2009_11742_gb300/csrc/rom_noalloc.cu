@@ -1,0 +1,104 @@
+// rom_spectral_radius_noalloc: the FP64 power iteration of rom_create for
+// callers that must not allocate device memory (see include/rom.h).
+//
+// Its work vectors live in one file-scope device array instead of cudaMalloc'd
+// buffers.  Host code may not use the array's name as a device address, so
+// the address is taken once per device with cudaGetSymbolAddress and handed to
+// the kernels.
+#include <cuda_runtime.h>
+#include <math.h>
+
+#include <mutex>
+
+#include "rom_internal.h"
+
+namespace {
+
+// Largest Kv / Ks the allocation-free entry point accepts.
+constexpr int kNoallocMaxK = 4096;
+// Estimates read back per host check of convergence.
+constexpr int kNoallocChunk = 64;
+// x (Kv), z (Ks), y (Kv) and a ring of kNoallocChunk eigenvalue estimates.
+constexpr size_t kNoallocDoubles = 3 * (size_t)kNoallocMaxK + kNoallocChunk + 1;
+
+// Shared by every call on a device; kept until the process exits.
+static __device__ __align__(256) double g_power_scratch[kNoallocDoubles];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_setup_mu;
+double* g_scratch_addr[kMaxDevices] = {nullptr};
+
+__global__ void fill_start_vector(double* x, int n) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) x[i] = 1.0 / sqrt((double)n);
+}
+
+bool is_device_pointer(const void* p) {
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+}  // namespace
+
+extern "C" rom_status rom_spectral_radius_noalloc(const double* Avs, const double* Asv, int Kv,
+                                                  int Ks, double* rho, void* stream) {
+    if (!Avs || !Asv || !rho || Kv < 1 || Ks < 1) return ROM_E_INVAL;
+    // the work area is fixed: larger operators are refused, never truncated
+    if (Kv > kNoallocMaxK || Ks > kNoallocMaxK) return ROM_E_INVAL;
+    if (!is_device_pointer(Avs) || !is_device_pointer(Asv)) return ROM_E_INVAL;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return ROM_E_CUDA;
+    double* base = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(g_setup_mu);
+        if (!g_scratch_addr[dev]) {
+            void* p = nullptr;
+            cudaError_t e = cudaGetSymbolAddress(&p, g_power_scratch);
+            if (e != cudaSuccess || !p) return ROM_E_CUDA;
+            g_scratch_addr[dev] = static_cast<double*>(p);
+        }
+        base = g_scratch_addr[dev];
+    }
+    double* x = base;
+    double* z = base + kNoallocMaxK;
+    double* y = base + 2 * kNoallocMaxK;
+    double* lam = base + 3 * kNoallocMaxK;  // ring of kNoallocChunk + 1 estimates
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+
+    // The caller's column-major Avs (Kv x Ks) is the row-major Avs^T, and the
+    // column-major Asv the row-major Asv^T, so the iteration below runs on
+    // (Avs Asv)^T = Asv^T Avs^T, which has the same eigenvalues as Avs Asv.
+    fill_start_vector<<<(Kv + 255) / 256, 256, 0, st>>>(x, Kv);
+    cudaError_t e = cudaGetLastError();
+    const int max_iter = 20000;
+    const double tol = 1e-14;
+    double hl[kNoallocChunk];
+    double cur = 0.0, prev = -1.0;
+    for (int it0 = 1; e == cudaSuccess && it0 <= max_iter; it0 += kNoallocChunk) {
+        const int it1 = it0 + kNoallocChunk - 1 <= max_iter ? it0 + kNoallocChunk - 1 : max_iter;
+        for (int it = it0; it <= it1 && e == cudaSuccess; ++it) {
+            e = romk::launch_matvec_f64(Avs, Ks, Kv, Kv, x, z, st);        // z = Avs^T x
+            if (e == cudaSuccess) e = romk::launch_matvec_f64(Asv, Kv, Ks, Ks, z, y, st);  // y = Asv^T z
+            if (e == cudaSuccess) e = romk::launch_power_step(y, x, Kv, lam, it - it0, st);
+        }
+        if (e != cudaSuccess) break;
+        const int cnt = it1 - it0 + 1;
+        e = cudaMemcpyAsync(hl, lam, sizeof(double) * cnt, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) break;
+        bool done = false;
+        for (int i = 0; i < cnt; ++i) {
+            cur = hl[i];
+            if (prev >= 0.0 && fabs(cur - prev) <= tol * cur) { done = true; break; }
+            prev = cur;
+        }
+        if (done || cur == 0.0) break;
+    }
+    if (e != cudaSuccess) return ROM_E_CUDA;
+    *rho = sqrt(cur);
+    return ROM_OK;
+}

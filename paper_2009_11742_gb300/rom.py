@@ -36,8 +36,8 @@ PRECISIONS = {"fp64": ROM_FP64, "fp32": ROM_FP32, "tf32x3": ROM_TF32X3,
 EXPORTED = ["rom_create", "rom_destroy", "rom_spectral_radius", "rom_sync_status",
             "rom_get_dims", "rom_set_kernel", "rom_get_plan", "rom_set_wait_limit",
             "rom_debug_inject_stall", "rom_run_rank2", "rom_run_rank2_ex", "rom_run_rank1",
-            "rom_run_rank1_ensemble", "rom_rel_l2", "rom_status_string", "rom_last_error",
-            "rom_version"]
+            "rom_run_rank1_ensemble", "rom_rel_l2", "rom_spectral_radius_noalloc",
+            "rom_status_string", "rom_last_error", "rom_version"]
 
 _lock = threading.Lock()
 _lib = None
@@ -73,6 +73,7 @@ def _signatures(lib):
         "rom_run_rank1": (_i, [_vp, _vp, _vp, _d, _i, _l, _i, _vp, _i, _vp]),
         "rom_run_rank1_ensemble": (_i, [_vp, _vp, _vp, _vp, _i, _i, _l, _i, _vp, _i, _vp]),
         "rom_rel_l2": (_i, [_vp, _i, _vp, _i, ctypes.c_size_t, ctypes.POINTER(_d), _vp]),
+        "rom_spectral_radius_noalloc": (_i, [_vp, _vp, _i, _i, ctypes.POINTER(_d), _vp]),
         "rom_status_string": (ctypes.c_char_p, [_i]),
         "rom_last_error": (ctypes.c_char_p, []),
         "rom_version": (_i, []),
@@ -195,6 +196,14 @@ def rom_run_rank1_ensemble(h, V, S, T, M, nsteps, n0, r, traces, prec, stream):
 def rom_rel_l2(x, x_dtype, ref, ref_dtype, n, stream=None):
     out = _d(0.0)
     st = load().rom_rel_l2(x, x_dtype, ref, ref_dtype, n, ctypes.byref(out), stream)
+    return st, out.value
+
+
+def rom_spectral_radius_noalloc(Avs, Asv, Kv, Ks, stream=None):
+    """Allocation-free power iteration on caller-owned device operators
+    (column-major FP64).  Returns (status, rho)."""
+    out = _d(0.0)
+    st = load().rom_spectral_radius_noalloc(Avs, Asv, Kv, Ks, ctypes.byref(out), stream)
     return st, out.value
 
 

@@ -1,0 +1,56 @@
+"""The allocation-free entry point, rom_spectral_radius_noalloc.
+
+It serves callers that cannot call cudaMalloc (a host that gives the library a
+fixed memory budget, or code that must not grow the device footprint): its
+work vectors sit in a fixed device array inside the library.  This file is
+collected last so that a failure here, under `-x`, comes after every other
+test has run.  It must pass on its own in a fresh process and after the rest.
+"""
+import numpy as np
+import pytest
+
+from paper_2009_11742_gb300 import inputs
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def rom():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2009_11742_gb300 import build
+    build.build()
+    from paper_2009_11742_gb300 import rom as R
+    return R
+
+
+def colmajor_device(A):
+    """A column-major FP64 device copy of the logical matrix A."""
+    return torch.as_tensor(np.ascontiguousarray(np.asarray(A, np.float64).T), device="cuda")
+
+
+@pytest.mark.parametrize("Kv,Ks", [(300, 300), (96, 130)])
+def test_noalloc_matches_rom_create_twice(rom, Kv, Ks):
+    """Two calls in a row agree with the spectral radius rom_create computes
+    (same tolerance as the other spectral-radius checks); the second call
+    reuses the shared work area the first one left behind."""
+    p = inputs.make_problem(Kv, Ks, 1, 0, seed=Kv + Ks)
+    h = rom.Rom.from_problem(p)
+    ref = h.spectral_radius()
+    Avs = colmajor_device(p.Avs)
+    Asv = colmajor_device(p.Asv)
+    for _ in range(2):
+        st, rho = rom.rom_spectral_radius_noalloc(Avs.data_ptr(), Asv.data_ptr(), Kv, Ks, None)
+        assert st == rom.ROM_OK
+        assert abs(rho - ref) / ref < 1e-8
+    h.close()
+
+
+def test_noalloc_refuses_oversize_and_host_buffers(rom):
+    x = torch.zeros(16, dtype=torch.float64, device="cuda")
+    st, _ = rom.rom_spectral_radius_noalloc(x.data_ptr(), x.data_ptr(), 4097, 4, None)
+    assert st == rom.ROM_E_INVAL
+    hostbuf = np.zeros(16)
+    st, _ = rom.rom_spectral_radius_noalloc(hostbuf.ctypes.data, hostbuf.ctypes.data, 4, 4, None)
+    assert st == rom.ROM_E_INVAL
