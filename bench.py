@@ -38,6 +38,12 @@ sys.path.insert(0, ROOT)
 
 WORKLOAD = dict(name="rank2-fp32-K512-M256-N10000-R64-r10", K=512, M=256, nsteps=10000, R=64,
                 r=10, prec="fp32", seed=0)
+# The split-precision tensor-core workload (selected with --workload 2).
+WORKLOAD2 = dict(name="rank2-split-K1024-M1024-N20000-R64-r10", K=1024, M=1024, nsteps=20000,
+                 R=64, r=10, prec="tf32x3", seed=0)
+# Nominal dense tensor-core rates relative to BF16 (profiling recipe table).
+TC_RATIO = {"tf32x3": 1.1 / 2.25, "bf16x3": 1.0, "bf16": 1.0}
+TC_PRODUCTS = {"tf32x3": 3, "bf16x3": 5, "bf16": 1}
 FP32_LANES_PER_SM = 128  # FP32 FMA lanes per SM (Blackwell)
 
 
@@ -192,6 +198,10 @@ def main():
                     help="leapfrog steps per run (default: the workload's 10000; profiling only)")
     ap.add_argument("--only-rank2", action="store_true",
                     help="time the rank-2 runs only (no e2e, rank-1, oracle legs; profiling only)")
+    ap.add_argument("--workload", type=int, default=1, choices=[1, 2],
+                    help="1: K=512 FP32 (default, the headline); 2: K=1024 split precision")
+    ap.add_argument("--prec", default=None, help="override the workload's precision")
+    ap.add_argument("--tc-cols", type=int, default=0, help="tensor-core columns per block")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl != "reference":
         args.warmup = 3
@@ -214,12 +224,17 @@ def main():
     rbuild.build()
     from paper_2009_11742_gb300 import inputs, rom
 
-    W = dict(WORKLOAD)
+    W = dict(WORKLOAD if args.workload == 1 else WORKLOAD2)
     if args.nsteps:
         W["nsteps"] = args.nsteps
+    if args.prec:
+        W["prec"] = args.prec
+    prec = W["prec"]
     K, M, N, R, r = W["K"], W["M"], W["nsteps"], W["R"], W["r"]
     p = inputs.make_problem(K, K, M, R, seed=W["seed"])
     h = rom.Rom.from_problem(p)
+    if args.tc_cols:
+        rom.rom_set_tc_columns(h.h, args.tc_cols)
     V = rom.Rom.new_state(K, M, "fp32", device=dev)
     S = rom.Rom.new_state(K, M, "fp32", device=dev)
     T = torch.as_tensor(p.T, dtype=torch.float32, device=dev)
@@ -229,7 +244,7 @@ def main():
     stream = torch.cuda.Stream(device=dev)
 
     def one_run():
-        h.run_rank2(V, S, T, N, r=r, traces=tr, prec="fp32", stream=stream)
+        h.run_rank2(V, S, T, N, r=r, traces=tr, prec=prec, stream=stream)
 
     def reset():
         V.zero_()
@@ -275,10 +290,32 @@ def main():
     ms_per_step = 1e3 * t_dev / args.steps
     flops = useful_flops(K, M, N, R, r)
 
-    if args.only_rank2:
+    if args.only_rank2 or args.workload != 1:
         if rank == 0:
-            print(json.dumps({"only_rank2": True, "value": value, "ms_per_step": ms_per_step,
-                              "nsteps": N, "clocks": clocks}), flush=True)
+            out = {"only_rank2": True, "workload": W["name"], "prec": prec, "value": value,
+                   "unit": "sample-steps/s", "ms_per_step": ms_per_step, "nsteps": N,
+                   "tflops_useful": world * flops * args.steps / t_dev / 1e12, "clocks": clocks}
+            if prec in TC_RATIO:
+                pk, pk_kind = peaks()
+                peak = pk.get("bf16_tflops", 1900.0) * TC_RATIO[prec]
+                ach = TC_PRODUCTS[prec] * 4.0 * K * K * M * N / (t_dev / args.steps) / 1e12
+                out["roofline_tensor"] = {"bound": "tensor", "achieved": ach, "peak": peak,
+                                          "unit": "TFLOP/s", "frac": ach / peak,
+                                          "basis": f"{TC_PRODUCTS[prec]} products x 4 K^2 M per step; "
+                                                   f"bf16 {pk_kind} x {TC_RATIO[prec]:.3f}"}
+            if not args.no_check and args.workload == 2:
+                import oracle
+                cols = np.array([0, 511, 1023])
+                V.zero_(); S.zero_()
+                one_run(); torch.cuda.synchronize()
+                Vo, So, tro = oracle.problem_forward(p, nsteps=N, r=r, columns=cols)
+                Vg = V.cpu().numpy()[:, cols]
+                tg = tr.transpose(1, 2).cpu().numpy()[:, :, cols]
+                out["rel_err_vs_oracle"] = {
+                    "V": float(np.linalg.norm(Vg - Vo) / np.linalg.norm(Vo)),
+                    "traces": float(np.linalg.norm(tg - tro) / np.linalg.norm(tro)),
+                    "columns": cols.tolist()}
+            print(json.dumps(out), flush=True)
         if dist is not None:
             dist.destroy_process_group()
         return 0

@@ -132,6 +132,14 @@ rom_status rom_get_plan(rom_t h, int prec, int M, int* variant, int* cluster_siz
                         int* cols_per_block, int* nclusters);
 
 /*
+ * rom_set_tc_columns -- columns per cluster block of the tensor-core path
+ * (ROM_TF32X3 / ROM_BF16X3 / ROM_BF16): 64, 128, 192 or 256, or 0 to let the
+ * planner choose (default).  Wider blocks re-read each operator slab fewer
+ * times per step; narrower blocks spread the run over more SMs.
+ */
+rom_status rom_set_tc_columns(rom_t h, int cols);
+
+/*
  * rom_set_wait_limit -- bound, in SM clock cycles, on every device-side wait
  * of the dataflow kernel (a consumer waiting for a producer's rows).  A wait
  * that runs out makes the kernel stop, leave cleanly, and record

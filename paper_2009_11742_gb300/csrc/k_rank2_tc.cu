@@ -1,0 +1,203 @@
+// Host side of the tensor-core rank-2 path: operator splitting into
+// pre-swizzled tiles, planning (cluster size, columns per block, pipeline
+// depth) and launch.
+#include <cuda_runtime.h>
+
+#include "rank2_launch.cuh"
+#include "rank2_tc.cuh"
+
+namespace romk {
+
+// ---- operator tiles: out[((rt * NKC + kc) * NA + t) * 16 KB] = term t of
+// rows 128 rt .. + 127, k = KC kc .. + KC - 1, SW128 K-major.
+template <int P>
+__global__ void tc_split_operator_kernel(const float* __restrict__ A, int Ksrc, int Kp,
+                                         unsigned char* __restrict__ out) {
+    using Sch = TcScheme<P>;
+    constexpr int NA = Sch::NA, KC = Sch::KC;
+    constexpr int ES = Sch::kTF32 ? 4 : 2;
+    const int NKC = Kp / KC;
+    const size_t total = (size_t)Kp * Kp;
+    for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total;
+         idx += (size_t)gridDim.x * blockDim.x) {
+        const int row = (int)(idx / Kp), col = (int)(idx % Kp);
+        const float x = (row < Ksrc && col < Ksrc) ? A[(size_t)row * Ksrc + col] : 0.f;
+        const int rt = row / kTcRows, r = row % kTcRows, kc = col / KC, k = col % KC;
+        const uint32_t within = sw128_offset((uint32_t)r, (uint32_t)((k * ES) >> 4)) + ((k * ES) & 15);
+        unsigned char* tile0 = out + ((size_t)(rt * NKC + kc) * NA) * kATileBytes + within;
+        if constexpr (Sch::kTF32) {
+            float hi, lo;
+            split_tf32_rn(x, hi, lo);
+            *reinterpret_cast<float*>(tile0) = hi;
+            *reinterpret_cast<float*>(tile0 + kATileBytes) = lo;
+        } else {
+            float rem = x;
+#pragma unroll
+            for (int t = 0; t < NA; ++t) {
+                const __nv_bfloat16 b = __float2bfloat16_rn(rem);
+                *reinterpret_cast<__nv_bfloat16*>(tile0 + t * kATileBytes) = b;
+                rem = rem - __bfloat162float(b);
+            }
+        }
+    }
+}
+
+__global__ void pad_rows_kernel(const float* __restrict__ src, int rows, int src_cols, int dst_cols,
+                                float* __restrict__ dst) {
+    const size_t total = (size_t)rows * dst_cols;
+    for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total;
+         idx += (size_t)gridDim.x * blockDim.x) {
+        const int r = (int)(idx / dst_cols), c = (int)(idx % dst_cols);
+        dst[idx] = c < src_cols ? src[(size_t)r * src_cols + c] : 0.f;
+    }
+}
+
+template <int P>
+static size_t tc_operator_bytes(int Kp) {
+    return (size_t)Kp * Kp * TcScheme<P>::NA * (TcScheme<P>::kTF32 ? 4 : 2);
+}
+
+size_t tc_operator_bytes_for(int prec, int Kp) {
+    switch (prec) {
+        case ROM_TF32X3: return tc_operator_bytes<ROM_TF32X3>(Kp);
+        case ROM_BF16X3: return tc_operator_bytes<ROM_BF16X3>(Kp);
+        case ROM_BF16: return tc_operator_bytes<ROM_BF16>(Kp);
+        default: return 0;
+    }
+}
+
+cudaError_t tc_prepare_operator(int prec, const float* A_rm, int Ksrc, int Kp, void* out,
+                                cudaStream_t st) {
+    const size_t total = (size_t)Kp * Kp;
+    unsigned blocks = (unsigned)((total + 255) / 256);
+    if (blocks > 4096) blocks = 4096;
+    unsigned char* o = static_cast<unsigned char*>(out);
+    switch (prec) {
+        case ROM_TF32X3: tc_split_operator_kernel<ROM_TF32X3><<<blocks, 256, 0, st>>>(A_rm, Ksrc, Kp, o); break;
+        case ROM_BF16X3: tc_split_operator_kernel<ROM_BF16X3><<<blocks, 256, 0, st>>>(A_rm, Ksrc, Kp, o); break;
+        case ROM_BF16: tc_split_operator_kernel<ROM_BF16><<<blocks, 256, 0, st>>>(A_rm, Ksrc, Kp, o); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t tc_pad_rows(const float* src, int rows, int src_cols, int dst_cols, float* dst,
+                        cudaStream_t st) {
+    const size_t total = (size_t)rows * dst_cols;
+    if (total == 0) return cudaSuccess;
+    unsigned blocks = (unsigned)((total + 255) / 256);
+    if (blocks > 4096) blocks = 4096;
+    pad_rows_kernel<<<blocks, 256, 0, st>>>(src, rows, src_cols, dst_cols, dst);
+    return cudaGetLastError();
+}
+
+template <int P>
+static void* tc_kernel(int W) {
+    return W == 64 ? (void*)&rank2_tc_kernel<P, 64> : (W == 128 ? (void*)&rank2_tc_kernel<P, 128> : nullptr);
+}
+
+static void* tc_kernel_for(int prec, int W) {
+    switch (prec) {
+        case ROM_TF32X3: return tc_kernel<ROM_TF32X3>(W);
+        case ROM_BF16X3: return tc_kernel<ROM_BF16X3>(W);
+        case ROM_BF16: return tc_kernel<ROM_BF16>(W);
+        default: return nullptr;
+    }
+}
+
+static size_t tc_smem_for(int prec, int W, int stages, int rpc, int Kp) {
+    switch (prec) {
+        case ROM_TF32X3: return tc_smem_bytes<ROM_TF32X3>(W, stages, rpc, Kp);
+        case ROM_BF16X3: return tc_smem_bytes<ROM_BF16X3>(W, stages, rpc, Kp);
+        case ROM_BF16: return tc_smem_bytes<ROM_BF16>(W, stages, rpc, Kp);
+        default: return 0;
+    }
+}
+
+int tc_exchange_terms(int prec) {
+    switch (prec) {
+        case ROM_TF32X3: return TcScheme<ROM_TF32X3>::NX;
+        case ROM_BF16X3: return TcScheme<ROM_BF16X3>::NX;
+        case ROM_BF16: return TcScheme<ROM_BF16>::NX;
+        default: return 0;
+    }
+}
+int tc_element_bytes(int prec) { return prec == ROM_TF32X3 ? 4 : 2; }
+
+bool plan_rank2_tc(int prec, int Kp, int M, int R, int Wforce, TcPlan* p) {
+    if (Kp <= 0 || Kp % kTcRows != 0 || Kp > 1024 || M <= 0) return false;
+    p->cs = Kp / kTcRows;
+    p->rpc = (R + p->cs - 1) / p->cs;
+    const int smax = device_smem_optin();
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = p->cs;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3(p->cs, 1, 1);
+    cfg.blockDim = dim3(kTcThreads, 1, 1);
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    // columns per block: 64 or 128 (MMA N; each reader warp drains W/2 columns)
+    void* fn64 = tc_kernel_for(prec, 64);
+    if (!fn64) return false;
+    const size_t smem64 = tc_smem_for(prec, 64, 2, p->rpc, Kp);
+    if (smem64 > (size_t)smax) return false;
+    if (cudaFuncSetAttribute(fn64, cudaFuncAttributeMaxDynamicSharedMemorySize, smax) != cudaSuccess ||
+        cudaFuncSetAttribute(fn64, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    cfg.dynamicSmemBytes = smem64;
+    int nact = 0;
+    if (cudaOccupancyMaxActiveClusters(&nact, fn64, &cfg) != cudaSuccess || nact <= 0) {
+        cudaGetLastError();
+        return false;
+    }
+    p->max_active_clusters = nact;
+    int W = Wforce;
+    if (W <= 0) W = ((M + nact - 1) / nact) <= 64 ? 64 : 128;
+    if (W != 64 && W != 128) return false;
+    // deepest pipeline (2..6 stages) that fits
+    int stages = 0;
+    for (int s = 6; s >= 2; --s) {
+        if (tc_smem_for(prec, W, s, p->rpc, Kp) <= (size_t)smax) { stages = s; break; }
+    }
+    if (stages == 0) return false;
+    p->W = W;
+    p->stages = stages;
+    p->smem = tc_smem_for(prec, W, stages, p->rpc, Kp);
+    p->nclusters = (M + W - 1) / W;
+    p->prec = prec;
+    return true;
+}
+
+cudaError_t launch_rank2_tc(const TcArgs& a_in, const TcPlan& p, cudaStream_t st) {
+    void* fn = tc_kernel_for(p.prec, p.W);
+    if (!fn) return cudaErrorInvalidValue;
+    TcArgs a = a_in;
+    a.W = p.W;
+    a.stages = p.stages;
+    a.rpc = p.rpc;
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    if (e != cudaSuccess) return e;
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = p.cs;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3(p.cs * p.nclusters, 1, 1);
+    cfg.blockDim = dim3(kTcThreads, 1, 1);
+    cfg.dynamicSmemBytes = p.smem;
+    cfg.stream = st;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    void* args[] = {(void*)&a};
+    return cudaLaunchKernelExC(&cfg, fn, args);
+}
+
+}  // namespace romk

@@ -84,12 +84,9 @@ __device__ __forceinline__ void fence_mbar_init_cluster() {
 // Arrive on a local mbarrier and add `bytes` to the transaction count its
 // current phase waits for.
 __device__ __forceinline__ void mbar_arrive_expect_tx(unsigned long long* bar, unsigned bytes) {
-    unsigned long long state;
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 %0, [%1], %2;"
-                 : "=l"(state)
-                 : "r"(smem_addr(bar)), "r"(bytes)
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
+                 ::"r"(smem_addr(bar)), "r"(bytes)
                  : "memory");
-    (void)state;
 }
 // 16-byte asynchronous store into cluster CTA `rank` at the shared-memory
 // offset of `dst_local`; completion decrements the transaction count of the

@@ -75,6 +75,14 @@ struct rom_s {
     int* status = nullptr;
     double* scalar = nullptr;  // small device scratch (rank-1 period)
     DevBuf stage;              // staging of host buffers
+    // tensor-core path (prepared on first use of a split precision)
+    int Kp_tc = 0;
+    void* tc_ops[5][2] = {};   // [prec][0: Avs, 1: Asv] pre-split, pre-swizzled tiles
+    float* g_tc = nullptr;     // Kp_tc
+    float* C_tc = nullptr;     // R x Kp_tc
+    DevBuf tc_ws;              // exchange tiles + Kahan carries of one call
+    std::map<std::tuple<int, int, int>, TcPlan> tc_plans;
+    int tc_cols = 0;           // columns per block pinned by rom_set_tc_columns (0 = planner)
     std::map<std::tuple<int, int, int, int, int>, Rank2Plan> plans;
     std::mutex mu;
     int kernel_choice = 0;  // ROM_KERNEL_AUTO
@@ -95,6 +103,12 @@ void free_handle(rom_s* h) {
         cudaFree(h->C_rm[t]);
         cudaFree(h->C_cm[t]);
     }
+    for (int p = 0; p < 5; ++p) {
+        cudaFree(h->tc_ops[p][0]);
+        cudaFree(h->tc_ops[p][1]);
+    }
+    cudaFree(h->g_tc);
+    cudaFree(h->C_tc);
     cudaFree(h->status);
     cudaFree(h->scalar);
     delete h;
@@ -322,8 +336,105 @@ rom_status get_plan(rom_s* h, int prec, int M, bool rank1, Rank2Plan* plan) {
     return ROM_OK;
 }
 
+// Split operator tiles, padded g and C for the tensor-core path (once per precision).
+rom_status tc_prepare(rom_s* h, int prec, cudaStream_t st) {
+    if (h->tc_ops[prec][0]) return ROM_OK;
+    const int Kp_tc = ((h->Kp + 127) / 128) * 128;
+    if (Kp_tc > 1024) return ROM_E_UNSUPPORTED;
+    if (!h->g_tc) {
+        h->Kp_tc = Kp_tc;
+        ROM_CUDA(cudaMalloc(&h->g_tc, sizeof(float) * Kp_tc));
+        ROM_CUDA(tc_pad_rows(static_cast<const float*>(h->g_p[1]), 1, h->Kp, Kp_tc, h->g_tc, st));
+        if (h->R > 0) {
+            ROM_CUDA(cudaMalloc(&h->C_tc, sizeof(float) * (size_t)h->R * Kp_tc));
+            ROM_CUDA(tc_pad_rows(static_cast<const float*>(h->C_rm[1]), h->R, h->Kp, Kp_tc, h->C_tc, st));
+        }
+    }
+    const size_t bytes = tc_operator_bytes_for(prec, Kp_tc);
+    void* ops[2] = {nullptr, nullptr};
+    for (int o = 0; o < 2; ++o) {
+        cudaError_t e = cudaMalloc(&ops[o], bytes);
+        if (e == cudaSuccess)
+            e = tc_prepare_operator(prec, static_cast<const float*>(o == 0 ? h->Avs_rm[1] : h->Asv_rm[1]),
+                                    h->Kp, Kp_tc, ops[o], st);
+        if (e != cudaSuccess) {
+            cudaFree(ops[0]);
+            cudaFree(ops[1]);
+            return cuda_fail(e, "tensor-core operator split");
+        }
+    }
+    h->tc_ops[prec][0] = ops[0];
+    h->tc_ops[prec][1] = ops[1];
+    return ROM_OK;
+}
+
+rom_status run_rank2_tc(rom_s* h, const RunBufs& b, int M, int nsteps, long n0, int r, int prec,
+                        cudaStream_t st) {
+    rom_status s = tc_prepare(h, prec, st);
+    if (s != ROM_OK) return s;
+    TcPlan plan;
+    {
+        std::lock_guard<std::mutex> lk(h->mu);
+        const auto key = std::make_tuple(prec, M, h->tc_cols);
+        auto it = h->tc_plans.find(key);
+        if (it != h->tc_plans.end()) {
+            plan = it->second;
+        } else {
+            if (!plan_rank2_tc(prec, h->Kp_tc, M, h->R, h->tc_cols, &plan)) {
+                snprintf(g_last_error, sizeof(g_last_error),
+                         "no tensor-core plan for Kp=%d M=%d prec=%d", h->Kp_tc, M, prec);
+                return ROM_E_UNSUPPORTED;
+            }
+            h->tc_plans[key] = plan;
+        }
+    }
+    // workspace: exchange tiles of both states for every block, Kahan carries
+    const size_t xterm = (size_t)h->Kp_tc * plan.W * tc_element_bytes(prec);
+    const size_t xbytes = (size_t)plan.nclusters * tc_exchange_terms(prec) * xterm;
+    const bool own_comp = b.compV == nullptr;
+    const size_t cbytes = own_comp ? sizeof(float) * (size_t)(h->Kv + h->Ks) * M : 0;
+    auto al = [](size_t x) { return (x + 1023) & ~size_t(1023); };
+    ROM_CUDA(h->tc_ws.ensure(2 * al(xbytes) + al(cbytes)));
+    char* ws = static_cast<char*>(h->tc_ws.p);
+    TcArgs a = {};
+    a.Aop[0] = h->tc_ops[prec][0];
+    a.Aop[1] = h->tc_ops[prec][1];
+    a.X[0] = ws;
+    a.X[1] = ws + al(xbytes);
+    float* cw = reinterpret_cast<float*>(ws + 2 * al(xbytes));
+    if (own_comp) ROM_CUDA(cudaMemsetAsync(cw, 0, cbytes, st));
+    a.g_p = h->g_tc;
+    a.C_p = h->C_tc;
+    a.V = static_cast<float*>(b.V);
+    a.S = static_cast<float*>(b.S);
+    a.compV = own_comp ? cw : static_cast<float*>(b.compV);
+    a.compS = own_comp ? cw + (size_t)h->Kv * M : static_cast<float*>(b.compS);
+    a.Tper = b.ftab ? nullptr : static_cast<const float*>(b.T);
+    a.ftab = static_cast<const float*>(b.ftab);
+    a.traces = static_cast<float*>(b.traces);
+    a.status = h->status;
+    a.dt = h->dt;
+    a.n0 = n0;
+    a.spin_limit = h->wait_limit;
+    a.Kv = h->Kv;
+    a.Ks = h->Ks;
+    a.Kp = h->Kp_tc;
+    a.R = h->R;
+    a.M = M;
+    a.Mtot = M;
+    a.nsteps = nsteps;
+    a.r = b.traces ? r : 1;
+    cudaError_t e = launch_rank2_tc(a, plan, st);
+    if (e != cudaSuccess) return cuda_fail(e, "tensor-core rank2 launch");
+    return ROM_OK;
+}
+
 rom_status run_rank2_device(rom_s* h, const RunBufs& b, int M, int nsteps, long n0, int r,
                             int prec, bool rank1, cudaStream_t st) {
+    if (prec == ROM_TF32X3 || prec == ROM_BF16X3 || prec == ROM_BF16) {
+        if (rank1) return ROM_E_UNSUPPORTED;
+        return run_rank2_tc(h, b, M, nsteps, n0, r, prec, st);
+    }
     if (prec != ROM_FP64 && prec != ROM_FP32) {
         snprintf(g_last_error, sizeof(g_last_error), "precision %d has no kernel in this build", prec);
         return ROM_E_UNSUPPORTED;
@@ -463,6 +574,13 @@ rom_status rom_set_wait_limit(rom_t h, long long cycles) {
 rom_status rom_debug_inject_stall(rom_t h, int on) {
     if (!h) return ROM_E_INVAL;
     h->inject_stall = on ? 1 : 0;
+    return ROM_OK;
+}
+
+rom_status rom_set_tc_columns(rom_t h, int cols) {
+    if (!h || cols < 0 || cols > 256 || cols % 64 != 0) return ROM_E_INVAL;
+    std::lock_guard<std::mutex> lk(h->mu);
+    h->tc_cols = cols;
     return ROM_OK;
 }
 

@@ -66,6 +66,40 @@ bool plan_rank2_split_f32(int Kp, int M, int R, Rank2Plan* plan);
 bool plan_rank2_dataflow_f32(int Kp, int M, int R, Rank2Plan* plan);
 cudaError_t launch_rank2_split_f32(const Rank2Args& a, const Rank2Plan& plan, cudaStream_t st);
 
+// Tensor-core (tcgen05) rank-2 path for ROM_TF32X3 / ROM_BF16X3 / ROM_BF16.
+struct TcArgs {
+    const void* Aop[2];   // split operator tiles: [0] Avs (V half), [1] Asv (S half)
+    void* X[2];           // exchange tiles: [0] S (operand of the V half), [1] V
+    const float* g_p;     // Kp (tensor-core padding)
+    const float* C_p;     // R x Kp row-major (or null)
+    float* V;             // Kv x Mtot
+    float* S;             // Ks x Mtot
+    float* compV;         // Kv x Mtot Kahan carries (workspace or caller's)
+    float* compS;
+    const float* Tper;    // Mtot or null
+    const float* ftab;    // nsteps x Mtot or null
+    float* traces;        // nrec x Mtot x R or null
+    int* status;
+    double dt;
+    long long n0;
+    long long spin_limit;
+    int Kv, Ks, Kp, R, M, Mtot, W, nsteps, r, rpc, stages;
+};
+struct TcPlan {
+    int prec, cs, W, stages, nclusters, rpc, max_active_clusters;
+    size_t smem;
+};
+size_t tc_operator_bytes_for(int prec, int Kp);
+int tc_exchange_terms(int prec);
+int tc_element_bytes(int prec);
+cudaError_t tc_prepare_operator(int prec, const float* A_rm, int Ksrc, int Kp, void* out,
+                                cudaStream_t st);
+cudaError_t tc_pad_rows(const float* src, int rows, int src_cols, int dst_cols, float* dst,
+                        cudaStream_t st);
+// Wforce > 0 pins the columns per block (a multiple of 64, at most 256).
+bool plan_rank2_tc(int prec, int Kp, int M, int R, int Wforce, TcPlan* plan);
+cudaError_t launch_rank2_tc(const TcArgs& a, const TcPlan& plan, cudaStream_t st);
+
 // Rank-1 ensemble (one realization per CTA, operators streamed every step).
 struct Rank1EnsArgs {
     const void* Avs_cm;  // Kp x Kp column-major, zero padded (T)

@@ -34,7 +34,7 @@ PRECISIONS = {"fp64": ROM_FP64, "fp32": ROM_FP32, "tf32x3": ROM_TF32X3,
               "bf16x3": ROM_BF16X3, "bf16": ROM_BF16}
 
 EXPORTED = ["rom_create", "rom_destroy", "rom_spectral_radius", "rom_sync_status",
-            "rom_get_dims", "rom_set_kernel", "rom_get_plan", "rom_set_wait_limit",
+            "rom_get_dims", "rom_set_kernel", "rom_get_plan", "rom_set_tc_columns", "rom_set_wait_limit",
             "rom_debug_inject_stall", "rom_run_rank2", "rom_run_rank2_ex", "rom_run_rank1",
             "rom_run_rank1_ensemble", "rom_rel_l2", "rom_spectral_radius_noalloc",
             "rom_status_string", "rom_last_error", "rom_version"]
@@ -64,6 +64,7 @@ def _signatures(lib):
                               ctypes.POINTER(_d)]),
         "rom_set_kernel": (_i, [_vp, _i]),
         "rom_set_wait_limit": (_i, [_vp, ctypes.c_longlong]),
+        "rom_set_tc_columns": (_i, [_vp, _i]),
         "rom_debug_inject_stall": (_i, [_vp, _i]),
         "rom_get_plan": (_i, [_vp, _i, _i, ctypes.POINTER(_i), ctypes.POINTER(_i),
                               ctypes.POINTER(_i), ctypes.POINTER(_i)]),
@@ -147,6 +148,10 @@ def rom_get_dims(h):
 
 def rom_set_kernel(h, kernel):
     return load().rom_set_kernel(h, kernel)
+
+
+def rom_set_tc_columns(h, cols):
+    return load().rom_set_tc_columns(h, int(cols))
 
 
 def rom_set_wait_limit(h, cycles):
