@@ -198,8 +198,9 @@ def main():
                     help="leapfrog steps per run (default: the workload's 10000; profiling only)")
     ap.add_argument("--only-rank2", action="store_true",
                     help="time the rank-2 runs only (no e2e, rank-1, oracle legs; profiling only)")
-    ap.add_argument("--workload", type=int, default=1, choices=[1, 2],
-                    help="1: K=512 FP32 (default, the headline); 2: K=1024 split precision")
+    ap.add_argument("--workload", type=int, default=1, choices=[1, 2, 3],
+                    help="1: K=512 FP32 (default, the headline); 2: K=1024 split precision; "
+                         "3: 64 batched ROMs")
     ap.add_argument("--prec", default=None, help="override the workload's precision")
     ap.add_argument("--tc-cols", type=int, default=0, help="tensor-core columns per block")
     args = ap.parse_args()
@@ -223,6 +224,9 @@ def main():
     from paper_2009_11742_gb300 import build as rbuild
     rbuild.build()
     from paper_2009_11742_gb300 import inputs, rom
+
+    if args.workload == 3:
+        return bench_batched(args, torch, dev, inputs, rom)
 
     W = dict(WORKLOAD if args.workload == 1 else WORKLOAD2)
     if args.nsteps:
@@ -440,6 +444,43 @@ def main():
     if dist is not None:
         dist.destroy_process_group()
     h.close()
+    return 0
+
+
+def bench_batched(args, torch, dev, inputs, rom):
+    """Workload 3: 64 independent ROMs (K_i in {64..768}, M_i in [4, 256]),
+    5000 steps each, one graph launch per bench step."""
+    probs = inputs.batched_problems()
+    N = args.nsteps or 5000
+    items = []
+    for p in probs:
+        h = rom.Rom.from_problem(p)
+        items.append((h, rom.Rom.new_state(p.Kv, p.M, "fp32", device=dev),
+                      rom.Rom.new_state(p.Ks, p.M, "fp32", device=dev),
+                      torch.as_tensor(p.T, dtype=torch.float32, device=dev), None))
+    stream = torch.cuda.Stream(device=dev)
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            rom.run_batched(items, N, prec="fp32", stream=stream)
+    torch.cuda.synchronize()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps)]
+    with torch.cuda.stream(stream):
+        for i in range(args.steps):
+            for (_, V, S, _, _) in items:
+                V.zero_()
+                S.zero_()
+            evs[i][0].record(stream)
+            rom.run_batched(items, N, prec="fp32", stream=stream)
+            evs[i][1].record(stream)
+    torch.cuda.synchronize()
+    t = sum(a.elapsed_time(b) for a, b in evs) * 1e-3 / args.steps
+    ss = sum(p.M for p in probs) * N
+    fl = sum(4.0 * p.Kv * p.Ks * p.M for p in probs) * N
+    print(json.dumps({"only_rank2": True, "workload": "batched-64roms-K64..768-M4..256-N5000",
+                      "nsteps": N, "value": ss / t, "unit": "sample-steps/s",
+                      "ms_per_step": 1e3 * t, "tflops_useful": fl / t / 1e12,
+                      "columns_total": sum(p.M for p in probs)}), flush=True)
     return 0
 
 

@@ -208,6 +208,30 @@ rom_status rom_run_rank1_ensemble(rom_t h, void* V, void* S, const void* T, int 
                                   int nsteps, long n0, int r, void* traces, int prec,
                                   void* stream);
 
+/*
+ * rom_run_batched -- many ensembles at once: job i advances its handle's
+ * model (any Kv, Ks <= 1024) for its M columns exactly as rom_run_rank2 would
+ * with n0 = 0, and all jobs run in ONE launch of a CUDA graph on `stream`.
+ * The scheduler gives every job a share of the GPU proportional to its work
+ * per step, 4 K^2 M (the rank-2 GEMM cost of Sec. 2.5), which sets its columns
+ * per cluster block, and issues the longest jobs first.  The graph is built
+ * (captured and instantiated) on the first call for a given job list and
+ * replayed afterwards.  Requirements: device buffers only, one job per
+ * handle, traces (per job, optional) need r > 0 and receiver rows.
+ * Asynchronous on `stream`.  This is the first step of the rank-3 outlook of
+ * Sec. 5 (many operators and many forcings in one launch).
+ */
+typedef struct {
+    rom_t h;         /* the job's model */
+    void* V;         /* Kv x M, column-major, device, updated in place */
+    void* S;         /* Ks x M */
+    const void* T;   /* M periods, or NULL for no forcing */
+    int M;           /* realizations of this job */
+    void* traces;    /* floor(nsteps / r) records of R x M, or NULL */
+} rom_job;
+rom_status rom_run_batched(const rom_job* jobs, int njobs, int nsteps, int r, int prec,
+                           void* stream);
+
 /* ------------------------------------------------------------- utilities */
 
 /*

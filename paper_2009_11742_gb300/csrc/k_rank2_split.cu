@@ -26,7 +26,7 @@ static size_t two_block_smem(int Wa, int Kp, int rpc) {
 }
 
 template <bool DF>
-static bool plan_two_block(int Kp, int M, int R, Rank2Plan* p) {
+static bool plan_two_block(int Kp, int M, int R, Rank2Plan* p, int cluster_budget = 0) {
     if (Kp <= 0 || Kp % 64 != 0 || Kp > 512 || M <= 0) return false;
     p->KI = Kp / 64;
     p->cs = Kp / 32;  // H = Kp / 64 CTAs per role
@@ -63,7 +63,9 @@ static bool plan_two_block(int Kp, int M, int R, Rank2Plan* p) {
         return false;
     }
     p->max_active_clusters = nact;
-    int wv = (M + 2 * nact - 1) / (2 * nact);
+    const int budget = cluster_budget > 0 && cluster_budget < nact ? cluster_budget : nact;
+    p->nrt = 1;
+    int wv = (M + 2 * budget - 1) / (2 * budget);
     wv = ((wv + kSplitCB - 1) / kSplitCB) * kSplitCB;
     if (wv > wcap) wv = wcap;
     p->Wv = wv;
@@ -101,7 +103,7 @@ static cudaError_t launch_two_block(const Rank2Args& a_in, const Rank2Plan& p, c
     return cudaLaunchKernelExC(&cfg, fn, args);
 }
 
-bool plan_rank2_split_f32(int Kp, int M, int R, Rank2Plan* p) { return plan_two_block<false>(Kp, M, R, p); }
+bool plan_rank2_split_f32(int Kp, int M, int R, Rank2Plan* p, int budget) { return plan_two_block<false>(Kp, M, R, p, budget); }
 bool plan_rank2_dataflow_f32(int Kp, int M, int R, Rank2Plan* p) { return plan_two_block<true>(Kp, M, R, p); }
 cudaError_t launch_rank2_split_f32(const Rank2Args& a, const Rank2Plan& p, cudaStream_t st) {
     return p.variant == 3 ? launch_two_block<true>(a, p, st) : launch_two_block<false>(a, p, st);

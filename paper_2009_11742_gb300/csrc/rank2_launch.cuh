@@ -18,10 +18,12 @@ struct Rank2Kernel {
 // FP32 keeps both operators in registers up to KI = 8 (K <= 512); FP64 up to
 // KI = 4 (K <= 256) and re-reads its 32-row operator slab from L2 each
 // half-step beyond that.
+// FP32 beyond KI = 8 (K > 512) streams two 32-row operator tiles per CTA per
+// half-step (one-block kernel with nrt = 2); FP64 stops at K = 512.
 template <typename T, int CB>
 static void* rank2_kernel_for(int KI, bool* resident) {
     constexpr bool f64 = sizeof(T) == 8;
-    *resident = !(f64 && KI > 4);
+    *resident = !(f64 && KI > 4) && KI <= 8;
     switch (KI) {
         case 1: return Rank2Kernel<T, 1, CB, true>::fn();
         case 2: return Rank2Kernel<T, 2, CB, true>::fn();
@@ -31,8 +33,22 @@ static void* rank2_kernel_for(int KI, bool* resident) {
         case 6: return Rank2Kernel<T, 6, CB, !f64>::fn();
         case 7: return Rank2Kernel<T, 7, CB, !f64>::fn();
         case 8: return Rank2Kernel<T, 8, CB, !f64>::fn();
-        default: return nullptr;
+        default: break;
     }
+    if constexpr (!f64) {
+        switch (KI) {
+            case 9: return Rank2Kernel<T, 9, CB, false>::fn();
+            case 10: return Rank2Kernel<T, 10, CB, false>::fn();
+            case 11: return Rank2Kernel<T, 11, CB, false>::fn();
+            case 12: return Rank2Kernel<T, 12, CB, false>::fn();
+            case 13: return Rank2Kernel<T, 13, CB, false>::fn();
+            case 14: return Rank2Kernel<T, 14, CB, false>::fn();
+            case 15: return Rank2Kernel<T, 15, CB, false>::fn();
+            case 16: return Rank2Kernel<T, 16, CB, false>::fn();
+            default: break;
+        }
+    }
+    return nullptr;
 }
 
 template <typename T>
@@ -57,26 +73,30 @@ static cudaError_t prepare_kernel(void* fn, size_t smem) {
     return cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
 }
 
+// cluster_budget > 0 caps the clusters the plan assumes it may keep busy (the
+// batched scheduler hands each ROM its share of the GPU).
 template <typename T>
-static bool plan_rank2(int Kp, int M, int R, bool rank1, Rank2Plan* p) {
-    if (Kp <= 0 || Kp % 64 != 0 || Kp > 512 || M <= 0) return false;
+static bool plan_rank2(int Kp, int M, int R, bool rank1, Rank2Plan* p, int cluster_budget = 0) {
+    const int kmax = sizeof(T) == 4 ? 1024 : 512;
+    if (Kp <= 0 || Kp % 64 != 0 || Kp > kmax || M <= 0) return false;
     constexpr int CBW = sizeof(T) == 4 ? 8 : 4;
     p->KI = Kp / 64;
-    p->cs = Kp / 32;
+    p->nrt = Kp > 512 ? 2 : 1;
+    p->cs = Kp / (32 * p->nrt);
     p->cb = rank1 ? 1 : CBW;
     const int rpc = (R + p->cs - 1) / p->cs;
     const int smax = device_smem_optin();
     // widest allocation that fits shared memory
     int wcap = 0;
     for (int w = p->cb; w <= 4096; w += p->cb) {
-        if (rank2_smem_layout<T>(w, Kp, rpc).total > (size_t)smax) break;
+        if (rank2_smem_layout<T>(w, Kp, rpc, p->nrt).total > (size_t)smax) break;
         wcap = w;
     }
     if (wcap == 0) return false;
     void* fn = rank2_kernel<T>(p->KI, p->cb, &p->resident);
     if (!fn) return false;
     const int wprobe = rank1 ? 1 : wcap;
-    const size_t smem_probe = rank2_smem_layout<T>(wprobe, Kp, rpc).total;
+    const size_t smem_probe = rank2_smem_layout<T>(wprobe, Kp, rpc, p->nrt).total;
     if (prepare_kernel<T>(fn, smem_probe) != cudaSuccess) return false;
     cudaLaunchConfig_t cfg = {};
     cudaLaunchAttribute attr[1];
@@ -95,13 +115,15 @@ static bool plan_rank2(int Kp, int M, int R, bool rank1, Rank2Plan* p) {
         return false;
     }
     p->max_active_clusters = nact;
-    int wv = (M + nact - 1) / nact;
+    const int budget = cluster_budget > 0 && cluster_budget < nact ? cluster_budget : nact;
+    int wv = (M + budget - 1) / budget;
     wv = ((wv + p->cb - 1) / p->cb) * p->cb;
     if (wv > wcap) wv = wcap;
     p->Wv = wv;
     p->Wa = wv;
     p->nclusters = (M + wv - 1) / wv;
-    p->smem = rank2_smem_layout<T>(p->Wa, Kp, rpc).total;
+    p->smem = rank2_smem_layout<T>(p->Wa, Kp, rpc, p->nrt).total;
+    p->variant = 1;
     return true;
 }
 
@@ -110,6 +132,7 @@ static cudaError_t launch_rank2(const Rank2Args& a_in, const Rank2Plan& p, cudaS
     Rank2Args a = a_in;
     a.Wv = p.Wv;
     a.Wa = p.Wa;
+    a.nrt = p.nrt;
     a.rpc = (a.R + p.cs - 1) / p.cs;
     bool res = false;
     void* fn = rank2_kernel<T>(p.KI, p.cb, &res);

@@ -39,8 +39,9 @@ struct Rank2Smem {
     size_t Vf, Sf, C, f, T, g, cV, cS, total;
 };
 
+// nrt: 32-row tiles owned per CTA (1, or 2 with operators streamed from L2).
 template <typename T>
-__host__ __device__ inline Rank2Smem rank2_smem_layout(int Wa, int Kp, int rpc) {
+__host__ __device__ inline Rank2Smem rank2_smem_layout(int Wa, int Kp, int rpc, int nrt = 1) {
     Rank2Smem s{};
     size_t o = 0;
     s.Vf = o; o += align16((size_t)Wa * Kp * sizeof(T));
@@ -48,9 +49,9 @@ __host__ __device__ inline Rank2Smem rank2_smem_layout(int Wa, int Kp, int rpc) 
     s.C = o;  o += align16((size_t)rpc * Kp * sizeof(T));
     s.f = o;  o += align16((size_t)Wa * sizeof(T));
     s.T = o;  o += align16((size_t)Wa * sizeof(T));
-    s.g = o;  o += align16((size_t)kRowsPerCta * sizeof(T));
-    s.cV = o; o += align16((size_t)Wa * kRowsPerCta * sizeof(float));
-    s.cS = o; o += align16((size_t)Wa * kRowsPerCta * sizeof(float));
+    s.g = o;  o += align16((size_t)nrt * kRowsPerCta * sizeof(T));
+    s.cV = o; o += align16((size_t)nrt * Wa * kRowsPerCta * sizeof(float));
+    s.cS = o; o += align16((size_t)nrt * Wa * kRowsPerCta * sizeof(float));
     s.total = o;
     return s;
 }
@@ -141,8 +142,8 @@ __device__ __forceinline__ void half_step(const T (&op)[2][4 * KI], const T* __r
 // of every other CTA of the cluster (distributed shared memory stores).
 template <typename T>
 __device__ __forceinline__ void push_own_rows(cg::cluster_group& cluster, T* Y, int Wa, int Kp,
-                                              int row0, int cs, int crank) {
-    constexpr int VPC = kRowsPerCta * (int)sizeof(T) / 16;  // 16-byte vectors per column
+                                              int row0, int cs, int crank, int nrt) {
+    const int VPC = nrt * kRowsPerCta * (int)sizeof(T) / 16;  // 16-byte vectors per column
     const int nvec = Wa * VPC;
     for (int idx = threadIdx.x; idx < nvec; idx += kThreads) {
         const int c = idx / VPC, part = idx % VPC;
@@ -194,11 +195,13 @@ __global__ void __launch_bounds__(kThreads, 1) rank2_simt_kernel(const Rank2Args
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int j = lane & 15;
     const int rp = warp * 2 + (lane >> 4);
-    const int row0 = crank * kRowsPerCta;
+    const int nrt = a.nrt;
+    const int own_rows = nrt * kRowsPerCta;
+    const int row0 = crank * own_rows;
     const T dt = (T)a.dt;
 
     extern __shared__ __align__(16) unsigned char smem[];
-    const Rank2Smem L = rank2_smem_layout<T>(Wa, Kp, a.rpc);
+    const Rank2Smem L = rank2_smem_layout<T>(Wa, Kp, a.rpc, nrt);
     T* Vf = reinterpret_cast<T*>(smem + L.Vf);
     T* Sf = reinterpret_cast<T*>(smem + L.Sf);
     T* Cown = reinterpret_cast<T*>(smem + L.C);
@@ -218,8 +221,11 @@ __global__ void __launch_bounds__(kThreads, 1) rank2_simt_kernel(const Rank2Args
         Vf[idx] = (c < ncol && k < a.Kv) ? Vin[(size_t)(gc0 + c) * a.Kv + k] : T(0);
         Sf[idx] = (c < ncol && k < a.Ks) ? Sin[(size_t)(gc0 + c) * a.Ks + k] : T(0);
     }
-    for (int idx = tid; idx < Wa * kRowsPerCta; idx += kThreads) {
-        const int c = idx / kRowsPerCta, rl = idx % kRowsPerCta, row = row0 + rl;
+    // carries: [row tile][column][32 rows]
+    for (int idx = tid; idx < nrt * Wa * kRowsPerCta; idx += kThreads) {
+        const int rt = idx / (Wa * kRowsPerCta);
+        const int rem = idx - rt * Wa * kRowsPerCta;
+        const int c = rem / kRowsPerCta, rl = rem % kRowsPerCta, row = row0 + rt * kRowsPerCta + rl;
         const float* cvin = static_cast<const float*>(a.compV);
         const float* csin = static_cast<const float*>(a.compS);
         cV[idx] = (cvin && c < ncol && row < a.Kv) ? cvin[(size_t)(gc0 + c) * a.Kv + row] : 0.f;
@@ -230,7 +236,7 @@ __global__ void __launch_bounds__(kThreads, 1) rank2_simt_kernel(const Rank2Args
         const int jj = idx / Kp, k = idx % Kp, jr = crank * a.rpc + jj;
         Cown[idx] = (Cp && jr < a.R) ? Cp[(size_t)jr * Kp + k] : T(0);
     }
-    if (tid < kRowsPerCta) gown[tid] = static_cast<const T*>(a.g_p)[row0 + tid];
+    for (int i = tid; i < own_rows; i += kThreads) gown[i] = static_cast<const T*>(a.g_p)[row0 + i];
     for (int c = tid; c < Wa; c += kThreads) {
         Tcol[c] = (a.Tper && c < ncol) ? static_cast<const T*>(a.Tper)[gc0 + c] : T(1);
     }
@@ -253,15 +259,23 @@ __global__ void __launch_bounds__(kThreads, 1) rank2_simt_kernel(const Rank2Args
     T* traces = static_cast<T*>(a.traces);
     for (int n = 0; n < a.nsteps; ++n) {
         // ---- velocity half-step: V_own += dt (Avs_own S + g f_n^T)
-        if (!RESIDENT) load_op_rows<T, KI>(opA, Avs, Kp, row0 + 2 * rp, j);
-        half_step<T, KI, CB, true>(opA, Sf, Vf, cV, gown, fcol, dt, Wa, Kp, row0, rp, j);
+        for (int rt = 0; rt < nrt; ++rt) {
+            const int rowt = row0 + rt * kRowsPerCta;
+            if (!RESIDENT) load_op_rows<T, KI>(opA, Avs, Kp, rowt + 2 * rp, j);
+            half_step<T, KI, CB, true>(opA, Sf, Vf, cV + rt * Wa * kRowsPerCta, gown + rt * kRowsPerCta,
+                                       fcol, dt, Wa, Kp, rowt, rp, j);
+        }
         __syncthreads();
-        push_own_rows<T>(cluster, Vf, Wa, Kp, row0, cs, crank);
+        push_own_rows<T>(cluster, Vf, Wa, Kp, row0, cs, crank, nrt);
         cluster.sync();
 
         // ---- stress half-step with the new velocity: S_own += dt Asv_own V
-        if (!RESIDENT) load_op_rows<T, KI>(opB, Asv, Kp, row0 + 2 * rp, j);
-        half_step<T, KI, CB, false>(opB, Vf, Sf, cS, gown, fcol, dt, Wa, Kp, row0, rp, j);
+        for (int rt = 0; rt < nrt; ++rt) {
+            const int rowt = row0 + rt * kRowsPerCta;
+            if (!RESIDENT) load_op_rows<T, KI>(opB, Asv, Kp, rowt + 2 * rp, j);
+            half_step<T, KI, CB, false>(opB, Vf, Sf, cS + rt * Wa * kRowsPerCta, gown, fcol, dt, Wa, Kp,
+                                        rowt, rp, j);
+        }
 
         // ---- receiver traces y = C V^{n+1} (this CTA's rows of C)
         if (traces && ((n + 1) % a.r) == 0) {
@@ -290,7 +304,7 @@ __global__ void __launch_bounds__(kThreads, 1) rank2_simt_kernel(const Rank2Args
             }
         }
         __syncthreads();
-        push_own_rows<T>(cluster, Sf, Wa, Kp, row0, cs, crank);
+        push_own_rows<T>(cluster, Sf, Wa, Kp, row0, cs, crank, nrt);
         cluster.sync();
     }
 
@@ -300,18 +314,19 @@ __global__ void __launch_bounds__(kThreads, 1) rank2_simt_kernel(const Rank2Args
     float* cvout = static_cast<float*>(a.compV);
     float* csout = static_cast<float*>(a.compS);
     int bad = 0;
-    for (int idx = tid; idx < ncol * kRowsPerCta; idx += kThreads) {
-        const int c = idx / kRowsPerCta, rl = idx % kRowsPerCta, row = row0 + rl;
+    for (int idx = tid; idx < ncol * own_rows; idx += kThreads) {
+        const int c = idx / own_rows, ro = idx % own_rows, row = row0 + ro;
+        const int ci = (ro / kRowsPerCta) * Wa * kRowsPerCta + c * kRowsPerCta + ro % kRowsPerCta;
         if (row < a.Kv) {
             const T x = Vf[(size_t)c * Kp + row];
             Vout[(size_t)(gc0 + c) * a.Kv + row] = x;
-            if (cvout) cvout[(size_t)(gc0 + c) * a.Kv + row] = cV[c * kRowsPerCta + rl];
+            if (cvout) cvout[(size_t)(gc0 + c) * a.Kv + row] = cV[ci];
             bad |= !is_finite(x);
         }
         if (row < a.Ks) {
             const T x = Sf[(size_t)c * Kp + row];
             Sout[(size_t)(gc0 + c) * a.Ks + row] = x;
-            if (csout) csout[(size_t)(gc0 + c) * a.Ks + row] = cS[c * kRowsPerCta + rl];
+            if (csout) csout[(size_t)(gc0 + c) * a.Ks + row] = cS[ci];
             bad |= !is_finite(x);
         }
     }

@@ -5,6 +5,7 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <algorithm>
 #include <map>
 #include <mutex>
 #include <tuple>
@@ -161,6 +162,9 @@ rom_status power_iteration(rom_s* h, double* rho_out) {
 
 bool valid_prec(int prec) { return prec >= ROM_FP64 && prec <= ROM_BF16; }
 
+// Forget cached batched graphs that reference handle h (defined with them below).
+void drop_batch_graphs(rom_s* h);
+
 }  // namespace
 
 extern "C" {
@@ -266,6 +270,7 @@ rom_status rom_create(const void* Avs, const void* Asv, const void* g, const voi
 rom_status rom_destroy(rom_t h) {
     if (!h) return ROM_E_INVAL;
     cudaDeviceSynchronize();
+    drop_batch_graphs(h);
     free_handle(h);
     return ROM_OK;
 }
@@ -429,6 +434,9 @@ rom_status run_rank2_tc(rom_s* h, const RunBufs& b, int M, int nsteps, long n0, 
     return ROM_OK;
 }
 
+rom_status launch_simt_with_plan(rom_s* h, const RunBufs& b, int M, int nsteps, long n0, int r,
+                                 int prec, const Rank2Plan& plan, cudaStream_t st);
+
 rom_status run_rank2_device(rom_s* h, const RunBufs& b, int M, int nsteps, long n0, int r,
                             int prec, bool rank1, cudaStream_t st) {
     if (prec == ROM_TF32X3 || prec == ROM_BF16X3 || prec == ROM_BF16) {
@@ -442,6 +450,11 @@ rom_status run_rank2_device(rom_s* h, const RunBufs& b, int M, int nsteps, long 
     Rank2Plan plan;
     rom_status s = get_plan(h, prec, M, rank1, &plan);
     if (s != ROM_OK) return s;
+    return launch_simt_with_plan(h, b, M, nsteps, n0, r, prec, plan, st);
+}
+
+rom_status launch_simt_with_plan(rom_s* h, const RunBufs& b, int M, int nsteps, long n0, int r,
+                                 int prec, const Rank2Plan& plan, cudaStream_t st) {
     const int t = prec == ROM_FP64 ? 0 : 1;
     Rank2Args a = {};
     a.Avs_rm = h->Avs_rm[t];
@@ -660,6 +673,176 @@ rom_status rom_run_rank1(rom_t h, void* v, void* s, double T, int nsteps, long n
     ROM_CUDA(cudaMemcpyAsync(s, b.S, nS * es, cudaMemcpyDeviceToHost, st));
     if (nTr) ROM_CUDA(cudaMemcpyAsync(trace, b.traces, nTr * es, cudaMemcpyDeviceToHost, st));
     ROM_CUDA(cudaStreamSynchronize(st));
+    return ROM_OK;
+}
+
+// ---------------------------------------------------------------- batched
+//
+// Many ROMs with uneven K and M in one CUDA-graph launch.  Each job keeps its
+// own persistent cluster kernel; the scheduler gives job i a share of the
+// GPU's SMs proportional to its work 4 K_i^2 M_i (its cluster budget, which
+// fixes the columns per cluster block), orders the launches longest-first and
+// captures them, forked over a pool of streams, into one graph that is
+// instantiated once per job list and replayed.
+}  // extern "C"
+
+namespace {
+
+struct BatchKey {
+    std::vector<uintptr_t> words;
+    bool operator<(const BatchKey& o) const { return words < o.words; }
+};
+std::mutex g_batch_mu;
+std::map<BatchKey, cudaGraphExec_t> g_batch_graphs;
+std::vector<cudaStream_t> g_batch_streams;
+std::vector<cudaEvent_t> g_batch_events;
+cudaStream_t g_capture_stream = nullptr;  // private: the caller's stream may be the legacy one
+
+void drop_batch_graphs(rom_s* h) {
+    std::lock_guard<std::mutex> lk(g_batch_mu);
+    for (auto it = g_batch_graphs.begin(); it != g_batch_graphs.end();) {
+        bool uses = false;
+        const auto& w = it->first.words;
+        for (size_t k = 6; k < w.size(); k += 6) uses |= (w[k] == (uintptr_t)h);
+        if (uses) {
+            cudaGraphExecDestroy(it->second);
+            it = g_batch_graphs.erase(it);
+        } else {
+            ++it;
+        }
+    }
+}
+
+rom_status batch_streams(size_t n) {
+    if (!g_capture_stream) ROM_CUDA(cudaStreamCreateWithFlags(&g_capture_stream, cudaStreamNonBlocking));
+    while (g_batch_streams.size() < n) {
+        cudaStream_t s;
+        ROM_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+        g_batch_streams.push_back(s);
+    }
+    while (g_batch_events.size() < n + 1) {
+        cudaEvent_t e;
+        ROM_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        g_batch_events.push_back(e);
+    }
+    return ROM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+rom_status rom_run_batched(const rom_job* jobs, int njobs, int nsteps, int r, int prec, void* stream) {
+    if (!jobs || njobs < 1 || nsteps < 0 || r < 0 || !valid_prec(prec)) return ROM_E_INVAL;
+    for (int i = 0; i < njobs; ++i) {
+        const rom_job& j = jobs[i];
+        if (!j.h || !j.V || !j.S || j.M < 1) return ROM_E_INVAL;
+        if (!is_device_ptr(j.V) || !is_device_ptr(j.S)) return ROM_E_INVAL;  // device buffers only
+        if (j.traces && (r < 1 || j.h->R < 1)) return ROM_E_INVAL;
+        for (int k = 0; k < i; ++k)
+            if (jobs[k].h == j.h) return ROM_E_INVAL;  // one job per handle (handles own workspaces)
+    }
+    if (nsteps == 0) return ROM_OK;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const bool tc = prec == ROM_TF32X3 || prec == ROM_BF16X3 || prec == ROM_BF16;
+    int dev = 0, nsm = 0;
+    ROM_CUDA(cudaGetDevice(&dev));
+    ROM_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    // share of the SMs per job, proportional to its work per step
+    std::vector<double> cost(njobs);
+    double total = 0.0;
+    for (int i = 0; i < njobs; ++i) {
+        const double K = (double)(jobs[i].h->Kv > jobs[i].h->Ks ? jobs[i].h->Kv : jobs[i].h->Ks);
+        cost[i] = 4.0 * K * K * jobs[i].M;
+        total += cost[i];
+    }
+    std::vector<Rank2Plan> plans(njobs);
+    std::vector<double> est(njobs);
+    for (int i = 0; i < njobs; ++i) {
+        rom_s* h = jobs[i].h;
+        if (tc) {
+            rom_status s = tc_prepare(h, prec, st);
+            if (s != ROM_OK) return s;
+            est[i] = cost[i];
+            continue;
+        }
+        const int Kp = h->Kp;
+        const int cs_guess = Kp > 512 ? Kp / 64 : Kp / 32;
+        const int budget = (int)((double)nsm * cost[i] / total / cs_guess);
+        bool ok = false;
+        if (prec == ROM_FP32) ok = plan_rank2_split_f32(Kp, jobs[i].M, h->R, &plans[i], budget > 0 ? budget : 1);
+        if (ok) plans[i].variant = 2;
+        if (!ok) {
+            ok = prec == ROM_FP64 ? plan_rank2_simt_f64(Kp, jobs[i].M, h->R, false, &plans[i])
+                                  : plan_rank2_simt_f32(Kp, jobs[i].M, h->R, false, &plans[i],
+                                                        budget > 0 ? budget : 1);
+            if (ok) plans[i].variant = 1;
+        }
+        if (!ok) return ROM_E_UNSUPPORTED;
+        est[i] = cost[i] / (double)(plans[i].nclusters * plans[i].cs);
+    }
+    std::vector<int> order(njobs);
+    for (int i = 0; i < njobs; ++i) order[i] = i;
+    std::sort(order.begin(), order.end(), [&](int x, int y) { return est[x] > est[y]; });
+
+    BatchKey key;
+    key.words = {(uintptr_t)njobs, (uintptr_t)nsteps, (uintptr_t)r, (uintptr_t)prec, (uintptr_t)st,
+                 (uintptr_t)dev};
+    for (int i = 0; i < njobs; ++i) {
+        const rom_job& j = jobs[i];
+        key.words.insert(key.words.end(), {(uintptr_t)j.h, (uintptr_t)j.V, (uintptr_t)j.S,
+                                           (uintptr_t)j.T, (uintptr_t)j.M, (uintptr_t)j.traces});
+    }
+    std::lock_guard<std::mutex> lk(g_batch_mu);
+    auto it = g_batch_graphs.find(key);
+    if (it == g_batch_graphs.end()) {
+        const size_t npool = (size_t)(njobs < 32 ? njobs : 32);
+        rom_status s = batch_streams(npool);
+        if (s != ROM_OK) return s;
+        cudaGraph_t graph = nullptr;
+        cudaStream_t cap = g_capture_stream;
+        ROM_CUDA(cudaStreamBeginCapture(cap, cudaStreamCaptureModeRelaxed));
+        cudaEvent_t fork = g_batch_events[npool];
+        cudaError_t e = cudaEventRecord(fork, cap);
+        rom_status rs = ROM_OK;
+        for (size_t k = 0; k < npool && e == cudaSuccess; ++k) e = cudaStreamWaitEvent(g_batch_streams[k], fork, 0);
+        for (int oi = 0; oi < njobs && e == cudaSuccess && rs == ROM_OK; ++oi) {
+            const int i = order[oi];
+            const rom_job& j = jobs[i];
+            cudaStream_t ss = g_batch_streams[oi % npool];
+            RunBufs b = {j.V, j.S, const_cast<void*>(j.T), nullptr, nullptr, nullptr, j.traces};
+            rs = tc ? run_rank2_tc(j.h, b, j.M, nsteps, 0, r, prec, ss)
+                    : launch_simt_with_plan(j.h, b, j.M, nsteps, 0, r, prec, plans[i], ss);
+        }
+        for (size_t k = 0; k < npool && e == cudaSuccess; ++k) {
+            e = cudaEventRecord(g_batch_events[k], g_batch_streams[k]);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(cap, g_batch_events[k], 0);
+        }
+        cudaError_t e2 = cudaStreamEndCapture(cap, &graph);
+        if (e == cudaSuccess) e = e2;
+        if (rs != ROM_OK) {
+            if (graph) cudaGraphDestroy(graph);
+            return rs;
+        }
+        if (e != cudaSuccess) {
+            if (graph) cudaGraphDestroy(graph);
+            return cuda_fail(e, "rom_run_batched capture");
+        }
+        cudaGraphExec_t exec = nullptr;
+        e = cudaGraphInstantiate(&exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) return cuda_fail(e, "rom_run_batched instantiate");
+        it = g_batch_graphs.emplace(key, exec).first;
+    }
+    ROM_CUDA(cudaGraphLaunch(it->second, st));
+    if (tc) {
+        // tensor-core jobs use per-handle workspaces that a later call may
+        // reallocate: their graphs are not kept
+        cudaGraphExec_t exec = it->second;
+        g_batch_graphs.erase(it);
+        ROM_CUDA(cudaStreamSynchronize(st));
+        cudaGraphExecDestroy(exec);
+    }
     return ROM_OK;
 }
 

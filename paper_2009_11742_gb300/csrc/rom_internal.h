@@ -34,6 +34,7 @@ struct Rank2Args {
     int nsteps;
     int r;         // trace interval (> 0 when traces != null)
     int rpc;       // trace rows of C per CTA
+    int nrt;               // 32-row tiles owned per CTA by the one-block kernel (1 or 2)
     long long spin_limit;  // clock cycles a device-side wait may last before ROM_E_TIMEOUT
     int debug_skip_push;   // fault injection: CTA 0 never publishes (forces the timeout path)
 };
@@ -49,6 +50,7 @@ struct Rank2Plan {
     size_t smem;
     bool resident; // operators kept in registers for the whole run
     int variant;   // 1: one-block, 2: two-block split-role, 3: two-block dataflow
+    int nrt;       // one-block kernel: 32-row tiles per CTA (2 when Kp > 512)
 };
 
 // Host launchers (defined in the kernel translation units).  Return a CUDA
@@ -56,13 +58,13 @@ struct Rank2Plan {
 cudaError_t launch_rank2_simt_f32(const Rank2Args& a, const Rank2Plan& plan, cudaStream_t st);
 cudaError_t launch_rank2_simt_f64(const Rank2Args& a, const Rank2Plan& plan, cudaStream_t st);
 // Fill `plan` for M columns; returns false if the shape is not supported.
-bool plan_rank2_simt_f32(int Kp, int M, int R, bool rank1, Rank2Plan* plan);
+bool plan_rank2_simt_f32(int Kp, int M, int R, bool rank1, Rank2Plan* plan, int cluster_budget = 0);
 bool plan_rank2_simt_f64(int Kp, int M, int R, bool rank1, Rank2Plan* plan);
 
 // Two-block split-role FP32 kernels (velocity and stress rows on different
 // CTAs): variant 2 synchronises with a cluster barrier per phase, variant 3
 // with per-block mbarriers fed by asynchronous stores (bounded waits).
-bool plan_rank2_split_f32(int Kp, int M, int R, Rank2Plan* plan);
+bool plan_rank2_split_f32(int Kp, int M, int R, Rank2Plan* plan, int cluster_budget = 0);
 bool plan_rank2_dataflow_f32(int Kp, int M, int R, Rank2Plan* plan);
 cudaError_t launch_rank2_split_f32(const Rank2Args& a, const Rank2Plan& plan, cudaStream_t st);
 

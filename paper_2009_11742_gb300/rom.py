@@ -36,7 +36,7 @@ PRECISIONS = {"fp64": ROM_FP64, "fp32": ROM_FP32, "tf32x3": ROM_TF32X3,
 EXPORTED = ["rom_create", "rom_destroy", "rom_spectral_radius", "rom_sync_status",
             "rom_get_dims", "rom_set_kernel", "rom_get_plan", "rom_set_tc_columns", "rom_set_wait_limit",
             "rom_debug_inject_stall", "rom_run_rank2", "rom_run_rank2_ex", "rom_run_rank1",
-            "rom_run_rank1_ensemble", "rom_rel_l2", "rom_spectral_radius_noalloc",
+            "rom_run_rank1_ensemble", "rom_run_batched", "rom_rel_l2", "rom_spectral_radius_noalloc",
             "rom_status_string", "rom_last_error", "rom_version"]
 
 _lock = threading.Lock()
@@ -73,6 +73,7 @@ def _signatures(lib):
                                   _vp]),
         "rom_run_rank1": (_i, [_vp, _vp, _vp, _d, _i, _l, _i, _vp, _i, _vp]),
         "rom_run_rank1_ensemble": (_i, [_vp, _vp, _vp, _vp, _i, _i, _l, _i, _vp, _i, _vp]),
+        "rom_run_batched": (_i, [ctypes.c_void_p, _i, _i, _i, _i, _vp]),
         "rom_rel_l2": (_i, [_vp, _i, _vp, _i, ctypes.c_size_t, ctypes.POINTER(_d), _vp]),
         "rom_spectral_radius_noalloc": (_i, [_vp, _vp, _i, _i, ctypes.POINTER(_d), _vp]),
         "rom_status_string": (ctypes.c_char_p, [_i]),
@@ -196,6 +197,35 @@ def rom_run_rank1(h, v, s, T, nsteps, n0, r, trace, prec, stream):
 
 def rom_run_rank1_ensemble(h, V, S, T, M, nsteps, n0, r, traces, prec, stream):
     return load().rom_run_rank1_ensemble(h, V, S, T, M, nsteps, n0, r, traces, prec, stream)
+
+
+class rom_job(ctypes.Structure):
+    _fields_ = [("h", _vp), ("V", _vp), ("S", _vp), ("T", _vp), ("M", _i), ("traces", _vp)]
+
+
+def rom_run_batched(jobs, njobs, nsteps, r, prec, stream):
+    """jobs: a ctypes array of rom_job."""
+    return load().rom_run_batched(ctypes.cast(jobs, ctypes.c_void_p), njobs, nsteps, r, prec,
+                                  stream)
+
+
+def run_batched(items, nsteps, r=0, prec="fp32", stream=None):
+    """items: list of (Rom, V, S, T, traces or None) with column-major device
+    states as for Rom.run_rank2.  One graph launch for all of them."""
+    p = PRECISIONS.get(prec, prec)
+    dt = Rom.dtype_of(p)
+    arr = (rom_job * len(items))()
+    for i, (h, V, S, T, tr) in enumerate(items):
+        M = V.shape[1]
+        _check_colmajor(V, h.Kv, M, "V", dt)
+        _check_colmajor(S, h.Ks, M, "S", dt)
+        if T is not None:
+            _check_vec(T, M, "T", dt)
+        if tr is not None:
+            _check_vec(tr, (nsteps // r) * M * h.R, "traces", dt)
+        arr[i] = rom_job(h.h, _ptr(V), _ptr(S), _ptr(T), M, _ptr(tr))
+    st = rom_run_batched(arr, len(items), int(nsteps), int(r), p, _stream_handle(stream))
+    _chk(st, "rom_run_batched")
 
 
 def rom_rel_l2(x, x_dtype, ref, ref_dtype, n, stream=None):

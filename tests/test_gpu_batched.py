@@ -1,0 +1,110 @@
+"""GPU parity of the batched many-ensemble launch (rom_run_batched) against
+the FP64 oracle and against one-at-a-time rank-2 runs."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2009_11742_gb300 import inputs
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def rel(a, b):
+    a = np.asarray(a, np.float64)
+    b = np.asarray(b, np.float64)
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+@pytest.fixture(scope="module")
+def rom():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2009_11742_gb300 import build
+    build.build()
+    from paper_2009_11742_gb300 import rom as R
+    return R
+
+
+def make_jobs(R, sizes, with_traces, seed0=100):
+    jobs, probs = [], []
+    for i, (K, M, Rr) in enumerate(sizes):
+        p = inputs.make_problem(K, K, M, Rr, seed=seed0 + i)
+        h = R.Rom.from_problem(p)
+        V = R.Rom.new_state(K, M, "fp32")
+        S = R.Rom.new_state(K, M, "fp32")
+        T = torch.as_tensor(p.T, device="cuda")
+        tr = None
+        if with_traces and Rr:
+            tr = torch.zeros((with_traces, M, Rr), device="cuda")
+        jobs.append((h, V, S, T, tr))
+        probs.append(p)
+    return jobs, probs
+
+
+SIZES = [(64, 4, 2), (128, 17, 3), (200, 33, 0), (512, 64, 8), (576, 100, 4), (768, 5, 2),
+         (320, 250, 0), (64, 256, 1)]
+
+
+def test_batched_vs_oracle_and_individual(rom):
+    N, r = 120, 10
+    jobs, probs = make_jobs(rom, SIZES, with_traces=N // r)
+    rom.run_batched(jobs, N, r=r, prec="fp32")
+    torch.cuda.synchronize()
+    for (h, V, S, T, tr), p in zip(jobs, probs):
+        assert h.sync_status() == 0
+        Z = np.zeros((p.Kv, p.M))
+        Vo, So, tro = oracle.forward(p.Avs, p.Asv, p.g, p.C if p.R else None, p.dt, Z, Z, N,
+                                     T=p.T, r=r if p.R else 0)
+        assert rel(V.cpu().numpy(), Vo) <= 1e-4 and rel(S.cpu().numpy(), So) <= 1e-4
+        if tr is not None:
+            assert rel(tr.transpose(1, 2).cpu().numpy(), tro) <= 1e-4
+        # the same job alone through rom_run_rank2 gives the same bits
+        V1 = rom.Rom.new_state(p.Kv, p.M, "fp32")
+        S1 = rom.Rom.new_state(p.Ks, p.M, "fp32")
+        h.run_rank2(V1, S1, T, N, prec="fp32")
+        torch.cuda.synchronize()
+        assert torch.equal(V1, V) and torch.equal(S1, S)
+
+
+def test_batched_graph_replay(rom):
+    """The second call replays the cached graph: the state advances by
+    another nsteps (forcing restarts at t = 0 for every call)."""
+    sizes = [(96, 10, 0), (256, 40, 0), (640, 12, 0)]
+    jobs, probs = make_jobs(rom, sizes, with_traces=0, seed0=200)
+    N = 80
+    rom.run_batched(jobs, N, prec="fp32")
+    rom.run_batched(jobs, N, prec="fp32")
+    torch.cuda.synchronize()
+    for (h, V, S, T, _), p in zip(jobs, probs):
+        Z = np.zeros((p.Kv, p.M))
+        V1, S1, _ = oracle.forward(p.Avs, p.Asv, p.g, None, p.dt, Z, Z, N, T=p.T)
+        V2, S2, _ = oracle.forward(p.Avs, p.Asv, p.g, None, p.dt, V1, S1, N, T=p.T)
+        assert rel(V.cpu().numpy(), V2) <= 1e-4 and rel(S.cpu().numpy(), S2) <= 1e-4
+
+
+def test_batched_rejects_bad_jobs(rom):
+    jobs, _ = make_jobs(rom, [(64, 4, 0), (64, 4, 0)], with_traces=0, seed0=300)
+    dup = [jobs[0], jobs[0]]
+    with pytest.raises(rom.RomError):
+        rom.run_batched(dup, 10, prec="fp32")
+
+
+def test_batched_workload3_full_size_sampled(rom):
+    """Workload 3: 64 ROMs, K_i in {64..768}, M_i in [4, 256], 5000 steps, one
+    graph launch; the oracle recomputes two columns of every eighth ROM."""
+    probs = inputs.batched_problems()
+    jobs = []
+    for p in probs:
+        h = rom.Rom.from_problem(p)
+        jobs.append((h, rom.Rom.new_state(p.Kv, p.M, "fp32"), rom.Rom.new_state(p.Ks, p.M, "fp32"),
+                     torch.as_tensor(p.T, device="cuda"), None))
+    rom.run_batched(jobs, 5000, prec="fp32")
+    torch.cuda.synchronize()
+    for i in range(0, 64, 8):
+        h, V, S, T, _ = jobs[i]
+        p = probs[i]
+        cols = np.array([0, p.M - 1])
+        Vo, So, _ = oracle.problem_forward(p, nsteps=5000, r=0, columns=cols)
+        assert rel(V.cpu().numpy()[:, cols], Vo) <= 1e-4
+        assert rel(S.cpu().numpy()[:, cols], So) <= 1e-4
