@@ -232,6 +232,30 @@ typedef struct {
 rom_status rom_run_batched(const rom_job* jobs, int njobs, int nsteps, int r, int prec,
                            void* stream);
 
+/*
+ * rom_adjoint -- gradients of the receiver-trace misfit
+ *     L = sum_{n=1..N} sum_m || C V_m^n - ystar_m^n ||^2
+ * with respect to the initial state (V0, S0) and the Ricker periods T, by a
+ * reverse-time leapfrog (the paper has no adjoint; the reverse step is the
+ * exact transpose of the forward step of Sec. 3.1):
+ *     lamV += 2 C^T r^{n+1} + dt Asv^T lamS ,  dL/dT_m += dt g^T lamV df/dT ,
+ *     lamS += dt Avs^T lamV ,                  n = N-1 .. 0,
+ * r^n = C V^n - ystar^n.  ystar holds N records, record n-1 = ystar^n as
+ * R x M column-major ([n-1][m][j]).  The forward states come from a forward
+ * sweep that keeps a checkpoint (V, S and their Kahan carries) every
+ * ckpt_every steps (0: keep every trace, one segment) and recomputes each
+ * segment's traces, bit for bit, before reversing it.
+ * Outputs: gV0 (Kv x M), gS0 (Ks x M), gT (M) device float; *loss (host).
+ * workspace: device, rom_adjoint_workspace_size bytes, or NULL to let the
+ * library allocate it for the call.  Device buffers only; FP32 only;
+ * Kv, Ks <= 512.  Synchronous on `stream`.
+ */
+rom_status rom_adjoint(rom_t h, const void* V0, const void* S0, const void* T, int M, int nsteps,
+                       const void* ystar, int ckpt_every, void* gV0, void* gS0, void* gT,
+                       double* loss, void* workspace, size_t ws_bytes, int prec, void* stream);
+/* Workspace bytes rom_adjoint needs (0 for unsupported arguments). */
+size_t rom_adjoint_workspace_size(rom_t h, int M, int nsteps, int ckpt_every, int prec);
+
 /* ------------------------------------------------------------- utilities */
 
 /*

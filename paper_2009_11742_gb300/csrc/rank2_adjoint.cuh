@@ -1,0 +1,198 @@
+// Reverse-time adjoint of the rank-2 leapfrog for the receiver-trace misfit
+//     L = sum_{n=1..N} sum_m || C V_m^n - ystar_m^n ||^2 .
+// The paper has no adjoint; this is the exact reverse of the forward step
+// V^{n+1} = V^n + dt (Avs S^n + g f_n^T), S^{n+1} = S^n + dt Asv V^{n+1}
+// (Sec. 3.1).  With lamV, lamS the adjoints of (V, S), reverse step n
+// (n = N-1 .. 0) is
+//     half A:  lamV <- lamV + 2 C^T r^{n+1} + dt Asv^T lamS      (= a_V^n)
+//              dL/dT_m += dt g^T a_V^n[:, m] df/dT(t_n; T_m)
+//     half B:  lamS <- lamS + dt Avs^T a_V^n
+// with r^n = C V^n - ystar^n, starting from lamV = lamS = 0; after n = 0,
+// lamV = dL/dV^0 and lamS = dL/dS^0.
+//
+// The kernel is the one-block cluster kernel of rank2_simt.cuh run backwards
+// in time with the transposed operators (the column-major copies of Asv and
+// Avs are the row-major Asv^T and Avs^T) resident in registers; half A's
+// epilogue adds the rank-R source 2 C^T r^{n+1} (C columns of the CTA's rows
+// and the step's residuals staged in shared memory), and a deterministic
+// per-CTA column reduction accumulates the period gradient.
+#pragma once
+
+#include <cooperative_groups.h>
+#include <cuda_runtime.h>
+
+#include "dev_common.cuh"
+#include "rank2_simt.cuh"
+#include "rom_internal.h"
+
+namespace romk {
+
+struct AdjSmem {
+    size_t Vf, Sf, cV, cS, Ccol, rbuf, g, T, gT, total;
+};
+
+__host__ __device__ inline AdjSmem adj_smem_layout(int Wa, int Kp, int R) {
+    AdjSmem s{};
+    size_t o = 0;
+    s.Vf = o;   o += align16((size_t)Wa * Kp * sizeof(float));
+    s.Sf = o;   o += align16((size_t)Wa * Kp * sizeof(float));
+    s.cV = o;   o += align16((size_t)Wa * kRowsPerCta * sizeof(float));
+    s.cS = o;   o += align16((size_t)Wa * kRowsPerCta * sizeof(float));
+    s.Ccol = o; o += align16((size_t)R * kRowsPerCta * sizeof(float));
+    s.rbuf = o; o += align16((size_t)R * Wa * sizeof(float));
+    s.g = o;    o += align16((size_t)kRowsPerCta * sizeof(float));
+    s.T = o;    o += align16((size_t)Wa * sizeof(float));
+    s.gT = o;   o += align16((size_t)Wa * sizeof(float));
+    s.total = o;
+    return s;
+}
+
+// Half A of a reverse step on the CTA's 32 rows:
+//   Y_own += dt (op . X) + 2 C_own^T r   (Kahan-compensated).
+template <int KI, int CB>
+__device__ __forceinline__ void adj_half_a(const float (&op)[2][4 * KI], const float* __restrict__ X,
+                                           float* __restrict__ Y, float* __restrict__ comp,
+                                           const float* __restrict__ Ccol, const float* __restrict__ rbuf,
+                                           const int R, const float dt, const int Wa, const int Kp,
+                                           const int row0, const int rp, const int j) {
+    for (int c0 = 0; c0 < Wa; c0 += CB) {
+        float acc[2][CB];
+#pragma unroll
+        for (int cc = 0; cc < CB; ++cc) { acc[0][cc] = 0.f; acc[1][cc] = 0.f; }
+#pragma unroll
+        for (int i = 0; i < KI; ++i) {
+            float x[CB][4];
+#pragma unroll
+            for (int cc = 0; cc < CB; ++cc) load4(X + (size_t)(c0 + cc) * Kp + 64 * i + 4 * j, x[cc]);
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+#pragma unroll
+                for (int cc = 0; cc < CB; ++cc) {
+                    acc[0][cc] = __fmaf_rn(op[0][4 * i + q], x[cc][q], acc[0][cc]);
+                    acc[1][cc] = __fmaf_rn(op[1][4 * i + q], x[cc][q], acc[1][cc]);
+                }
+        }
+        float v[2 * CB];
+#pragma unroll
+        for (int cc = 0; cc < CB; ++cc) { v[cc] = acc[0][cc]; v[CB + cc] = acc[1][cc]; }
+        int vi;
+        bool active;
+        const float tot = reduce_scatter16<float, 2 * CB>(v, j, vi, active);
+        if (active) {
+            const int rl = 2 * rp + vi / CB;
+            const int c = c0 + vi % CB;
+            float src = 0.f;
+            for (int jr = 0; jr < R; ++jr) src = __fmaf_rn(Ccol[jr * kRowsPerCta + rl], rbuf[jr * Wa + c], src);
+            const float inc = __fmaf_rn(tot, dt, 2.f * src);
+            float* yp = Y + (size_t)c * Kp + row0 + rl;
+            *yp = kahan_add(*yp, inc, comp[c * kRowsPerCta + rl]);
+        }
+    }
+}
+
+template <int KI, int CB>
+__global__ void __launch_bounds__(kThreads, 1) rank2_adjoint_kernel(const AdjArgs a) {
+    cg::cluster_group cluster = cg::this_cluster();
+    const int cs = (int)cluster.num_blocks();
+    const int crank = (int)cluster.block_rank();
+    const int blk = blockIdx.x / cs;
+    const int col0 = blk * a.Wv;
+    const int ncol = min(a.Wv, a.M - col0);
+    const int Wa = a.Wa, Kp = a.Kp, R = a.R;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int j = lane & 15;
+    const int rp = warp * 2 + (lane >> 4);
+    const int row0 = crank * kRowsPerCta;
+    const float dt = (float)a.dt;
+
+    extern __shared__ __align__(16) unsigned char smem[];
+    const AdjSmem L = adj_smem_layout(Wa, Kp, R);
+    float* Vf = reinterpret_cast<float*>(smem + L.Vf);
+    float* Sf = reinterpret_cast<float*>(smem + L.Sf);
+    float* cV = reinterpret_cast<float*>(smem + L.cV);
+    float* cS = reinterpret_cast<float*>(smem + L.cS);
+    float* Ccol = reinterpret_cast<float*>(smem + L.Ccol);  // [R][32]: C[j][row0 + rl]
+    float* rbuf = reinterpret_cast<float*>(smem + L.rbuf);  // [R][Wa]: residual of the step
+    float* gown = reinterpret_cast<float*>(smem + L.g);
+    float* Tcol = reinterpret_cast<float*>(smem + L.T);
+    float* gTacc = reinterpret_cast<float*>(smem + L.gT);
+
+    for (int idx = tid; idx < Wa * Kp; idx += kThreads) {
+        const int c = idx / Kp, k = idx % Kp;
+        Vf[idx] = (c < ncol && k < a.Kv) ? a.lamV[(size_t)(col0 + c) * a.Kv + k] : 0.f;
+        Sf[idx] = (c < ncol && k < a.Ks) ? a.lamS[(size_t)(col0 + c) * a.Ks + k] : 0.f;
+    }
+    for (int idx = tid; idx < Wa * kRowsPerCta; idx += kThreads) {
+        const int c = idx / kRowsPerCta, rl = idx % kRowsPerCta, row = row0 + rl;
+        cV[idx] = (c < ncol && row < a.Kv) ? a.compV[(size_t)(col0 + c) * a.Kv + row] : 0.f;
+        cS[idx] = (c < ncol && row < a.Ks) ? a.compS[(size_t)(col0 + c) * a.Ks + row] : 0.f;
+    }
+    for (int idx = tid; idx < R * kRowsPerCta; idx += kThreads) {
+        const int jr = idx / kRowsPerCta, rl = idx % kRowsPerCta;
+        Ccol[idx] = a.C_rm[(size_t)jr * Kp + row0 + rl];
+    }
+    if (tid < kRowsPerCta) gown[tid] = a.g_p[row0 + tid];
+    for (int c = tid; c < Wa; c += kThreads) {
+        Tcol[c] = (c < ncol) ? a.Tper[col0 + c] : 1.f;
+        gTacc[c] = (c < ncol) ? a.gTpart[(size_t)crank * a.M + col0 + c] : 0.f;
+    }
+    float opA[2][4 * KI], opB[2][4 * KI];
+    load_op_rows<float, KI>(opA, a.opA_rm, Kp, row0 + 2 * rp, j);
+    load_op_rows<float, KI>(opB, a.opB_rm, Kp, row0 + 2 * rp, j);
+    cluster.sync();
+
+    for (int n = a.n_hi - 1; n >= a.n_lo; --n) {
+        // residual r^{n+1} = C V^{n+1} - ystar^{n+1} of this block's columns
+        const int rec = n + 1 - a.rec_base;  // trace record holding C V^{n+1}
+        for (int idx = tid; idx < R * Wa; idx += kThreads) {
+            const int jr = idx / Wa, c = idx % Wa;
+            float rv = 0.f;
+            if (c < ncol) {
+                const size_t o = ((size_t)rec * a.M + col0 + c) * R + jr;
+                const size_t oy = ((size_t)n * a.M + col0 + c) * R + jr;  // ystar record of V^{n+1}
+                rv = a.traces[o] - a.ystar[oy];
+            }
+            rbuf[idx] = rv;
+        }
+        __syncthreads();
+        // ---- half A: lamV <- lamV + 2 C^T r^{n+1} + dt Asv^T lamS
+        adj_half_a<KI, CB>(opA, Sf, Vf, cV, Ccol, rbuf, R, dt, Wa, Kp, row0, rp, j);
+        __syncthreads();
+        // period gradient: dt (g_own . a_V[:, c]) df/dT(t_n; T_c), fixed reduction order
+        for (int c = warp; c < ncol; c += kThreads / 32) {
+            float s = gown[lane] * Vf[(size_t)c * Kp + row0 + lane];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+            if (lane == 0) gTacc[c] = __fmaf_rn(dt * s, ricker_dT_eval((long long)a.n0 + n, a.dt, Tcol[c]), gTacc[c]);
+        }
+        push_own_rows<float>(cluster, Vf, Wa, Kp, row0, cs, crank, 1);
+        cluster.sync();
+        // ---- half B: lamS <- lamS + dt Avs^T a_V
+        half_step<float, KI, CB, false>(opB, Vf, Sf, cS, gown, gown, dt, Wa, Kp, row0, rp, j);
+        __syncthreads();
+        push_own_rows<float>(cluster, Sf, Wa, Kp, row0, cs, crank, 1);
+        cluster.sync();
+    }
+
+    int bad = 0;
+    for (int idx = tid; idx < ncol * kRowsPerCta; idx += kThreads) {
+        const int c = idx / kRowsPerCta, rl = idx % kRowsPerCta, row = row0 + rl;
+        if (row < a.Kv) {
+            const float x = Vf[(size_t)c * Kp + row];
+            a.lamV[(size_t)(col0 + c) * a.Kv + row] = x;
+            a.compV[(size_t)(col0 + c) * a.Kv + row] = cV[c * kRowsPerCta + rl];
+            bad |= !is_finite(x);
+        }
+        if (row < a.Ks) {
+            const float x = Sf[(size_t)c * Kp + row];
+            a.lamS[(size_t)(col0 + c) * a.Ks + row] = x;
+            a.compS[(size_t)(col0 + c) * a.Ks + row] = cS[c * kRowsPerCta + rl];
+            bad |= !is_finite(x);
+        }
+    }
+    for (int c = tid; c < ncol; c += kThreads) a.gTpart[(size_t)crank * a.M + col0 + c] = gTacc[c];
+    bad = __syncthreads_or(bad);
+    if (bad && tid == 0 && a.status) atomicCAS(a.status, 0, 6 /* ROM_E_NONFINITE */);
+}
+
+}  // namespace romk

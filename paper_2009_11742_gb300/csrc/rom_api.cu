@@ -846,6 +846,157 @@ rom_status rom_run_batched(const rom_job* jobs, int njobs, int nsteps, int r, in
     return ROM_OK;
 }
 
+// ---------------------------------------------------------------- adjoint
+
+}  // extern "C"
+
+namespace {
+
+struct AdjLayout {
+    size_t traces, ckpt, work, acomp, gtp, acc, total;
+    int seg, nseg;
+};
+
+AdjLayout adjoint_layout(const rom_s* h, int M, int nsteps, int ckpt_every) {
+    AdjLayout L{};
+    auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
+    L.seg = ckpt_every > 0 && ckpt_every < nsteps ? ckpt_every : nsteps;
+    L.nseg = (nsteps + L.seg - 1) / L.seg;
+    const size_t kvm = (size_t)(h->Kv + h->Ks) * M;  // one (V, S) pair
+    size_t o = 0;
+    L.traces = o; o += al(sizeof(float) * (size_t)L.seg * h->R * M);
+    L.ckpt = o;   o += al(sizeof(float) * 2 * kvm * (size_t)L.nseg);   // state + Kahan carries
+    L.work = o;   o += al(sizeof(float) * 2 * kvm);
+    L.acomp = o;  o += al(sizeof(float) * kvm);
+    L.gtp = o;    o += al(sizeof(float) * 16 * (size_t)M);
+    L.acc = o;    o += al(sizeof(double) * 2);
+    L.total = o;
+    return L;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t rom_adjoint_workspace_size(rom_t h, int M, int nsteps, int ckpt_every, int prec) {
+    if (!h || M < 1 || nsteps < 1 || ckpt_every < 0 || prec != ROM_FP32) return 0;
+    return adjoint_layout(h, M, nsteps, ckpt_every).total;
+}
+
+rom_status rom_adjoint(rom_t h, const void* V0, const void* S0, const void* T, int M, int nsteps,
+                       const void* ystar, int ckpt_every, void* gV0, void* gS0, void* gT,
+                       double* loss, void* workspace, size_t ws_bytes, int prec, void* stream) {
+    if (!h || !V0 || !S0 || !T || !ystar || !gV0 || !gS0 || !gT || M < 1 || nsteps < 1 ||
+        ckpt_every < 0 || h->R < 1)
+        return ROM_E_INVAL;
+    if (prec != ROM_FP32) return ROM_E_UNSUPPORTED;
+    const void* ptrs[] = {V0, S0, T, ystar, gV0, gS0, gT};
+    for (const void* p : ptrs)
+        if (!is_device_ptr(p)) return ROM_E_INVAL;
+    AdjPlan ap;
+    if (!plan_adjoint(h->Kp, M, h->R, &ap)) {
+        snprintf(g_last_error, sizeof(g_last_error), "no adjoint plan for Kp=%d M=%d", h->Kp, M);
+        return ROM_E_UNSUPPORTED;
+    }
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const AdjLayout L = adjoint_layout(h, M, nsteps, ckpt_every);
+    void* own_ws = nullptr;
+    if (!workspace) {
+        ROM_CUDA(cudaMalloc(&own_ws, L.total));
+        workspace = own_ws;
+    } else if (ws_bytes < L.total) {
+        return ROM_E_INVAL;
+    }
+    char* ws = static_cast<char*>(workspace);
+    float* traces = reinterpret_cast<float*>(ws + L.traces);
+    float* ckpt = reinterpret_cast<float*>(ws + L.ckpt);
+    float* work = reinterpret_cast<float*>(ws + L.work);
+    float* acomp = reinterpret_cast<float*>(ws + L.acomp);
+    float* gtp = reinterpret_cast<float*>(ws + L.gtp);
+    double* acc = reinterpret_cast<double*>(ws + L.acc);
+    const size_t nv = (size_t)h->Kv * M, ns = (size_t)h->Ks * M, kvm = nv + ns;
+    float* wV = work;
+    float* wS = work + nv;
+    float* wcV = work + kvm;
+    float* wcS = work + kvm + nv;
+    const size_t rec = (size_t)h->R * M;
+    const float* ys = static_cast<const float*>(ystar);
+    rom_status s = ROM_OK;
+    cudaError_t e = cudaSuccess;
+    auto fail = [&](cudaError_t err, const char* where) {
+        s = cuda_fail(err, where);
+        return s;
+    };
+    auto forward = [&](int n_start, int len) -> rom_status {
+        RunBufs b = {wV, wS, const_cast<void*>(T), nullptr, wcV, wcS, traces};
+        return run_rank2_device(h, b, M, len, n_start, 1, ROM_FP32, false, st);
+    };
+    // ---- forward sweep: checkpoints, traces, misfit
+    e = cudaMemcpyAsync(wV, V0, sizeof(float) * nv, cudaMemcpyDeviceToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(wS, S0, sizeof(float) * ns, cudaMemcpyDeviceToDevice, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(wcV, 0, sizeof(float) * kvm, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(acc, 0, sizeof(double) * 2, st);
+    for (int k = 0; k < L.nseg && e == cudaSuccess && s == ROM_OK; ++k) {
+        const int n_start = k * L.seg, len = nsteps - n_start < L.seg ? nsteps - n_start : L.seg;
+        e = cudaMemcpyAsync(ckpt + (size_t)k * 2 * kvm, work, sizeof(float) * 2 * kvm,
+                            cudaMemcpyDeviceToDevice, st);
+        if (e != cudaSuccess) break;
+        s = forward(n_start, len);
+        if (s == ROM_OK) e = launch_rel_l2(traces, 1, ys + (size_t)n_start * rec, 1, (size_t)len * rec, acc, st);
+    }
+    // ---- reverse sweep, segment by segment (recomputing each one's traces)
+    if (e == cudaSuccess && s == ROM_OK) {
+        e = cudaMemsetAsync(gV0, 0, sizeof(float) * nv, st);
+        if (e == cudaSuccess) e = cudaMemsetAsync(gS0, 0, sizeof(float) * ns, st);
+        if (e == cudaSuccess) e = cudaMemsetAsync(acomp, 0, sizeof(float) * kvm, st);
+        if (e == cudaSuccess) e = cudaMemsetAsync(gtp, 0, sizeof(float) * 16 * (size_t)M, st);
+    }
+    for (int k = L.nseg - 1; k >= 0 && e == cudaSuccess && s == ROM_OK; --k) {
+        const int n_start = k * L.seg, len = nsteps - n_start < L.seg ? nsteps - n_start : L.seg;
+        if (k != L.nseg - 1) {  // the last segment's traces are still in place
+            e = cudaMemcpyAsync(work, ckpt + (size_t)k * 2 * kvm, sizeof(float) * 2 * kvm,
+                                cudaMemcpyDeviceToDevice, st);
+            if (e != cudaSuccess) break;
+            s = forward(n_start, len);
+            if (s != ROM_OK) break;
+        }
+        AdjArgs aa = {};
+        aa.opA_rm = static_cast<const float*>(h->Asv_cm[1]);
+        aa.opB_rm = static_cast<const float*>(h->Avs_cm[1]);
+        aa.g_p = static_cast<const float*>(h->g_p[1]);
+        aa.C_rm = static_cast<const float*>(h->C_rm[1]);
+        aa.lamV = static_cast<float*>(gV0);
+        aa.lamS = static_cast<float*>(gS0);
+        aa.compV = acomp;
+        aa.compS = acomp + nv;
+        aa.Tper = static_cast<const float*>(T);
+        aa.traces = traces;
+        aa.ystar = ys;
+        aa.gTpart = gtp;
+        aa.status = h->status;
+        aa.dt = h->dt;
+        aa.n0 = 0;
+        aa.n_lo = n_start;
+        aa.n_hi = n_start + len;
+        aa.rec_base = n_start + 1;
+        aa.Kv = h->Kv;
+        aa.Ks = h->Ks;
+        aa.Kp = h->Kp;
+        aa.R = h->R;
+        aa.M = M;
+        e = launch_adjoint(aa, ap, st);
+    }
+    if (e == cudaSuccess && s == ROM_OK) e = launch_sum_partials(gtp, ap.cs, M, static_cast<float*>(gT), st);
+    double hacc[2] = {0.0, 0.0};
+    if (e == cudaSuccess && s == ROM_OK) e = cudaMemcpyAsync(hacc, acc, sizeof(hacc), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess && s == ROM_OK) e = cudaStreamSynchronize(st);
+    if (own_ws) cudaFree(own_ws);
+    if (s != ROM_OK) return s;
+    if (e != cudaSuccess) return fail(e, "rom_adjoint");
+    if (loss) *loss = hacc[0];
+    return ROM_OK;
+}
+
 rom_status rom_rel_l2(const void* x, int x_dtype, const void* ref, int ref_dtype, size_t n,
                       double* out, void* stream) {
     if (!x || !ref || !out || n == 0 || (x_dtype != 0 && x_dtype != 1) ||

@@ -102,6 +102,35 @@ cudaError_t tc_pad_rows(const float* src, int rows, int src_cols, int dst_cols, 
 bool plan_rank2_tc(int prec, int Kp, int M, int R, int Wforce, TcPlan* plan);
 cudaError_t launch_rank2_tc(const TcArgs& a, const TcPlan& plan, cudaStream_t st);
 
+// Reverse-time adjoint kernel (FP32, K <= 512).
+struct AdjArgs {
+    const float* opA_rm;  // Asv^T as Kp x Kp row-major (the column-major copy of Asv)
+    const float* opB_rm;  // Avs^T as Kp x Kp row-major
+    const float* g_p;     // Kp
+    const float* C_rm;    // R x Kp row-major
+    float* lamV;          // Kv x M adjoint of V (in: running value, out: after the range)
+    float* lamS;          // Ks x M
+    float* compV;         // Kahan carries of lamV / lamS
+    float* compS;
+    const float* Tper;    // M periods
+    const float* traces;  // forward records: record k = C V^{rec_base + k}, [k][m][j]
+    const float* ystar;   // targets: record n = ystar^{n+1}, [n][m][j]
+    float* gTpart;        // cs x M per-CTA partial dL/dT (in/out)
+    int* status;
+    double dt;
+    long long n0;
+    int n_lo, n_hi;       // reverse steps n_hi-1 .. n_lo
+    int rec_base;
+    int Kv, Ks, Kp, R, M, Wv, Wa;
+};
+struct AdjPlan {
+    int cs, KI, cb, Wv, Wa, nclusters;
+    size_t smem;
+};
+bool plan_adjoint(int Kp, int M, int R, AdjPlan* p);
+cudaError_t launch_adjoint(const AdjArgs& a, const AdjPlan& p, cudaStream_t st);
+cudaError_t launch_sum_partials(const float* part, int cs, int M, float* out, cudaStream_t st);
+
 // Rank-1 ensemble (one realization per CTA, operators streamed every step).
 struct Rank1EnsArgs {
     const void* Avs_cm;  // Kp x Kp column-major, zero padded (T)

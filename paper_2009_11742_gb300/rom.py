@@ -36,7 +36,8 @@ PRECISIONS = {"fp64": ROM_FP64, "fp32": ROM_FP32, "tf32x3": ROM_TF32X3,
 EXPORTED = ["rom_create", "rom_destroy", "rom_spectral_radius", "rom_sync_status",
             "rom_get_dims", "rom_set_kernel", "rom_get_plan", "rom_set_tc_columns", "rom_set_wait_limit",
             "rom_debug_inject_stall", "rom_run_rank2", "rom_run_rank2_ex", "rom_run_rank1",
-            "rom_run_rank1_ensemble", "rom_run_batched", "rom_rel_l2", "rom_spectral_radius_noalloc",
+            "rom_run_rank1_ensemble", "rom_run_batched", "rom_adjoint",
+            "rom_adjoint_workspace_size", "rom_rel_l2", "rom_spectral_radius_noalloc",
             "rom_status_string", "rom_last_error", "rom_version"]
 
 _lock = threading.Lock()
@@ -74,6 +75,9 @@ def _signatures(lib):
         "rom_run_rank1": (_i, [_vp, _vp, _vp, _d, _i, _l, _i, _vp, _i, _vp]),
         "rom_run_rank1_ensemble": (_i, [_vp, _vp, _vp, _vp, _i, _i, _l, _i, _vp, _i, _vp]),
         "rom_run_batched": (_i, [ctypes.c_void_p, _i, _i, _i, _i, _vp]),
+        "rom_adjoint": (_i, [_vp, _vp, _vp, _vp, _i, _i, _vp, _i, _vp, _vp, _vp,
+                             ctypes.POINTER(_d), _vp, ctypes.c_size_t, _i, _vp]),
+        "rom_adjoint_workspace_size": (ctypes.c_size_t, [_vp, _i, _i, _i, _i]),
         "rom_rel_l2": (_i, [_vp, _i, _vp, _i, ctypes.c_size_t, ctypes.POINTER(_d), _vp]),
         "rom_spectral_radius_noalloc": (_i, [_vp, _vp, _i, _i, ctypes.POINTER(_d), _vp]),
         "rom_status_string": (ctypes.c_char_p, [_i]),
@@ -226,6 +230,18 @@ def run_batched(items, nsteps, r=0, prec="fp32", stream=None):
         arr[i] = rom_job(h.h, _ptr(V), _ptr(S), _ptr(T), M, _ptr(tr))
     st = rom_run_batched(arr, len(items), int(nsteps), int(r), p, _stream_handle(stream))
     _chk(st, "rom_run_batched")
+
+
+def rom_adjoint(h, V0, S0, T, M, nsteps, ystar, ckpt_every, gV0, gS0, gT, workspace, ws_bytes,
+                prec, stream):
+    loss = _d(0.0)
+    st = load().rom_adjoint(h, V0, S0, T, M, nsteps, ystar, ckpt_every, gV0, gS0, gT,
+                            ctypes.byref(loss), workspace, ws_bytes, prec, stream)
+    return st, loss.value
+
+
+def rom_adjoint_workspace_size(h, M, nsteps, ckpt_every, prec):
+    return load().rom_adjoint_workspace_size(h, M, nsteps, ckpt_every, prec)
 
 
 def rom_rel_l2(x, x_dtype, ref, ref_dtype, n, stream=None):
@@ -424,6 +440,62 @@ class Rom:
         st = rom_run_rank1_ensemble(self.h, _ptr(V), _ptr(S), _ptr(T), M, int(nsteps), int(n0),
                                     int(r), _ptr(traces), p, _stream_handle(stream))
         _chk(st, "rom_run_rank1_ensemble")
+
+
+def adjoint(h, V0, S0, T, ystar, nsteps, ckpt_every=0, stream=None):
+    """Loss and gradients of sum_n ||C V^n - ystar^n||^2 (FP32, device tensors).
+    V0 (Kv, M) and S0 (Ks, M) column-major; ystar a contiguous (nsteps, M, R)
+    tensor (record n-1 = ystar^n).  Returns (loss, gV0, gS0, gT)."""
+    torch = _torch()
+    M = V0.shape[1]
+    _check_colmajor(V0, h.Kv, M, "V0", np.float32)
+    _check_colmajor(S0, h.Ks, M, "S0", np.float32)
+    _check_vec(T, M, "T", np.float32)
+    _check_vec(ystar, nsteps * M * h.R, "ystar", np.float32)
+    gV = Rom.new_state(h.Kv, M, "fp32", device=V0.device)
+    gS = Rom.new_state(h.Ks, M, "fp32", device=V0.device)
+    gT = torch.zeros(M, dtype=torch.float32, device=V0.device)
+    st, loss = rom_adjoint(h.h, _ptr(V0), _ptr(S0), _ptr(T), M, int(nsteps), _ptr(ystar),
+                           int(ckpt_every), _ptr(gV), _ptr(gS), _ptr(gT), None, 0, ROM_FP32,
+                           _stream_handle(stream))
+    _chk(st, "rom_adjoint")
+    return loss, gV, gS, gT
+
+
+def _adjoint_function():
+    torch = _torch()
+
+    class RomAdjointFn(torch.autograd.Function):
+        """loss = sum_n ||C V^n - ystar^n||^2 as a differentiable function of
+        (V0, S0, T); the backward pass returns the reverse-leapfrog gradients
+        computed together with the loss."""
+
+        @staticmethod
+        def forward(ctx, V0, S0, T, h, ystar, nsteps, ckpt_every):
+            loss, gV, gS, gT = adjoint(h, V0.detach(), S0.detach(), T.detach(), ystar, nsteps,
+                                       ckpt_every)
+            ctx.save_for_backward(gV, gS, gT)
+            return torch.tensor(loss, dtype=torch.float64, device=V0.device)
+
+        @staticmethod
+        def backward(ctx, gout):
+            gV, gS, gT = ctx.saved_tensors
+            s = gout.to(torch.float32)
+            return s * gV, s * gS, s * gT, None, None, None, None
+
+    return RomAdjointFn
+
+
+_RomAdjointFn = None
+
+
+def rom_loss(h, V0, S0, T, ystar, nsteps, ckpt_every=0):
+    """Differentiable misfit (torch.autograd): call .backward() for dL/dV0,
+    dL/dS0, dL/dT."""
+    global _RomAdjointFn
+    if _RomAdjointFn is None:
+        _RomAdjointFn = _adjoint_function()
+    return _RomAdjointFn.apply(V0, S0, T, h, ystar, nsteps, ckpt_every)
 
 
 def rel_l2(x, ref, stream=None) -> float:
