@@ -185,6 +185,19 @@ def cpu_baseline_sample(p, target_s=12.0):
                       f"steps ({dt:.1f} s, OpenMP over columns)"}
 
 
+def profiled_traffic(kname, nsteps):
+    """DRAM bytes (read + write) of one full-size launch, from the committed
+    ncu summary of that kernel on this workload, or None."""
+    import re
+    stem = kname.split("<")[0]
+    prof = os.path.join(ROOT, "profiles", f"{stem}_fp32_K512_M256_N{nsteps}.md")
+    try:
+        m = re.search(r"^dram_bytes_per_launch:\s*(\d+)", open(prof).read(), re.M)
+    except OSError:
+        return None
+    return int(m.group(1)) if m else None
+
+
 # ------------------------------------------------------------------- gb300 --
 def main():
     ap = argparse.ArgumentParser()
@@ -198,9 +211,9 @@ def main():
                     help="leapfrog steps per run (default: the workload's 10000; profiling only)")
     ap.add_argument("--only-rank2", action="store_true",
                     help="time the rank-2 runs only (no e2e, rank-1, oracle legs; profiling only)")
-    ap.add_argument("--workload", type=int, default=1, choices=[1, 2, 3],
+    ap.add_argument("--workload", type=int, default=1, choices=[1, 2, 3, 4],
                     help="1: K=512 FP32 (default, the headline); 2: K=1024 split precision; "
-                         "3: 64 batched ROMs")
+                         "3: 64 batched ROMs; 4: adjoint K=512 M=128 N=4000 c=64")
     ap.add_argument("--prec", default=None, help="override the workload's precision")
     ap.add_argument("--tc-cols", type=int, default=0, help="tensor-core columns per block")
     args = ap.parse_args()
@@ -227,6 +240,8 @@ def main():
 
     if args.workload == 3:
         return bench_batched(args, torch, dev, inputs, rom)
+    if args.workload == 4:
+        return bench_adjoint(args, torch, dev, inputs, rom)
 
     W = dict(WORKLOAD if args.workload == 1 else WORKLOAD2)
     if args.nsteps:
@@ -399,16 +414,10 @@ def main():
     nsm = torch.cuda.get_device_properties(dev).multi_processor_count
     fp32_peak = nsm * FP32_LANES_PER_SM * 2 * sm_clock_max * 1e6 / 1e12  # TFLOP/s
     achieved = flops / (t_dev / args.steps) / 1e12
-    traffic = None
-    prof = os.path.join(ROOT, "profiles", "rank2_simt_f32_K512_M256.traffic.json")
-    if os.path.exists(prof):
-        try:
-            traffic = json.load(open(prof)).get("dram_bytes_per_launch")
-        except (OSError, ValueError):
-            traffic = None
     plan = h.plan(M, "fp32")
     kname = ("rank2_split_kernel<8>" if plan["variant"] == 2
              else "rank2_simt_kernel<float,8,8,true>")
+    traffic = profiled_traffic(kname, N) if (K, M, R, r) == (512, 256, 64, 10) else None
     roof = {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
             "frac": achieved / fp32_peak, "traffic": traffic,
             "kernel": kname, "plan": plan,
@@ -444,6 +453,61 @@ def main():
     if dist is not None:
         dist.destroy_process_group()
     h.close()
+    return 0
+
+
+def bench_adjoint(args, torch, dev, inputs, rom):
+    """Workload 4: gradients of the trace misfit (K = 512, M = 128, 4000 steps,
+    R = 64, checkpoints every 64 steps) against the forward run with every
+    trace recorded; reports the time ratio adjoint / forward."""
+    p = inputs.config(4)
+    K, M, R = 512, 128, 64
+    N = args.nsteps or 4000
+    h = rom.Rom.from_problem(p)
+    V0 = rom.Rom.new_state(K, M, "fp32", device=dev)
+    S0 = rom.Rom.new_state(K, M, "fp32", device=dev)
+    T = torch.as_tensor(p.T, dtype=torch.float32, device=dev)
+    g = torch.Generator(device="cpu").manual_seed(0)
+    ys = (0.01 * torch.randn((N, M, R), generator=g)).to(dev)  # synthetic targets (timing only)
+    tr = torch.zeros((N, M, R), dtype=torch.float32, device=dev)
+    V = rom.Rom.new_state(K, M, "fp32", device=dev)
+    S = rom.Rom.new_state(K, M, "fp32", device=dev)
+    ws = torch.empty(rom.rom_adjoint_workspace_size(h.h, M, N, 64, rom.ROM_FP32), dtype=torch.uint8,
+                     device=dev)
+    gV = rom.Rom.new_state(K, M, "fp32", device=dev)
+    gS = rom.Rom.new_state(K, M, "fp32", device=dev)
+    gT = torch.zeros(M, dtype=torch.float32, device=dev)
+
+    def fwd():
+        V.zero_(); S.zero_()
+        h.run_rank2(V, S, T, N, r=1, traces=tr, prec="fp32")
+
+    def adj():
+        st, _ = rom.rom_adjoint(h.h, V0.data_ptr(), S0.data_ptr(), T.data_ptr(), M, N,
+                                ys.data_ptr(), 64, gV.data_ptr(), gS.data_ptr(), gT.data_ptr(),
+                                ws.data_ptr(), ws.numel(), rom.ROM_FP32, None)
+        assert st == 0
+
+    for _ in range(args.warmup):
+        fwd(); adj()
+    torch.cuda.synchronize()
+
+    def timed(fn):
+        ts = []
+        for _ in range(args.steps):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            fn()
+            torch.cuda.synchronize()
+            ts.append(time.perf_counter() - t0)
+        return sum(ts) / len(ts)
+    tf = timed(fwd)
+    ta = timed(adj)
+    print(json.dumps({"only_rank2": True, "workload": "adjoint-K512-M128-N4000-R64-r1-c64",
+                      "nsteps": N, "forward_ms": 1e3 * tf, "adjoint_ms": 1e3 * ta,
+                      "adjoint_over_forward": ta / tf,
+                      "adjoint_sample_steps_per_s": M * N / ta, "unit": "sample-steps/s"}),
+          flush=True)
     return 0
 
 
