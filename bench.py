@@ -42,8 +42,8 @@ WORKLOAD = dict(name="rank2-fp32-K512-M256-N10000-R64-r10", K=512, M=256, nsteps
 WORKLOAD2 = dict(name="rank2-split-K1024-M1024-N20000-R64-r10", K=1024, M=1024, nsteps=20000,
                  R=64, r=10, prec="tf32x3", seed=0)
 # Nominal dense tensor-core rates relative to BF16 (profiling recipe table).
-TC_RATIO = {"tf32x3": 1.1 / 2.25, "bf16x3": 1.0, "bf16": 1.0}
-TC_PRODUCTS = {"tf32x3": 3, "bf16x3": 5, "bf16": 1}
+TC_RATIO = {"tf32x3": 1.1 / 2.25, "bf16x3": 1.0, "bf16": 1.0, "bf16s": 1.0}
+TC_PRODUCTS = {"tf32x3": 3, "bf16x3": 5, "bf16": 1, "bf16s": 6}
 FP32_LANES_PER_SM = 128  # FP32 FMA lanes per SM (Blackwell)
 
 

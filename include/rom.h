@@ -68,7 +68,10 @@ typedef enum {
     ROM_FP32 = 1,   /* FP32 SIMT products, Kahan-compensated state update */
     ROM_TF32X3 = 2, /* tensor cores, tf32 hi/lo split, 3 products, Kahan update */
     ROM_BF16X3 = 3, /* tensor cores, bf16 3-term operator / 2-term state split */
-    ROM_BF16 = 4    /* tensor cores, plain bf16 products (reported, not accepted) */
+    ROM_BF16 = 4,   /* tensor cores, plain bf16 products (reported, not accepted) */
+    ROM_BF16S = 5   /* tensor cores, exact sliced-integer bf16: operator rows and state
+                       columns as three 8-bit digits with power-of-two scales, six digit
+                       products accumulated without rounding, Kahan update */
 } rom_prec;
 
 typedef enum { ROM_IN_F64 = 0, ROM_IN_F32 = 1 } rom_dtype;
@@ -132,10 +135,12 @@ rom_status rom_get_plan(rom_t h, int prec, int M, int* variant, int* cluster_siz
                         int* cols_per_block, int* nclusters);
 
 /*
- * rom_set_tc_columns -- columns per cluster block of the tensor-core path
- * (ROM_TF32X3 / ROM_BF16X3 / ROM_BF16): 64, 128, 192 or 256, or 0 to let the
- * planner choose (default).  Wider blocks re-read each operator slab fewer
- * times per step; narrower blocks spread the run over more SMs.
+ * rom_set_tc_columns -- columns per cluster block of the tensor-core path:
+ * 64 or 128 for ROM_TF32X3 / ROM_BF16X3 / ROM_BF16, 32, 64, 80 or 128 for
+ * ROM_BF16S, or 0 to let the planner choose (default).  Wider blocks re-read
+ * each operator slab fewer times per step; narrower blocks spread the run
+ * over more SMs.  A width the precision does not provide makes the next run
+ * return ROM_E_UNSUPPORTED.
  */
 rom_status rom_set_tc_columns(rom_t h, int cols);
 

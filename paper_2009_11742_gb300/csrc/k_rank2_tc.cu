@@ -5,6 +5,7 @@
 
 #include "rank2_launch.cuh"
 #include "rank2_tc.cuh"
+#include "rank2_tcs.cuh"
 
 namespace romk {
 
@@ -42,6 +43,39 @@ __global__ void tc_split_operator_kernel(const float* __restrict__ A, int Ksrc, 
     }
 }
 
+// ---- ROM_BF16S operator: per-row exponent (one warp per row), then the three
+// integer digits of A[r][k] * 2^(7 - e_r) into the same tile layout.
+__global__ void tcs_row_scale_kernel(const float* __restrict__ A, int Ksrc, int Kp, float* __restrict__ scale) {
+    const int row = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+    const int lane = threadIdx.x & 31;
+    if (row >= Kp) return;
+    float mx = 0.f;
+    if (row < Ksrc)
+        for (int k = lane; k < Ksrc; k += 32) mx = fmaxf(mx, fabsf(A[(size_t)row * Ksrc + k]));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if (lane == 0) scale[row] = ldexpf(1.f, bound_exponent(mx) - 7);
+}
+
+__global__ void tcs_split_operator_kernel(const float* __restrict__ A, int Ksrc, int Kp,
+                                          const float* __restrict__ scale, unsigned char* __restrict__ out) {
+    const int NKC = Kp / kTcsKC;
+    const size_t total = (size_t)Kp * Kp;
+    for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total;
+         idx += (size_t)gridDim.x * blockDim.x) {
+        const int row = (int)(idx / Kp), col = (int)(idx % Kp);
+        const float x = (row < Ksrc && col < Ksrc) ? A[(size_t)row * Ksrc + col] : 0.f;
+        const int rt = row / kTcRows, r = row % kTcRows, kc = col / kTcsKC, k = col % kTcsKC;
+        const uint32_t within = sw128_offset((uint32_t)r, (uint32_t)((k * 2) >> 4)) + ((k * 2) & 15);
+        unsigned char* tile0 = out + ((size_t)(rt * NKC + kc) * kTcsTerms) * kATileBytes + within;
+        float d0, d1, d2;
+        slice_digits(x * (1.f / scale[row]), d0, d1, d2);
+        *reinterpret_cast<__nv_bfloat16*>(tile0) = __float2bfloat16_rn(d0);
+        *reinterpret_cast<__nv_bfloat16*>(tile0 + kATileBytes) = __float2bfloat16_rn(d1);
+        *reinterpret_cast<__nv_bfloat16*>(tile0 + 2 * kATileBytes) = __float2bfloat16_rn(d2);
+    }
+}
+
 __global__ void pad_rows_kernel(const float* __restrict__ src, int rows, int src_cols, int dst_cols,
                                 float* __restrict__ dst) {
     const size_t total = (size_t)rows * dst_cols;
@@ -57,8 +91,13 @@ static size_t tc_operator_bytes(int Kp) {
     return (size_t)Kp * Kp * TcScheme<P>::NA * (TcScheme<P>::kTF32 ? 4 : 2);
 }
 
+size_t tc_scale_offset(int prec, int Kp) {
+    return prec == ROM_BF16S ? (size_t)Kp * Kp * kTcsTerms * 2 : 0;
+}
+
 size_t tc_operator_bytes_for(int prec, int Kp) {
     switch (prec) {
+        case ROM_BF16S: return tc_scale_offset(prec, Kp) + (size_t)Kp * sizeof(float);
         case ROM_TF32X3: return tc_operator_bytes<ROM_TF32X3>(Kp);
         case ROM_BF16X3: return tc_operator_bytes<ROM_BF16X3>(Kp);
         case ROM_BF16: return tc_operator_bytes<ROM_BF16>(Kp);
@@ -72,6 +111,12 @@ cudaError_t tc_prepare_operator(int prec, const float* A_rm, int Ksrc, int Kp, v
     unsigned blocks = (unsigned)((total + 255) / 256);
     if (blocks > 4096) blocks = 4096;
     unsigned char* o = static_cast<unsigned char*>(out);
+    if (prec == ROM_BF16S) {
+        float* scale = reinterpret_cast<float*>(o + tc_scale_offset(prec, Kp));
+        tcs_row_scale_kernel<<<(Kp + 7) / 8, 256, 0, st>>>(A_rm, Ksrc, Kp, scale);
+        tcs_split_operator_kernel<<<blocks, 256, 0, st>>>(A_rm, Ksrc, Kp, scale, o);
+        return cudaGetLastError();
+    }
     switch (prec) {
         case ROM_TF32X3: tc_split_operator_kernel<ROM_TF32X3><<<blocks, 256, 0, st>>>(A_rm, Ksrc, Kp, o); break;
         case ROM_BF16X3: tc_split_operator_kernel<ROM_BF16X3><<<blocks, 256, 0, st>>>(A_rm, Ksrc, Kp, o); break;
@@ -116,6 +161,7 @@ static size_t tc_smem_for(int prec, int W, int stages, int rpc, int Kp) {
 
 int tc_exchange_terms(int prec) {
     switch (prec) {
+        case ROM_BF16S: return kTcsTerms;
         case ROM_TF32X3: return TcScheme<ROM_TF32X3>::NX;
         case ROM_BF16X3: return TcScheme<ROM_BF16X3>::NX;
         case ROM_BF16: return TcScheme<ROM_BF16>::NX;
@@ -124,7 +170,75 @@ int tc_exchange_terms(int prec) {
 }
 int tc_element_bytes(int prec) { return prec == ROM_TF32X3 ? 4 : 2; }
 
+static void* tcs_kernel(int W) {
+    switch (W) {
+        case 32: return (void*)&rank2_tcs_kernel<32>;
+        case 64: return (void*)&rank2_tcs_kernel<64>;
+        case 80: return (void*)&rank2_tcs_kernel<80>;
+        case 128: return (void*)&rank2_tcs_kernel<128>;
+        default: return nullptr;
+    }
+}
+
+// ROM_BF16S: the block width with the least estimated time, taken as the
+// number of waves of clusters times (W + a fixed per-chunk cost of about 48
+// columns' worth of MMA time).
+static bool plan_rank2_tcs(int Kp, int M, int R, int Wforce, TcPlan* p) {
+    if (Kp <= 0 || Kp % kTcRows != 0 || Kp > 1024 || M <= 0) return false;
+    const int cs = Kp / kTcRows;
+    const int smax = device_smem_optin();
+    const int cands[4] = {32, 64, 80, 128};
+    long best = -1;
+    for (int ci = 0; ci < 4; ++ci) {
+        const int W = cands[ci];
+        if (Wforce > 0 && W != Wforce) continue;
+        void* fn = tcs_kernel(W);
+        int stages = 0;
+        for (int s = 4; s >= 2; --s)
+            if (tcs_smem_bytes(W, s) <= (size_t)smax) { stages = s; break; }
+        if (!fn || stages == 0) continue;
+        const size_t smem = tcs_smem_bytes(W, stages);
+        if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
+            cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) {
+            cudaGetLastError();
+            continue;
+        }
+        cudaLaunchConfig_t cfg = {};
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = cs;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.gridDim = dim3(cs, 1, 1);
+        cfg.blockDim = dim3(kTcThreads, 1, 1);
+        cfg.dynamicSmemBytes = smem;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        int nact = 0;
+        if (cudaOccupancyMaxActiveClusters(&nact, fn, &cfg) != cudaSuccess || nact <= 0) {
+            cudaGetLastError();
+            continue;
+        }
+        const int ncl = (M + W - 1) / W;
+        const long waves = (ncl + nact - 1) / nact;
+        const long cost = waves * (W + 48);
+        if (best < 0 || cost < best) {
+            best = cost;
+            p->prec = ROM_BF16S;
+            p->cs = cs;
+            p->rpc = (R + cs - 1) / cs;
+            p->W = W;
+            p->stages = stages;
+            p->smem = smem;
+            p->nclusters = ncl;
+            p->max_active_clusters = nact;
+        }
+    }
+    return best >= 0;
+}
+
 bool plan_rank2_tc(int prec, int Kp, int M, int R, int Wforce, TcPlan* p) {
+    if (prec == ROM_BF16S) return plan_rank2_tcs(Kp, M, R, Wforce, p);
     if (Kp <= 0 || Kp % kTcRows != 0 || Kp > 1024 || M <= 0) return false;
     p->cs = Kp / kTcRows;
     p->rpc = (R + p->cs - 1) / p->cs;
@@ -174,7 +288,7 @@ bool plan_rank2_tc(int prec, int Kp, int M, int R, int Wforce, TcPlan* p) {
 }
 
 cudaError_t launch_rank2_tc(const TcArgs& a_in, const TcPlan& p, cudaStream_t st) {
-    void* fn = tc_kernel_for(p.prec, p.W);
+    void* fn = p.prec == ROM_BF16S ? tcs_kernel(p.W) : tc_kernel_for(p.prec, p.W);
     if (!fn) return cudaErrorInvalidValue;
     TcArgs a = a_in;
     a.W = p.W;

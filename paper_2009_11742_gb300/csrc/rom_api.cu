@@ -78,7 +78,7 @@ struct rom_s {
     DevBuf stage;              // staging of host buffers
     // tensor-core path (prepared on first use of a split precision)
     int Kp_tc = 0;
-    void* tc_ops[5][2] = {};   // [prec][0: Avs, 1: Asv] pre-split, pre-swizzled tiles
+    void* tc_ops[6][2] = {};   // [prec][0: Avs, 1: Asv] pre-split, pre-swizzled tiles
     float* g_tc = nullptr;     // Kp_tc
     float* C_tc = nullptr;     // R x Kp_tc
     DevBuf tc_ws;              // exchange tiles + Kahan carries of one call
@@ -104,7 +104,7 @@ void free_handle(rom_s* h) {
         cudaFree(h->C_rm[t]);
         cudaFree(h->C_cm[t]);
     }
-    for (int p = 0; p < 5; ++p) {
+    for (int p = 0; p < 6; ++p) {
         cudaFree(h->tc_ops[p][0]);
         cudaFree(h->tc_ops[p][1]);
     }
@@ -160,7 +160,10 @@ rom_status power_iteration(rom_s* h, double* rho_out) {
     return st;
 }
 
-bool valid_prec(int prec) { return prec >= ROM_FP64 && prec <= ROM_BF16; }
+bool valid_prec(int prec) { return prec >= ROM_FP64 && prec <= ROM_BF16S; }
+bool tc_prec(int prec) {
+    return prec == ROM_TF32X3 || prec == ROM_BF16X3 || prec == ROM_BF16 || prec == ROM_BF16S;
+}
 
 // Forget cached batched graphs that reference handle h (defined with them below).
 void drop_batch_graphs(rom_s* h);
@@ -404,6 +407,11 @@ rom_status run_rank2_tc(rom_s* h, const RunBufs& b, int M, int nsteps, long n0, 
     TcArgs a = {};
     a.Aop[0] = h->tc_ops[prec][0];
     a.Aop[1] = h->tc_ops[prec][1];
+    if (prec == ROM_BF16S) {
+        const size_t so = tc_scale_offset(prec, h->Kp_tc);
+        a.Ascale[0] = reinterpret_cast<const float*>(static_cast<const char*>(a.Aop[0]) + so);
+        a.Ascale[1] = reinterpret_cast<const float*>(static_cast<const char*>(a.Aop[1]) + so);
+    }
     a.X[0] = ws;
     a.X[1] = ws + al(xbytes);
     float* cw = reinterpret_cast<float*>(ws + 2 * al(xbytes));
@@ -439,7 +447,7 @@ rom_status launch_simt_with_plan(rom_s* h, const RunBufs& b, int M, int nsteps, 
 
 rom_status run_rank2_device(rom_s* h, const RunBufs& b, int M, int nsteps, long n0, int r,
                             int prec, bool rank1, cudaStream_t st) {
-    if (prec == ROM_TF32X3 || prec == ROM_BF16X3 || prec == ROM_BF16) {
+    if (tc_prec(prec)) {
         if (rank1) return ROM_E_UNSUPPORTED;
         return run_rank2_tc(h, b, M, nsteps, n0, r, prec, st);
     }
@@ -591,7 +599,7 @@ rom_status rom_debug_inject_stall(rom_t h, int on) {
 }
 
 rom_status rom_set_tc_columns(rom_t h, int cols) {
-    if (!h || cols < 0 || cols > 256 || cols % 64 != 0) return ROM_E_INVAL;
+    if (!h || cols < 0 || cols > 256 || cols % 16 != 0) return ROM_E_INVAL;
     std::lock_guard<std::mutex> lk(h->mu);
     h->tc_cols = cols;
     return ROM_OK;
@@ -744,7 +752,7 @@ rom_status rom_run_batched(const rom_job* jobs, int njobs, int nsteps, int r, in
     }
     if (nsteps == 0) return ROM_OK;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    const bool tc = prec == ROM_TF32X3 || prec == ROM_BF16X3 || prec == ROM_BF16;
+    const bool tc = tc_prec(prec);
     int dev = 0, nsm = 0;
     ROM_CUDA(cudaGetDevice(&dev));
     ROM_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));

@@ -68,9 +68,10 @@ bool plan_rank2_split_f32(int Kp, int M, int R, Rank2Plan* plan, int cluster_bud
 bool plan_rank2_dataflow_f32(int Kp, int M, int R, Rank2Plan* plan);
 cudaError_t launch_rank2_split_f32(const Rank2Args& a, const Rank2Plan& plan, cudaStream_t st);
 
-// Tensor-core (tcgen05) rank-2 path for ROM_TF32X3 / ROM_BF16X3 / ROM_BF16.
+// Tensor-core (tcgen05) rank-2 path for ROM_TF32X3 / ROM_BF16X3 / ROM_BF16 / ROM_BF16S.
 struct TcArgs {
     const void* Aop[2];   // split operator tiles: [0] Avs (V half), [1] Asv (S half)
+    const float* Ascale[2];  // ROM_BF16S: per-row scales 2^(e_r - 7) of the operator digits
     void* X[2];           // exchange tiles: [0] S (operand of the V half), [1] V
     const float* g_p;     // Kp (tensor-core padding)
     const float* C_p;     // R x Kp row-major (or null)
@@ -92,13 +93,15 @@ struct TcPlan {
     size_t smem;
 };
 size_t tc_operator_bytes_for(int prec, int Kp);
+// Offset of the per-row scales inside a prepared ROM_BF16S operator (after the tiles).
+size_t tc_scale_offset(int prec, int Kp);
 int tc_exchange_terms(int prec);
 int tc_element_bytes(int prec);
 cudaError_t tc_prepare_operator(int prec, const float* A_rm, int Ksrc, int Kp, void* out,
                                 cudaStream_t st);
 cudaError_t tc_pad_rows(const float* src, int rows, int src_cols, int dst_cols, float* dst,
                         cudaStream_t st);
-// Wforce > 0 pins the columns per block (a multiple of 64, at most 256).
+// Wforce > 0 pins the columns per block (64 or 128; for ROM_BF16S 32, 64, 80 or 128).
 bool plan_rank2_tc(int prec, int Kp, int M, int R, int Wforce, TcPlan* plan);
 cudaError_t launch_rank2_tc(const TcArgs& a, const TcPlan& plan, cudaStream_t st);
 
