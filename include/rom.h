@@ -136,7 +136,7 @@ rom_status rom_get_plan(rom_t h, int prec, int M, int* variant, int* cluster_siz
 
 /*
  * rom_set_tc_columns -- columns per cluster block of the tensor-core path:
- * 64 or 128 for ROM_TF32X3 / ROM_BF16X3 / ROM_BF16, 32, 64, 80 or 128 for
+ * 64 or 128 for ROM_TF32X3 / ROM_BF16X3 / ROM_BF16, 32, 48, 64 or 80 for
  * ROM_BF16S, or 0 to let the planner choose (default).  Wider blocks re-read
  * each operator slab fewer times per step; narrower blocks spread the run
  * over more SMs.  A width the precision does not provide makes the next run

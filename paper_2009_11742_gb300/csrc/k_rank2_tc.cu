@@ -173,9 +173,9 @@ int tc_element_bytes(int prec) { return prec == ROM_TF32X3 ? 4 : 2; }
 static void* tcs_kernel(int W) {
     switch (W) {
         case 32: return (void*)&rank2_tcs_kernel<32>;
+        case 48: return (void*)&rank2_tcs_kernel<48>;
         case 64: return (void*)&rank2_tcs_kernel<64>;
         case 80: return (void*)&rank2_tcs_kernel<80>;
-        case 128: return (void*)&rank2_tcs_kernel<128>;
         default: return nullptr;
     }
 }
@@ -187,7 +187,7 @@ static bool plan_rank2_tcs(int Kp, int M, int R, int Wforce, TcPlan* p) {
     if (Kp <= 0 || Kp % kTcRows != 0 || Kp > 1024 || M <= 0) return false;
     const int cs = Kp / kTcRows;
     const int smax = device_smem_optin();
-    const int cands[4] = {32, 64, 80, 128};
+    const int cands[4] = {32, 48, 64, 80};
     long best = -1;
     for (int ci = 0; ci < 4; ++ci) {
         const int W = cands[ci];

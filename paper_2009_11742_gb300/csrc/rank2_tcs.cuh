@@ -66,10 +66,12 @@ __device__ __forceinline__ int bound_exponent(float mx) {
     return e;
 }
 
-// Column stride of the accumulators in tensor memory and the allocation.
+// Column stride of the accumulators in tensor memory; after the four
+// accumulators the new state of each readout warp (W columns in all) is
+// parked between the update and the slicing.  Allocation: next power of two.
 __host__ __device__ constexpr int tcs_acc_stride(int W) { return ((W + 31) / 32) * 32; }
 __host__ __device__ constexpr uint32_t tcs_tmem_cols(int W) {
-    return 4 * tcs_acc_stride(W) <= 128 ? 128u : (4 * tcs_acc_stride(W) <= 256 ? 256u : 512u);
+    return 4 * tcs_acc_stride(W) + W <= 128 ? 128u : (4 * tcs_acc_stride(W) + W <= 256 ? 256u : 512u);
 }
 
 __host__ __device__ inline size_t tcs_stage_bytes(int W) {
@@ -127,6 +129,38 @@ __device__ __forceinline__ void tmem_wait_ld4(uint32_t (&a)[8], uint32_t (&b)[8]
                  : "memory");
 }
 
+__device__ __forceinline__ void tmem_st8(uint32_t taddr, const float (&v)[8]) {
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};"
+                 ::"r"(taddr), "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])),
+                   "r"(__float_as_uint(v[2])), "r"(__float_as_uint(v[3])), "r"(__float_as_uint(v[4])),
+                   "r"(__float_as_uint(v[5])), "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7]))
+                 : "memory");
+}
+__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float (&v)[8]) {
+    uint32_t r[8];
+    tmem_ld8_nowait(taddr, r);
+    asm volatile("tcgen05.wait::ld.sync.aligned;"
+                 : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7])
+                 :
+                 : "memory");
+#pragma unroll
+    for (int q = 0; q < 8; ++q) v[q] = __uint_as_float(r[q]);
+}
+
+// Old state and carries of 8 columns of one row (zero outside the valid range).
+__device__ __forceinline__ void load_group8(const float* __restrict__ Y, const float* __restrict__ Cy,
+                                            int Kown, int col_first, int ncol_left, bool rowok,
+                                            float (&y)[8], float (&c)[8]) {
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        const bool ok = rowok && q < ncol_left;
+        const size_t gi = (size_t)(col_first + q) * Kown;
+        y[q] = ok ? Y[gi] : 0.f;
+        c[q] = ok ? Cy[gi] : 0.f;
+    }
+}
+
 __device__ __forceinline__ void reader_bar_sync() {
     asm volatile("bar.sync 1, %0;" ::"r"(kTcReadWarps * 32) : "memory");
 }
@@ -136,7 +170,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) rank2_tcs_kernel(const TcArgs a
     constexpr int WH = W / 2;                       // columns per readout warp
     constexpr int AST = tcs_acc_stride(W);          // accumulator column stride
     constexpr uint32_t NCOLS = tcs_tmem_cols(W);
-    static_assert(W % 16 == 0 && W >= 32 && W <= 128 && WH % 8 == 0, "unsupported block width");
+    static_assert(W % 16 == 0 && W >= 32 && W <= 80 && WH % 8 == 0, "unsupported block width");
     cg::cluster_group cluster = cg::this_cluster();
     const int CS = (int)cluster.num_blocks();
     const int crank = (int)cluster.block_rank();
@@ -292,7 +326,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) rank2_tcs_kernel(const TcArgs a
                         const uint32_t d2 = tbase + (uint32_t)(3 * AST);
                         const bool first0 = kc == 0;
                         const bool first1 = kc == (t1b ? KC_T1B : 0);
-#pragma unroll
+#pragma unroll 1
                         for (int ks = 0; ks < 4; ++ks) {  // four 16-deep K steps per 128-byte chunk
                             const uint32_t ko = 32u * ks;
                             const uint64_t a0 = sw128_desc(sA + ko);
@@ -317,19 +351,30 @@ __global__ void __launch_bounds__(kTcThreads, 1) rank2_tcs_kernel(const TcArgs a
                 __syncwarp();
             } else if (reader) {
                 // ---- readers: one readout of the four accumulators, the fused
-                //      forcing and Kahan update, column maxima of the new state
+                //      forcing and Kahan update, the column maxima of the new
+                //      state.  The old rows and carries are loaded two 8-column
+                //      groups ahead (the first two while the MMAs run); the new
+                //      rows wait in spare tensor-memory columns for the slicing.
+                const int row = row0 + rl;
+                const int Kown = half == 0 ? a.Kv : a.Ks;
+                float* Y = (half == 0 ? a.V : a.S) + row;
+                float* Cy = (half == 0 ? a.compV : a.compS) + row;
+                const bool rowok = row < Kown;
+                const int jbase = chalf * WH;
+                constexpr int NG = WH / 8;
+                float ya[8], ca[8], yb[8], cb[8];
+                load_group8(Y, Cy, Kown, col0 + jbase, ncol - jbase, rowok, ya, ca);
+                if (NG > 1) load_group8(Y, Cy, Kown, col0 + jbase + 8, ncol - jbase - 8, rowok, yb, cb);
                 int gotl = 0;
                 if (lane == 0) gotl = (*abort_flag == 0) && mbarrier_wait(dready, (uint32_t)(hs & 1), limit, abort_flag);
                 have = __shfl_sync(0xffffffffu, gotl, 0) != 0;
                 tc_fence_after();
-                const int row = row0 + rl;
-                const int Kown = half == 0 ? a.Kv : a.Ks;
-                float* Y = half == 0 ? a.V : a.S;
-                float* Cy = half == 0 ? a.compV : a.compS;
                 const float ars = arow[half * kTcRows + rl];
-                const uint32_t tl = tbase + ((uint32_t)(32 * quad) << 16) + (uint32_t)(chalf * WH);
-#pragma unroll
-                for (int i0 = 0; i0 < WH; i0 += 8) {
+                const uint32_t tl = tbase + ((uint32_t)(32 * quad) << 16) + (uint32_t)jbase;
+                // one 8-column group: readout, update, new state parked in TMEM,
+                // loads of the group two ahead into the same buffers
+                auto group = [&](const int g, float (&yg)[8], float (&cg_)[8]) {
+                    const int i0 = 8 * g;
                     uint32_t r0[8], r1a[8], r1b[8], r2[8];
                     if (have) {
                         tmem_ld8_nowait(tl + (uint32_t)i0, r0);
@@ -343,27 +388,38 @@ __global__ void __launch_bounds__(kTcThreads, 1) rank2_tcs_kernel(const TcArgs a
                         if (!have || !two_t1) r1b[q] = 0u;
                     }
                     if (have) tmem_wait_ld4(r0, r1a, r1b, r2);
+                    float ynew[8];
 #pragma unroll
                     for (int q = 0; q < 8; ++q) {
-                        const int j = chalf * WH + i0 + q;
-                        float y = 0.f;
-                        if (have && j < ncol && row < Kown) {
+                        const int j = jbase + i0 + q;
+                        float y = yg[q];
+                        if (have && rowok && j < ncol) {
                             const float t1 = __fadd_rn(__uint_as_float(r1a[q]), __uint_as_float(r1b[q]));
                             const float u = __fmaf_rn(__uint_as_float(r2[q]), 1.f / 65536.f, t1 * (1.f / 256.f));
                             const float R = __fadd_rn(__uint_as_float(r0[q]), u);
                             float inc = R * (ars * xsc[j]);
                             if (half == 0) inc = __fmaf_rn(grow[rl], fcol[j], inc);
                             inc = inc * dt;
-                            const size_t gi = (size_t)(col0 + j) * Kown + row;
-                            float cc = Cy[gi];
-                            y = kahan_add(Y[gi], inc, cc);
+                            float c = cg_[q];
+                            y = kahan_add(y, inc, c);
+                            const size_t gi = (size_t)(col0 + j) * Kown;
                             Y[gi] = y;
-                            Cy[gi] = cc;
+                            Cy[gi] = c;
                         }
+                        ynew[q] = y;
                         const unsigned m = __reduce_max_sync(0xffffffffu, __float_as_uint(fabsf(y)));
                         if (lane == 0) colmax[quad * W + j] = m;
                     }
+                    tmem_st8(tl + (uint32_t)(4 * AST + i0), ynew);
+                    if (g + 2 < NG)
+                        load_group8(Y, Cy, Kown, col0 + jbase + i0 + 16, ncol - jbase - i0 - 16, rowok, yg, cg_);
+                };
+#pragma unroll 1
+                for (int g = 0; g < NG; g += 2) {
+                    group(g, ya, ca);
+                    if (g + 1 < NG) group(g + 1, yb, cb);
                 }
+                tmem_wait_st();
                 tc_fence_before();
                 reader_bar_sync();
                 // block maxima of this CTA, stored into every CTA of the cluster
@@ -386,17 +442,21 @@ __global__ void __launch_bounds__(kTcThreads, 1) rank2_tcs_kernel(const TcArgs a
             }
             __syncthreads();
             if (reader) {
-                // the new rows, read back from the state this thread has just written
                 unsigned char* Xdst = half ? Xblk0 : Xblk1;  // V feeds the S half and vice versa
                 const int row = row0 + rl;
-                const int Kown = half == 0 ? a.Kv : a.Ks;
-                const float* Y = half == 0 ? a.V : a.S;
-#pragma unroll 4
-                for (int i = 0; i < WH; ++i) {
-                    const int j = chalf * WH + i;
-                    const float y = (have && j < ncol && row < Kown) ? Y[(size_t)(col0 + j) * Kown + row] : 0.f;
-                    tcs_store_digits(Xdst, xterm, tcs_xoffset(row, j, W), y * xinv[j]);
+                const uint32_t ts = tbase + ((uint32_t)(32 * quad) << 16) + (uint32_t)(4 * AST + chalf * WH);
+                tc_fence_after();
+#pragma unroll 1
+                for (int i0 = 0; i0 < WH; i0 += 8) {
+                    float yn[8];
+                    tmem_ld8(ts + (uint32_t)i0, yn);
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) {
+                        const int j = chalf * WH + i0 + q;
+                        tcs_store_digits(Xdst, xterm, tcs_xoffset(row, j, W), yn[q] * xinv[j]);
+                    }
                 }
+                tc_fence_before();
             }
             fence_proxy_async_global();
             // forcing of the next step (read by the next velocity epilogue)
@@ -435,6 +495,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) rank2_tcs_kernel(const TcArgs a
                     const float* vcol = a.V + (size_t)(col0 + c) * a.Kv;
                     const float* crow = a.C_p + (size_t)jr * Kp;
                     float tacc = 0.f;
+#pragma unroll 4
                     for (int k = lane; k < a.Kv; k += 32) tacc = __fmaf_rn(crow[k], __ldcg(vcol + k), tacc);
 #pragma unroll
                     for (int o = 16; o > 0; o >>= 1) tacc += __shfl_xor_sync(0xffffffffu, tacc, o);

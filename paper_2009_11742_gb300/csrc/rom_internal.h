@@ -101,7 +101,7 @@ cudaError_t tc_prepare_operator(int prec, const float* A_rm, int Ksrc, int Kp, v
                                 cudaStream_t st);
 cudaError_t tc_pad_rows(const float* src, int rows, int src_cols, int dst_cols, float* dst,
                         cudaStream_t st);
-// Wforce > 0 pins the columns per block (64 or 128; for ROM_BF16S 32, 64, 80 or 128).
+// Wforce > 0 pins the columns per block (64 or 128; for ROM_BF16S 32, 48, 64 or 80).
 bool plan_rank2_tc(int prec, int Kp, int M, int R, int Wforce, TcPlan* plan);
 cudaError_t launch_rank2_tc(const TcArgs& a, const TcPlan& plan, cudaStream_t st);
 

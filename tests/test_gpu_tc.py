@@ -106,7 +106,7 @@ def test_tc_chunked_is_bitwise_equal(rom, prec):
     assert torch.equal(V, V2) and torch.equal(S, S2)
 
 
-@pytest.mark.parametrize("cols", [32, 64, 80, 128])
+@pytest.mark.parametrize("cols", [32, 48, 64, 80])
 def test_bf16s_k1024_every_width(rom, cols):
     """K = 1024 (8-CTA clusters, the split T1 accumulators) for every block
     width of the sliced scheme, with a ragged last block and random state."""
