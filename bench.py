@@ -185,6 +185,24 @@ def cpu_baseline_sample(p, target_s=12.0):
                       f"steps ({dt:.1f} s, OpenMP over columns)"}
 
 
+def rank_periods(T_all, rank, world):
+    """Periods of the realizations one rank integrates: an ensemble of
+    world * M realizations split into contiguous shards of M (replicas by
+    realization, no data-path exchange)."""
+    M = len(T_all) // world
+    return T_all[rank * M:(rank + 1) * M]
+
+
+def max_over_ranks(t, dist, device):
+    """Job time = the slowest rank's time (every rank's value when dist is None)."""
+    if dist is None:
+        return t
+    import torch
+    tt = torch.tensor([t], dtype=torch.float64, device=device)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    return float(tt.item())
+
+
 def profiled_traffic(kname, nsteps):
     """DRAM bytes (read + write) of one full-size launch, from the committed
     ncu summary of that kernel on this workload, or None."""
@@ -250,7 +268,8 @@ def main():
         W["prec"] = args.prec
     prec = W["prec"]
     K, M, N, R, r = W["K"], W["M"], W["nsteps"], W["R"], W["r"]
-    p = inputs.make_problem(K, K, M, R, seed=W["seed"])
+    p = inputs.make_problem(K, K, M * world, R, seed=W["seed"])
+    p.T = rank_periods(p.T, rank, world)
     h = rom.Rom.from_problem(p)
     if args.tc_cols:
         rom.rom_set_tc_columns(h.h, args.tc_cols)
@@ -300,11 +319,7 @@ def main():
     if st != 0:
         raise RuntimeError(f"device status {rom.status_string(st)}")
     per = [a.elapsed_time(b) * 1e-3 for a, b in evs]
-    t_dev = sum(per)
-    if dist is not None:
-        tt = torch.tensor([t_dev], dtype=torch.float64, device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_dev = float(tt.item())
+    t_dev = max_over_ranks(sum(per), dist, dev)
     value = world * M * N * args.steps / t_dev
     ms_per_step = 1e3 * t_dev / args.steps
     flops = useful_flops(K, M, N, R, r)
@@ -352,11 +367,7 @@ def main():
         t0 = time.perf_counter()
         h.run_rank2(Vh, Sh, Th, N, r=r, traces=trh, prec="fp32")
         e2e_times.append(time.perf_counter() - t0)
-    e2e_t = sum(e2e_times) / len(e2e_times)
-    if dist is not None:
-        tt = torch.tensor([e2e_t], dtype=torch.float64, device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        e2e_t = float(tt.item())
+    e2e_t = max_over_ranks(sum(e2e_times) / len(e2e_times), dist, dev)
 
     if rank != 0:
         if dist is not None:
