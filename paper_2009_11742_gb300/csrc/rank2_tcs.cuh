@@ -45,6 +45,15 @@ namespace romk {
 constexpr int kTcsTerms = 3;    // digits per operand
 constexpr int kTcsKC = 64;      // k per chunk (128 bytes of bf16)
 constexpr int kTcsMaxCS = 8;    // CTAs per cluster (Kp <= 1024)
+constexpr int kTcsTraceR = 64;  // receiver rows handled on chip (partial C.V per CTA)
+constexpr int kTcsTStride = 132;  // padded row stride (floats) of the on-chip trace operands
+
+// On-chip receiver traces reuse the stage ring during the epilogue: the new
+// rows Ys[W][132], the CTA's slab of C, Cs[64][132], and the partial traces
+// P[64][W] of this CTA's 128 rows.
+__host__ __device__ inline size_t tcs_trace_scratch_bytes(int W) {
+    return ((size_t)W * kTcsTStride + (size_t)kTcsTraceR * kTcsTStride + (size_t)kTcsTraceR * W) * 4;
+}
 
 // Integer digits of xs (|xs| <= 128): xs = d0 + 2^-8 d1 + 2^-16 d2 + e with
 // |e| <= 2^-17 and every d in [-128, 128].  Each operation is exact in FP32:
@@ -180,6 +189,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) rank2_tcs_kernel(const TcArgs a
     const int ncol = min(W, a.M - col0);
     const int row0 = crank * kTcRows;
     const int NKC = Kp / kTcsKC;
+    // receiver traces from on-chip data when C has at most 64 rows and the
+    // scratch fits in the stage ring (decided identically on the host)
+    const bool chip_tr = a.traces && a.R <= kTcsTraceR &&
+                         tcs_trace_scratch_bytes(W) <= (size_t)STAGES * tcs_stage_bytes(W);
     const int KC_T1B = 512 / kTcsKC;                // first chunk accumulated into T1b
     const bool two_t1 = Kp > 512;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -214,6 +227,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) rank2_tcs_kernel(const TcArgs a
     float* arow = grow + kTcRows;                   // [2][128]: 2^(eA_r - 7) of Avs, Asv
     unsigned* colmax = reinterpret_cast<unsigned*>(arow + 2 * kTcRows);  // [4][W] |y| bits
     float* gmax = reinterpret_cast<float*>(colmax + 4 * W);             // [CS][W]
+    float* Ys = reinterpret_cast<float*>(smem);                         // trace scratch (stage ring)
+    float* Cs = Ys + (size_t)W * kTcsTStride;
+    float* Pt = Cs + (size_t)kTcsTraceR * kTcsTStride;
 
     if (tid == 0) {
         *abort_flag = 0;
@@ -290,6 +306,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) rank2_tcs_kernel(const TcArgs a
             const unsigned char* Aop = static_cast<const unsigned char*>(half ? a.Aop[1] : a.Aop[0]) +
                                        (size_t)crank * NKC * kTcsTerms * kATileBytes;
             const unsigned char* Xsrc = half ? Xblk1 : Xblk0;
+            const bool tr_step = half == 0 && a.traces && ((n + 1) % a.r) == 0;
+            const bool chip_step = tr_step && chip_tr;
             bool have = false;
             if (warp == 0) {
                 if (lane == 0 && !*abort_flag) {
@@ -407,6 +425,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) rank2_tcs_kernel(const TcArgs a
                             Cy[gi] = c;
                         }
                         ynew[q] = y;
+                        if (chip_step) Ys[(size_t)j * kTcsTStride + rl] = y;
                         const unsigned m = __reduce_max_sync(0xffffffffu, __float_as_uint(fabsf(y)));
                         if (lane == 0) colmax[quad * W + j] = m;
                     }
@@ -421,7 +440,49 @@ __global__ void __launch_bounds__(kTcThreads, 1) rank2_tcs_kernel(const TcArgs a
                 }
                 tmem_wait_st();
                 tc_fence_before();
+                if (chip_step) {
+                    // this CTA's 128 columns of C (rows jr < 64; zero beyond R)
+                    for (int idx = ridx; idx < kTcsTraceR * kTcRows; idx += kTcReadWarps * 32) {
+                        const int jr = idx / kTcRows, r = idx % kTcRows;
+                        Cs[(size_t)jr * kTcsTStride + r] = jr < a.R ? a.C_p[(size_t)jr * Kp + row0 + r] : 0.f;
+                    }
+                }
                 reader_bar_sync();
+                if (chip_step) {
+                    // partial traces over the own rows, P[jr][c] = sum_r Cs[jr][r] Ys[c][r]
+                    // (fixed order): reader t computes jr = 4 (t / 16) + 0..3 and
+                    // columns (t % 16) * (W / 16) + 0..W/16-1
+                    constexpr int CB = W / 16;
+                    const int cgp = ridx % 16, jg = ridx / 16;
+                    float pacc[4][CB];
+#pragma unroll
+                    for (int t = 0; t < 4; ++t)
+#pragma unroll
+                        for (int i = 0; i < CB; ++i) pacc[t][i] = 0.f;
+#pragma unroll 2
+                    for (int r = 0; r < kTcRows; r += 4) {
+                        float4 cv4[4], yv4[CB];
+#pragma unroll
+                        for (int t = 0; t < 4; ++t)
+                            cv4[t] = *reinterpret_cast<const float4*>(Cs + (size_t)(4 * jg + t) * kTcsTStride + r);
+#pragma unroll
+                        for (int i = 0; i < CB; ++i)
+                            yv4[i] = *reinterpret_cast<const float4*>(Ys + (size_t)(cgp * CB + i) * kTcsTStride + r);
+#pragma unroll
+                        for (int t = 0; t < 4; ++t)
+#pragma unroll
+                            for (int i = 0; i < CB; ++i) {
+                                pacc[t][i] = __fmaf_rn(cv4[t].x, yv4[i].x, pacc[t][i]);
+                                pacc[t][i] = __fmaf_rn(cv4[t].y, yv4[i].y, pacc[t][i]);
+                                pacc[t][i] = __fmaf_rn(cv4[t].z, yv4[i].z, pacc[t][i]);
+                                pacc[t][i] = __fmaf_rn(cv4[t].w, yv4[i].w, pacc[t][i]);
+                            }
+                    }
+#pragma unroll
+                    for (int t = 0; t < 4; ++t)
+#pragma unroll
+                        for (int i = 0; i < CB; ++i) Pt[(size_t)(4 * jg + t) * W + cgp * CB + i] = pacc[t][i];
+                }
                 // block maxima of this CTA, stored into every CTA of the cluster
                 if (ridx < W) {
                     const unsigned bm = max(max(colmax[ridx], colmax[W + ridx]),
@@ -441,6 +502,19 @@ __global__ void __launch_bounds__(kTcThreads, 1) rank2_tcs_kernel(const TcArgs a
                 xinv[j] = ldexpf(1.f, 7 - e);
             }
             __syncthreads();
+            if (chip_step) {
+                // receiver rows crank*rpc .. : sum of the CTAs' partials in rank order
+                const int rec = (n + 1) / a.r - 1;
+                const int npair = a.rpc * ncol;
+                for (int pr = tid; pr < npair; pr += kTcThreads) {
+                    const int c = pr / a.rpc, jj = pr % a.rpc, jr = crank * a.rpc + jj;
+                    if (jr >= a.R) continue;
+                    float tsum = 0.f;
+                    for (int q = 0; q < CS; ++q) tsum += *cluster.map_shared_rank(Pt + (size_t)jr * W + c, q);
+                    a.traces[((size_t)rec * a.Mtot + col0 + c) * a.R + jr] = tsum;
+                }
+                fence_proxy_async_shared();  // scratch writes before the next bulk copies into the ring
+            }
             if (reader) {
                 unsigned char* Xdst = half ? Xblk0 : Xblk1;  // V feeds the S half and vice versa
                 const int row = row0 + rl;
@@ -486,7 +560,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) rank2_tcs_kernel(const TcArgs a
             __syncthreads();
             if (*abort_all) break;
             // ---- receiver traces of V^{n+1} (after the velocity half is published)
-            if (half == 0 && a.traces && ((n + 1) % a.r) == 0) {
+            if (tr_step && !chip_step) {
                 const int rec = (n + 1) / a.r - 1;
                 const int npair = a.rpc * ncol;
                 for (int pr = warp; pr < npair; pr += kTcThreads / 32) {
