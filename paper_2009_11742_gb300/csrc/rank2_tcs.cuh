@@ -170,6 +170,31 @@ __device__ __forceinline__ void load_group8(const float* __restrict__ Y, const f
     }
 }
 
+// Maximum over the 32 lanes of each of 8 values (|y| bits of 8 columns, one
+// row per lane), as a butterfly reduce-scatter: afterwards lane l holds the
+// maximum for column 4 b16 + 2 b8 + b4 (b_o = bit o of l), every lane of a
+// group of four the same.
+__device__ __forceinline__ unsigned colmax8(unsigned (&v)[8], int lane, int& col) {
+    int base = 0;
+#pragma unroll
+    for (int s = 0; s < 3; ++s) {
+        const int o = 16 >> s;
+        const int half = 4 >> s;
+        const bool up = (lane & o) != 0;
+#pragma unroll
+        for (int k = 0; k < half; ++k) {
+            const unsigned send = up ? v[k] : v[k + half];
+            const unsigned keep = up ? v[k + half] : v[k];
+            v[k] = max(keep, __shfl_xor_sync(0xffffffffu, send, o));
+        }
+        base += up ? half : 0;
+    }
+    v[0] = max(v[0], __shfl_xor_sync(0xffffffffu, v[0], 2));
+    v[0] = max(v[0], __shfl_xor_sync(0xffffffffu, v[0], 1));
+    col = base;
+    return v[0];
+}
+
 __device__ __forceinline__ void reader_bar_sync() {
     asm volatile("bar.sync 1, %0;" ::"r"(kTcReadWarps * 32) : "memory");
 }
@@ -388,6 +413,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) rank2_tcs_kernel(const TcArgs a
                 have = __shfl_sync(0xffffffffu, gotl, 0) != 0;
                 tc_fence_after();
                 const float ars = arow[half * kTcRows + rl];
+                const float grw = grow[rl];
                 const uint32_t tl = tbase + ((uint32_t)(32 * quad) << 16) + (uint32_t)jbase;
                 // one 8-column group: readout, update, new state parked in TMEM,
                 // loads of the group two ahead into the same buffers
@@ -406,7 +432,13 @@ __global__ void __launch_bounds__(kTcThreads, 1) rank2_tcs_kernel(const TcArgs a
                         if (!have || !two_t1) r1b[q] = 0u;
                     }
                     if (have) tmem_wait_ld4(r0, r1a, r1b, r2);
-                    float ynew[8];
+                    float ynew[8], scl[8], fq[8];
+                    unsigned ybits[8];
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) {  // shared-memory operands before any global store
+                        scl[q] = ars * xsc[jbase + i0 + q];
+                        fq[q] = half == 0 ? fcol[jbase + i0 + q] : 0.f;
+                    }
 #pragma unroll
                     for (int q = 0; q < 8; ++q) {
                         const int j = jbase + i0 + q;
@@ -415,8 +447,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) rank2_tcs_kernel(const TcArgs a
                             const float t1 = __fadd_rn(__uint_as_float(r1a[q]), __uint_as_float(r1b[q]));
                             const float u = __fmaf_rn(__uint_as_float(r2[q]), 1.f / 65536.f, t1 * (1.f / 256.f));
                             const float R = __fadd_rn(__uint_as_float(r0[q]), u);
-                            float inc = R * (ars * xsc[j]);
-                            if (half == 0) inc = __fmaf_rn(grow[rl], fcol[j], inc);
+                            float inc = R * scl[q];
+                            if (half == 0) inc = __fmaf_rn(grw, fq[q], inc);
                             inc = inc * dt;
                             float c = cg_[q];
                             y = kahan_add(y, inc, c);
@@ -425,9 +457,13 @@ __global__ void __launch_bounds__(kTcThreads, 1) rank2_tcs_kernel(const TcArgs a
                             Cy[gi] = c;
                         }
                         ynew[q] = y;
+                        ybits[q] = __float_as_uint(fabsf(y));
                         if (chip_step) Ys[(size_t)j * kTcsTStride + rl] = y;
-                        const unsigned m = __reduce_max_sync(0xffffffffu, __float_as_uint(fabsf(y)));
-                        if (lane == 0) colmax[quad * W + j] = m;
+                    }
+                    {
+                        int cq;
+                        const unsigned m = colmax8(ybits, lane, cq);
+                        if ((lane & 3) == 0) colmax[quad * W + jbase + i0 + cq] = m;
                     }
                     tmem_st8(tl + (uint32_t)(4 * AST + i0), ynew);
                     if (g + 2 < NG)
@@ -522,12 +558,14 @@ __global__ void __launch_bounds__(kTcThreads, 1) rank2_tcs_kernel(const TcArgs a
                 tc_fence_after();
 #pragma unroll 1
                 for (int i0 = 0; i0 < WH; i0 += 8) {
-                    float yn[8];
+                    float yn[8], xi[8];
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) xi[q] = xinv[chalf * WH + i0 + q];  // before any store
                     tmem_ld8(ts + (uint32_t)i0, yn);
 #pragma unroll
                     for (int q = 0; q < 8; ++q) {
                         const int j = chalf * WH + i0 + q;
-                        tcs_store_digits(Xdst, xterm, tcs_xoffset(row, j, W), yn[q] * xinv[j]);
+                        tcs_store_digits(Xdst, xterm, tcs_xoffset(row, j, W), yn[q] * xi[q]);
                     }
                 }
                 tc_fence_before();
