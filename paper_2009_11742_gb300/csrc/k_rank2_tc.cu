@@ -210,7 +210,7 @@ static bool plan_rank2_tcs(int Kp, int M, int R, int Wforce, TcPlan* p) {
         attr[0].val.clusterDim.y = 1;
         attr[0].val.clusterDim.z = 1;
         cfg.gridDim = dim3(cs, 1, 1);
-        cfg.blockDim = dim3(kTcThreads, 1, 1);
+        cfg.blockDim = dim3(kTcsThreads, 1, 1);
         cfg.dynamicSmemBytes = smem;
         cfg.attrs = attr;
         cfg.numAttrs = 1;
@@ -305,7 +305,7 @@ cudaError_t launch_rank2_tc(const TcArgs& a_in, const TcPlan& p, cudaStream_t st
     attr[0].val.clusterDim.y = 1;
     attr[0].val.clusterDim.z = 1;
     cfg.gridDim = dim3(p.cs * p.nclusters, 1, 1);
-    cfg.blockDim = dim3(kTcThreads, 1, 1);
+    cfg.blockDim = dim3(p.prec == ROM_BF16S ? kTcsThreads : kTcThreads, 1, 1);
     cfg.dynamicSmemBytes = p.smem;
     cfg.stream = st;
     cfg.attrs = attr;

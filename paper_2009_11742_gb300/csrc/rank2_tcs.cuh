@@ -25,10 +25,11 @@
 // The state's column exponent needs the column maximum over all rows, which
 // the CTAs of a cluster agree on through distributed shared memory with one
 // extra cluster barrier per half-step.  Work split, pipeline and bounded
-// waits are those of rank2_tc.cuh: warp 0 streams operator and state digit
-// tiles into a ring of stages, warp 1 issues the MMAs, warps 2..9 read out,
-// fuse the forcing g f^T (Sec. 2.2, 3.2) and the Kahan-compensated update,
-// and slice the new state into the exchange tiles of the next half-step.
+// waits follow rank2_tc.cuh: lane 0 of warp 0 streams operator and state
+// digit tiles into a ring of stages, lane 0 of warp 1 issues the MMAs, and
+// then all eight warps read out, fuse the forcing g f^T (Sec. 2.2, 3.2) and
+// the Kahan-compensated update, and slice the new state into the exchange
+// tiles of the next half-step.
 #pragma once
 
 #include <cooperative_groups.h>
@@ -45,6 +46,7 @@ namespace romk {
 constexpr int kTcsTerms = 3;    // digits per operand
 constexpr int kTcsKC = 64;      // k per chunk (128 bytes of bf16)
 constexpr int kTcsMaxCS = 8;    // CTAs per cluster (Kp <= 1024)
+constexpr int kTcsThreads = 256;  // 8 warps, all read out; lane 0 of warps 0 / 1 also produce / issue MMAs
 constexpr int kTcsTraceR = 64;  // receiver rows handled on chip (partial C.V per CTA)
 constexpr int kTcsTStride = 132;  // padded row stride (floats) of the on-chip trace operands
 
@@ -196,11 +198,11 @@ __device__ __forceinline__ unsigned colmax8(unsigned (&v)[8], int lane, int& col
 }
 
 __device__ __forceinline__ void reader_bar_sync() {
-    asm volatile("bar.sync 1, %0;" ::"r"(kTcReadWarps * 32) : "memory");
+    asm volatile("bar.sync 1, %0;" ::"r"(kTcsThreads) : "memory");
 }
 
 template <int W>
-__global__ void __launch_bounds__(kTcThreads, 1) rank2_tcs_kernel(const TcArgs a) {
+__global__ void __launch_bounds__(kTcsThreads, 1) rank2_tcs_kernel(const TcArgs a) {
     constexpr int WH = W / 2;                       // columns per readout warp
     constexpr int AST = tcs_acc_stride(W);          // accumulator column stride
     constexpr uint32_t NCOLS = tcs_tmem_cols(W);
@@ -223,11 +225,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) rank2_tcs_kernel(const TcArgs a
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const float dt = (float)a.dt;
     const long long limit = a.spin_limit;
-    const bool reader = warp >= kTcReadWarp0;
     const int quad = warp & 3;                      // TMEM lane quadrant of this warp
-    const int chalf = (warp - kTcReadWarp0) / 4;    // column half of a readout warp
+    const int chalf = warp / 4;                     // column half of a readout warp
     const int rl = 32 * quad + lane;                // row (within the slab) of a reader
-    const int ridx = tid - 32 * kTcReadWarp0;       // reader index 0..255
+    const int ridx = tid;                           // reader index 0..255
 
     extern __shared__ unsigned char smem_raw[];
     unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -266,29 +267,29 @@ __global__ void __launch_bounds__(kTcThreads, 1) rank2_tcs_kernel(const TcArgs a
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 1) { tmem_alloc(tslot, NCOLS); tmem_relinquish(); }
-    for (int c = tid; c < W; c += kTcThreads) Tcol[c] = (a.Tper && c < ncol) ? a.Tper[col0 + c] : 1.f;
+    for (int c = tid; c < W; c += kTcsThreads) Tcol[c] = (a.Tper && c < ncol) ? a.Tper[col0 + c] : 1.f;
     if (tid < kTcRows) {
         grow[tid] = a.g_p[row0 + tid];
         arow[tid] = a.Ascale[0][row0 + tid];
         arow[kTcRows + tid] = a.Ascale[1][row0 + tid];
     }
-    for (int i = tid; i < 4 * W; i += kTcThreads) colmax[i] = 0u;
+    for (int i = tid; i < 4 * W; i += kTcsThreads) colmax[i] = 0u;
     __syncthreads();
 
     // ---- column maxima of S^0 over the own rows, agreed across the cluster
-    for (int idx = tid; idx < kTcRows * W; idx += kTcThreads) {
+    for (int idx = tid; idx < kTcRows * W; idx += kTcsThreads) {
         const int j = idx / kTcRows, r = idx % kTcRows, row = row0 + r;
         const float x = (j < ncol && row < a.Ks) ? a.S[(size_t)(col0 + j) * a.Ks + row] : 0.f;
         atomicMax(&colmax[j], __float_as_uint(fabsf(x)));
     }
     cluster.sync();  // every CTA runs and is initialised before remote stores
-    for (int j = tid; j < W; j += kTcThreads) {
+    for (int j = tid; j < W; j += kTcsThreads) {
         const float bm = __uint_as_float(colmax[j]);
         for (int q = 0; q < CS; ++q) *cluster.map_shared_rank(gmax + crank * W + j, q) = bm;
     }
     cluster.sync();
     int bad = 0;
-    for (int j = tid; j < W; j += kTcThreads) {
+    for (int j = tid; j < W; j += kTcsThreads) {
         float mx = 0.f;
         for (int q = 0; q < CS; ++q) mx = fmaxf(mx, gmax[q * W + j]);
         bad |= !isfinite(mx);
@@ -300,12 +301,12 @@ __global__ void __launch_bounds__(kTcThreads, 1) rank2_tcs_kernel(const TcArgs a
     const size_t xterm = (size_t)Kp * W * 2;  // bytes of one digit term of one block
     unsigned char* const Xblk0 = static_cast<unsigned char*>(a.X[0]) + (size_t)blk * kTcsTerms * xterm;
     unsigned char* const Xblk1 = static_cast<unsigned char*>(a.X[1]) + (size_t)blk * kTcsTerms * xterm;
-    for (int idx = tid; idx < kTcRows * W; idx += kTcThreads) {
+    for (int idx = tid; idx < kTcRows * W; idx += kTcsThreads) {
         const int j = idx / kTcRows, r = idx % kTcRows, row = row0 + r;
         const float x = (j < ncol && row < a.Ks) ? a.S[(size_t)(col0 + j) * a.Ks + row] : 0.f;
         tcs_store_digits(Xblk0, xterm, tcs_xoffset(row, j, W), x * xinv[j]);
     }
-    for (int c = tid; c < W; c += kTcThreads) {
+    for (int c = tid; c < W; c += kTcsThreads) {
         float f = 0.f;
         if (c < ncol) {
             if (a.ftab) f = a.ftab[col0 + c];
@@ -334,6 +335,17 @@ __global__ void __launch_bounds__(kTcThreads, 1) rank2_tcs_kernel(const TcArgs a
             const bool tr_step = half == 0 && a.traces && ((n + 1) % a.r) == 0;
             const bool chip_step = tr_step && chip_tr;
             bool have = false;
+            // ---- readout warps first start loading their old rows and carries
+            const int row = row0 + rl;
+            const int Kown = half == 0 ? a.Kv : a.Ks;
+            float* Y = (half == 0 ? a.V : a.S) + row;
+            float* Cy = (half == 0 ? a.compV : a.compS) + row;
+            const bool rowok = row < Kown;
+            const int jbase = chalf * WH;
+            constexpr int NG = WH / 8;
+            float ya[8], ca[8], yb[8], cb[8];
+            load_group8(Y, Cy, Kown, col0 + jbase, ncol - jbase, rowok, ya, ca);
+            if (NG > 1) load_group8(Y, Cy, Kown, col0 + jbase + 8, ncol - jbase - 8, rowok, yb, cb);
             if (warp == 0) {
                 if (lane == 0 && !*abort_flag) {
                     // ---- producer: stream every k-chunk's digit tiles into the stage ring
@@ -392,22 +404,13 @@ __global__ void __launch_bounds__(kTcThreads, 1) rank2_tcs_kernel(const TcArgs a
                     if (ok) mma_commit(dready);
                 }
                 __syncwarp();
-            } else if (reader) {
+            }
+            {
                 // ---- readers: one readout of the four accumulators, the fused
                 //      forcing and Kahan update, the column maxima of the new
                 //      state.  The old rows and carries are loaded two 8-column
                 //      groups ahead (the first two while the MMAs run); the new
                 //      rows wait in spare tensor-memory columns for the slicing.
-                const int row = row0 + rl;
-                const int Kown = half == 0 ? a.Kv : a.Ks;
-                float* Y = (half == 0 ? a.V : a.S) + row;
-                float* Cy = (half == 0 ? a.compV : a.compS) + row;
-                const bool rowok = row < Kown;
-                const int jbase = chalf * WH;
-                constexpr int NG = WH / 8;
-                float ya[8], ca[8], yb[8], cb[8];
-                load_group8(Y, Cy, Kown, col0 + jbase, ncol - jbase, rowok, ya, ca);
-                if (NG > 1) load_group8(Y, Cy, Kown, col0 + jbase + 8, ncol - jbase - 8, rowok, yb, cb);
                 int gotl = 0;
                 if (lane == 0) gotl = (*abort_flag == 0) && mbarrier_wait(dready, (uint32_t)(hs & 1), limit, abort_flag);
                 have = __shfl_sync(0xffffffffu, gotl, 0) != 0;
@@ -478,7 +481,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) rank2_tcs_kernel(const TcArgs a
                 tc_fence_before();
                 if (chip_step) {
                     // this CTA's 128 columns of C (rows jr < 64; zero beyond R)
-                    for (int idx = ridx; idx < kTcsTraceR * kTcRows; idx += kTcReadWarps * 32) {
+                    for (int idx = ridx; idx < kTcsTraceR * kTcRows; idx += kTcsThreads) {
                         const int jr = idx / kTcRows, r = idx % kTcRows;
                         Cs[(size_t)jr * kTcsTStride + r] = jr < a.R ? a.C_p[(size_t)jr * Kp + row0 + r] : 0.f;
                     }
@@ -529,7 +532,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) rank2_tcs_kernel(const TcArgs a
             }
             cluster.sync();
             // ---- column exponents of the new state (the B operand of the next half-step)
-            for (int j = tid; j < W; j += kTcThreads) {
+            for (int j = tid; j < W; j += kTcsThreads) {
                 float mx = 0.f;
                 for (int q = 0; q < CS; ++q) mx = fmaxf(mx, gmax[q * W + j]);
                 bad |= !isfinite(mx);
@@ -542,7 +545,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) rank2_tcs_kernel(const TcArgs a
                 // receiver rows crank*rpc .. : sum of the CTAs' partials in rank order
                 const int rec = (n + 1) / a.r - 1;
                 const int npair = a.rpc * ncol;
-                for (int pr = tid; pr < npair; pr += kTcThreads) {
+                for (int pr = tid; pr < npair; pr += kTcsThreads) {
                     const int c = pr / a.rpc, jj = pr % a.rpc, jr = crank * a.rpc + jj;
                     if (jr >= a.R) continue;
                     float tsum = 0.f;
@@ -551,9 +554,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) rank2_tcs_kernel(const TcArgs a
                 }
                 fence_proxy_async_shared();  // scratch writes before the next bulk copies into the ring
             }
-            if (reader) {
+            {
                 unsigned char* Xdst = half ? Xblk0 : Xblk1;  // V feeds the S half and vice versa
-                const int row = row0 + rl;
                 const uint32_t ts = tbase + ((uint32_t)(32 * quad) << 16) + (uint32_t)(4 * AST + chalf * WH);
                 tc_fence_after();
 #pragma unroll 1
@@ -573,7 +575,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) rank2_tcs_kernel(const TcArgs a
             fence_proxy_async_global();
             // forcing of the next step (read by the next velocity epilogue)
             if (half == 1 && n + 1 < N) {
-                for (int c = tid; c < W; c += kTcThreads) {
+                for (int c = tid; c < W; c += kTcsThreads) {
                     float f = 0.f;
                     if (c < ncol) {
                         if (a.ftab) f = a.ftab[(size_t)(n + 1) * a.Mtot + col0 + c];
@@ -601,7 +603,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) rank2_tcs_kernel(const TcArgs a
             if (tr_step && !chip_step) {
                 const int rec = (n + 1) / a.r - 1;
                 const int npair = a.rpc * ncol;
-                for (int pr = warp; pr < npair; pr += kTcThreads / 32) {
+                for (int pr = warp; pr < npair; pr += kTcsThreads / 32) {
                     const int jj = pr / ncol, c = pr % ncol, jr = crank * a.rpc + jj;
                     if (jr >= a.R) continue;
                     const float* vcol = a.V + (size_t)(col0 + c) * a.Kv;
