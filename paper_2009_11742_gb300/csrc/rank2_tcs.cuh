@@ -442,26 +442,32 @@ __global__ void __launch_bounds__(kTcsThreads, 1) rank2_tcs_kernel(const TcArgs 
                         scl[q] = ars * xsc[jbase + i0 + q];
                         fq[q] = half == 0 ? fcol[jbase + i0 + q] : 0.f;
                     }
+                    // branch-free update of the 8 columns (the valid entries are
+                    // selected afterwards), so that their dependency chains interleave
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) {
+                        const float t1 = __fadd_rn(__uint_as_float(r1a[q]), __uint_as_float(r1b[q]));
+                        const float u = __fmaf_rn(__uint_as_float(r2[q]), 1.f / 65536.f, t1 * (1.f / 256.f));
+                        const float R = __fadd_rn(__uint_as_float(r0[q]), u);
+                        float inc = R * scl[q];
+                        inc = half == 0 ? __fmaf_rn(grw, fq[q], inc) : inc;
+                        inc = inc * dt;
+                        float c = cg_[q];
+                        const float y = kahan_add(yg[q], inc, c);
+                        const bool ok = have && rowok && jbase + i0 + q < ncol;
+                        ynew[q] = ok ? y : yg[q];
+                        cg_[q] = ok ? c : cg_[q];
+                        ybits[q] = __float_as_uint(fabsf(ynew[q]));
+                    }
 #pragma unroll
                     for (int q = 0; q < 8; ++q) {
                         const int j = jbase + i0 + q;
-                        float y = yg[q];
                         if (have && rowok && j < ncol) {
-                            const float t1 = __fadd_rn(__uint_as_float(r1a[q]), __uint_as_float(r1b[q]));
-                            const float u = __fmaf_rn(__uint_as_float(r2[q]), 1.f / 65536.f, t1 * (1.f / 256.f));
-                            const float R = __fadd_rn(__uint_as_float(r0[q]), u);
-                            float inc = R * scl[q];
-                            if (half == 0) inc = __fmaf_rn(grw, fq[q], inc);
-                            inc = inc * dt;
-                            float c = cg_[q];
-                            y = kahan_add(y, inc, c);
                             const size_t gi = (size_t)(col0 + j) * Kown;
-                            Y[gi] = y;
-                            Cy[gi] = c;
+                            Y[gi] = ynew[q];
+                            Cy[gi] = cg_[q];
                         }
-                        ynew[q] = y;
-                        ybits[q] = __float_as_uint(fabsf(y));
-                        if (chip_step) Ys[(size_t)j * kTcsTStride + rl] = y;
+                        if (chip_step) Ys[(size_t)j * kTcsTStride + rl] = ynew[q];
                     }
                     {
                         int cq;
