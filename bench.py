@@ -180,9 +180,21 @@ def cpu_baseline_sample(p, target_s=12.0):
     t0 = time.perf_counter()
     oracle.problem_forward(p, nsteps=nst, r=WORKLOAD["r"], columns=cols)
     dt = time.perf_counter() - t0
+    # the same oracle on one thread (a few columns, a few seconds)
+    c1 = cols[:2]
+    t0 = time.perf_counter()
+    oracle.problem_forward(p, nsteps=100, r=WORKLOAD["r"], columns=c1, threads=1)
+    per1 = (time.perf_counter() - t0) / 100
+    n1 = int(max(100, min(WORKLOAD["nsteps"], 4.0 / max(per1, 1e-9))))
+    n1 -= n1 % WORKLOAD["r"]
+    t0 = time.perf_counter()
+    oracle.problem_forward(p, nsteps=n1, r=WORKLOAD["r"], columns=c1, threads=1)
+    dt1 = time.perf_counter() - t0
     return {"value": ncol * nst / dt, "unit": "sample-steps/s", "cores": cores, "kind": "oracle",
             "sample": f"{ncol} of {WORKLOAD['M']} columns x {nst} of {WORKLOAD['nsteps']} "
-                      f"steps ({dt:.1f} s, OpenMP over columns)"}
+                      f"steps ({dt:.1f} s, OpenMP over columns)",
+            "one_thread": {"value": len(c1) * n1 / dt1, "unit": "sample-steps/s",
+                           "sample": f"{len(c1)} columns x {n1} steps ({dt1:.1f} s)"}}
 
 
 def rank_periods(T_all, rank, world):
@@ -229,9 +241,10 @@ def main():
                     help="leapfrog steps per run (default: the workload's 10000; profiling only)")
     ap.add_argument("--only-rank2", action="store_true",
                     help="time the rank-2 runs only (no e2e, rank-1, oracle legs; profiling only)")
-    ap.add_argument("--workload", type=int, default=1, choices=[1, 2, 3, 4],
-                    help="1: K=512 FP32 (default, the headline); 2: K=1024 split precision; "
-                         "3: 64 batched ROMs; 4: adjoint K=512 M=128 N=4000 c=64")
+    ap.add_argument("--workload", type=int, default=1, choices=[0, 1, 2, 3, 4, 5],
+                    help="0: K=128 M=16 N=1000 FP64; 1: K=512 FP32 (default, the headline); "
+                         "2: K=1024 split precision; 3: 64 batched ROMs; 4: adjoint K=512 M=128 N=4000 c=64; "
+                         "5: many-query UQ run (Kv=436, Ks=417, M=512, 20000 steps) with ensemble statistics")
     ap.add_argument("--prec", default=None, help="override the workload's precision")
     ap.add_argument("--tc-cols", type=int, default=0, help="tensor-core columns per block")
     args = ap.parse_args()
@@ -256,6 +269,10 @@ def main():
     rbuild.build()
     from paper_2009_11742_gb300 import inputs, rom
 
+    if args.workload == 0:
+        return bench_fp64(args, torch, dev, inputs, rom)
+    if args.workload == 5:
+        return bench_uq(args, torch, dev, inputs, rom)
     if args.workload == 3:
         return bench_batched(args, torch, dev, inputs, rom)
     if args.workload == 4:
@@ -457,13 +474,134 @@ def main():
         "clocks": clocks,
         "wall_s_timed_region": wall,
         "rank1": {"single_sample_steps_s": r1_single, "ensemble_sample_steps_s": r1_ens,
-                  "rank2_speedup_vs_best_rank1": value / world / rank1_best},
+                  "rank2_speedup_vs_best_rank1": value / world / rank1_best,
+                  # operator bytes per sample-step: both K x K FP32 operators (2 MB at
+                  # K = 512, L2-resident, so L2 rather than HBM is the ceiling)
+                  "single_operator_gbs": r1_single * 8.0 * K * K / 1e9,
+                  "ensemble_operator_gbs": r1_ens * 8.0 * K * K / 1e9,
+                  "hbm_gbs_measured": pk.get("hbm_gbs")},
         "rel_err_vs_oracle": err,
     }
     print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
     h.close()
+    return 0
+
+
+def bench_uq(args, torch, dev, inputs, rom):
+    """Workload 5: the many-query UQ run of Sec. 4.5.2 on synthetic operators
+    (Kv = 436, Ks = 417, 512 realizations of T ~ U(31, 69) steps, 20000
+    steps, 64 receivers every 10 steps), then the per-receiver ensemble mean
+    and 5/50/95 % bands on the device.  Reports both times, the rank-2 vs
+    rank-1 ensemble throughput ratio and sampled accuracy."""
+    c = inputs.CONFIGS[5]
+    p = inputs.config(5)
+    N = args.nsteps or c["steps"]
+    r, M, R, Kv, Ks = c["r"], p.M, p.R, p.Kv, p.Ks
+    h = rom.Rom.from_problem(p)
+    V = rom.Rom.new_state(Kv, M, "fp32", device=dev)
+    S = rom.Rom.new_state(Ks, M, "fp32", device=dev)
+    T = torch.as_tensor(p.T, dtype=torch.float32, device=dev)
+    tr = torch.zeros((N // r, M, R), dtype=torch.float32, device=dev)
+    stream = torch.cuda.Stream(device=dev)
+
+    def one():
+        V.zero_(); S.zero_()
+        h.run_rank2(V, S, T, N, r=r, traces=tr, prec="fp32", stream=stream)
+
+    for _ in range(max(1, args.warmup)):
+        one()
+        with torch.cuda.stream(stream):
+            rom.trace_stats(tr, c["probs"], stream=stream)
+    torch.cuda.synchronize()
+    t_run, t_stats = [], []
+    for _ in range(args.steps):
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        V.zero_(); S.zero_()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        h.run_rank2(V, S, T, N, r=r, traces=tr, prec="fp32", stream=stream)
+        e1.record(stream)
+        with torch.cuda.stream(stream):
+            mean, q = rom.trace_stats(tr, c["probs"], stream=stream)
+        e2.record(stream)
+        torch.cuda.synchronize()
+        t_run.append(e0.elapsed_time(e1) * 1e-3)
+        t_stats.append(e1.elapsed_time(e2) * 1e-3)
+    tr_run, tr_stats = sum(t_run) / len(t_run), sum(t_stats) / len(t_stats)
+    # rank-1 ensemble (one realization per CTA, operators streamed) on 2000 steps
+    N1 = min(N, 2000)
+    Ve = rom.Rom.new_state(Kv, M, "fp32", device=dev)
+    Se = rom.Rom.new_state(Ks, M, "fp32", device=dev)
+    h.run_rank1_ensemble(Ve, Se, T, 200, prec="fp32", stream=stream)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    h.run_rank1_ensemble(Ve, Se, T, N1, prec="fp32", stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    r1 = M * N1 / (e0.elapsed_time(e1) * 1e-3)
+    # accuracy: 4 sampled realizations over the first 2000 steps
+    import oracle
+    Na = min(N, 2000)
+    V.zero_(); S.zero_()
+    tra = torch.zeros((Na // r, M, R), dtype=torch.float32, device=dev)
+    h.run_rank2(V, S, T, Na, r=r, traces=tra, prec="fp32", stream=stream)
+    torch.cuda.synchronize()
+    cols = np.array([0, 170, 341, 511])
+    _, _, tro = oracle.problem_forward(p, nsteps=Na, r=r, columns=cols)
+    tg = tra.transpose(1, 2).cpu().numpy()[:, :, cols]
+    err = float(np.linalg.norm(tg - tro) / np.linalg.norm(tro))
+    print(json.dumps({"only_rank2": True, "workload": c["name"], "nsteps": N,
+                      "value": M * N / tr_run, "unit": "sample-steps/s",
+                      "run_ms": 1e3 * tr_run, "stats_ms": 1e3 * tr_stats,
+                      "stats": {"records": N // r, "receivers": R, "realizations": M,
+                                "probs": list(c["probs"])},
+                      "rank1_ensemble_sample_steps_s": r1,
+                      "rank2_over_rank1_ensemble": (M * N / tr_run) / r1,
+                      "rel_err_traces_vs_oracle": {"value": err, "columns": cols.tolist(), "steps": Na}}),
+          flush=True)
+    return 0
+
+
+def bench_fp64(args, torch, dev, inputs, rom):
+    """Workload 0: the FP64 check path (K = 128, M = 16, 1000 steps, no traces):
+    latency-bound; achieved FP64 rate against the 1.25 TFLOP/s nominal FP64
+    rate, and the error against the FP64 oracle."""
+    p = inputs.config(0)
+    K, M, N = 128, 16, args.nsteps or 1000
+    h = rom.Rom.from_problem(p)
+    V = rom.Rom.new_state(K, M, "fp64", device=dev)
+    S = rom.Rom.new_state(K, M, "fp64", device=dev)
+    T = torch.as_tensor(p.T, dtype=torch.float64, device=dev)
+    stream = torch.cuda.Stream(device=dev)
+    for _ in range(args.warmup):
+        V.zero_(); S.zero_()
+        h.run_rank2(V, S, T, N, prec="fp64", stream=stream)
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(args.steps):
+        V.zero_(); S.zero_()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        h.run_rank2(V, S, T, N, prec="fp64", stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1) * 1e-3)
+    t = sum(ts) / len(ts)
+    import oracle
+    Vo, So, _ = oracle.problem_forward(p, nsteps=N, r=0)
+    Vg, Sg = V.cpu().numpy(), S.cpu().numpy()
+    flops = 4.0 * K * K * M * N
+    print(json.dumps({"only_rank2": True, "workload": "rank2-fp64-K128-M16-N1000", "nsteps": N,
+                      "value": M * N / t, "unit": "sample-steps/s", "ms_per_step": 1e3 * t,
+                      "us_per_leapfrog_step": 1e6 * t / N,
+                      "gflops_fp64": flops / t / 1e9, "frac_of_fp64_nominal_1250_gflops": flops / t / 1.25e12,
+                      "bound": "latency (1 MFLOP per leapfrog step)",
+                      "rel_err_vs_oracle": {"V": float(np.linalg.norm(Vg - Vo) / np.linalg.norm(Vo)),
+                                            "S": float(np.linalg.norm(Sg - So) / np.linalg.norm(So))}}),
+          flush=True)
     return 0
 
 

@@ -261,6 +261,31 @@ rom_status rom_adjoint(rom_t h, const void* V0, const void* S0, const void* T, i
 /* Workspace bytes rom_adjoint needs (0 for unsupported arguments). */
 size_t rom_adjoint_workspace_size(rom_t h, int M, int nsteps, int ckpt_every, int prec);
 
+/* ------------------------------------------------------ ensemble statistics */
+
+/*
+ * rom_trace_stats -- per-receiver statistics of an ensemble of receiver
+ * traces: the mean and percentile bands of the seismograms over the
+ * realizations, as in the Monte Carlo study of Sec. 4.5.2 (there over 512
+ * samples of the source period).
+ *   traces   device float, nrec x M x R in the layout rom_run_rank2 writes
+ *            (record k, realization m, receiver j at traces[(k M + m) R + j]);
+ *            every value finite.
+ *   probs    host array of nprobs probabilities in [0, 1] (nprobs <= 16).
+ *   mean_out device double, nrec x R (may be NULL): mean over the M
+ *            realizations, summed in FP64 by a fixed pairwise tree.
+ *   q_out    device double, nprobs x nrec x R (may be NULL): for each p the
+ *            quantile by linear interpolation between order statistics
+ *            (Hyndman-Fan type 7): h = (M - 1) p, i = floor(h), t = h - i,
+ *            q = x(i) + t (x(i+1) - x(i)) with x(.) the values sorted
+ *            ascending on the device, evaluated as b - (1 - t)(b - a) when
+ *            t >= 1/2 (a = x(i), b = x(i+1)).
+ * 1 <= M <= 4096.  Asynchronous on `stream`.  Errors: ROM_E_INVAL (sizes,
+ * host pointers, a probability outside [0, 1]), ROM_E_CUDA.
+ */
+rom_status rom_trace_stats(const float* traces, int nrec, int R, int M, const double* probs,
+                           int nprobs, double* mean_out, double* q_out, void* stream);
+
 /* ------------------------------------------------------------- utilities */
 
 /*

@@ -9,10 +9,11 @@ of Sec. 4.5.2) and independent of the CUDA path.
 Pins (tests/test_oracle_*.py): discrete-energy invariance, closed form by
 eigendecomposition of the amplification matrix, the K = 1 textbook
 oscillator, superposition, exact zeros, time reversal, spectral radius vs.
-numpy's 2-norm, adjoint vs. finite differences and brute-force Jacobians.
+numpy's 2-norm, adjoint vs. finite differences and brute-force Jacobians,
+ensemble statistics vs. numpy's quantile and hand-computed order statistics.
 """
 from .oracle import (adjoint, build, energy, forward, inverse, max_threads,
-                     problem_forward, ricker, spectral_radius)
+                     problem_forward, ricker, spectral_radius, trace_stats)
 
 __all__ = ["adjoint", "build", "energy", "forward", "inverse", "max_threads",
-           "problem_forward", "ricker", "spectral_radius"]
+           "problem_forward", "ricker", "spectral_radius", "trace_stats"]

@@ -230,3 +230,28 @@ def problem_forward(p, V0=None, S0=None, nsteps=None, r=None, n0=0, T=None,
     rr = p.meta.get("r", 0) if r is None else r
     return forward(p.Avs, p.Asv, p.g, p.C if p.C.shape[0] > 0 else None, p.dt, V0, S0,
                    steps, T=Tm, n0=n0, r=rr, threads=threads)
+
+
+def trace_stats(traces, probs):
+    """Ensemble statistics of receiver traces (Sec. 4.5.2: mean and
+    percentile bands of the seismograms over the realizations).
+    traces: (nrec, M, R) array (record, realization, receiver).  Returns
+    (mean (nrec, R), q (len(probs), nrec, R)) in float64: the mean over the
+    realizations, and for each p the quantile by linear interpolation between
+    order statistics (Hyndman-Fan type 7): h = (M - 1) p, i = floor(h),
+    t = h - i, q = x(i) + t (x(i+1) - x(i)), written as b - (1 - t)(b - a)
+    for t >= 1/2 (a = x(i), b = x(i+1))."""
+    x = np.asarray(traces, np.float64)
+    nrec, M, R = x.shape
+    mean = x.mean(axis=1)
+    xs = np.sort(x, axis=1)
+    q = np.zeros((len(probs), nrec, R))
+    for n, p in enumerate(probs):
+        h = (M - 1) * float(p)
+        i = min(int(np.floor(h)), M - 1)
+        t = h - i
+        a = xs[:, i, :]
+        b = xs[:, min(i + 1, M - 1), :]
+        d = b - a
+        q[n] = b - d * (1.0 - t) if t >= 0.5 else a + d * t
+    return mean, q

@@ -80,8 +80,10 @@ def _f32(x):
 
 
 def make_problem(Kv: int, Ks: int | None = None, M: int = 1, R: int = 0,
-                 seed: int = 0, dt: float | None = None) -> RomProblem:
-    """Draw one problem with the recipe in the module docstring."""
+                 seed: int = 0, dt: float | None = None,
+                 period_range: tuple = (30.0, 60.0)) -> RomProblem:
+    """Draw one problem with the recipe in the module docstring (periods
+    T_m = u_m dt with u_m uniform on `period_range`, in steps)."""
     if Ks is None:
         Ks = Kv
     rng = np.random.default_rng(seed)
@@ -89,7 +91,7 @@ def make_problem(Kv: int, Ks: int | None = None, M: int = 1, R: int = 0,
     g = rng.standard_normal(Kv)
     g = _f32(g / np.linalg.norm(g))
     C = _f32(rng.standard_normal((R, Kv)) / np.sqrt(Kv))
-    u = rng.uniform(30.0, 60.0, M)
+    u = rng.uniform(period_range[0], period_range[1], M)
     Avs = np.ascontiguousarray(-Asv.T)
     if dt is None:
         dt = 0.5 / np.linalg.norm(Asv.astype(np.float64), 2)
@@ -118,14 +120,26 @@ CONFIGS = {
             prec="fp32", nroms=64),
     4: dict(name="adjoint-K512-M128-N4000-R64-r1-c64", K=512, M=128, R=64,
             steps=4000, r=1, seed=0, prec="fp32", ckpt=64, tstar_scale=1.05),
+    # many-query UQ run shaped like the Monte Carlo study of Sec. 4.5.2:
+    # K_v = 436, K_s = 417, 512 realizations of T ~ U(31, 69) (in steps),
+    # 20000 steps, receiver traces every 10 steps, ensemble mean and
+    # 5-95 % bands per receiver
+    5: dict(name="uq-Kv436-Ks417-M512-N20000-R64-r10", Kv=436, Ks=417, M=512, R=64,
+            steps=20000, r=10, seed=0, prec="fp32", period_range=(31.0, 69.0),
+            probs=(0.05, 0.5, 0.95)),
 }
 
 
 def config(i: int) -> RomProblem:
-    """The problem of workload i (0, 1, 2 or 4)."""
+    """The problem of workload i (0, 1, 2, 4 or 5)."""
     c = CONFIGS[i]
     if i == 3:
         raise ValueError("workload 3 is a batch; use batched_problems()")
+    if i == 5:
+        p = make_problem(c["Kv"], c["Ks"], c["M"], c["R"], seed=c["seed"],
+                         period_range=c["period_range"])
+        p.meta.update(c)
+        return p
     p = make_problem(c["K"], c["K"], c["M"], c["R"], seed=c["seed"])
     p.meta.update(c)
     return p

@@ -38,7 +38,7 @@ EXPORTED = ["rom_create", "rom_destroy", "rom_spectral_radius", "rom_sync_status
             "rom_debug_inject_stall", "rom_run_rank2", "rom_run_rank2_ex", "rom_run_rank1",
             "rom_run_rank1_ensemble", "rom_run_batched", "rom_adjoint",
             "rom_adjoint_workspace_size", "rom_rel_l2", "rom_spectral_radius_noalloc",
-            "rom_status_string", "rom_last_error", "rom_version"]
+            "rom_trace_stats", "rom_status_string", "rom_last_error", "rom_version"]
 
 _lock = threading.Lock()
 _lib = None
@@ -80,6 +80,7 @@ def _signatures(lib):
         "rom_adjoint_workspace_size": (ctypes.c_size_t, [_vp, _i, _i, _i, _i]),
         "rom_rel_l2": (_i, [_vp, _i, _vp, _i, ctypes.c_size_t, ctypes.POINTER(_d), _vp]),
         "rom_spectral_radius_noalloc": (_i, [_vp, _vp, _i, _i, ctypes.POINTER(_d), _vp]),
+        "rom_trace_stats": (_i, [_vp, _i, _i, _i, ctypes.POINTER(_d), _i, _vp, _vp, _vp]),
         "rom_status_string": (ctypes.c_char_p, [_i]),
         "rom_last_error": (ctypes.c_char_p, []),
         "rom_version": (_i, []),
@@ -259,6 +260,25 @@ def rom_spectral_radius_noalloc(Avs, Asv, Kv, Ks, stream=None):
 
 
 # ------------------------------------------------------------ tensor glue --
+def rom_trace_stats(traces, nrec, R, M, probs, nprobs, mean_out, q_out, stream=None):
+    pr = (_d * max(1, nprobs))(*[float(x) for x in probs])
+    return load().rom_trace_stats(traces, nrec, R, M, pr, nprobs, mean_out, q_out, stream)
+
+
+def trace_stats(traces, probs=(0.05, 0.5, 0.95), stream=None):
+    """Mean and quantile bands over the realizations of a (nrec, M, R) device
+    float32 trace buffer (the layout run_rank2 writes).  Returns device
+    float64 tensors mean (nrec, R) and q (len(probs), nrec, R)."""
+    torch = _torch()
+    nrec, M, R = traces.shape
+    mean = torch.empty((nrec, R), dtype=torch.float64, device=traces.device)
+    q = torch.empty((len(probs), nrec, R), dtype=torch.float64, device=traces.device)
+    st = stream.cuda_stream if hasattr(stream, "cuda_stream") else stream
+    _chk(rom_trace_stats(traces.data_ptr(), nrec, R, M, list(probs), len(probs), mean.data_ptr(),
+                         q.data_ptr(), st), "rom_trace_stats")
+    return mean, q
+
+
 def _torch():
     import torch
     return torch
