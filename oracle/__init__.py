@@ -13,7 +13,7 @@ numpy's 2-norm, adjoint vs. finite differences and brute-force Jacobians,
 ensemble statistics vs. numpy's quantile and hand-computed order statistics.
 """
 from .oracle import (adjoint, build, energy, forward, inverse, max_threads,
-                     problem_forward, ricker, spectral_radius, trace_stats)
+                     problem_forward, ricker, spectral_radius, trace_stats, wavelet)
 
 __all__ = ["adjoint", "build", "energy", "forward", "inverse", "max_threads",
-           "problem_forward", "ricker", "spectral_radius", "trace_stats"]
+           "problem_forward", "ricker", "spectral_radius", "trace_stats", "wavelet"]

@@ -53,11 +53,11 @@ def _load():
             lib.orc_forward.argtypes = [_dp, _dp, _dp, _dp, ctypes.c_int, ctypes.c_int,
                                         ctypes.c_int, ctypes.c_double, _dp, _dp, _dp, _dp,
                                         ctypes.c_int, ctypes.c_int, ctypes.c_long,
-                                        ctypes.c_int, _dp, ctypes.c_int]
+                                        ctypes.c_int, _dp, ctypes.c_int, ctypes.c_int]
             lib.orc_inverse.restype = ctypes.c_int
             lib.orc_inverse.argtypes = [_dp, _dp, _dp, ctypes.c_int, ctypes.c_int,
                                         ctypes.c_double, _dp, _dp, _dp, _dp, ctypes.c_int,
-                                        ctypes.c_int, ctypes.c_long, ctypes.c_int]
+                                        ctypes.c_int, ctypes.c_long, ctypes.c_int, ctypes.c_int]
             lib.orc_energy.restype = ctypes.c_double
             lib.orc_energy.argtypes = [_dp, ctypes.c_int, ctypes.c_int, ctypes.c_double,
                                        _dp, _dp, ctypes.c_int]
@@ -68,9 +68,11 @@ def _load():
             lib.orc_adjoint.argtypes = [_dp, _dp, _dp, _dp, ctypes.c_int, ctypes.c_int,
                                         ctypes.c_int, ctypes.c_double, _dp, _dp, _dp,
                                         ctypes.c_int, ctypes.c_int, ctypes.c_long, _dp,
-                                        _dp, _dp, _dp, _dp, ctypes.c_int]
+                                        _dp, _dp, _dp, _dp, ctypes.c_int, ctypes.c_int]
             lib.orc_ricker.restype = None
             lib.orc_ricker.argtypes = [_dp, _dp, ctypes.c_int, _dp, _dp]
+            lib.orc_wavelet.restype = None
+            lib.orc_wavelet.argtypes = [ctypes.c_int, _dp, _dp, ctypes.c_int, _dp, _dp]
             lib.orc_max_threads.restype = ctypes.c_int
             _lib = lib
     return _lib
@@ -96,6 +98,20 @@ def _check(rc: int, what: str):
         raise RuntimeError(f"oracle {what} failed with code {rc}")
 
 
+def wavelet(kind, t, T):
+    """Source signal of `kind` (0 Ricker, 1 first derivative of a Gaussian,
+    Sec. 3.2) and its T-derivative, elementwise (float64)."""
+    t = np.asarray(t, np.float64)
+    T = np.asarray(T, np.float64)
+    shape = np.broadcast(t, T).shape
+    tb = np.ascontiguousarray(np.broadcast_to(t, shape)).ravel()
+    Tb = np.ascontiguousarray(np.broadcast_to(T, shape)).ravel()
+    f = np.empty_like(tb)
+    d = np.empty_like(tb)
+    _load().orc_wavelet(int(kind), _ptr(tb), _ptr(Tb), tb.size, _ptr(f), _ptr(d))
+    return f.reshape(shape), d.reshape(shape)
+
+
 def ricker(t, T):
     """Ricker wavelet f(t; T) and its T-derivative, elementwise (float64)."""
     t = np.asarray(t, np.float64)
@@ -110,9 +126,11 @@ def ricker(t, T):
 
 
 def forward(Avs, Asv, g, C, dt, V0, S0, nsteps, T=None, ftab=None, n0=0, r=0,
-            threads=0):
+            threads=0, wavelet=0):
     """Leapfrog forward run.  Returns (V, S, traces) as float64 arrays;
-    traces is (nsteps // r, R, M) or None when r == 0 or C has no rows."""
+    traces is (nsteps // r, R, M) or None when r == 0 or C has no rows.
+    `wavelet` selects the source signal of the periods T (0 Ricker, 1 first
+    derivative of a Gaussian)."""
     Avs = _cm(Avs)
     Asv = _cm(Asv)
     Kv, Ks = Avs.shape
@@ -133,13 +151,13 @@ def forward(Avs, Asv, g, C, dt, V0, S0, nsteps, T=None, ftab=None, n0=0, r=0,
     rc = _load().orc_forward(_ptr(Avs), _ptr(Asv), _ptr(g), _ptr(Cm) if R > 0 else None,
                              Kv, Ks, R, float(dt), _ptr(V), _ptr(S), _ptr(Tc), _ptr(Fc),
                              M, int(nsteps), int(n0), int(r) if nrec > 0 else 0,
-                             _ptr(tr), int(threads))
+                             _ptr(tr), int(threads), int(wavelet))
     _check(rc, "forward")
     traces = None if tr is None else np.ascontiguousarray(tr.transpose(0, 2, 1))
     return np.ascontiguousarray(V), np.ascontiguousarray(S), traces
 
 
-def inverse(Avs, Asv, g, dt, V, S, nsteps, T=None, ftab=None, n0=0, threads=0):
+def inverse(Avs, Asv, g, dt, V, S, nsteps, T=None, ftab=None, n0=0, threads=0, wavelet=0):
     """Undo ``nsteps`` leapfrog steps (time reversal).  Returns (V0, S0)."""
     Avs = _cm(Avs)
     Asv = _cm(Asv)
@@ -152,7 +170,7 @@ def inverse(Avs, Asv, g, dt, V, S, nsteps, T=None, ftab=None, n0=0, threads=0):
     Fc = None if ftab is None else np.ascontiguousarray(np.asarray(ftab, np.float64))
     rc = _load().orc_inverse(_ptr(Avs), _ptr(Asv), _ptr(g), Kv, Ks, float(dt), _ptr(V),
                              _ptr(S), _ptr(Tc), _ptr(Fc), M, int(nsteps), int(n0),
-                             int(threads))
+                             int(threads), int(wavelet))
     _check(rc, "inverse")
     return np.ascontiguousarray(V), np.ascontiguousarray(S)
 
@@ -180,7 +198,7 @@ def spectral_radius(Avs, Asv, max_iter=5000, tol=1e-13):
     return float(out.value), int(it)
 
 
-def adjoint(Avs, Asv, g, C, dt, V0, S0, T, nsteps, ystar, n0=0, threads=0):
+def adjoint(Avs, Asv, g, C, dt, V0, S0, T, nsteps, ystar, n0=0, threads=0, wavelet=0):
     """Loss and gradients of sum_n sum_m ||C V_m^n - ystar_m^n||^2.
     ystar is (nsteps, R, M).  Returns (loss, gV0, gS0, gT)."""
     Avs = _cm(Avs)
@@ -202,13 +220,13 @@ def adjoint(Avs, Asv, g, C, dt, V0, S0, T, nsteps, ystar, n0=0, threads=0):
     rc = _load().orc_adjoint(_ptr(Avs), _ptr(Asv), _ptr(g), _ptr(Cm), Kv, Ks, R,
                              float(dt), _ptr(V0), _ptr(S0), _ptr(Tc), M, int(nsteps),
                              int(n0), _ptr(ys), _ptr(gV), _ptr(gS), _ptr(gT),
-                             ctypes.byref(loss), int(threads))
+                             ctypes.byref(loss), int(threads), int(wavelet))
     _check(rc, "adjoint")
     return float(loss.value), np.ascontiguousarray(gV), np.ascontiguousarray(gS), gT
 
 
 def problem_forward(p, V0=None, S0=None, nsteps=None, r=None, n0=0, T=None,
-                    threads=0, columns=None):
+                    threads=0, columns=None, wavelet=0):
     """Convenience: run a ``RomProblem``-like object (fields Avs, Asv, g, C, dt, T).
     ``columns`` restricts the run to a subset of realizations (columns are
     independent, so a subset gives exactly those columns of the full run)."""
@@ -229,7 +247,7 @@ def problem_forward(p, V0=None, S0=None, nsteps=None, r=None, n0=0, T=None,
     steps = p.meta.get("steps") if nsteps is None else nsteps
     rr = p.meta.get("r", 0) if r is None else r
     return forward(p.Avs, p.Asv, p.g, p.C if p.C.shape[0] > 0 else None, p.dt, V0, S0,
-                   steps, T=Tm, n0=n0, r=rr, threads=threads)
+                   steps, T=Tm, n0=n0, r=rr, threads=threads, wavelet=wavelet)
 
 
 def trace_stats(traces, probs):

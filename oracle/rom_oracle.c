@@ -23,7 +23,8 @@
  *
  *   Point-source forcing (Sec. 2.2, sparse case; Sec. 3.2 signal): the
  *   reduced forcing of realization m is g * f(t; T_m) with the Ricker wavelet
- *       f(t; T) = (1 - 2 u) exp(-u),  u = pi^2 (t - t0)^2 / T^2,  t0 = 1.5 T.
+ *       f(t; T) = (1 - 2 u) exp(-u),  u = pi^2 (t - t0)^2 / T^2,  t0 = 1.5 T,
+ *   or (wavelet = 1) the first derivative of a Gaussian defined below.
  *
  *   Receiver traces (seismograms from basis rows, Sec. 4.5.2):
  *       y = C V^{n+1}  after every step with (n + 1) mod r == 0.
@@ -80,6 +81,41 @@ static double ricker_dT(double t, double T) {
     return dfdu * dudT;
 }
 
+/* First derivative of a Gaussian, the paper's second source signal
+ * (Sec. 3.2), read as the tau-derivative of the Ricker's Gaussian envelope
+ * exp(-pi^2 tau^2 / T^2), delay t0 = 1.5 T, scaled to unit peak magnitude:
+ *   f = -sqrt(2e) a exp(-a^2),   a = pi tau / T,   tau = t - 1.5 T
+ * (extrema -1 at tau = +T / (pi sqrt 2) and +1 at tau = -T / (pi sqrt 2)). */
+#define ORC_SQRT2E 2.33164398159712420
+static double gauss1(double t, double T) {
+    double a = ORC_PI * (t - 1.5 * T) / T;
+    return -ORC_SQRT2E * a * exp(-a * a);
+}
+
+/* d f / d T at fixed t: df/da = -sqrt(2e) (1 - 2a^2) e^{-a^2},
+ * da/dT = -pi t / T^2 (a = pi t / T - 1.5 pi). */
+static double gauss1_dT(double t, double T) {
+    double a = ORC_PI * (t - 1.5 * T) / T;
+    double dfda = -ORC_SQRT2E * (1.0 - 2.0 * a * a) * exp(-a * a);
+    double dadT = -ORC_PI * t / (T * T);
+    return dfda * dadT;
+}
+
+/* Source signal of kind `wavelet`: 0 Ricker, 1 first derivative of a Gaussian. */
+static double wavelet_f(int wavelet, double t, double T) {
+    return wavelet == 1 ? gauss1(t, T) : ricker(t, T);
+}
+static double wavelet_dT(int wavelet, double t, double T) {
+    return wavelet == 1 ? gauss1_dT(t, T) : ricker_dT(t, T);
+}
+
+void orc_wavelet(int wavelet, const double* t, const double* T, int n, double* f, double* dfdT) {
+    for (int i = 0; i < n; ++i) {
+        if (f) f[i] = wavelet_f(wavelet, t[i], T[i]);
+        if (dfdT) dfdT[i] = wavelet_dT(wavelet, t[i], T[i]);
+    }
+}
+
 void orc_ricker(const double* t, const double* T, int n, double* f, double* dfdT) {
     for (int i = 0; i < n; ++i) {
         if (f) f[i] = ricker(t[i], T[i]);
@@ -109,9 +145,9 @@ static void matvec_t(const double* A, int rows, int cols, const double* x, doubl
 }
 
 static double forcing_value(const double* T, const double* ftab, int M, int m,
-                            int n, long n0, double dt) {
+                            int n, long n0, double dt, int wavelet) {
     if (ftab) return ftab[(size_t)n * M + m];
-    return ricker((double)(n0 + n) * dt, T[m]);
+    return wavelet_f(wavelet, (double)(n0 + n) * dt, T[m]);
 }
 
 /*
@@ -124,7 +160,7 @@ static double forcing_value(const double* T, const double* ftab, int M, int m,
 int orc_forward(const double* Avs, const double* Asv, const double* g, const double* C,
                 int Kv, int Ks, int R, double dt,
                 double* V, double* S, const double* T, const double* ftab, int M,
-                int nsteps, long n0, int r, double* traces, int nthreads) {
+                int nsteps, long n0, int r, double* traces, int nthreads, int wavelet) {
     if (Kv <= 0 || Ks <= 0 || M < 0 || nsteps < 0 || R < 0) return -1;
     if (traces && (r <= 0 || R <= 0 || !C)) return -1;
     orc_set_threads(nthreads);
@@ -143,7 +179,7 @@ int orc_forward(const double* Avs, const double* Asv, const double* g, const dou
                 double* v = V + (size_t)m * Kv;
                 double* s = S + (size_t)m * Ks;
                 for (int n = 0; n < nsteps; ++n) {
-                    const double f = (T || ftab) ? forcing_value(T, ftab, M, m, n, n0, dt) : 0.0;
+                    const double f = (T || ftab) ? forcing_value(T, ftab, M, m, n, n0, dt, wavelet) : 0.0;
                     /* velocity first: v <- v + dt (Avs s + g f) */
                     matvec(Avs, Kv, Ks, s, tv);
                     for (int i = 0; i < Kv; ++i) v[i] = v[i] + dt * (tv[i] + g[i] * f);
@@ -174,7 +210,7 @@ int orc_forward(const double* Avs, const double* Asv, const double* g, const dou
 int orc_inverse(const double* Avs, const double* Asv, const double* g,
                 int Kv, int Ks, double dt, double* V, double* S,
                 const double* T, const double* ftab, int M, int nsteps, long n0,
-                int nthreads) {
+                int nthreads, int wavelet) {
     if (Kv <= 0 || Ks <= 0 || M < 0 || nsteps < 0) return -1;
     orc_set_threads(nthreads);
     int err = 0;
@@ -191,7 +227,7 @@ int orc_inverse(const double* Avs, const double* Asv, const double* g,
                 double* v = V + (size_t)m * Kv;
                 double* s = S + (size_t)m * Ks;
                 for (int n = nsteps - 1; n >= 0; --n) {
-                    const double f = (T || ftab) ? forcing_value(T, ftab, M, m, n, n0, dt) : 0.0;
+                    const double f = (T || ftab) ? forcing_value(T, ftab, M, m, n, n0, dt, wavelet) : 0.0;
                     matvec(Asv, Ks, Kv, v, ts);
                     for (int i = 0; i < Ks; ++i) s[i] = s[i] - dt * ts[i];
                     matvec(Avs, Kv, Ks, s, tv);
@@ -294,7 +330,8 @@ int orc_adjoint(const double* Avs, const double* Asv, const double* g, const dou
                 int Kv, int Ks, int R, double dt,
                 const double* V0, const double* S0, const double* T, int M,
                 int nsteps, long n0, const double* ystar,
-                double* gV0, double* gS0, double* gT, double* loss, int nthreads) {
+                double* gV0, double* gS0, double* gT, double* loss, int nthreads,
+                int wavelet) {
     if (Kv <= 0 || Ks <= 0 || R <= 0 || M < 0 || nsteps < 0 || !C || !ystar || !T) return -1;
     orc_set_threads(nthreads);
     int err = 0;
@@ -322,7 +359,7 @@ int orc_adjoint(const double* Avs, const double* Asv, const double* g, const dou
                 memcpy(s, S0 + (size_t)m * Ks, sizeof(double) * (size_t)Ks);
                 double lm = 0.0;
                 for (int n = 0; n < nsteps; ++n) {
-                    const double f = ricker((double)(n0 + n) * dt, T[m]);
+                    const double f = wavelet_f(wavelet, (double)(n0 + n) * dt, T[m]);
                     matvec(Avs, Kv, Ks, s, tv);
                     for (int i = 0; i < Kv; ++i) v[i] = v[i] + dt * (tv[i] + g[i] * f);
                     matvec(Asv, Ks, Kv, v, ts);
@@ -351,7 +388,7 @@ int orc_adjoint(const double* Avs, const double* Asv, const double* g, const dou
                     for (int i = 0; i < Kv; ++i) av[i] = lv[i] + dt * tv[i];
                     double gav = 0.0;
                     for (int i = 0; i < Kv; ++i) gav += g[i] * av[i];
-                    gt += dt * gav * ricker_dT((double)(n0 + n) * dt, T[m]);
+                    gt += dt * gav * wavelet_dT(wavelet, (double)(n0 + n) * dt, T[m]);
                     /* lamS = aS + dt Avs^T aV */
                     matvec_t(Avs, Kv, Ks, av, ts);
                     for (int i = 0; i < Ks; ++i) ls[i] = ls[i] + dt * ts[i];
