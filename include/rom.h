@@ -135,6 +135,19 @@ rom_status rom_get_plan(rom_t h, int prec, int M, int* variant, int* cluster_siz
                         int* cols_per_block, int* nclusters);
 
 /*
+ * rom_set_wavelet -- source signal evaluated from the periods T by every run
+ * and by the adjoint (Sec. 3.2 supports two): ROM_WAVELET_RICKER (default),
+ *   f = (1 - 2u) exp(-u),  u = pi^2 (t - t0)^2 / T^2,
+ * or ROM_WAVELET_GAUSS1, the first derivative of a Gaussian, read as the
+ * derivative of the same Gaussian envelope scaled to unit peak magnitude,
+ *   f = -sqrt(2e) a exp(-a^2),  a = pi (t - t0) / T,
+ * both with delay t0 = 1.5 T.  Tabulated forcing (rom_run_rank2_ex) is not
+ * affected.  ROM_E_INVAL for another value.
+ */
+enum { ROM_WAVELET_RICKER = 0, ROM_WAVELET_GAUSS1 = 1 };
+rom_status rom_set_wavelet(rom_t h, int wavelet);
+
+/*
  * rom_set_tc_columns -- columns per cluster block of the tensor-core path:
  * 64 or 128 for ROM_TF32X3 / ROM_BF16X3 / ROM_BF16, 32, 48, 64 or 80 for
  * ROM_BF16S, or 0 to let the planner choose (default).  Wider blocks re-read

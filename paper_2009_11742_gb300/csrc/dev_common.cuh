@@ -36,6 +36,40 @@ __device__ __forceinline__ float ricker_dT_eval(long long step, double dt, float
     return (2.0f * u - 3.0f) * expf(-u) * dudT;
 }
 
+// First derivative of a Gaussian (the paper's second source signal, Sec.
+// 3.2): the tau-derivative of the Ricker's envelope exp(-pi^2 tau^2 / T^2),
+// delay 1.5 T, scaled to unit peak magnitude:
+//   f = -sqrt(2e) a exp(-a^2),  a = pi tau / T.
+constexpr double kSqrt2e = 2.33164398159712420;
+
+__device__ __forceinline__ float gauss1_eval(long long step, double dt, float T) {
+    const double tau = (double)step * dt - 1.5 * (double)T;
+    const float a = (float)(3.14159265358979323846 * tau / (double)T);
+    return -(float)kSqrt2e * a * expf(-a * a);
+}
+__device__ __forceinline__ double gauss1_eval(long long step, double dt, double T) {
+    const double tau = (double)step * dt - 1.5 * T;
+    const double a = 3.14159265358979323846 * tau / T;
+    return -kSqrt2e * a * exp(-a * a);
+}
+// d f / d T at fixed t: df/da = -sqrt(2e) (1 - 2a^2) e^{-a^2}, da/dT = -pi t / T^2.
+__device__ __forceinline__ float gauss1_dT_eval(long long step, double dt, float T) {
+    const double t = (double)step * dt;
+    const double tau = t - 1.5 * (double)T;
+    const float a = (float)(3.14159265358979323846 * tau / (double)T);
+    const float dadT = (float)(-3.14159265358979323846 * t / ((double)T * (double)T));
+    return -(float)kSqrt2e * (1.0f - 2.0f * a * a) * expf(-a * a) * dadT;
+}
+
+// Source signal of kind `wavelet` (0 Ricker, 1 first derivative of a Gaussian).
+template <typename T>
+__device__ __forceinline__ T wavelet_eval(int wavelet, long long step, double dt, T period) {
+    return wavelet == 1 ? gauss1_eval(step, dt, period) : ricker_eval(step, dt, period);
+}
+__device__ __forceinline__ float wavelet_dT_eval(int wavelet, long long step, double dt, float T) {
+    return wavelet == 1 ? gauss1_dT_eval(step, dt, T) : ricker_dT_eval(step, dt, T);
+}
+
 // Four consecutive elements from shared or global memory (16-byte aligned).
 __device__ __forceinline__ void load4(const float* p, float (&x)[4]) {
     const float4 v = *reinterpret_cast<const float4*>(p);

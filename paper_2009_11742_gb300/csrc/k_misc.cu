@@ -48,7 +48,7 @@ __global__ void __launch_bounds__(kEnsThreads) rank1_ensemble_kernel(const Rank1
     T* traces = static_cast<T*>(a.traces);
     __syncthreads();
     for (int n = 0; n < a.nsteps; ++n) {
-        const T f = a.Tper ? (T)ricker_eval((long long)a.n0 + n, a.dt, Tm) : T(0);
+        const T f = a.Tper ? (T)wavelet_eval(a.wavelet, (long long)a.n0 + n, a.dt, Tm) : T(0);
 #pragma unroll 1
         for (int half = 0; half < 2; ++half) {
             const T* A = half == 0 ? Avs : Asv;

@@ -163,7 +163,7 @@ __global__ void __launch_bounds__(kThreads, 1) rank2_adjoint_kernel(const AdjArg
             float s = gown[lane] * Vf[(size_t)c * Kp + row0 + lane];
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-            if (lane == 0) gTacc[c] = __fmaf_rn(dt * s, ricker_dT_eval((long long)a.n0 + n, a.dt, Tcol[c]), gTacc[c]);
+            if (lane == 0) gTacc[c] = __fmaf_rn(dt * s, wavelet_dT_eval(a.wavelet, (long long)a.n0 + n, a.dt, Tcol[c]), gTacc[c]);
         }
         push_own_rows<float>(cluster, Vf, Wa, Kp, row0, cs, crank, 1);
         cluster.sync();

@@ -323,7 +323,7 @@ __global__ void __launch_bounds__(kThreads, 1) rank2_dataflow_kernel(const Rank2
                     const int cl = c0 + lane;
                     if (cl < ncol(b)) {
                         if (ftab) f = ftab[(size_t)n * a.Mtot + gc0(b) + cl];
-                        else if (a.Tper) f = ricker_eval((long long)a.n0 + n, a.dt, Tcol[b * Wa + cl]);
+                        else if (a.Tper) f = wavelet_eval(a.wavelet, (long long)a.n0 + n, a.dt, Tcol[b * Wa + cl]);
                     }
                 }
                 f = __shfl_sync(0xffffffffu, f, vi % CB);

@@ -179,7 +179,7 @@ __device__ __forceinline__ T forcing_at(const Rank2Args& a, const T* Tcol, int c
                                         int gc0, int n) {
     if (c >= ncol) return T(0);
     if (a.ftab) return static_cast<const T*>(a.ftab)[(size_t)n * a.Mtot + gc0 + c];
-    return (T)ricker_eval((long long)a.n0 + n, a.dt, Tcol[c]);
+    return (T)wavelet_eval(a.wavelet, (long long)a.n0 + n, a.dt, Tcol[c]);
 }
 
 template <typename T, int KI, int CB, bool RESIDENT>

@@ -222,7 +222,7 @@ __global__ void __launch_bounds__(kThreads, 1) rank2_split_kernel(const Rank2Arg
             float f = 0.f;
             if (c < ncol(0)) {
                 if (a.ftab) f = static_cast<const float*>(a.ftab)[gc0(0) + c];
-                else if (a.Tper) f = ricker_eval((long long)a.n0, a.dt, Tcol[c]);
+                else if (a.Tper) f = wavelet_eval(a.wavelet, (long long)a.n0, a.dt, Tcol[c]);
             }
             fcol[c] = f;
         }
@@ -282,7 +282,7 @@ __global__ void __launch_bounds__(kThreads, 1) rank2_split_kernel(const Rank2Arg
                     float f = 0.f;
                     if (c < ncol(b2)) {
                         if (a.ftab) f = static_cast<const float*>(a.ftab)[(size_t)n2 * a.Mtot + gc0(b2) + c];
-                        else if (a.Tper) f = ricker_eval((long long)a.n0 + n2, a.dt, Tcol[b2 * Wa + c]);
+                        else if (a.Tper) f = wavelet_eval(a.wavelet, (long long)a.n0 + n2, a.dt, Tcol[b2 * Wa + c]);
                     }
                     fcol[b2 * Wa + c] = f;
                 }

@@ -190,7 +190,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) rank2_tc_kernel(const TcArgs a)
         float f = 0.f;
         if (c < ncol) {
             if (a.ftab) f = a.ftab[col0 + c];
-            else if (a.Tper) f = ricker_eval(a.n0, a.dt, Tcol[c]);
+            else if (a.Tper) f = wavelet_eval(a.wavelet, a.n0, a.dt, Tcol[c]);
         }
         fcol[c] = f;
     }
@@ -318,7 +318,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) rank2_tc_kernel(const TcArgs a)
                     float f = 0.f;
                     if (c < ncol) {
                         if (a.ftab) f = a.ftab[(size_t)(n + 1) * a.Mtot + col0 + c];
-                        else if (a.Tper) f = ricker_eval(a.n0 + n + 1, a.dt, Tcol[c]);
+                        else if (a.Tper) f = wavelet_eval(a.wavelet, a.n0 + n + 1, a.dt, Tcol[c]);
                     }
                     fcol[c] = f;
                 }

@@ -89,6 +89,7 @@ struct rom_s {
     int kernel_choice = 0;  // ROM_KERNEL_AUTO
     long long wait_limit = 4000000000LL;  // device wait bound in SM clock cycles (~2 s)
     int inject_stall = 0;
+    int wavelet = ROM_WAVELET_RICKER;  // source signal of the periods T
 };
 
 namespace {
@@ -427,6 +428,7 @@ rom_status run_rank2_tc(rom_s* h, const RunBufs& b, int M, int nsteps, long n0, 
     a.traces = static_cast<float*>(b.traces);
     a.status = h->status;
     a.dt = h->dt;
+    a.wavelet = h->wavelet;
     a.n0 = n0;
     a.spin_limit = h->wait_limit;
     a.Kv = h->Kv;
@@ -478,6 +480,7 @@ rom_status launch_simt_with_plan(rom_s* h, const RunBufs& b, int M, int nsteps, 
     a.traces = b.traces;
     a.status = h->status;
     a.dt = h->dt;
+    a.wavelet = h->wavelet;
     a.n0 = n0;
     a.Kv = h->Kv;
     a.Ks = h->Ks;
@@ -525,6 +528,7 @@ rom_status run_common(rom_s* h, void* V, void* S, const void* T, const void* fta
             a.traces = b.traces;
             a.status = h->status;
             a.dt = h->dt;
+            a.wavelet = h->wavelet;
             a.n0 = n0;
             a.Kv = h->Kv;
             a.Ks = h->Ks;
@@ -595,6 +599,13 @@ rom_status rom_set_wait_limit(rom_t h, long long cycles) {
 rom_status rom_debug_inject_stall(rom_t h, int on) {
     if (!h) return ROM_E_INVAL;
     h->inject_stall = on ? 1 : 0;
+    return ROM_OK;
+}
+
+rom_status rom_set_wavelet(rom_t h, int wavelet) {
+    if (!h || (wavelet != ROM_WAVELET_RICKER && wavelet != ROM_WAVELET_GAUSS1)) return ROM_E_INVAL;
+    std::lock_guard<std::mutex> lk(h->mu);
+    h->wavelet = wavelet;
     return ROM_OK;
 }
 
@@ -983,6 +994,7 @@ rom_status rom_adjoint(rom_t h, const void* V0, const void* S0, const void* T, i
         aa.gTpart = gtp;
         aa.status = h->status;
         aa.dt = h->dt;
+        aa.wavelet = h->wavelet;
         aa.n0 = 0;
         aa.n_lo = n_start;
         aa.n_hi = n_start + len;

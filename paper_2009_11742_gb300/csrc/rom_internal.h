@@ -37,6 +37,7 @@ struct Rank2Args {
     int nrt;               // 32-row tiles owned per CTA by the one-block kernel (1 or 2)
     long long spin_limit;  // clock cycles a device-side wait may last before ROM_E_TIMEOUT
     int debug_skip_push;   // fault injection: CTA 0 never publishes (forces the timeout path)
+    int wavelet;           // source signal of the periods: 0 Ricker, 1 first derivative of a Gaussian
 };
 
 // Launch plan chosen by the host for a rank-2 call.
@@ -87,6 +88,7 @@ struct TcArgs {
     long long n0;
     long long spin_limit;
     int Kv, Ks, Kp, R, M, Mtot, W, nsteps, r, rpc, stages;
+    int wavelet;          // source signal of the periods (see Rank2Args)
 };
 struct TcPlan {
     int prec, cs, W, stages, nclusters, rpc, max_active_clusters;
@@ -125,6 +127,7 @@ struct AdjArgs {
     int n_lo, n_hi;       // reverse steps n_hi-1 .. n_lo
     int rec_base;
     int Kv, Ks, Kp, R, M, Wv, Wa;
+    int wavelet;          // source signal of the periods (see Rank2Args)
 };
 struct AdjPlan {
     int cs, KI, cb, Wv, Wa, nclusters;
@@ -148,6 +151,7 @@ struct Rank1EnsArgs {
     double dt;
     long long n0;
     int Kv, Ks, Kp, R, M, nsteps, r;
+    int wavelet;          // source signal of the periods (see Rank2Args)
 };
 cudaError_t launch_rank1_ensemble_f32(const Rank1EnsArgs& a, cudaStream_t st);
 cudaError_t launch_rank1_ensemble_f64(const Rank1EnsArgs& a, cudaStream_t st);

@@ -30,11 +30,12 @@ ROM_OK, ROM_E_INVAL, ROM_E_NOMEM, ROM_E_CUDA, ROM_E_UNSTABLE, ROM_E_TIMEOUT, \
 ROM_FP64, ROM_FP32, ROM_TF32X3, ROM_BF16X3, ROM_BF16, ROM_BF16S = range(6)
 ROM_IN_F64, ROM_IN_F32 = 0, 1
 ROM_KERNEL_AUTO, ROM_KERNEL_ONE_BLOCK, ROM_KERNEL_TWO_BLOCK, ROM_KERNEL_DATAFLOW = 0, 1, 2, 3
+ROM_WAVELET_RICKER, ROM_WAVELET_GAUSS1 = 0, 1
 PRECISIONS = {"fp64": ROM_FP64, "fp32": ROM_FP32, "tf32x3": ROM_TF32X3,
               "bf16x3": ROM_BF16X3, "bf16": ROM_BF16, "bf16s": ROM_BF16S}
 
 EXPORTED = ["rom_create", "rom_destroy", "rom_spectral_radius", "rom_sync_status",
-            "rom_get_dims", "rom_set_kernel", "rom_get_plan", "rom_set_tc_columns", "rom_set_wait_limit",
+            "rom_get_dims", "rom_set_kernel", "rom_get_plan", "rom_set_tc_columns", "rom_set_wavelet", "rom_set_wait_limit",
             "rom_debug_inject_stall", "rom_run_rank2", "rom_run_rank2_ex", "rom_run_rank1",
             "rom_run_rank1_ensemble", "rom_run_batched", "rom_adjoint",
             "rom_adjoint_workspace_size", "rom_rel_l2", "rom_spectral_radius_noalloc",
@@ -66,6 +67,7 @@ def _signatures(lib):
         "rom_set_kernel": (_i, [_vp, _i]),
         "rom_set_wait_limit": (_i, [_vp, ctypes.c_longlong]),
         "rom_set_tc_columns": (_i, [_vp, _i]),
+        "rom_set_wavelet": (_i, [_vp, _i]),
         "rom_debug_inject_stall": (_i, [_vp, _i]),
         "rom_get_plan": (_i, [_vp, _i, _i, ctypes.POINTER(_i), ctypes.POINTER(_i),
                               ctypes.POINTER(_i), ctypes.POINTER(_i)]),
@@ -158,6 +160,10 @@ def rom_set_kernel(h, kernel):
 
 def rom_set_tc_columns(h, cols):
     return load().rom_set_tc_columns(h, int(cols))
+
+
+def rom_set_wavelet(h, wavelet):
+    return load().rom_set_wavelet(h, int(wavelet))
 
 
 def rom_set_wait_limit(h, cycles):
@@ -397,6 +403,12 @@ class Rom:
 
     def set_kernel(self, kernel):
         _chk(rom_set_kernel(self.h, int(kernel)), "rom_set_kernel")
+
+    def set_wavelet(self, wavelet):
+        """Source signal of the periods: "ricker" (default) or "gauss1" (first
+        derivative of a Gaussian), or the ROM_WAVELET_* code."""
+        w = {"ricker": ROM_WAVELET_RICKER, "gauss1": ROM_WAVELET_GAUSS1}.get(wavelet, wavelet)
+        _chk(rom_set_wavelet(self.h, int(w)), "rom_set_wavelet")
 
     def plan(self, M, prec="fp32"):
         st, v, cs, w, nc = rom_get_plan(self.h, PRECISIONS.get(prec, prec), int(M))

@@ -61,12 +61,13 @@ def test_adjoint_vs_oracle(rom, Kv, Ks, M, R, N, ckpt):
 
 def test_checkpointed_equals_stored_traces_bitwise(rom):
     """Recomputed segments reproduce the forward sweep bit for bit, so the
-    gradients do not depend on the checkpoint interval."""
+    gradients do not depend on the checkpoint interval.  The FP64 misfit is
+    summed per segment with atomic adds, so only its last bits may differ."""
     p, V0, S0, ystar = case(128, 128, 16, 4, 90, seed=5)
     h = rom.Rom.from_problem(p)
     a = gpu_adjoint(rom, h, p, V0, S0, ystar, 90, 0)
     b = gpu_adjoint(rom, h, p, V0, S0, ystar, 90, 20)
-    assert a[0] == b[0]
+    assert abs(a[0] - b[0]) <= 1e-13 * abs(a[0])
     for x, y in zip(a[1:], b[1:]):
         np.testing.assert_array_equal(x, y)
 
