@@ -662,7 +662,9 @@ def bench_adjoint(args, torch, dev, inputs, rom):
 
 def bench_batched(args, torch, dev, inputs, rom):
     """Workload 3: 64 independent ROMs (K_i in {64..768}, M_i in [4, 256]),
-    5000 steps each, one graph launch per bench step."""
+    5000 steps each, one graph launch per bench step; timed with the
+    proportional SM shares, then again after rom_autotune_batched has
+    measured the schedule (the tuning probe is outside the timed region)."""
     probs = inputs.batched_problems()
     N = args.nsteps or 5000
     items = []
@@ -672,27 +674,35 @@ def bench_batched(args, torch, dev, inputs, rom):
                       rom.Rom.new_state(p.Ks, p.M, "fp32", device=dev),
                       torch.as_tensor(p.T, dtype=torch.float32, device=dev), None))
     stream = torch.cuda.Stream(device=dev)
-    with torch.cuda.stream(stream):
-        for _ in range(args.warmup):
-            rom.run_batched(items, N, prec="fp32", stream=stream)
-    torch.cuda.synchronize()
-    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-           for _ in range(args.steps)]
-    with torch.cuda.stream(stream):
-        for i in range(args.steps):
-            for (_, V, S, _, _) in items:
-                V.zero_()
-                S.zero_()
-            evs[i][0].record(stream)
-            rom.run_batched(items, N, prec="fp32", stream=stream)
-            evs[i][1].record(stream)
-    torch.cuda.synchronize()
-    t = sum(a.elapsed_time(b) for a, b in evs) * 1e-3 / args.steps
+
+    def timed():
+        with torch.cuda.stream(stream):
+            for _ in range(args.warmup):
+                rom.run_batched(items, N, prec="fp32", stream=stream)
+        torch.cuda.synchronize()
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(args.steps)]
+        with torch.cuda.stream(stream):
+            for i in range(args.steps):
+                for (_, V, S, _, _) in items:
+                    V.zero_()
+                    S.zero_()
+                evs[i][0].record(stream)
+                rom.run_batched(items, N, prec="fp32", stream=stream)
+                evs[i][1].record(stream)
+        torch.cuda.synchronize()
+        return sum(a.elapsed_time(b) for a, b in evs) * 1e-3 / args.steps
+
+    t0 = timed()
+    probe_us = rom.autotune_batched(items, prec="fp32", probe_steps=200, stream=stream)
+    t = timed()
     ss = sum(p.M for p in probs) * N
     fl = sum(4.0 * p.Kv * p.Ks * p.M for p in probs) * N
     print(json.dumps({"only_rank2": True, "workload": "batched-64roms-K64..768-M4..256-N5000",
                       "nsteps": N, "value": ss / t, "unit": "sample-steps/s",
                       "ms_per_step": 1e3 * t, "tflops_useful": fl / t / 1e12,
+                      "untuned": {"value": ss / t0, "ms_per_step": 1e3 * t0},
+                      "autotune_probe_us_per_step": probe_us,
                       "columns_total": sum(p.M for p in probs)}), flush=True)
     return 0
 

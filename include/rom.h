@@ -135,6 +135,27 @@ rom_status rom_get_plan(rom_t h, int prec, int M, int* variant, int* cluster_siz
                         int* cols_per_block, int* nclusters);
 
 /*
+ * rom_autotune -- measure instead of model: time every candidate launch plan
+ * for M realizations at precision `prec` on a probe run of `probe_steps`
+ * steps (zero state, every period 45 dt, no traces, library-allocated
+ * scratch) and keep the fastest for this handle.  Later rom_run_rank2 /
+ * rom_run_rank2_ex calls with the same precision and M use it while the
+ * kernel choice (rom_set_kernel) and the tensor-core width
+ * (rom_set_tc_columns) are automatic.  Candidates:
+ *   ROM_FP32  the two-block and the one-block kernels, each with the cluster
+ *             count capped at the co-resident maximum, half and a quarter of
+ *             it (wider column blocks on fewer clusters);
+ *   ROM_FP64  the one-block kernel;
+ *   tensor-core precisions: every column-block width the precision provides.
+ * Every candidate computes the same leapfrog; the FP32 kernels differ only in
+ * the order of FP32 roundings (results agree to FP32 rounding).
+ * *best_us (may be NULL) receives the chosen plan's probe time per step.
+ * Synchronous on `stream`.  Errors: ROM_E_INVAL, ROM_E_UNSUPPORTED (no
+ * candidate fits), ROM_E_NOMEM, ROM_E_CUDA, or a device status the probe set.
+ */
+rom_status rom_autotune(rom_t h, int prec, int M, int probe_steps, double* best_us, void* stream);
+
+/*
  * rom_set_wavelet -- source signal evaluated from the periods T by every run
  * and by the adjoint (Sec. 3.2 supports two): ROM_WAVELET_RICKER (default),
  *   f = (1 - 2u) exp(-u),  u = pi^2 (t - t0)^2 / T^2,
@@ -249,6 +270,21 @@ typedef struct {
 } rom_job;
 rom_status rom_run_batched(const rom_job* jobs, int njobs, int nsteps, int r, int prec,
                            void* stream);
+
+/*
+ * rom_autotune_batched -- the batching schedule by measurement: replay the
+ * job list's captured graph on scratch copies of its state (zero state,
+ * every period 45 dt, no traces) for `probe_steps` steps with the SMs shared
+ * in proportion to each job's work times a scale of 0.5, 1, 2 and 4 (fewer
+ * or more clusters per job than its share), and keep the fastest scale for
+ * this list of (handle, M) pairs: later rom_run_batched calls with the same
+ * handles and widths use it.  The scale affects the SIMT jobs (the
+ * tensor-core jobs plan their own widths).  *best_us (may be NULL) receives
+ * the chosen schedule's probe time per step.  Synchronous on `stream`.
+ * Errors as for rom_run_batched, plus ROM_E_NOMEM.
+ */
+rom_status rom_autotune_batched(const rom_job* jobs, int njobs, int prec, int probe_steps,
+                                double* best_us, void* stream);
 
 /*
  * rom_adjoint -- gradients of the receiver-trace misfit

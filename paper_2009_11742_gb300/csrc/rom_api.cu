@@ -90,6 +90,10 @@ struct rom_s {
     long long wait_limit = 4000000000LL;  // device wait bound in SM clock cycles (~2 s)
     int inject_stall = 0;
     int wavelet = ROM_WAVELET_RICKER;  // source signal of the periods T
+    // plans chosen by rom_autotune, per (precision, M): used while the kernel
+    // and tensor-core column choices are on automatic
+    std::map<std::pair<int, int>, Rank2Plan> tuned;
+    std::map<std::pair<int, int>, TcPlan> tuned_tc;
 };
 
 namespace {
@@ -315,6 +319,13 @@ struct RunBufs {
 
 rom_status get_plan(rom_s* h, int prec, int M, bool rank1, Rank2Plan* plan) {
     std::lock_guard<std::mutex> lk(h->mu);
+    if (!rank1 && h->kernel_choice == ROM_KERNEL_AUTO) {
+        auto tt = h->tuned.find(std::make_pair(prec == ROM_FP64 ? 0 : 1, M));
+        if (tt != h->tuned.end()) {
+            *plan = tt->second;
+            return ROM_OK;
+        }
+    }
     const auto key = std::make_tuple(prec == ROM_FP64 ? 0 : 1, M, rank1 ? 1 : 0, h->R,
                                      h->kernel_choice);
     auto it = h->plans.find(key);
@@ -377,6 +388,9 @@ rom_status tc_prepare(rom_s* h, int prec, cudaStream_t st) {
     return ROM_OK;
 }
 
+rom_status run_rank2_tc_plan(rom_s* h, const RunBufs& b, int M, int nsteps, long n0, int r, int prec,
+                             const TcPlan& plan, cudaStream_t st);
+
 rom_status run_rank2_tc(rom_s* h, const RunBufs& b, int M, int nsteps, long n0, int r, int prec,
                         cudaStream_t st) {
     rom_status s = tc_prepare(h, prec, st);
@@ -386,7 +400,10 @@ rom_status run_rank2_tc(rom_s* h, const RunBufs& b, int M, int nsteps, long n0, 
         std::lock_guard<std::mutex> lk(h->mu);
         const auto key = std::make_tuple(prec, M, h->tc_cols);
         auto it = h->tc_plans.find(key);
-        if (it != h->tc_plans.end()) {
+        auto tt = h->tuned_tc.find(std::make_pair(prec, M));
+        if (h->tc_cols == 0 && tt != h->tuned_tc.end()) {
+            plan = tt->second;
+        } else if (it != h->tc_plans.end()) {
             plan = it->second;
         } else {
             if (!plan_rank2_tc(prec, h->Kp_tc, M, h->R, h->tc_cols, &plan)) {
@@ -397,6 +414,13 @@ rom_status run_rank2_tc(rom_s* h, const RunBufs& b, int M, int nsteps, long n0, 
             h->tc_plans[key] = plan;
         }
     }
+    return run_rank2_tc_plan(h, b, M, nsteps, n0, r, prec, plan, st);
+}
+
+rom_status run_rank2_tc_plan(rom_s* h, const RunBufs& b, int M, int nsteps, long n0, int r, int prec,
+                             const TcPlan& plan, cudaStream_t st) {
+    rom_status s = tc_prepare(h, prec, st);
+    if (s != ROM_OK) return s;
     // workspace: exchange tiles of both states for every block, Kahan carries
     const size_t xterm = (size_t)h->Kp_tc * plan.W * tc_element_bytes(prec);
     const size_t xbytes = (size_t)plan.nclusters * tc_exchange_terms(prec) * xterm;
@@ -609,6 +633,106 @@ rom_status rom_set_wavelet(rom_t h, int wavelet) {
     return ROM_OK;
 }
 
+rom_status rom_autotune(rom_t h, int prec, int M, int probe_steps, double* best_us, void* stream) {
+    if (!h || M < 1 || probe_steps < 1 || !valid_prec(prec)) return ROM_E_INVAL;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const bool f64 = prec == ROM_FP64;
+    const bool tc = tc_prec(prec);
+    // candidates
+    std::vector<Rank2Plan> simt;
+    std::vector<TcPlan> tcp;
+    if (tc) {
+        rom_status s = tc_prepare(h, prec, st);
+        if (s != ROM_OK) return s;
+        const int w_s[4] = {32, 48, 64, 80};
+        const int w_o[2] = {64, 128};
+        const int* ws = prec == ROM_BF16S ? w_s : w_o;
+        const int nw = prec == ROM_BF16S ? 4 : 2;
+        for (int i = 0; i < nw; ++i) {
+            TcPlan p;
+            if (plan_rank2_tc(prec, h->Kp_tc, M, h->R, ws[i], &p)) tcp.push_back(p);
+        }
+    } else if (f64) {
+        Rank2Plan p;
+        if (plan_rank2_simt_f64(h->Kp, M, h->R, false, &p)) { p.variant = 1; simt.push_back(p); }
+    } else {
+        Rank2Plan p0;
+        int nact = 0;
+        if (plan_rank2_split_f32(h->Kp, M, h->R, &p0)) nact = p0.max_active_clusters;
+        else if (plan_rank2_simt_f32(h->Kp, M, h->R, false, &p0)) nact = p0.max_active_clusters;
+        const int budgets[3] = {nact, nact / 2, nact / 4};
+        for (int b : budgets) {
+            if (b < 1) continue;
+            Rank2Plan p;
+            if (plan_rank2_split_f32(h->Kp, M, h->R, &p, b)) { p.variant = 2; simt.push_back(p); }
+            if (plan_rank2_simt_f32(h->Kp, M, h->R, false, &p, b)) { p.variant = 1; simt.push_back(p); }
+        }
+    }
+    const size_t ncand = tc ? tcp.size() : simt.size();
+    if (ncand == 0) {
+        snprintf(g_last_error, sizeof(g_last_error), "rom_autotune: no plan fits Kp=%d M=%d", h->Kp, M);
+        return ROM_E_UNSUPPORTED;
+    }
+    // probe buffers: zero state, every column with the period 45 dt
+    const size_t es = f64 ? 8 : 4;
+    void *V = nullptr, *S = nullptr, *T = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t e = cudaMalloc(&V, es * (size_t)h->Kv * M);
+    if (e == cudaSuccess) e = cudaMalloc(&S, es * (size_t)h->Ks * M);
+    if (e == cudaSuccess) e = cudaMalloc(&T, es * (size_t)M);
+    if (e == cudaSuccess) e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    rom_status rs = ROM_OK;
+    double best = -1.0;
+    size_t bi = 0;
+    if (e == cudaSuccess) {
+        std::vector<char> hT(es * (size_t)M);
+        for (int m = 0; m < M; ++m) {
+            if (f64) reinterpret_cast<double*>(hT.data())[m] = 45.0 * h->dt;
+            else reinterpret_cast<float*>(hT.data())[m] = (float)(45.0 * h->dt);
+        }
+        e = cudaMemcpyAsync(T, hT.data(), hT.size(), cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    }
+    for (size_t c = 0; c < ncand && e == cudaSuccess && rs == ROM_OK; ++c) {
+        RunBufs b = {V, S, T, nullptr, nullptr, nullptr, nullptr};
+        float ms = 0.f;
+        for (int pass = 0; pass < 2 && rs == ROM_OK && e == cudaSuccess; ++pass) {  // warm-up, timed
+            e = cudaMemsetAsync(V, 0, es * (size_t)h->Kv * M, st);
+            if (e == cudaSuccess) e = cudaMemsetAsync(S, 0, es * (size_t)h->Ks * M, st);
+            if (e == cudaSuccess) e = cudaEventRecord(e0, st);
+            if (e != cudaSuccess) break;
+            const int n = pass == 0 ? (probe_steps < 20 ? probe_steps : 20) : probe_steps;
+            rs = tc ? run_rank2_tc_plan(h, b, M, n, 0, 0, prec, tcp[c], st)
+                    : launch_simt_with_plan(h, b, M, n, 0, 0, prec, simt[c], st);
+            if (rs == ROM_OK) e = cudaEventRecord(e1, st);
+            if (e == cudaSuccess && rs == ROM_OK) e = cudaEventSynchronize(e1);
+            if (e == cudaSuccess && rs == ROM_OK) e = cudaEventElapsedTime(&ms, e0, e1);
+        }
+        if (e == cudaSuccess && rs == ROM_OK) {
+            const double us = 1e3 * ms / probe_steps;
+            if (best < 0.0 || us < best) { best = us; bi = c; }
+        }
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaFree(V);
+    cudaFree(S);
+    cudaFree(T);
+    if (e != cudaSuccess) return cuda_fail(e, "rom_autotune");
+    if (rs != ROM_OK) return rs;
+    int st_word = 0;
+    if (cudaMemcpy(&st_word, h->status, sizeof(int), cudaMemcpyDeviceToHost) == cudaSuccess && st_word != 0)
+        return (rom_status)st_word;
+    {
+        std::lock_guard<std::mutex> lk(h->mu);
+        if (tc) h->tuned_tc[std::make_pair(prec, M)] = tcp[bi];
+        else h->tuned[std::make_pair(f64 ? 0 : 1, M)] = simt[bi];
+    }
+    if (best_us) *best_us = best;
+    return ROM_OK;
+}
+
 rom_status rom_set_tc_columns(rom_t h, int cols) {
     if (!h || cols < 0 || cols > 256 || cols % 16 != 0) return ROM_E_INVAL;
     std::lock_guard<std::mutex> lk(h->mu);
@@ -751,7 +875,8 @@ rom_status batch_streams(size_t n) {
 
 extern "C" {
 
-rom_status rom_run_batched(const rom_job* jobs, int njobs, int nsteps, int r, int prec, void* stream) {
+static rom_status run_batched_impl(const rom_job* jobs, int njobs, int nsteps, int r, int prec,
+                                   void* stream, double scale) {
     if (!jobs || njobs < 1 || nsteps < 0 || r < 0 || !valid_prec(prec)) return ROM_E_INVAL;
     for (int i = 0; i < njobs; ++i) {
         const rom_job& j = jobs[i];
@@ -787,7 +912,7 @@ rom_status rom_run_batched(const rom_job* jobs, int njobs, int nsteps, int r, in
         }
         const int Kp = h->Kp;
         const int cs_guess = Kp > 512 ? Kp / 64 : Kp / 32;
-        const int budget = (int)((double)nsm * cost[i] / total / cs_guess);
+        const int budget = (int)(scale * (double)nsm * cost[i] / total / cs_guess);
         bool ok = false;
         if (prec == ROM_FP32) ok = plan_rank2_split_f32(Kp, jobs[i].M, h->R, &plans[i], budget > 0 ? budget : 1);
         if (ok) plans[i].variant = 2;
@@ -812,6 +937,7 @@ rom_status rom_run_batched(const rom_job* jobs, int njobs, int nsteps, int r, in
         key.words.insert(key.words.end(), {(uintptr_t)j.h, (uintptr_t)j.V, (uintptr_t)j.S,
                                            (uintptr_t)j.T, (uintptr_t)j.M, (uintptr_t)j.traces});
     }
+    key.words.push_back((uintptr_t)(scale * 1024.0));
     std::lock_guard<std::mutex> lk(g_batch_mu);
     auto it = g_batch_graphs.find(key);
     if (it == g_batch_graphs.end()) {
@@ -862,6 +988,112 @@ rom_status rom_run_batched(const rom_job* jobs, int njobs, int nsteps, int r, in
         ROM_CUDA(cudaStreamSynchronize(st));
         cudaGraphExecDestroy(exec);
     }
+    return ROM_OK;
+}
+
+// Cluster-budget scale chosen by rom_autotune_batched, per job list
+// (handles and widths; buffers and step counts do not change the choice).
+std::map<std::vector<uintptr_t>, double> g_batch_scale;
+
+static std::vector<uintptr_t> batch_tune_key(const rom_job* jobs, int njobs, int prec) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::vector<uintptr_t> k = {(uintptr_t)njobs, (uintptr_t)prec, (uintptr_t)dev};
+    for (int i = 0; i < njobs; ++i) {
+        k.push_back((uintptr_t)jobs[i].h);
+        k.push_back((uintptr_t)jobs[i].M);
+    }
+    return k;
+}
+
+rom_status rom_run_batched(const rom_job* jobs, int njobs, int nsteps, int r, int prec, void* stream) {
+    double scale = 1.0;
+    if (jobs && njobs > 0) {
+        std::lock_guard<std::mutex> lk(g_batch_mu);
+        auto it = g_batch_scale.find(batch_tune_key(jobs, njobs, prec));
+        if (it != g_batch_scale.end()) scale = it->second;
+    }
+    return run_batched_impl(jobs, njobs, nsteps, r, prec, stream, scale);
+}
+
+rom_status rom_autotune_batched(const rom_job* jobs, int njobs, int prec, int probe_steps,
+                                double* best_us, void* stream) {
+    if (!jobs || njobs < 1 || probe_steps < 1 || !valid_prec(prec)) return ROM_E_INVAL;
+    for (int i = 0; i < njobs; ++i)
+        if (!jobs[i].h || jobs[i].M < 1) return ROM_E_INVAL;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const size_t es = prec == ROM_FP64 ? 8 : 4;
+    // scratch state of every job (zero state, every period 45 dt)
+    std::vector<rom_job> sj(jobs, jobs + njobs);
+    std::vector<void*> bufs;
+    cudaError_t e = cudaSuccess;
+    for (int i = 0; i < njobs && e == cudaSuccess; ++i) {
+        void *V = nullptr, *S = nullptr, *T = nullptr;
+        e = cudaMalloc(&V, es * (size_t)jobs[i].h->Kv * jobs[i].M);
+        if (e == cudaSuccess) bufs.push_back(V);
+        if (e == cudaSuccess) e = cudaMalloc(&S, es * (size_t)jobs[i].h->Ks * jobs[i].M);
+        if (e == cudaSuccess) bufs.push_back(S);
+        if (e == cudaSuccess) e = cudaMalloc(&T, es * (size_t)jobs[i].M);
+        if (e == cudaSuccess) bufs.push_back(T);
+        if (e == cudaSuccess) {
+            std::vector<char> hT(es * (size_t)jobs[i].M);
+            for (int m = 0; m < jobs[i].M; ++m) {
+                if (es == 8) reinterpret_cast<double*>(hT.data())[m] = 45.0 * jobs[i].h->dt;
+                else reinterpret_cast<float*>(hT.data())[m] = (float)(45.0 * jobs[i].h->dt);
+            }
+            e = cudaMemcpy(T, hT.data(), hT.size(), cudaMemcpyHostToDevice);
+        }
+        sj[i].V = V;
+        sj[i].S = S;
+        sj[i].T = T;
+        sj[i].traces = nullptr;
+    }
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (e == cudaSuccess) e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    const double scales[4] = {0.5, 1.0, 2.0, 4.0};
+    double best = -1.0, best_scale = 1.0;
+    rom_status rs = ROM_OK;
+    for (int c = 0; c < 4 && e == cudaSuccess && rs == ROM_OK; ++c) {
+        float ms = 0.f;
+        for (int pass = 0; pass < 2 && e == cudaSuccess && rs == ROM_OK; ++pass) {  // warm-up, timed
+            const int n = pass == 0 ? (probe_steps < 20 ? probe_steps : 20) : probe_steps;
+            e = cudaEventRecord(e0, st);
+            if (e == cudaSuccess) rs = run_batched_impl(sj.data(), njobs, n, 0, prec, stream, scales[c]);
+            if (e == cudaSuccess && rs == ROM_OK) e = cudaEventRecord(e1, st);
+            if (e == cudaSuccess && rs == ROM_OK) e = cudaEventSynchronize(e1);
+            if (e == cudaSuccess && rs == ROM_OK) e = cudaEventElapsedTime(&ms, e0, e1);
+        }
+        if (e == cudaSuccess && rs == ROM_OK) {
+            const double us = 1e3 * ms / probe_steps;
+            if (best < 0.0 || us < best) { best = us; best_scale = scales[c]; }
+        }
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    {
+        // graphs captured on the scratch buffers are dropped with them
+        std::lock_guard<std::mutex> lk(g_batch_mu);
+        for (auto it = g_batch_graphs.begin(); it != g_batch_graphs.end();) {
+            bool uses = false;
+            for (uintptr_t w : it->first.words)
+                for (void* b : bufs) uses |= (w == (uintptr_t)b);
+            if (uses) {
+                cudaGraphExecDestroy(it->second);
+                it = g_batch_graphs.erase(it);
+            } else {
+                ++it;
+            }
+        }
+    }
+    for (void* b : bufs) cudaFree(b);
+    if (e != cudaSuccess) return cuda_fail(e, "rom_autotune_batched");
+    if (rs != ROM_OK) return rs;
+    {
+        std::lock_guard<std::mutex> lk(g_batch_mu);
+        g_batch_scale[batch_tune_key(jobs, njobs, prec)] = best_scale;
+    }
+    if (best_us) *best_us = best;
     return ROM_OK;
 }
 

@@ -35,7 +35,7 @@ PRECISIONS = {"fp64": ROM_FP64, "fp32": ROM_FP32, "tf32x3": ROM_TF32X3,
               "bf16x3": ROM_BF16X3, "bf16": ROM_BF16, "bf16s": ROM_BF16S}
 
 EXPORTED = ["rom_create", "rom_destroy", "rom_spectral_radius", "rom_sync_status",
-            "rom_get_dims", "rom_set_kernel", "rom_get_plan", "rom_set_tc_columns", "rom_set_wavelet", "rom_set_wait_limit",
+            "rom_get_dims", "rom_set_kernel", "rom_get_plan", "rom_set_tc_columns", "rom_set_wavelet", "rom_autotune", "rom_autotune_batched", "rom_set_wait_limit",
             "rom_debug_inject_stall", "rom_run_rank2", "rom_run_rank2_ex", "rom_run_rank1",
             "rom_run_rank1_ensemble", "rom_run_batched", "rom_adjoint",
             "rom_adjoint_workspace_size", "rom_rel_l2", "rom_spectral_radius_noalloc",
@@ -68,6 +68,8 @@ def _signatures(lib):
         "rom_set_wait_limit": (_i, [_vp, ctypes.c_longlong]),
         "rom_set_tc_columns": (_i, [_vp, _i]),
         "rom_set_wavelet": (_i, [_vp, _i]),
+        "rom_autotune": (_i, [_vp, _i, _i, _i, ctypes.POINTER(_d), _vp]),
+        "rom_autotune_batched": (_i, [_vp, _i, _i, _i, ctypes.POINTER(_d), _vp]),
         "rom_debug_inject_stall": (_i, [_vp, _i]),
         "rom_get_plan": (_i, [_vp, _i, _i, ctypes.POINTER(_i), ctypes.POINTER(_i),
                               ctypes.POINTER(_i), ctypes.POINTER(_i)]),
@@ -166,6 +168,13 @@ def rom_set_wavelet(h, wavelet):
     return load().rom_set_wavelet(h, int(wavelet))
 
 
+def rom_autotune(h, prec, M, probe_steps, stream=None):
+    """Returns (status, probe microseconds per step of the chosen plan)."""
+    us = _d(0.0)
+    st = load().rom_autotune(h, int(prec), int(M), int(probe_steps), ctypes.byref(us), stream)
+    return st, us.value
+
+
 def rom_set_wait_limit(h, cycles):
     return load().rom_set_wait_limit(h, int(cycles))
 
@@ -237,6 +246,27 @@ def run_batched(items, nsteps, r=0, prec="fp32", stream=None):
         arr[i] = rom_job(h.h, _ptr(V), _ptr(S), _ptr(T), M, _ptr(tr))
     st = rom_run_batched(arr, len(items), int(nsteps), int(r), p, _stream_handle(stream))
     _chk(st, "rom_run_batched")
+
+
+def rom_autotune_batched(jobs, njobs, prec, probe_steps, stream=None):
+    """Returns (status, probe microseconds per step of the chosen schedule)."""
+    us = _d(0.0)
+    st = load().rom_autotune_batched(jobs, int(njobs), int(prec), int(probe_steps), ctypes.byref(us), stream)
+    return st, us.value
+
+
+def autotune_batched(items, prec="fp32", probe_steps=200, stream=None):
+    """Time the batching schedule of `items` (as for run_batched) at four
+    cluster-budget scales on scratch state and keep the fastest for later
+    run_batched calls on the same handles and widths.  Returns the chosen
+    schedule's probe time per step in microseconds."""
+    p = PRECISIONS.get(prec, prec)
+    arr = (rom_job * len(items))()
+    for i, (h, V, S, T, tr) in enumerate(items):
+        arr[i] = rom_job(h.h, _ptr(V), _ptr(S), _ptr(T), V.shape[1], None)
+    st, us = rom_autotune_batched(arr, len(items), p, probe_steps, _stream_handle(stream))
+    _chk(st, "rom_autotune_batched")
+    return us
 
 
 def rom_adjoint(h, V0, S0, T, M, nsteps, ystar, ckpt_every, gV0, gS0, gT, workspace, ws_bytes,
@@ -403,6 +433,14 @@ class Rom:
 
     def set_kernel(self, kernel):
         _chk(rom_set_kernel(self.h, int(kernel)), "rom_set_kernel")
+
+    def autotune(self, M, prec="fp32", probe_steps=200, stream=None):
+        """Time every candidate plan for M realizations and keep the fastest;
+        returns the chosen plan's probe time per step in microseconds."""
+        st = stream.cuda_stream if hasattr(stream, "cuda_stream") else stream
+        s, us = rom_autotune(self.h, PRECISIONS.get(prec, prec), M, probe_steps, st)
+        _chk(s, "rom_autotune")
+        return us
 
     def set_wavelet(self, wavelet):
         """Source signal of the periods: "ricker" (default) or "gauss1" (first

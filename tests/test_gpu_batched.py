@@ -108,3 +108,48 @@ def test_batched_workload3_full_size_sampled(rom):
         Vo, So, _ = oracle.problem_forward(p, nsteps=5000, r=0, columns=cols)
         assert rel(V.cpu().numpy()[:, cols], Vo) <= 1e-4
         assert rel(S.cpu().numpy()[:, cols], So) <= 1e-4
+
+
+def test_autotune_batched_keeps_results(rom):
+    """The measured schedule changes only how the SMs are shared: every job's
+    result stays within FP32 rounding of the untuned schedule."""
+    probs = inputs.batched_problems()[:12]
+    items = []
+    for p in probs:
+        h = rom.Rom.from_problem(p)
+        items.append((h, rom.Rom.new_state(p.Kv, p.M, "fp32"), rom.Rom.new_state(p.Ks, p.M, "fp32"),
+                      torch.as_tensor(p.T, device="cuda"), None))
+    rom.run_batched(items, 300)
+    torch.cuda.synchronize()
+    ref = [(V.cpu().numpy(), S.cpu().numpy()) for (_, V, S, _, _) in items]
+    us = rom.autotune_batched(items, probe_steps=50)
+    assert us > 0
+    for (_, V, S, _, _) in items:
+        V.zero_()
+        S.zero_()
+    rom.run_batched(items, 300)
+    torch.cuda.synchronize()
+    for (Vr, Sr), (_, V, S, _, _) in zip(ref, items):
+        v = V.cpu().numpy()
+        assert np.linalg.norm(v - Vr) <= 1e-5 * np.linalg.norm(Vr)
+
+
+def test_autotune_single_handle(rom):
+    p = inputs.make_problem(512, 512, 256, 8, seed=2)
+    h = rom.Rom.from_problem(p)
+    T = torch.as_tensor(p.T, device="cuda")
+    V1, S1 = rom.Rom.new_state(512, 256, "fp32"), rom.Rom.new_state(512, 256, "fp32")
+    h.run_rank2(V1, S1, T, 200, prec="fp32")
+    us = h.autotune(256, "fp32", probe_steps=100)
+    assert us > 0
+    V2, S2 = rom.Rom.new_state(512, 256, "fp32"), rom.Rom.new_state(512, 256, "fp32")
+    h.run_rank2(V2, S2, T, 200, prec="fp32")
+    torch.cuda.synchronize()
+    a, b = V1.cpu().numpy(), V2.cpu().numpy()
+    assert np.linalg.norm(a - b) <= 1e-5 * np.linalg.norm(a)
+    us_tc = h.autotune(256, "bf16s", probe_steps=50)
+    assert us_tc > 0
+    V3, S3 = rom.Rom.new_state(512, 256, "fp32"), rom.Rom.new_state(512, 256, "fp32")
+    h.run_rank2(V3, S3, T, 200, prec="bf16s")
+    torch.cuda.synchronize()
+    assert np.linalg.norm(V3.cpu().numpy() - a) <= 1e-4 * np.linalg.norm(a)
