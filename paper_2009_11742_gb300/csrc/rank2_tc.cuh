@@ -158,6 +158,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) rank2_tc_kernel(const TcArgs a)
     uint32_t* tslot = reinterpret_cast<uint32_t*>(drain + 1);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tslot + 1);
     volatile int* abort_all = reinterpret_cast<volatile int*>(tslot + 2);
+    // abort flag as published for the cluster-wide decision: written after
+    // the half-step's last wait, read by the peers after the barrier
+    volatile int* abort_pub = reinterpret_cast<volatile int*>(tslot + 3);
     long long* consumed = reinterpret_cast<long long*>(tslot + 4);
     float* fcol = reinterpret_cast<float*>(tslot + 6);
     float* Tcol = fcol + W;
@@ -166,6 +169,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) rank2_tc_kernel(const TcArgs a)
     if (tid == 0) {
         *abort_flag = 0;
         *abort_all = 0;
+        *abort_pub = 0;
         for (int s = 0; s < STAGES; ++s) { mbarrier_init(&full[s], 1); mbarrier_init(&empty[s], 1); }
         for (int b = 0; b < 2; ++b) { mbarrier_init(&dready[b], 1); mbarrier_init(&dempty[b], kTcReadWarps); }
         mbarrier_init(drain, 1);
@@ -323,14 +327,16 @@ __global__ void __launch_bounds__(kTcThreads, 1) rank2_tc_kernel(const TcArgs a)
                     fcol[c] = f;
                 }
             }
+            __syncthreads();  // every wait of this half-step is over
+            if (tid == 0) *abort_pub = *abort_flag;
             tc_fence_before();
             cluster.sync();
             tc_fence_after();
-            // cluster-uniform abort decision
+            // cluster-uniform abort decision from the published flags
             if (tid == 0) {
-                int any = *abort_flag;
+                int any = 0;
                 for (int q = 0; q < CS; ++q) {
-                    const int* pf = cluster.map_shared_rank(const_cast<int*>(abort_flag), q);
+                    const int* pf = cluster.map_shared_rank(const_cast<int*>(abort_pub), q);
                     any |= *reinterpret_cast<volatile const int*>(pf);
                 }
                 *abort_all = any;
