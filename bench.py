@@ -47,6 +47,16 @@ TC_PRODUCTS = {"tf32x3": 3, "bf16x3": 5, "bf16": 1, "bf16s": 6}
 FP32_LANES_PER_SM = 128  # FP32 FMA lanes per SM (Blackwell)
 
 
+METRIC = "rank-2 ROM sample-steps/s (FP32 leapfrog, rel err <= 1e-4)"
+
+
+def bench_config(W, world):
+    """The `config` object of the headline line (both arms)."""
+    return {"workload": W["name"], "K": W["K"], "M": W["M"], "nsteps": W["nsteps"], "R": W["R"],
+            "r": W["r"], "prec": W["prec"], "parallelism": f"replicas-by-realization x{world}",
+            "l2": "flushed (256 MB write) before every timed step"}
+
+
 def useful_flops(K, M, N, R, r):
     return (4.0 * K * K * M + (2.0 * R * K * M / r if r else 0.0)) * N
 
@@ -149,13 +159,11 @@ def run_reference(args):
     value = ncol * nst * args.steps / tot
     sample = f"{ncol} of {WORKLOAD['M']} columns x {nst} of {WORKLOAD['nsteps']} steps per step"
     line = {
-        "impl": "reference", "metric": "rank-2 ROM sample-steps/s (FP64 CPU oracle)",
+        "impl": "reference", "metric": METRIC,
         "value": value, "unit": "sample-steps/s", "n_gpus": args.gpus, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": {"workload": WORKLOAD["name"], "K": WORKLOAD["K"],
-                                        "M": WORKLOAD["M"], "nsteps": WORKLOAD["nsteps"],
-                                        "R": WORKLOAD["R"], "r": WORKLOAD["r"]},
+        "data": "synthetic", "config": bench_config(WORKLOAD, int(os.environ.get("WORLD_SIZE", "1"))),
         "cpu_baseline": {"value": value, "unit": "sample-steps/s", "cores": cores,
                          "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": "sample-steps/s", "h2d_bytes_per_step": 0,
@@ -458,13 +466,11 @@ def main():
     h2d = (2 * K * M + M) * es
     d2h = (2 * K * M + nrec * R * M) * es
     line = {
-        "metric": "rank-2 ROM sample-steps/s (FP32 leapfrog, rel err <= 1e-4)",
+        "metric": METRIC,
         "value": value, "unit": "sample-steps/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": W["name"], "K": K, "M": M, "nsteps": N, "R": R, "r": r,
-                   "prec": "fp32", "parallelism": f"replicas-by-realization x{world}",
-                   "l2": "flushed (256 MB write) before every timed step"},
+        "config": bench_config(W, world),
         "tflops_useful": world * flops * args.steps / t_dev / 1e12,
         "roofline": roof,
         "cpu_baseline": cpu,
