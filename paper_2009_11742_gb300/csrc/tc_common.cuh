@@ -169,21 +169,6 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
 }
 
 // ---- operand splitting
-// x = hi + lo with hi holding the top 11 significand bits (TF32 keeps the
-// sign, exponent and 10 explicit bits); lo = x - hi is exact in FP32.
-__host__ __device__ __forceinline__ void split_tf32(float x, float& hi, float& lo) {
-#ifdef __CUDA_ARCH__
-    const uint32_t u = __float_as_uint(x);
-    hi = __uint_as_float(u & 0xFFFFE000u);
-#else
-    uint32_t u;
-    __builtin_memcpy(&u, &x, 4);
-    u &= 0xFFFFE000u;
-    __builtin_memcpy(&hi, &u, 4);
-#endif
-    lo = x - hi;
-}
-
 // x = hi + lo with hi = x rounded to the nearest TF32 value (ties to even)
 // and lo = x - hi (exact in FP32) also rounded to TF32.  Both terms are
 // exact TF32 numbers, so the tensor core sees them unchanged, and the
