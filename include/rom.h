@@ -14,9 +14,12 @@
  *     V^{n+1} = V^n + dt (Avs S^n + g f_n^T),   S^{n+1} = S^n + dt Asv V^{n+1},
  *
  * with f_n[m] = f(t_n; T_m), t_n = (n0 + n) dt, and the point-source Ricker
- * wavelet of Sec. 3.2 (sparse reduced forcing, Sec. 2.2):
+ * wavelet of Sec. 3.2 (sparse reduced forcing, Sec. 2.2)
  *
- *     f(t; T) = (1 - 2u) exp(-u),  u = pi^2 (t - 1.5 T)^2 / T^2.
+ *     f(t; T) = (1 - 2u) exp(-u),  u = pi^2 (t - 1.5 T)^2 / T^2,
+ *
+ * or the paper's second signal, the first derivative of a Gaussian
+ * (rom_set_wavelet).
  *
  * Receiver traces (seismograms from basis rows, Sec. 4.5.2) are y = C V^{n+1}
  * after every step with (n + 1) mod r == 0.
@@ -38,8 +41,9 @@
  *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default).
  *  - A handle is not re-entrant: do not run two calls on one handle
  *    concurrently on different streams.
- *  - Device-side failures (non-finite final state) are recorded in a
- *    per-handle status word read by rom_sync_status().
+ *  - Device-side failures (a non-finite final state, a bounded wait that
+ *    ran out) are recorded in a per-handle status word read by
+ *    rom_sync_status().
  */
 #ifndef ROM_H
 #define ROM_H
@@ -123,14 +127,17 @@ rom_status rom_get_dims(rom_t h, int* Kv, int* Ks, int* R, double* dt);
  *  ROM_KERNEL_DATAFLOW  the two-block schedule synchronised by per-block
  *                       mbarriers fed with asynchronous remote stores; its
  *                       waits are bounded (rom_set_wait_limit).
- * All compute the same leapfrog (Sec. 3.1) with the same summation order. */
+ * All compute the same leapfrog (Sec. 3.1); their results agree to FP32
+ * rounding. */
 enum { ROM_KERNEL_AUTO = 0, ROM_KERNEL_ONE_BLOCK = 1, ROM_KERNEL_TWO_BLOCK = 2,
        ROM_KERNEL_DATAFLOW = 3 };
 rom_status rom_set_kernel(rom_t h, int kernel);
 
-/* The launch plan the handle would use for M realizations at precision prec:
- * kernel variant (1 or 2), cluster size, columns per column block and number
- * of clusters (outputs may be NULL).  ROM_E_UNSUPPORTED if no kernel fits. */
+/* The launch plan the handle would use for M realizations at precision prec
+ * (ROM_FP32 or ROM_FP64): kernel variant (1 one-block, 2 two-block, 3
+ * dataflow), cluster size, columns per column block and number of clusters
+ * (outputs may be NULL).  ROM_E_UNSUPPORTED for another precision or if no
+ * kernel fits. */
 rom_status rom_get_plan(rom_t h, int prec, int M, int* variant, int* cluster_size,
                         int* cols_per_block, int* nclusters);
 
@@ -180,9 +187,10 @@ rom_status rom_set_tc_columns(rom_t h, int cols);
 
 /*
  * rom_set_wait_limit -- bound, in SM clock cycles, on every device-side wait
- * of the dataflow kernel (a consumer waiting for a producer's rows).  A wait
- * that runs out makes the kernel stop, leave cleanly, and record
- * ROM_E_TIMEOUT in the handle's status word (rom_sync_status).  Default
+ * of the dataflow kernel (a consumer waiting for a producer's rows) and of
+ * the tensor-core kernels (stage and accumulator handshakes).  A wait that
+ * runs out makes the kernel stop, leave cleanly, and record ROM_E_TIMEOUT in
+ * the handle's status word (rom_sync_status).  Default
  * 4e9 cycles (about 2 s), far above any legitimate wait.
  */
 rom_status rom_set_wait_limit(rom_t h, long long cycles);
@@ -201,8 +209,8 @@ rom_status rom_debug_inject_stall(rom_t h, int on);
  * rom_run_rank2 -- the rank-2 Galerkin leapfrog (Eq. (rom_ode_tensor) with the
  * split of Eq. (shwave_rom_ode_tensor), leapfrog of Sec. 3.1): advance all M
  * realizations sharing the handle's operators by nsteps steps, IN PLACE on V
- * (Kv x M) and S (Ks x M).  T (M) holds each realization's Ricker period in
- * time units.  Steps n = 0 .. nsteps-1 use t_n = (n0 + n) dt.  traces (may be
+ * (Kv x M) and S (Ks x M).  T (M) holds each realization's source period in
+ * time units (signal chosen by rom_set_wavelet).  Steps n = 0 .. nsteps-1 use t_n = (n0 + n) dt.  traces (may be
  * NULL; r must then be 0) receives floor(nsteps / r) records of C V.
  * nsteps == 0 is a no-op.  Errors: ROM_E_INVAL (bad pointer/size, r < 0, or
  * traces without receiver rows), ROM_E_UNSUPPORTED (precision not provided
@@ -214,7 +222,7 @@ rom_status rom_run_rank2(rom_t h, void* V, void* S, const void* T, int M, int ns
 /*
  * rom_run_rank2_ex -- rom_run_rank2 with the optional inputs spelled out.
  *  ftab : if non-NULL, an nsteps x M forcing table (element [n * M + m]) used
- *         in place of the Ricker wavelet; T is then ignored (may be NULL).
+ *         in place of the wavelet; T is then ignored (may be NULL).
  *         This is the dense reduced-forcing mode of Sec. 2.2 (precomputed
  *         Phi^T f(t) at every target time).
  *  compV, compS : optional FP32 Kahan compensation carries (Kv x M, Ks x M,
