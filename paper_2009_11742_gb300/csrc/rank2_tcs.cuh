@@ -420,21 +420,32 @@ __global__ void __launch_bounds__(kTcsThreads, 1) rank2_tcs_kernel(const TcArgs 
                 const uint32_t tl = tbase + ((uint32_t)(32 * quad) << 16) + (uint32_t)jbase;
                 // one 8-column group: readout, update, new state parked in TMEM,
                 // loads of the group two ahead into the same buffers
-                auto group = [&](const int g, float (&yg)[8], float (&cg_)[8]) {
+                // accumulator registers of one group, double-buffered: the next
+                // group's loads are issued before the current group's update
+                struct Acc8 { uint32_t r0[8], r1a[8], r1b[8], r2[8]; };
+                auto acc_issue = [&](const int g, Acc8& t) {
+                    if (!have) return;
                     const int i0 = 8 * g;
-                    uint32_t r0[8], r1a[8], r1b[8], r2[8];
-                    if (have) {
-                        tmem_ld8_nowait(tl + (uint32_t)i0, r0);
-                        tmem_ld8_nowait(tl + (uint32_t)(AST + i0), r1a);
-                        if (two_t1) tmem_ld8_nowait(tl + (uint32_t)(2 * AST + i0), r1b);
-                        tmem_ld8_nowait(tl + (uint32_t)(3 * AST + i0), r2);
-                    }
+                    tmem_ld8_nowait(tl + (uint32_t)i0, t.r0);
+                    tmem_ld8_nowait(tl + (uint32_t)(AST + i0), t.r1a);
+                    if (two_t1) tmem_ld8_nowait(tl + (uint32_t)(2 * AST + i0), t.r1b);
+                    tmem_ld8_nowait(tl + (uint32_t)(3 * AST + i0), t.r2);
+                };
+                auto acc_wait = [&](Acc8& t) {
 #pragma unroll
                     for (int q = 0; q < 8; ++q) {
-                        if (!have) { r0[q] = 0u; r1a[q] = 0u; r2[q] = 0u; }
-                        if (!have || !two_t1) r1b[q] = 0u;
+                        if (!have) { t.r0[q] = 0u; t.r1a[q] = 0u; t.r2[q] = 0u; }
+                        if (!have || !two_t1) t.r1b[q] = 0u;
                     }
-                    if (have) tmem_wait_ld4(r0, r1a, r1b, r2);
+                    if (have) tmem_wait_ld4(t.r0, t.r1a, t.r1b, t.r2);
+                };
+                auto group = [&](const int g, Acc8& cur, Acc8& nxt, float (&yg)[8], float (&cg_)[8]) {
+                    const int i0 = 8 * g;
+                    if (g + 1 < NG) acc_issue(g + 1, nxt);
+                    const uint32_t(&r0)[8] = cur.r0;
+                    const uint32_t(&r1a)[8] = cur.r1a;
+                    const uint32_t(&r1b)[8] = cur.r1b;
+                    const uint32_t(&r2)[8] = cur.r2;
                     float ynew[8], scl[8], fq[8];
                     unsigned ybits[8];
 #pragma unroll
@@ -477,11 +488,15 @@ __global__ void __launch_bounds__(kTcsThreads, 1) rank2_tcs_kernel(const TcArgs 
                     tmem_st8(tl + (uint32_t)(4 * AST + i0), ynew);
                     if (g + 2 < NG)
                         load_group8(Y, Cy, Kown, col0 + jbase + i0 + 16, ncol - jbase - i0 - 16, rowok, yg, cg_);
+                    if (g + 1 < NG) acc_wait(nxt);
                 };
+                Acc8 accA, accB;
+                acc_issue(0, accA);
+                acc_wait(accA);
 #pragma unroll 1
                 for (int g = 0; g < NG; g += 2) {
-                    group(g, ya, ca);
-                    if (g + 1 < NG) group(g + 1, yb, cb);
+                    group(g, accA, accB, ya, ca);
+                    if (g + 1 < NG) group(g + 1, accB, accA, yb, cb);
                 }
                 tmem_wait_st();
                 tc_fence_before();
