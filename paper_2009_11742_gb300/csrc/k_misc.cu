@@ -15,15 +15,29 @@ namespace romk {
 // so a warp reads contiguous 512-byte segments.  No operator value is reused
 // across realizations: this is the bandwidth-bound rank-1 formulation of
 // Sec. 2.3, run M times side by side.
+//
+// The stream is latency-bound: its rate is the bytes each SM keeps in flight,
+// i.e. the loads of its resident warps.  The CTA therefore takes NT = 256, 512
+// or 1024 threads, the most that still keeps all M CTAs resident in one wave
+// (64 registers a thread, so NT * CTAs per SM <= 1024), with at most 8
+// k-splits so that the per-row sum of the partials stays short.  Co-resident
+// CTAs read the same operator lines at about the same time and share them
+// in L1.
 // ---------------------------------------------------------------------------
-constexpr int kEnsThreads = 256;
+constexpr int kEnsMaxSplit = 8;
 
-template <typename T>
-__global__ void __launch_bounds__(kEnsThreads) rank1_ensemble_kernel(const Rank1EnsArgs a) {
+__host__ __device__ inline int ens_ksplit(int NT, int Kp) {
+    const int G = Kp / 4;
+    const int ks = NT / G;
+    return ks < 1 ? 1 : (ks > kEnsMaxSplit ? kEnsMaxSplit : ks);
+}
+
+template <typename T, int NT>
+__global__ void __launch_bounds__(NT, 1024 / NT) rank1_ensemble_kernel(const Rank1EnsArgs a) {
     const int m = blockIdx.x;
     const int Kp = a.Kp;
     const int G = Kp / 4;                 // row groups of 4
-    const int KS = kEnsThreads / G > 0 ? kEnsThreads / G : 1;
+    const int KS = ens_ksplit(NT, Kp);
     const int tid = threadIdx.x;
     const int gq = tid % G;
     const int ks = tid / G;
@@ -34,7 +48,7 @@ __global__ void __launch_bounds__(kEnsThreads) rank1_ensemble_kernel(const Rank1
     T* part = s + Kp;  // KS x Kp partial sums
     const T* Vin = static_cast<const T*>(a.V);
     const T* Sin = static_cast<const T*>(a.S);
-    for (int k = tid; k < Kp; k += kEnsThreads) {
+    for (int k = tid; k < Kp; k += NT) {
         v[k] = k < a.Kv ? Vin[(size_t)m * a.Kv + k] : T(0);
         s[k] = k < a.Ks ? Sin[(size_t)m * a.Ks + k] : T(0);
     }
@@ -87,7 +101,7 @@ __global__ void __launch_bounds__(kEnsThreads) rank1_ensemble_kernel(const Rank1
         }
         if (traces && ((n + 1) % a.r) == 0) {
             const int rec = (n + 1) / a.r - 1;
-            for (int jr = tid; jr < a.R; jr += kEnsThreads) {
+            for (int jr = tid; jr < a.R; jr += NT) {
                 T acc = T(0);
                 for (int k = 0; k < a.Kv; ++k) acc += Cc[(size_t)k * a.R + jr] * v[k];
                 traces[((size_t)rec * a.M + m) * a.R + jr] = acc;
@@ -97,7 +111,7 @@ __global__ void __launch_bounds__(kEnsThreads) rank1_ensemble_kernel(const Rank1
     T* Vout = static_cast<T*>(a.V);
     T* Sout = static_cast<T*>(a.S);
     int bad = 0;
-    for (int k = tid; k < Kp; k += kEnsThreads) {
+    for (int k = tid; k < Kp; k += NT) {
         if (k < a.Kv) { Vout[(size_t)m * a.Kv + k] = v[k]; bad |= !is_finite(v[k]); }
         if (k < a.Ks) { Sout[(size_t)m * a.Ks + k] = s[k]; bad |= !is_finite(s[k]); }
     }
@@ -105,16 +119,29 @@ __global__ void __launch_bounds__(kEnsThreads) rank1_ensemble_kernel(const Rank1
     if (bad && tid == 0 && a.status) atomicCAS(a.status, 0, 6 /* ROM_E_NONFINITE */);
 }
 
-template <typename T>
-static cudaError_t launch_ens(const Rank1EnsArgs& a, cudaStream_t st) {
-    const int G = a.Kp / 4;
-    const int KS = kEnsThreads / G > 0 ? kEnsThreads / G : 1;
+template <typename T, int NT>
+static cudaError_t launch_ens_nt(const Rank1EnsArgs& a, cudaStream_t st) {
+    const int KS = ens_ksplit(NT, a.Kp);
     const size_t smem = sizeof(T) * (size_t)(2 * a.Kp + KS * a.Kp);
-    auto fn = rank1_ensemble_kernel<T>;
+    auto fn = rank1_ensemble_kernel<T, NT>;
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    fn<<<a.M, kEnsThreads, smem, st>>>(a);
+    fn<<<a.M, NT, smem, st>>>(a);
     return cudaGetLastError();
+}
+
+template <typename T>
+static cudaError_t launch_ens(const Rank1EnsArgs& a, cudaStream_t st) {
+    if (a.Kp <= 0 || a.Kp % 64 != 0 || a.Kp > 1024 || a.M <= 0) return cudaErrorInvalidValue;
+    int dev = 0, nsm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (nsm <= 0) return cudaErrorInvalidDevice;
+    int NT = a.M <= nsm ? 1024 : (a.M <= 2 * nsm ? 512 : 256);
+    while (NT > 256 && NT / (a.Kp / 4) > kEnsMaxSplit) NT /= 2;
+    if (NT == 1024) return launch_ens_nt<T, 1024>(a, st);
+    if (NT == 512) return launch_ens_nt<T, 512>(a, st);
+    return launch_ens_nt<T, 256>(a, st);
 }
 
 cudaError_t launch_rank1_ensemble_f32(const Rank1EnsArgs& a, cudaStream_t st) { return launch_ens<float>(a, st); }

@@ -27,8 +27,11 @@
 
 namespace romk {
 
+// Steps of df/dT tabulated at a time (shared memory, kAdjTab x Wa floats).
+constexpr int kAdjTab = 64;
+
 struct AdjSmem {
-    size_t Vf, Sf, cV, cS, Ccol, rbuf, g, T, gT, total;
+    size_t Vf, Sf, cV, cS, Ccol, rbuf, g, T, gT, dfT, total;
 };
 
 __host__ __device__ inline AdjSmem adj_smem_layout(int Wa, int Kp, int R) {
@@ -43,6 +46,7 @@ __host__ __device__ inline AdjSmem adj_smem_layout(int Wa, int Kp, int R) {
     s.g = o;    o += align16((size_t)kRowsPerCta * sizeof(float));
     s.T = o;    o += align16((size_t)Wa * sizeof(float));
     s.gT = o;   o += align16((size_t)Wa * sizeof(float));
+    s.dfT = o;  o += align16((size_t)kAdjTab * Wa * sizeof(float));
     s.total = o;
     return s;
 }
@@ -116,6 +120,7 @@ __global__ void __launch_bounds__(kThreads, 1) rank2_adjoint_kernel(const AdjArg
     float* gown = reinterpret_cast<float*>(smem + L.g);
     float* Tcol = reinterpret_cast<float*>(smem + L.T);
     float* gTacc = reinterpret_cast<float*>(smem + L.gT);
+    float* dfT = reinterpret_cast<float*>(smem + L.dfT);    // [kAdjTab][Wa]: df/dT of the chunk
 
     for (int idx = tid; idx < Wa * Kp; idx += kThreads) {
         const int c = idx / Kp, k = idx % Kp;
@@ -142,6 +147,20 @@ __global__ void __launch_bounds__(kThreads, 1) rank2_adjoint_kernel(const AdjArg
     cluster.sync();
 
     for (int n = a.n_hi - 1; n >= a.n_lo; --n) {
+        // df/dT(t_n; T_c) for the next kAdjTab steps, all threads at once: the
+        // evaluation (FP64 time arithmetic) stays off the per-step critical
+        // path.  The previous chunk's last readers passed the cluster barrier
+        // at the end of the previous step; the barrier after the residual
+        // below publishes the new entries.
+        const int done = a.n_hi - 1 - n;
+        if (done % kAdjTab == 0) {
+            for (int idx = tid; idx < kAdjTab * ncol; idx += kThreads) {
+                const int i = idx / ncol, c = idx % ncol;
+                if (n - i >= a.n_lo)
+                    dfT[i * Wa + c] = wavelet_dT_eval(a.wavelet, (long long)a.n0 + n - i, a.dt, Tcol[c]);
+            }
+        }
+        const float* dfn = dfT + (done % kAdjTab) * Wa;
         // residual r^{n+1} = C V^{n+1} - ystar^{n+1} of this block's columns
         const int rec = n + 1 - a.rec_base;  // trace record holding C V^{n+1}
         for (int idx = tid; idx < R * Wa; idx += kThreads) {
@@ -163,7 +182,7 @@ __global__ void __launch_bounds__(kThreads, 1) rank2_adjoint_kernel(const AdjArg
             float s = gown[lane] * Vf[(size_t)c * Kp + row0 + lane];
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-            if (lane == 0) gTacc[c] = __fmaf_rn(dt * s, wavelet_dT_eval(a.wavelet, (long long)a.n0 + n, a.dt, Tcol[c]), gTacc[c]);
+            if (lane == 0) gTacc[c] = __fmaf_rn(dt * s, dfn[c], gTacc[c]);
         }
         push_own_rows<float>(cluster, Vf, Wa, Kp, row0, cs, crank, 1);
         cluster.sync();

@@ -171,6 +171,38 @@ def test_rank1_ensemble_vs_oracle(rom, prec):
     assert rel(tr.transpose(1, 2).cpu().numpy(), tro) <= tol
 
 
+@pytest.mark.parametrize("Kv,Ks,M,N,prec", [
+    (512, 512, 256, 200, "fp32"),   # the rank-1 comparison of the FP32 workload: 512 threads, 4 k-splits
+    (436, 417, 512, 120, "fp32"),   # the UQ shape: 256 threads, 2 k-splits
+    (64, 64, 700, 300, "fp32"),     # more CTAs than one wave holds; 16 row groups
+    (1024, 1000, 40, 40, "fp32"),   # 1024 threads, 4 k-splits
+    (1024, 960, 24, 20, "fp64"),    # FP64, 1024 threads
+    (192, 160, 300, 60, "fp64"),    # 512 threads would need 10 k-splits of 48 row groups: 256
+])
+def test_rank1_ensemble_launch_shapes(rom, Kv, Ks, M, N, prec):
+    """The rank-1 ensemble over its launch shapes (256, 512 and 1024
+    threads, k-splits 1 to 8, more CTAs than one wave), sampled columns
+    against the oracle run one column at a time."""
+    p = inputs.make_problem(Kv, Ks, M, 8, seed=23)
+    h = rom.Rom.from_problem(p)
+    V0 = inputs.random_state(Kv, M, seed=5, scale=0.1)
+    S0 = inputs.random_state(Ks, M, seed=6, scale=0.1)
+    r = 5
+    V = rom.Rom.new_state(Kv, M, prec, fill=V0)
+    S = rom.Rom.new_state(Ks, M, prec, fill=S0)
+    T = torch.as_tensor(p.T, dtype=tdt(prec), device="cuda")
+    tr = torch.zeros((N // r, M, 8), dtype=tdt(prec), device="cuda")
+    h.run_rank1_ensemble(V, S, T, N, r=r, traces=tr, prec=prec)
+    assert h.sync_status() == rom.ROM_OK
+    cols = sorted({0, 1, M // 2, M - 1})
+    Vo, So, tro = oracle.forward(p.Avs, p.Asv, p.g, p.C, p.dt, V0[:, cols], S0[:, cols], N,
+                                 T=p.T[cols], r=r)
+    Vg, Sg = V.cpu().numpy()[:, cols], S.cpu().numpy()[:, cols]
+    trg = tr.cpu().numpy()[:, cols, :].transpose(0, 2, 1)
+    tol = TOL[prec]
+    assert rel(Vg, Vo) <= tol and rel(Sg, So) <= tol and rel(trg, tro) <= tol
+
+
 @pytest.mark.parametrize("prec", ["fp32", "fp64"])
 def test_zero_in_zero_out_bitwise(rom, prec):
     p = inputs.make_problem(128, 96, 9, 4, seed=14)
