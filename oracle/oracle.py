@@ -53,11 +53,12 @@ def _load():
             lib.orc_forward.argtypes = [_dp, _dp, _dp, _dp, ctypes.c_int, ctypes.c_int,
                                         ctypes.c_int, ctypes.c_double, _dp, _dp, _dp, _dp,
                                         ctypes.c_int, ctypes.c_int, ctypes.c_long,
-                                        ctypes.c_int, _dp, ctypes.c_int, ctypes.c_int]
+                                        ctypes.c_int, _dp, ctypes.c_int, ctypes.c_int, _dp, _dp]
             lib.orc_inverse.restype = ctypes.c_int
             lib.orc_inverse.argtypes = [_dp, _dp, _dp, ctypes.c_int, ctypes.c_int,
                                         ctypes.c_double, _dp, _dp, _dp, _dp, ctypes.c_int,
-                                        ctypes.c_int, ctypes.c_long, ctypes.c_int, ctypes.c_int]
+                                        ctypes.c_int, ctypes.c_long, ctypes.c_int, ctypes.c_int,
+                                        _dp, _dp]
             lib.orc_energy.restype = ctypes.c_double
             lib.orc_energy.argtypes = [_dp, ctypes.c_int, ctypes.c_int, ctypes.c_double,
                                        _dp, _dp, ctypes.c_int]
@@ -68,7 +69,8 @@ def _load():
             lib.orc_adjoint.argtypes = [_dp, _dp, _dp, _dp, ctypes.c_int, ctypes.c_int,
                                         ctypes.c_int, ctypes.c_double, _dp, _dp, _dp,
                                         ctypes.c_int, ctypes.c_int, ctypes.c_long, _dp,
-                                        _dp, _dp, _dp, _dp, ctypes.c_int, ctypes.c_int]
+                                        _dp, _dp, _dp, _dp, ctypes.c_int, ctypes.c_int,
+                                        _dp, _dp]
             lib.orc_ricker.restype = None
             lib.orc_ricker.argtypes = [_dp, _dp, ctypes.c_int, _dp, _dp]
             lib.orc_wavelet.restype = None
@@ -125,12 +127,27 @@ def ricker(t, T):
     return f.reshape(shape), d.reshape(shape)
 
 
+def _xref(xref, Kv, Ks, M):
+    """The reduced reference state (Eq. (rom_ode_tensor)) as two column-major
+    FP64 blocks (Kv x M, Ks x M); None drops the term."""
+    if xref is None:
+        return None, None
+    Xv, Xs = xref
+    Xv = None if Xv is None else _cm(Xv)
+    Xs = None if Xs is None else _cm(Xs)
+    assert Xv is None or Xv.shape == (Kv, M)
+    assert Xs is None or Xs.shape == (Ks, M)
+    return Xv, Xs
+
+
 def forward(Avs, Asv, g, C, dt, V0, S0, nsteps, T=None, ftab=None, n0=0, r=0,
-            threads=0, wavelet=0):
+            threads=0, wavelet=0, xref=None):
     """Leapfrog forward run.  Returns (V, S, traces) as float64 arrays;
     traces is (nsteps // r, R, M) or None when r == 0 or C has no rows.
     `wavelet` selects the source signal of the periods T (0 Ricker, 1 first
-    derivative of a Gaussian)."""
+    derivative of a Gaussian).  `xref` = (Xv, Xs) adds the reduced reference
+    state (Kv x M, Ks x M; either may be None) to the two halves of every
+    step."""
     Avs = _cm(Avs)
     Asv = _cm(Asv)
     Kv, Ks = Avs.shape
@@ -146,18 +163,20 @@ def forward(Avs, Asv, g, C, dt, V0, S0, nsteps, T=None, ftab=None, n0=0, r=0,
     if Fc is not None:
         assert Fc.shape == (nsteps, M)
     nrec = nsteps // r if (r > 0 and R > 0) else 0
+    Xv, Xs = _xref(xref, Kv, Ks, M)
     # records are [rec][m][j] in C: allocate (nrec, M, R) C-order
     tr = np.zeros((nrec, M, R), np.float64) if nrec > 0 else None
     rc = _load().orc_forward(_ptr(Avs), _ptr(Asv), _ptr(g), _ptr(Cm) if R > 0 else None,
                              Kv, Ks, R, float(dt), _ptr(V), _ptr(S), _ptr(Tc), _ptr(Fc),
                              M, int(nsteps), int(n0), int(r) if nrec > 0 else 0,
-                             _ptr(tr), int(threads), int(wavelet))
+                             _ptr(tr), int(threads), int(wavelet), _ptr(Xv), _ptr(Xs))
     _check(rc, "forward")
     traces = None if tr is None else np.ascontiguousarray(tr.transpose(0, 2, 1))
     return np.ascontiguousarray(V), np.ascontiguousarray(S), traces
 
 
-def inverse(Avs, Asv, g, dt, V, S, nsteps, T=None, ftab=None, n0=0, threads=0, wavelet=0):
+def inverse(Avs, Asv, g, dt, V, S, nsteps, T=None, ftab=None, n0=0, threads=0, wavelet=0,
+            xref=None):
     """Undo ``nsteps`` leapfrog steps (time reversal).  Returns (V0, S0)."""
     Avs = _cm(Avs)
     Asv = _cm(Asv)
@@ -168,9 +187,10 @@ def inverse(Avs, Asv, g, dt, V, S, nsteps, T=None, ftab=None, n0=0, threads=0, w
     M = V.shape[1]
     Tc = None if T is None else np.ascontiguousarray(np.asarray(T, np.float64))
     Fc = None if ftab is None else np.ascontiguousarray(np.asarray(ftab, np.float64))
+    Xv, Xs = _xref(xref, Kv, Ks, M)
     rc = _load().orc_inverse(_ptr(Avs), _ptr(Asv), _ptr(g), Kv, Ks, float(dt), _ptr(V),
                              _ptr(S), _ptr(Tc), _ptr(Fc), M, int(nsteps), int(n0),
-                             int(threads), int(wavelet))
+                             int(threads), int(wavelet), _ptr(Xv), _ptr(Xs))
     _check(rc, "inverse")
     return np.ascontiguousarray(V), np.ascontiguousarray(S)
 
@@ -198,9 +218,11 @@ def spectral_radius(Avs, Asv, max_iter=5000, tol=1e-13):
     return float(out.value), int(it)
 
 
-def adjoint(Avs, Asv, g, C, dt, V0, S0, T, nsteps, ystar, n0=0, threads=0, wavelet=0):
+def adjoint(Avs, Asv, g, C, dt, V0, S0, T, nsteps, ystar, n0=0, threads=0, wavelet=0,
+            xref=None):
     """Loss and gradients of sum_n sum_m ||C V_m^n - ystar_m^n||^2.
-    ystar is (nsteps, R, M).  Returns (loss, gV0, gS0, gT)."""
+    ystar is (nsteps, R, M).  Returns (loss, gV0, gS0, gT).  `xref` as in
+    forward (it shifts the forward sweep only)."""
     Avs = _cm(Avs)
     Asv = _cm(Asv)
     Kv, Ks = Avs.shape
@@ -217,10 +239,12 @@ def adjoint(Avs, Asv, g, C, dt, V0, S0, T, nsteps, ystar, n0=0, threads=0, wavel
     gS = np.zeros((Ks, M), order="F")
     gT = np.zeros(M)
     loss = ctypes.c_double(0.0)
+    Xv, Xs = _xref(xref, Kv, Ks, M)
     rc = _load().orc_adjoint(_ptr(Avs), _ptr(Asv), _ptr(g), _ptr(Cm), Kv, Ks, R,
                              float(dt), _ptr(V0), _ptr(S0), _ptr(Tc), M, int(nsteps),
                              int(n0), _ptr(ys), _ptr(gV), _ptr(gS), _ptr(gT),
-                             ctypes.byref(loss), int(threads), int(wavelet))
+                             ctypes.byref(loss), int(threads), int(wavelet),
+                             _ptr(Xv), _ptr(Xs))
     _check(rc, "adjoint")
     return float(loss.value), np.ascontiguousarray(gV), np.ascontiguousarray(gS), gT
 

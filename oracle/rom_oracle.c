@@ -21,6 +21,14 @@
  *       S^{n+1} = S^n + dt  Asv V^{n+1}
  *   with t_n = (n0 + n) dt, forcing sampled at the start of the step.
  *
+ *   Reduced reference state (Eq. (rom_ode), Eq. (rom_ode_tensor)): the
+ *   time-independent term Xhat_ref = Phi^T A X_ref, one column per
+ *   realization, split like the state into Xv (Kv x M) and Xs (Ks x M),
+ *   enters both halves of the step as one more constant forcing:
+ *       V^{n+1} = V^n + dt (Avs S^n + g f(t_n) + Xv)
+ *       S^{n+1} = S^n + dt (Asv V^{n+1} + Xs)
+ *   NULL (the default, and the paper's seismic runs, Sec. 3.1) drops it.
+ *
  *   Point-source forcing (Sec. 2.2, sparse case; Sec. 3.2 signal): the
  *   reduced forcing of realization m is g * f(t; T_m) with the Ricker wavelet
  *       f(t; T) = (1 - 2 u) exp(-u),  u = pi^2 (t - t0)^2 / T^2,  t0 = 1.5 T,
@@ -160,7 +168,8 @@ static double forcing_value(const double* T, const double* ftab, int M, int m,
 int orc_forward(const double* Avs, const double* Asv, const double* g, const double* C,
                 int Kv, int Ks, int R, double dt,
                 double* V, double* S, const double* T, const double* ftab, int M,
-                int nsteps, long n0, int r, double* traces, int nthreads, int wavelet) {
+                int nsteps, long n0, int r, double* traces, int nthreads, int wavelet,
+                const double* Xv, const double* Xs) {
     if (Kv <= 0 || Ks <= 0 || M < 0 || nsteps < 0 || R < 0) return -1;
     if (traces && (r <= 0 || R <= 0 || !C)) return -1;
     orc_set_threads(nthreads);
@@ -178,14 +187,16 @@ int orc_forward(const double* Avs, const double* Asv, const double* g, const dou
             for (int m = 0; m < M; ++m) {
                 double* v = V + (size_t)m * Kv;
                 double* s = S + (size_t)m * Ks;
+                const double* xv = Xv ? Xv + (size_t)m * Kv : NULL;
+                const double* xs = Xs ? Xs + (size_t)m * Ks : NULL;
                 for (int n = 0; n < nsteps; ++n) {
                     const double f = (T || ftab) ? forcing_value(T, ftab, M, m, n, n0, dt, wavelet) : 0.0;
-                    /* velocity first: v <- v + dt (Avs s + g f) */
+                    /* velocity first: v <- v + dt (Avs s + g f + xv) */
                     matvec(Avs, Kv, Ks, s, tv);
-                    for (int i = 0; i < Kv; ++i) v[i] = v[i] + dt * (tv[i] + g[i] * f);
-                    /* then stress with the new velocity: s <- s + dt Asv v */
+                    for (int i = 0; i < Kv; ++i) v[i] = v[i] + dt * (tv[i] + g[i] * f + (xv ? xv[i] : 0.0));
+                    /* then stress with the new velocity: s <- s + dt (Asv v + xs) */
                     matvec(Asv, Ks, Kv, v, ts);
-                    for (int i = 0; i < Ks; ++i) s[i] = s[i] + dt * ts[i];
+                    for (int i = 0; i < Ks; ++i) s[i] = s[i] + dt * (ts[i] + (xs ? xs[i] : 0.0));
                     if (traces && ((n + 1) % r) == 0) {
                         const int rec = (n + 1) / r - 1;
                         matvec(C, R, Kv, v, ty);
@@ -205,12 +216,12 @@ int orc_forward(const double* Avs, const double* Asv, const double* g, const dou
 /*
  * Inverse leapfrog: undoes orc_forward step by step (time reversibility,
  * Sec. 3.1).  Step n (taken from n = nsteps-1 down to 0) applies
- *   S^n = S^{n+1} - dt Asv V^{n+1},   V^n = V^{n+1} - dt (Avs S^n + g f(t_n)).
+ *   S^n = S^{n+1} - dt (Asv V^{n+1} + Xs),   V^n = V^{n+1} - dt (Avs S^n + g f(t_n) + Xv).
  */
 int orc_inverse(const double* Avs, const double* Asv, const double* g,
                 int Kv, int Ks, double dt, double* V, double* S,
                 const double* T, const double* ftab, int M, int nsteps, long n0,
-                int nthreads, int wavelet) {
+                int nthreads, int wavelet, const double* Xv, const double* Xs) {
     if (Kv <= 0 || Ks <= 0 || M < 0 || nsteps < 0) return -1;
     orc_set_threads(nthreads);
     int err = 0;
@@ -226,12 +237,14 @@ int orc_inverse(const double* Avs, const double* Asv, const double* g,
             for (int m = 0; m < M; ++m) {
                 double* v = V + (size_t)m * Kv;
                 double* s = S + (size_t)m * Ks;
+                const double* xv = Xv ? Xv + (size_t)m * Kv : NULL;
+                const double* xs = Xs ? Xs + (size_t)m * Ks : NULL;
                 for (int n = nsteps - 1; n >= 0; --n) {
                     const double f = (T || ftab) ? forcing_value(T, ftab, M, m, n, n0, dt, wavelet) : 0.0;
                     matvec(Asv, Ks, Kv, v, ts);
-                    for (int i = 0; i < Ks; ++i) s[i] = s[i] - dt * ts[i];
+                    for (int i = 0; i < Ks; ++i) s[i] = s[i] - dt * (ts[i] + (xs ? xs[i] : 0.0));
                     matvec(Avs, Kv, Ks, s, tv);
-                    for (int i = 0; i < Kv; ++i) v[i] = v[i] - dt * (tv[i] + g[i] * f);
+                    for (int i = 0; i < Kv; ++i) v[i] = v[i] - dt * (tv[i] + g[i] * f + (xv ? xv[i] : 0.0));
                 }
             }
         }
@@ -324,6 +337,9 @@ int orc_spectral_radius(const double* Avs, const double* Asv, int Kv, int Ks,
  *   dL/dV0 = lamV, dL/dS0 = lamS,  dL/dT_m = sum_n dL/df_n df/dT(t_n; T_m).
  *
  * Per column it stores the N residuals C V^n - y^n (N x R doubles).
+ * The reference-state term Xv, Xs (may be NULL) shifts the forward sweep
+ * only: it depends on neither the state nor T, so the reverse recurrence
+ * above is unchanged.
  * gV0, gS0, gT may be NULL.  *loss receives L.  Returns 0 or negative.
  */
 int orc_adjoint(const double* Avs, const double* Asv, const double* g, const double* C,
@@ -331,7 +347,7 @@ int orc_adjoint(const double* Avs, const double* Asv, const double* g, const dou
                 const double* V0, const double* S0, const double* T, int M,
                 int nsteps, long n0, const double* ystar,
                 double* gV0, double* gS0, double* gT, double* loss, int nthreads,
-                int wavelet) {
+                int wavelet, const double* Xv, const double* Xs) {
     if (Kv <= 0 || Ks <= 0 || R <= 0 || M < 0 || nsteps < 0 || !C || !ystar || !T) return -1;
     orc_set_threads(nthreads);
     int err = 0;
@@ -358,12 +374,14 @@ int orc_adjoint(const double* Avs, const double* Asv, const double* g, const dou
                 memcpy(v, V0 + (size_t)m * Kv, sizeof(double) * (size_t)Kv);
                 memcpy(s, S0 + (size_t)m * Ks, sizeof(double) * (size_t)Ks);
                 double lm = 0.0;
+                const double* xv = Xv ? Xv + (size_t)m * Kv : NULL;
+                const double* xs = Xs ? Xs + (size_t)m * Ks : NULL;
                 for (int n = 0; n < nsteps; ++n) {
                     const double f = wavelet_f(wavelet, (double)(n0 + n) * dt, T[m]);
                     matvec(Avs, Kv, Ks, s, tv);
-                    for (int i = 0; i < Kv; ++i) v[i] = v[i] + dt * (tv[i] + g[i] * f);
+                    for (int i = 0; i < Kv; ++i) v[i] = v[i] + dt * (tv[i] + g[i] * f + (xv ? xv[i] : 0.0));
                     matvec(Asv, Ks, Kv, v, ts);
-                    for (int i = 0; i < Ks; ++i) s[i] = s[i] + dt * ts[i];
+                    for (int i = 0; i < Ks; ++i) s[i] = s[i] + dt * (ts[i] + (xs ? xs[i] : 0.0));
                     matvec(C, R, Kv, v, ty);
                     const double* yst = ystar + ((size_t)n * M + m) * R;
                     double* rn = res + (size_t)n * R;

@@ -109,6 +109,68 @@ def test_closed_form_eig(K, M, N, skew):
     assert rel(np.vstack([V, S]), X) < 1e-10
 
 
+def _xref_case(Kv, Ks, M, seed):
+    rng = np.random.default_rng(seed)
+    p = inputs.make_problem(Kv, Ks, M, 0, seed=seed)
+    Xv = rng.standard_normal((Kv, M))
+    Xs = rng.standard_normal((Ks, M))
+    return p, rng, Xv, Xs
+
+
+@pytest.mark.parametrize("Kv,Ks,M,N", [(1, 1, 2, 300), (5, 4, 3, 250), (8, 8, 2, 400)])
+def test_reference_state_closed_form(Kv, Ks, M, N):
+    """Reduced reference state (Eq. (rom_ode_tensor)): a constant term per
+    column in both halves.  With it one step is X^{n+1} = G X^n + b f_n + h,
+    h = [dt Xv; dt^2 Asv Xv + dt Xs], so X^N = G^N X0 + sum_n G^{N-1-n} b f_n
+    + (sum_{i<N} G^i) h.  The last sum is taken per eigenvalue of G."""
+    p, rng, Xv, Xs = _xref_case(Kv, Ks, M, 60 + Kv)
+    Avs, Asv, dt = p.Avs.astype(np.float64), p.Asv.astype(np.float64), p.dt
+    V0 = rng.standard_normal((Kv, M))
+    S0 = rng.standard_normal((Ks, M))
+    ftab = rng.standard_normal((N, M))
+    V, S, _ = oracle.forward(Avs, Asv, p.g, None, dt, V0, S0, N, ftab=ftab, xref=(Xv, Xs))
+    G, b = amplification(Avs, Asv, p.g.astype(np.float64), dt)
+    X = eig_solution(G, b, np.vstack([V0, S0]), ftab)
+    H = np.vstack([dt * Xv, dt * dt * Asv @ Xv + dt * Xs])
+    lam, P = np.linalg.eig(G)
+    geo = (lam[:, None] ** np.arange(N)[None, :]).sum(axis=1)  # sum_{i<N} lam^i
+    X = X + (P @ (geo[:, None] * (np.linalg.inv(P) @ H.astype(np.complex128)))).real
+    assert rel(np.vstack([V, S]), X) < 1e-10
+
+
+def test_reference_state_fixed_point():
+    """With Xv = -Avs S* and Xs = -Asv V*, (V*, S*) is a fixed point of the
+    unforced step: the state must not move (to FP64 rounding)."""
+    Kv, Ks, M = 40, 32, 3
+    p, rng, _, _ = _xref_case(Kv, Ks, M, 71)
+    Vs = rng.standard_normal((Kv, M))
+    Ss = rng.standard_normal((Ks, M))
+    Xv = -p.Avs.astype(np.float64) @ Ss
+    Xs = -p.Asv.astype(np.float64) @ Vs
+    V, S, _ = oracle.forward(p.Avs, p.Asv, p.g, None, p.dt, Vs, Ss, 500, xref=(Xv, Xs))
+    assert rel(V, Vs) < 1e-13 and rel(S, Ss) < 1e-13
+    # one of the two terms alone moves it
+    V1, S1, _ = oracle.forward(p.Avs, p.Asv, p.g, None, p.dt, Vs, Ss, 5, xref=(Xv, None))
+    assert rel(np.vstack([V1, S1]), np.vstack([Vs, Ss])) > 1e-6
+
+
+def test_reference_state_time_reversal_and_superposition():
+    """The step with the constant term stays reversible, and the response is
+    linear: Run(X0, f, Xref) = Run(X0, f, 0) + Run(0, 0, Xref)."""
+    Kv, Ks, M, N = 24, 20, 3, 300
+    p, rng, Xv, Xs = _xref_case(Kv, Ks, M, 72)
+    V0 = rng.standard_normal((Kv, M))
+    S0 = rng.standard_normal((Ks, M))
+    T = p.T.astype(np.float64)
+    V, S, _ = oracle.forward(p.Avs, p.Asv, p.g, None, p.dt, V0, S0, N, T=T, xref=(Xv, Xs))
+    Vb, Sb = oracle.inverse(p.Avs, p.Asv, p.g, p.dt, V, S, N, T=T, xref=(Xv, Xs))
+    assert rel(Vb, V0) < 1e-10 and rel(Sb, S0) < 1e-10
+    Va, Sa, _ = oracle.forward(p.Avs, p.Asv, p.g, None, p.dt, V0, S0, N, T=T)
+    Vr, Sr, _ = oracle.forward(p.Avs, p.Asv, p.g, None, p.dt, np.zeros((Kv, M)),
+                               np.zeros((Ks, M)), N, xref=(Xv, Xs))
+    assert rel(V, Va + Vr) < 1e-12 and rel(S, Sa + Sr) < 1e-12
+
+
 def test_k1_textbook_oscillator():
     """K = 1 with Avs = -a/dt, Asv = a/dt: the step matrix is
     G = [[1, -a], [a, 1 - a^2]] (det 1, cos theta = 1 - a^2/2) and
@@ -321,6 +383,38 @@ def test_adjoint_vs_central_difference():
         e = np.zeros_like(T)
         e[m] = 1e-3
         fdT = (_loss(p, V0, S0, T + e, N, ystar) - _loss(p, V0, S0, T - e, N, ystar)) / 2e-3
+        assert abs(fdT - gT[m]) <= 1e-4 * max(abs(gT[m]), 1e-12) + 1e-9
+
+
+def test_adjoint_with_reference_state_vs_central_difference():
+    """The reference-state term shifts the forward sweep; the adjoint's
+    gradients with respect to (V0, S0) and T must still match central
+    differences of the misfit of runs that carry the same term."""
+    p, V0, S0, ystar = _adjoint_case(K=5, M=2, N=150, R=2, seed=37)
+    N = ystar.shape[0]
+    T = p.T.astype(np.float64)
+    rng = np.random.default_rng(9)
+    xref = (0.05 * rng.standard_normal(V0.shape), 0.05 * rng.standard_normal(S0.shape))
+
+    def loss(V0_, S0_, T_):
+        _, _, tr = oracle.forward(p.Avs, p.Asv, p.g, p.C, p.dt, V0_, S0_, N, T=T_, r=1,
+                                  xref=xref)
+        return float(np.sum((tr - ystar) ** 2))
+
+    L, gV, gS, gT = oracle.adjoint(p.Avs, p.Asv, p.g, p.C, p.dt, V0, S0, T, N, ystar, xref=xref)
+    assert abs(L - loss(V0, S0, T)) <= 1e-12 * L
+    L0, gV0, _, _ = oracle.adjoint(p.Avs, p.Asv, p.g, p.C, p.dt, V0, S0, T, N, ystar)
+    assert abs(L - L0) > 1e-6 * L0 and rel(gV, gV0) > 1e-6  # the term matters here
+    dV = rng.standard_normal(V0.shape)
+    dS = rng.standard_normal(S0.shape)
+    h = 1e-3
+    fd = (loss(V0 + h * dV, S0 + h * dS, T) - loss(V0 - h * dV, S0 - h * dS, T)) / (2 * h)
+    an = float(np.sum(gV * dV) + np.sum(gS * dS))
+    assert abs(fd - an) <= 1e-8 * abs(an)
+    for m in range(T.size):
+        e = np.zeros_like(T)
+        e[m] = 1e-3
+        fdT = (loss(V0, S0, T + e) - loss(V0, S0, T - e)) / 2e-3
         assert abs(fdT - gT[m]) <= 1e-4 * max(abs(gT[m]), 1e-12) + 1e-9
 
 
