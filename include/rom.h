@@ -176,6 +176,23 @@ enum { ROM_WAVELET_RICKER = 0, ROM_WAVELET_GAUSS1 = 1 };
 rom_status rom_set_wavelet(rom_t h, int wavelet);
 
 /*
+ * rom_set_reference -- the reduced reference state of Eq. (rom_ode) and
+ * Eq. (rom_ode_tensor), Xhat_ref = Phi^T A X_ref: a time-independent term, one
+ * column per realization, split like the state into Xv (Kv x M) and Xs
+ * (Ks x M), column-major, FP64 or FP32 (in_dtype), host or device.  Later
+ * runs on this handle add it to both halves of every leapfrog step,
+ *     V += dt (Avs S + g f + Xv),   S += dt (Asv V + Xs),
+ * on every path (rank-2 in every precision, the rank-1 runs with M = 1, the
+ * ensemble, the batched launch, and the forward and recomputed sweeps of the
+ * adjoint, whose reverse sweep the constant does not change).  Either part
+ * may be NULL (zero); both NULL clears it (the default, and the paper's
+ * seismic runs, Sec. 3.1).  The data is copied; the caller may free it on
+ * return.  A run over a number of columns other than M returns
+ * ROM_E_INVAL.  Synchronous.  Errors: ROM_E_INVAL, ROM_E_NOMEM, ROM_E_CUDA.
+ */
+rom_status rom_set_reference(rom_t h, const void* Xv, const void* Xs, int M, int in_dtype);
+
+/*
  * rom_set_tc_columns -- columns per cluster block of the tensor-core path:
  * 64 or 128 for ROM_TF32X3 / ROM_BF16X3 / ROM_BF16, 32, 48, 64 or 80 for
  * ROM_BF16S, or 0 to let the planner choose (default).  Wider blocks re-read

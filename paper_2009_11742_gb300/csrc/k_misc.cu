@@ -32,7 +32,9 @@ __host__ __device__ inline int ens_ksplit(int NT, int Kp) {
     return ks < 1 ? 1 : (ks > kEnsMaxSplit ? kEnsMaxSplit : ks);
 }
 
-template <typename T, int NT>
+// XR: add the reduced reference state (a template flag, so that runs without
+// it compile to the code they had without it).
+template <typename T, int NT, bool XR>
 __global__ void __launch_bounds__(NT, 1024 / NT) rank1_ensemble_kernel(const Rank1EnsArgs a) {
     const int m = blockIdx.x;
     const int Kp = a.Kp;
@@ -58,6 +60,9 @@ __global__ void __launch_bounds__(NT, 1024 / NT) rank1_ensemble_kernel(const Ran
     const T* __restrict__ Cc = static_cast<const T*>(a.C_cm);
     const T Tm = a.Tper ? static_cast<const T*>(a.Tper)[m] : T(1);
     const T dt = (T)a.dt;
+    // reduced reference state (velocity, stress parts) or null
+    const T* XrV = static_cast<const T*>(a.Xv);
+    const T* XrS = static_cast<const T*>(a.Xs);
     float cv[4] = {0.f, 0.f, 0.f, 0.f}, cs[4] = {0.f, 0.f, 0.f, 0.f};
     T* traces = static_cast<T*>(a.traces);
     __syncthreads();
@@ -89,6 +94,11 @@ __global__ void __launch_bounds__(NT, 1024 / NT) rank1_ensemble_kernel(const Ran
                     T tot = part[row];
                     for (int k2 = 1; k2 < KS; ++k2) tot += part[(size_t)k2 * Kp + row];
                     if (half == 0) tot += gp[row] * f;
+                    if constexpr (XR) {
+                        const T* xh = half == 0 ? XrV : XrS;
+                        const int kh = half == 0 ? a.Kv : a.Ks;
+                        if (xh && row < kh) tot += xh[(size_t)m * kh + row];
+                    }
                     const T inc = tot * dt;
                     if constexpr (sizeof(T) == 4) {
                         y[row] = kahan_add(y[row], inc, half == 0 ? cv[q] : cs[q]);
@@ -123,7 +133,7 @@ template <typename T, int NT>
 static cudaError_t launch_ens_nt(const Rank1EnsArgs& a, cudaStream_t st) {
     const int KS = ens_ksplit(NT, a.Kp);
     const size_t smem = sizeof(T) * (size_t)(2 * a.Kp + KS * a.Kp);
-    auto fn = rank1_ensemble_kernel<T, NT>;
+    auto fn = (a.Xv || a.Xs) ? rank1_ensemble_kernel<T, NT, true> : rank1_ensemble_kernel<T, NT, false>;
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     fn<<<a.M, NT, smem, st>>>(a);

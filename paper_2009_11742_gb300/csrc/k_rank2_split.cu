@@ -8,10 +8,14 @@
 
 namespace romk {
 
+// xr: the split kernel instance that adds the reduced reference state (the
+// dataflow kernel tests for it at run time).
 template <bool DF>
-static void* two_block_kernel(int KI) {
-#define ROM_TB_CASE(k) \
-    case k: return DF ? (void*)&rank2_dataflow_kernel<k> : (void*)&rank2_split_kernel<k>;
+static void* two_block_kernel(int KI, bool xr = false) {
+#define ROM_TB_CASE(k)                                                   \
+    case k:                                                              \
+        return DF ? (void*)&rank2_dataflow_kernel<k>                     \
+                  : (xr ? (void*)&rank2_split_kernel<k, true> : (void*)&rank2_split_kernel<k, false>);
     switch (KI) {
         ROM_TB_CASE(1) ROM_TB_CASE(2) ROM_TB_CASE(3) ROM_TB_CASE(4)
         ROM_TB_CASE(5) ROM_TB_CASE(6) ROM_TB_CASE(7) ROM_TB_CASE(8)
@@ -83,7 +87,7 @@ static cudaError_t launch_two_block(const Rank2Args& a_in, const Rank2Plan& p, c
     a.Wa = p.Wa;
     const int H = p.cs / 2;
     a.rpc = (a.R + H - 1) / H;
-    void* fn = two_block_kernel<DF>(p.KI);
+    void* fn = two_block_kernel<DF>(p.KI, a.Xv != nullptr || a.Xs != nullptr);
     if (!fn) return cudaErrorInvalidValue;
     cudaError_t e = prepare_kernel<float>(fn, p.smem);
     if (e != cudaSuccess) return e;

@@ -170,12 +170,13 @@ int tc_exchange_terms(int prec) {
 }
 int tc_element_bytes(int prec) { return prec == ROM_TF32X3 ? 4 : 2; }
 
-static void* tcs_kernel(int W) {
+// xr: the instance that adds the reduced reference state.
+static void* tcs_kernel(int W, bool xr = false) {
     switch (W) {
-        case 32: return (void*)&rank2_tcs_kernel<32>;
-        case 48: return (void*)&rank2_tcs_kernel<48>;
-        case 64: return (void*)&rank2_tcs_kernel<64>;
-        case 80: return (void*)&rank2_tcs_kernel<80>;
+        case 32: return xr ? (void*)&rank2_tcs_kernel<32, true> : (void*)&rank2_tcs_kernel<32, false>;
+        case 48: return xr ? (void*)&rank2_tcs_kernel<48, true> : (void*)&rank2_tcs_kernel<48, false>;
+        case 64: return xr ? (void*)&rank2_tcs_kernel<64, true> : (void*)&rank2_tcs_kernel<64, false>;
+        case 80: return xr ? (void*)&rank2_tcs_kernel<80, true> : (void*)&rank2_tcs_kernel<80, false>;
         default: return nullptr;
     }
 }
@@ -288,13 +289,24 @@ bool plan_rank2_tc(int prec, int Kp, int M, int R, int Wforce, TcPlan* p) {
 }
 
 cudaError_t launch_rank2_tc(const TcArgs& a_in, const TcPlan& p, cudaStream_t st) {
-    void* fn = p.prec == ROM_BF16S ? tcs_kernel(p.W) : tc_kernel_for(p.prec, p.W);
+    const bool xr = a_in.Xv != nullptr || a_in.Xs != nullptr;
+    void* fn = p.prec == ROM_BF16S ? tcs_kernel(p.W, xr) : tc_kernel_for(p.prec, p.W);
     if (!fn) return cudaErrorInvalidValue;
     TcArgs a = a_in;
     a.W = p.W;
     a.stages = p.stages;
     a.rpc = p.rpc;
-    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem);
+    size_t smem = p.smem;
+    if (p.prec == ROM_BF16S && xr) {
+        // room for the reference-state staging: fewer stages if needed
+        const size_t smax = (size_t)device_smem_optin();
+        int s = p.stages;
+        while (s > 2 && tcs_smem_bytes(p.W, s) + tcs_xref_bytes(p.W) > smax) --s;
+        smem = tcs_smem_bytes(p.W, s) + tcs_xref_bytes(p.W);
+        if (smem > smax) return cudaErrorInvalidValue;
+        a.stages = s;
+    }
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     if (e != cudaSuccess) return e;
@@ -306,7 +318,7 @@ cudaError_t launch_rank2_tc(const TcArgs& a_in, const TcPlan& p, cudaStream_t st
     attr[0].val.clusterDim.z = 1;
     cfg.gridDim = dim3(p.cs * p.nclusters, 1, 1);
     cfg.blockDim = dim3(p.prec == ROM_BF16S ? kTcsThreads : kTcThreads, 1, 1);
-    cfg.dynamicSmemBytes = p.smem;
+    cfg.dynamicSmemBytes = smem;
     cfg.stream = st;
     cfg.attrs = attr;
     cfg.numAttrs = 1;

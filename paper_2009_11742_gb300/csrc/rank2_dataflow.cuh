@@ -234,6 +234,7 @@ __global__ void __launch_bounds__(kThreads, 1) rank2_dataflow_kernel(const Rank2
     const int N = a.nsteps;
     const int nphase = 2 * N + 1;
     const bool stall_test = a.debug_skip_push && crank == 0;
+    const float* Xrole = static_cast<const float*>(vrole ? a.Xv : a.Xs);  // reference state or null
     for (int p = 0; p < nphase; ++p) {
         int b, n;
         if (vrole) { b = p & 1; n = (p - b) >> 1; }
@@ -265,6 +266,13 @@ __global__ void __launch_bounds__(kThreads, 1) rank2_dataflow_kernel(const Rank2
         }
         for (int g = 0; g < G; ++g) {
             const int c0 = g * CB;
+            // this lane's reference-state value, fetched before the products
+            float xr = 0.f;
+            if (Xrole) {
+                const int si = rs16_slot<4 * CB>(j);
+                const int rl = 4 * q + si / CB, c = c0 + si % CB;
+                if (c < ncol(b) && row0 + rl < Kown) xr = Xrole[(size_t)(gc0(b) + c) * Kown + row0 + rl];
+            }
             // ---- products of this group
             float acc[4][CB];
 #pragma unroll
@@ -329,6 +337,7 @@ __global__ void __launch_bounds__(kThreads, 1) rank2_dataflow_kernel(const Rank2
                 f = __shfl_sync(0xffffffffu, f, vi % CB);
                 inc = __fmaf_rn(gown[rl], f, inc);
             }
+            if (Xrole) inc = inc + xr;
             inc = inc * dt;
             float* yp = ownb + c * kOwnStride + rl;
             *yp = kahan_add(*yp, inc, compb[c * kOwnStride + rl]);

@@ -56,6 +56,20 @@ __host__ __device__ inline Rank2Smem rank2_smem_layout(int Wa, int Kp, int rpc, 
     return s;
 }
 
+// The value index reduce_scatter16<T, NV> leaves with lane chunk j (the same
+// stage rule, without the data), so that a lane can fetch what its epilogue
+// needs before the products.
+template <int NV>
+__device__ __forceinline__ int rs16_slot(int j) {
+    int base = 0;
+#pragma unroll
+    for (int s = 0; s < 4; ++s) {
+        const int n = NV >> s;
+        if (n > 1 && (j & (8 >> s))) base += n / 2;
+    }
+    return base;
+}
+
 __device__ __forceinline__ float fmadd(float a, float b, float c) { return __fmaf_rn(a, b, c); }
 __device__ __forceinline__ double fmadd(double a, double b, double c) { return __fma_rn(a, b, c); }
 
@@ -182,6 +196,31 @@ __device__ __forceinline__ T forcing_at(const Rank2Args& a, const T* Tcol, int c
     return (T)wavelet_eval(a.wavelet, (long long)a.n0 + n, a.dt, Tcol[c]);
 }
 
+// The reduced reference state's share of a half-step on the CTA's own rows:
+// Y_own += dt Xref, with the same Kahan carries (FP32), as a pass after the
+// products (Xref: the block's first column, Krows x columns).  Used only when
+// the term is given, so the product loop above is the same with or without it.
+template <typename T>
+__device__ __forceinline__ void add_reference(T* __restrict__ Y, float* __restrict__ comp,
+                                              const T* __restrict__ Xref, const int Krows,
+                                              const int ncol, const T dt, const int Wa,
+                                              const int Kp, const int row0, const int nrt) {
+    for (int idx = threadIdx.x; idx < nrt * ncol * kRowsPerCta; idx += kThreads) {
+        const int rt = idx / (ncol * kRowsPerCta);
+        const int rem = idx - rt * ncol * kRowsPerCta;
+        const int c = rem / kRowsPerCta, rl = rem % kRowsPerCta;
+        const int row = row0 + rt * kRowsPerCta + rl;
+        if (row >= Krows) continue;
+        const T inc = Xref[(size_t)c * Krows + row] * dt;
+        T* yp = Y + (size_t)c * Kp + row;
+        if constexpr (sizeof(T) == 4) {
+            *yp = kahan_add(*yp, inc, comp[(size_t)rt * Wa * kRowsPerCta + c * kRowsPerCta + rl]);
+        } else {
+            *yp = *yp + inc;
+        }
+    }
+}
+
 template <typename T, int KI, int CB, bool RESIDENT>
 __global__ void __launch_bounds__(kThreads, 1) rank2_simt_kernel(const Rank2Args a) {
     cg::cluster_group cluster = cg::this_cluster();
@@ -258,23 +297,34 @@ __global__ void __launch_bounds__(kThreads, 1) rank2_simt_kernel(const Rank2Args
 
     T* traces = static_cast<T*>(a.traces);
     for (int n = 0; n < a.nsteps; ++n) {
-        // ---- velocity half-step: V_own += dt (Avs_own S + g f_n^T)
+        // ---- velocity half-step: V_own += dt (Avs_own S + g f_n^T [+ Xv])
         for (int rt = 0; rt < nrt; ++rt) {
             const int rowt = row0 + rt * kRowsPerCta;
             if (!RESIDENT) load_op_rows<T, KI>(opA, Avs, Kp, rowt + 2 * rp, j);
             half_step<T, KI, CB, true>(opA, Sf, Vf, cV + rt * Wa * kRowsPerCta, gown + rt * kRowsPerCta,
                                        fcol, dt, Wa, Kp, rowt, rp, j);
         }
+        if (a.Xv) {  // kernel parameters, read where used: no register held across the loop
+            __syncthreads();
+            add_reference<T>(Vf, cV, static_cast<const T*>(a.Xv) + (size_t)(a.col_base + col0) * a.Kv,
+                             a.Kv, ncol, dt, Wa, Kp, row0, nrt);
+        }
         __syncthreads();
         push_own_rows<T>(cluster, Vf, Wa, Kp, row0, cs, crank, nrt);
         cluster.sync();
 
-        // ---- stress half-step with the new velocity: S_own += dt Asv_own V
+        // ---- stress half-step with the new velocity: S_own += dt (Asv_own V [+ Xs])
         for (int rt = 0; rt < nrt; ++rt) {
             const int rowt = row0 + rt * kRowsPerCta;
             if (!RESIDENT) load_op_rows<T, KI>(opB, Asv, Kp, rowt + 2 * rp, j);
             half_step<T, KI, CB, false>(opB, Vf, Sf, cS + rt * Wa * kRowsPerCta, gown, fcol, dt, Wa, Kp,
                                         rowt, rp, j);
+        }
+        if (a.Xs) {
+            __syncthreads();
+            add_reference<T>(Sf, cS, static_cast<const T*>(a.Xs) + (size_t)(a.col_base + col0) * a.Ks,
+                             a.Ks, ncol, dt, Wa, Kp, row0, nrt);
+            __syncthreads();
         }
 
         // ---- receiver traces y = C V^{n+1} (this CTA's rows of C)

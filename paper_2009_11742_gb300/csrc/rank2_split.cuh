@@ -77,9 +77,13 @@ __device__ __forceinline__ void load_op_quad(float (&op)[4][4 * KI], const float
     }
 }
 
-// One phase of one role on block b: own rows += dt (op . X_b [+ g f^T]),
+// One phase of one role on block b: own rows += dt (op . X_b [+ g f^T] [+ Xref]),
 // pushing every finished 8 x 4 warp tile to the H peer CTAs of the other role.
-template <int KI, bool FORCED>
+// With XR, Xref points at block b's first column of the role's reduced
+// reference state (Krows x columns); each lane fetches its epilogue's value
+// before the products.  XR is a template flag so that runs without the term
+// compile to exactly the code they had without it.
+template <int KI, bool FORCED, bool XR>
 __device__ __forceinline__ void split_phase(cg::cluster_group& cluster, const float (&op)[4][4 * KI],
                                             const float* __restrict__ X, float* __restrict__ own,
                                             float* __restrict__ comp, const float* __restrict__ gown,
@@ -87,9 +91,17 @@ __device__ __forceinline__ void split_phase(cg::cluster_group& cluster, const fl
                                             const float dt, const int Wa, const int Kp,
                                             const int row0, const int H, const int peer0,
                                             const int q, const int j, const int warp,
-                                            const int lane) {
+                                            const int lane, const float* __restrict__ Xref,
+                                            const int Krows, const int ncol) {
     constexpr int CB = kSplitCB;
     for (int c0 = 0; c0 < Wa; c0 += CB) {
+        float xr = 0.f;
+        if constexpr (XR) {
+            // Xref is null for a role whose part of the term is not given
+            const int si = rs16_slot<4 * CB>(j);
+            const int rl = 4 * q + si / CB, c = c0 + si % CB;
+            if (Xref && c < ncol && row0 + rl < Krows) xr = Xref[(size_t)c * Krows + row0 + rl];
+        }
         float acc[4][CB];
 #pragma unroll
         for (int r = 0; r < 4; ++r)
@@ -121,6 +133,7 @@ __device__ __forceinline__ void split_phase(cg::cluster_group& cluster, const fl
             const int c = c0 + vi % CB;
             float inc = tot;
             if (FORCED) inc = __fmaf_rn(gown[rl], fcol[c], inc);
+            if constexpr (XR) inc = inc + xr;
             inc = inc * dt;
             float* yp = own + c * kOwnStride + rl;
             *yp = kahan_add(*yp, inc, comp[c * kOwnStride + rl]);
@@ -142,7 +155,7 @@ __device__ __forceinline__ void split_phase(cg::cluster_group& cluster, const fl
     }
 }
 
-template <int KI>
+template <int KI, bool XR>
 __global__ void __launch_bounds__(kThreads, 1) rank2_split_kernel(const Rank2Args a) {
     cg::cluster_group cluster = cg::this_cluster();
     const int cs = (int)cluster.num_blocks();
@@ -234,6 +247,7 @@ __global__ void __launch_bounds__(kThreads, 1) rank2_split_kernel(const Rank2Arg
     cluster.sync();
 
     float* traces = static_cast<float*>(a.traces);
+    const float* Xrole = static_cast<const float*>(vrole ? a.Xv : a.Xs);
     const int N = a.nsteps;
     const int nphase = 2 * N + 1;
     for (int p = 0; p < nphase; ++p) {
@@ -245,12 +259,13 @@ __global__ void __launch_bounds__(kThreads, 1) rank2_split_kernel(const Rank2Arg
             float* Xb = X + (size_t)b * Wa * Kp;
             float* ownb = own + (size_t)b * Wa * kOwnStride;
             float* compb = comp + (size_t)b * Wa * kOwnStride;
+            const float* Xr = Xrole ? Xrole + (size_t)gc0(b) * Kown : nullptr;
             if (vrole) {
-                split_phase<KI, true>(cluster, op, Xb, ownb, compb, gown, fcol + b * Wa, Xb, dt, Wa,
-                                      Kp, row0, H, peer0, q, j, warp, lane);
+                split_phase<KI, true, XR>(cluster, op, Xb, ownb, compb, gown, fcol + b * Wa, Xb, dt, Wa,
+                                          Kp, row0, H, peer0, q, j, warp, lane, Xr, Kown, ncol(b));
             } else {
-                split_phase<KI, false>(cluster, op, Xb, ownb, compb, gown, fcol, Xb, dt, Wa, Kp,
-                                       row0, H, peer0, q, j, warp, lane);
+                split_phase<KI, false, XR>(cluster, op, Xb, ownb, compb, gown, fcol, Xb, dt, Wa, Kp,
+                                           row0, H, peer0, q, j, warp, lane, Xr, Kown, ncol(b));
                 // receiver traces of V^{n+1} (the full new V of block b is in Xb)
                 if (traces && ((n + 1) % a.r) == 0) {
                     const int rec = (n + 1) / a.r - 1;

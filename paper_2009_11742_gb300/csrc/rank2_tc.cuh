@@ -296,6 +296,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) rank2_tc_kernel(const TcArgs a)
                 const int Kown = half == 0 ? a.Kv : a.Ks;
                 float* Y = half == 0 ? a.V : a.S;
                 float* Cy = half == 0 ? a.compV : a.compS;
+                const float* Xref = half == 0 ? a.Xv : a.Xs;  // reduced reference state or null
                 unsigned char* Xdst = half ? Xblk0 : Xblk1;  // V feeds the S half and vice versa
 #pragma unroll
                 for (int i = 0; i < WH; ++i) {
@@ -305,6 +306,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) rank2_tc_kernel(const TcArgs a)
                         const size_t gi = (size_t)(col0 + j) * Kown + row;
                         float inc = acc[i];
                         if (half == 0) inc = __fmaf_rn(grow[rl], fcol[j], inc);
+                        if (Xref) inc = inc + Xref[gi];
                         inc = inc * dt;
                         float cc = Cy[gi];
                         y = kahan_add(Y[gi], inc, cc);

@@ -197,11 +197,29 @@ __device__ __forceinline__ unsigned colmax8(unsigned (&v)[8], int lane, int& col
     return v[0];
 }
 
+// 4-byte asynchronous global -> shared copy (zero fill when src_bytes is 0),
+// and the wait for all of this thread's outstanding ones.
+__device__ __forceinline__ void cp_async4(void* sdst, const void* gsrc, int src_bytes) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;"
+                 ::"r"(cvta_shared(sdst)), "l"(gsrc), "r"(src_bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+    asm volatile("cp.async.wait_all;" ::: "memory");
+}
+
+// Shared memory for the reduced reference state of one half-step: WH values
+// per reader thread, [WH][256] so that a warp's accesses are consecutive.
+__host__ __device__ inline size_t tcs_xref_bytes(int W) {
+    return (size_t)(W / 2) * kTcsThreads * 4;
+}
+
 __device__ __forceinline__ void reader_bar_sync() {
     asm volatile("bar.sync 1, %0;" ::"r"(kTcsThreads) : "memory");
 }
 
-template <int W>
+// XR: add the reduced reference state (a template flag, so that runs without
+// it compile to the code they had without it).
+template <int W, bool XR>
 __global__ void __launch_bounds__(kTcsThreads, 1) rank2_tcs_kernel(const TcArgs a) {
     constexpr int WH = W / 2;                       // columns per readout warp
     constexpr int AST = tcs_acc_stride(W);          // accumulator column stride
@@ -253,6 +271,7 @@ __global__ void __launch_bounds__(kTcsThreads, 1) rank2_tcs_kernel(const TcArgs 
     float* arow = grow + kTcRows;                   // [2][128]: 2^(eA_r - 7) of Avs, Asv
     unsigned* colmax = reinterpret_cast<unsigned*>(arow + 2 * kTcRows);  // [4][W] |y| bits
     float* gmax = reinterpret_cast<float*>(colmax + 4 * W);             // [CS][W]
+    float* xst = gmax + (size_t)kTcsMaxCS * W;  // [WH][256] reference state (only when given)
     float* Ys = reinterpret_cast<float*>(smem);                         // trace scratch (stage ring)
     float* Cs = Ys + (size_t)W * kTcsTStride;
     float* Pt = Cs + (size_t)kTcsTraceR * kTcsTStride;
@@ -346,6 +365,18 @@ __global__ void __launch_bounds__(kTcsThreads, 1) rank2_tcs_kernel(const TcArgs 
             float ya[8], ca[8], yb[8], cb[8];
             load_group8(Y, Cy, Kown, col0 + jbase, ncol - jbase, rowok, ya, ca);
             if (NG > 1) load_group8(Y, Cy, Kown, col0 + jbase + 8, ncol - jbase - 8, rowok, yb, cb);
+            // this thread's values of the reduced reference state, copied
+            // asynchronously while the products run (no registers, no stall)
+            const float* Xref = half == 0 ? a.Xv : a.Xs;
+            if (XR && Xref) {
+#pragma unroll 1
+                for (int i = 0; i < WH; ++i) {
+                    const int j = jbase + i;
+                    const bool ok = rowok && j < ncol;
+                    cp_async4(xst + (size_t)i * kTcsThreads + ridx,
+                              ok ? Xref + (size_t)(col0 + j) * Kown + row : Xref, ok ? 4 : 0);
+                }
+            }
             if (warp == 0) {
                 if (lane == 0 && !*abort_flag) {
                     // ---- producer: stream every k-chunk's digit tiles into the stage ring
@@ -415,6 +446,7 @@ __global__ void __launch_bounds__(kTcsThreads, 1) rank2_tcs_kernel(const TcArgs 
                 if (lane == 0) gotl = (*abort_flag == 0) && mbarrier_wait(dready, (uint32_t)(hs & 1), limit, abort_flag);
                 have = __shfl_sync(0xffffffffu, gotl, 0) != 0;
                 tc_fence_after();
+                if constexpr (XR) cp_async_wait_all();  // this thread's own copies only
                 const float ars = arow[half * kTcRows + rl];
                 const float grw = grow[rl];
                 const uint32_t tl = tbase + ((uint32_t)(32 * quad) << 16) + (uint32_t)jbase;
@@ -462,6 +494,7 @@ __global__ void __launch_bounds__(kTcsThreads, 1) rank2_tcs_kernel(const TcArgs 
                         const float R = __fadd_rn(__uint_as_float(r0[q]), u);
                         float inc = R * scl[q];
                         inc = half == 0 ? __fmaf_rn(grw, fq[q], inc) : inc;
+                        if (XR && Xref) inc = inc + xst[(size_t)(i0 + q) * kTcsThreads + ridx];
                         inc = inc * dt;
                         float c = cg_[q];
                         const float y = kahan_add(yg[q], inc, c);

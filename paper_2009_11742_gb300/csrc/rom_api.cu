@@ -94,6 +94,10 @@ struct rom_s {
     // and tensor-core column choices are on automatic
     std::map<std::pair<int, int>, Rank2Plan> tuned;
     std::map<std::pair<int, int>, TcPlan> tuned_tc;
+    // reduced reference state (rom_set_reference): [0] f64, [1] f32 copies of
+    // the velocity (Kv x xref_M) and stress (Ks x xref_M) parts; xref_M = 0: none
+    void* xref[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
+    int xref_M = 0;
 };
 
 namespace {
@@ -117,7 +121,27 @@ void free_handle(rom_s* h) {
     cudaFree(h->C_tc);
     cudaFree(h->status);
     cudaFree(h->scalar);
+    for (int t = 0; t < 2; ++t) {
+        cudaFree(h->xref[t][0]);
+        cudaFree(h->xref[t][1]);
+    }
     delete h;
+}
+
+// Reference-state pointers of precision copy t (0 f64, 1 f32) for a run over
+// M columns; ROM_E_INVAL when one is set for another number of columns.
+rom_status xref_for(const rom_s* h, int t, int M, const void** Xv, const void** Xs) {
+    *Xv = nullptr;
+    *Xs = nullptr;
+    if (h->xref_M == 0) return ROM_OK;
+    if (M != h->xref_M) {
+        snprintf(g_last_error, sizeof(g_last_error),
+                 "the reference state has %d columns, the run %d", h->xref_M, M);
+        return ROM_E_INVAL;
+    }
+    *Xv = h->xref[t][0];
+    *Xs = h->xref[t][1];
+    return ROM_OK;
 }
 
 // FP64 power iteration for rho(Avs Asv) on the GPU.
@@ -455,6 +479,13 @@ rom_status run_rank2_tc_plan(rom_s* h, const RunBufs& b, int M, int nsteps, long
     a.wavelet = h->wavelet;
     a.n0 = n0;
     a.spin_limit = h->wait_limit;
+    {
+        const void *xv, *xs;
+        const rom_status xst = xref_for(h, 1, M, &xv, &xs);
+        if (xst != ROM_OK) return xst;
+        a.Xv = static_cast<const float*>(xv);
+        a.Xs = static_cast<const float*>(xs);
+    }
     a.Kv = h->Kv;
     a.Ks = h->Ks;
     a.Kp = h->Kp_tc;
@@ -517,6 +548,10 @@ rom_status launch_simt_with_plan(rom_s* h, const RunBufs& b, int M, int nsteps, 
     a.r = b.traces ? r : 1;
     a.spin_limit = h->wait_limit;
     a.debug_skip_push = h->inject_stall;
+    {
+        const rom_status xst = xref_for(h, t, M, &a.Xv, &a.Xs);
+        if (xst != ROM_OK) return xst;
+    }
     cudaError_t e = prec == ROM_FP64   ? launch_rank2_simt_f64(a, plan, st)
                     : plan.variant >= 2 ? launch_rank2_split_f32(a, plan, st)
                                         : launch_rank2_simt_f32(a, plan, st);
@@ -553,6 +588,10 @@ rom_status run_common(rom_s* h, void* V, void* S, const void* T, const void* fta
             a.status = h->status;
             a.dt = h->dt;
             a.wavelet = h->wavelet;
+            {
+                const rom_status xst = xref_for(h, t, M, &a.Xv, &a.Xs);
+                if (xst != ROM_OK) return xst;
+            }
             a.n0 = n0;
             a.Kv = h->Kv;
             a.Ks = h->Ks;
@@ -623,6 +662,60 @@ rom_status rom_set_wait_limit(rom_t h, long long cycles) {
 rom_status rom_debug_inject_stall(rom_t h, int on) {
     if (!h) return ROM_E_INVAL;
     h->inject_stall = on ? 1 : 0;
+    return ROM_OK;
+}
+
+rom_status rom_set_reference(rom_t h, const void* Xv, const void* Xs, int M, int in_dtype) {
+    if (!h) return ROM_E_INVAL;
+    std::lock_guard<std::mutex> lk(h->mu);
+    if (!Xv && !Xs) {
+        cudaDeviceSynchronize();  // earlier launches may still read the old copies
+        for (int t = 0; t < 2; ++t)
+            for (int part = 0; part < 2; ++part) {
+                cudaFree(h->xref[t][part]);
+                h->xref[t][part] = nullptr;
+            }
+        h->xref_M = 0;
+        return ROM_OK;
+    }
+    if (M < 1 || (in_dtype != ROM_IN_F64 && in_dtype != ROM_IN_F32)) return ROM_E_INVAL;
+    const size_t es = in_dtype == ROM_IN_F64 ? 8 : 4;
+    const void* src[2] = {Xv, Xs};
+    const int rows[2] = {h->Kv, h->Ks};
+    void* tmp[2] = {nullptr, nullptr};
+    const void* dsrc[2] = {nullptr, nullptr};
+    void* fresh[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
+    cudaError_t e = cudaSuccess;
+    for (int part = 0; part < 2 && e == cudaSuccess; ++part) {
+        if (!src[part]) continue;
+        const size_t n = (size_t)rows[part] * M;
+        if (is_device_ptr(src[part])) {
+            dsrc[part] = src[part];
+        } else {
+            e = cudaMalloc(&tmp[part], n * es);
+            if (e == cudaSuccess) e = cudaMemcpy(tmp[part], src[part], n * es, cudaMemcpyHostToDevice);
+            dsrc[part] = tmp[part];
+        }
+        for (int t = 0; t < 2 && e == cudaSuccess; ++t) {
+            e = cudaMalloc(&fresh[t][part], n * (t == 0 ? 8 : 4));
+            if (e == cudaSuccess)
+                e = launch_pad_copy(dsrc[part], in_dtype == ROM_IN_F64 ? 0 : 1, rows[part], M, rows[part], M,
+                                    false, fresh[t][part], t, 0);
+        }
+    }
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    for (int part = 0; part < 2; ++part) cudaFree(tmp[part]);
+    if (e != cudaSuccess) {
+        for (int t = 0; t < 2; ++t)
+            for (int part = 0; part < 2; ++part) cudaFree(fresh[t][part]);
+        return e == cudaErrorMemoryAllocation ? ROM_E_NOMEM : cuda_fail(e, "rom_set_reference");
+    }
+    for (int t = 0; t < 2; ++t)
+        for (int part = 0; part < 2; ++part) {
+            cudaFree(h->xref[t][part]);
+            h->xref[t][part] = fresh[t][part];
+        }
+    h->xref_M = M;
     return ROM_OK;
 }
 
@@ -1141,6 +1234,7 @@ rom_status rom_adjoint(rom_t h, const void* V0, const void* S0, const void* T, i
         ckpt_every < 0 || h->R < 1)
         return ROM_E_INVAL;
     if (prec != ROM_FP32) return ROM_E_UNSUPPORTED;
+    if (h->xref_M != 0 && h->xref_M != M) return ROM_E_INVAL;  // reference state of another ensemble
     const void* ptrs[] = {V0, S0, T, ystar, gV0, gS0, gT};
     for (const void* p : ptrs)
         if (!is_device_ptr(p)) return ROM_E_INVAL;

@@ -38,6 +38,8 @@ struct Rank2Args {
     long long spin_limit;  // clock cycles a device-side wait may last before ROM_E_TIMEOUT
     int debug_skip_push;   // fault injection: CTA 0 never publishes (forces the timeout path)
     int wavelet;           // source signal of the periods: 0 Ricker, 1 first derivative of a Gaussian
+    const void* Xv;        // reduced reference state, velocity part, Kv x Mtot (T), or null
+    const void* Xs;        // stress part, Ks x Mtot (T), or null
 };
 
 // Launch plan chosen by the host for a rank-2 call.
@@ -89,6 +91,8 @@ struct TcArgs {
     long long spin_limit;
     int Kv, Ks, Kp, R, M, Mtot, W, nsteps, r, rpc, stages;
     int wavelet;          // source signal of the periods (see Rank2Args)
+    const float* Xv;      // reduced reference state (see Rank2Args), or null
+    const float* Xs;
 };
 struct TcPlan {
     int prec, cs, W, stages, nclusters, rpc, max_active_clusters;
@@ -152,6 +156,8 @@ struct Rank1EnsArgs {
     long long n0;
     int Kv, Ks, Kp, R, M, nsteps, r;
     int wavelet;          // source signal of the periods (see Rank2Args)
+    const void* Xv;       // reduced reference state (see Rank2Args), or null
+    const void* Xs;
 };
 cudaError_t launch_rank1_ensemble_f32(const Rank1EnsArgs& a, cudaStream_t st);
 cudaError_t launch_rank1_ensemble_f64(const Rank1EnsArgs& a, cudaStream_t st);

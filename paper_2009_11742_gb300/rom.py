@@ -35,7 +35,7 @@ PRECISIONS = {"fp64": ROM_FP64, "fp32": ROM_FP32, "tf32x3": ROM_TF32X3,
               "bf16x3": ROM_BF16X3, "bf16": ROM_BF16, "bf16s": ROM_BF16S}
 
 EXPORTED = ["rom_create", "rom_destroy", "rom_spectral_radius", "rom_sync_status",
-            "rom_get_dims", "rom_set_kernel", "rom_get_plan", "rom_set_tc_columns", "rom_set_wavelet", "rom_autotune", "rom_autotune_batched", "rom_set_wait_limit",
+            "rom_get_dims", "rom_set_kernel", "rom_get_plan", "rom_set_tc_columns", "rom_set_wavelet", "rom_set_reference", "rom_autotune", "rom_autotune_batched", "rom_set_wait_limit",
             "rom_debug_inject_stall", "rom_run_rank2", "rom_run_rank2_ex", "rom_run_rank1",
             "rom_run_rank1_ensemble", "rom_run_batched", "rom_adjoint",
             "rom_adjoint_workspace_size", "rom_rel_l2", "rom_spectral_radius_noalloc",
@@ -68,6 +68,7 @@ def _signatures(lib):
         "rom_set_wait_limit": (_i, [_vp, ctypes.c_longlong]),
         "rom_set_tc_columns": (_i, [_vp, _i]),
         "rom_set_wavelet": (_i, [_vp, _i]),
+        "rom_set_reference": (_i, [_vp, _vp, _vp, _i, _i]),
         "rom_autotune": (_i, [_vp, _i, _i, _i, ctypes.POINTER(_d), _vp]),
         "rom_autotune_batched": (_i, [_vp, _i, _i, _i, ctypes.POINTER(_d), _vp]),
         "rom_debug_inject_stall": (_i, [_vp, _i]),
@@ -166,6 +167,11 @@ def rom_set_tc_columns(h, cols):
 
 def rom_set_wavelet(h, wavelet):
     return load().rom_set_wavelet(h, int(wavelet))
+
+
+def rom_set_reference(h, Xv, Xs, M, in_dtype):
+    """Raw call: Xv, Xs are addresses (or None), column-major."""
+    return load().rom_set_reference(h, Xv, Xs, int(M), int(in_dtype))
 
 
 def rom_autotune(h, prec, M, probe_steps, stream=None):
@@ -447,6 +453,31 @@ class Rom:
         derivative of a Gaussian), or the ROM_WAVELET_* code."""
         w = {"ricker": ROM_WAVELET_RICKER, "gauss1": ROM_WAVELET_GAUSS1}.get(wavelet, wavelet)
         _chk(rom_set_wavelet(self.h, int(w)), "rom_set_wavelet")
+
+    def set_reference(self, Xv=None, Xs=None):
+        """Reduced reference state of Eq. (rom_ode_tensor): Xv (Kv, M) and Xs
+        (Ks, M), numpy arrays or torch tensors (host or device), either may
+        be None; both None clears it.  Later runs add it to the two halves of
+        every step.  The values are passed as float64 (the library keeps its
+        own FP64 and FP32 copies)."""
+        if Xv is None and Xs is None:
+            _chk(rom_set_reference(self.h, None, None, 0, ROM_IN_F64), "rom_set_reference")
+            return
+        parts, M = [], None
+        for X, K in ((Xv, self.Kv), (Xs, self.Ks)):
+            if X is None:
+                parts.append(None)
+                continue
+            if isinstance(X, np.ndarray):
+                X = np.asfortranarray(X, dtype=np.float64)
+            else:
+                X = X.double().t().contiguous().t()  # column-major storage
+            if X.ndim != 2 or X.shape[0] != K or (M is not None and X.shape[1] != M):
+                raise ValueError("reference state parts must be (Kv, M) and (Ks, M)")
+            M = X.shape[1]
+            parts.append(X)
+        _chk(rom_set_reference(self.h, _ptr(parts[0]), _ptr(parts[1]), M, ROM_IN_F64),
+             "rom_set_reference")
 
     def plan(self, M, prec="fp32"):
         st, v, cs, w, nc = rom_get_plan(self.h, PRECISIONS.get(prec, prec), int(M))
