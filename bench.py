@@ -249,10 +249,11 @@ def main():
                     help="leapfrog steps per run (default: the workload's 10000; profiling only)")
     ap.add_argument("--only-rank2", action="store_true",
                     help="time the rank-2 runs only (no e2e, rank-1, oracle legs; profiling only)")
-    ap.add_argument("--workload", type=int, default=1, choices=[0, 1, 2, 3, 4, 5],
+    ap.add_argument("--workload", type=int, default=1, choices=[0, 1, 2, 3, 4, 5, 6],
                     help="0: K=128 M=16 N=1000 FP64; 1: K=512 FP32 (default, the headline); "
                          "2: K=1024 split precision; 3: 64 batched ROMs; 4: adjoint K=512 M=128 N=4000 c=64; "
-                         "5: many-query UQ run (Kv=436, Ks=417, M=512, 20000 steps) with ensemble statistics")
+                         "5: many-query UQ run (Kv=436, Ks=417, M=512, 20000 steps) with ensemble statistics; "
+                         "6: rank-3 (16 operators x 16 forcings, K=256, 10000 steps) in one launch")
     ap.add_argument("--prec", default=None, help="override the workload's precision")
     ap.add_argument("--tc-cols", type=int, default=0, help="tensor-core columns per block")
     args = ap.parse_args()
@@ -285,6 +286,8 @@ def main():
         return bench_batched(args, torch, dev, inputs, rom)
     if args.workload == 4:
         return bench_adjoint(args, torch, dev, inputs, rom)
+    if args.workload == 6:
+        return bench_rank3(args, torch, dev, inputs, rom)
 
     W = dict(WORKLOAD if args.workload == 1 else WORKLOAD2)
     if args.nsteps:
@@ -710,6 +713,84 @@ def bench_batched(args, torch, dev, inputs, rom):
                       "untuned": {"value": ss / t0, "ms_per_step": 1e3 * t0},
                       "autotune_probe_us_per_step": probe_us,
                       "columns_total": sum(p.M for p in probs)}), flush=True)
+    return 0
+
+
+def bench_rank3(args, torch, dev, inputs, rom):
+    """Workload 6: the rank-3 outlook (Sec. 5).  16 operators (K = 256, one
+    shared dt) times 16 forcings each, 10000 FP32 steps with traces every 10
+    steps, in one launch (rom_run_rank3).  Beside it, the same work as a
+    batched graph of 16 rank-2 runs and as 16 rank-2 runs one after another."""
+    import numpy as np
+    nops, K, M, R, r = 16, 256, 16, 64, 10
+    N = args.nsteps or 10000
+    probs = inputs.rank3_problems(nops, K, K, M, R, seed=600)
+    roms = [rom.Rom.from_problem(p) for p in probs]
+    Mt = nops * M
+    V = rom.Rom.new_state(K, Mt, "fp32", device=dev)
+    S = rom.Rom.new_state(K, Mt, "fp32", device=dev)
+    T = torch.as_tensor(np.concatenate([p.T for p in probs]), dtype=torch.float32, device=dev)
+    tr = torch.zeros(((N // r) * Mt * R,), dtype=torch.float32, device=dev)
+    # per-operator column slices (contiguous: the state is column-major)
+    Vs = [V[:, i * M:(i + 1) * M] for i in range(nops)]
+    Ss = [S[:, i * M:(i + 1) * M] for i in range(nops)]
+    Ts = [T[i * M:(i + 1) * M] for i in range(nops)]
+    trs = [torch.zeros(((N // r) * M * R,), dtype=torch.float32, device=dev) for _ in range(nops)]
+    stream = torch.cuda.Stream(device=dev)
+
+    def rank3():
+        rom.run_rank3(roms, V, S, T, N, r=r, traces=tr, prec="fp32", stream=stream)
+
+    def batched():
+        rom.run_batched([(roms[i], Vs[i], Ss[i], Ts[i], trs[i]) for i in range(nops)], N, r=r,
+                        prec="fp32", stream=stream)
+
+    def sequential():
+        for i in range(nops):
+            roms[i].run_rank2(Vs[i], Ss[i], Ts[i], N, r=r, traces=trs[i], prec="fp32", stream=stream)
+
+    def timed(fn):
+        with torch.cuda.stream(stream):
+            for _ in range(args.warmup):
+                V.zero_()
+                S.zero_()
+                fn()
+        torch.cuda.synchronize()
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(args.steps)]
+        with torch.cuda.stream(stream):
+            for i in range(args.steps):
+                V.zero_()
+                S.zero_()
+                evs[i][0].record(stream)
+                fn()
+                evs[i][1].record(stream)
+        torch.cuda.synchronize()
+        return sum(a.elapsed_time(b) for a, b in evs) * 1e-3 / args.steps
+
+    t_b = timed(batched)
+    t_s = timed(sequential)
+    t3 = timed(rank3)  # last, so that V and the traces hold the rank-3 result
+    ss = Mt * N
+    out = {"only_rank2": True, "workload": f"rank3-{nops}ops-K{K}-M{M}-N{N}-R{R}-r{r}", "nsteps": N,
+           "value": ss / t3, "unit": "sample-steps/s", "ms_per_step": 1e3 * t3,
+           "tflops_useful": 4.0 * K * K * Mt * N / t3 / 1e12,
+           "batched_graph": {"value": ss / t_b, "ms_per_step": 1e3 * t_b},
+           "sequential_rank2": {"value": ss / t_s, "ms_per_step": 1e3 * t_s}}
+    if not args.no_check:
+        import oracle
+        Vg = V.cpu().numpy()
+        trg = tr.cpu().numpy().reshape(N // r, Mt, R)
+        errs = []
+        for i, m in ((0, 0), (nops // 2, M // 2), (nops - 1, M - 1)):
+            p = probs[i]
+            z = np.zeros((K, 1))
+            Vo, _, tro = oracle.forward(p.Avs, p.Asv, p.g, p.C, p.dt, z, z, N, T=p.T[m:m + 1], r=r)
+            c = i * M + m
+            errs.append(max(float(np.linalg.norm(Vg[:, c] - Vo[:, 0]) / np.linalg.norm(Vo[:, 0])),
+                            float(np.linalg.norm(trg[:, c, :] - tro[:, :, 0]) / np.linalg.norm(tro[:, :, 0]))))
+        out["rel_err_vs_oracle"] = {"value": max(errs), "columns": "3 sampled (operator, forcing) pairs"}
+    print(json.dumps(out), flush=True)
     return 0
 
 

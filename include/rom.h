@@ -297,6 +297,27 @@ rom_status rom_run_batched(const rom_job* jobs, int njobs, int nsteps, int r, in
                            void* stream);
 
 /*
+ * rom_run_rank3 -- the rank-3 outlook of Sec. 5: many realizations of the
+ * system operator (nops handles) times many forcings (M columns each) in ONE
+ * launch of the persistent kernel.  The handles must share Kv, Ks, R, dt and
+ * the wavelet, and carry no reference state.  The state is the rank-3
+ * tensor of nops slabs of M columns stored as one column-major matrix:
+ * V is Kv x (M nops) (operator i owns columns [i M, (i+1) M)), S is
+ * Ks x (M nops), T (or NULL) holds M nops periods in the same order, and
+ * traces (optional, r > 0) holds floor(nsteps / r) records of
+ * R x (M nops).  Each operator gets an equal share of the GPU's co-resident
+ * clusters, each of which keeps one operator in registers; the result for
+ * operator i equals rom_run_rank2 on handle i over its slab.  Device
+ * buffers only, n0 = 0, ROM_FP32 or ROM_FP64 (other precisions:
+ * ROM_E_UNSUPPORTED).  Asynchronous on `stream`; device-side status goes to
+ * the first handle.  The first call for a handle list copies a small
+ * operator table to the device (synchronous); it is kept until one of the
+ * handles is destroyed.
+ */
+rom_status rom_run_rank3(const rom_t* handles, int nops, void* V, void* S, const void* T, int M,
+                         int nsteps, int r, void* traces, int prec, void* stream);
+
+/*
  * rom_autotune_batched -- the batching schedule by measurement: replay the
  * job list's captured graph on scratch copies of its state (zero state,
  * every period 45 dt, no traces) for `probe_steps` steps with the SMs shared

@@ -3,8 +3,8 @@
 
 namespace romk {
 
-bool plan_rank2_simt_f64(int Kp, int M, int R, bool rank1, Rank2Plan* p) {
-    return plan_rank2<double>(Kp, M, R, rank1, p);
+bool plan_rank2_simt_f64(int Kp, int M, int R, bool rank1, Rank2Plan* p, int budget) {
+    return plan_rank2<double>(Kp, M, R, rank1, p, budget);
 }
 
 cudaError_t launch_rank2_simt_f64(const Rank2Args& a, const Rank2Plan& p, cudaStream_t st) {

@@ -8,14 +8,17 @@
 
 namespace romk {
 
-// xr: the split kernel instance that adds the reduced reference state (the
-// dataflow kernel tests for it at run time).
+// mode: the split kernel instance (0 plain, 1 with the reduced reference
+// state, 2 rank-3 grouped); the dataflow kernel tests for the reference
+// state at run time and has no grouped form.
 template <bool DF>
-static void* two_block_kernel(int KI, bool xr = false) {
-#define ROM_TB_CASE(k)                                                   \
-    case k:                                                              \
-        return DF ? (void*)&rank2_dataflow_kernel<k>                     \
-                  : (xr ? (void*)&rank2_split_kernel<k, true> : (void*)&rank2_split_kernel<k, false>);
+static void* two_block_kernel(int KI, int mode = 0) {
+#define ROM_TB_CASE(k)                                                              \
+    case k:                                                                         \
+        return DF ? (void*)&rank2_dataflow_kernel<k>                                \
+                  : (mode == 2   ? (void*)&rank2_split_kernel<k, 2>                 \
+                     : mode == 1 ? (void*)&rank2_split_kernel<k, 1>                 \
+                                 : (void*)&rank2_split_kernel<k, 0>);
     switch (KI) {
         ROM_TB_CASE(1) ROM_TB_CASE(2) ROM_TB_CASE(3) ROM_TB_CASE(4)
         ROM_TB_CASE(5) ROM_TB_CASE(6) ROM_TB_CASE(7) ROM_TB_CASE(8)
@@ -87,7 +90,10 @@ static cudaError_t launch_two_block(const Rank2Args& a_in, const Rank2Plan& p, c
     a.Wa = p.Wa;
     const int H = p.cs / 2;
     a.rpc = (a.R + H - 1) / H;
-    void* fn = two_block_kernel<DF>(p.KI, a.Xv != nullptr || a.Xs != nullptr);
+    if (DF && a.group) return cudaErrorInvalidValue;
+    const int mode = a.group ? 2 : (a.Xv != nullptr || a.Xs != nullptr ? 1 : 0);
+    if (a.group && mode == 2 && (a.Xv || a.Xs)) return cudaErrorInvalidValue;
+    void* fn = two_block_kernel<DF>(p.KI, mode);
     if (!fn) return cudaErrorInvalidValue;
     cudaError_t e = prepare_kernel<float>(fn, p.smem);
     if (e != cudaSuccess) return e;

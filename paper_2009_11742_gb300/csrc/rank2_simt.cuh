@@ -226,7 +226,10 @@ __global__ void __launch_bounds__(kThreads, 1) rank2_simt_kernel(const Rank2Args
     cg::cluster_group cluster = cg::this_cluster();
     const int cs = (int)cluster.num_blocks();
     const int crank = (int)cluster.block_rank();
-    const int blk = blockIdx.x / cs;
+    // rank-3 grouped launch: operator `job` of the table, column block `blk` of it
+    const int job = a.group ? (int)(blockIdx.x / cs) / a.group_cpj : 0;
+    const int blk = a.group ? (int)(blockIdx.x / cs) % a.group_cpj : (int)(blockIdx.x / cs);
+    const GroupOp* gop = a.group ? a.group + job : nullptr;
     const int col0 = blk * a.Wv;                 // first column of this block (within the job)
     const int ncol = min(a.Wv, a.M - col0);      // valid columns
     const int Wa = a.Wa;
@@ -252,7 +255,7 @@ __global__ void __launch_bounds__(kThreads, 1) rank2_simt_kernel(const Rank2Args
 
     const T* __restrict__ Vin = static_cast<const T*>(a.V);
     const T* __restrict__ Sin = static_cast<const T*>(a.S);
-    const int gc0 = a.col_base + col0;  // first column in the caller's arrays
+    const int gc0 = a.col_base + job * a.M + col0;  // first column in the caller's arrays
 
     // ---- load the column block (all rows) and the per-CTA constants
     for (int idx = tid; idx < Wa * Kp; idx += kThreads) {
@@ -270,12 +273,12 @@ __global__ void __launch_bounds__(kThreads, 1) rank2_simt_kernel(const Rank2Args
         cV[idx] = (cvin && c < ncol && row < a.Kv) ? cvin[(size_t)(gc0 + c) * a.Kv + row] : 0.f;
         cS[idx] = (csin && c < ncol && row < a.Ks) ? csin[(size_t)(gc0 + c) * a.Ks + row] : 0.f;
     }
-    const T* Cp = static_cast<const T*>(a.C_p);
+    const T* Cp = static_cast<const T*>(gop ? gop->C_p : a.C_p);
     for (int idx = tid; idx < a.rpc * Kp; idx += kThreads) {
         const int jj = idx / Kp, k = idx % Kp, jr = crank * a.rpc + jj;
         Cown[idx] = (Cp && jr < a.R) ? Cp[(size_t)jr * Kp + k] : T(0);
     }
-    for (int i = tid; i < own_rows; i += kThreads) gown[i] = static_cast<const T*>(a.g_p)[row0 + i];
+    for (int i = tid; i < own_rows; i += kThreads) gown[i] = static_cast<const T*>(gop ? gop->g_p : a.g_p)[row0 + i];
     for (int c = tid; c < Wa; c += kThreads) {
         Tcol[c] = (a.Tper && c < ncol) ? static_cast<const T*>(a.Tper)[gc0 + c] : T(1);
     }
@@ -286,8 +289,8 @@ __global__ void __launch_bounds__(kThreads, 1) rank2_simt_kernel(const Rank2Args
 
     T opA[2][4 * KI];
     T opB[2][4 * KI];
-    const T* __restrict__ Avs = static_cast<const T*>(a.Avs_rm);
-    const T* __restrict__ Asv = static_cast<const T*>(a.Asv_rm);
+    const T* __restrict__ Avs = static_cast<const T*>(gop ? gop->Avs_rm : a.Avs_rm);
+    const T* __restrict__ Asv = static_cast<const T*>(gop ? gop->Asv_rm : a.Asv_rm);
     if (RESIDENT) {
         load_op_rows<T, KI>(opA, Avs, Kp, row0 + 2 * rp, j);
         load_op_rows<T, KI>(opB, Asv, Kp, row0 + 2 * rp, j);
@@ -306,7 +309,7 @@ __global__ void __launch_bounds__(kThreads, 1) rank2_simt_kernel(const Rank2Args
         }
         if (a.Xv) {  // kernel parameters, read where used: no register held across the loop
             __syncthreads();
-            add_reference<T>(Vf, cV, static_cast<const T*>(a.Xv) + (size_t)(a.col_base + col0) * a.Kv,
+            add_reference<T>(Vf, cV, static_cast<const T*>(a.Xv) + (size_t)gc0 * a.Kv,
                              a.Kv, ncol, dt, Wa, Kp, row0, nrt);
         }
         __syncthreads();
@@ -322,7 +325,7 @@ __global__ void __launch_bounds__(kThreads, 1) rank2_simt_kernel(const Rank2Args
         }
         if (a.Xs) {
             __syncthreads();
-            add_reference<T>(Sf, cS, static_cast<const T*>(a.Xs) + (size_t)(a.col_base + col0) * a.Ks,
+            add_reference<T>(Sf, cS, static_cast<const T*>(a.Xs) + (size_t)gc0 * a.Ks,
                              a.Ks, ncol, dt, Wa, Kp, row0, nrt);
             __syncthreads();
         }

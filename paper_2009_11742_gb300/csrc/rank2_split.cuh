@@ -155,8 +155,13 @@ __device__ __forceinline__ void split_phase(cg::cluster_group& cluster, const fl
     }
 }
 
-template <int KI, bool XR>
+// MODE: 0 plain; 1 adds the reduced reference state (a.Xv / a.Xs); 2 is the
+// rank-3 grouped launch (operator table a.group).  A template parameter, so
+// that each instance compiles to exactly the code its runs need.
+template <int KI, int MODE>
 __global__ void __launch_bounds__(kThreads, 1) rank2_split_kernel(const Rank2Args a) {
+    constexpr bool XR = MODE == 1;
+    constexpr bool GROUPED = MODE == 2;
     cg::cluster_group cluster = cg::this_cluster();
     const int cs = (int)cluster.num_blocks();
     const int H = cs / 2;
@@ -165,7 +170,10 @@ __global__ void __launch_bounds__(kThreads, 1) rank2_split_kernel(const Rank2Arg
     const int s = vrole ? crank : crank - H;  // row slab
     const int row0 = s * kSplitRows;
     const int peer0 = vrole ? H : 0;          // first CTA of the other role
-    const int clu = blockIdx.x / cs;
+    // rank-3 grouped launch: operator `job` of the table, cluster `clu` of it
+    const int job = GROUPED ? (int)(blockIdx.x / cs) / a.group_cpj : 0;
+    const int clu = GROUPED ? (int)(blockIdx.x / cs) % a.group_cpj : (int)(blockIdx.x / cs);
+    const GroupOp* gop = GROUPED ? a.group + job : nullptr;
     const int Wa = a.Wa, Kp = a.Kp;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int j = lane & 15;
@@ -184,7 +192,7 @@ __global__ void __launch_bounds__(kThreads, 1) rank2_split_kernel(const Rank2Arg
 
     // column ranges of the two blocks, kept in scalars so that runtime block
     // indices do not force a local-memory array
-    const int gc0_0 = a.col_base + (2 * clu) * a.Wv;
+    const int gc0_0 = a.col_base + job * a.M + (2 * clu) * a.Wv;
     const int gc0_1 = gc0_0 + a.Wv;
     const int nr0 = a.M - (2 * clu) * a.Wv, nr1 = nr0 - a.Wv;
     const int nc0 = nr0 < 0 ? 0 : (nr0 > a.Wv ? a.Wv : nr0);
@@ -216,14 +224,14 @@ __global__ void __launch_bounds__(kThreads, 1) rank2_split_kernel(const Rank2Arg
         own[idx] = ok ? own_in[(size_t)(gc0(b) + c) * Kown + row] : 0.f;
         comp[idx] = (ok && comp_in) ? comp_in[(size_t)(gc0(b) + c) * Kown + row] : 0.f;
     }
-    const float* Cp = static_cast<const float*>(a.C_p);
+    const float* Cp = static_cast<const float*>(GROUPED ? gop->C_p : a.C_p);
     if (!vrole) {
         for (int idx = tid; idx < a.rpc * Kp; idx += kThreads) {
             const int jj = idx / Kp, k = idx % Kp, jr = s * a.rpc + jj;
             Cown[idx] = (Cp && jr < a.R) ? Cp[(size_t)jr * Kp + k] : 0.f;
         }
     }
-    if (tid < kSplitRows) gown[tid] = vrole ? static_cast<const float*>(a.g_p)[row0 + tid] : 0.f;
+    if (tid < kSplitRows) gown[tid] = vrole ? static_cast<const float*>(GROUPED ? gop->g_p : a.g_p)[row0 + tid] : 0.f;
     for (int idx = tid; idx < 2 * Wa; idx += kThreads) {
         const int b = idx / Wa, c = idx % Wa;
         Tcol[idx] = (a.Tper && c < ncol(b)) ? static_cast<const float*>(a.Tper)[gc0(b) + c] : 1.f;
@@ -242,7 +250,9 @@ __global__ void __launch_bounds__(kThreads, 1) rank2_split_kernel(const Rank2Arg
     }
 
     float op[4][4 * KI];
-    load_op_quad<KI>(op, static_cast<const float*>(vrole ? a.Avs_rm : a.Asv_rm), Kp, row0 + 4 * q, j);
+    load_op_quad<KI>(op, static_cast<const float*>(vrole ? (GROUPED ? gop->Avs_rm : a.Avs_rm)
+                                                         : (GROUPED ? gop->Asv_rm : a.Asv_rm)),
+                     Kp, row0 + 4 * q, j);
     // every CTA's copies must be initialised before any peer pushes into them
     cluster.sync();
 

@@ -196,6 +196,8 @@ bool tc_prec(int prec) {
 
 // Forget cached batched graphs that reference handle h (defined with them below).
 void drop_batch_graphs(rom_s* h);
+// Forget cached rank-3 operator tables that reference handle h (defined below).
+void drop_group_tables(rom_s* h);
 
 }  // namespace
 
@@ -303,6 +305,7 @@ rom_status rom_destroy(rom_t h) {
     if (!h) return ROM_E_INVAL;
     cudaDeviceSynchronize();
     drop_batch_graphs(h);
+    drop_group_tables(h);
     free_handle(h);
     return ROM_OK;
 }
@@ -1187,6 +1190,153 @@ rom_status rom_autotune_batched(const rom_job* jobs, int njobs, int prec, int pr
         g_batch_scale[batch_tune_key(jobs, njobs, prec)] = best_scale;
     }
     if (best_us) *best_us = best;
+    return ROM_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------- rank-3
+//
+// Many operators (realizations of the system parameters) times many
+// forcings in ONE launch (the rank-3 outlook of Sec. 5).  The operators share
+// K, R and dt; the state is the rank-3 tensor of nops slabs of M columns,
+// stored as one Kv x (M nops) matrix.  A device table holds each operator's
+// pointers; cluster c of the persistent kernel advances operator c / cpj on
+// its own column block, so every cluster keeps one operator resident.
+
+namespace {
+
+std::mutex g_group_mu;
+std::map<std::vector<uintptr_t>, GroupOp*> g_group_tables;  // key: t, then the handles
+
+void drop_group_tables(rom_s* h) {
+    std::lock_guard<std::mutex> lk(g_group_mu);
+    for (auto it = g_group_tables.begin(); it != g_group_tables.end();) {
+        bool uses = false;
+        for (size_t k = 1; k < it->first.size(); ++k) uses |= (it->first[k] == (uintptr_t)h);
+        if (uses) {
+            cudaFree(it->second);
+            it = g_group_tables.erase(it);
+        } else {
+            ++it;
+        }
+    }
+}
+
+// The device operator table of this handle list and precision copy t
+// (built once, then reused).
+rom_status group_table(const rom_t* hs, int nops, int t, const GroupOp** out) {
+    std::vector<uintptr_t> key;
+    key.push_back((uintptr_t)t);
+    for (int i = 0; i < nops; ++i) key.push_back((uintptr_t)hs[i]);
+    std::lock_guard<std::mutex> lk(g_group_mu);
+    auto it = g_group_tables.find(key);
+    if (it == g_group_tables.end()) {
+        std::vector<GroupOp> host(nops);
+        for (int i = 0; i < nops; ++i)
+            host[i] = {hs[i]->Avs_rm[t], hs[i]->Asv_rm[t], hs[i]->g_p[t], hs[i]->C_rm[t]};
+        GroupOp* dev = nullptr;
+        ROM_CUDA(cudaMalloc(&dev, sizeof(GroupOp) * nops));
+        const cudaError_t e = cudaMemcpy(dev, host.data(), sizeof(GroupOp) * nops, cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) {
+            cudaFree(dev);
+            return cuda_fail(e, "rank-3 operator table");
+        }
+        it = g_group_tables.emplace(key, dev).first;
+    }
+    *out = it->second;
+    return ROM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+rom_status rom_run_rank3(const rom_t* hs, int nops, void* V, void* S, const void* T, int M,
+                         int nsteps, int r, void* traces, int prec, void* stream) {
+    if (!hs || nops < 1 || !V || !S || M < 1 || nsteps < 0 || r < 0 || !valid_prec(prec))
+        return ROM_E_INVAL;
+    const rom_s* h0 = hs[0];
+    if (!h0) return ROM_E_INVAL;
+    for (int i = 0; i < nops; ++i) {
+        const rom_s* h = hs[i];
+        if (!h || h->Kv != h0->Kv || h->Ks != h0->Ks || h->R != h0->R || h->dt != h0->dt ||
+            h->wavelet != h0->wavelet)
+            return ROM_E_INVAL;
+        if (h->xref_M != 0) {
+            snprintf(g_last_error, sizeof(g_last_error), "rom_run_rank3 takes no reference state");
+            return ROM_E_UNSUPPORTED;
+        }
+    }
+    if (prec != ROM_FP32 && prec != ROM_FP64) return ROM_E_UNSUPPORTED;
+    if (traces && (r < 1 || h0->R < 1)) return ROM_E_INVAL;
+    if (!is_device_ptr(V) || !is_device_ptr(S) || (T && !is_device_ptr(T)) ||
+        (traces && !is_device_ptr(traces)))
+        return ROM_E_INVAL;
+    if (nsteps == 0) return ROM_OK;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const int t = prec == ROM_FP64 ? 0 : 1;
+    const int Kp = h0->Kp, R = h0->R;
+    // each operator gets an equal share of the co-resident clusters
+    Rank2Plan p;
+    bool ok = false;
+    if (prec == ROM_FP32) {
+        Rank2Plan p0;
+        if (plan_rank2_split_f32(Kp, M, R, &p0)) {
+            const int budget = p0.max_active_clusters / nops > 0 ? p0.max_active_clusters / nops : 1;
+            ok = plan_rank2_split_f32(Kp, M, R, &p, budget);
+            if (ok) p.variant = 2;
+        }
+    }
+    if (!ok) {
+        Rank2Plan p0;
+        const bool ok0 = prec == ROM_FP64 ? plan_rank2_simt_f64(Kp, M, R, false, &p0)
+                                          : plan_rank2_simt_f32(Kp, M, R, false, &p0);
+        if (ok0) {
+            const int budget = p0.max_active_clusters / nops > 0 ? p0.max_active_clusters / nops : 1;
+            ok = prec == ROM_FP64 ? plan_rank2_simt_f64(Kp, M, R, false, &p, budget)
+                                  : plan_rank2_simt_f32(Kp, M, R, false, &p, budget);
+            if (ok) p.variant = 1;
+        }
+    }
+    if (!ok) {
+        snprintf(g_last_error, sizeof(g_last_error), "no rank-3 plan for Kp=%d M=%d", Kp, M);
+        return ROM_E_UNSUPPORTED;
+    }
+    const int cpj = p.nclusters;  // clusters (column-block pairs or blocks) per operator
+    p.nclusters = cpj * nops;
+    const GroupOp* table = nullptr;
+    rom_status gs = group_table(hs, nops, t, &table);
+    if (gs != ROM_OK) return gs;
+    Rank2Args a = {};
+    a.Avs_rm = h0->Avs_rm[t];
+    a.Asv_rm = h0->Asv_rm[t];
+    a.g_p = h0->g_p[t];
+    a.C_p = h0->C_rm[t];
+    a.group = table;
+    a.group_cpj = cpj;
+    a.V = V;
+    a.S = S;
+    a.Tper = T;
+    a.traces = traces;
+    a.status = h0->status;
+    a.dt = h0->dt;
+    a.wavelet = h0->wavelet;
+    a.n0 = 0;
+    a.Kv = h0->Kv;
+    a.Ks = h0->Ks;
+    a.Kp = Kp;
+    a.R = R;
+    a.M = M;
+    a.Mtot = M * nops;
+    a.col_base = 0;
+    a.nsteps = nsteps;
+    a.r = traces ? r : 1;
+    a.spin_limit = h0->wait_limit;
+    cudaError_t e = prec == ROM_FP64   ? launch_rank2_simt_f64(a, p, st)
+                    : p.variant >= 2 ? launch_rank2_split_f32(a, p, st)
+                                     : launch_rank2_simt_f32(a, p, st);
+    if (e != cudaSuccess) return cuda_fail(e, "rank-3 launch");
     return ROM_OK;
 }
 

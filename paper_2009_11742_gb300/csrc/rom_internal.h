@@ -10,6 +10,14 @@ namespace romk {
 
 // Arguments of one rank-2 launch (all device pointers).  Element type T of
 // the state-like buffers is double for ROM_FP64 and float otherwise.
+// One operator of a grouped (rank-3) launch: its handle's device copies.
+struct GroupOp {
+    const void* Avs_rm;
+    const void* Asv_rm;
+    const void* g_p;
+    const void* C_p;
+};
+
 struct Rank2Args {
     const void* Avs_rm;  // Kp x Kp row-major, zero padded (T)
     const void* Asv_rm;  // Kp x Kp row-major, zero padded (T)
@@ -40,6 +48,12 @@ struct Rank2Args {
     int wavelet;           // source signal of the periods: 0 Ricker, 1 first derivative of a Gaussian
     const void* Xv;        // reduced reference state, velocity part, Kv x Mtot (T), or null
     const void* Xs;        // stress part, Ks x Mtot (T), or null
+    // rank-3 grouped launch: operator table (device) and clusters (one-block
+    // kernel: column blocks) per operator; cluster c advances operator
+    // c / group_cpj on that operator's M columns, global columns
+    // job * M + local.  Null: one operator (the fields above).
+    const GroupOp* group;
+    int group_cpj;
 };
 
 // Launch plan chosen by the host for a rank-2 call.
@@ -62,7 +76,7 @@ cudaError_t launch_rank2_simt_f32(const Rank2Args& a, const Rank2Plan& plan, cud
 cudaError_t launch_rank2_simt_f64(const Rank2Args& a, const Rank2Plan& plan, cudaStream_t st);
 // Fill `plan` for M columns; returns false if the shape is not supported.
 bool plan_rank2_simt_f32(int Kp, int M, int R, bool rank1, Rank2Plan* plan, int cluster_budget = 0);
-bool plan_rank2_simt_f64(int Kp, int M, int R, bool rank1, Rank2Plan* plan);
+bool plan_rank2_simt_f64(int Kp, int M, int R, bool rank1, Rank2Plan* plan, int cluster_budget = 0);
 
 // Two-block split-role FP32 kernels (velocity and stress rows on different
 // CTAs): variant 2 synchronises with a cluster barrier per phase, variant 3

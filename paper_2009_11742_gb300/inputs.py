@@ -157,6 +157,15 @@ def batched_sizes(nroms: int = 64, seed: int = 0, pow2_m: bool = False):
     return [(int(k), int(m)) for k, m in zip(K, M)]
 
 
+def rank3_problems(nops: int, Kv: int, Ks: int, M: int, R: int = 0, seed: int = 0):
+    """nops operators (seeds seed .. seed + nops - 1) that share one time step:
+    the smallest of their own stable steps, so that every one of them is
+    stable.  Each keeps its own g, C and periods."""
+    first = [make_problem(Kv, Ks, M, R, seed=seed + i) for i in range(nops)]
+    dt = min(p.dt for p in first)
+    return [make_problem(Kv, Ks, M, R, seed=seed + i, dt=dt) for i in range(nops)]
+
+
 def batched_problems(nroms: int = 64, seed: int = 0, pow2_m: bool = False):
     """The batched workload: ROM i is drawn with seed i + 1."""
     out = []

@@ -37,7 +37,7 @@ PRECISIONS = {"fp64": ROM_FP64, "fp32": ROM_FP32, "tf32x3": ROM_TF32X3,
 EXPORTED = ["rom_create", "rom_destroy", "rom_spectral_radius", "rom_sync_status",
             "rom_get_dims", "rom_set_kernel", "rom_get_plan", "rom_set_tc_columns", "rom_set_wavelet", "rom_set_reference", "rom_autotune", "rom_autotune_batched", "rom_set_wait_limit",
             "rom_debug_inject_stall", "rom_run_rank2", "rom_run_rank2_ex", "rom_run_rank1",
-            "rom_run_rank1_ensemble", "rom_run_batched", "rom_adjoint",
+            "rom_run_rank1_ensemble", "rom_run_batched", "rom_run_rank3", "rom_adjoint",
             "rom_adjoint_workspace_size", "rom_rel_l2", "rom_spectral_radius_noalloc",
             "rom_trace_stats", "rom_status_string", "rom_last_error", "rom_version"]
 
@@ -80,6 +80,7 @@ def _signatures(lib):
         "rom_run_rank1": (_i, [_vp, _vp, _vp, _d, _i, _l, _i, _vp, _i, _vp]),
         "rom_run_rank1_ensemble": (_i, [_vp, _vp, _vp, _vp, _i, _i, _l, _i, _vp, _i, _vp]),
         "rom_run_batched": (_i, [ctypes.c_void_p, _i, _i, _i, _i, _vp]),
+        "rom_run_rank3": (_i, [ctypes.c_void_p, _i, _vp, _vp, _vp, _i, _i, _i, _vp, _i, _vp]),
         "rom_adjoint": (_i, [_vp, _vp, _vp, _vp, _i, _i, _vp, _i, _vp, _vp, _vp,
                              ctypes.POINTER(_d), _vp, ctypes.c_size_t, _i, _vp]),
         "rom_adjoint_workspace_size": (ctypes.c_size_t, [_vp, _i, _i, _i, _i]),
@@ -233,6 +234,37 @@ def rom_run_batched(jobs, njobs, nsteps, r, prec, stream):
     """jobs: a ctypes array of rom_job."""
     return load().rom_run_batched(ctypes.cast(jobs, ctypes.c_void_p), njobs, nsteps, r, prec,
                                   stream)
+
+
+def rom_run_rank3(handles, nops, V, S, T, M, nsteps, r, traces, prec, stream):
+    """Raw call: handles is a ctypes array of nops handle pointers."""
+    return load().rom_run_rank3(ctypes.cast(handles, ctypes.c_void_p), int(nops), V, S, T, int(M),
+                                int(nsteps), int(r), traces, int(prec), stream)
+
+
+def run_rank3(roms, V, S, T, nsteps, r=0, traces=None, prec="fp32", stream=None):
+    """Rank-3 run: len(roms) operators (sharing Kv, Ks, R, dt) times M forcings
+    in one launch.  V (Kv, M * nops) and S (Ks, M * nops) column-major device
+    tensors, operator i owning columns [i M, (i + 1) M); T (M * nops) periods
+    or None; traces (optional) floor(nsteps / r) records of R x (M nops)."""
+    p = PRECISIONS.get(prec, prec)
+    dt = Rom.dtype_of(p)
+    nops = len(roms)
+    h0 = roms[0]
+    Mt = V.shape[1]
+    if Mt % nops:
+        raise ValueError("V must have M * len(roms) columns")
+    M = Mt // nops
+    _check_colmajor(V, h0.Kv, Mt, "V", dt)
+    _check_colmajor(S, h0.Ks, Mt, "S", dt)
+    if T is not None:
+        _check_vec(T, Mt, "T", dt)
+    if traces is not None:
+        _check_vec(traces, (nsteps // r) * Mt * h0.R, "traces", dt)
+    arr = (ctypes.c_void_p * nops)(*[h.h for h in roms])
+    st = rom_run_rank3(arr, nops, _ptr(V), _ptr(S), _ptr(T), M, nsteps, r, _ptr(traces), p,
+                       _stream_handle(stream))
+    _chk(st, "rom_run_rank3")
 
 
 def run_batched(items, nsteps, r=0, prec="fp32", stream=None):
