@@ -11,9 +11,15 @@ eigendecomposition of the amplification matrix, the K = 1 textbook
 oscillator, superposition, exact zeros, time reversal, spectral radius vs.
 numpy's 2-norm, adjoint vs. finite differences and brute-force Jacobians,
 ensemble statistics vs. numpy's quantile and hand-computed order statistics.
+The full-order model (fom_oracle.c, Sec. 3): exact fixed points of the
+stencils (rigid rotation, hoop stress), exact discrete-energy invariance
+under the weights that make the flux-form operator skew-adjoint, the
+radial travel time at the shear speed, superposition.
 """
-from .oracle import (adjoint, build, energy, forward, inverse, max_threads,
-                     problem_forward, ricker, spectral_radius, trace_stats, wavelet)
+from .oracle import (FOM_APP_A, adjoint, build, energy, fom_dims, fom_forward, forward,
+                     inverse, max_threads, problem_forward, ricker, spectral_radius,
+                     trace_stats, wavelet)
 
-__all__ = ["adjoint", "build", "energy", "forward", "inverse", "max_threads",
-           "problem_forward", "ricker", "spectral_radius", "trace_stats", "wavelet"]
+__all__ = ["FOM_APP_A", "adjoint", "build", "energy", "fom_dims", "fom_forward", "forward",
+           "inverse", "max_threads", "problem_forward", "ricker", "spectral_radius",
+           "trace_stats", "wavelet"]

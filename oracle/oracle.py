@@ -21,6 +21,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "rom_oracle.c")
+_SRCS = [_SRC, os.path.join(_HERE, "fom_oracle.c")]
 _OUT_DIR = os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_OUT_DIR, "liborc.so")
 _lock = threading.Lock()
@@ -34,11 +35,11 @@ def build(force: bool = False) -> str:
     no FMA contraction so every product and sum rounds on its own)."""
     os.makedirs(_OUT_DIR, exist_ok=True)
     if (not force and os.path.exists(_LIB_PATH)
-            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
+            and all(os.path.getmtime(_LIB_PATH) >= os.path.getmtime(f) for f in _SRCS)):
         return _LIB_PATH
     tmp = _LIB_PATH + f".tmp{os.getpid()}"
     cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp",
-           "-ffp-contract=off", "-fno-fast-math", _SRC, "-o", tmp, "-lm"]
+           "-ffp-contract=off", "-fno-fast-math", *_SRCS, "-o", tmp, "-lm"]
     subprocess.run(cmd, check=True)
     os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
@@ -76,6 +77,16 @@ def _load():
             lib.orc_wavelet.restype = None
             lib.orc_wavelet.argtypes = [ctypes.c_int, _dp, _dp, ctypes.c_int, _dp, _dp]
             lib.orc_max_threads.restype = ctypes.c_int
+            _ip = ctypes.POINTER(ctypes.c_int)
+            lib.orc_fom_dims.restype = None
+            lib.orc_fom_dims.argtypes = [ctypes.c_int, ctypes.c_int, _ip, _ip, _ip]
+            lib.orc_fom_forward.restype = ctypes.c_int
+            lib.orc_fom_forward.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                            ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                            ctypes.c_double, _dp, _dp, _dp, ctypes.c_int,
+                                            ctypes.c_int, ctypes.c_long, ctypes.c_int, _dp, _dp,
+                                            ctypes.c_int, ctypes.c_int, _ip, ctypes.c_int, _dp,
+                                            ctypes.c_int]
             _lib = lib
     return _lib
 
@@ -297,3 +308,50 @@ def trace_stats(traces, probs):
         d = b - a
         q[n] = b - d * (1.0 - t) if t >= 0.5 else a + d * t
     return mean, q
+
+
+# ------------------------------------------------------------------ FOM --
+# The full-order shear-wave model of Sec. 3 (fom_oracle.c): staggered grid of
+# Nr x Nt intervals on r_cmb <= r <= r_earth, 0 <= theta <= pi.
+
+FOM_APP_A = {"rho": 2500.0, "vs": 5000.0, "r_cmb": 3480e3, "r_earth": 6371e3,
+             "dt": 0.05, "src_depth": 640e3}
+"""The homogeneous single-layer setup of App. A in SI units (rho in kg/m^3:
+the paper's "g/cm^3" is read as a unit slip), dt in s, lengths in m."""
+
+
+def fom_dims(Nr, Nt):
+    """(nv, n1, n2): velocity, sigma_rp and sigma_tp unknowns of the grid."""
+    a, b, c = ctypes.c_int(0), ctypes.c_int(0), ctypes.c_int(0)
+    _load().orc_fom_dims(int(Nr), int(Nt), ctypes.byref(a), ctypes.byref(b), ctypes.byref(c))
+    return a.value, b.value, c.value
+
+
+def fom_forward(Nr, Nt, V0, S10, S20, nsteps, src=-1, T=None, ftab=None, wavelet=1, n0=0,
+                recv=None, r=0, rho=2500.0, vs=5000.0, dt=0.05, r_cmb=3480e3,
+                r_earth=6371e3, threads=0):
+    """Leapfrog run of the FOM, one realization at a time.  V0 (nv, M),
+    S10 (n1, M), S20 (n2, M); src: velocity unknown of the point source (-1:
+    none); T (M) periods or ftab (nsteps, M); recv: velocity unknowns
+    recorded every r steps.  Returns (V, S1, S2, traces (nrec, nrecv, M) or None)."""
+    nv, n1, n2 = fom_dims(Nr, Nt)
+    V = _cm(V0).copy(order="F")
+    S1 = _cm(S10).copy(order="F")
+    S2 = _cm(S20).copy(order="F")
+    M = V.shape[1]
+    assert V.shape == (nv, M) and S1.shape == (n1, M) and S2.shape == (n2, M)
+    Tc = None if T is None else np.ascontiguousarray(np.asarray(T, np.float64))
+    Fc = None if ftab is None else np.ascontiguousarray(np.asarray(ftab, np.float64))
+    rc = None if recv is None else np.ascontiguousarray(np.asarray(recv, np.int32))
+    nrecv = 0 if rc is None else rc.size
+    nrec = nsteps // r if (r > 0 and nrecv > 0) else 0
+    tr = np.zeros((nrec, M, nrecv), np.float64) if nrec > 0 else None
+    ip = None if rc is None else rc.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
+    ret = _load().orc_fom_forward(int(Nr), int(Nt), float(r_cmb), float(r_earth), float(rho),
+                                  float(vs), float(dt), _ptr(V), _ptr(S1), _ptr(S2), M,
+                                  int(nsteps), int(n0), int(src), _ptr(Tc), _ptr(Fc),
+                                  int(wavelet), nrecv, ip, int(r) if nrec > 0 else 0, _ptr(tr),
+                                  int(threads))
+    _check(ret, "fom_forward")
+    traces = None if tr is None else np.ascontiguousarray(tr.transpose(0, 2, 1))
+    return np.ascontiguousarray(V), np.ascontiguousarray(S1), np.ascontiguousarray(S2), traces
