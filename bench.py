@@ -249,11 +249,12 @@ def main():
                     help="leapfrog steps per run (default: the workload's 10000; profiling only)")
     ap.add_argument("--only-rank2", action="store_true",
                     help="time the rank-2 runs only (no e2e, rank-1, oracle legs; profiling only)")
-    ap.add_argument("--workload", type=int, default=1, choices=[0, 1, 2, 3, 4, 5, 6],
+    ap.add_argument("--workload", type=int, default=1, choices=[0, 1, 2, 3, 4, 5, 6, 7],
                     help="0: K=128 M=16 N=1000 FP64; 1: K=512 FP32 (default, the headline); "
                          "2: K=1024 split precision; 3: 64 batched ROMs; 4: adjoint K=512 M=128 N=4000 c=64; "
                          "5: many-query UQ run (Kv=436, Ks=417, M=512, 20000 steps) with ensemble statistics; "
-                         "6: rank-3 (16 operators x 16 forcings, K=256, 10000 steps) in one launch")
+                         "6: rank-3 (16 operators x 16 forcings, K=256, 10000 steps) in one launch; "
+                         "7: rank-2 full-order model (512 x 2048 grid, 3.14 M unknowns, M=32, 1000 steps)")
     ap.add_argument("--prec", default=None, help="override the workload's precision")
     ap.add_argument("--tc-cols", type=int, default=0, help="tensor-core columns per block")
     args = ap.parse_args()
@@ -288,6 +289,8 @@ def main():
         return bench_adjoint(args, torch, dev, inputs, rom)
     if args.workload == 6:
         return bench_rank3(args, torch, dev, inputs, rom)
+    if args.workload == 7:
+        return bench_fom(args, torch, dev, inputs, rom)
 
     W = dict(WORKLOAD if args.workload == 1 else WORKLOAD2)
     if args.nsteps:
@@ -713,6 +716,72 @@ def bench_batched(args, torch, dev, inputs, rom):
                       "untuned": {"value": ss / t0, "ms_per_step": 1e3 * t0},
                       "autotune_probe_us_per_step": probe_us,
                       "columns_total": sum(p.M for p in probs)}), flush=True)
+    return 0
+
+
+def bench_fom(args, torch, dev, inputs, rom):
+    """Workload 7: the rank-2 full-order model of Sec. 3 at one of the
+    paper's FOM sizes (3,143,168 unknowns in App. B; here a 512 x 2048 grid,
+    3,141,633 unknowns) with the App. A setup: homogeneous layer, rho 2500,
+    vs 5000, dt 0.05 s, a source 640 km deep next to the axis, the first
+    derivative of a Gaussian with periods drawn in (60, 80) s, 1000 steps,
+    64 surface receivers every 10 steps.  M = 32 realizations in one run,
+    beside the rank-1 FOM (M = 1) on the same grid.  The roofline is HBM:
+    12 M bytes per unknown per step in FP32 (24 M in FP64)."""
+    import numpy as np
+    Nr, Nt, M = 512, 2048, 32
+    N = args.nsteps or 1000
+    prec = args.prec or "fp32"
+    es = 8 if prec == "fp64" else 4
+    tdt = torch.float64 if prec == "fp64" else torch.float32
+    f = rom.Fom(Nr, Nt)
+    src = f.source_index(640e3, j=1)
+    recv = torch.tensor([f.vindex(Nr - 1, j) for j in np.linspace(1, Nt - 1, 64).astype(int)],
+                        dtype=torch.int32, device=dev)
+    rng = np.random.default_rng(7)
+    nun = f.nv + f.n1 + f.n2
+    stream = torch.cuda.Stream(device=dev)
+
+    def timed(Mx):
+        V, S1, S2 = f.new_state(Mx, prec, device=dev)
+        T = torch.as_tensor(rng.uniform(60.0, 80.0, Mx), dtype=tdt, device=dev)
+        tr = torch.zeros((N // 10, recv.numel(), Mx), dtype=tdt, device=dev)
+
+        def one():
+            f.run(V, S1, S2, N, src=src, T=T, recv=recv, r=10, traces=tr, prec=prec, stream=stream)
+
+        with torch.cuda.stream(stream):
+            for _ in range(args.warmup):
+                one()
+        torch.cuda.synchronize()
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(args.steps)]
+        with torch.cuda.stream(stream):
+            for i in range(args.steps):
+                for x in (V, S1, S2):
+                    x.zero_()
+                evs[i][0].record(stream)
+                one()
+                evs[i][1].record(stream)
+        torch.cuda.synchronize()
+        return sum(a.elapsed_time(b) for a, b in evs) * 1e-3 / args.steps
+
+    t = timed(M)
+    t1 = timed(1)
+    byts = 12.0 * es / 4 * nun * M * N
+    pk, pk_kind = peaks()
+    hbm = pk.get("hbm_gbs")
+    out = {"only_rank2": True, "workload": f"fom-{Nr}x{Nt}-{nun}unknowns-M{M}-N{N}-{prec}",
+           "nsteps": N, "value": M * N / t, "unit": "sample-steps/s", "ms_per_step": 1e3 * t / N,
+           "unknown_updates_per_s": nun * M * N / t,
+           "roofline": {"bound": "hbm", "achieved": byts / t / 1e9, "peak": hbm, "unit": "GB/s",
+                        "frac": (byts / t / 1e9 / hbm) if hbm else None, "peak_kind": pk_kind,
+                        "basis": f"{3 * es} B per unknown per realization per step "
+                                 "(each of V, S read in both passes or written once: 3 accesses)"},
+           "rank1": {"value": N / t1, "ms_per_step": 1e3 * t1 / N,
+                     "achieved_gbs": 12.0 * es / 4 * nun * N / t1 / 1e9},
+           "rank2_over_rank1_per_realization": (M * N / t) / (N / t1)}
+    print(json.dumps(out), flush=True)
     return 0
 
 

@@ -426,6 +426,59 @@ const char* rom_last_error(void);
 /* Library version as major * 10000 + minor * 100 + patch. */
 int rom_version(void);
 
+/*
+ * ---- Rank-2 full-order model (FOM) of the test case (Sec. 3) ----
+ *
+ * The axisymmetric elastic shear-wave system of Eq. (fom_asym) in
+ * velocity-stress form on the shell r_cmb <= r <= r_earth, 0 <= theta <= pi,
+ * a homogeneous material (density rho, shear speed vs, mu = rho vs^2; the
+ * single layer of App. A), discretized on a second-order staggered grid of
+ * Nr x Ntheta intervals in flux form:
+ *     v        at (r_{i+1/2}, theta_j),       i in [0, Nr), j in [1, Ntheta)
+ *     sigma_rp at (r_i, theta_j),             i in [1, Nr), j in [1, Ntheta)
+ *     sigma_tp at (r_{i+1/2}, theta_{j+1/2}), i in [0, Nr), j in [1, Ntheta - 1)
+ * with v = 0 on the axis and sigma_rp = 0 on the axis and the free surfaces
+ * (Sec. 3), and sigma_tp = 0 next to the axis.  At most four non-zeros per
+ * velocity row and two per stress row.  Advanced by the velocity-first
+ * leapfrog for M forcing realizations at once (the rank-2 FOM,
+ * Eq. (shwave_ode_tensor)); each run is one point source on one velocity
+ * unknown whose signal has period T_m (ROM_WAVELET_*, delay 1.5 T).
+ */
+typedef struct rom_fom_s* rom_fom_t;
+
+/* rom_fom_create -- grid, material and time step; lengths in m, rho in
+ * kg/m^3, vs in m/s, dt in s.  The caller chooses a stable dt (the leapfrog
+ * needs dt rho(L) < 2).  Synchronous.  Errors: ROM_E_INVAL (Nr < 2 or
+ * > 65535, Ntheta < 3, non-positive or non-finite values, more than 2^31 unknowns
+ * per field), ROM_E_NOMEM, ROM_E_CUDA. */
+rom_status rom_fom_create(int Nr, int Ntheta, double r_cmb, double r_earth, double rho, double vs,
+                          double dt, rom_fom_t* out);
+rom_status rom_fom_destroy(rom_fom_t f);
+
+/* Unknowns per realization: velocity Nr (Ntheta - 1), sigma_rp
+ * (Nr - 1)(Ntheta - 1), sigma_tp Nr (Ntheta - 2). */
+rom_status rom_fom_dims(rom_fom_t f, int* nv, int* n1, int* n2);
+
+/*
+ * rom_fom_run -- nsteps leapfrog steps (t_n = (n0 + n) dt) of M realizations,
+ * in place.  States are unknown-major with the M realizations contiguous
+ * per unknown (device, FP64 or FP32 per prec):
+ *     V[k M + m], k = i (Ntheta - 1) + (j - 1);
+ *     S1[k M + m], k = (i - 1)(Ntheta - 1) + (j - 1);
+ *     S2[k M + m], k = i (Ntheta - 2) + (j - 1).
+ * T (M periods, or NULL for no forcing) drives velocity unknown src.
+ * recv (device int[nrecv], velocity unknowns) are recorded after every step
+ * with (n + 1) mod r == 0 into traces[(rec nrecv + k) M + m] (NULL: none).
+ * The run is a CUDA graph of 64 steps, captured on the first call for a
+ * given set of buffers and arguments and replayed; it is asynchronous on
+ * `stream`.  A handle is not re-entrant across concurrent streams.  Errors:
+ * ROM_E_INVAL (host buffers, bad indices), ROM_E_UNSUPPORTED (prec other than
+ * ROM_FP32 / ROM_FP64), ROM_E_CUDA.
+ */
+rom_status rom_fom_run(rom_fom_t f, void* V, void* S1, void* S2, int M, int nsteps, long n0,
+                       int src, const void* T, int wavelet, const int* recv, int nrecv, int r,
+                       void* traces, int prec, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -19,6 +19,12 @@ namespace {
 
 thread_local char g_last_error[256] = "";
 
+}  // namespace
+
+void romk::set_last_error(const char* msg) { snprintf(g_last_error, sizeof(g_last_error), "%s", msg); }
+
+namespace {
+
 rom_status cuda_fail(cudaError_t e, const char* where) {
     snprintf(g_last_error, sizeof(g_last_error), "%s: %s", where, cudaGetErrorString(e));
     return e == cudaErrorMemoryAllocation ? ROM_E_NOMEM : ROM_E_CUDA;

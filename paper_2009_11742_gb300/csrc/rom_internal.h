@@ -8,6 +8,9 @@
 
 namespace romk {
 
+// Record a message for rom_last_error() (this thread).
+void set_last_error(const char* msg);
+
 // Arguments of one rank-2 launch (all device pointers).  Element type T of
 // the state-like buffers is double for ROM_FP64 and float otherwise.
 // One operator of a grouped (rank-3) launch: its handle's device copies.

@@ -39,7 +39,8 @@ EXPORTED = ["rom_create", "rom_destroy", "rom_spectral_radius", "rom_sync_status
             "rom_debug_inject_stall", "rom_run_rank2", "rom_run_rank2_ex", "rom_run_rank1",
             "rom_run_rank1_ensemble", "rom_run_batched", "rom_run_rank3", "rom_adjoint",
             "rom_adjoint_workspace_size", "rom_rel_l2", "rom_spectral_radius_noalloc",
-            "rom_trace_stats", "rom_status_string", "rom_last_error", "rom_version"]
+            "rom_trace_stats", "rom_fom_create", "rom_fom_destroy", "rom_fom_dims", "rom_fom_run",
+            "rom_status_string", "rom_last_error", "rom_version"]
 
 _lock = threading.Lock()
 _lib = None
@@ -87,6 +88,11 @@ def _signatures(lib):
         "rom_rel_l2": (_i, [_vp, _i, _vp, _i, ctypes.c_size_t, ctypes.POINTER(_d), _vp]),
         "rom_spectral_radius_noalloc": (_i, [_vp, _vp, _i, _i, ctypes.POINTER(_d), _vp]),
         "rom_trace_stats": (_i, [_vp, _i, _i, _i, ctypes.POINTER(_d), _i, _vp, _vp, _vp]),
+        "rom_fom_create": (_i, [_i, _i, _d, _d, _d, _d, _d, ctypes.POINTER(_vp)]),
+        "rom_fom_destroy": (_i, [_vp]),
+        "rom_fom_dims": (_i, [_vp, ctypes.POINTER(_i), ctypes.POINTER(_i), ctypes.POINTER(_i)]),
+        "rom_fom_run": (_i, [_vp, _vp, _vp, _vp, _i, _i, ctypes.c_long, _i, _vp, _i, _vp, _i, _i,
+                             _vp, _i, _vp]),
         "rom_status_string": (ctypes.c_char_p, [_i]),
         "rom_last_error": (ctypes.c_char_p, []),
         "rom_version": (_i, []),
@@ -643,3 +649,78 @@ def rel_l2(x, ref, stream=None) -> float:
                        xc.numel(), _stream_handle(stream))
     _chk(st, "rom_rel_l2")
     return v
+
+
+# ------------------------------------------------------------------ FOM --
+
+def rom_fom_create(Nr, Ntheta, r_cmb, r_earth, rho, vs, dt):
+    """Raw call.  Returns (status, handle)."""
+    h = _vp()
+    st = load().rom_fom_create(int(Nr), int(Ntheta), float(r_cmb), float(r_earth), float(rho),
+                               float(vs), float(dt), ctypes.byref(h))
+    return st, h.value
+
+
+def rom_fom_destroy(h):
+    return load().rom_fom_destroy(h)
+
+
+def rom_fom_dims(h):
+    """Returns (status, nv, n1, n2)."""
+    a, b, c = _i(0), _i(0), _i(0)
+    st = load().rom_fom_dims(h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c))
+    return st, a.value, b.value, c.value
+
+
+def rom_fom_run(h, V, S1, S2, M, nsteps, n0, src, T, wavelet, recv, nrecv, r, traces, prec, stream):
+    return load().rom_fom_run(h, V, S1, S2, int(M), int(nsteps), int(n0), int(src), T, int(wavelet),
+                              recv, int(nrecv), int(r), traces, int(prec), stream)
+
+
+class Fom:
+    """The rank-2 full-order shear-wave model of Sec. 3 (rom_fom_* of the C
+    ABI).  Defaults: the homogeneous layer of App. A (rho 2500 kg/m^3, vs
+    5000 m/s, dt 0.05 s) on the mantle shell 3480-6371 km.  States are
+    unknown-major (n, M) contiguous device tensors, M realizations per row."""
+
+    def __init__(self, Nr, Ntheta, r_cmb=3480e3, r_earth=6371e3, rho=2500.0, vs=5000.0, dt=0.05):
+        st, h = rom_fom_create(Nr, Ntheta, r_cmb, r_earth, rho, vs, dt)
+        _chk(st, "rom_fom_create")
+        self.h = h
+        self.Nr, self.Ntheta = int(Nr), int(Ntheta)
+        self.r_cmb, self.r_earth, self.rho, self.vs, self.dt = r_cmb, r_earth, rho, vs, dt
+        st, self.nv, self.n1, self.n2 = rom_fom_dims(h)
+        _chk(st, "rom_fom_dims")
+
+    def __del__(self):
+        if getattr(self, "h", None):
+            rom_fom_destroy(self.h)
+            self.h = None
+
+    def vindex(self, i, j):
+        """Velocity unknown of grid point (r_{i+1/2}, theta_j)."""
+        return int(i) * (self.Ntheta - 1) + (int(j) - 1)
+
+    def source_index(self, depth, j=1):
+        """Velocity unknown in the radial cell at `depth` below r_earth, on
+        polar line j (default: next to the symmetry axis)."""
+        dr = (self.r_earth - self.r_cmb) / self.Nr
+        i = int((self.r_earth - depth - self.r_cmb) / dr)
+        return self.vindex(min(max(i, 0), self.Nr - 1), j)
+
+    def new_state(self, M, prec="fp32", device="cuda"):
+        torch = _torch()
+        dt = torch.float64 if prec == "fp64" else torch.float32
+        return tuple(torch.zeros((n, M), dtype=dt, device=device) for n in (self.nv, self.n1, self.n2))
+
+    def run(self, V, S1, S2, nsteps, src=-1, T=None, wavelet=ROM_WAVELET_GAUSS1, recv=None, r=0,
+            traces=None, prec="fp32", n0=0, stream=None):
+        p = PRECISIONS.get(prec, prec)
+        M = V.shape[1]
+        for x, n, name in ((V, self.nv, "V"), (S1, self.n1, "S1"), (S2, self.n2, "S2")):
+            if tuple(x.shape) != (n, M) or not x.is_contiguous():
+                raise ValueError(f"{name}: need a contiguous ({n}, {M}) tensor")
+        nrecv = 0 if recv is None else recv.numel()
+        st = rom_fom_run(self.h, _ptr(V), _ptr(S1), _ptr(S2), M, nsteps, n0, src, _ptr(T), wavelet,
+                         _ptr(recv), nrecv, r, _ptr(traces), p, _stream_handle(stream))
+        _chk(st, "rom_fom_run")
