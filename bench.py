@@ -727,7 +727,8 @@ def bench_fom(args, torch, dev, inputs, rom):
     derivative of a Gaussian with periods drawn in (60, 80) s, 1000 steps,
     64 surface receivers every 10 steps.  M = 32 realizations in one run,
     beside the rank-1 FOM (M = 1) on the same grid.  The roofline is HBM:
-    12 M bytes per unknown per step in FP32 (24 M in FP64)."""
+    8 M bytes per unknown per step in FP32 (16 M in FP64), every state value
+    read and written once."""
     import numpy as np
     Nr, Nt, M = 512, 2048, 32
     N = args.nsteps or 1000
@@ -768,7 +769,8 @@ def bench_fom(args, torch, dev, inputs, rom):
 
     t = timed(M)
     t1 = timed(1)
-    byts = 12.0 * es / 4 * nun * M * N
+    # the algorithmic minimum of a step: every state value read once and written once
+    byts = 2.0 * es * nun * M * N
     pk, pk_kind = peaks()
     hbm = pk.get("hbm_gbs")
     out = {"only_rank2": True, "workload": f"fom-{Nr}x{Nt}-{nun}unknowns-M{M}-N{N}-{prec}",
@@ -776,10 +778,10 @@ def bench_fom(args, torch, dev, inputs, rom):
            "unknown_updates_per_s": nun * M * N / t,
            "roofline": {"bound": "hbm", "achieved": byts / t / 1e9, "peak": hbm, "unit": "GB/s",
                         "frac": (byts / t / 1e9 / hbm) if hbm else None, "peak_kind": pk_kind,
-                        "basis": f"{3 * es} B per unknown per realization per step "
-                                 "(each of V, S read in both passes or written once: 3 accesses)"},
+                        "basis": f"{2 * es} B per unknown per realization per step "
+                                 "(every state value read once and written once; the fused pass)"},
            "rank1": {"value": N / t1, "ms_per_step": 1e3 * t1 / N,
-                     "achieved_gbs": 12.0 * es / 4 * nun * N / t1 / 1e9},
+                     "achieved_gbs": 2.0 * es * nun * N / t1 / 1e9},
            "rank2_over_rank1_per_realization": (M * N / t) / (N / t1)}
     print(json.dumps(out), flush=True)
     return 0

@@ -455,6 +455,14 @@ rom_status rom_fom_create(int Nr, int Ntheta, double r_cmb, double r_earth, doub
                           double dt, rom_fom_t* out);
 rom_status rom_fom_destroy(rom_fom_t f);
 
+/* rom_fom_set_passes -- 1 (default): one fused pass per step that reads
+ * and writes every state value once (8 bytes per unknown and realization
+ * in FP32), ping-ponging between the caller's buffers and a library-owned
+ * second set (allocated on the first run that needs it, sized by M); 2: a
+ * velocity pass then a stress pass in place (12 bytes).  Both compute the
+ * same arithmetic.  ROM_E_INVAL for another value. */
+rom_status rom_fom_set_passes(rom_fom_t f, int passes);
+
 /* Unknowns per realization: velocity Nr (Ntheta - 1), sigma_rp
  * (Nr - 1)(Ntheta - 1), sigma_tp Nr (Ntheta - 2). */
 rom_status rom_fom_dims(rom_fom_t f, int* nv, int* n1, int* n2);
@@ -471,7 +479,7 @@ rom_status rom_fom_dims(rom_fom_t f, int* nv, int* n1, int* n2);
  * with (n + 1) mod r == 0 into traces[(rec nrecv + k) M + m] (NULL: none).
  * The run is a CUDA graph of 64 steps, captured on the first call for a
  * given set of buffers and arguments and replayed; it is asynchronous on
- * `stream`.  A handle is not re-entrant across concurrent streams.  Errors:
+ * `stream` (the first fused run allocates the second buffer set).  A handle is not re-entrant across concurrent streams.  Errors:
  * ROM_E_INVAL (host buffers, bad indices), ROM_E_UNSUPPORTED (prec other than
  * ROM_FP32 / ROM_FP64), ROM_E_CUDA.
  */

@@ -43,6 +43,7 @@ namespace romk {
 
 constexpr int kFomThreads = 256;
 constexpr int kFomGraphSteps = 64;
+constexpr int kFomSegRows = 32;  // radial rows per block of the fused pass
 
 struct FomCtl {
     long long step, nsteps, n0;
@@ -74,6 +75,12 @@ struct FomArgs {
     const FomCtl* ctl;
     int Nr, Nt, M, src, nrecv, r, wavelet;
     double dt, rho;
+    // fused single pass: second buffer set (ping-pong by step parity), the
+    // source's grid point and the radial rows per block
+    T* V2;
+    T* S12;
+    T* S22;
+    int fused, src_i, src_j, seg_rows;
 };
 
 // Vector of VW consecutive realizations (16-byte loads when VW > 1).
@@ -163,9 +170,113 @@ __global__ void __launch_bounds__(kFomThreads) fom_record_kernel(const FomArgs<T
     if (n >= a.ctl->nsteps || ((n + 1) % a.r) != 0) return;
     const long long rec = (n + 1) / a.r - 1;
     const int tot = a.nrecv * a.M;
+    const T* V = (a.fused && !(n & 1)) ? a.V2 : a.V;  // the buffer this step wrote
     for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < tot; idx += gridDim.x * blockDim.x) {
         const int kk = idx / a.M, m = idx - kk * a.M;
-        a.traces[(rec * a.nrecv + kk) * a.M + m] = a.V[(long long)a.recv[kk] * a.M + m];
+        a.traces[(rec * a.nrecv + kk) * a.M + m] = V[(long long)a.recv[kk] * a.M + m];
+    }
+}
+
+// Fused single pass of one step.  Reads the old state and writes the new
+// one into the other buffer set (step parity picks which), so neighbouring
+// blocks never see each other's writes within a step.  Block = a strip of
+// TJ = blockDim.y - 1 polar columns (thread row ty; ty = TJ is a halo column
+// whose new velocity the strip's last stress sigma_tp needs) times a segment
+// of seg_rows radial rows, marched outward in r: the lower sigma_rp face and
+// the previous row's new velocity stay in registers, the row's new velocity
+// goes through shared memory to the left neighbour.  The segment starts one
+// row early to recompute the new velocity below it.  Every state value is
+// read once and written once per step (plus the halo column and row), 8 M
+// bytes per unknown in FP32, against 12 M for the two passes.  The halo
+// values are computed by the same arithmetic as their owners' (forcing
+// included), so they are bitwise the owners' values.
+template <typename T, int VW>
+__global__ void __launch_bounds__(kFomThreads) fom_fused_kernel(const FomArgs<T> a) {
+    const long long n = a.ctl->step;
+    if (n >= a.ctl->nsteps) return;
+    const bool odd = (n & 1) != 0;
+    const T* __restrict__ Vo = odd ? a.V2 : a.V;
+    const T* __restrict__ S1o = odd ? a.S12 : a.S1;
+    const T* __restrict__ S2o = odd ? a.S22 : a.S2;
+    T* __restrict__ Vn = odd ? a.V : a.V2;
+    T* __restrict__ S1n = odd ? a.S1 : a.S12;
+    T* __restrict__ S2n = odd ? a.S2 : a.S22;
+    const int Nt1 = a.Nt - 1, Nt2 = a.Nt - 2, M = a.M;
+    const int TJ = (int)blockDim.y - 1;
+    const int nstrip = (Nt1 + TJ - 1) / TJ;
+    const int strip = (int)blockIdx.x % nstrip, seg = (int)blockIdx.x / nstrip;
+    const int ia = seg * a.seg_rows;
+    const int ib = min(a.Nr, ia + a.seg_rows);
+    const int ty = threadIdx.y, tx = threadIdx.x;
+    const int j = strip * TJ + ty + 1;            // polar index of this thread's column
+    const bool act = j <= Nt1;                    // a velocity column
+    const bool own = act && ty < TJ;              // written by this block
+    const T dt = (T)a.dt;
+    const T pp = act ? a.tb.pt_p[j] : T(0), pm = act ? a.tb.pt_m[j] : T(0);
+    const bool has_s2 = own && j <= Nt2;
+    const T wp = has_s2 ? a.tb.w_p[j] : T(0), wm = has_s2 ? a.tb.w_m[j] : T(0);
+    const bool src_col = a.Tper && act && j == a.src_j;
+    const T csrc = (T)(a.dt / a.rho);
+    extern __shared__ __align__(16) unsigned char fom_smem[];
+    T* row = reinterpret_cast<T*>(fom_smem);      // [blockDim.y][blockDim.x * VW] new velocity
+    const int i0 = ia > 0 ? ia - 1 : 0;
+    const int chunk = (int)blockDim.x * VW;
+    for (int mb = 0; mb < M; mb += chunk) {       // same trip count in every thread
+        const int m0 = mb + tx * VW;
+        const bool lane = act && m0 < M;
+        T prev_s1[VW], prev_v[VW];
+#pragma unroll
+        for (int q = 0; q < VW; ++q) prev_s1[q] = prev_v[q] = T(0);
+        if (lane && i0 >= 1) fom_load<T, VW>(S1o + ((size_t)(i0 - 1) * Nt1 + (j - 1)) * M + m0, prev_s1);
+        for (int i = i0; i < ib; ++i) {
+            T s1u[VW], s2r[VW], s2l[VW], vo[VW], vn[VW];
+#pragma unroll
+            for (int q = 0; q < VW; ++q) s1u[q] = s2r[q] = s2l[q] = vo[q] = T(0);
+            if (lane) {
+                if (i + 1 <= a.Nr - 1) fom_load<T, VW>(S1o + ((size_t)i * Nt1 + (j - 1)) * M + m0, s1u);
+                if (j <= Nt2) fom_load<T, VW>(S2o + ((size_t)i * Nt2 + (j - 1)) * M + m0, s2r);
+                if (j >= 2) fom_load<T, VW>(S2o + ((size_t)i * Nt2 + (j - 2)) * M + m0, s2l);
+                fom_load<T, VW>(Vo + ((size_t)i * Nt1 + (j - 1)) * M + m0, vo);
+            }
+            const T cp = a.tb.cr_p[i], cm = a.tb.cr_m[i], ir = a.tb.inv_rh[i];
+#pragma unroll
+            for (int q = 0; q < VW; ++q) vn[q] = vo[q] + dt * (cp * s1u[q] - cm * prev_s1[q] + ir * (pp * s2r[q] - pm * s2l[q]));
+            if (lane && src_col && i == a.src_i) {
+#pragma unroll
+                for (int q = 0; q < VW; ++q)
+                    vn[q] = vn[q] + csrc * (T)wavelet_eval(a.wavelet, a.ctl->n0 + n, a.dt, a.Tper[m0 + q]);
+            }
+            if (i >= ia) {                        // block-uniform
+                if (own && m0 < M) fom_store<T, VW>(Vn + ((size_t)i * Nt1 + (j - 1)) * M + m0, vn);
+#pragma unroll
+                for (int q = 0; q < VW; ++q) row[(ty * blockDim.x + tx) * VW + q] = vn[q];
+                __syncthreads();
+                if (own && m0 < M) {
+                    if (i >= 1) {
+                        const T qu = a.tb.q_u[i], qd = a.tb.q_d[i];
+                        T s1[VW];
+#pragma unroll
+                        for (int q = 0; q < VW; ++q) s1[q] = prev_s1[q] + dt * (qu * vn[q] - qd * prev_v[q]);
+                        fom_store<T, VW>(S1n + ((size_t)(i - 1) * Nt1 + (j - 1)) * M + m0, s1);
+                    }
+                    if (has_s2) {
+                        T s2[VW];
+#pragma unroll
+                        for (int q = 0; q < VW; ++q) {
+                            const T vr = row[((ty + 1) * blockDim.x + tx) * VW + q];
+                            s2[q] = s2r[q] + dt * ir * (wp * vr - wm * vn[q]);
+                        }
+                        fom_store<T, VW>(S2n + ((size_t)i * Nt2 + (j - 1)) * M + m0, s2);
+                    }
+                }
+                __syncthreads();
+            }
+#pragma unroll
+            for (int q = 0; q < VW; ++q) {
+                prev_s1[q] = s1u[q];
+                prev_v[q] = vn[q];
+            }
+        }
     }
 }
 
@@ -244,6 +355,9 @@ struct rom_fom_s {
     cudaStream_t cap = nullptr;
     std::mutex mu;
     std::map<std::vector<long long>, cudaGraphExec_t> graphs;
+    int passes = 1;          // 1: fused single pass (default), 2: velocity and stress passes
+    void* ws = nullptr;      // second state buffer set of the fused pass
+    size_t ws_bytes = 0;
 };
 
 namespace {
@@ -261,7 +375,8 @@ cudaError_t capture_steps(rom_fom_s* f, const FomArgs<T>& a, long long nv, long 
     // 16-byte vectors along m when every row starts on a 16-byte boundary
     constexpr int VWIDE = 16 / (int)sizeof(T);
     bool wide = a.M % VWIDE == 0;
-    for (const void* p : {(const void*)a.V, (const void*)a.S1, (const void*)a.S2})
+    for (const void* p : {(const void*)a.V, (const void*)a.S1, (const void*)a.S2, (const void*)a.V2,
+                          (const void*)a.S12, (const void*)a.S22})
         wide = wide && ((uintptr_t)p % 16 == 0);
     const int vw = wide ? VWIDE : 1;
     // block: bx realization groups x by polar points; persistent grid of
@@ -289,9 +404,19 @@ cudaError_t capture_steps(rom_fom_s* f, const FomArgs<T>& a, long long nv, long 
         const long long b = (work + kFomThreads - 1) / kFomThreads;
         return (unsigned)(b < 1 ? 1 : (b > 1024 ? 1024 : b));
     };
+    // fused pass: strips of by - 1 polar columns x segments of seg_rows radial rows
+    const unsigned gfused = (unsigned)(((a.Nt - 1 + by - 2) / (by - 1)) * ((a.Nr + a.seg_rows - 1) / a.seg_rows));
+    const size_t fsmem = (size_t)by * bx * vw * sizeof(T);
     cudaError_t e = cudaStreamBeginCapture(f->cap, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return e;
-    for (int s = 0; s < kFomGraphSteps && e == cudaSuccess; ++s) {
+    for (int s = 0; s < kFomGraphSteps && e == cudaSuccess && a.fused; ++s) {
+        if (wide) fom_fused_kernel<T, VWIDE><<<gfused, blk, fsmem, f->cap>>>(a);
+        else fom_fused_kernel<T, 1><<<gfused, blk, fsmem, f->cap>>>(a);
+        if (a.traces) fom_record_kernel<T><<<blocks((long long)a.nrecv * a.M), kFomThreads, 0, f->cap>>>(a);
+        fom_tick_kernel<<<1, 1, 0, f->cap>>>(const_cast<FomCtl*>(a.ctl));
+        e = cudaGetLastError();
+    }
+    for (int s = 0; s < kFomGraphSteps && e == cudaSuccess && !a.fused; ++s) {
         if (wide) fom_velocity_kernel<T, VWIDE><<<gv, blk, 0, f->cap>>>(a);
         else fom_velocity_kernel<T, 1><<<gv, blk, 0, f->cap>>>(a);
         if (a.Tper) fom_source_kernel<T><<<blocks(a.M), kFomThreads, 0, f->cap>>>(a);
@@ -387,8 +512,16 @@ rom_status rom_fom_destroy(rom_fom_t f) {
     cudaFree(f->tables[0]);
     cudaFree(f->tables[1]);
     cudaFree(f->ctl);
+    cudaFree(f->ws);
     if (f->cap) cudaStreamDestroy(f->cap);
     delete f;
+    return ROM_OK;
+}
+
+rom_status rom_fom_set_passes(rom_fom_t f, int passes) {
+    if (!f || (passes != 1 && passes != 2)) return ROM_E_INVAL;
+    std::lock_guard<std::mutex> lk(f->mu);
+    f->passes = passes;
     return ROM_OK;
 }
 
@@ -425,10 +558,57 @@ rom_status rom_fom_run(rom_fom_t f, void* V, void* S1, void* S2, int M, int nste
     if (nsteps == 0) return ROM_OK;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     std::lock_guard<std::mutex> lk(f->mu);
+    // the fused pass writes every other step into a second buffer set
+    const bool fused = f->passes == 1;
+    const size_t es = prec == ROM_FP64 ? 8 : 4;
+    const size_t need = (size_t)(nv + ns) * (size_t)M * es + 64;
+    if (fused && f->ws_bytes < need) {
+        cudaStreamSynchronize(st);
+        cudaDeviceSynchronize();
+        for (auto& kv : f->graphs) cudaGraphExecDestroy(kv.second);
+        f->graphs.clear();
+        cudaFree(f->ws);
+        f->ws = nullptr;
+        f->ws_bytes = 0;
+        cudaError_t em = cudaMalloc(&f->ws, need);
+        if (em != cudaSuccess) {
+            set_last_error(cudaGetErrorString(em));
+            return em == cudaErrorMemoryAllocation ? ROM_E_NOMEM : ROM_E_CUDA;
+        }
+        f->ws_bytes = need;
+    }
+    char* w = static_cast<char*>(f->ws);
+    auto al = [](size_t b) { return (b + 255) & ~(size_t)255; };
+    void* V2 = fused ? w : nullptr;
+    void* S12 = fused ? w + al((size_t)nv * M * es) : nullptr;
+    void* S22 = fused ? w + al((size_t)nv * M * es) + al((size_t)(f->Nr - 1) * (f->Nt - 1) * M * es) : nullptr;
+    if (fused && (size_t)((char*)S22 - w) + (size_t)f->Nr * (f->Nt - 2) * M * es > f->ws_bytes) {
+        // the aligned layout needs a little more than `need`: grow once more
+        cudaDeviceSynchronize();
+        for (auto& kv : f->graphs) cudaGraphExecDestroy(kv.second);
+        f->graphs.clear();
+        cudaFree(f->ws);
+        f->ws_bytes = 0;
+        const size_t need2 = need + 1024;
+        cudaError_t em = cudaMalloc(&f->ws, need2);
+        if (em != cudaSuccess) {
+            f->ws = nullptr;
+            set_last_error(cudaGetErrorString(em));
+            return em == cudaErrorMemoryAllocation ? ROM_E_NOMEM : ROM_E_CUDA;
+        }
+        f->ws_bytes = need2;
+        w = static_cast<char*>(f->ws);
+        V2 = w;
+        S12 = w + al((size_t)nv * M * es);
+        S22 = w + al((size_t)nv * M * es) + al((size_t)(f->Nr - 1) * (f->Nt - 1) * M * es);
+    }
+    const int src_i = src >= 0 ? (int)(src / (f->Nt - 1)) : -1;
+    const int src_j = src >= 0 ? (int)(src % (f->Nt - 1)) + 1 : -1;
     const std::vector<long long> key = {(long long)(uintptr_t)V, (long long)(uintptr_t)S1,
                                         (long long)(uintptr_t)S2, M, src, (long long)(uintptr_t)T,
                                         wavelet, (long long)(uintptr_t)recv, nrecv, traces ? r : 0,
-                                        (long long)(uintptr_t)traces, prec};
+                                        (long long)(uintptr_t)traces, prec, fused,
+                                        (long long)(uintptr_t)V2};
     auto it = f->graphs.find(key);
     if (it == f->graphs.end()) {
         cudaGraphExec_t ge = nullptr;
@@ -437,13 +617,17 @@ rom_status rom_fom_run(rom_fom_t f, void* V, void* S1, void* S2, int M, int nste
             FomArgs<double> a = {tables_of<double>(f), static_cast<double*>(V), static_cast<double*>(S1),
                                  static_cast<double*>(S2), static_cast<const double*>(T), recv,
                                  static_cast<double*>(traces), f->ctl, f->Nr, f->Nt, M, src, nrecv,
-                                 traces ? r : 1, wavelet, f->dt, f->rho};
+                                 traces ? r : 1, wavelet, f->dt, f->rho,
+                                 static_cast<double*>(V2), static_cast<double*>(S12), static_cast<double*>(S22),
+                                 fused ? 1 : 0, src_i, src_j, kFomSegRows};
             e = capture_steps<double>(f, a, nv, ns, &ge);
         } else {
             FomArgs<float> a = {tables_of<float>(f), static_cast<float*>(V), static_cast<float*>(S1),
                                 static_cast<float*>(S2), static_cast<const float*>(T), recv,
                                 static_cast<float*>(traces), f->ctl, f->Nr, f->Nt, M, src, nrecv,
-                                traces ? r : 1, wavelet, f->dt, f->rho};
+                                traces ? r : 1, wavelet, f->dt, f->rho,
+                                static_cast<float*>(V2), static_cast<float*>(S12), static_cast<float*>(S22),
+                                fused ? 1 : 0, src_i, src_j, kFomSegRows};
             e = capture_steps<float>(f, a, nv, ns, &ge);
         }
         if (e != cudaSuccess) {
@@ -461,6 +645,14 @@ rom_status rom_fom_run(rom_fom_t f, void* V, void* S1, void* S2, int M, int nste
     cudaError_t e = cudaGetLastError();
     const int reps = (nsteps + kFomGraphSteps - 1) / kFomGraphSteps;
     for (int k = 0; k < reps && e == cudaSuccess; ++k) e = cudaGraphLaunch(it->second, st);
+    if (e == cudaSuccess && fused && (nsteps & 1)) {
+        // an odd number of fused steps leaves the result in the second buffer set
+        e = cudaMemcpyAsync(V, V2, (size_t)nv * M * es, cudaMemcpyDeviceToDevice, st);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(S1, S12, (size_t)(f->Nr - 1) * (f->Nt - 1) * M * es, cudaMemcpyDeviceToDevice, st);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(S2, S22, (size_t)f->Nr * (f->Nt - 2) * M * es, cudaMemcpyDeviceToDevice, st);
+    }
     if (e != cudaSuccess) {
         set_last_error(cudaGetErrorString(e));
         return ROM_E_CUDA;

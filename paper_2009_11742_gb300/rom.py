@@ -40,6 +40,7 @@ EXPORTED = ["rom_create", "rom_destroy", "rom_spectral_radius", "rom_sync_status
             "rom_run_rank1_ensemble", "rom_run_batched", "rom_run_rank3", "rom_adjoint",
             "rom_adjoint_workspace_size", "rom_rel_l2", "rom_spectral_radius_noalloc",
             "rom_trace_stats", "rom_fom_create", "rom_fom_destroy", "rom_fom_dims", "rom_fom_run",
+            "rom_fom_set_passes",
             "rom_status_string", "rom_last_error", "rom_version"]
 
 _lock = threading.Lock()
@@ -90,6 +91,7 @@ def _signatures(lib):
         "rom_trace_stats": (_i, [_vp, _i, _i, _i, ctypes.POINTER(_d), _i, _vp, _vp, _vp]),
         "rom_fom_create": (_i, [_i, _i, _d, _d, _d, _d, _d, ctypes.POINTER(_vp)]),
         "rom_fom_destroy": (_i, [_vp]),
+        "rom_fom_set_passes": (_i, [_vp, _i]),
         "rom_fom_dims": (_i, [_vp, ctypes.POINTER(_i), ctypes.POINTER(_i), ctypes.POINTER(_i)]),
         "rom_fom_run": (_i, [_vp, _vp, _vp, _vp, _i, _i, ctypes.c_long, _i, _vp, _i, _vp, _i, _i,
                              _vp, _i, _vp]),
@@ -665,6 +667,10 @@ def rom_fom_destroy(h):
     return load().rom_fom_destroy(h)
 
 
+def rom_fom_set_passes(h, passes):
+    return load().rom_fom_set_passes(h, int(passes))
+
+
 def rom_fom_dims(h):
     """Returns (status, nv, n1, n2)."""
     a, b, c = _i(0), _i(0), _i(0)
@@ -696,6 +702,11 @@ class Fom:
         if getattr(self, "h", None):
             rom_fom_destroy(self.h)
             self.h = None
+
+    def set_passes(self, passes):
+        """1: fused single pass (default, 8 B per unknown and realization
+        in FP32); 2: velocity pass then stress pass (12 B)."""
+        _chk(rom_fom_set_passes(self.h, passes), "rom_fom_set_passes")
 
     def vindex(self, i, j):
         """Velocity unknown of grid point (r_{i+1/2}, theta_j)."""

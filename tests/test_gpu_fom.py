@@ -60,11 +60,13 @@ def gpu_run(rom, f, X0, N, prec, src=-1, T=None, recv=None, r=0, n0=0, wavelet=1
             None if tr is None else tr.cpu().numpy())
 
 
-@pytest.mark.parametrize("prec,tol", [("fp64", 1e-12), ("fp32", 1e-4)])
-def test_fom_vs_oracle(rom, prec, tol):
+@pytest.mark.parametrize("prec,tol,passes", [("fp64", 1e-12, 1), ("fp32", 1e-4, 1),
+                                             ("fp64", 1e-12, 2), ("fp32", 1e-4, 2)])
+def test_fom_vs_oracle(rom, prec, tol, passes):
     Nr, Nt, M, N, r = 24, 40, 5, 300, 7
     dt = stable_dt(Nr, Nt)
     f = rom.Fom(Nr, Nt, dt=dt)
+    f.set_passes(passes)
     X0 = case(Nr, Nt, M, seed=1)
     T = np.linspace(60.0, 80.0, M)
     src = f.source_index(P["src_depth"], j=Nt // 3)
@@ -72,7 +74,7 @@ def test_fom_vs_oracle(rom, prec, tol):
     V, S1, S2, tr = gpu_run(rom, f, X0, N, prec, src=src, T=T, recv=recv, r=r)
     Vo, S1o, S2o, tro = oracle.fom_forward(Nr, Nt, *X0, N, src=src, T=T, wavelet=1, recv=recv, r=r, dt=dt)
     errs = [rel(V, Vo), rel(S1, S1o), rel(S2, S2o), rel(tr, tro)]
-    print(prec, "rel errors V/S1/S2/traces", errs)
+    print(prec, passes, "rel errors V/S1/S2/traces", errs)
     assert max(errs) <= tol, errs
     assert rel(Vo, X0[0]) > 0.1  # the run moved the state
 
@@ -93,23 +95,43 @@ def test_fom_rank2_equals_rank1_bitwise(rom):
         assert np.array_equal(s2[:, 0], S2[:, m])
 
 
-def test_fom_chunked_equals_one_run_and_zero(rom):
-    """n0 continues the forcing clock: 70 + 130 steps equal 200 steps
-    bitwise (the 64-step graph is replayed with steps past the end idle);
-    zero state without forcing stays exactly zero."""
+@pytest.mark.parametrize("passes", [1, 2])
+def test_fom_chunked_equals_one_run_and_zero(rom, passes):
+    """n0 continues the forcing clock: 71 + 129 steps equal 200 steps
+    bitwise (the 64-step graph is replayed with steps past the end idle; an
+    odd count ends in the fused pass's second buffer set and is copied
+    back); zero state without forcing stays exactly zero."""
     Nr, Nt, M = 12, 20, 3
     f = rom.Fom(Nr, Nt, dt=stable_dt(Nr, Nt))
+    f.set_passes(passes)
     X0 = case(Nr, Nt, M, seed=3)
     T = np.array([60.0, 70.0, 80.0])
     src = f.source_index(P["src_depth"], j=2)
     full = gpu_run(rom, f, X0, 200, "fp64", src=src, T=T)
-    a = gpu_run(rom, f, X0, 70, "fp64", src=src, T=T)
-    b = gpu_run(rom, f, a[:3], 130, "fp64", src=src, T=T, n0=70)
+    a = gpu_run(rom, f, X0, 71, "fp64", src=src, T=T)
+    b = gpu_run(rom, f, a[:3], 129, "fp64", src=src, T=T, n0=71)
     for k in range(3):
         assert np.array_equal(full[k], b[k])
     nv, n1, n2 = f.nv, f.n1, f.n2
     z = gpu_run(rom, f, (np.zeros((nv, M)), np.zeros((n1, M)), np.zeros((n2, M))), 100, "fp32")
     assert not any(x.any() for x in z[:3])
+
+
+def test_fom_fused_equals_two_passes(rom):
+    """The fused pass computes the two passes' arithmetic (its halo values
+    are recomputed by the same expressions): equal to FP32 rounding, on a
+    grid with ragged strips and segments and the source in a halo column."""
+    Nr, Nt, M, N = 45, 70, 32, 120
+    f = rom.Fom(Nr, Nt, dt=stable_dt(20, 30) * 0.25)
+    X0 = case(Nr, Nt, M, seed=4)
+    T = np.linspace(60.0, 80.0, M)
+    src = f.vindex(31, 32)  # halo column of strip 0 and recomputed row of segment 1
+    outs = []
+    for passes in (1, 2):
+        f.set_passes(passes)
+        outs.append(gpu_run(rom, f, X0, N, "fp32", src=src, T=T, recv=[src, f.vindex(Nr - 1, 5)], r=3))
+    for k in range(4):
+        assert rel(outs[0][k], outs[1][k]) <= 1e-6, k
 
 
 def test_fom_rejects_bad_arguments(rom):
@@ -124,3 +146,5 @@ def test_fom_rejects_bad_arguments(rom):
         f.run(Vh, S1h, S2h, 10)
     with pytest.raises(RuntimeError):
         rom.Fom(1, 12)
+    with pytest.raises(RuntimeError):
+        f.set_passes(3)
