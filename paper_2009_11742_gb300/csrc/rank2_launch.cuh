@@ -86,17 +86,25 @@ static bool plan_rank2(int Kp, int M, int R, bool rank1, Rank2Plan* p, int clust
     p->cb = rank1 ? 1 : CBW;
     const int rpc = (R + p->cs - 1) / p->cs;
     const int smax = device_smem_optin();
-    // widest allocation that fits shared memory
+    // widest allocation that fits shared memory; when the CTA's receiver rows
+    // leave no room, they are read from global memory instead
     int wcap = 0;
-    for (int w = p->cb; w <= 4096; w += p->cb) {
-        if (rank2_smem_layout<T>(w, Kp, rpc, p->nrt).total > (size_t)smax) break;
-        wcap = w;
+    p->c_global = false;
+    for (int pass = 0; pass < 2 && wcap == 0; ++pass) {
+        p->c_global = pass == 1;
+        const int rpc_s = p->c_global ? 0 : rpc;
+        for (int w = p->cb; w <= 4096; w += p->cb) {
+            if (rank2_smem_layout<T>(w, Kp, rpc_s, p->nrt).total > (size_t)smax) break;
+            wcap = w;
+        }
+        if (rpc == 0) break;
     }
     if (wcap == 0) return false;
+    const int rpc_smem = p->c_global ? 0 : rpc;
     void* fn = rank2_kernel<T>(p->KI, p->cb, &p->resident);
     if (!fn) return false;
     const int wprobe = rank1 ? 1 : wcap;
-    const size_t smem_probe = rank2_smem_layout<T>(wprobe, Kp, rpc, p->nrt).total;
+    const size_t smem_probe = rank2_smem_layout<T>(wprobe, Kp, rpc_smem, p->nrt).total;
     if (prepare_kernel<T>(fn, smem_probe) != cudaSuccess) return false;
     cudaLaunchConfig_t cfg = {};
     cudaLaunchAttribute attr[1];
@@ -122,7 +130,7 @@ static bool plan_rank2(int Kp, int M, int R, bool rank1, Rank2Plan* p, int clust
     p->Wv = wv;
     p->Wa = wv;
     p->nclusters = (M + wv - 1) / wv;
-    p->smem = rank2_smem_layout<T>(p->Wa, Kp, rpc, p->nrt).total;
+    p->smem = rank2_smem_layout<T>(p->Wa, Kp, rpc_smem, p->nrt).total;
     p->variant = 1;
     return true;
 }
@@ -134,6 +142,7 @@ static cudaError_t launch_rank2(const Rank2Args& a_in, const Rank2Plan& p, cudaS
     a.Wa = p.Wa;
     a.nrt = p.nrt;
     a.rpc = (a.R + p.cs - 1) / p.cs;
+    a.c_global = p.c_global ? 1 : 0;
     bool res = false;
     void* fn = rank2_kernel<T>(p.KI, p.cb, &res);
     if (!fn) return cudaErrorInvalidValue;

@@ -243,7 +243,9 @@ __global__ void __launch_bounds__(kThreads, 1) rank2_simt_kernel(const Rank2Args
     const T dt = (T)a.dt;
 
     extern __shared__ __align__(16) unsigned char smem[];
-    const Rank2Smem L = rank2_smem_layout<T>(Wa, Kp, a.rpc, nrt);
+    // receiver rows staged in shared memory, or (c_global: too many to stage
+    // beside the state) read from the row-major C in global memory
+    const Rank2Smem L = rank2_smem_layout<T>(Wa, Kp, a.c_global ? 0 : a.rpc, nrt);
     T* Vf = reinterpret_cast<T*>(smem + L.Vf);
     T* Sf = reinterpret_cast<T*>(smem + L.Sf);
     T* Cown = reinterpret_cast<T*>(smem + L.C);
@@ -274,7 +276,7 @@ __global__ void __launch_bounds__(kThreads, 1) rank2_simt_kernel(const Rank2Args
         cS[idx] = (csin && c < ncol && row < a.Ks) ? csin[(size_t)(gc0 + c) * a.Ks + row] : 0.f;
     }
     const T* Cp = static_cast<const T*>(gop ? gop->C_p : a.C_p);
-    for (int idx = tid; idx < a.rpc * Kp; idx += kThreads) {
+    for (int idx = tid; idx < (a.c_global ? 0 : a.rpc * Kp); idx += kThreads) {
         const int jj = idx / Kp, k = idx % Kp, jr = crank * a.rpc + jj;
         Cown[idx] = (Cp && jr < a.R) ? Cp[(size_t)jr * Kp + k] : T(0);
     }
@@ -337,10 +339,11 @@ __global__ void __launch_bounds__(kThreads, 1) rank2_simt_kernel(const Rank2Args
             for (int pr = warp; pr < npair; pr += kThreads / 32) {
                 const int jj = pr / ncol, c = pr % ncol, jr = crank * a.rpc + jj;
                 if (jr >= a.R) continue;
+                const T* crow = a.c_global ? Cp + (size_t)jr * Kp : Cown + (size_t)jj * Kp;
                 T acc = T(0);
                 for (int k = 4 * lane; k < Kp; k += 128) {
                     T cx[4], vx[4];
-                    load4(Cown + (size_t)jj * Kp + k, cx);
+                    load4(crow + k, cx);
                     load4(Vf + (size_t)c * Kp + k, vx);
 #pragma unroll
                     for (int q = 0; q < 4; ++q) acc = fmadd(cx[q], vx[q], acc);

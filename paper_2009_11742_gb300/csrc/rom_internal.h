@@ -57,6 +57,7 @@ struct Rank2Args {
     // job * M + local.  Null: one operator (the fields above).
     const GroupOp* group;
     int group_cpj;
+    int c_global;          // one-block kernel: read receiver rows from C_p instead of shared memory
 };
 
 // Launch plan chosen by the host for a rank-2 call.
@@ -70,6 +71,7 @@ struct Rank2Plan {
     size_t smem;
     bool resident; // operators kept in registers for the whole run
     int variant;   // 1: one-block, 2: two-block split-role, 3: two-block dataflow
+    bool c_global; // one-block: the CTA's receiver rows are read from global memory (too many to stage)
     int nrt;       // one-block kernel: 32-row tiles per CTA (2 when Kp > 512)
 };
 

@@ -301,6 +301,31 @@ def test_nsteps_zero_and_bad_args(rom):
     assert st == rom.ROM_E_INVAL
 
 
+@pytest.mark.parametrize("prec,Kv,Ks,M,R,N", [
+    ("fp32", 1024, 1024, 64, 64, 40),    # largest K: the one-block kernel with two row tiles per CTA
+    ("fp32", 1024, 1, 16, 8, 40),        # Kv at the limit, a one-dimensional stress space
+    ("fp64", 512, 512, 24, 16, 40),      # largest K of the FP64 path
+    ("fp32", 256, 256, 3000, 4, 20),     # more column blocks than co-resident clusters (waves)
+    ("fp32", 512, 512, 32, 1024, 20),    # the largest receiver count
+    ("fp32", 1024, 1024, 16, 1024, 20),  # largest K with the largest receiver count
+])
+def test_maximum_sizes(rom, prec, Kv, Ks, M, R, N):
+    """The limits rom_create accepts (K <= 1024, R <= 1024) and a wide
+    ensemble, on sampled columns against the oracle."""
+    p = inputs.make_problem(Kv, Ks, M, R, seed=40 + M)
+    h = rom.Rom.from_problem(p)
+    V0 = inputs.random_state(Kv, M, seed=41, scale=0.1)
+    S0 = inputs.random_state(Ks, M, seed=42, scale=0.1)
+    r = 5
+    V, S, tr = gpu_run(rom, h, p, V0, S0, N, prec, r=r)
+    cols = sorted({0, M // 3, M - 1})
+    Vo, So, tro = oracle.forward(p.Avs, p.Asv, p.g, p.C, p.dt, V0[:, cols], S0[:, cols], N,
+                                 T=p.T[cols], r=r)
+    tol = TOL[prec]
+    assert rel(V[:, cols], Vo) <= tol and rel(S[:, cols], So) <= tol
+    assert rel(tr[:, :, cols], tro) <= tol
+
+
 def test_rel_l2_gpu(rom):
     x = torch.randn(1000, dtype=torch.float64, device="cuda")
     y = x + 1e-3 * torch.randn(1000, dtype=torch.float64, device="cuda")
