@@ -79,6 +79,21 @@ def test_fom_vs_oracle(rom, prec, tol, passes):
     assert rel(Vo, X0[0]) > 0.1  # the run moved the state
 
 
+@pytest.mark.parametrize("passes", [1, 2])
+def test_fom_smallest_grid(rom, passes):
+    """Nr = 2, Ntheta = 3: one sigma_rp face, one sigma_tp column, both
+    velocity columns next to the axis."""
+    Nr, Nt, M, N = 2, 3, 3, 200
+    dt = stable_dt(Nr, Nt)
+    f = rom.Fom(Nr, Nt, dt=dt)
+    f.set_passes(passes)
+    X0 = case(Nr, Nt, M, seed=5)
+    T = np.array([60.0, 70.0, 80.0])
+    V, S1, S2, _ = gpu_run(rom, f, X0, N, "fp64", src=1, T=T)
+    Vo, S1o, S2o, _ = oracle.fom_forward(Nr, Nt, *X0, N, src=1, T=T, wavelet=1, dt=dt)
+    assert rel(V, Vo) <= 1e-12 and rel(S1, S1o) <= 1e-12 and rel(S2, S2o) <= 1e-12
+
+
 def test_fom_rank2_equals_rank1_bitwise(rom):
     """Each realization's arithmetic does not depend on M: column m of a
     rank-2 run equals the single-realization run bitwise."""

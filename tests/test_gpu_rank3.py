@@ -57,6 +57,7 @@ def rank3_run(rom, probs, V0, S0, N, prec, r):
     ("fp32", 9, 512, 448, 8, 120),    # more operators than co-resident clusters
     ("fp32", 2, 640, 600, 24, 100),   # one-block kernel (K > 512)
     ("fp64", 4, 192, 160, 10, 200),   # FP64 one-block kernel
+    ("fp32", 1, 256, 256, 10, 100),   # one operator: the rank-2 run
 ])
 def test_rank3_vs_oracle(rom, prec, nops, Kv, Ks, M, N):
     R, r = 5, 4
