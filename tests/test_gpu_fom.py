@@ -94,6 +94,29 @@ def test_fom_smallest_grid(rom, passes):
     assert rel(V, Vo) <= 1e-12 and rel(S1, S1o) <= 1e-12 and rel(S2, S2o) <= 1e-12
 
 
+def test_fom_app_a_setup(rom):
+    """The App. A setup on a 64 x 256 grid: rho 2500, vs 5000, dt 0.05 s,
+    a source 640 km deep next to the axis, the first derivative of a
+    Gaussian with periods in (60, 80) s and delay 1.5 T, 1000 FP32 steps from
+    rest starting at t = 60 s (the pulse falls inside the run), receivers
+    around the source; the fused pass against the oracle."""
+    Nr, Nt, M, N, r, n0 = 64, 256, 4, 1000, 10, 1200
+    f = rom.Fom(Nr, Nt)
+    src = f.source_index(P["src_depth"], j=1)
+    i_s = src // (Nt - 1)
+    recv = [f.vindex(i, j) for i in (i_s - 3, i_s, i_s + 3) for j in (1, 4, 12)]
+    T = np.random.default_rng(6).uniform(60.0, 80.0, M)
+    nv, n1, n2 = f.nv, f.n1, f.n2
+    X0 = (np.zeros((nv, M)), np.zeros((n1, M)), np.zeros((n2, M)))
+    V, S1, S2, tr = gpu_run(rom, f, X0, N, "fp32", src=src, T=T, recv=recv, r=r, n0=n0)
+    Vo, S1o, S2o, tro = oracle.fom_forward(Nr, Nt, *X0, N, src=src, T=T, wavelet=1, recv=recv, r=r,
+                                           n0=n0, dt=P["dt"])
+    errs = [rel(V, Vo), rel(S1, S1o), rel(S2, S2o), rel(tr, tro)]
+    print("App. A setup rel errors V/S1/S2/traces", errs)
+    assert max(errs) <= 1e-4, errs
+    assert np.abs(Vo).max() > 0
+
+
 def test_fom_rank2_equals_rank1_bitwise(rom):
     """Each realization's arithmetic does not depend on M: column m of a
     rank-2 run equals the single-realization run bitwise."""
