@@ -56,6 +56,21 @@ def test_null_arguments_rejected_without_gpu(lib):
     assert rc == 1  # ROM_E_INVAL
     rc = lib.rom_run_rank2(None, None, None, None, 1, 1, ctypes.c_long(0), 0, None, 1, None)
     assert rc == 1
+    assert lib.rom_run_rank3(None, 2, None, None, None, 4, 10, 0, None, 1, None) == 1
+    assert lib.rom_set_reference(None, None, None, 4, 0) == 1
+    d = ctypes.c_double
+    f = ctypes.c_void_p()
+    for bad in [(1, 12), (8, 2), (70000, 12)]:  # Nr < 2, Ntheta < 3, Nr > 65535
+        rc = lib.rom_fom_create(bad[0], bad[1], d(3480e3), d(6371e3), d(2500.0), d(5000.0),
+                                d(0.05), ctypes.byref(f))
+        assert rc == 1 and not f.value
+    rc = lib.rom_fom_create(8, 12, d(3480e3), d(3000e3), d(2500.0), d(5000.0), d(0.05),
+                            ctypes.byref(f))
+    assert rc == 1  # r_earth below r_cmb
+    assert lib.rom_fom_run(None, None, None, None, 1, 10, ctypes.c_long(0), -1, None, 1, None, 0,
+                           0, None, 1, None) == 1
+    assert lib.rom_fom_set_passes(None, 1) == 1
+    assert lib.rom_fom_dims(None, None, None, None) == 1
 
 
 def test_missing_library_fails_loudly(tmp_path):
