@@ -679,6 +679,7 @@ def bench_batched(args, torch, dev, inputs, rom):
     measured the schedule (the tuning probe is outside the timed region)."""
     probs = inputs.batched_problems()
     N = args.nsteps or 5000
+    prec = args.prec or "fp32"
     items = []
     for p in probs:
         h = rom.Rom.from_problem(p)
@@ -690,7 +691,7 @@ def bench_batched(args, torch, dev, inputs, rom):
     def timed():
         with torch.cuda.stream(stream):
             for _ in range(args.warmup):
-                rom.run_batched(items, N, prec="fp32", stream=stream)
+                rom.run_batched(items, N, prec=prec, stream=stream)
         torch.cuda.synchronize()
         evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
                for _ in range(args.steps)]
@@ -700,17 +701,17 @@ def bench_batched(args, torch, dev, inputs, rom):
                     V.zero_()
                     S.zero_()
                 evs[i][0].record(stream)
-                rom.run_batched(items, N, prec="fp32", stream=stream)
+                rom.run_batched(items, N, prec=prec, stream=stream)
                 evs[i][1].record(stream)
         torch.cuda.synchronize()
         return sum(a.elapsed_time(b) for a, b in evs) * 1e-3 / args.steps
 
     t0 = timed()
-    probe_us = rom.autotune_batched(items, prec="fp32", probe_steps=200, stream=stream)
+    probe_us = rom.autotune_batched(items, prec=prec, probe_steps=200, stream=stream)
     t = timed()
     ss = sum(p.M for p in probs) * N
     fl = sum(4.0 * p.Kv * p.Ks * p.M for p in probs) * N
-    print(json.dumps({"only_rank2": True, "workload": "batched-64roms-K64..768-M4..256-N5000",
+    print(json.dumps({"only_rank2": True, "workload": "batched-64roms-K64..768-M4..256-N5000", "prec": prec,
                       "nsteps": N, "value": ss / t, "unit": "sample-steps/s",
                       "ms_per_step": 1e3 * t, "tflops_useful": fl / t / 1e12,
                       "untuned": {"value": ss / t0, "ms_per_step": 1e3 * t0},

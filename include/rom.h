@@ -73,9 +73,12 @@ typedef enum {
     ROM_TF32X3 = 2, /* tensor cores, tf32 hi/lo split, 3 products, Kahan update */
     ROM_BF16X3 = 3, /* tensor cores, bf16 3-term operator / 2-term state split */
     ROM_BF16 = 4,   /* tensor cores, plain bf16 products (reported, not accepted) */
-    ROM_BF16S = 5   /* tensor cores, exact sliced-integer bf16: operator rows and state
+    ROM_BF16S = 5,  /* tensor cores, exact sliced-integer bf16: operator rows and state
                        columns as three 8-bit digits with power-of-two scales, six digit
                        products accumulated without rounding, Kahan update */
+    ROM_AUTO = 6    /* rom_run_batched / rom_autotune_batched only: each job runs ROM_FP32
+                       or ROM_BF16S (both meet the FP32 accuracy bar), BF16S for jobs with
+                       max(Kv, Ks) at or above a threshold (256 unless tuned) */
 } rom_prec;
 
 typedef enum { ROM_IN_F64 = 0, ROM_IN_F32 = 1 } rom_dtype;
@@ -282,8 +285,10 @@ rom_status rom_run_rank1_ensemble(rom_t h, void* V, void* S, const void* T, int 
  * (captured and instantiated) on the first call for a given job list and
  * replayed afterwards.  Requirements: device buffers only, one job per
  * handle, traces (per job, optional) need r > 0 and receiver rows.
- * Asynchronous on `stream`.  This is the first step of the rank-3 outlook of
- * Sec. 5 (many operators and many forcings in one launch).
+ * With prec = ROM_AUTO every job takes ROM_FP32 or ROM_BF16S by its size
+ * (the threshold that rom_autotune_batched measured for this job list, else
+ * 256).  Asynchronous on `stream`.  This is the first step of the rank-3
+ * outlook of Sec. 5 (many operators and many forcings in one launch).
  */
 typedef struct {
     rom_t h;         /* the job's model */
@@ -325,9 +330,11 @@ rom_status rom_run_rank3(const rom_t* handles, int nops, void* V, void* S, const
  * or more clusters per job than its share), and keep the fastest scale for
  * this list of (handle, M) pairs: later rom_run_batched calls with the same
  * handles and widths use it.  The scale affects the SIMT jobs (the
- * tensor-core jobs plan their own widths).  *best_us (may be NULL) receives
- * the chosen schedule's probe time per step.  Synchronous on `stream`.
- * Errors as for rom_run_batched, plus ROM_E_NOMEM.
+ * tensor-core jobs plan their own widths).  With prec = ROM_AUTO it also
+ * tries the size thresholds 0 (every job BF16S), 256, 512 and none (every
+ * job FP32) and keeps the fastest (threshold, scale) pair.  *best_us (may be
+ * NULL) receives the chosen schedule's probe time per step.  Synchronous on
+ * `stream`.  Errors as for rom_run_batched, plus ROM_E_NOMEM.
  */
 rom_status rom_autotune_batched(const rom_job* jobs, int njobs, int prec, int probe_steps,
                                 double* best_us, void* stream);

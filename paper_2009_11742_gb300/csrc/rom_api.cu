@@ -977,9 +977,15 @@ rom_status batch_streams(size_t n) {
 
 extern "C" {
 
+// Default size threshold of ROM_AUTO: jobs with max(Kv, Ks) at or above it
+// run the exact-slice BF16 tensor-core path, the others FP32 SIMT.
+constexpr int kAutoKthr = 256;
+
+static bool batch_prec(int prec) { return valid_prec(prec) || prec == ROM_AUTO; }
+
 static rom_status run_batched_impl(const rom_job* jobs, int njobs, int nsteps, int r, int prec,
-                                   void* stream, double scale) {
-    if (!jobs || njobs < 1 || nsteps < 0 || r < 0 || !valid_prec(prec)) return ROM_E_INVAL;
+                                   void* stream, double scale, int kthr = kAutoKthr) {
+    if (!jobs || njobs < 1 || nsteps < 0 || r < 0 || !batch_prec(prec)) return ROM_E_INVAL;
     for (int i = 0; i < njobs; ++i) {
         const rom_job& j = jobs[i];
         if (!j.h || !j.V || !j.S || j.M < 1) return ROM_E_INVAL;
@@ -990,7 +996,14 @@ static rom_status run_batched_impl(const rom_job* jobs, int njobs, int nsteps, i
     }
     if (nsteps == 0) return ROM_OK;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    const bool tc = tc_prec(prec);
+    // the precision of every job (ROM_AUTO: by size)
+    std::vector<int> jp(njobs);
+    bool any_tc = false;
+    for (int i = 0; i < njobs; ++i) {
+        const int K = jobs[i].h->Kv > jobs[i].h->Ks ? jobs[i].h->Kv : jobs[i].h->Ks;
+        jp[i] = prec != ROM_AUTO ? prec : (K >= kthr ? ROM_BF16S : ROM_FP32);
+        any_tc = any_tc || tc_prec(jp[i]);
+    }
     int dev = 0, nsm = 0;
     ROM_CUDA(cudaGetDevice(&dev));
     ROM_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
@@ -1006,8 +1019,9 @@ static rom_status run_batched_impl(const rom_job* jobs, int njobs, int nsteps, i
     std::vector<double> est(njobs);
     for (int i = 0; i < njobs; ++i) {
         rom_s* h = jobs[i].h;
-        if (tc) {
-            rom_status s = tc_prepare(h, prec, st);
+        const int pj = jp[i];
+        if (tc_prec(pj)) {
+            rom_status s = tc_prepare(h, pj, st);
             if (s != ROM_OK) return s;
             est[i] = cost[i];
             continue;
@@ -1016,10 +1030,10 @@ static rom_status run_batched_impl(const rom_job* jobs, int njobs, int nsteps, i
         const int cs_guess = Kp > 512 ? Kp / 64 : Kp / 32;
         const int budget = (int)(scale * (double)nsm * cost[i] / total / cs_guess);
         bool ok = false;
-        if (prec == ROM_FP32) ok = plan_rank2_split_f32(Kp, jobs[i].M, h->R, &plans[i], budget > 0 ? budget : 1);
+        if (pj == ROM_FP32) ok = plan_rank2_split_f32(Kp, jobs[i].M, h->R, &plans[i], budget > 0 ? budget : 1);
         if (ok) plans[i].variant = 2;
         if (!ok) {
-            ok = prec == ROM_FP64 ? plan_rank2_simt_f64(Kp, jobs[i].M, h->R, false, &plans[i])
+            ok = pj == ROM_FP64 ? plan_rank2_simt_f64(Kp, jobs[i].M, h->R, false, &plans[i])
                                   : plan_rank2_simt_f32(Kp, jobs[i].M, h->R, false, &plans[i],
                                                         budget > 0 ? budget : 1);
             if (ok) plans[i].variant = 1;
@@ -1040,6 +1054,7 @@ static rom_status run_batched_impl(const rom_job* jobs, int njobs, int nsteps, i
                                            (uintptr_t)j.T, (uintptr_t)j.M, (uintptr_t)j.traces});
     }
     key.words.push_back((uintptr_t)(scale * 1024.0));
+    key.words.push_back((uintptr_t)(prec == ROM_AUTO ? kthr : -1));
     std::lock_guard<std::mutex> lk(g_batch_mu);
     auto it = g_batch_graphs.find(key);
     if (it == g_batch_graphs.end()) {
@@ -1058,8 +1073,8 @@ static rom_status run_batched_impl(const rom_job* jobs, int njobs, int nsteps, i
             const rom_job& j = jobs[i];
             cudaStream_t ss = g_batch_streams[oi % npool];
             RunBufs b = {j.V, j.S, const_cast<void*>(j.T), nullptr, nullptr, nullptr, j.traces};
-            rs = tc ? run_rank2_tc(j.h, b, j.M, nsteps, 0, r, prec, ss)
-                    : launch_simt_with_plan(j.h, b, j.M, nsteps, 0, r, prec, plans[i], ss);
+            rs = tc_prec(jp[i]) ? run_rank2_tc(j.h, b, j.M, nsteps, 0, r, jp[i], ss)
+                                : launch_simt_with_plan(j.h, b, j.M, nsteps, 0, r, jp[i], plans[i], ss);
         }
         for (size_t k = 0; k < npool && e == cudaSuccess; ++k) {
             e = cudaEventRecord(g_batch_events[k], g_batch_streams[k]);
@@ -1082,7 +1097,7 @@ static rom_status run_batched_impl(const rom_job* jobs, int njobs, int nsteps, i
         it = g_batch_graphs.emplace(key, exec).first;
     }
     ROM_CUDA(cudaGraphLaunch(it->second, st));
-    if (tc) {
+    if (any_tc) {
         // tensor-core jobs use per-handle workspaces that a later call may
         // reallocate: their graphs are not kept
         cudaGraphExec_t exec = it->second;
@@ -1093,9 +1108,11 @@ static rom_status run_batched_impl(const rom_job* jobs, int njobs, int nsteps, i
     return ROM_OK;
 }
 
-// Cluster-budget scale chosen by rom_autotune_batched, per job list
-// (handles and widths; buffers and step counts do not change the choice).
+// Cluster-budget scale (and, for ROM_AUTO, the size threshold) chosen by
+// rom_autotune_batched, per job list (handles and widths; buffers and step
+// counts do not change the choice).
 std::map<std::vector<uintptr_t>, double> g_batch_scale;
+std::map<std::vector<uintptr_t>, int> g_batch_kthr;
 
 static std::vector<uintptr_t> batch_tune_key(const rom_job* jobs, int njobs, int prec) {
     int dev = 0;
@@ -1110,17 +1127,23 @@ static std::vector<uintptr_t> batch_tune_key(const rom_job* jobs, int njobs, int
 
 rom_status rom_run_batched(const rom_job* jobs, int njobs, int nsteps, int r, int prec, void* stream) {
     double scale = 1.0;
+    int kthr = kAutoKthr;
     if (jobs && njobs > 0) {
+        for (int i = 0; i < njobs; ++i)
+            if (!jobs[i].h) return ROM_E_INVAL;
         std::lock_guard<std::mutex> lk(g_batch_mu);
-        auto it = g_batch_scale.find(batch_tune_key(jobs, njobs, prec));
+        const auto key = batch_tune_key(jobs, njobs, prec);
+        auto it = g_batch_scale.find(key);
         if (it != g_batch_scale.end()) scale = it->second;
+        auto kt = g_batch_kthr.find(key);
+        if (kt != g_batch_kthr.end()) kthr = kt->second;
     }
-    return run_batched_impl(jobs, njobs, nsteps, r, prec, stream, scale);
+    return run_batched_impl(jobs, njobs, nsteps, r, prec, stream, scale, kthr);
 }
 
 rom_status rom_autotune_batched(const rom_job* jobs, int njobs, int prec, int probe_steps,
                                 double* best_us, void* stream) {
-    if (!jobs || njobs < 1 || probe_steps < 1 || !valid_prec(prec)) return ROM_E_INVAL;
+    if (!jobs || njobs < 1 || probe_steps < 1 || !batch_prec(prec)) return ROM_E_INVAL;
     for (int i = 0; i < njobs; ++i)
         if (!jobs[i].h || jobs[i].M < 1) return ROM_E_INVAL;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -1154,21 +1177,33 @@ rom_status rom_autotune_batched(const rom_job* jobs, int njobs, int prec, int pr
     if (e == cudaSuccess) e = cudaEventCreate(&e0);
     if (e == cudaSuccess) e = cudaEventCreate(&e1);
     const double scales[4] = {0.5, 1.0, 2.0, 4.0};
+    // ROM_AUTO: size thresholds from every job on BF16S to every job on FP32
+    const int kthrs[4] = {0, 256, 512, 1 << 20};
+    const int nk = prec == ROM_AUTO ? 4 : 1;
     double best = -1.0, best_scale = 1.0;
+    int best_kthr = kAutoKthr;
     rom_status rs = ROM_OK;
-    for (int c = 0; c < 4 && e == cudaSuccess && rs == ROM_OK; ++c) {
-        float ms = 0.f;
-        for (int pass = 0; pass < 2 && e == cudaSuccess && rs == ROM_OK; ++pass) {  // warm-up, timed
-            const int n = pass == 0 ? (probe_steps < 20 ? probe_steps : 20) : probe_steps;
-            e = cudaEventRecord(e0, st);
-            if (e == cudaSuccess) rs = run_batched_impl(sj.data(), njobs, n, 0, prec, stream, scales[c]);
-            if (e == cudaSuccess && rs == ROM_OK) e = cudaEventRecord(e1, st);
-            if (e == cudaSuccess && rs == ROM_OK) e = cudaEventSynchronize(e1);
-            if (e == cudaSuccess && rs == ROM_OK) e = cudaEventElapsedTime(&ms, e0, e1);
-        }
-        if (e == cudaSuccess && rs == ROM_OK) {
-            const double us = 1e3 * ms / probe_steps;
-            if (best < 0.0 || us < best) { best = us; best_scale = scales[c]; }
+    for (int t = 0; t < nk && e == cudaSuccess && rs == ROM_OK; ++t) {
+        for (int c = 0; c < 4 && e == cudaSuccess && rs == ROM_OK; ++c) {
+            float ms = 0.f;
+            for (int pass = 0; pass < 2 && e == cudaSuccess && rs == ROM_OK; ++pass) {  // warm-up, timed
+                const int n = pass == 0 ? (probe_steps < 20 ? probe_steps : 20) : probe_steps;
+                e = cudaEventRecord(e0, st);
+                if (e == cudaSuccess)
+                    rs = run_batched_impl(sj.data(), njobs, n, 0, prec, stream, scales[c],
+                                          prec == ROM_AUTO ? kthrs[t] : kAutoKthr);
+                if (e == cudaSuccess && rs == ROM_OK) e = cudaEventRecord(e1, st);
+                if (e == cudaSuccess && rs == ROM_OK) e = cudaEventSynchronize(e1);
+                if (e == cudaSuccess && rs == ROM_OK) e = cudaEventElapsedTime(&ms, e0, e1);
+            }
+            if (e == cudaSuccess && rs == ROM_OK) {
+                const double us = 1e3 * ms / probe_steps;
+                if (best < 0.0 || us < best) {
+                    best = us;
+                    best_scale = scales[c];
+                    best_kthr = prec == ROM_AUTO ? kthrs[t] : kAutoKthr;
+                }
+            }
         }
     }
     if (e0) cudaEventDestroy(e0);
@@ -1194,6 +1229,7 @@ rom_status rom_autotune_batched(const rom_job* jobs, int njobs, int prec, int pr
     {
         std::lock_guard<std::mutex> lk(g_batch_mu);
         g_batch_scale[batch_tune_key(jobs, njobs, prec)] = best_scale;
+        if (prec == ROM_AUTO) g_batch_kthr[batch_tune_key(jobs, njobs, prec)] = best_kthr;
     }
     if (best_us) *best_us = best;
     return ROM_OK;

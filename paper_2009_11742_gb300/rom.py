@@ -27,12 +27,12 @@ LIB_PATH = os.path.join(HERE, "_build", "librom.so")
 
 ROM_OK, ROM_E_INVAL, ROM_E_NOMEM, ROM_E_CUDA, ROM_E_UNSTABLE, ROM_E_TIMEOUT, \
     ROM_E_NONFINITE, ROM_E_UNSUPPORTED = range(8)
-ROM_FP64, ROM_FP32, ROM_TF32X3, ROM_BF16X3, ROM_BF16, ROM_BF16S = range(6)
+ROM_FP64, ROM_FP32, ROM_TF32X3, ROM_BF16X3, ROM_BF16, ROM_BF16S, ROM_AUTO = range(7)
 ROM_IN_F64, ROM_IN_F32 = 0, 1
 ROM_KERNEL_AUTO, ROM_KERNEL_ONE_BLOCK, ROM_KERNEL_TWO_BLOCK, ROM_KERNEL_DATAFLOW = 0, 1, 2, 3
 ROM_WAVELET_RICKER, ROM_WAVELET_GAUSS1 = 0, 1
 PRECISIONS = {"fp64": ROM_FP64, "fp32": ROM_FP32, "tf32x3": ROM_TF32X3,
-              "bf16x3": ROM_BF16X3, "bf16": ROM_BF16, "bf16s": ROM_BF16S}
+              "bf16x3": ROM_BF16X3, "bf16": ROM_BF16, "bf16s": ROM_BF16S, "auto": ROM_AUTO}
 
 EXPORTED = ["rom_create", "rom_destroy", "rom_spectral_radius", "rom_sync_status",
             "rom_get_dims", "rom_set_kernel", "rom_get_plan", "rom_set_tc_columns", "rom_set_wavelet", "rom_set_reference", "rom_autotune", "rom_autotune_batched", "rom_set_wait_limit",
@@ -288,6 +288,8 @@ def run_batched(items, nsteps, r=0, prec="fp32", stream=None):
         if T is not None:
             _check_vec(T, M, "T", dt)
         if tr is not None:
+            if r <= 0:
+                raise ValueError("traces need r > 0")
             _check_vec(tr, (nsteps // r) * M * h.R, "traces", dt)
         arr[i] = rom_job(h.h, _ptr(V), _ptr(S), _ptr(T), M, _ptr(tr))
     st = rom_run_batched(arr, len(items), int(nsteps), int(r), p, _stream_handle(stream))

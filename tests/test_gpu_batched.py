@@ -153,3 +153,42 @@ def test_autotune_single_handle(rom):
     h.run_rank2(V3, S3, T, 200, prec="bf16s")
     torch.cuda.synchronize()
     assert np.linalg.norm(V3.cpu().numpy() - a) <= 1e-4 * np.linalg.norm(a)
+
+
+def test_batched_auto_precision(rom):
+    """prec="auto": jobs with max(Kv, Ks) >= 256 take the exact-slice BF16
+    tensor-core path, the others FP32; every result meets the FP32 bar
+    against the oracle and equals the job run alone at its chosen precision
+    bitwise.  After the threshold is tuned the results still meet the bar."""
+    N, r = 120, 10
+    jobs, probs = make_jobs(rom, SIZES, with_traces=N // r, seed0=400)
+    rom.run_batched(jobs, N, r=r, prec="auto")
+    torch.cuda.synchronize()
+    chosen = set()
+    for (h, V, S, T, tr), p in zip(jobs, probs):
+        assert h.sync_status() == 0
+        Z = np.zeros((p.Kv, p.M))
+        Vo, So, tro = oracle.forward(p.Avs, p.Asv, p.g, p.C if p.R else None, p.dt, Z, Z, N,
+                                     T=p.T, r=r if p.R else 0)
+        assert rel(V.cpu().numpy(), Vo) <= 1e-4 and rel(S.cpu().numpy(), So) <= 1e-4
+        if tr is not None:
+            assert rel(tr.transpose(1, 2).cpu().numpy(), tro) <= 1e-4
+        prec = "bf16s" if max(p.Kv, p.Ks) >= 256 else "fp32"
+        chosen.add(prec)
+        V1 = rom.Rom.new_state(p.Kv, p.M, "fp32")
+        S1 = rom.Rom.new_state(p.Ks, p.M, "fp32")
+        h.run_rank2(V1, S1, T, N, prec=prec)
+        torch.cuda.synchronize()
+        assert torch.equal(V1, V) and torch.equal(S1, S), prec
+    assert chosen == {"fp32", "bf16s"}
+    us = rom.autotune_batched(jobs, prec="auto", probe_steps=50)
+    assert us > 0
+    for (_, V, S, _, _) in jobs:
+        V.zero_()
+        S.zero_()
+    rom.run_batched([(h, V, S, T, None) for (h, V, S, T, _) in jobs], N, prec="auto")
+    torch.cuda.synchronize()
+    for (h, V, S, T, _), p in zip(jobs, probs):
+        Z = np.zeros((p.Kv, p.M))
+        Vo, So, _ = oracle.forward(p.Avs, p.Asv, p.g, None, p.dt, Z, Z, N, T=p.T)
+        assert rel(V.cpu().numpy(), Vo) <= 1e-4 and rel(S.cpu().numpy(), So) <= 1e-4
