@@ -200,7 +200,8 @@ bool tc_prec(int prec) {
     return prec == ROM_TF32X3 || prec == ROM_BF16X3 || prec == ROM_BF16 || prec == ROM_BF16S;
 }
 
-// Forget cached batched graphs that reference handle h (defined with them below).
+// Forget cached batched graphs, and the tuned schedules of job lists, that
+// reference handle h (defined with them below).
 void drop_batch_graphs(rom_s* h);
 // Forget cached rank-3 operator tables that reference handle h (defined below).
 void drop_group_tables(rom_s* h);
@@ -943,8 +944,24 @@ std::vector<cudaStream_t> g_batch_streams;
 std::vector<cudaEvent_t> g_batch_events;
 cudaStream_t g_capture_stream = nullptr;  // private: the caller's stream may be the legacy one
 
+// Cluster-budget scale (and, for ROM_AUTO, the size threshold) chosen by
+// rom_autotune_batched, per job list (handles and widths; buffers and step
+// counts do not change the choice).  Keys: (njobs, prec, device), then
+// (handle, M) per job.
+std::map<std::vector<uintptr_t>, double> g_batch_scale;
+std::map<std::vector<uintptr_t>, int> g_batch_kthr;
+
 void drop_batch_graphs(rom_s* h) {
     std::lock_guard<std::mutex> lk(g_batch_mu);
+    auto tuned_for_h = [h](const std::vector<uintptr_t>& k) {
+        for (size_t i = 3; i < k.size(); i += 2)
+            if (k[i] == (uintptr_t)h) return true;
+        return false;
+    };
+    for (auto it = g_batch_scale.begin(); it != g_batch_scale.end();)
+        it = tuned_for_h(it->first) ? g_batch_scale.erase(it) : std::next(it);
+    for (auto it = g_batch_kthr.begin(); it != g_batch_kthr.end();)
+        it = tuned_for_h(it->first) ? g_batch_kthr.erase(it) : std::next(it);
     for (auto it = g_batch_graphs.begin(); it != g_batch_graphs.end();) {
         bool uses = false;
         const auto& w = it->first.words;
@@ -1107,12 +1124,6 @@ static rom_status run_batched_impl(const rom_job* jobs, int njobs, int nsteps, i
     }
     return ROM_OK;
 }
-
-// Cluster-budget scale (and, for ROM_AUTO, the size threshold) chosen by
-// rom_autotune_batched, per job list (handles and widths; buffers and step
-// counts do not change the choice).
-std::map<std::vector<uintptr_t>, double> g_batch_scale;
-std::map<std::vector<uintptr_t>, int> g_batch_kthr;
 
 static std::vector<uintptr_t> batch_tune_key(const rom_job* jobs, int njobs, int prec) {
     int dev = 0;
