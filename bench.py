@@ -578,8 +578,9 @@ def bench_uq(args, torch, dev, inputs, rom):
 
 def bench_fp64(args, torch, dev, inputs, rom):
     """Workload 0: the FP64 check path (K = 128, M = 16, 1000 steps, no traces):
-    latency-bound; achieved FP64 rate against the 1.25 TFLOP/s nominal FP64
-    rate, and the error against the FP64 oracle."""
+    achieved FP64 rate against the 1.25 TFLOP/s nominal FP64 rate, the FP64
+    rank-1 paths on the same operator, and the error against the FP64
+    oracle."""
     p = inputs.config(0)
     K, M, N = 128, 16, args.nsteps or 1000
     h = rom.Rom.from_problem(p)
@@ -602,6 +603,25 @@ def bench_fp64(args, torch, dev, inputs, rom):
         torch.cuda.synchronize()
         ts.append(e0.elapsed_time(e1) * 1e-3)
     t = sum(ts) / len(ts)
+    # rank-1 FP64 baselines on the same operator: one realization at a time,
+    # and the M realizations as independent GEMV solves
+    v1 = torch.zeros(K, dtype=torch.float64, device=dev)
+    s1 = torch.zeros(K, dtype=torch.float64, device=dev)
+    Ve = rom.Rom.new_state(K, M, "fp64", device=dev)
+    Se = rom.Rom.new_state(K, M, "fp64", device=dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    h.run_rank1(v1, s1, float(p.T[0]), N, prec="fp64", stream=stream)
+    e0.record(stream)
+    h.run_rank1(v1, s1, float(p.T[0]), N, prec="fp64", stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    r1_single = N / (e0.elapsed_time(e1) * 1e-3)
+    h.run_rank1_ensemble(Ve, Se, T, N, prec="fp64", stream=stream)
+    e0.record(stream)
+    h.run_rank1_ensemble(Ve, Se, T, N, prec="fp64", stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    r1_ens = M * N / (e0.elapsed_time(e1) * 1e-3)
     import oracle
     Vo, So, _ = oracle.problem_forward(p, nsteps=N, r=0)
     Vg, Sg = V.cpu().numpy(), S.cpu().numpy()
@@ -610,7 +630,10 @@ def bench_fp64(args, torch, dev, inputs, rom):
                       "value": M * N / t, "unit": "sample-steps/s", "ms_per_step": 1e3 * t,
                       "us_per_leapfrog_step": 1e6 * t / N,
                       "gflops_fp64": flops / t / 1e9, "frac_of_fp64_nominal_1250_gflops": flops / t / 1.25e12,
-                      "bound": "latency (1 MFLOP per leapfrog step)",
+                      "bound": "FP64 units and cluster barriers (1 MFLOP per leapfrog step)",
+                      "plan": h.plan(M, "fp64"),
+                      "rank1_fp64": {"single_sample_steps_s": r1_single, "ensemble_sample_steps_s": r1_ens,
+                                     "rank2_speedup_vs_best_rank1": (M * N / t) / max(r1_single, r1_ens)},
                       "rel_err_vs_oracle": {"V": float(np.linalg.norm(Vg - Vo) / np.linalg.norm(Vo)),
                                             "S": float(np.linalg.norm(Sg - So) / np.linalg.norm(So))}}),
           flush=True)

@@ -53,9 +53,10 @@ static void* rank2_kernel_for(int KI, bool* resident) {
 
 template <typename T>
 static void* rank2_kernel(int KI, int cb, bool* resident) {
-    constexpr int CBW = sizeof(T) == 4 ? 8 : 4;  // wide column group
     if (cb == 1) return rank2_kernel_for<T, 1>(KI, resident);
-    if (cb == CBW) return rank2_kernel_for<T, CBW>(KI, resident);
+    if constexpr (sizeof(T) == 4) {
+        if (cb == 8) return rank2_kernel_for<T, 8>(KI, resident);  // wide column group (FP32)
+    }
     return nullptr;
 }
 
@@ -79,11 +80,14 @@ template <typename T>
 static bool plan_rank2(int Kp, int M, int R, bool rank1, Rank2Plan* p, int cluster_budget = 0) {
     const int kmax = sizeof(T) == 4 ? 1024 : 512;
     if (Kp <= 0 || Kp % 64 != 0 || Kp > kmax || M <= 0) return false;
-    constexpr int CBW = sizeof(T) == 4 ? 8 : 4;
+    constexpr int CBW = 8;  // wide column group (FP32)
     p->KI = Kp / 64;
     p->nrt = Kp > 512 ? 2 : 1;
     p->cs = Kp / (32 * p->nrt);
-    p->cb = rank1 ? 1 : CBW;
+    // FP64 runs one-column groups: it is bound by the SMs' few FP64 units,
+    // not by the shuffles and loads a wider group saves, and a narrow group
+    // lets a small ensemble spread one column per cluster.
+    p->cb = (rank1 || sizeof(T) == 8) ? 1 : CBW;
     const int rpc = (R + p->cs - 1) / p->cs;
     const int smax = device_smem_optin();
     // widest allocation that fits shared memory; when the CTA's receiver rows
