@@ -36,22 +36,9 @@ bool plan_adjoint(int Kp, int M, int R, AdjPlan* p) {
     if (!fn) return false;
     const size_t smem_probe = adj_smem_layout(wcap, Kp, R).total;
     if (prepare_kernel<float>(fn, smem_probe) != cudaSuccess) return false;
-    cudaLaunchConfig_t cfg = {};
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = p->cs;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
-    cfg.gridDim = dim3(p->cs, 1, 1);
-    cfg.blockDim = dim3(kThreads, 1, 1);
-    cfg.dynamicSmemBytes = smem_probe;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    int nact = 0;
-    if (cudaOccupancyMaxActiveClusters(&nact, fn, &cfg) != cudaSuccess || nact <= 0) {
-        cudaGetLastError();
-        return false;
-    }
+    ClusterLaunch probe(p->cs, 1, kThreads, smem_probe);
+    const int nact = probe.max_active(fn);
+    if (nact <= 0) return false;
     int wv = (M + nact - 1) / nact;
     wv = ((wv + 7) / 8) * 8;
     if (wv > wcap) wv = wcap;
@@ -70,20 +57,9 @@ cudaError_t launch_adjoint(const AdjArgs& a_in, const AdjPlan& p, cudaStream_t s
     if (!fn) return cudaErrorInvalidValue;
     cudaError_t e = prepare_kernel<float>(fn, p.smem);
     if (e != cudaSuccess) return e;
-    cudaLaunchConfig_t cfg = {};
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = p.cs;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
-    cfg.gridDim = dim3(p.cs * p.nclusters, 1, 1);
-    cfg.blockDim = dim3(kThreads, 1, 1);
-    cfg.dynamicSmemBytes = p.smem;
-    cfg.stream = st;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
+    ClusterLaunch L(p.cs, p.nclusters, kThreads, p.smem, st);
     void* args[] = {(void*)&a};
-    return cudaLaunchKernelExC(&cfg, fn, args);
+    return L.launch(fn, args);
 }
 
 // out[m] = sum over CTAs (in rank order) of part[rank][m].

@@ -53,22 +53,9 @@ static bool plan_two_block(int Kp, int M, int R, Rank2Plan* p, int cluster_budge
     if (!fn) return false;
     const size_t smem_probe = two_block_smem<DF>(wcap, Kp, rpc);
     if (prepare_kernel<float>(fn, smem_probe) != cudaSuccess) return false;
-    cudaLaunchConfig_t cfg = {};
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = p->cs;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
-    cfg.gridDim = dim3(p->cs, 1, 1);
-    cfg.blockDim = dim3(kThreads, 1, 1);
-    cfg.dynamicSmemBytes = smem_probe;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    int nact = 0;
-    if (cudaOccupancyMaxActiveClusters(&nact, fn, &cfg) != cudaSuccess || nact <= 0) {
-        cudaGetLastError();
-        return false;
-    }
+    ClusterLaunch probe(p->cs, 1, kThreads, smem_probe);
+    const int nact = probe.max_active(fn);
+    if (nact <= 0) return false;
     p->max_active_clusters = nact;
     const int budget = cluster_budget > 0 && cluster_budget < nact ? cluster_budget : nact;
     p->nrt = 1;
@@ -97,20 +84,9 @@ static cudaError_t launch_two_block(const Rank2Args& a_in, const Rank2Plan& p, c
     if (!fn) return cudaErrorInvalidValue;
     cudaError_t e = prepare_kernel<float>(fn, p.smem);
     if (e != cudaSuccess) return e;
-    cudaLaunchConfig_t cfg = {};
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = p.cs;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
-    cfg.gridDim = dim3(p.cs * p.nclusters, 1, 1);
-    cfg.blockDim = dim3(kThreads, 1, 1);
-    cfg.dynamicSmemBytes = p.smem;
-    cfg.stream = st;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
+    ClusterLaunch L(p.cs, p.nclusters, kThreads, p.smem, st);
     void* args[] = {(void*)&a};
-    return cudaLaunchKernelExC(&cfg, fn, args);
+    return L.launch(fn, args);
 }
 
 bool plan_rank2_split_f32(int Kp, int M, int R, Rank2Plan* p, int budget) { return plan_two_block<false>(Kp, M, R, p, budget); }

@@ -204,22 +204,9 @@ static bool plan_rank2_tcs(int Kp, int M, int R, int Wforce, TcPlan* p) {
             cudaGetLastError();
             continue;
         }
-        cudaLaunchConfig_t cfg = {};
-        cudaLaunchAttribute attr[1];
-        attr[0].id = cudaLaunchAttributeClusterDimension;
-        attr[0].val.clusterDim.x = cs;
-        attr[0].val.clusterDim.y = 1;
-        attr[0].val.clusterDim.z = 1;
-        cfg.gridDim = dim3(cs, 1, 1);
-        cfg.blockDim = dim3(kTcsThreads, 1, 1);
-        cfg.dynamicSmemBytes = smem;
-        cfg.attrs = attr;
-        cfg.numAttrs = 1;
-        int nact = 0;
-        if (cudaOccupancyMaxActiveClusters(&nact, fn, &cfg) != cudaSuccess || nact <= 0) {
-            cudaGetLastError();
-            continue;
-        }
+        ClusterLaunch probe(cs, 1, kTcsThreads, smem);
+        const int nact = probe.max_active(fn);
+        if (nact <= 0) continue;
         const int ncl = (M + W - 1) / W;
         const long waves = (ncl + nact - 1) / nact;
         const long cost = waves * (W + 48);
@@ -244,16 +231,6 @@ bool plan_rank2_tc(int prec, int Kp, int M, int R, int Wforce, TcPlan* p) {
     p->cs = Kp / kTcRows;
     p->rpc = (R + p->cs - 1) / p->cs;
     const int smax = device_smem_optin();
-    cudaLaunchConfig_t cfg = {};
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = p->cs;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
-    cfg.gridDim = dim3(p->cs, 1, 1);
-    cfg.blockDim = dim3(kTcThreads, 1, 1);
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
     // columns per block: 64 or 128 (MMA N; each reader warp drains W/2 columns)
     void* fn64 = tc_kernel_for(prec, 64);
     if (!fn64) return false;
@@ -264,12 +241,9 @@ bool plan_rank2_tc(int prec, int Kp, int M, int R, int Wforce, TcPlan* p) {
         cudaGetLastError();
         return false;
     }
-    cfg.dynamicSmemBytes = smem64;
-    int nact = 0;
-    if (cudaOccupancyMaxActiveClusters(&nact, fn64, &cfg) != cudaSuccess || nact <= 0) {
-        cudaGetLastError();
-        return false;
-    }
+    ClusterLaunch probe(p->cs, 1, kTcThreads, smem64);
+    const int nact = probe.max_active(fn64);
+    if (nact <= 0) return false;
     p->max_active_clusters = nact;
     int W = Wforce;
     if (W <= 0) W = ((M + nact - 1) / nact) <= 64 ? 64 : 128;
@@ -310,20 +284,9 @@ cudaError_t launch_rank2_tc(const TcArgs& a_in, const TcPlan& p, cudaStream_t st
     if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     if (e != cudaSuccess) return e;
-    cudaLaunchConfig_t cfg = {};
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = p.cs;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
-    cfg.gridDim = dim3(p.cs * p.nclusters, 1, 1);
-    cfg.blockDim = dim3(p.prec == ROM_BF16S ? kTcsThreads : kTcThreads, 1, 1);
-    cfg.dynamicSmemBytes = smem;
-    cfg.stream = st;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
+    ClusterLaunch L(p.cs, p.nclusters, p.prec == ROM_BF16S ? kTcsThreads : kTcThreads, smem, st);
     void* args[] = {(void*)&a};
-    return cudaLaunchKernelExC(&cfg, fn, args);
+    return L.launch(fn, args);
 }
 
 }  // namespace romk

@@ -9,6 +9,39 @@
 
 namespace romk {
 
+// Launch configuration of a grid of `nclusters` clusters of `cs` CTAs (one
+// cluster for an occupancy query).  The attribute array lives in the object,
+// so it is neither copied nor moved.
+struct ClusterLaunch {
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1] = {};
+    ClusterLaunch(int cs, int nclusters, int threads, size_t smem, cudaStream_t st = nullptr) {
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = cs;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.gridDim = dim3(cs * nclusters, 1, 1);
+        cfg.blockDim = dim3(threads, 1, 1);
+        cfg.dynamicSmemBytes = smem;
+        cfg.stream = st;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+    }
+    ClusterLaunch(const ClusterLaunch&) = delete;
+    ClusterLaunch& operator=(const ClusterLaunch&) = delete;
+    // Clusters of this shape that fit on the device at once (0: none, or the
+    // query failed; the error is cleared).
+    int max_active(const void* fn) {
+        int n = 0;
+        if (cudaOccupancyMaxActiveClusters(&n, fn, &cfg) != cudaSuccess) {
+            cudaGetLastError();
+            return 0;
+        }
+        return n;
+    }
+    cudaError_t launch(const void* fn, void** args) { return cudaLaunchKernelExC(&cfg, fn, args); }
+};
+
 template <typename T, int KI, int CB, bool RES>
 struct Rank2Kernel {
     static void* fn() { return (void*)&rank2_simt_kernel<T, KI, CB, RES>; }
@@ -110,22 +143,9 @@ static bool plan_rank2(int Kp, int M, int R, bool rank1, Rank2Plan* p, int clust
     const int wprobe = rank1 ? 1 : wcap;
     const size_t smem_probe = rank2_smem_layout<T>(wprobe, Kp, rpc_smem, p->nrt).total;
     if (prepare_kernel<T>(fn, smem_probe) != cudaSuccess) return false;
-    cudaLaunchConfig_t cfg = {};
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = p->cs;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
-    cfg.gridDim = dim3(p->cs, 1, 1);
-    cfg.blockDim = dim3(kThreads, 1, 1);
-    cfg.dynamicSmemBytes = smem_probe;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    int nact = 0;
-    if (cudaOccupancyMaxActiveClusters(&nact, fn, &cfg) != cudaSuccess || nact <= 0) {
-        cudaGetLastError();
-        return false;
-    }
+    ClusterLaunch probe(p->cs, 1, kThreads, smem_probe);
+    const int nact = probe.max_active(fn);
+    if (nact <= 0) return false;
     p->max_active_clusters = nact;
     const int budget = cluster_budget > 0 && cluster_budget < nact ? cluster_budget : nact;
     int wv = (M + budget - 1) / budget;
@@ -152,20 +172,9 @@ static cudaError_t launch_rank2(const Rank2Args& a_in, const Rank2Plan& p, cudaS
     if (!fn) return cudaErrorInvalidValue;
     cudaError_t e = prepare_kernel<T>(fn, p.smem);
     if (e != cudaSuccess) return e;
-    cudaLaunchConfig_t cfg = {};
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = p.cs;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
-    cfg.gridDim = dim3(p.cs * p.nclusters, 1, 1);
-    cfg.blockDim = dim3(kThreads, 1, 1);
-    cfg.dynamicSmemBytes = p.smem;
-    cfg.stream = st;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
+    ClusterLaunch L(p.cs, p.nclusters, kThreads, p.smem, st);
     void* args[] = {(void*)&a};
-    return cudaLaunchKernelExC(&cfg, fn, args);
+    return L.launch(fn, args);
 }
 
 }  // namespace romk
