@@ -77,6 +77,9 @@ def test_config0_fp64(rom):
     V, S, _ = gpu_run(rom, h, p, Z, Z, 1000, "fp64")
     Vo, So, _ = oracle.problem_forward(p, nsteps=1000, r=0)
     assert rel(V, Vo) <= TOL["fp64"] and rel(S, So) <= TOL["fp64"]
+    # FP64 runs one-column groups: the 16 realizations take 16 clusters
+    plan = h.plan(16, "fp64")
+    assert plan["cols_per_block"] == 1 and plan["nclusters"] == 16 and plan["cluster_size"] == 4
 
 
 @pytest.mark.parametrize("prec,kernel", [("fp64", 0), ("fp32", 1), ("fp32", 2), ("fp32", 3)])
