@@ -192,3 +192,25 @@ def test_batched_auto_precision(rom):
         Z = np.zeros((p.Kv, p.M))
         Vo, So, _ = oracle.forward(p.Avs, p.Asv, p.g, None, p.dt, Z, Z, N, T=p.T)
         assert rel(V.cpu().numpy(), Vo) <= 1e-4 and rel(S.cpu().numpy(), So) <= 1e-4
+
+
+def test_destroyed_handles_leave_no_tuned_schedule(rom):
+    """rom_destroy forgets the graphs and the tuned schedules of every job
+    list that names the handle: a new list (whose handles may reuse the
+    freed addresses) plans afresh and meets the bar."""
+    sizes = [(128, 20, 0), (320, 40, 0), (512, 16, 0)]
+    jobs, _ = make_jobs(rom, sizes, with_traces=0, seed0=500)
+    rom.autotune_batched(jobs, prec="auto", probe_steps=20)
+    rom.run_batched(jobs, 30, prec="auto")
+    torch.cuda.synchronize()
+    for (h, _, _, _, _) in jobs:
+        h.close()
+    del jobs
+    jobs2, probs2 = make_jobs(rom, sizes, with_traces=0, seed0=510)
+    N = 60
+    rom.run_batched(jobs2, N, prec="auto")
+    torch.cuda.synchronize()
+    for (h, V, S, T, _), p in zip(jobs2, probs2):
+        Z = np.zeros((p.Kv, p.M))
+        Vo, So, _ = oracle.forward(p.Avs, p.Asv, p.g, None, p.dt, Z, Z, N, T=p.T)
+        assert rel(V.cpu().numpy(), Vo) <= 1e-4 and rel(S.cpu().numpy(), So) <= 1e-4
