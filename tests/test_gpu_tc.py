@@ -64,6 +64,32 @@ def test_tc_small_vs_oracle(rom, prec, Kv, Ks, M, R, N, r):
     assert max(errs) <= TOL[prec], errs
 
 
+@pytest.mark.parametrize("prec", ["tf32x3", "bf16x3", "bf16", "bf16s"])
+@pytest.mark.parametrize("Kv,Ks,M,R,N,r", [(1, 1, 1, 1, 100, 1),       # K = 1, M = 1: one padded tile, one column
+                                           (256, 130, 33, 0, 90, 0),   # no receivers, Ks < Kv
+                                           (130, 256, 129, 3, 60, 60)])  # Kv < Ks, one column past two blocks, one record
+def test_tc_edge_shapes_vs_oracle(rom, prec, Kv, Ks, M, R, N, r):
+    p = inputs.make_problem(Kv, Ks, M, R, seed=Kv + 2 * M + 5)
+    h = rom.Rom.from_problem(p)
+    V0 = inputs.random_state(Kv, M, seed=5, scale=0.1)
+    S0 = inputs.random_state(Ks, M, seed=6, scale=0.1)
+    V, S, tr = run_tc(rom, h, p, V0, S0, N, prec, r=r)
+    Vo, So, tro = oracle.forward(p.Avs, p.Asv, p.g, p.C if R else None, p.dt, V0, S0, N, T=p.T, r=r)
+    errs = [rel(V, Vo), rel(S, So)]
+    if R:
+        errs.append(rel(tr, tro))
+    else:
+        assert tr is None and tro is None
+    tol = TOL[prec]
+    if prec == "bf16" and Kv == 1:
+        # plain BF16 is reported, not held to a bar: with a 1 x 1 operator no
+        # sum over K averages the 2^-9 rounding of the single entry, which
+        # shifts the oscillator's frequency by up to 0.2 % (about 0.1 rad of
+        # phase over 100 steps of 0.5 rad); only gross errors are caught here
+        tol = 0.5
+    assert max(errs) <= tol, errs
+
+
 @pytest.mark.parametrize("cols", [64, 128])
 def test_tc_k1024_tf32x3(rom, cols):
     """K = 1024 (8-CTA clusters, the workload-2 operator size) over a short run,
