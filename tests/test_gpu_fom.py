@@ -186,3 +186,25 @@ def test_fom_rejects_bad_arguments(rom):
         rom.Fom(1, 12)
     with pytest.raises(RuntimeError):
         f.set_passes(3)
+
+
+def test_fom_full_size_sampled(rom):
+    """The benchmark's grid and launch (512 x 2048, 3.14 M unknowns, M = 32,
+    FP32 fused pass, the source 640 km deep next to the axis, 64 surface
+    receivers every 10 steps), from a random state with the forcing clock at
+    the pulse (n0 = 1700 steps = 85 s): realizations 0 and 31 against the
+    oracle over 300 steps."""
+    Nr, Nt, M, N, r, n0 = 512, 2048, 32, 300, 10, 1700
+    f = rom.Fom(Nr, Nt)
+    src = f.source_index(P["src_depth"], j=1)
+    recv = [f.vindex(Nr - 1, int(j)) for j in np.linspace(1, Nt - 1, 64).astype(int)]
+    X0 = case(Nr, Nt, M, seed=8)
+    T = np.random.default_rng(9).uniform(60.0, 80.0, M)
+    V, S1, S2, tr = gpu_run(rom, f, X0, N, "fp32", src=src, T=T, recv=recv, r=r, n0=n0)
+    cols = [0, M - 1]
+    Vo, S1o, S2o, tro = oracle.fom_forward(Nr, Nt, *(x[:, cols] for x in X0), N, src=src, T=T[cols],
+                                           wavelet=1, recv=recv, r=r, n0=n0, dt=P["dt"])
+    errs = [rel(V[:, cols], Vo), rel(S1[:, cols], S1o), rel(S2[:, cols], S2o), rel(tr[:, :, cols], tro)]
+    print("full-size FOM rel errors V/S1/S2/traces", errs)
+    assert max(errs) <= 1e-4, errs
+    assert rel(Vo, X0[0][:, cols]) > 1e-3  # the run moved the state
