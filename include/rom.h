@@ -287,7 +287,11 @@ rom_status rom_run_rank1_ensemble(rom_t h, void* V, void* S, const void* T, int 
  * handle, traces (per job, optional) need r > 0 and receiver rows.
  * With prec = ROM_AUTO every job takes ROM_FP32 or ROM_BF16S by its size
  * (the threshold that rom_autotune_batched measured for this job list, else
- * 256).  Asynchronous on `stream`.  This is the first step of the rank-3
+ * 256).  A tensor-core job runs blocks as wide as its columns allow (the
+ * narrowest width that holds all M columns, else the widest; a width pinned
+ * with rom_set_tc_columns wins): an MMA costs the same at every width, so
+ * among jobs that share the SMs wide blocks give the most columns per SM.
+ * Asynchronous on `stream`.  This is the first step of the rank-3
  * outlook of Sec. 5 (many operators and many forcings in one launch).
  */
 typedef struct {
@@ -332,7 +336,8 @@ rom_status rom_run_rank3(const rom_t* handles, int nops, void* V, void* S, const
  * handles and widths use it.  The scale affects the SIMT jobs (the
  * tensor-core jobs plan their own widths).  With prec = ROM_AUTO it also
  * tries the size thresholds 0 (every job BF16S), 256, 512 and none (every
- * job FP32) and keeps the fastest (threshold, scale) pair.  *best_us (may be
+ * job FP32), and with tensor-core jobs both the batch widths and the ones
+ * the planner picks for a job alone; it keeps the fastest combination.  *best_us (may be
  * NULL) receives the chosen schedule's probe time per step.  Synchronous on
  * `stream`.  Errors as for rom_run_batched, plus ROM_E_NOMEM.
  */

@@ -950,6 +950,7 @@ cudaStream_t g_capture_stream = nullptr;  // private: the caller's stream may be
 // (handle, M) per job.
 std::map<std::vector<uintptr_t>, double> g_batch_scale;
 std::map<std::vector<uintptr_t>, int> g_batch_kthr;
+std::map<std::vector<uintptr_t>, int> g_batch_tcw;
 
 void drop_batch_graphs(rom_s* h) {
     std::lock_guard<std::mutex> lk(g_batch_mu);
@@ -962,6 +963,8 @@ void drop_batch_graphs(rom_s* h) {
         it = tuned_for_h(it->first) ? g_batch_scale.erase(it) : std::next(it);
     for (auto it = g_batch_kthr.begin(); it != g_batch_kthr.end();)
         it = tuned_for_h(it->first) ? g_batch_kthr.erase(it) : std::next(it);
+    for (auto it = g_batch_tcw.begin(); it != g_batch_tcw.end();)
+        it = tuned_for_h(it->first) ? g_batch_tcw.erase(it) : std::next(it);
     for (auto it = g_batch_graphs.begin(); it != g_batch_graphs.end();) {
         bool uses = false;
         const auto& w = it->first.words;
@@ -1000,8 +1003,24 @@ constexpr int kAutoKthr = 256;
 
 static bool batch_prec(int prec) { return valid_prec(prec) || prec == ROM_AUTO; }
 
+// Block width of a tensor-core job in a batch: the narrowest width that
+// holds all M columns in one block, else the widest.  A tcgen05 MMA costs the
+// same for every block width up to 128 columns, so when jobs share the SMs
+// the widest block yields the most columns per SM and step (the planner's
+// own choice, tuned for one job alone, spreads it over more SMs instead).
+static int batch_tc_width(int prec, int M) {
+    if (prec == ROM_BF16S) {
+        const int w[4] = {32, 48, 64, 80};
+        for (int c : w)
+            if (M <= c) return c;
+        return 80;
+    }
+    return M <= 64 ? 64 : 128;
+}
+
+// tcw: tensor-core block widths, 1 = batch_tc_width, 0 = the planner's.
 static rom_status run_batched_impl(const rom_job* jobs, int njobs, int nsteps, int r, int prec,
-                                   void* stream, double scale, int kthr = kAutoKthr) {
+                                   void* stream, double scale, int kthr = kAutoKthr, int tcw = 1) {
     if (!jobs || njobs < 1 || nsteps < 0 || r < 0 || !batch_prec(prec)) return ROM_E_INVAL;
     for (int i = 0; i < njobs; ++i) {
         const rom_job& j = jobs[i];
@@ -1034,6 +1053,8 @@ static rom_status run_batched_impl(const rom_job* jobs, int njobs, int nsteps, i
     }
     std::vector<Rank2Plan> plans(njobs);
     std::vector<double> est(njobs);
+    std::vector<TcPlan> tcplans(njobs);
+    std::vector<char> tcwide(njobs, 0);
     for (int i = 0; i < njobs; ++i) {
         rom_s* h = jobs[i].h;
         const int pj = jp[i];
@@ -1041,6 +1062,10 @@ static rom_status run_batched_impl(const rom_job* jobs, int njobs, int nsteps, i
             rom_status s = tc_prepare(h, pj, st);
             if (s != ROM_OK) return s;
             est[i] = cost[i];
+            // a width pinned with rom_set_tc_columns wins over the batch rule
+            if (tcw == 1 && h->tc_cols == 0 &&
+                plan_rank2_tc(pj, h->Kp_tc, jobs[i].M, h->R, batch_tc_width(pj, jobs[i].M), &tcplans[i]))
+                tcwide[i] = 1;
             continue;
         }
         const int Kp = h->Kp;
@@ -1072,6 +1097,7 @@ static rom_status run_batched_impl(const rom_job* jobs, int njobs, int nsteps, i
     }
     key.words.push_back((uintptr_t)(scale * 1024.0));
     key.words.push_back((uintptr_t)(prec == ROM_AUTO ? kthr : -1));
+    key.words.push_back((uintptr_t)tcw);
     std::lock_guard<std::mutex> lk(g_batch_mu);
     auto it = g_batch_graphs.find(key);
     if (it == g_batch_graphs.end()) {
@@ -1090,8 +1116,12 @@ static rom_status run_batched_impl(const rom_job* jobs, int njobs, int nsteps, i
             const rom_job& j = jobs[i];
             cudaStream_t ss = g_batch_streams[oi % npool];
             RunBufs b = {j.V, j.S, const_cast<void*>(j.T), nullptr, nullptr, nullptr, j.traces};
-            rs = tc_prec(jp[i]) ? run_rank2_tc(j.h, b, j.M, nsteps, 0, r, jp[i], ss)
-                                : launch_simt_with_plan(j.h, b, j.M, nsteps, 0, r, jp[i], plans[i], ss);
+            if (!tc_prec(jp[i]))
+                rs = launch_simt_with_plan(j.h, b, j.M, nsteps, 0, r, jp[i], plans[i], ss);
+            else if (tcwide[i])
+                rs = run_rank2_tc_plan(j.h, b, j.M, nsteps, 0, r, jp[i], tcplans[i], ss);
+            else
+                rs = run_rank2_tc(j.h, b, j.M, nsteps, 0, r, jp[i], ss);
         }
         for (size_t k = 0; k < npool && e == cudaSuccess; ++k) {
             e = cudaEventRecord(g_batch_events[k], g_batch_streams[k]);
@@ -1138,7 +1168,7 @@ static std::vector<uintptr_t> batch_tune_key(const rom_job* jobs, int njobs, int
 
 rom_status rom_run_batched(const rom_job* jobs, int njobs, int nsteps, int r, int prec, void* stream) {
     double scale = 1.0;
-    int kthr = kAutoKthr;
+    int kthr = kAutoKthr, tcw = 1;
     if (jobs && njobs > 0) {
         for (int i = 0; i < njobs; ++i)
             if (!jobs[i].h) return ROM_E_INVAL;
@@ -1148,8 +1178,10 @@ rom_status rom_run_batched(const rom_job* jobs, int njobs, int nsteps, int r, in
         if (it != g_batch_scale.end()) scale = it->second;
         auto kt = g_batch_kthr.find(key);
         if (kt != g_batch_kthr.end()) kthr = kt->second;
+        auto tw = g_batch_tcw.find(key);
+        if (tw != g_batch_tcw.end()) tcw = tw->second;
     }
-    return run_batched_impl(jobs, njobs, nsteps, r, prec, stream, scale, kthr);
+    return run_batched_impl(jobs, njobs, nsteps, r, prec, stream, scale, kthr, tcw);
 }
 
 rom_status rom_autotune_batched(const rom_job* jobs, int njobs, int prec, int probe_steps,
@@ -1191,28 +1223,34 @@ rom_status rom_autotune_batched(const rom_job* jobs, int njobs, int prec, int pr
     // ROM_AUTO: size thresholds from every job on BF16S to every job on FP32
     const int kthrs[4] = {0, 256, 512, 1 << 20};
     const int nk = prec == ROM_AUTO ? 4 : 1;
+    // tensor-core block widths: the batch rule (1) and the planner's (0)
+    const int ntw = (prec == ROM_AUTO || tc_prec(prec)) ? 2 : 1;
     double best = -1.0, best_scale = 1.0;
-    int best_kthr = kAutoKthr;
+    int best_kthr = kAutoKthr, best_tcw = 1;
     rom_status rs = ROM_OK;
     for (int t = 0; t < nk && e == cudaSuccess && rs == ROM_OK; ++t) {
-        for (int c = 0; c < 4 && e == cudaSuccess && rs == ROM_OK; ++c) {
-            float ms = 0.f;
-            for (int pass = 0; pass < 2 && e == cudaSuccess && rs == ROM_OK; ++pass) {  // warm-up, timed
-                const int n = pass == 0 ? (probe_steps < 20 ? probe_steps : 20) : probe_steps;
-                e = cudaEventRecord(e0, st);
-                if (e == cudaSuccess)
-                    rs = run_batched_impl(sj.data(), njobs, n, 0, prec, stream, scales[c],
-                                          prec == ROM_AUTO ? kthrs[t] : kAutoKthr);
-                if (e == cudaSuccess && rs == ROM_OK) e = cudaEventRecord(e1, st);
-                if (e == cudaSuccess && rs == ROM_OK) e = cudaEventSynchronize(e1);
-                if (e == cudaSuccess && rs == ROM_OK) e = cudaEventElapsedTime(&ms, e0, e1);
-            }
-            if (e == cudaSuccess && rs == ROM_OK) {
-                const double us = 1e3 * ms / probe_steps;
-                if (best < 0.0 || us < best) {
-                    best = us;
-                    best_scale = scales[c];
-                    best_kthr = prec == ROM_AUTO ? kthrs[t] : kAutoKthr;
+        for (int tw = 0; tw < ntw && e == cudaSuccess && rs == ROM_OK; ++tw) {
+            const int tcw = 1 - tw;
+            for (int c = 0; c < 4 && e == cudaSuccess && rs == ROM_OK; ++c) {
+                float ms = 0.f;
+                for (int pass = 0; pass < 2 && e == cudaSuccess && rs == ROM_OK; ++pass) {  // warm-up, timed
+                    const int n = pass == 0 ? (probe_steps < 20 ? probe_steps : 20) : probe_steps;
+                    e = cudaEventRecord(e0, st);
+                    if (e == cudaSuccess)
+                        rs = run_batched_impl(sj.data(), njobs, n, 0, prec, stream, scales[c],
+                                              prec == ROM_AUTO ? kthrs[t] : kAutoKthr, tcw);
+                    if (e == cudaSuccess && rs == ROM_OK) e = cudaEventRecord(e1, st);
+                    if (e == cudaSuccess && rs == ROM_OK) e = cudaEventSynchronize(e1);
+                    if (e == cudaSuccess && rs == ROM_OK) e = cudaEventElapsedTime(&ms, e0, e1);
+                }
+                if (e == cudaSuccess && rs == ROM_OK) {
+                    const double us = 1e3 * ms / probe_steps;
+                    if (best < 0.0 || us < best) {
+                        best = us;
+                        best_scale = scales[c];
+                        best_kthr = prec == ROM_AUTO ? kthrs[t] : kAutoKthr;
+                        best_tcw = tcw;
+                    }
                 }
             }
         }
@@ -1241,6 +1279,7 @@ rom_status rom_autotune_batched(const rom_job* jobs, int njobs, int prec, int pr
         std::lock_guard<std::mutex> lk(g_batch_mu);
         g_batch_scale[batch_tune_key(jobs, njobs, prec)] = best_scale;
         if (prec == ROM_AUTO) g_batch_kthr[batch_tune_key(jobs, njobs, prec)] = best_kthr;
+        g_batch_tcw[batch_tune_key(jobs, njobs, prec)] = best_tcw;
     }
     if (best_us) *best_us = best;
     return ROM_OK;
