@@ -88,19 +88,6 @@ __device__ __forceinline__ void mbar_arrive_expect_tx(unsigned long long* bar, u
                  ::"r"(smem_addr(bar)), "r"(bytes)
                  : "memory");
 }
-// 16-byte asynchronous store into cluster CTA `rank` at the shared-memory
-// offset of `dst_local`; completion decrements the transaction count of the
-// mbarrier at the offset of `bar_local` in that CTA.
-__device__ __forceinline__ void st_async_v4(const void* dst_local, const float4& v,
-                                            const unsigned long long* bar_local, int rank) {
-    unsigned rdst, rbar;
-    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(rdst) : "r"(smem_addr(dst_local)), "r"(rank));
-    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(rbar) : "r"(smem_addr(bar_local)), "r"(rank));
-    asm volatile(
-        "st.async.shared::cluster.mbarrier::complete_tx::bytes.v4.f32 [%0], {%1, %2, %3, %4}, [%5];"
-        ::"r"(rdst), "f"(v.x), "f"(v.y), "f"(v.z), "f"(v.w), "r"(rbar)
-        : "memory");
-}
 __device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned parity) {
     unsigned ok;
     asm volatile(
