@@ -155,6 +155,62 @@ __device__ __forceinline__ void split_phase(cg::cluster_group& cluster, const fl
     }
 }
 
+// One stage of a 32-lane reduce-scatter of 16 values: lanes with bit `o`
+// set keep the upper H entries, the others the lower H, each adding its
+// partner's copy of the entries it keeps.
+template <int H>
+__device__ __forceinline__ void rs32_stage(float (&v)[16], int lane, int o) {
+    const bool up = (lane & o) != 0;
+#pragma unroll
+    for (int i = 0; i < H; ++i) {
+        const float send = up ? v[i] : v[i + H];
+        const float keep = up ? v[i + H] : v[i];
+        v[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+    }
+}
+
+// Receiver traces y = C V^{n+1} of one block (Sec. 4.5.2): out[c R + jj] for
+// this CTA's nj receiver rows Cown (row-major, Kp wide) and the nc columns of
+// the new V in Xb (column-major, Kp rows).  A warp takes a tile of 4
+// receivers x 4 columns over the whole K: each lane sums 4-wide stripes of k
+// into 16 independent accumulators, then a 32-lane reduce-scatter (fixed
+// order) leaves entry lane / 2 of the tile in lanes 2e and 2e + 1.
+__device__ __forceinline__ void split_traces(const float* __restrict__ Cown, const float* __restrict__ Xb,
+                                             int Kp, int nj, int nc, int warp, int lane,
+                                             float* __restrict__ out, int R) {
+    const int tcn = (nc + 3) >> 2;
+    const int ntile = ((nj + 3) >> 2) * tcn;
+    for (int t = warp; t < ntile; t += kSplitWarps) {
+        const int tj = t / tcn;
+        const int j0 = 4 * tj, c0 = 4 * (t - tj * tcn);
+        float acc[16];
+#pragma unroll
+        for (int i = 0; i < 16; ++i) acc[i] = 0.f;
+#pragma unroll 1
+        for (int k = 4 * lane; k < Kp; k += 128) {
+            float cv[4][4], xv[4][4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                load4(Cown + (size_t)min(j0 + u, nj - 1) * Kp + k, cv[u]);
+                load4(Xb + (size_t)min(c0 + u, nc - 1) * Kp + k, xv[u]);
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int w = 0; w < 4; ++w)
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) acc[4 * u + w] = __fmaf_rn(cv[u][q], xv[w][q], acc[4 * u + w]);
+        }
+        rs32_stage<8>(acc, lane, 16);
+        rs32_stage<4>(acc, lane, 8);
+        rs32_stage<2>(acc, lane, 4);
+        rs32_stage<1>(acc, lane, 2);
+        acc[0] += __shfl_xor_sync(0xffffffffu, acc[0], 1);
+        const int e = lane >> 1, jj = j0 + (e >> 2), c = c0 + (e & 3);
+        if ((lane & 1) == 0 && jj < nj && c < nc) out[(size_t)c * R + jj] = acc[0];
+    }
+}
+
 // MODE: 0 plain; 1 adds the reduced reference state (a.Xv / a.Xs); 2 is the
 // rank-3 grouped launch (operator table a.group).  A template parameter, so
 // that each instance compiles to exactly the code its runs need.
@@ -279,22 +335,9 @@ __global__ void __launch_bounds__(kThreads, 1) rank2_split_kernel(const Rank2Arg
                 // receiver traces of V^{n+1} (the full new V of block b is in Xb)
                 if (traces && ((n + 1) % a.r) == 0) {
                     const int rec = (n + 1) / a.r - 1;
-                    const int npair = a.rpc * ncol(b);
-                    for (int pr = warp; pr < npair; pr += kSplitWarps) {
-                        const int jj = pr / ncol(b), c = pr % ncol(b), jr = s * a.rpc + jj;
-                        if (jr >= a.R) continue;
-                        float acc = 0.f;
-                        for (int k = 4 * lane; k < Kp; k += 128) {
-                            float cx[4], vx[4];
-                            load4(Cown + (size_t)jj * Kp + k, cx);
-                            load4(Xb + (size_t)c * Kp + k, vx);
-#pragma unroll
-                            for (int t = 0; t < 4; ++t) acc = __fmaf_rn(cx[t], vx[t], acc);
-                        }
-#pragma unroll
-                        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-                        if (lane == 0) traces[((size_t)rec * a.Mtot + gc0(b) + c) * a.R + jr] = acc;
-                    }
+                    const int nj = min(a.rpc, a.R - s * a.rpc);  // this CTA's receivers
+                    split_traces(Cown, Xb, Kp, nj > 0 ? nj : 0, ncol(b), warp, lane,
+                                 traces + ((size_t)rec * a.Mtot + gc0(b)) * a.R + s * a.rpc, a.R);
                 }
             }
         }
