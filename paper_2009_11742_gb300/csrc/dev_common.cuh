@@ -61,6 +61,18 @@ __device__ __forceinline__ float gauss1_dT_eval(long long step, double dt, float
     return -(float)kSqrt2e * (1.0f - 2.0f * a * a) * expf(-a * a) * dadT;
 }
 
+// The FP32 source signal of kind `wavelet` from per-column FP64 constants
+// m15T = -1.5 T and piT = pi / T set once per run: a = (t - 1.5 T) pi / T
+// takes one FMA and one multiply in FP64 instead of a division per step,
+// and the rest is the float expressions of ricker_eval / gauss1_eval.
+__device__ __forceinline__ float wavelet_eval_pre(int wavelet, long long step, double dt, double m15T,
+                                                  double piT) {
+    const float a = (float)(fma((double)step, dt, m15T) * piT);
+    if (wavelet == 1) return -(float)kSqrt2e * a * expf(-a * a);
+    const float u = a * a;
+    return (1.0f - 2.0f * u) * expf(-u);
+}
+
 // Source signal of kind `wavelet` (0 Ricker, 1 first derivative of a Gaussian).
 template <typename T>
 __device__ __forceinline__ T wavelet_eval(int wavelet, long long step, double dt, T period) {

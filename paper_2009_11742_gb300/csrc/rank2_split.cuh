@@ -45,7 +45,7 @@ constexpr int kSplitCB = 4;      // columns per register group
 constexpr int kSplitWarps = kThreads / 32;
 
 struct SplitSmem {
-    size_t X, own, comp, C, f, T, g, total;
+    size_t X, own, comp, C, f, T, Tpre, g, total;
 };
 
 __host__ __device__ inline SplitSmem split_smem_layout(int Wa, int Kp, int rpc) {
@@ -57,6 +57,7 @@ __host__ __device__ inline SplitSmem split_smem_layout(int Wa, int Kp, int rpc) 
     s.C = o;    o += align16((size_t)rpc * Kp * sizeof(float));
     s.f = o;    o += align16((size_t)2 * Wa * sizeof(float));
     s.T = o;    o += align16((size_t)2 * Wa * sizeof(float));
+    s.Tpre = o; o += align16((size_t)2 * Wa * 2 * sizeof(double));
     s.g = o;    o += align16((size_t)kSplitRows * sizeof(float));
     s.total = o;
     return s;
@@ -244,6 +245,7 @@ __global__ void __launch_bounds__(kThreads, 1) rank2_split_kernel(const Rank2Arg
     float* Cown = reinterpret_cast<float*>(smem + L.C);     // [rpc][Kp]
     float* fcol = reinterpret_cast<float*>(smem + L.f);     // [2][Wa]
     float* Tcol = reinterpret_cast<float*>(smem + L.T);     // [2][Wa]
+    double* Tpre = reinterpret_cast<double*>(smem + L.Tpre);  // [2][Wa][-1.5 T, pi / T]
     float* gown = reinterpret_cast<float*>(smem + L.g);     // [64]
 
     // column ranges of the two blocks, kept in scalars so that runtime block
@@ -291,6 +293,8 @@ __global__ void __launch_bounds__(kThreads, 1) rank2_split_kernel(const Rank2Arg
     for (int idx = tid; idx < 2 * Wa; idx += kThreads) {
         const int b = idx / Wa, c = idx % Wa;
         Tcol[idx] = (a.Tper && c < ncol(b)) ? static_cast<const float*>(a.Tper)[gc0(b) + c] : 1.f;
+        Tpre[2 * idx] = -1.5 * (double)Tcol[idx];
+        Tpre[2 * idx + 1] = 3.14159265358979323846 / (double)Tcol[idx];
     }
     __syncthreads();
     // forcing of the first V phase (block A, step 0)
@@ -299,7 +303,7 @@ __global__ void __launch_bounds__(kThreads, 1) rank2_split_kernel(const Rank2Arg
             float f = 0.f;
             if (c < ncol(0)) {
                 if (a.ftab) f = static_cast<const float*>(a.ftab)[gc0(0) + c];
-                else if (a.Tper) f = wavelet_eval(a.wavelet, (long long)a.n0, a.dt, Tcol[c]);
+                else if (a.Tper) f = wavelet_eval_pre(a.wavelet, (long long)a.n0, a.dt, Tpre[2 * c], Tpre[2 * c + 1]);
             }
             fcol[c] = f;
         }
@@ -350,7 +354,10 @@ __global__ void __launch_bounds__(kThreads, 1) rank2_split_kernel(const Rank2Arg
                     float f = 0.f;
                     if (c < ncol(b2)) {
                         if (a.ftab) f = static_cast<const float*>(a.ftab)[(size_t)n2 * a.Mtot + gc0(b2) + c];
-                        else if (a.Tper) f = wavelet_eval(a.wavelet, (long long)a.n0 + n2, a.dt, Tcol[b2 * Wa + c]);
+                        else if (a.Tper) {
+                            const double* tp = Tpre + 2 * (b2 * Wa + c);
+                            f = wavelet_eval_pre(a.wavelet, (long long)a.n0 + n2, a.dt, tp[0], tp[1]);
+                        }
                     }
                     fcol[b2 * Wa + c] = f;
                 }
