@@ -26,3 +26,18 @@ def test_reference_arm_line_keeps_the_contract():
     assert d["cpu_baseline"]["value"] == d["value"]
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
     assert d["config"]["workload"].startswith("rank2-fp32-K512-M256")
+
+
+def test_roofline_traffic_comes_from_the_committed_profile():
+    """The headline line's roofline `traffic` is read from the ncu summary of
+    the split kernel on the headline workload; the summary must keep the
+    line the bench parses, with read + write bytes of one full launch."""
+    import re
+    import bench
+    t = bench.profiled_traffic("rank2_split_kernel<8>", 10000)
+    assert isinstance(t, int) and t > 0
+    text = open(os.path.join(ROOT, "profiles", "rank2_split_kernel_fp32_K512_M256_N10000.md")).read()
+    rd = int(re.search(r"dram__bytes_read\.sum \| ([\d,]+) B", text).group(1).replace(",", ""))
+    wr = int(re.search(r"dram__bytes_write\.sum \| ([\d,]+) B", text).group(1).replace(",", ""))
+    assert t == rd + wr
+    assert bench.profiled_traffic("rank2_split_kernel<8>", 1234) is None
