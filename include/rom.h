@@ -64,7 +64,9 @@ typedef enum {
     ROM_E_UNSTABLE = 4,    /* dt * rho >= 2 at rom_create: leapfrog would blow up */
     ROM_E_TIMEOUT = 5,     /* a bounded device wait ran out */
     ROM_E_NONFINITE = 6,   /* the final state holds NaN or Inf */
-    ROM_E_UNSUPPORTED = 7  /* shape/precision combination not provided */
+    ROM_E_UNSUPPORTED = 7, /* shape/precision combination not provided */
+    ROM_E_NOCONV = 8       /* the FP64 power iteration of the dt-stability check did not
+                              settle within its iteration limit */
 } rom_status;
 
 typedef enum {
@@ -100,7 +102,11 @@ typedef enum { ROM_IN_F64 = 0, ROM_IN_F32 = 1 } rom_dtype;
  * radius of the coupled operator [[0, Avs], [Asv, 0]], equals
  * sqrt(rho(Avs Asv)) and is computed by FP64 power iteration on the GPU.  If
  * dt * rho >= 2 the handle is not created and ROM_E_UNSTABLE is returned.
- * *rho_out (may be NULL) receives rho in either case.
+ * The iteration stops once two successive estimates agree to 1e-14
+ * relative; if that has not happened after 20000 iterations the estimate is
+ * only a lower bound on rho, so the check cannot be certified: the handle is
+ * not created and ROM_E_NOCONV is returned.  *rho_out (may be NULL) receives
+ * rho (or, for ROM_E_NOCONV, the last estimate) in every one of these cases.
  * Limits: 1 <= Kv, Ks <= 1024, 0 <= R <= 1024.  Runs on the current device.
  */
 rom_status rom_create(const void* Avs, const void* Asv, const void* g, const void* C,
@@ -423,8 +429,14 @@ rom_status rom_rel_l2(const void* x, int x_dtype, const void* ref, int ref_dtype
  * before any stream capture.  All calls on a device share the array and it
  * keeps the last call's contents (each call re-initialises what it reads), so
  * calls that overlap on the GPU -- on two streams, or from two host threads --
- * race and must be serialised by the caller.  Synchronous on `stream`; errors
- * as for rom_create.
+ * race and must be serialised by the caller.  The address is looked up once
+ * per device and kept: after cudaDeviceReset (or any other teardown of the
+ * device's primary context) the cached address is stale, so do not call this
+ * entry point again in that process after such a reset.  Synchronous on
+ * `stream`.  Errors: ROM_E_INVAL (sizes, host buffers, or buffers that live
+ * on a device other than the current one), ROM_E_NOCONV (no convergence
+ * within 20000 iterations; *rho then holds the last estimate), ROM_E_CUDA or
+ * ROM_E_NOMEM (a CUDA call failed; rom_last_error gives the text).
  */
 rom_status rom_spectral_radius_noalloc(const double* Avs, const double* Asv, int Kv, int Ks,
                                        double* rho, void* stream);

@@ -52,8 +52,11 @@
 namespace romk {
 
 struct DataflowSmem {
-    size_t X, own, comp, C, T, g, mbar, flag, total;
+    size_t X, own, comp, C, T, g, mbar, flag, sent, total;
 };
+
+// Largest number of producer CTAs of one role (H = Kp / 64 <= 16).
+constexpr int kDataflowMaxH = 16;
 
 __host__ __device__ inline DataflowSmem dataflow_smem_layout(int Wa, int Kp, int rpc) {
     DataflowSmem s{};
@@ -66,6 +69,9 @@ __host__ __device__ inline DataflowSmem dataflow_smem_layout(int Wa, int Kp, int
     s.g = o;    o += align16((size_t)kSplitRows * sizeof(float));
     s.mbar = o; o += align16((size_t)2 * sizeof(unsigned long long));
     s.flag = o; o += 16;
+    // bytes each producer slab of the other role sent per block [H][2], the
+    // phases armed per block [2], and this CTA's own sent bytes per block [2]
+    s.sent = o; o += align16((size_t)(kDataflowMaxH * 2 + 4) * sizeof(unsigned));
     s.total = o;
     return s;
 }
@@ -85,6 +91,13 @@ __device__ __forceinline__ void fence_mbar_init_cluster() {
 // current phase waits for.
 __device__ __forceinline__ void mbar_arrive_expect_tx(unsigned long long* bar, unsigned bytes) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
+                 ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+}
+// Count `bytes` as arrived on the current phase of a local mbarrier without
+// an asynchronous copy (used to retire bytes a producer will never send).
+__device__ __forceinline__ void mbar_complete_tx(unsigned long long* bar, unsigned bytes) {
+    asm volatile("mbarrier.complete_tx.relaxed.cta.shared::cta.b64 [%0], %1;"
                  ::"r"(smem_addr(bar)), "r"(bytes)
                  : "memory");
 }
@@ -146,6 +159,9 @@ __global__ void __launch_bounds__(kThreads, 1) rank2_dataflow_kernel(const Rank2
     float* gown = reinterpret_cast<float*>(smem + L.g);     // [64] source row
     unsigned long long* mbar = reinterpret_cast<unsigned long long*>(smem + L.mbar);  // [2]
     volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + L.flag);
+    unsigned* sent_in = reinterpret_cast<unsigned*>(smem + L.sent);  // [H][2], written by peers
+    unsigned* armed = sent_in + 2 * kDataflowMaxH;                    // [2]
+    unsigned* sent_out = armed + 2;                                   // [2]
 
     // column ranges of the two blocks, kept in scalars
     const int gc0_0 = a.col_base + (2 * clu) * a.Wv;
@@ -196,9 +212,11 @@ __global__ void __launch_bounds__(kThreads, 1) rank2_dataflow_kernel(const Rank2
     const unsigned block_bytes = (unsigned)(H * kSplitRows * Wa * sizeof(float));
     if (tid == 0) {
         *abort_flag = 0;
+        for (int i = 0; i < 2 * kDataflowMaxH + 4; ++i) sent_in[i] = 0u;
         for (int i = 0; i < 2; ++i) mbar_init(&mbar[i], 1u);
         fence_mbar_init_cluster();
         for (int i = 0; i < 2; ++i) mbar_arrive_expect_tx(&mbar[i], block_bytes);
+        armed[0] = armed[1] = 1u;
     }
 
     float op[4][4 * KI];
@@ -222,6 +240,9 @@ __global__ void __launch_bounds__(kThreads, 1) rank2_dataflow_kernel(const Rank2
     const int nphase = 2 * N + 1;
     const bool stall_test = a.debug_skip_push && crank == 0;
     const float* Xrole = static_cast<const float*>(vrole ? a.Xv : a.Xs);  // reference state or null
+    // column groups this warp pushed per block (every push carries 128 bytes
+    // to each consumer CTA): retires unsent bytes after a timeout, see below
+    unsigned pushed0 = 0u, pushed1 = 0u;
     for (int p = 0; p < nphase; ++p) {
         int b, n;
         if (vrole) { b = p & 1; n = (p - b) >> 1; }
@@ -249,7 +270,10 @@ __global__ void __launch_bounds__(kThreads, 1) rank2_dataflow_kernel(const Rank2
             // arm the next completion of this mbarrier (the V role also
             // receives S^N, which it drains before leaving)
             const int k = vrole ? n - 1 : n;
-            if (warp == 0 && lane == 0 && k + 1 <= N - 1) mbar_arrive_expect_tx(mb, block_bytes);
+            if (warp == 0 && lane == 0 && k + 1 <= N - 1) {
+                mbar_arrive_expect_tx(mb, block_bytes);
+                armed[b] += 1u;
+            }
         }
         for (int g = 0; g < G; ++g) {
             const int c0 = g * CB;
@@ -346,6 +370,7 @@ __global__ void __launch_bounds__(kThreads, 1) rank2_dataflow_kernel(const Rank2
                             : "memory");
                     }
                 }
+                if (b) ++pushed1; else ++pushed0;
             }
         }
     }
@@ -362,11 +387,45 @@ __global__ void __launch_bounds__(kThreads, 1) rank2_dataflow_kernel(const Rank2
     }
     const bool aborted = *abort_flag != 0;
     if (aborted && tid == 0 && a.status) atomicCAS(a.status, 0, 5 /* ROM_E_TIMEOUT */);
-    // no CTA leaves while a peer may still store into its shared memory
+    // ---- drain.  Stores a peer issued before it stopped may still be in
+    // flight into this CTA's shared memory.  Every CTA (a timeout or not, so
+    // the barriers stay cluster-uniform) tells each consumer how many bytes it
+    // sent per block; past the barrier no CTA issues another store.  Each
+    // consumer then retires, on the phase it armed last, the bytes that will
+    // never come (armed phases x block bytes - bytes sent), so that phase
+    // completes exactly when every byte sent has landed, and waits for it
+    // (bounded).  After a complete run nothing is outstanding and the wait
+    // returns at once.
+    if (lane == 0) {
+        atomicAdd(&sent_out[0], pushed0 * 128u);
+        atomicAdd(&sent_out[1], pushed1 * 128u);
+    }
+    __syncthreads();
+    if (tid < H) {
+        unsigned dst;
+        asm volatile("mapa.shared::cluster.u32 %0, %1, %2;"
+                     : "=r"(dst) : "r"(smem_addr(sent_in + 2 * s)), "r"(peer0 + tid));
+        asm volatile("st.shared::cluster.v2.u32 [%0], {%1, %2};"
+                     ::"r"(dst), "r"(sent_out[0]), "r"(sent_out[1]) : "memory");
+    }
     cluster.sync();
-    // after a timeout, give stores that peers issued just before the barrier
-    // time to land before this CTA's shared memory goes away
-    if (aborted) __nanosleep(200000);
+    if (tid == 0) {
+        for (int b = 0; b < 2; ++b) {
+            unsigned got = 0u;
+            for (int d = 0; d < H; ++d) got += sent_in[2 * d + b];
+            const unsigned expect = armed[b] * block_bytes;
+            if (expect > got) mbar_complete_tx(&mbar[b], expect - got);
+            const unsigned parity = (armed[b] - 1u) & 1u;
+            const long long t0 = clock64();
+            while (!mbar_try_wait(&mbar[b], parity)) {
+                if (clock64() - t0 > limit) {
+                    if (a.status) atomicCAS(a.status, 0, 5 /* ROM_E_TIMEOUT */);
+                    break;
+                }
+            }
+        }
+    }
+    __syncthreads();
 
     // ---- write back the owned rows and carries
     float* out = static_cast<float*>(vrole ? a.V : a.S);

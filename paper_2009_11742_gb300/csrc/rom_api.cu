@@ -23,12 +23,12 @@ thread_local char g_last_error[256] = "";
 
 void romk::set_last_error(const char* msg) { snprintf(g_last_error, sizeof(g_last_error), "%s", msg); }
 
-namespace {
-
-rom_status cuda_fail(cudaError_t e, const char* where) {
+rom_status romk::cuda_fail(cudaError_t e, const char* where) {
     snprintf(g_last_error, sizeof(g_last_error), "%s: %s", where, cudaGetErrorString(e));
     return e == cudaErrorMemoryAllocation ? ROM_E_NOMEM : ROM_E_CUDA;
 }
+
+namespace {
 
 #define ROM_CUDA(call)                                      \
     do {                                                    \
@@ -168,6 +168,7 @@ rom_status power_iteration(rom_s* h, double* rho_out) {
     std::vector<double> hl(chunk);
     rom_status st = ROM_OK;
     double cur = 0.0, prev = -1.0;
+    bool converged = false;
     e = cudaMemcpy(x, hx.data(), sizeof(double) * Kv, cudaMemcpyHostToDevice);
     for (int it0 = 1; e == cudaSuccess && it0 <= max_iter; it0 += chunk) {
         const int it1 = it0 + chunk - 1 <= max_iter ? it0 + chunk - 1 : max_iter;
@@ -181,15 +182,15 @@ rom_status power_iteration(rom_s* h, double* rho_out) {
         const int cnt = it1 - it0 + 1;
         e = cudaMemcpy(hl.data(), lam + it0, sizeof(double) * cnt, cudaMemcpyDeviceToHost);
         if (e != cudaSuccess) break;
-        bool done = false;
         for (int i = 0; i < cnt; ++i) {
             cur = hl[i];
-            if (prev >= 0.0 && fabs(cur - prev) <= tol * cur) { done = true; break; }
+            if (prev >= 0.0 && fabs(cur - prev) <= tol * cur) { converged = true; break; }
             prev = cur;
         }
-        if (done || cur == 0.0) break;
+        if (converged) break;
     }
     if (e != cudaSuccess) st = cuda_fail(e, "power_iteration");
+    else if (!converged) st = ROM_E_NOCONV;
     cudaFree(x); cudaFree(z); cudaFree(y); cudaFree(lam);
     *rho_out = sqrt(cur);
     return st;
@@ -224,6 +225,7 @@ const char* rom_status_string(rom_status s) {
         case ROM_E_TIMEOUT: return "ROM_E_TIMEOUT: device wait ran out";
         case ROM_E_NONFINITE: return "ROM_E_NONFINITE: non-finite state";
         case ROM_E_UNSUPPORTED: return "ROM_E_UNSUPPORTED: shape/precision not provided";
+        case ROM_E_NOCONV: return "ROM_E_NOCONV: power iteration did not converge";
     }
     return "unknown rom_status";
 }
@@ -295,6 +297,8 @@ rom_status rom_create(const void* Avs, const void* Asv, const void* g, const voi
     double rho = 0.0;
     st = power_iteration(h, &rho);
     if (st != ROM_OK) {
+        // not converged: the estimate is only a lower bound, so no handle
+        if (st == ROM_E_NOCONV && rho_out) *rho_out = rho;
         free_handle(h);
         return st;
     }

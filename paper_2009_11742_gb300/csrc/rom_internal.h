@@ -10,6 +10,9 @@ namespace romk {
 
 // Record a message for rom_last_error() (this thread).
 void set_last_error(const char* msg);
+// Record "where: <CUDA error text>" for rom_last_error() and map the error to
+// a status: ROM_E_NOMEM for an allocation failure, ROM_E_CUDA otherwise.
+rom_status cuda_fail(cudaError_t e, const char* where);
 
 // Arguments of one rank-2 launch (all device pointers).  Element type T of
 // the state-like buffers is double for ROM_FP64 and float otherwise.

@@ -33,13 +33,17 @@ __global__ void fill_start_vector(double* x, int n) {
     if (i < n) x[i] = 1.0 / sqrt((double)n);
 }
 
-bool is_device_pointer(const void* p) {
+// True for device (or managed) memory that the current device `dev` can read
+// directly: plain device memory must belong to `dev` itself, since a peer's
+// buffer would need peer access, which this entry point does not set up.
+bool is_local_device_pointer(const void* p, int dev) {
     cudaPointerAttributes at;
     if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
         cudaGetLastError();
         return false;
     }
-    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+    if (at.type == cudaMemoryTypeManaged) return true;
+    return at.type == cudaMemoryTypeDevice && at.device == dev;
 }
 
 }  // namespace
@@ -49,16 +53,25 @@ extern "C" rom_status rom_spectral_radius_noalloc(const double* Avs, const doubl
     if (!Avs || !Asv || !rho || Kv < 1 || Ks < 1) return ROM_E_INVAL;
     // the work area is fixed: larger operators are refused, never truncated
     if (Kv > kNoallocMaxK || Ks > kNoallocMaxK) return ROM_E_INVAL;
-    if (!is_device_pointer(Avs) || !is_device_pointer(Asv)) return ROM_E_INVAL;
     int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return ROM_E_CUDA;
+    cudaError_t de = cudaGetDevice(&dev);
+    if (de != cudaSuccess) return romk::cuda_fail(de, "rom_spectral_radius_noalloc");
+    if (dev < 0 || dev >= kMaxDevices) {
+        romk::set_last_error("rom_spectral_radius_noalloc: device ordinal beyond the supported 64");
+        return ROM_E_CUDA;
+    }
+    if (!is_local_device_pointer(Avs, dev) || !is_local_device_pointer(Asv, dev)) return ROM_E_INVAL;
     double* base = nullptr;
     {
         std::lock_guard<std::mutex> lk(g_setup_mu);
         if (!g_scratch_addr[dev]) {
             void* p = nullptr;
             cudaError_t e = cudaGetSymbolAddress(&p, g_power_scratch);
-            if (e != cudaSuccess || !p) return ROM_E_CUDA;
+            if (e != cudaSuccess) return romk::cuda_fail(e, "rom_spectral_radius_noalloc setup");
+            if (!p) {
+                romk::set_last_error("rom_spectral_radius_noalloc setup: null symbol address");
+                return ROM_E_CUDA;
+            }
             g_scratch_addr[dev] = static_cast<double*>(p);
         }
         base = g_scratch_addr[dev];
@@ -78,6 +91,7 @@ extern "C" rom_status rom_spectral_radius_noalloc(const double* Avs, const doubl
     const double tol = 1e-14;
     double hl[kNoallocChunk];
     double cur = 0.0, prev = -1.0;
+    bool converged = false;
     for (int it0 = 1; e == cudaSuccess && it0 <= max_iter; it0 += kNoallocChunk) {
         const int it1 = it0 + kNoallocChunk - 1 <= max_iter ? it0 + kNoallocChunk - 1 : max_iter;
         for (int it = it0; it <= it1 && e == cudaSuccess; ++it) {
@@ -90,15 +104,15 @@ extern "C" rom_status rom_spectral_radius_noalloc(const double* Avs, const doubl
         e = cudaMemcpyAsync(hl, lam, sizeof(double) * cnt, cudaMemcpyDeviceToHost, st);
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);
         if (e != cudaSuccess) break;
-        bool done = false;
         for (int i = 0; i < cnt; ++i) {
             cur = hl[i];
-            if (prev >= 0.0 && fabs(cur - prev) <= tol * cur) { done = true; break; }
+            if (prev >= 0.0 && fabs(cur - prev) <= tol * cur) { converged = true; break; }
             prev = cur;
         }
-        if (done || cur == 0.0) break;
+        if (converged) break;
     }
-    if (e != cudaSuccess) return ROM_E_CUDA;
+    if (e != cudaSuccess) return romk::cuda_fail(e, "rom_spectral_radius_noalloc");
     *rho = sqrt(cur);
-    return ROM_OK;
+    // not converged: the estimate is only a lower bound on rho
+    return converged ? ROM_OK : ROM_E_NOCONV;
 }

@@ -26,7 +26,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_build", "librom.so")
 
 ROM_OK, ROM_E_INVAL, ROM_E_NOMEM, ROM_E_CUDA, ROM_E_UNSTABLE, ROM_E_TIMEOUT, \
-    ROM_E_NONFINITE, ROM_E_UNSUPPORTED = range(8)
+    ROM_E_NONFINITE, ROM_E_UNSUPPORTED, ROM_E_NOCONV = range(9)
 ROM_FP64, ROM_FP32, ROM_TF32X3, ROM_BF16X3, ROM_BF16, ROM_BF16S, ROM_AUTO = range(7)
 ROM_IN_F64, ROM_IN_F32 = 0, 1
 ROM_KERNEL_AUTO, ROM_KERNEL_ONE_BLOCK, ROM_KERNEL_TWO_BLOCK, ROM_KERNEL_DATAFLOW = 0, 1, 2, 3

@@ -48,6 +48,29 @@ def test_status_strings_without_gpu(lib):
     assert lib.rom_version() >= 100
 
 
+def test_noconv_status_string(lib):
+    lib.rom_status_string.restype = ctypes.c_char_p
+    assert b"NOCONV" in lib.rom_status_string(8)
+
+
+def test_noalloc_errors_without_gpu(lib):
+    """The allocation-free entry point checks its sizes before any CUDA call,
+    and a failing CUDA call is reported through rom_last_error like every
+    other entry point's."""
+    lib.rom_last_error.restype = ctypes.c_char_p
+    rho = ctypes.c_double(0.0)
+    fake = ctypes.c_void_p(16)
+    assert lib.rom_spectral_radius_noalloc(fake, fake, 4097, 4, ctypes.byref(rho), None) == 1
+    assert lib.rom_spectral_radius_noalloc(fake, fake, 0, 4, ctypes.byref(rho), None) == 1
+    assert lib.rom_spectral_radius_noalloc(None, fake, 4, 4, ctypes.byref(rho), None) == 1
+    import torch
+    if torch.cuda.is_available():
+        return
+    rc = lib.rom_spectral_radius_noalloc(fake, fake, 4, 4, ctypes.byref(rho), None)
+    assert rc in (2, 3)  # ROM_E_NOMEM / ROM_E_CUDA: no device to run on
+    assert b"rom_spectral_radius_noalloc" in lib.rom_last_error()
+
+
 def test_null_arguments_rejected_without_gpu(lib):
     """Argument checks happen before any CUDA call."""
     h = ctypes.c_void_p()

@@ -16,6 +16,14 @@ def rel(a, b):
     return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
 
 
+def colmax_rel(a, b):
+    """Largest per-column relative L2 error (columns are realizations)."""
+    a = np.asarray(a, np.float64)
+    b = np.asarray(b, np.float64)
+    num = np.linalg.norm(a - b, axis=0)
+    return float(np.max(num / np.maximum(np.linalg.norm(b, axis=0), 1e-300)))
+
+
 @pytest.fixture(scope="module")
 def rom():
     if not torch.cuda.is_available():
@@ -88,21 +96,49 @@ def test_autograd_function(rom):
     np.testing.assert_allclose(T.grad.cpu().numpy(), 3.0 * gT, rtol=1e-6)
 
 
-def test_period_gradient_vs_gpu_finite_difference(rom):
-    """dL/dT_m against central differences (h = 1e-3) of the GPU misfit."""
-    p, V0, S0, ystar = case(96, 96, 4, 4, 150, seed=13, x0=0.0)
+def test_gradients_vs_fp64_finite_differences_workload4_shape(rom):
+    """Workload-4 shapes (K = 512, R = 64, a record every step, checkpoints
+    every 64 steps) on four sampled realizations over 300 steps, from a seeded
+    nonzero start.  The GPU adjoint's dL/dT_m and its gradients w.r.t. V0 and
+    S0, projected on seeded random directions, are held to 1e-4 relative of
+    central differences (h = 1e-3) of the misfit that the FP64 oracle's
+    forward run gives.  The misfit is quadratic in (V0, S0), so those
+    differences are exact up to rounding; for T the difference quotient's own
+    error is O(h^2), far below the bar."""
+    p = inputs.config(4)
+    N, K = 300, 512
+    cols = np.array([0, 41, 77, 127])
+    M = len(cols)
+    T = p.T.astype(np.float64)[cols]
+    Z = np.zeros((K, M))
+    _, _, ys = oracle.forward(p.Avs, p.Asv, p.g, p.C, p.dt, Z, Z, N, T=1.05 * T, r=1)
+    ystar = ys.astype(np.float32)
+    ys64 = ystar.astype(np.float64)
+    V0 = inputs.random_state(K, M, seed=41, scale=0.05).astype(np.float32).astype(np.float64)
+    S0 = inputs.random_state(K, M, seed=42, scale=0.05).astype(np.float32).astype(np.float64)
     h = rom.Rom.from_problem(p)
-    _, _, _, gT = gpu_adjoint(rom, h, p, V0, S0, ystar, 150, 0)
+    loss, gV, gS, gT = gpu_adjoint(rom, h, _with_T(p, T), V0, S0, ystar, N, 64)
+
+    def misfit(V0_, S0_, T_):
+        _, _, tr = oracle.forward(p.Avs, p.Asv, p.g, p.C, p.dt, V0_, S0_, N, T=T_, r=1)
+        return float(np.sum((tr - ys64) ** 2))
+
+    L0 = misfit(V0, S0, T)
+    assert abs(loss - L0) <= 1e-4 * L0
     step = 1e-3
-    for m in (0, 3):
-        Tp = p.T.astype(np.float64).copy()
-        Tm = Tp.copy()
+    for m in range(M):
+        Tp, Tm = T.copy(), T.copy()
         Tp[m] += step
         Tm[m] -= step
-        Lp = gpu_adjoint(rom, h, _with_T(p, Tp), V0, S0, ystar, 150, 0)[0]
-        Lm = gpu_adjoint(rom, h, _with_T(p, Tm), V0, S0, ystar, 150, 0)[0]
-        fd = (Lp - Lm) / (2 * step)
-        assert abs(fd - gT[m]) <= 2e-3 * abs(gT[m]), (fd, gT[m])
+        fd = (misfit(V0, S0, Tp) - misfit(V0, S0, Tm)) / (2 * step)
+        assert abs(gT[m] - fd) <= 1e-4 * abs(fd), (m, gT[m], fd)
+    rng = np.random.default_rng(7)
+    for _ in range(2):
+        D = rng.standard_normal((K, M))
+        fdV = (misfit(V0 + step * D, S0, T) - misfit(V0 - step * D, S0, T)) / (2 * step)
+        fdS = (misfit(V0, S0 + step * D, T) - misfit(V0, S0 - step * D, T)) / (2 * step)
+        assert abs(float(np.sum(gV * D)) - fdV) <= 1e-4 * abs(fdV), (np.sum(gV * D), fdV)
+        assert abs(float(np.sum(gS * D)) - fdS) <= 1e-4 * abs(fdS), (np.sum(gS * D), fdS)
 
 
 def _with_T(p, T):
@@ -130,6 +166,6 @@ def test_adjoint_workload4_full_size_sampled(rom):
     loss, gV, gS, gT = gpu_adjoint(rom, h, p, V0, V0, ystar, N, 64)
     Lo, gVo, gSo, gTo = oracle.adjoint(p.Avs, p.Asv, p.g, p.C, p.dt, Z, Z, T_s, N,
                                        ys_s.astype(np.float32))
-    assert rel(gV[:, cols], gVo) <= 1e-4
-    assert rel(gS[:, cols], gSo) <= 1e-4
-    assert rel(gT[cols], gTo) <= 1e-4
+    assert colmax_rel(gV[:, cols], gVo) <= 1e-4
+    assert colmax_rel(gS[:, cols], gSo) <= 1e-4
+    assert np.max(np.abs(gT[cols] - gTo) / np.abs(gTo)) <= 1e-4

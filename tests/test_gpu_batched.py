@@ -16,6 +16,14 @@ def rel(a, b):
     return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
 
 
+def colmax_rel(a, b):
+    """Largest per-column relative L2 error (columns are realizations)."""
+    a = np.asarray(a, np.float64)
+    b = np.asarray(b, np.float64)
+    num = np.linalg.norm(a - b, axis=0)
+    return float(np.max(num / np.maximum(np.linalg.norm(b, axis=0), 1e-300)))
+
+
 @pytest.fixture(scope="module")
 def rom():
     if not torch.cuda.is_available():
@@ -92,7 +100,8 @@ def test_batched_rejects_bad_jobs(rom):
 
 def test_batched_workload3_full_size_sampled(rom):
     """Workload 3: 64 ROMs, K_i in {64..768}, M_i in [4, 256], 5000 steps, one
-    graph launch; the oracle recomputes two columns of every eighth ROM."""
+    graph launch; the oracle recomputes the first, middle and last column of
+    every fourth ROM, each column held to the bar on its own."""
     probs = inputs.batched_problems()
     jobs = []
     for p in probs:
@@ -101,13 +110,13 @@ def test_batched_workload3_full_size_sampled(rom):
                      torch.as_tensor(p.T, device="cuda"), None))
     rom.run_batched(jobs, 5000, prec="fp32")
     torch.cuda.synchronize()
-    for i in range(0, 64, 8):
+    for i in range(0, 64, 4):
         h, V, S, T, _ = jobs[i]
         p = probs[i]
-        cols = np.array([0, p.M - 1])
+        cols = np.unique([0, p.M // 2, p.M - 1])
         Vo, So, _ = oracle.problem_forward(p, nsteps=5000, r=0, columns=cols)
-        assert rel(V.cpu().numpy()[:, cols], Vo) <= 1e-4
-        assert rel(S.cpu().numpy()[:, cols], So) <= 1e-4
+        assert colmax_rel(V.cpu().numpy()[:, cols], Vo) <= 1e-4
+        assert colmax_rel(S.cpu().numpy()[:, cols], So) <= 1e-4
 
 
 def test_autotune_batched_keeps_results(rom):

@@ -30,6 +30,19 @@ def rom():
     return R
 
 
+def colmax_rel(a, b):
+    """Largest per-realization relative L2 error (Eq. (errors), Sec. 4.4):
+    the last axis indexes the realizations (columns), every other axis is
+    one realization's values.  One bad column cannot hide among good ones."""
+    a = np.asarray(a, np.float64)
+    b = np.asarray(b, np.float64)
+    a = a.reshape(-1, a.shape[-1])
+    b = b.reshape(-1, b.shape[-1])
+    num = np.linalg.norm(a - b, axis=0)
+    den = np.maximum(np.linalg.norm(b, axis=0), 1e-300)
+    return float(np.max(num / den))
+
+
 def tdt(prec):
     return torch.float64 if prec == "fp64" else torch.float32
 
@@ -67,6 +80,16 @@ def test_unstable_dt_refused(rom):
     with pytest.raises(rom.RomError) as ei:
         rom.Rom(p.Avs, p.Asv, p.g, None, dt=4.1 / np.linalg.norm(p.Asv.astype(np.float64), 2))
     assert ei.value.status == rom.ROM_E_UNSTABLE
+
+
+def test_unconverged_power_iteration_refused(rom):
+    """rom_create refuses an operator pair whose power iteration never
+    settles (Avs Asv with the complex dominant pair +-2i of a non-normal
+    matrix): the estimate would only be a lower bound on rho, so the dt check
+    cannot be certified."""
+    with pytest.raises(rom.RomError) as ei:
+        rom.Rom(np.eye(2), np.array([[0.0, -4.0], [1.0, 0.0]]), np.ones(2), None, dt=0.01)
+    assert ei.value.status == rom.ROM_E_NOCONV
 
 
 def test_config0_fp64(rom):
@@ -110,11 +133,16 @@ def test_config1_fp32_sampled_columns(rom):
     h = rom.Rom.from_problem(p)
     Z = np.zeros((512, 256))
     V, S, tr = gpu_run(rom, h, p, Z, Z, 10000, "fp32", r=10)
-    cols = np.array([0, 31, 32, 100, 159, 200, 254, 255])
+    # 40 of the 256 columns: both ends of every cluster's column blocks and a
+    # seeded random draw; each column is held to the bar on its own
+    rng = np.random.default_rng(1)
+    cols = np.unique(np.concatenate([[0, 17, 18, 19, 20, 36, 37, 127, 128, 236, 254, 255],
+                                     rng.choice(256, 28, replace=False)]))
+    assert len(cols) >= 32
     Vo, So, tro = oracle.problem_forward(p, nsteps=10000, r=10, columns=cols)
-    assert rel(V[:, cols], Vo) <= 1e-4
-    assert rel(S[:, cols], So) <= 1e-4
-    assert rel(tr[:, :, cols], tro) <= 1e-4
+    assert colmax_rel(V[:, cols], Vo) <= 1e-4
+    assert colmax_rel(S[:, cols], So) <= 1e-4
+    assert colmax_rel(tr[:, :, cols], tro) <= 1e-4
     # every column is finite and non-trivial
     assert np.all(np.isfinite(V)) and np.all(np.linalg.norm(V, axis=0) > 0)
 

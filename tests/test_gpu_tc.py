@@ -1,10 +1,18 @@
 """GPU parity of the tensor-core (tcgen05) rank-2 path against the FP64 oracle.
 
-TF32x3 is held to the FP32 bar (relative L2 <= 1e-4, Eq. (errors), Sec. 4.4).
-The 16-bit splits are reported with looser bounds: BF16x3 keeps a two-term
-state, plain BF16 one term.  The exact sliced-integer BF16 scheme (bf16s)
-rounds nowhere inside the tensor core and is held to 1e-5 on short runs and
-to 1e-4 over the full 20000-step horizon.
+Accepted (held to the FP32 bar, relative L2 <= 1e-4, Eq. (errors), Sec. 4.4,
+over the full horizon): the exact sliced-integer BF16 scheme (bf16s), which
+rounds nowhere inside the tensor core.  It is held to 1e-5 on short runs and
+to 1e-4 over workload 2's 20000 steps.
+
+Reported, not accepted: TF32x3, BF16x3 and plain BF16.  Their term splits
+are accurate enough in exact arithmetic (a numpy emulation of the TF32x3 and
+BF16x3 splits with exact sums stays within 5e-7 and 8e-6 of the oracle over
+200 steps), but the tensor core's FP32 accumulation truncates, which biases
+every product toward zero; over workload 2's 20000 steps TF32x3 then ends
+about 1e-3 from the oracle.  Here they get short-run checks only: TF32x3
+still meets 1e-4 on short runs; BF16x3 and BF16 get sanity bounds, as a
+reported path does.
 """
 import numpy as np
 import pytest
@@ -15,7 +23,20 @@ from paper_2009_11742_gb300 import inputs
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
+# bars against the FP64 oracle on short runs: bf16s (accepted) and tf32x3;
+# sanity bounds for the reported-only bf16x3 and bf16
 TOL = {"tf32x3": 1e-4, "bf16x3": 1e-3, "bf16": 5e-2, "bf16s": 1e-5}
+
+
+def colmax_rel(a, b):
+    """Largest per-realization relative L2 error: the last axis indexes the
+    realizations, every other axis is one realization's values."""
+    a = np.asarray(a, np.float64)
+    b = np.asarray(b, np.float64)
+    a = a.reshape(-1, a.shape[-1])
+    b = b.reshape(-1, b.shape[-1])
+    num = np.linalg.norm(a - b, axis=0)
+    return float(np.max(num / np.maximum(np.linalg.norm(b, axis=0), 1e-300)))
 
 
 def rel(a, b):
@@ -48,11 +69,14 @@ def run_tc(R, h, p, V0, S0, N, prec, r=0, n0=0, ftab=None, comp=None):
     return V.cpu().numpy(), S.cpu().numpy(), (None if tr is None else tr.transpose(1, 2).cpu().numpy())
 
 
+SMALL_CASES = [(128, 128, 64, 4, 200, 10),   # one-CTA cluster
+               (200, 180, 100, 8, 150, 6),   # ragged rows, 2 blocks
+               (64, 64, 5, 2, 120, 4),       # K < 128, M < 64
+               (384, 384, 70, 16, 100, 5)]   # 3-CTA cluster
+
+
 @pytest.mark.parametrize("prec", ["tf32x3", "bf16x3", "bf16", "bf16s"])
-@pytest.mark.parametrize("Kv,Ks,M,R,N,r", [(128, 128, 64, 4, 200, 10),   # one-CTA cluster
-                                           (200, 180, 100, 8, 150, 6),   # ragged rows, 2 blocks
-                                           (64, 64, 5, 2, 120, 4),       # K < 128, M < 64
-                                           (384, 384, 70, 16, 100, 5)])  # 3-CTA cluster
+@pytest.mark.parametrize("Kv,Ks,M,R,N,r", SMALL_CASES)
 def test_tc_small_vs_oracle(rom, prec, Kv, Ks, M, R, N, r):
     p = inputs.make_problem(Kv, Ks, M, R, seed=Kv + M + 1)
     h = rom.Rom.from_problem(p)
@@ -173,14 +197,6 @@ def test_bf16s_scales_span_many_binades(rom):
         assert rel(V[:, m], Vo[:, m]) <= 1e-5 and rel(S[:, m], So[:, m]) <= 1e-5
 
 
-# Measured full-horizon bound of the tensor-core TF32x3 path.  The tensor
-# core's FP32 accumulation rounds toward zero; chunk-wise readout into FP32
-# registers removes most of the resulting drift, but over 20000 steps the
-# remaining bias still leaves the final state about 1e-3 away from the FP64
-# oracle (short horizons meet 1e-4, see test_tc_k1024_tf32x3).
-TC_FULL_HORIZON_BOUND = 2e-3
-
-
 def test_bf16s_config2_full_size_sampled(rom):
     """Workload 2 at full size with the exact sliced-integer scheme: the
     FP32 bar (relative L2 <= 1e-4) over all 20000 steps."""
@@ -188,23 +204,12 @@ def test_bf16s_config2_full_size_sampled(rom):
     h = rom.Rom.from_problem(p)
     Z = np.zeros((1024, 1024))
     V, S, tr = run_tc(rom, h, p, Z, Z, 20000, "bf16s", r=10)
-    cols = np.array([0, 79, 80, 511, 1000, 1023])
+    # block edges of the planner's 80-column blocks, the ragged tail and a
+    # seeded draw; every column is held to the bar on its own
+    rng = np.random.default_rng(2)
+    cols = np.unique(np.concatenate([[0, 79, 80, 511, 959, 960, 1000, 1023],
+                                     rng.choice(1024, 8, replace=False)]))
     Vo, So, tro = oracle.problem_forward(p, nsteps=20000, r=10, columns=cols)
-    errs = (rel(V[:, cols], Vo), rel(S[:, cols], So), rel(tr[:, :, cols], tro))
+    errs = (colmax_rel(V[:, cols], Vo), colmax_rel(S[:, cols], So), colmax_rel(tr[:, :, cols], tro))
     assert max(errs) <= 1e-4, errs
-    assert np.all(np.isfinite(V))
-
-
-def test_tc_config2_full_size_sampled(rom):
-    """Workload 2 at full size (K = 1024, M = 1024, 20000 steps, R = 64, r = 10)
-    with TF32x3 in the planner's launch configuration; the oracle recomputes a
-    sample of columns."""
-    p = inputs.config(2)
-    h = rom.Rom.from_problem(p)
-    Z = np.zeros((1024, 1024))
-    V, S, tr = run_tc(rom, h, p, Z, Z, 20000, "tf32x3", r=10)
-    cols = np.array([0, 63, 64, 511, 1000, 1023])
-    Vo, So, tro = oracle.problem_forward(p, nsteps=20000, r=10, columns=cols)
-    errs = (rel(V[:, cols], Vo), rel(S[:, cols], So), rel(tr[:, :, cols], tro))
-    assert max(errs) <= TC_FULL_HORIZON_BOUND, errs
     assert np.all(np.isfinite(V))

@@ -1,7 +1,8 @@
 """GPU parity of the reduced reference state (rom_set_reference; Eq. (rom_ode),
 Eq. (rom_ode_tensor)) on every path against the FP64 oracle run with the same
 term.  Tolerances: relative L2 (Eq. (errors), Sec. 4.4) of 1e-12 for FP64 and
-1e-4 for FP32 and the accepted tensor-core path."""
+1e-4 for FP32 and the tensor-core paths (TF32x3, which is reported rather than
+accepted over long horizons, on a short run)."""
 import numpy as np
 import pytest
 
@@ -11,7 +12,7 @@ from paper_2009_11742_gb300 import inputs
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-TOL = {"fp64": 1e-12, "fp32": 1e-4, "bf16s": 1e-4, "tf32x3": 1e-3}
+TOL = {"fp64": 1e-12, "fp32": 1e-4, "bf16s": 1e-4, "tf32x3": 1e-4}
 
 
 def rel(a, b):
@@ -64,7 +65,7 @@ def run(rom, h, p, V0, S0, N, prec, r=0):
     ("fp32", 3, 256, 256, 40, 300),     # dataflow kernel
     ("bf16s", 0, 1024, 1000, 100, 200),
     ("bf16s", 0, 384, 384, 40, 300),
-    ("tf32x3", 0, 512, 500, 70, 200),
+    ("tf32x3", 0, 512, 500, 70, 40),
 ])
 def test_reference_state_vs_oracle(rom, prec, kernel, Kv, Ks, M, N):
     p, Xv, Xs, V0, S0 = case(Kv, Ks, M, 6, seed=Kv + M)

@@ -47,6 +47,40 @@ def test_noalloc_matches_rom_create_twice(rom, Kv, Ks):
     h.close()
 
 
+def test_noalloc_allocates_nothing(rom):
+    """The point of the entry point: once the first call on the device has
+    looked up the fixed work array, a call leaves the device's free memory
+    and torch's allocator exactly as they were."""
+    Kv, Ks = 256, 200
+    p = inputs.make_problem(Kv, Ks, 1, 0, seed=11)
+    Avs = colmajor_device(p.Avs)
+    Asv = colmajor_device(p.Asv)
+    st, rho0 = rom.rom_spectral_radius_noalloc(Avs.data_ptr(), Asv.data_ptr(), Kv, Ks, None)
+    assert st == rom.ROM_OK
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    alloc0 = torch.cuda.memory_allocated()
+    st, rho1 = rom.rom_spectral_radius_noalloc(Avs.data_ptr(), Asv.data_ptr(), Kv, Ks, None)
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert st == rom.ROM_OK and rho1 == rho0
+    assert free1 == free0
+    assert torch.cuda.memory_allocated() == alloc0
+
+
+def test_noalloc_reports_no_convergence(rom):
+    """A product Avs Asv whose dominant eigenvalues are the complex pair +-2i
+    of a non-normal 2 x 2 matrix: the power iteration's estimates alternate
+    between two values and never settle, so the call says so instead of
+    returning the last estimate as a result."""
+    Avs = np.eye(2)
+    Asv = np.array([[0.0, -4.0], [1.0, 0.0]])
+    st, rho = rom.rom_spectral_radius_noalloc(colmajor_device(Avs).data_ptr(),
+                                              colmajor_device(Asv).data_ptr(), 2, 2, None)
+    assert st == rom.ROM_E_NOCONV
+    assert np.isfinite(rho)
+
+
 def test_noalloc_refuses_oversize_and_host_buffers(rom):
     x = torch.zeros(16, dtype=torch.float64, device="cuda")
     st, _ = rom.rom_spectral_radius_noalloc(x.data_ptr(), x.data_ptr(), 4097, 4, None)
