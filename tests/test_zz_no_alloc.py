@@ -73,10 +73,11 @@ def test_noalloc_reports_no_convergence(rom):
     of a non-normal 2 x 2 matrix: the power iteration's estimates alternate
     between two values and never settle, so the call says so instead of
     returning the last estimate as a result."""
-    Avs = np.eye(2)
-    Asv = np.array([[0.0, -4.0], [1.0, 0.0]])
-    st, rho = rom.rom_spectral_radius_noalloc(colmajor_device(Avs).data_ptr(),
-                                              colmajor_device(Asv).data_ptr(), 2, 2, None)
+    # keep both device copies alive for the call: a temporary's memory goes
+    # back to torch's cache at once and the second copy could reuse it
+    Avs = colmajor_device(np.eye(2))
+    Asv = colmajor_device(np.array([[0.0, -4.0], [1.0, 0.0]]))
+    st, rho = rom.rom_spectral_radius_noalloc(Avs.data_ptr(), Asv.data_ptr(), 2, 2, None)
     assert st == rom.ROM_E_NOCONV
     assert np.isfinite(rho)
 
