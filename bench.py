@@ -70,6 +70,19 @@ def peaks():
                 "sm_max_mhz": 2070.0}, "fallback"
 
 
+def measured_pipe_peaks(rom):
+    """The roofline denominators measured live on this device by the library's
+    microbenchmarks (rom_measure_peak): FP32 / FP64 FMA and TF32 / BF16 tensor
+    TFLOP/s, L2 read GB/s.  A kind that fails is left out."""
+    out = {}
+    for kind in ("fp32", "fp64", "tf32", "bf16", "l2"):
+        try:
+            out[kind] = rom.measure_peak(kind)[0]
+        except Exception as exc:  # a failed probe leaves that denominator to the nominal basis
+            out[kind + "_error"] = str(exc)
+    return out
+
+
 class ClockSampler:
     """nvidia-smi samples of SM clock and throttle reasons during a region."""
 
@@ -362,12 +375,18 @@ def main():
                    "tflops_useful": world * flops * args.steps / t_dev / 1e12, "clocks": clocks}
             if prec in TC_RATIO:
                 pk, pk_kind = peaks()
-                peak = pk.get("bf16_tflops", 1900.0) * TC_RATIO[prec]
+                mp = measured_pipe_peaks(rom)
                 ach = TC_PRODUCTS[prec] * 4.0 * K * K * M * N / (t_dev / args.steps) / 1e12
+                if prec == "tf32x3" and "tf32" in mp:
+                    # TF32 products against the TF32 pipe's own measured rate
+                    peak, basis = mp["tf32"], "tf32 tcgen05 microbenchmark (rom_measure_peak), this run"
+                else:
+                    peak = pk.get("bf16_tflops", 1900.0) * TC_RATIO[prec]
+                    basis = f"bf16 cuBLAS {pk_kind}" + (f" x {TC_RATIO[prec]:.3f}" if TC_RATIO[prec] != 1.0 else "")
                 out["roofline_tensor"] = {"bound": "tensor", "achieved": ach, "peak": peak,
                                           "unit": "TFLOP/s", "frac": ach / peak,
-                                          "basis": f"{TC_PRODUCTS[prec]} products x 4 K^2 M per step; "
-                                                   f"bf16 {pk_kind} x {TC_RATIO[prec]:.3f}"}
+                                          "basis": f"{TC_PRODUCTS[prec]} products x 4 K^2 M per step; {basis}",
+                                          "measured_pipe_peaks": mp}
             if not args.no_check and args.workload == 2:
                 import oracle
                 cols = np.array([0, 511, 1023])
@@ -454,19 +473,27 @@ def main():
     pk, pk_kind = peaks()
     sm_clock_max = float(pk.get("sm_max_mhz", 2070.0))
     nsm = torch.cuda.get_device_properties(dev).multi_processor_count
-    fp32_peak = nsm * FP32_LANES_PER_SM * 2 * sm_clock_max * 1e6 / 1e12  # TFLOP/s
+    fp32_nominal = nsm * FP32_LANES_PER_SM * 2 * sm_clock_max * 1e6 / 1e12  # TFLOP/s
+    mp = measured_pipe_peaks(rom)
     achieved = flops / (t_dev / args.steps) / 1e12
     plan = h.plan(M, "fp32")
     kname = ("rank2_split_kernel<8>" if plan["variant"] == 2
              else "rank2_simt_kernel<float,8,8,true>")
     traffic = profiled_traffic(kname, N) if (K, M, R, r) == (512, 256, 64, 10) else None
+    if "fp32" in mp:
+        fp32_peak = mp["fp32"]
+        basis = ("measured: FP32 FMA microbenchmark over all SMs (rom_measure_peak), this run; "
+                 f"nominal {nsm} SMs x {FP32_LANES_PER_SM} lanes x 2 x {sm_clock_max:.0f} MHz = "
+                 f"{fp32_nominal:.1f}")
+    else:
+        fp32_peak = fp32_nominal
+        basis = (f"{nsm} SMs x {FP32_LANES_PER_SM} FP32 FMA lanes x 2 x "
+                 f"{sm_clock_max:.0f} MHz (max SM clock, {pk_kind})")
     roof = {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
             "frac": achieved / fp32_peak, "traffic": traffic,
-            "kernel": kname, "plan": plan,
-            "peak_basis": f"{nsm} SMs x {FP32_LANES_PER_SM} FP32 FMA lanes x 2 x "
-                          f"{sm_clock_max:.0f} MHz (max SM clock, {pk_kind})"}
-    if clocks and clocks.get("sm_mhz"):
-        roof["frac_at_measured_clock"] = achieved / (fp32_peak * clocks["sm_mhz"] / sm_clock_max)
+            "kernel": kname, "plan": plan, "peak_basis": basis,
+            "peak_nominal": fp32_nominal, "frac_of_nominal": achieved / fp32_nominal,
+            "measured_pipe_peaks": mp}
 
     es = 4
     h2d = (2 * K * M + M) * es
@@ -491,7 +518,9 @@ def main():
                   # K = 512, L2-resident, so L2 rather than HBM is the ceiling)
                   "single_operator_gbs": r1_single * 8.0 * K * K / 1e9,
                   "ensemble_operator_gbs": r1_ens * 8.0 * K * K / 1e9,
-                  "hbm_gbs_measured": pk.get("hbm_gbs")},
+                  "hbm_gbs_measured": pk.get("hbm_gbs"),
+                  "l2_gbs_measured": mp.get("l2"),
+                  "ensemble_frac_of_l2": (r1_ens * 8.0 * K * K / 1e9 / mp["l2"]) if mp.get("l2") else None},
         "rel_err_vs_oracle": err,
     }
     print(json.dumps(line), flush=True)
@@ -578,7 +607,8 @@ def bench_uq(args, torch, dev, inputs, rom):
 
 def bench_fp64(args, torch, dev, inputs, rom):
     """Workload 0: the FP64 check path (K = 128, M = 16, 1000 steps, no traces):
-    achieved FP64 rate against the 1.25 TFLOP/s nominal FP64 rate, the FP64
+    achieved FP64 rate against the FP64 rate measured by the library's
+    microbenchmark (and the 1.25 TFLOP/s nominal), the FP64
     rank-1 paths on the same operator, and the error against the FP64
     oracle."""
     p = inputs.config(0)
@@ -622,6 +652,7 @@ def bench_fp64(args, torch, dev, inputs, rom):
     e1.record(stream)
     torch.cuda.synchronize()
     r1_ens = M * N / (e0.elapsed_time(e1) * 1e-3)
+    mp = measured_pipe_peaks(rom)
     import oracle
     Vo, So, _ = oracle.problem_forward(p, nsteps=N, r=0)
     Vg, Sg = V.cpu().numpy(), S.cpu().numpy()
@@ -630,6 +661,8 @@ def bench_fp64(args, torch, dev, inputs, rom):
                       "value": M * N / t, "unit": "sample-steps/s", "ms_per_step": 1e3 * t,
                       "us_per_leapfrog_step": 1e6 * t / N,
                       "gflops_fp64": flops / t / 1e9, "frac_of_fp64_nominal_1250_gflops": flops / t / 1.25e12,
+                      "fp64_peak_measured_tflops": mp.get("fp64"),
+                      "frac_of_fp64_measured": (flops / t / 1e12 / mp["fp64"]) if mp.get("fp64") else None,
                       "bound": "FP64 units and cluster barriers (1 MFLOP per leapfrog step)",
                       "plan": h.plan(M, "fp64"),
                       "rank1_fp64": {"single_sample_steps_s": r1_single, "ensemble_sample_steps_s": r1_ens,

@@ -441,6 +441,28 @@ rom_status rom_rel_l2(const void* x, int x_dtype, const void* ref, int ref_dtype
 rom_status rom_spectral_radius_noalloc(const double* Avs, const double* Asv, int Kv, int Ks,
                                        double* rho, void* stream);
 
+/*
+ * rom_measure_peak -- measure, on the current device, a denominator of the
+ * roofline fractions this library reports (the paper has no counterpart: it
+ * measures CPU runs only).  Each kind is one throughput microbenchmark over
+ * every SM, run once untimed and once timed with CUDA events on `stream`:
+ *   ROM_PEAK_FP32  FP32 FMA pipe: 8 independent FMA chains per thread, 4
+ *                  blocks of 512 threads per SM; *value in TFLOP/s (2 per FMA);
+ *   ROM_PEAK_FP64  the same in FP64; TFLOP/s;
+ *   ROM_PEAK_TF32  tcgen05.mma kind::tf32, M = 128, N = 256, K = 8, 100000
+ *                  back-to-back MMAs per SM from resident shared-memory tiles
+ *                  into one tensor-memory accumulator; TFLOP/s;
+ *   ROM_PEAK_BF16  the same with kind::f16 BF16 operands, K = 16; TFLOP/s;
+ *   ROM_PEAK_L2    16 passes of 16-byte L2-cached loads over a 32 MB
+ *                  (L2-resident) buffer; GB/s.
+ * *ms (may be NULL) receives the timed launch's duration.  Synchronous.
+ * Allocates a few MB of scratch (32 MB for ROM_PEAK_L2) for the call.
+ * Errors: ROM_E_INVAL (kind), ROM_E_TIMEOUT (an MMA completion wait ran past
+ * about 2 s), ROM_E_CUDA / ROM_E_NOMEM.
+ */
+enum { ROM_PEAK_FP32 = 0, ROM_PEAK_FP64 = 1, ROM_PEAK_TF32 = 2, ROM_PEAK_BF16 = 3, ROM_PEAK_L2 = 4 };
+rom_status rom_measure_peak(int kind, double* value, double* ms, void* stream);
+
 /* Human-readable name of a status code (static storage). */
 const char* rom_status_string(rom_status s);
 

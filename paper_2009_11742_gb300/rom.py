@@ -39,6 +39,7 @@ EXPORTED = ["rom_create", "rom_destroy", "rom_spectral_radius", "rom_sync_status
             "rom_debug_inject_stall", "rom_run_rank2", "rom_run_rank2_ex", "rom_run_rank1",
             "rom_run_rank1_ensemble", "rom_run_batched", "rom_run_rank3", "rom_adjoint",
             "rom_adjoint_workspace_size", "rom_rel_l2", "rom_spectral_radius_noalloc",
+            "rom_measure_peak",
             "rom_trace_stats", "rom_fom_create", "rom_fom_destroy", "rom_fom_dims", "rom_fom_run",
             "rom_fom_set_passes",
             "rom_status_string", "rom_last_error", "rom_version"]
@@ -88,6 +89,7 @@ def _signatures(lib):
         "rom_adjoint_workspace_size": (ctypes.c_size_t, [_vp, _i, _i, _i, _i]),
         "rom_rel_l2": (_i, [_vp, _i, _vp, _i, ctypes.c_size_t, ctypes.POINTER(_d), _vp]),
         "rom_spectral_radius_noalloc": (_i, [_vp, _vp, _i, _i, ctypes.POINTER(_d), _vp]),
+        "rom_measure_peak": (_i, [_i, ctypes.POINTER(_d), ctypes.POINTER(_d), _vp]),
         "rom_trace_stats": (_i, [_vp, _i, _i, _i, ctypes.POINTER(_d), _i, _vp, _vp, _vp]),
         "rom_fom_create": (_i, [_i, _i, _d, _d, _d, _d, _d, ctypes.POINTER(_vp)]),
         "rom_fom_destroy": (_i, [_vp]),
@@ -341,6 +343,27 @@ def rom_spectral_radius_noalloc(Avs, Asv, Kv, Ks, stream=None):
     out = _d(0.0)
     st = load().rom_spectral_radius_noalloc(Avs, Asv, Kv, Ks, ctypes.byref(out), stream)
     return st, out.value
+
+
+ROM_PEAK_FP32, ROM_PEAK_FP64, ROM_PEAK_TF32, ROM_PEAK_BF16, ROM_PEAK_L2 = range(5)
+PEAK_KINDS = {"fp32": ROM_PEAK_FP32, "fp64": ROM_PEAK_FP64, "tf32": ROM_PEAK_TF32,
+              "bf16": ROM_PEAK_BF16, "l2": ROM_PEAK_L2}
+
+
+def rom_measure_peak(kind, stream=None):
+    """Measured peak of one pipe (TFLOP/s) or of L2 reads (GB/s) on the
+    current device.  Returns (status, value, ms)."""
+    v, ms = _d(0.0), _d(0.0)
+    st = load().rom_measure_peak(int(kind), ctypes.byref(v), ctypes.byref(ms), stream)
+    return st, v.value, ms.value
+
+
+def measure_peak(kind):
+    """rom_measure_peak by name ("fp32", "fp64", "tf32", "bf16", "l2");
+    raises RomError on failure."""
+    st, v, ms = rom_measure_peak(PEAK_KINDS[kind])
+    _chk(st, "rom_measure_peak")
+    return v, ms
 
 
 # ------------------------------------------------------------ tensor glue --
