@@ -453,7 +453,7 @@ rom_status rom_spectral_radius_noalloc(const double* Avs, const double* Asv, int
  *                  back-to-back MMAs per SM from resident shared-memory tiles
  *                  into one tensor-memory accumulator; TFLOP/s;
  *   ROM_PEAK_BF16  the same with kind::f16 BF16 operands, K = 16; TFLOP/s;
- *   ROM_PEAK_L2    16 passes of 16-byte L2-cached loads over a 32 MB
+ *   ROM_PEAK_L2    512 passes of 16-byte L2-cached loads over a 32 MB
  *                  (L2-resident) buffer; GB/s.
  * *ms (may be NULL) receives the timed launch's duration.  Synchronous.
  * Allocates a few MB of scratch (32 MB for ROM_PEAK_L2) for the call.

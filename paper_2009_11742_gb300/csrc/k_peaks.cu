@@ -166,7 +166,7 @@ extern "C" rom_status rom_measure_peak(int kind, double* value, double* ms_out, 
                 break;
             }
             case ROM_PEAK_L2: {
-                const int passes = 16;
+                const int passes = 512;  // about 1 ms at L2 rates
                 l2_read_kernel<<<nsm * 4, kL2Threads, 0, st>>>(
                     static_cast<const float4*>(scratch), l2_bytes / 16, passes,
                     reinterpret_cast<float*>(static_cast<unsigned char*>(scratch) + l2_bytes));
