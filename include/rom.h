@@ -144,11 +144,44 @@ rom_status rom_set_kernel(rom_t h, int kernel);
 
 /* The launch plan the handle would use for M realizations at precision prec
  * (ROM_FP32 or ROM_FP64): kernel variant (1 one-block, 2 two-block, 3
- * dataflow), cluster size, columns per column block and number of clusters
- * (outputs may be NULL).  ROM_E_UNSUPPORTED for another precision or if no
- * kernel fits. */
+ * dataflow, 4 two-block with the streaming companion of rom_set_companion on
+ * the last columns), cluster size, columns per column block and number of
+ * clusters of the main kernel (outputs may be NULL).  ROM_E_UNSUPPORTED for
+ * another precision or if no kernel fits. */
 rom_status rom_get_plan(rom_t h, int prec, int M, int* variant, int* cluster_size,
                         int* cols_per_block, int* nclusters);
+
+/*
+ * rom_set_companion -- the streaming companion of the FP32 two-block kernel.
+ * The two-block kernel keeps both operators in the registers of clusters of
+ * Kp/32 CTAs (16 at K = 512); clusters that large only fit where a GPU
+ * processing cluster has that many free SMs, and the rest of the SMs stay
+ * idle.  The companion runs beside it on those SMs as a second kernel on a
+ * private stream (forked from and joined back to the caller's stream) and
+ * integrates the LAST columns of the run with the same leapfrog: clusters of
+ * 2 or 4 CTAs, each owning Kp/size rows of V and S for up to 4 columns,
+ * stream their operator rows from L2 every half-step.  Kp <= 512; the run
+ * must carry no reduced reference state (otherwise the two-block kernel
+ * runs alone).  Results agree with the two-block kernel's to FP32 rounding.
+ *   cluster_size 0  (default) the planner decides from a step-time model:
+ *                   when the two-block kernel already uses every cluster
+ *                   that fits, it narrows the column blocks and hands the
+ *                   freed columns to the companion if that is predicted to
+ *                   be at least 5 % faster;
+ *   cluster_size -1 never;
+ *   cluster_size 2 or 4: always, with `columns` (>= 1) columns on the
+ *                   companion (all of them when columns >= M).
+ * Applies while the kernel choice is ROM_KERNEL_AUTO.  Clears the plans
+ * rom_autotune kept.  If the run is captured in a CUDA graph, the two
+ * kernels become parallel nodes whose launch order the graph does not fix,
+ * so the large clusters may no longer be placed first.  ROM_E_INVAL for
+ * another cluster size or columns < 1 with a pinned size.
+ */
+rom_status rom_set_companion(rom_t h, int cluster_size, int columns);
+
+/* The companion part of the FP32 plan for M realizations: its cluster size,
+ * number of clusters and columns (all 0 when the plan has none). */
+rom_status rom_get_companion(rom_t h, int M, int* cluster_size, int* nclusters, int* columns);
 
 /*
  * rom_autotune -- measure instead of model: time every candidate launch plan
@@ -160,7 +193,10 @@ rom_status rom_get_plan(rom_t h, int prec, int M, int* variant, int* cluster_siz
  * (rom_set_tc_columns) are automatic.  Candidates:
  *   ROM_FP32  the two-block and the one-block kernels, each with the cluster
  *             count capped at the co-resident maximum, half and a quarter of
- *             it (wider column blocks on fewer clusters);
+ *             it (wider column blocks on fewer clusters); and, when the
+ *             two-block kernel fills every cluster that fits, the same with
+ *             4, 8 or 12 fewer columns per block and the freed columns on the
+ *             streaming companion (rom_set_companion) in clusters of 2 or 4;
  *   ROM_FP64  the one-block kernel;
  *   tensor-core precisions: every column-block width the precision provides.
  * Every candidate computes the same leapfrog; the FP32 kernels differ only in

@@ -19,7 +19,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "librom.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["rom_api.cu", "k_rank2_f32.cu", "k_rank2_f64.cu", "k_rank2_split.cu", "k_rank2_tc.cu", "k_adjoint.cu", "k_misc.cu",
+SOURCES = ["rom_api.cu", "k_rank2_f32.cu", "k_rank2_f64.cu", "k_rank2_split.cu", "k_rank2_stream.cu", "k_rank2_tc.cu", "k_adjoint.cu", "k_misc.cu",
            "rom_noalloc.cu", "k_stats.cu", "k_fom.cu", "k_peaks.cu"]
 
 

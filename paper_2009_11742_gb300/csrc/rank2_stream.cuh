@@ -1,0 +1,359 @@
+// Streaming companion kernel of the two-block FP32 split kernel.
+//
+// The split kernel (rank2_split.cuh) keeps both K x K operators in the
+// registers of a 2K/32-CTA cluster (16 CTAs at K = 512).  Clusters that large
+// fit only where a GPU processing cluster has that many free SMs, so some SMs
+// stay idle.  This kernel runs beside it on those SMs and advances a few of
+// the M realizations (columns are independent, Sec. 2.4) with the same
+// velocity-first leapfrog (Sec. 3.1):
+//
+//   V += dt (Avs S + g f_n^T),   S += dt Asv V   (the new V).
+//
+// A cluster of CSZ (2 or 4) CTAs owns up to kStrCols columns; CTA c owns rows
+// [c Kp / CSZ, (c + 1) Kp / CSZ) of V and of S and keeps the full V and S of
+// its columns in shared memory.  The operators do not fit on so few SMs, so
+// every half-step streams the CTA's rows of Avs (or Asv) from L2 with bulk
+// asynchronous copies of 16-row slabs into a ring of stages; the copies for
+// the next half-step start before the current one ends, since the operator
+// does not depend on the state.  Each of the 8 warps takes two rows of a
+// slab: lane l holds the operand at k = 64 i + 2 l + {0, 1} in registers and
+// forms partial dot products for both rows and every column, and a
+// butterfly reduce-scatter over the 32 lanes leaves each (row, column) sum in
+// four lanes for the fused epilogue (forcing g f^T, Kahan-compensated FP32
+// update).  After a half-step each CTA copies its new rows into its peers'
+// copies (distributed shared memory) and one cluster barrier publishes them.
+// Receiver traces y = C V (Sec. 4.5.2) are taken after the velocity half.
+// Every wait is bounded; a wait that runs out records ROM_E_TIMEOUT and the
+// cluster leaves together after draining its copies in flight.
+#pragma once
+
+#include <cooperative_groups.h>
+#include <cuda_runtime.h>
+
+#include "dev_common.cuh"
+#include "rank2_simt.cuh"
+#include "rom_internal.h"
+#include "tc_common.cuh"
+
+namespace romk {
+
+constexpr int kStrWarps = 8;                    // warps; each takes 2 rows of a slab
+constexpr int kStrThreads = kStrWarps * 32;
+constexpr int kStrRows = 2 * kStrWarps;         // operator rows per stage (one slab)
+constexpr int kStrCols = 4;                     // columns per cluster (at most)
+constexpr int kStrStages = 4;                   // slabs in flight
+
+struct StreamSmem {
+    size_t ring, Vf, Sf, cV, cS, f, Tpre, g, bar, flags, total;
+};
+
+// Shared-memory layout for Kp padded rows and a CSZ-CTA cluster.
+__host__ __device__ inline StreamSmem stream_smem_layout(int Kp, int csz) {
+    StreamSmem s{};
+    const size_t nr = (size_t)Kp / csz;
+    size_t o = 0;
+    s.ring = o;  o += (size_t)kStrStages * kStrRows * Kp * sizeof(float);
+    s.Vf = o;    o += align16((size_t)kStrCols * Kp * sizeof(float));
+    s.Sf = o;    o += align16((size_t)kStrCols * Kp * sizeof(float));
+    s.cV = o;    o += align16((size_t)kStrCols * nr * sizeof(float));
+    s.cS = o;    o += align16((size_t)kStrCols * nr * sizeof(float));
+    s.f = o;     o += align16((size_t)kStrCols * sizeof(float));
+    s.Tpre = o;  o += align16((size_t)kStrCols * 2 * sizeof(double));
+    s.g = o;     o += align16(nr * sizeof(float));
+    s.bar = o;   o += align16((size_t)2 * kStrStages * sizeof(uint64_t));
+    s.flags = o; o += 64;
+    s.total = o;
+    return s;
+}
+
+// Butterfly reduce-scatter of NV partial sums over the 32 lanes of a warp
+// (fixed pairing, so the result does not depend on timing).  Afterwards the
+// lane holds the full sum of value index `vi`; lanes that differ only in the
+// low 5 - log2(NV) bits hold the same value.
+template <int NV>
+__device__ __forceinline__ float reduce_scatter32(float (&v)[NV], int lane, int& vi) {
+    static_assert(NV >= 1 && NV <= 32 && (NV & (NV - 1)) == 0, "NV must be a power of 2 <= 32");
+    int base = 0;
+#pragma unroll
+    for (int s = 0; s < 5; ++s) {
+        const int o = 16 >> s;
+        const int n = NV >> s;
+        if (n > 1) {
+            const int half = n / 2;
+            const bool up = (lane & o) != 0;
+#pragma unroll
+            for (int k = 0; k < half; ++k) {
+                const float send = up ? v[k] : v[k + half];
+                const float keep = up ? v[k + half] : v[k];
+                v[k] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+            }
+            base += up ? half : 0;
+        } else {
+            v[0] += __shfl_xor_sync(0xffffffffu, v[0], o);
+        }
+    }
+    vi = base;
+    return v[0];
+}
+
+// KI = Kp / 64 (Kp <= 512); CSZ CTAs per cluster.
+template <int KI, int CSZ>
+__global__ void __launch_bounds__(kStrThreads, 1) rank2_stream_kernel(const Rank2Args a) {
+    constexpr int Kp = 64 * KI;
+    constexpr int NR = Kp / CSZ;              // rows owned per CTA
+    constexpr int NCH = NR / kStrRows;        // slabs per half-step
+    static_assert(NR % kStrRows == 0, "owned rows must be whole slabs");
+    constexpr uint32_t kSlabBytes = (uint32_t)kStrRows * Kp * sizeof(float);
+    cg::cluster_group cluster = cg::this_cluster();
+    const int crank = (int)cluster.block_rank();
+    const int clu = blockIdx.x / CSZ;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int r0 = crank * NR;
+    const int col0 = a.col_base + clu * a.Wv;
+    const int ncol = min(a.Wv, a.M - clu * a.Wv);
+    const float dt = (float)a.dt;
+    const long long limit = a.spin_limit;
+
+    extern __shared__ __align__(16) unsigned char smem[];
+    const StreamSmem L = stream_smem_layout(Kp, CSZ);
+    float* ring = reinterpret_cast<float*>(smem + L.ring);   // [stages][16][Kp]
+    float* Vf = reinterpret_cast<float*>(smem + L.Vf);       // [4][Kp] full V of the columns
+    float* Sf = reinterpret_cast<float*>(smem + L.Sf);       // [4][Kp] full S
+    float* cV = reinterpret_cast<float*>(smem + L.cV);       // [4][NR] Kahan carries, own rows
+    float* cS = reinterpret_cast<float*>(smem + L.cS);
+    float* fcol = reinterpret_cast<float*>(smem + L.f);      // [4] forcing of the current step
+    double* Tpre = reinterpret_cast<double*>(smem + L.Tpre); // [4][-1.5 T, pi / T]
+    float* gown = reinterpret_cast<float*>(smem + L.g);      // [NR] source rows
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem + L.bar);
+    uint64_t* empty = full + kStrStages;
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + L.flags);
+    volatile int* abort_all = abort_flag + 1;
+    // the flag as published at a half-step's barrier, by half-step parity: a
+    // peer reads slot p after the barrier, and this CTA writes slot p again
+    // only after the next barrier, which the reader must reach first
+    volatile int* abort_pub = abort_flag + 2;
+    long long* landed = reinterpret_cast<long long*>(smem + L.flags + 16);  // slabs warp 0 saw arrive
+
+    const float* Vin = static_cast<const float*>(a.V);
+    const float* Sin = static_cast<const float*>(a.S);
+    const float* cVin = static_cast<const float*>(a.compV);
+    const float* cSin = static_cast<const float*>(a.compS);
+    if (tid == 0) {
+        *abort_flag = 0;
+        abort_pub[0] = 0;
+        abort_pub[1] = 0;
+        *abort_all = 0;
+        *landed = 0;
+        for (int s = 0; s < kStrStages; ++s) {
+            mbarrier_init(&full[s], 1);
+            mbarrier_init(&empty[s], kStrWarps);
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    for (int idx = tid; idx < kStrCols * Kp; idx += kStrThreads) {
+        const int c = idx / Kp, k = idx % Kp;
+        const bool okc = c < ncol;
+        Vf[idx] = (okc && k < a.Kv) ? Vin[(size_t)(col0 + c) * a.Kv + k] : 0.f;
+        Sf[idx] = (okc && k < a.Ks) ? Sin[(size_t)(col0 + c) * a.Ks + k] : 0.f;
+    }
+    for (int idx = tid; idx < kStrCols * NR; idx += kStrThreads) {
+        const int c = idx / NR, rl = idx % NR, row = r0 + rl;
+        const bool okc = c < ncol;
+        cV[idx] = (okc && cVin && row < a.Kv) ? cVin[(size_t)(col0 + c) * a.Kv + row] : 0.f;
+        cS[idx] = (okc && cSin && row < a.Ks) ? cSin[(size_t)(col0 + c) * a.Ks + row] : 0.f;
+    }
+    for (int rl = tid; rl < NR; rl += kStrThreads) gown[rl] = static_cast<const float*>(a.g_p)[r0 + rl];
+    if (tid < kStrCols) {
+        const float T = (a.Tper && tid < ncol) ? static_cast<const float*>(a.Tper)[col0 + tid] : 1.f;
+        Tpre[2 * tid] = -1.5 * (double)T;
+        Tpre[2 * tid + 1] = 3.14159265358979323846 / (double)T;
+        float f = 0.f;
+        if (tid < ncol) {
+            if (a.ftab) f = static_cast<const float*>(a.ftab)[col0 + tid];
+            else if (a.Tper) f = wavelet_eval_pre(a.wavelet, (long long)a.n0, a.dt, Tpre[2 * tid], Tpre[2 * tid + 1]);
+        }
+        fcol[tid] = f;
+    }
+    __syncthreads();
+    // every CTA is initialised before any peer copies rows into it
+    cluster.sync();
+
+    const int N = a.nsteps;
+    const long long total = (long long)N * 2 * NCH;   // slabs of the whole run
+    const float* Avs = static_cast<const float*>(a.Avs_rm);
+    const float* Asv = static_cast<const float*>(a.Asv_rm);
+    long long issued = 0;                             // slabs issued (thread 0 only)
+    // slab g: half (g / NCH) & 1, rows r0 + 16 (g % NCH) of that half's operator
+    auto issue_upto = [&](long long upto) {
+        while (issued < upto && issued < total && !*abort_flag) {
+            const int s = (int)(issued % kStrStages);
+            const uint32_t use = (uint32_t)(issued / kStrStages);
+            if (use > 0 && !mbarrier_wait(&empty[s], (use - 1) & 1, limit, abort_flag)) break;
+            const int hh = (int)((issued / NCH) & 1);
+            const int ch = (int)(issued % NCH);
+            const float* src = (hh ? Asv : Avs) + (size_t)(r0 + ch * kStrRows) * Kp;
+            mbarrier_arrive_expect_tx(&full[s], kSlabBytes);
+            bulk_g2s(ring + (size_t)s * kStrRows * Kp, src, kSlabBytes, &full[s]);
+            ++issued;
+        }
+    };
+    if (tid == 0) issue_upto(kStrStages - 1);
+
+    float* traces = static_cast<float*>(a.traces);
+    const float* Cp = static_cast<const float*>(a.C_p);
+    const int Rc = (a.R + CSZ - 1) / CSZ;             // receivers per CTA
+    long long gidx = 0;                               // slab being consumed
+    for (int n = 0; n < N; ++n) {
+#pragma unroll 1
+        for (int h = 0; h < 2; ++h) {
+            const float* X = h ? Vf : Sf;             // operand of this half
+            float* Y = h ? Sf : Vf;                   // state updated in its own rows
+            float* cY = h ? cS : cV;
+            const int Kown = h ? a.Ks : a.Kv;
+            float xs[kStrCols][2 * KI];
+#pragma unroll
+            for (int c = 0; c < kStrCols; ++c)
+#pragma unroll
+                for (int i = 0; i < KI; ++i) {
+                    const float2 v = *reinterpret_cast<const float2*>(X + c * Kp + 64 * i + 2 * lane);
+                    xs[c][2 * i] = v.x;
+                    xs[c][2 * i + 1] = v.y;
+                }
+#pragma unroll 1
+            for (int ch = 0; ch < NCH; ++ch, ++gidx) {
+                if (warp == 0) {
+                    if (lane == 0) issue_upto(gidx + kStrStages);
+                    __syncwarp();
+                }
+                const int s = (int)(gidx % kStrStages);
+                const uint32_t use = (uint32_t)(gidx / kStrStages);
+                int ok = 1;
+                if (lane == 0) ok = (*abort_flag == 0) && mbarrier_wait(&full[s], use & 1, limit, abort_flag);
+                ok = __shfl_sync(0xffffffffu, ok, 0);
+                if (!ok) continue;
+                if (warp == 0 && lane == 0) *landed = gidx + 1;
+                const float* slab = ring + (size_t)s * kStrRows * Kp;
+                float v[2 * kStrCols];
+#pragma unroll
+                for (int q = 0; q < 2 * kStrCols; ++q) v[q] = 0.f;
+#pragma unroll
+                for (int rr = 0; rr < 2; ++rr) {
+                    const float* arow = slab + (size_t)(2 * warp + rr) * Kp;
+#pragma unroll
+                    for (int i = 0; i < KI; ++i) {
+                        const float2 av = *reinterpret_cast<const float2*>(arow + 64 * i + 2 * lane);
+#pragma unroll
+                        for (int c = 0; c < kStrCols; ++c) {
+                            v[rr * kStrCols + c] = __fmaf_rn(av.x, xs[c][2 * i], v[rr * kStrCols + c]);
+                            v[rr * kStrCols + c] = __fmaf_rn(av.y, xs[c][2 * i + 1], v[rr * kStrCols + c]);
+                        }
+                    }
+                }
+                // the slab has been read: release its stage
+                __syncwarp();
+                if (lane == 0) mbarrier_arrive(&empty[s]);
+                int vi;
+                const float tot = reduce_scatter32<2 * kStrCols>(v, lane, vi);
+                if ((lane & 3) == 0) {
+                    const int rr = vi / kStrCols, c = vi % kStrCols;
+                    const int rl = ch * kStrRows + 2 * warp + rr;
+                    if (c < ncol && r0 + rl < Kown) {
+                        float inc = tot;
+                        if (h == 0) inc = __fmaf_rn(gown[rl], fcol[c], inc);
+                        inc = inc * dt;
+                        float* yp = Y + c * Kp + r0 + rl;
+                        *yp = kahan_add(*yp, inc, cY[c * NR + rl]);
+                    }
+                }
+            }
+            __syncthreads();
+            // copy the new own rows into every peer's full copy
+            for (int idx = tid; idx < kStrCols * (NR / 4); idx += kStrThreads) {
+                const int c = idx / (NR / 4), q4 = idx % (NR / 4);
+                float* src = Y + c * Kp + r0 + 4 * q4;
+                const float4 val = *reinterpret_cast<const float4*>(src);
+#pragma unroll
+                for (int p = 1; p < CSZ; ++p)
+                    *reinterpret_cast<float4*>(cluster.map_shared_rank(src, (crank + p) % CSZ)) = val;
+            }
+            // forcing of the next step (its first use is after the barrier below)
+            if (h == 1 && tid < ncol && n + 1 < N) {
+                float f = 0.f;
+                if (a.ftab) f = static_cast<const float*>(a.ftab)[(size_t)(n + 1) * a.Mtot + col0 + tid];
+                else if (a.Tper) f = wavelet_eval_pre(a.wavelet, (long long)a.n0 + n + 1, a.dt, Tpre[2 * tid], Tpre[2 * tid + 1]);
+                fcol[tid] = f;
+            }
+            if (tid == 0) abort_pub[h] = *abort_flag;
+            cluster.sync();
+            if (tid == 0) {
+                int any = 0;
+                for (int p = 0; p < CSZ; ++p)
+                    any |= *reinterpret_cast<volatile const int*>(
+                        cluster.map_shared_rank(const_cast<int*>(abort_pub + h), p));
+                *abort_all = any;
+            }
+            __syncthreads();
+            if (*abort_all) goto done;
+            // receiver traces of V^{n+1}: this CTA's receivers, all columns
+            if (h == 0 && traces && ((n + 1) % a.r) == 0) {
+                const int rec = (n + 1) / a.r - 1;
+                for (int jj = warp; jj < Rc; jj += kStrWarps) {
+                    const int jr = crank * Rc + jj;
+                    if (jr >= a.R) break;
+                    float t[kStrCols];
+#pragma unroll
+                    for (int c = 0; c < kStrCols; ++c) t[c] = 0.f;
+#pragma unroll
+                    for (int i = 0; i < KI; ++i) {
+                        const float2 cv = __ldg(reinterpret_cast<const float2*>(Cp + (size_t)jr * Kp + 64 * i + 2 * lane));
+#pragma unroll
+                        for (int c = 0; c < kStrCols; ++c) {
+                            const float2 x = *reinterpret_cast<const float2*>(Vf + c * Kp + 64 * i + 2 * lane);
+                            t[c] = __fmaf_rn(cv.x, x.x, t[c]);
+                            t[c] = __fmaf_rn(cv.y, x.y, t[c]);
+                        }
+                    }
+                    int ti;
+                    const float ts = reduce_scatter32<kStrCols>(t, lane, ti);
+                    if ((lane & 7) == 0 && ti < ncol) traces[((size_t)rec * a.Mtot + col0 + ti) * a.R + jr] = ts;
+                }
+            }
+        }
+    }
+done:
+    // no slab copy may still be landing when the CTA leaves
+    if (tid == 0) {
+        for (long long g = *landed; g < issued; ++g) {
+            const int s = (int)(g % kStrStages);
+            const long long t0 = clock64();
+            while (!mbarrier_try_wait(&full[s], (uint32_t)((g / kStrStages) & 1))) {
+                if (clock64() - t0 > limit) break;
+            }
+        }
+    }
+    const bool aborted = *abort_flag != 0 || *abort_all != 0;
+    if (aborted && tid == 0 && a.status) atomicCAS(a.status, 0, 5 /* ROM_E_TIMEOUT */);
+    // ---- write back the own rows and carries
+    int bad = 0;
+    for (int idx = tid; idx < ncol * NR; idx += kStrThreads) {
+        const int c = idx / NR, rl = idx % NR, row = r0 + rl;
+        if (row < a.Kv) {
+            const float x = Vf[c * Kp + row];
+            static_cast<float*>(a.V)[(size_t)(col0 + c) * a.Kv + row] = x;
+            if (a.compV) static_cast<float*>(a.compV)[(size_t)(col0 + c) * a.Kv + row] = cV[c * NR + rl];
+            bad |= !is_finite(x);
+        }
+        if (row < a.Ks) {
+            const float x = Sf[c * Kp + row];
+            static_cast<float*>(a.S)[(size_t)(col0 + c) * a.Ks + row] = x;
+            if (a.compS) static_cast<float*>(a.compS)[(size_t)(col0 + c) * a.Ks + row] = cS[c * NR + rl];
+            bad |= !is_finite(x);
+        }
+    }
+    bad = __syncthreads_or(bad);
+    if (bad && tid == 0 && a.status) atomicCAS(a.status, 0, 6 /* ROM_E_NONFINITE */);
+    // peers may still read this CTA's flags until every CTA is here
+    cluster.sync();
+}
+
+}  // namespace romk

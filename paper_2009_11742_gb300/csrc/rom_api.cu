@@ -104,6 +104,13 @@ struct rom_s {
     // the velocity (Kv x xref_M) and stress (Ks x xref_M) parts; xref_M = 0: none
     void* xref[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
     int xref_M = 0;
+    // streaming companion of the FP32 split kernel (rom_set_companion):
+    // comp_cs 0 = the planner's choice, -1 = off, 2 / 4 = pinned with
+    // comp_cols columns; a private stream and two events fork it off the
+    // caller's stream and join it back
+    int comp_cs = 0, comp_cols = 0;
+    cudaStream_t aux = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
 };
 
 namespace {
@@ -131,6 +138,9 @@ void free_handle(rom_s* h) {
         cudaFree(h->xref[t][0]);
         cudaFree(h->xref[t][1]);
     }
+    if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+    if (h->ev_join) cudaEventDestroy(h->ev_join);
+    if (h->aux) cudaStreamDestroy(h->aux);
     delete h;
 }
 
@@ -379,6 +389,16 @@ rom_status get_plan(rom_s* h, int prec, int M, bool rank1, Rank2Plan* plan) {
         ok = plan_rank2_dataflow_f32(h->Kp, M, h->R, plan);
     } else if (two_block) {
         ok = plan_rank2_split_f32(h->Kp, M, h->R, plan);
+        // the streaming companion on the SMs the split kernel's clusters
+        // leave idle (automatic kernel choice only)
+        if (ok && h->kernel_choice == ROM_KERNEL_AUTO) {
+            Rank2Plan cp;
+            if (h->comp_cs == 0 && plan_rank2_companion(h->Kp, M, h->R, &cp)) *plan = cp;
+            else if ((h->comp_cs == 2 || h->comp_cs == 4) &&
+                     plan_rank2_companion_pinned(h->Kp, M, h->R, h->comp_cs,
+                                                 h->comp_cols < M ? h->comp_cols : M, &cp))
+                *plan = cp;
+        }
     }
     if (!ok && h->kernel_choice != ROM_KERNEL_TWO_BLOCK && h->kernel_choice != ROM_KERNEL_DATAFLOW) {
         ok = prec == ROM_FP64 ? plan_rank2_simt_f64(h->Kp, M, h->R, rank1, plan)
@@ -515,6 +535,7 @@ rom_status run_rank2_tc_plan(rom_s* h, const RunBufs& b, int M, int nsteps, long
 
 rom_status launch_simt_with_plan(rom_s* h, const RunBufs& b, int M, int nsteps, long n0, int r,
                                  int prec, const Rank2Plan& plan, cudaStream_t st);
+rom_status launch_with_companion(rom_s* h, const Rank2Args& a, const Rank2Plan& plan, cudaStream_t st);
 
 rom_status run_rank2_device(rom_s* h, const RunBufs& b, int M, int nsteps, long n0, int r,
                             int prec, bool rank1, cudaStream_t st) {
@@ -566,11 +587,49 @@ rom_status launch_simt_with_plan(rom_s* h, const RunBufs& b, int M, int nsteps, 
         const rom_status xst = xref_for(h, t, M, &a.Xv, &a.Xs);
         if (xst != ROM_OK) return xst;
     }
+    if (prec != ROM_FP64 && plan.variant == 2 && plan.comp_cols > 0) {
+        if (a.Xv || a.Xs) {
+            // the companion does not carry the reference state: split kernel alone
+            Rank2Plan p2;
+            if (!plan_rank2_split_f32(h->Kp, M, h->R, &p2)) return ROM_E_UNSUPPORTED;
+            cudaError_t e = launch_rank2_split_f32(a, p2, st);
+            return e == cudaSuccess ? ROM_OK : cuda_fail(e, "rank2 launch");
+        }
+        return launch_with_companion(h, a, plan, st);
+    }
     cudaError_t e = prec == ROM_FP64   ? launch_rank2_simt_f64(a, plan, st)
                     : plan.variant >= 2 ? launch_rank2_split_f32(a, plan, st)
                                         : launch_rank2_simt_f32(a, plan, st);
     if (e != cudaSuccess) return cuda_fail(e, "rank2 launch");
     return ROM_OK;
+}
+
+// The split kernel on the caller's stream over columns [0, M - comp_cols) and
+// the streaming companion over the rest on the handle's private stream,
+// forked after the work already queued on the caller's stream and joined
+// back before anything queued after this call.  The split kernel is issued
+// first so that its large clusters are placed before the companion's.
+rom_status launch_with_companion(rom_s* h, const Rank2Args& a, const Rank2Plan& plan, cudaStream_t st) {
+    cudaError_t e = cudaSuccess;
+    if (!h->aux) {
+        e = cudaStreamCreateWithFlags(&h->aux, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming);
+        if (e != cudaSuccess) return cuda_fail(e, "companion stream");
+    }
+    const int mc = plan.comp_cols;
+    Rank2Args am = a;
+    am.M = a.M - mc;
+    Rank2Args ac = a;
+    ac.col_base = a.col_base + (a.M - mc);
+    ac.M = mc;
+    e = cudaEventRecord(h->ev_fork, st);
+    if (e == cudaSuccess && am.M > 0) e = launch_rank2_split_f32(am, plan, st);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(h->aux, h->ev_fork, 0);
+    if (e == cudaSuccess) e = launch_rank2_stream_f32(ac, plan.comp_cs, plan.comp_W, plan.comp_n, h->aux);
+    if (e == cudaSuccess) e = cudaEventRecord(h->ev_join, h->aux);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(st, h->ev_join, 0);
+    return e == cudaSuccess ? ROM_OK : cuda_fail(e, "rank2 launch with companion");
 }
 
 // Validates and runs a rank-2 style call; stages host buffers when V is host memory.
@@ -774,6 +833,28 @@ rom_status rom_autotune(rom_t h, int prec, int M, int probe_steps, double* best_
             if (plan_rank2_split_f32(h->Kp, M, h->R, &p, b)) { p.variant = 2; simt.push_back(p); }
             if (plan_rank2_simt_f32(h->Kp, M, h->R, false, &p, b)) { p.variant = 1; simt.push_back(p); }
         }
+        // the saturated split kernel with 4, 8 or 12 fewer columns per block,
+        // the freed columns on the streaming companion (clusters of 2 or 4)
+        Rank2Plan ps;
+        if (h->comp_cs >= 0 && plan_rank2_split_f32(h->Kp, M, h->R, &ps) &&
+            ps.nclusters >= ps.max_active_clusters) {
+            for (int csz : {2, 4}) {
+                for (int d = 1; d <= 3; ++d) {
+                    const int w = ps.Wa - 4 * d;
+                    const int cols = M - 2 * ps.nclusters * w;
+                    if (w < 4 || cols < 1) continue;
+                    Rank2Plan p = ps;
+                    Rank2Plan pc;
+                    if (!plan_rank2_companion_pinned(h->Kp, M, h->R, csz, cols, &pc)) continue;
+                    p.Wv = p.Wa = w;
+                    p.comp_cs = pc.comp_cs;
+                    p.comp_n = pc.comp_n;
+                    p.comp_W = pc.comp_W;
+                    p.comp_cols = pc.comp_cols;
+                    simt.push_back(p);
+                }
+            }
+        }
     }
     const size_t ncand = tc ? tcp.size() : simt.size();
     if (ncand == 0) {
@@ -847,6 +928,18 @@ rom_status rom_set_tc_columns(rom_t h, int cols) {
     return ROM_OK;
 }
 
+rom_status rom_set_companion(rom_t h, int cluster_size, int columns) {
+    if (!h || !(cluster_size == -1 || cluster_size == 0 || cluster_size == 2 || cluster_size == 4))
+        return ROM_E_INVAL;
+    if ((cluster_size == 2 || cluster_size == 4) && columns < 1) return ROM_E_INVAL;
+    std::lock_guard<std::mutex> lk(h->mu);
+    h->comp_cs = cluster_size;
+    h->comp_cols = cluster_size > 0 ? columns : 0;
+    h->plans.clear();
+    h->tuned.clear();
+    return ROM_OK;
+}
+
 rom_status rom_set_kernel(rom_t h, int kernel) {
     if (!h || kernel < ROM_KERNEL_AUTO || kernel > ROM_KERNEL_DATAFLOW) return ROM_E_INVAL;
     std::lock_guard<std::mutex> lk(h->mu);
@@ -861,10 +954,22 @@ rom_status rom_get_plan(rom_t h, int prec, int M, int* variant, int* cluster_siz
     Rank2Plan p;
     rom_status s = get_plan(h, prec, M, false, &p);
     if (s != ROM_OK) return s;
-    if (variant) *variant = p.variant;
+    if (variant) *variant = p.comp_cols > 0 ? 4 : p.variant;
     if (cluster_size) *cluster_size = p.cs;
     if (cols_per_block) *cols_per_block = p.Wv;
     if (nclusters) *nclusters = p.nclusters;
+    return ROM_OK;
+}
+
+rom_status rom_get_companion(rom_t h, int M, int* cluster_size, int* nclusters, int* columns) {
+    if (!h || M < 1) return ROM_E_INVAL;
+    Rank2Plan p;
+    rom_status s = get_plan(h, ROM_FP32, M, false, &p);
+    if (s != ROM_OK) return s;
+    const bool on = p.variant == 2 && p.comp_cols > 0;
+    if (cluster_size) *cluster_size = on ? p.comp_cs : 0;
+    if (nclusters) *nclusters = on ? p.comp_n : 0;
+    if (columns) *columns = on ? p.comp_cols : 0;
     return ROM_OK;
 }
 

@@ -76,6 +76,10 @@ struct Rank2Plan {
     int variant;   // 1: one-block, 2: two-block split-role, 3: two-block dataflow
     bool c_global; // one-block: the CTA's receiver rows are read from global memory (too many to stage)
     int nrt;       // one-block kernel: 32-row tiles per CTA (2 when Kp > 512)
+    // streaming companion (two-block variant only): the last comp_cols
+    // columns run on comp_n clusters of comp_cs CTAs, comp_W columns each,
+    // beside the split kernel; comp_cols = 0: none
+    int comp_cs = 0, comp_n = 0, comp_W = 0, comp_cols = 0;
 };
 
 // Host launchers (defined in the kernel translation units).  Return a CUDA
@@ -92,6 +96,17 @@ bool plan_rank2_simt_f64(int Kp, int M, int R, bool rank1, Rank2Plan* plan, int 
 bool plan_rank2_split_f32(int Kp, int M, int R, Rank2Plan* plan, int cluster_budget = 0);
 bool plan_rank2_dataflow_f32(int Kp, int M, int R, Rank2Plan* plan);
 cudaError_t launch_rank2_split_f32(const Rank2Args& a, const Rank2Plan& plan, cudaStream_t st);
+
+// Streaming companion of the split kernel (FP32, Kp <= 512, clusters of 2
+// or 4 CTAs, at most 4 columns per cluster; operators streamed from L2).
+bool stream_supported(int Kp, int csz);
+int stream_max_columns_per_cluster();
+cudaError_t launch_rank2_stream_f32(const Rank2Args& a, int csz, int cols_per_cluster, int nclusters,
+                                    cudaStream_t st);
+// Model-based split at saturation (false: no gain predicted) and the split
+// for a caller-pinned number of companion columns.
+bool plan_rank2_companion(int Kp, int M, int R, Rank2Plan* plan);
+bool plan_rank2_companion_pinned(int Kp, int M, int R, int csz, int cols, Rank2Plan* plan);
 
 // Tensor-core (tcgen05) rank-2 path for ROM_TF32X3 / ROM_BF16X3 / ROM_BF16 / ROM_BF16S.
 struct TcArgs {

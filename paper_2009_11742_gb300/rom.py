@@ -39,7 +39,7 @@ EXPORTED = ["rom_create", "rom_destroy", "rom_spectral_radius", "rom_sync_status
             "rom_debug_inject_stall", "rom_run_rank2", "rom_run_rank2_ex", "rom_run_rank1",
             "rom_run_rank1_ensemble", "rom_run_batched", "rom_run_rank3", "rom_adjoint",
             "rom_adjoint_workspace_size", "rom_rel_l2", "rom_spectral_radius_noalloc",
-            "rom_measure_peak",
+            "rom_measure_peak", "rom_set_companion", "rom_get_companion",
             "rom_trace_stats", "rom_fom_create", "rom_fom_destroy", "rom_fom_dims", "rom_fom_run",
             "rom_fom_set_passes",
             "rom_status_string", "rom_last_error", "rom_version"]
@@ -90,6 +90,8 @@ def _signatures(lib):
         "rom_rel_l2": (_i, [_vp, _i, _vp, _i, ctypes.c_size_t, ctypes.POINTER(_d), _vp]),
         "rom_spectral_radius_noalloc": (_i, [_vp, _vp, _i, _i, ctypes.POINTER(_d), _vp]),
         "rom_measure_peak": (_i, [_i, ctypes.POINTER(_d), ctypes.POINTER(_d), _vp]),
+        "rom_set_companion": (_i, [_vp, _i, _i]),
+        "rom_get_companion": (_i, [_vp, _i, ctypes.POINTER(_i), ctypes.POINTER(_i), ctypes.POINTER(_i)]),
         "rom_trace_stats": (_i, [_vp, _i, _i, _i, ctypes.POINTER(_d), _i, _vp, _vp, _vp]),
         "rom_fom_create": (_i, [_i, _i, _d, _d, _d, _d, _d, ctypes.POINTER(_vp)]),
         "rom_fom_destroy": (_i, [_vp]),
@@ -205,6 +207,16 @@ def rom_get_plan(h, prec, M):
     st = load().rom_get_plan(h, prec, M, ctypes.byref(v), ctypes.byref(cs), ctypes.byref(w),
                              ctypes.byref(nc))
     return st, v.value, cs.value, w.value, nc.value
+
+
+def rom_set_companion(h, cluster_size, columns):
+    return load().rom_set_companion(h, int(cluster_size), int(columns))
+
+
+def rom_get_companion(h, M):
+    cs, nc, cols = _i(0), _i(0), _i(0)
+    st = load().rom_get_companion(h, int(M), ctypes.byref(cs), ctypes.byref(nc), ctypes.byref(cols))
+    return st, cs.value, nc.value, cols.value
 
 
 def rom_status_string(s):
@@ -547,7 +559,18 @@ class Rom:
     def plan(self, M, prec="fp32"):
         st, v, cs, w, nc = rom_get_plan(self.h, PRECISIONS.get(prec, prec), int(M))
         _chk(st, "rom_get_plan")
-        return {"variant": v, "cluster_size": cs, "cols_per_block": w, "nclusters": nc}
+        out = {"variant": v, "cluster_size": cs, "cols_per_block": w, "nclusters": nc}
+        if v == 4:
+            st, ccs, cn, ccols = rom_get_companion(self.h, int(M))
+            _chk(st, "rom_get_companion")
+            out["companion"] = {"cluster_size": ccs, "nclusters": cn, "columns": ccols}
+        return out
+
+    def set_companion(self, cluster_size=0, columns=0):
+        """Streaming companion of the FP32 two-block kernel: 0 lets the
+        planner decide, -1 turns it off, 2 or 4 pins clusters of that size
+        with `columns` columns."""
+        _chk(rom_set_companion(self.h, cluster_size, columns), "rom_set_companion")
 
     def sync_status(self):
         st, dev = rom_sync_status(self.h)
