@@ -12,10 +12,11 @@
 // A cluster of CSZ (2 or 4) CTAs owns up to kStrCols columns; CTA c owns rows
 // [c Kp / CSZ, (c + 1) Kp / CSZ) of V and of S and keeps the full V and S of
 // its columns in shared memory.  The operators do not fit on so few SMs, so
-// every half-step streams the CTA's rows of Avs (or Asv) from L2 with bulk
-// asynchronous copies of 16-row slabs into a ring of stages; the copies for
-// the next half-step start before the current one ends, since the operator
-// does not depend on the state.  Each of the 8 warps takes two rows of a
+// every half-step streams the CTA's rows of Avs (or Asv) from L2 into a ring
+// of 16-row slabs: every thread issues 16-byte asynchronous copies (L2 only)
+// of its share of a slab, and the slab's mbarrier completes when all of
+// them have landed.  Copies run several slabs ahead, across half-steps too,
+// since the operator does not depend on the state.  Each of the 8 warps takes two rows of a
 // slab: lane l holds the operand at k = 64 i + 2 l + {0, 1} in registers and
 // forms partial dot products for both rows and every column, and a
 // butterfly reduce-scatter over the 32 lanes leaves each (row, column) sum in
@@ -41,7 +42,7 @@ constexpr int kStrWarps = 8;                    // warps; each takes 2 rows of a
 constexpr int kStrThreads = kStrWarps * 32;
 constexpr int kStrRows = 2 * kStrWarps;         // operator rows per stage (one slab)
 constexpr int kStrCols = 4;                     // columns per cluster (at most)
-constexpr int kStrStages = 4;                   // slabs in flight
+constexpr int kStrStages = 6;                   // slabs in the ring (five copies in flight)
 
 struct StreamSmem {
     size_t ring, Vf, Sf, cV, cS, f, Tpre, g, bar, flags, total;
@@ -132,7 +133,6 @@ __global__ void __launch_bounds__(kStrThreads, 1) rank2_stream_kernel(const Rank
     // peer reads slot p after the barrier, and this CTA writes slot p again
     // only after the next barrier, which the reader must reach first
     volatile int* abort_pub = abort_flag + 2;
-    long long* landed = reinterpret_cast<long long*>(smem + L.flags + 16);  // slabs warp 0 saw arrive
 
     const float* Vin = static_cast<const float*>(a.V);
     const float* Sin = static_cast<const float*>(a.S);
@@ -143,9 +143,8 @@ __global__ void __launch_bounds__(kStrThreads, 1) rank2_stream_kernel(const Rank
         abort_pub[0] = 0;
         abort_pub[1] = 0;
         *abort_all = 0;
-        *landed = 0;
         for (int s = 0; s < kStrStages; ++s) {
-            mbarrier_init(&full[s], 1);
+            mbarrier_init(&full[s], kStrThreads);
             mbarrier_init(&empty[s], kStrWarps);
         }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -182,22 +181,35 @@ __global__ void __launch_bounds__(kStrThreads, 1) rank2_stream_kernel(const Rank
     const long long total = (long long)N * 2 * NCH;   // slabs of the whole run
     const float* Avs = static_cast<const float*>(a.Avs_rm);
     const float* Asv = static_cast<const float*>(a.Asv_rm);
-    long long issued = 0;                             // slabs issued (thread 0 only)
-    // slab g: half (g / NCH) & 1, rows r0 + 16 (g % NCH) of that half's operator
+    // slab g: half (g / NCH) & 1, rows r0 + 16 (g % NCH) of that half's
+    // operator.  Every thread copies its 16-byte pieces t, t + 256, ... of the
+    // slab and arrives on the slot's mbarrier when they have landed; before
+    // reusing a slot, each warp waits until all warps released its last slab.
+    long long issued = 0;                             // slabs issued by this thread
     auto issue_upto = [&](long long upto) {
-        while (issued < upto && issued < total && !*abort_flag) {
+        while (issued < upto && issued < total) {
             const int s = (int)(issued % kStrStages);
             const uint32_t use = (uint32_t)(issued / kStrStages);
-            if (use > 0 && !mbarrier_wait(&empty[s], (use - 1) & 1, limit, abort_flag)) break;
+            int ok = 1;
+            if (use > 0 && lane == 0) ok = (*abort_flag == 0) && mbarrier_wait(&empty[s], (use - 1) & 1, limit, abort_flag);
+            ok = __shfl_sync(0xffffffffu, ok, 0);
+            if (!ok) break;
             const int hh = (int)((issued / NCH) & 1);
             const int ch = (int)(issued % NCH);
-            const float* src = (hh ? Asv : Avs) + (size_t)(r0 + ch * kStrRows) * Kp;
-            mbarrier_arrive_expect_tx(&full[s], kSlabBytes);
-            bulk_g2s(ring + (size_t)s * kStrRows * Kp, src, kSlabBytes, &full[s]);
+            const float4* src = reinterpret_cast<const float4*>((hh ? Asv : Avs) + (size_t)(r0 + ch * kStrRows) * Kp);
+            float4* dst = reinterpret_cast<float4*>(ring + (size_t)s * kStrRows * Kp);
+#pragma unroll
+            for (int q = 0; q < kSlabBytes / 16 / kStrThreads; ++q) {
+                const int e = tid + q * kStrThreads;
+                asm volatile("cp.async.cg.shared.global [%0], [%1], 16;"
+                             ::"r"(cvta_shared(dst + e)), "l"(src + e) : "memory");
+            }
+            asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];"
+                         ::"r"(cvta_shared(&full[s])) : "memory");
             ++issued;
         }
     };
-    if (tid == 0) issue_upto(kStrStages - 1);
+    issue_upto(kStrStages - 1);
 
     float* traces = static_cast<float*>(a.traces);
     const float* Cp = static_cast<const float*>(a.C_p);
@@ -221,17 +233,13 @@ __global__ void __launch_bounds__(kStrThreads, 1) rank2_stream_kernel(const Rank
                 }
 #pragma unroll 1
             for (int ch = 0; ch < NCH; ++ch, ++gidx) {
-                if (warp == 0) {
-                    if (lane == 0) issue_upto(gidx + kStrStages);
-                    __syncwarp();
-                }
+                issue_upto(gidx + kStrStages);
                 const int s = (int)(gidx % kStrStages);
                 const uint32_t use = (uint32_t)(gidx / kStrStages);
                 int ok = 1;
                 if (lane == 0) ok = (*abort_flag == 0) && mbarrier_wait(&full[s], use & 1, limit, abort_flag);
                 ok = __shfl_sync(0xffffffffu, ok, 0);
                 if (!ok) continue;
-                if (warp == 0 && lane == 0) *landed = gidx + 1;
                 const float* slab = ring + (size_t)s * kStrRows * Kp;
                 float v[2 * kStrCols];
 #pragma unroll
@@ -321,16 +329,9 @@ __global__ void __launch_bounds__(kStrThreads, 1) rank2_stream_kernel(const Rank
         }
     }
 done:
-    // no slab copy may still be landing when the CTA leaves
-    if (tid == 0) {
-        for (long long g = *landed; g < issued; ++g) {
-            const int s = (int)(g % kStrStages);
-            const long long t0 = clock64();
-            while (!mbarrier_try_wait(&full[s], (uint32_t)((g / kStrStages) & 1))) {
-                if (clock64() - t0 > limit) break;
-            }
-        }
-    }
+    // no slab copy may still be landing when the CTA leaves: each thread
+    // waits for its own copies
+    asm volatile("cp.async.wait_all;" ::: "memory");
     const bool aborted = *abort_flag != 0 || *abort_all != 0;
     if (aborted && tid == 0 && a.status) atomicCAS(a.status, 0, 5 /* ROM_E_TIMEOUT */);
     // ---- write back the own rows and carries
