@@ -16,11 +16,11 @@
 // of 16-row slabs: every thread issues 16-byte asynchronous copies (L2 only)
 // of its share of a slab, and the slab's mbarrier completes when all of
 // them have landed.  Copies run several slabs ahead, across half-steps too,
-// since the operator does not depend on the state.  Each of the 8 warps takes two rows of a
-// slab: lane l holds the operand at k = 64 i + 2 l + {0, 1} in registers and
-// forms partial dot products for both rows and every column, and a
+// since the operator does not depend on the state.  Each of the 16 warps
+// takes one row of a slab: lane l holds the operand at k = 64 i + 2 l +
+// {0, 1} in registers and forms partial dot products for every column, and a
 // butterfly reduce-scatter over the 32 lanes leaves each (row, column) sum in
-// four lanes for the fused epilogue (forcing g f^T, Kahan-compensated FP32
+// eight lanes for the fused epilogue (forcing g f^T, Kahan-compensated FP32
 // update).  After a half-step each CTA copies its new rows into its peers'
 // copies (distributed shared memory) and one cluster barrier publishes them.
 // Receiver traces y = C V (Sec. 4.5.2) are taken after the velocity half.
@@ -38,9 +38,10 @@
 
 namespace romk {
 
-constexpr int kStrWarps = 8;                    // warps; each takes 2 rows of a slab
+constexpr int kStrWarps = 16;                   // warps; each takes one row of a slab
 constexpr int kStrThreads = kStrWarps * 32;
-constexpr int kStrRows = 2 * kStrWarps;         // operator rows per stage (one slab)
+constexpr int kStrRows = 16;                    // operator rows per stage (one slab)
+constexpr int kStrRpw = kStrRows / kStrWarps;   // rows per warp and slab
 constexpr int kStrCols = 4;                     // columns per cluster (at most)
 constexpr int kStrStages = 6;                   // slabs in the ring (five copies in flight)
 
@@ -199,11 +200,9 @@ __global__ void __launch_bounds__(kStrThreads, 1) rank2_stream_kernel(const Rank
             const float4* src = reinterpret_cast<const float4*>((hh ? Asv : Avs) + (size_t)(r0 + ch * kStrRows) * Kp);
             float4* dst = reinterpret_cast<float4*>(ring + (size_t)s * kStrRows * Kp);
 #pragma unroll
-            for (int q = 0; q < kSlabBytes / 16 / kStrThreads; ++q) {
-                const int e = tid + q * kStrThreads;
+            for (int e = tid; e < (int)(kSlabBytes / 16); e += kStrThreads)
                 asm volatile("cp.async.cg.shared.global [%0], [%1], 16;"
                              ::"r"(cvta_shared(dst + e)), "l"(src + e) : "memory");
-            }
             asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];"
                          ::"r"(cvta_shared(&full[s])) : "memory");
             ++issued;
@@ -241,12 +240,12 @@ __global__ void __launch_bounds__(kStrThreads, 1) rank2_stream_kernel(const Rank
                 ok = __shfl_sync(0xffffffffu, ok, 0);
                 if (!ok) continue;
                 const float* slab = ring + (size_t)s * kStrRows * Kp;
-                float v[2 * kStrCols];
+                float v[kStrRpw * kStrCols];
 #pragma unroll
-                for (int q = 0; q < 2 * kStrCols; ++q) v[q] = 0.f;
+                for (int q = 0; q < kStrRpw * kStrCols; ++q) v[q] = 0.f;
 #pragma unroll
-                for (int rr = 0; rr < 2; ++rr) {
-                    const float* arow = slab + (size_t)(2 * warp + rr) * Kp;
+                for (int rr = 0; rr < kStrRpw; ++rr) {
+                    const float* arow = slab + (size_t)(kStrRpw * warp + rr) * Kp;
 #pragma unroll
                     for (int i = 0; i < KI; ++i) {
                         const float2 av = *reinterpret_cast<const float2*>(arow + 64 * i + 2 * lane);
@@ -261,10 +260,10 @@ __global__ void __launch_bounds__(kStrThreads, 1) rank2_stream_kernel(const Rank
                 __syncwarp();
                 if (lane == 0) mbarrier_arrive(&empty[s]);
                 int vi;
-                const float tot = reduce_scatter32<2 * kStrCols>(v, lane, vi);
-                if ((lane & 3) == 0) {
+                const float tot = reduce_scatter32<kStrRpw * kStrCols>(v, lane, vi);
+                if ((lane & (32 / (kStrRpw * kStrCols) - 1)) == 0) {
                     const int rr = vi / kStrCols, c = vi % kStrCols;
-                    const int rl = ch * kStrRows + 2 * warp + rr;
+                    const int rl = ch * kStrRows + kStrRpw * warp + rr;
                     if (c < ncol && r0 + rl < Kown) {
                         float inc = tot;
                         if (h == 0) inc = __fmaf_rn(gown[rl], fcol[c], inc);
