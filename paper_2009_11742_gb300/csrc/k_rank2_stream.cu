@@ -10,16 +10,25 @@
 
 namespace romk {
 
+// Instances whose owned rows (Kp / csz) are whole 64-row passes.
 static void* stream_kernel(int KI, int csz) {
-#define ROM_STR_CASE(k)                                                                       \
-    case k:                                                                                   \
-        return csz == 4 ? (void*)&rank2_stream_kernel<k, 4> : (void*)&rank2_stream_kernel<k, 2>;
-    switch (KI) {
-        ROM_STR_CASE(1) ROM_STR_CASE(2) ROM_STR_CASE(3) ROM_STR_CASE(4)
-        ROM_STR_CASE(5) ROM_STR_CASE(6) ROM_STR_CASE(7) ROM_STR_CASE(8)
-        default: return nullptr;
+    if (csz == 2) {
+        switch (KI) {
+            case 2: return (void*)&rank2_stream_kernel<2, 2>;
+            case 4: return (void*)&rank2_stream_kernel<4, 2>;
+            case 6: return (void*)&rank2_stream_kernel<6, 2>;
+            case 8: return (void*)&rank2_stream_kernel<8, 2>;
+            default: return nullptr;
+        }
     }
-#undef ROM_STR_CASE
+    if (csz == 4) {
+        switch (KI) {
+            case 4: return (void*)&rank2_stream_kernel<4, 4>;
+            case 8: return (void*)&rank2_stream_kernel<8, 4>;
+            default: return nullptr;
+        }
+    }
+    return nullptr;
 }
 
 bool stream_supported(int Kp, int csz) {

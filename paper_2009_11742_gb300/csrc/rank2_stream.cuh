@@ -9,23 +9,25 @@
 //
 //   V += dt (Avs S + g f_n^T),   S += dt Asv V   (the new V).
 //
-// A cluster of CSZ (2 or 4) CTAs owns up to kStrCols columns; CTA c owns rows
-// [c Kp / CSZ, (c + 1) Kp / CSZ) of V and of S and keeps the full V and S of
-// its columns in shared memory.  The operators do not fit on so few SMs, so
-// every half-step streams the CTA's rows of Avs (or Asv) from L2 into a ring
-// of 16-row slabs: every thread issues 16-byte asynchronous copies (L2 only)
-// of its share of a slab, and the slab's mbarrier completes when all of
-// them have landed.  Copies run several slabs ahead, across half-steps too,
-// since the operator does not depend on the state.  Each of the 16 warps
-// takes one row of a slab: lane l holds the operand at k = 64 i + 2 l +
-// {0, 1} in registers and forms partial dot products for every column, and a
-// butterfly reduce-scatter over the 32 lanes leaves each (row, column) sum in
-// eight lanes for the fused epilogue (forcing g f^T, Kahan-compensated FP32
-// update).  After a half-step each CTA copies its new rows into its peers'
-// copies (distributed shared memory) and one cluster barrier publishes them.
-// Receiver traces y = C V (Sec. 4.5.2) are taken after the velocity half.
-// Every wait is bounded; a wait that runs out records ROM_E_TIMEOUT and the
-// cluster leaves together after draining its copies in flight.
+// A cluster of CSZ (2 or 4) CTAs owns up to 4 columns (one column group);
+// CTA c owns rows [c Kp / CSZ, (c + 1) Kp / CSZ) of V and of S and keeps the
+// full V and S of its columns in shared memory.  The operators do not fit on
+// so few SMs, so every half-step streams the CTA's rows of Avs (or Asv) from
+// L2 into a ring of 64-row x 64-k stages: every thread issues 16-byte
+// asynchronous copies (L2 only) of its share of a stage, and the stage's
+// mbarrier completes when all of them have landed.  Copies run several
+// stages ahead, across half-steps too, since the operator does not depend on
+// the state.  The arithmetic is the split kernel's, in the same order:
+// thread (row quad q, k lane j) holds the operand at k = 64 i + 4 j + t in
+// registers, accumulates 4 rows x 4 columns with k ascending, and the same
+// 16-lane butterfly reduce-scatter and fused epilogue (forcing g f^T,
+// Kahan-compensated FP32 update) follow; receiver traces y = C V (Sec.
+// 4.5.2) use the split kernel's receiver slabs and warp tiles.  So every
+// column comes out bit for bit as the split kernel computes it.  After a
+// half-step each CTA copies its new rows into its peers' copies (distributed
+// shared memory) and one cluster barrier publishes them.  Every wait is
+// bounded; a wait that runs out records ROM_E_TIMEOUT and the cluster leaves
+// together after draining its copies in flight.
 #pragma once
 
 #include <cooperative_groups.h>
@@ -33,17 +35,19 @@
 
 #include "dev_common.cuh"
 #include "rank2_simt.cuh"
+#include "rank2_split.cuh"
 #include "rom_internal.h"
 #include "tc_common.cuh"
 
 namespace romk {
 
-constexpr int kStrWarps = 16;                   // warps; each takes one row of a slab
-constexpr int kStrThreads = kStrWarps * 32;
-constexpr int kStrRows = 16;                    // operator rows per stage (one slab)
-constexpr int kStrRpw = kStrRows / kStrWarps;   // rows per warp and slab
-constexpr int kStrCols = 4;                     // columns per cluster (at most)
-constexpr int kStrStages = 6;                   // slabs in the ring (five copies in flight)
+constexpr int kStrWarps = kSplitWarps;           // 8 warps, the split kernel's thread mapping
+constexpr int kStrThreads = kThreads;             // 256: thread (row quad q, k lane j)
+constexpr int kStrRows = kSplitRows;              // 64 rows per pass (16 row quads)
+constexpr int kStrKC = 64;                        // k extent of one stage
+constexpr int kStrCols = kSplitCB;                // 4 columns per cluster (one column group)
+constexpr int kStrStages = 8;                     // stages in the ring (16 KB each)
+constexpr int kStrStageFloats = kStrRows * kStrKC;
 
 struct StreamSmem {
     size_t ring, Vf, Sf, cV, cS, f, Tpre, g, bar, flags, total;
@@ -54,7 +58,7 @@ __host__ __device__ inline StreamSmem stream_smem_layout(int Kp, int csz) {
     StreamSmem s{};
     const size_t nr = (size_t)Kp / csz;
     size_t o = 0;
-    s.ring = o;  o += (size_t)kStrStages * kStrRows * Kp * sizeof(float);
+    s.ring = o;  o += (size_t)kStrStages * kStrStageFloats * sizeof(float);
     s.Vf = o;    o += align16((size_t)kStrCols * Kp * sizeof(float));
     s.Sf = o;    o += align16((size_t)kStrCols * Kp * sizeof(float));
     s.cV = o;    o += align16((size_t)kStrCols * nr * sizeof(float));
@@ -68,48 +72,23 @@ __host__ __device__ inline StreamSmem stream_smem_layout(int Kp, int csz) {
     return s;
 }
 
-// Butterfly reduce-scatter of NV partial sums over the 32 lanes of a warp
-// (fixed pairing, so the result does not depend on timing).  Afterwards the
-// lane holds the full sum of value index `vi`; lanes that differ only in the
-// low 5 - log2(NV) bits hold the same value.
-template <int NV>
-__device__ __forceinline__ float reduce_scatter32(float (&v)[NV], int lane, int& vi) {
-    static_assert(NV >= 1 && NV <= 32 && (NV & (NV - 1)) == 0, "NV must be a power of 2 <= 32");
-    int base = 0;
-#pragma unroll
-    for (int s = 0; s < 5; ++s) {
-        const int o = 16 >> s;
-        const int n = NV >> s;
-        if (n > 1) {
-            const int half = n / 2;
-            const bool up = (lane & o) != 0;
-#pragma unroll
-            for (int k = 0; k < half; ++k) {
-                const float send = up ? v[k] : v[k + half];
-                const float keep = up ? v[k + half] : v[k];
-                v[k] = keep + __shfl_xor_sync(0xffffffffu, send, o);
-            }
-            base += up ? half : 0;
-        } else {
-            v[0] += __shfl_xor_sync(0xffffffffu, v[0], o);
-        }
-    }
-    vi = base;
-    return v[0];
-}
-
-// KI = Kp / 64 (Kp <= 512); CSZ CTAs per cluster.
+// KI = Kp / 64 (Kp <= 512); CSZ CTAs per cluster; Kp / CSZ a multiple of 64.
 template <int KI, int CSZ>
 __global__ void __launch_bounds__(kStrThreads, 1) rank2_stream_kernel(const Rank2Args a) {
     constexpr int Kp = 64 * KI;
-    constexpr int NR = Kp / CSZ;              // rows owned per CTA
-    constexpr int NCH = NR / kStrRows;        // slabs per half-step
-    static_assert(NR % kStrRows == 0, "owned rows must be whole slabs");
-    constexpr uint32_t kSlabBytes = (uint32_t)kStrRows * Kp * sizeof(float);
+    constexpr int NR = Kp / CSZ;               // rows owned per CTA
+    constexpr int NP = NR / kStrRows;          // 64-row passes per half-step
+    constexpr int NKS = Kp / kStrKC;           // k stages per pass (= KI)
+    constexpr int SPH = NP * NKS;              // stages per half-step
+    static_assert(NR % kStrRows == 0, "owned rows must be whole 64-row passes");
+    constexpr int kPieces = kStrStageFloats / 4;  // 16-byte pieces per stage
+    constexpr int CB = kStrCols;
     cg::cluster_group cluster = cg::this_cluster();
     const int crank = (int)cluster.block_rank();
     const int clu = blockIdx.x / CSZ;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int j = lane & 15;
+    const int q = warp * 2 + (lane >> 4);      // row quad within a pass
     const int r0 = crank * NR;
     const int col0 = a.col_base + clu * a.Wv;
     const int ncol = min(a.Wv, a.M - clu * a.Wv);
@@ -118,7 +97,7 @@ __global__ void __launch_bounds__(kStrThreads, 1) rank2_stream_kernel(const Rank
 
     extern __shared__ __align__(16) unsigned char smem[];
     const StreamSmem L = stream_smem_layout(Kp, CSZ);
-    float* ring = reinterpret_cast<float*>(smem + L.ring);   // [stages][16][Kp]
+    float* ring = reinterpret_cast<float*>(smem + L.ring);   // [stages][64 rows][64 k]
     float* Vf = reinterpret_cast<float*>(smem + L.Vf);       // [4][Kp] full V of the columns
     float* Sf = reinterpret_cast<float*>(smem + L.Sf);       // [4][Kp] full S
     float* cV = reinterpret_cast<float*>(smem + L.cV);       // [4][NR] Kahan carries, own rows
@@ -179,30 +158,35 @@ __global__ void __launch_bounds__(kStrThreads, 1) rank2_stream_kernel(const Rank
     cluster.sync();
 
     const int N = a.nsteps;
-    const long long total = (long long)N * 2 * NCH;   // slabs of the whole run
+    const long long total = (long long)N * 2 * SPH;   // stages of the whole run
     const float* Avs = static_cast<const float*>(a.Avs_rm);
     const float* Asv = static_cast<const float*>(a.Asv_rm);
-    // slab g: half (g / NCH) & 1, rows r0 + 16 (g % NCH) of that half's
-    // operator.  Every thread copies its 16-byte pieces t, t + 256, ... of the
-    // slab and arrives on the slot's mbarrier when they have landed; before
-    // reusing a slot, each warp waits until all warps released its last slab.
-    long long issued = 0;                             // slabs issued by this thread
+    // stage g: half (g / SPH) & 1, pass p, k stage ks of that half: rows
+    // r0 + 64 p .. + 63 and columns 64 ks .. + 63 of the half's operator.
+    // Every thread copies its 16-byte pieces t, t + 256, ... and arrives on
+    // the slot's mbarrier when they have landed; before reusing a slot, each
+    // warp waits until all warps released the stage it last held.
+    long long issued = 0;                             // stages issued by this thread
     auto issue_upto = [&](long long upto) {
         while (issued < upto && issued < total) {
             const int s = (int)(issued % kStrStages);
             const uint32_t use = (uint32_t)(issued / kStrStages);
             int ok = 1;
-            if (use > 0 && lane == 0) ok = (*abort_flag == 0) && mbarrier_wait(&empty[s], (use - 1) & 1, limit, abort_flag);
+            if (use > 0 && lane == 0) ok = (*abort_flag == 0) && mbarrier_spin(&empty[s], (use - 1) & 1, limit, abort_flag);
             ok = __shfl_sync(0xffffffffu, ok, 0);
             if (!ok) break;
-            const int hh = (int)((issued / NCH) & 1);
-            const int ch = (int)(issued % NCH);
-            const float4* src = reinterpret_cast<const float4*>((hh ? Asv : Avs) + (size_t)(r0 + ch * kStrRows) * Kp);
-            float4* dst = reinterpret_cast<float4*>(ring + (size_t)s * kStrRows * Kp);
+            const int hh = (int)((issued / SPH) & 1);
+            const int w = (int)(issued % SPH);
+            const int p = w / NKS, ks = w % NKS;
+            const float* src = (hh ? Asv : Avs) + (size_t)(r0 + p * kStrRows) * Kp + ks * kStrKC;
+            float* dst = ring + (size_t)s * kStrStageFloats;
 #pragma unroll
-            for (int e = tid; e < (int)(kSlabBytes / 16); e += kStrThreads)
+            for (int e = tid; e < kPieces; e += kStrThreads) {
+                const int row = e / (kStrKC / 4), c4 = e % (kStrKC / 4);
                 asm volatile("cp.async.cg.shared.global [%0], [%1], 16;"
-                             ::"r"(cvta_shared(dst + e)), "l"(src + e) : "memory");
+                             ::"r"(cvta_shared(dst + row * kStrKC + 4 * c4)),
+                               "l"(src + (size_t)row * Kp + 4 * c4) : "memory");
+            }
             asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];"
                          ::"r"(cvta_shared(&full[s])) : "memory");
             ++issued;
@@ -212,8 +196,9 @@ __global__ void __launch_bounds__(kStrThreads, 1) rank2_stream_kernel(const Rank
 
     float* traces = static_cast<float*>(a.traces);
     const float* Cp = static_cast<const float*>(a.C_p);
-    const int Rc = (a.R + CSZ - 1) / CSZ;             // receivers per CTA
-    long long gidx = 0;                               // slab being consumed
+    const int H = Kp / 64;                            // the split kernel's receiver slabs
+    const int rpc = (a.R + H - 1) / H;
+    long long gidx = 0;                               // stage being consumed
     for (int n = 0; n < N; ++n) {
 #pragma unroll 1
         for (int h = 0; h < 2; ++h) {
@@ -221,56 +206,65 @@ __global__ void __launch_bounds__(kStrThreads, 1) rank2_stream_kernel(const Rank
             float* Y = h ? Sf : Vf;                   // state updated in its own rows
             float* cY = h ? cS : cV;
             const int Kown = h ? a.Ks : a.Kv;
-            float xs[kStrCols][2 * KI];
+            // this lane's operand values: k = 64 i + 4 j + t, as in the split kernel
+            float xs[CB][4 * KI];
 #pragma unroll
-            for (int c = 0; c < kStrCols; ++c)
+            for (int cc = 0; cc < CB; ++cc)
 #pragma unroll
                 for (int i = 0; i < KI; ++i) {
-                    const float2 v = *reinterpret_cast<const float2*>(X + c * Kp + 64 * i + 2 * lane);
-                    xs[c][2 * i] = v.x;
-                    xs[c][2 * i + 1] = v.y;
+                    float x4[4];
+                    load4(X + (size_t)cc * Kp + 64 * i + 4 * j, x4);
+#pragma unroll
+                    for (int t = 0; t < 4; ++t) xs[cc][4 * i + t] = x4[t];
                 }
 #pragma unroll 1
-            for (int ch = 0; ch < NCH; ++ch, ++gidx) {
-                issue_upto(gidx + kStrStages);
-                const int s = (int)(gidx % kStrStages);
-                const uint32_t use = (uint32_t)(gidx / kStrStages);
-                int ok = 1;
-                if (lane == 0) ok = (*abort_flag == 0) && mbarrier_wait(&full[s], use & 1, limit, abort_flag);
-                ok = __shfl_sync(0xffffffffu, ok, 0);
-                if (!ok) continue;
-                const float* slab = ring + (size_t)s * kStrRows * Kp;
-                float v[kStrRpw * kStrCols];
+            for (int p = 0; p < NP; ++p) {
+                float acc[4][CB];
 #pragma unroll
-                for (int q = 0; q < kStrRpw * kStrCols; ++q) v[q] = 0.f;
+                for (int r = 0; r < 4; ++r)
 #pragma unroll
-                for (int rr = 0; rr < kStrRpw; ++rr) {
-                    const float* arow = slab + (size_t)(kStrRpw * warp + rr) * Kp;
+                    for (int cc = 0; cc < CB; ++cc) acc[r][cc] = 0.f;
 #pragma unroll
-                    for (int i = 0; i < KI; ++i) {
-                        const float2 av = *reinterpret_cast<const float2*>(arow + 64 * i + 2 * lane);
+                for (int ks = 0; ks < NKS; ++ks, ++gidx) {
+                    issue_upto(gidx + kStrStages);
+                    const int s = (int)(gidx % kStrStages);
+                    const uint32_t use = (uint32_t)(gidx / kStrStages);
+                    int ok = 1;
+                    if (lane == 0) ok = (*abort_flag == 0) && mbarrier_spin(&full[s], use & 1, limit, abort_flag);
+                    ok = __shfl_sync(0xffffffffu, ok, 0);
+                    if (!ok) continue;
+                    const float* st = ring + (size_t)s * kStrStageFloats;
+                    float op[4][4];
 #pragma unroll
-                        for (int c = 0; c < kStrCols; ++c) {
-                            v[rr * kStrCols + c] = __fmaf_rn(av.x, xs[c][2 * i], v[rr * kStrCols + c]);
-                            v[rr * kStrCols + c] = __fmaf_rn(av.y, xs[c][2 * i + 1], v[rr * kStrCols + c]);
-                        }
-                    }
+                    for (int r = 0; r < 4; ++r) load4(st + (4 * q + r) * kStrKC + 4 * j, op[r]);
+                    __syncwarp();
+                    if (lane == 0) mbarrier_arrive(&empty[s]);
+                    // the split kernel's FMA order: k ascending within the lane's stripe
+#pragma unroll
+                    for (int t = 0; t < 4; ++t)
+#pragma unroll
+                        for (int cc = 0; cc < CB; ++cc)
+#pragma unroll
+                            for (int r = 0; r < 4; ++r)
+                                acc[r][cc] = __fmaf_rn(op[r][t], xs[cc][4 * ks + t], acc[r][cc]);
                 }
-                // the slab has been read: release its stage
-                __syncwarp();
-                if (lane == 0) mbarrier_arrive(&empty[s]);
+                // reduce-scatter over the 16 k lanes and the fused epilogue
+                float v[4 * CB];
+#pragma unroll
+                for (int r = 0; r < 4; ++r)
+#pragma unroll
+                    for (int cc = 0; cc < CB; ++cc) v[r * CB + cc] = acc[r][cc];
                 int vi;
-                const float tot = reduce_scatter32<kStrRpw * kStrCols>(v, lane, vi);
-                if ((lane & (32 / (kStrRpw * kStrCols) - 1)) == 0) {
-                    const int rr = vi / kStrCols, c = vi % kStrCols;
-                    const int rl = ch * kStrRows + kStrRpw * warp + rr;
-                    if (c < ncol && r0 + rl < Kown) {
-                        float inc = tot;
-                        if (h == 0) inc = __fmaf_rn(gown[rl], fcol[c], inc);
-                        inc = inc * dt;
-                        float* yp = Y + c * Kp + r0 + rl;
-                        *yp = kahan_add(*yp, inc, cY[c * NR + rl]);
-                    }
+                bool active;
+                const float tot = reduce_scatter16<float, 4 * CB>(v, j, vi, active);
+                const int rl = p * kStrRows + 4 * q + vi / CB;
+                const int c = vi % CB;
+                if (active && c < ncol && r0 + rl < Kown && !*abort_flag) {
+                    float inc = tot;
+                    if (h == 0) inc = __fmaf_rn(gown[rl], fcol[c], inc);
+                    inc = inc * dt;
+                    float* yp = Y + c * Kp + r0 + rl;
+                    *yp = kahan_add(*yp, inc, cY[c * NR + rl]);
                 }
             }
             __syncthreads();
@@ -280,8 +274,8 @@ __global__ void __launch_bounds__(kStrThreads, 1) rank2_stream_kernel(const Rank
                 float* src = Y + c * Kp + r0 + 4 * q4;
                 const float4 val = *reinterpret_cast<const float4*>(src);
 #pragma unroll
-                for (int p = 1; p < CSZ; ++p)
-                    *reinterpret_cast<float4*>(cluster.map_shared_rank(src, (crank + p) % CSZ)) = val;
+                for (int pp = 1; pp < CSZ; ++pp)
+                    *reinterpret_cast<float4*>(cluster.map_shared_rank(src, (crank + pp) % CSZ)) = val;
             }
             // forcing of the next step (its first use is after the barrier below)
             if (h == 1 && tid < ncol && n + 1 < N) {
@@ -294,41 +288,28 @@ __global__ void __launch_bounds__(kStrThreads, 1) rank2_stream_kernel(const Rank
             cluster.sync();
             if (tid == 0) {
                 int any = 0;
-                for (int p = 0; p < CSZ; ++p)
+                for (int pp = 0; pp < CSZ; ++pp)
                     any |= *reinterpret_cast<volatile const int*>(
-                        cluster.map_shared_rank(const_cast<int*>(abort_pub + h), p));
+                        cluster.map_shared_rank(const_cast<int*>(abort_pub + h), pp));
                 *abort_all = any;
             }
             __syncthreads();
             if (*abort_all) goto done;
-            // receiver traces of V^{n+1}: this CTA's receivers, all columns
+            // receiver traces of V^{n+1}: the split kernel's receiver slabs
+            // crank, crank + CSZ, ..., each with the same warp tiles
             if (h == 0 && traces && ((n + 1) % a.r) == 0) {
                 const int rec = (n + 1) / a.r - 1;
-                for (int jj = warp; jj < Rc; jj += kStrWarps) {
-                    const int jr = crank * Rc + jj;
-                    if (jr >= a.R) break;
-                    float t[kStrCols];
-#pragma unroll
-                    for (int c = 0; c < kStrCols; ++c) t[c] = 0.f;
-#pragma unroll
-                    for (int i = 0; i < KI; ++i) {
-                        const float2 cv = __ldg(reinterpret_cast<const float2*>(Cp + (size_t)jr * Kp + 64 * i + 2 * lane));
-#pragma unroll
-                        for (int c = 0; c < kStrCols; ++c) {
-                            const float2 x = *reinterpret_cast<const float2*>(Vf + c * Kp + 64 * i + 2 * lane);
-                            t[c] = __fmaf_rn(cv.x, x.x, t[c]);
-                            t[c] = __fmaf_rn(cv.y, x.y, t[c]);
-                        }
-                    }
-                    int ti;
-                    const float ts = reduce_scatter32<kStrCols>(t, lane, ti);
-                    if ((lane & 7) == 0 && ti < ncol) traces[((size_t)rec * a.Mtot + col0 + ti) * a.R + jr] = ts;
+                for (int sl = crank; sl < H; sl += CSZ) {
+                    const int nj = min(rpc, a.R - sl * rpc);
+                    if (nj <= 0) break;
+                    split_traces(Cp + (size_t)sl * rpc * Kp, Vf, Kp, nj, ncol, warp, lane,
+                                 traces + ((size_t)rec * a.Mtot + col0) * a.R + sl * rpc, a.R);
                 }
             }
         }
     }
 done:
-    // no slab copy may still be landing when the CTA leaves: each thread
+    // no stage copy may still be landing when the CTA leaves: each thread
     // waits for its own copies
     asm volatile("cp.async.wait_all;" ::: "memory");
     const bool aborted = *abort_flag != 0 || *abort_all != 0;

@@ -70,6 +70,30 @@ __device__ __forceinline__ bool mbarrier_try_wait(uint64_t* bar, uint32_t parity
         : "=r"(ok) : "r"(cvta_shared(bar)), "r"(parity) : "memory");
     return ok != 0;
 }
+// Non-blocking probe of a phase (never suspends the thread).
+__device__ __forceinline__ bool mbarrier_test_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok) : "r"(cvta_shared(bar)), "r"(parity) : "memory");
+    return ok != 0;
+}
+// Bounded spin on mbarrier_test_wait; same contract as mbarrier_wait below.
+__device__ __forceinline__ bool mbarrier_spin(uint64_t* bar, uint32_t parity, long long limit,
+                                              volatile int* abort) {
+    if (mbarrier_test_wait(bar, parity)) return true;
+    const long long t0 = clock64();
+    while (!mbarrier_test_wait(bar, parity)) {
+        if (*abort) return false;
+        if (clock64() - t0 > limit) {
+            *abort = 1;
+            return false;
+        }
+    }
+    return true;
+}
 // Bounded wait.  Returns false when `limit` clock cycles pass without the
 // phase completing, or when *abort is raised by another thread.
 __device__ __forceinline__ bool mbarrier_wait(uint64_t* bar, uint32_t parity, long long limit,

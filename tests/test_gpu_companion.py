@@ -2,8 +2,10 @@
 (rom_set_companion): the last columns of a run integrated by clusters of 2 or
 4 CTAs that stream their operator rows from L2, beside the two-block kernel.
 Against the FP64 oracle (relative L2, Eq. (errors), Sec. 4.4; per column,
-<= 1e-4, the FP32 bar), bitwise across chunked runs with Kahan carries, and
-with the automatic plan of the benchmark's workload."""
+<= 1e-4, the FP32 bar); bitwise equal to the two-block kernel alone (the
+companion does the same arithmetic in the same order); bitwise across chunked
+runs with Kahan carries; and with the automatic plan of the benchmark's
+workload."""
 import numpy as np
 import pytest
 
@@ -51,7 +53,7 @@ def run(R, h, p, V0, S0, N, r=0, n0=0, ftab=None):
 @pytest.mark.parametrize("Kv,Ks,M,R,N,r,cols", [
     (512, 512, 19, 16, 120, 8, 5),     # K = 512: two 16-CTA clusters and 2 companion clusters
     (200, 180, 37, 6, 150, 7, 9),      # ragged rows (Kp = 256), 3 companion clusters
-    (64, 64, 6, 3, 200, 10, 6),        # every column on the companion, one 16-row slab per CTA
+    (256, 256, 6, 3, 200, 10, 6),      # every column on the companion, one 64-row pass per CTA
     (512, 500, 40, 64, 90, 3, 13),     # Ks < Kv, ragged last companion cluster, many receivers
 ])
 def test_companion_vs_oracle(rom, csz, Kv, Ks, M, R, N, r, cols):
@@ -67,6 +69,23 @@ def test_companion_vs_oracle(rom, csz, Kv, Ks, M, R, N, r, cols):
     Vo, So, tro = oracle.forward(p.Avs, p.Asv, p.g, p.C, p.dt, V0, S0, N, T=p.T, n0=4, r=r)
     assert colmax_rel(V, Vo) <= 1e-4 and colmax_rel(S, So) <= 1e-4
     assert colmax_rel(tr, tro) <= 1e-4
+
+
+@pytest.mark.parametrize("csz", [2, 4])
+def test_companion_bitwise_equals_two_block_kernel(rom, csz):
+    """The companion's columns (state and traces) are bit for bit what the
+    two-block kernel alone computes for them."""
+    Kv, M, N, r = 512, 40, 150, 5
+    p = inputs.make_problem(Kv, Kv, M, 64, seed=31)
+    V0 = inputs.random_state(Kv, M, seed=1, scale=0.1)
+    S0 = inputs.random_state(Kv, M, seed=2, scale=0.1)
+    h = rom.Rom.from_problem(p)
+    h.set_companion(-1, 0)
+    Va, Sa, tra = run(rom, h, p, V0, S0, N, r=r, n0=3)
+    h.set_companion(csz, 13)
+    assert h.plan(M)["variant"] == 4
+    Vb, Sb, trb = run(rom, h, p, V0, S0, N, r=r, n0=3)
+    assert np.array_equal(Va, Vb) and np.array_equal(Sa, Sb) and np.array_equal(tra, trb)
 
 
 def test_companion_forcing_table_and_zeros(rom):
