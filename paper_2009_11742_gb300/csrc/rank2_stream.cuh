@@ -13,21 +13,20 @@
 // CTA c owns rows [c Kp / CSZ, (c + 1) Kp / CSZ) of V and of S and keeps the
 // full V and S of its columns in shared memory.  The operators do not fit on
 // so few SMs, so every half-step streams the CTA's rows of Avs (or Asv) from
-// L2 into a ring of 64-row x 64-k stages: every thread issues 16-byte
-// asynchronous copies (L2 only) of its share of a stage, and the stage's
-// mbarrier completes when all of them have landed.  Copies run several
-// stages ahead, across half-steps too, since the operator does not depend on
-// the state.  The arithmetic is the split kernel's, in the same order:
-// thread (row quad q, k lane j) holds the operand at k = 64 i + 4 j + t in
-// registers, accumulates 4 rows x 4 columns with k ascending, and the same
-// 16-lane butterfly reduce-scatter and fused epilogue (forcing g f^T,
-// Kahan-compensated FP32 update) follow; receiver traces y = C V (Sec.
-// 4.5.2) use the split kernel's receiver slabs and warp tiles.  So every
-// column comes out bit for bit as the split kernel computes it.  After a
-// half-step each CTA copies its new rows into its peers' copies (distributed
-// shared memory) and one cluster barrier publishes them.  Every wait is
-// bounded; a wait that runs out records ROM_E_TIMEOUT and the cluster leaves
-// together after draining its copies in flight.
+// L2 in stages of 64 rows x 64 k: each thread loads its 4 rows x 4 k of a
+// stage straight into a ring of registers that holds a whole 64-row pass
+// (Kp / 64 stages), refilling each slot with the next pass's stage as soon as
+// it is used, so a pass worth of loads is always in flight, across
+// half-steps too (the operator does not depend on the state).  The
+// arithmetic is the split kernel's, in the same order: thread (row quad q,
+// k lane j) accumulates 4 rows x 4 columns over k = 64 i + 4 j + t with k
+// ascending, and the same 16-lane butterfly reduce-scatter and fused
+// epilogue (forcing g f^T, Kahan-compensated FP32 update) follow; receiver
+// traces y = C V (Sec. 4.5.2) use the split kernel's receiver slabs and warp
+// tiles.  So every column comes out bit for bit as the split kernel
+// computes it.  After a half-step each CTA copies its new rows into its
+// peers' copies (distributed shared memory) and one cluster barrier
+// publishes them.  The kernel waits on nothing but those barriers.
 #pragma once
 
 #include <cooperative_groups.h>
@@ -37,20 +36,16 @@
 #include "rank2_simt.cuh"
 #include "rank2_split.cuh"
 #include "rom_internal.h"
-#include "tc_common.cuh"
 
 namespace romk {
 
-constexpr int kStrWarps = kSplitWarps;           // 8 warps, the split kernel's thread mapping
 constexpr int kStrThreads = kThreads;             // 256: thread (row quad q, k lane j)
 constexpr int kStrRows = kSplitRows;              // 64 rows per pass (16 row quads)
 constexpr int kStrKC = 64;                        // k extent of one stage
 constexpr int kStrCols = kSplitCB;                // 4 columns per cluster (one column group)
-constexpr int kStrStages = 8;                     // stages in the ring (16 KB each)
-constexpr int kStrStageFloats = kStrRows * kStrKC;
 
 struct StreamSmem {
-    size_t ring, Vf, Sf, cV, cS, f, Tpre, g, bar, flags, total;
+    size_t Vf, Sf, cV, cS, f, Tpre, g, flags, total;
 };
 
 // Shared-memory layout for Kp padded rows and a CSZ-CTA cluster.
@@ -58,7 +53,6 @@ __host__ __device__ inline StreamSmem stream_smem_layout(int Kp, int csz) {
     StreamSmem s{};
     const size_t nr = (size_t)Kp / csz;
     size_t o = 0;
-    s.ring = o;  o += (size_t)kStrStages * kStrStageFloats * sizeof(float);
     s.Vf = o;    o += align16((size_t)kStrCols * Kp * sizeof(float));
     s.Sf = o;    o += align16((size_t)kStrCols * Kp * sizeof(float));
     s.cV = o;    o += align16((size_t)kStrCols * nr * sizeof(float));
@@ -66,8 +60,7 @@ __host__ __device__ inline StreamSmem stream_smem_layout(int Kp, int csz) {
     s.f = o;     o += align16((size_t)kStrCols * sizeof(float));
     s.Tpre = o;  o += align16((size_t)kStrCols * 2 * sizeof(double));
     s.g = o;     o += align16(nr * sizeof(float));
-    s.bar = o;   o += align16((size_t)2 * kStrStages * sizeof(uint64_t));
-    s.flags = o; o += 64;
+    s.flags = o; o += 16;
     s.total = o;
     return s;
 }
@@ -81,7 +74,6 @@ __global__ void __launch_bounds__(kStrThreads, 1) rank2_stream_kernel(const Rank
     constexpr int NKS = Kp / kStrKC;           // k stages per pass (= KI)
     constexpr int SPH = NP * NKS;              // stages per half-step
     static_assert(NR % kStrRows == 0, "owned rows must be whole 64-row passes");
-    constexpr int kPieces = kStrStageFloats / 4;  // 16-byte pieces per stage
     constexpr int CB = kStrCols;
     cg::cluster_group cluster = cg::this_cluster();
     const int crank = (int)cluster.block_rank();
@@ -93,11 +85,9 @@ __global__ void __launch_bounds__(kStrThreads, 1) rank2_stream_kernel(const Rank
     const int col0 = a.col_base + clu * a.Wv;
     const int ncol = min(a.Wv, a.M - clu * a.Wv);
     const float dt = (float)a.dt;
-    const long long limit = a.spin_limit;
 
     extern __shared__ __align__(16) unsigned char smem[];
     const StreamSmem L = stream_smem_layout(Kp, CSZ);
-    float* ring = reinterpret_cast<float*>(smem + L.ring);   // [stages][64 rows][64 k]
     float* Vf = reinterpret_cast<float*>(smem + L.Vf);       // [4][Kp] full V of the columns
     float* Sf = reinterpret_cast<float*>(smem + L.Sf);       // [4][Kp] full S
     float* cV = reinterpret_cast<float*>(smem + L.cV);       // [4][NR] Kahan carries, own rows
@@ -105,30 +95,11 @@ __global__ void __launch_bounds__(kStrThreads, 1) rank2_stream_kernel(const Rank
     float* fcol = reinterpret_cast<float*>(smem + L.f);      // [4] forcing of the current step
     double* Tpre = reinterpret_cast<double*>(smem + L.Tpre); // [4][-1.5 T, pi / T]
     float* gown = reinterpret_cast<float*>(smem + L.g);      // [NR] source rows
-    uint64_t* full = reinterpret_cast<uint64_t*>(smem + L.bar);
-    uint64_t* empty = full + kStrStages;
-    volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + L.flags);
-    volatile int* abort_all = abort_flag + 1;
-    // the flag as published at a half-step's barrier, by half-step parity: a
-    // peer reads slot p after the barrier, and this CTA writes slot p again
-    // only after the next barrier, which the reader must reach first
-    volatile int* abort_pub = abort_flag + 2;
 
     const float* Vin = static_cast<const float*>(a.V);
     const float* Sin = static_cast<const float*>(a.S);
     const float* cVin = static_cast<const float*>(a.compV);
     const float* cSin = static_cast<const float*>(a.compS);
-    if (tid == 0) {
-        *abort_flag = 0;
-        abort_pub[0] = 0;
-        abort_pub[1] = 0;
-        *abort_all = 0;
-        for (int s = 0; s < kStrStages; ++s) {
-            mbarrier_init(&full[s], kStrThreads);
-            mbarrier_init(&empty[s], kStrWarps);
-        }
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    }
     for (int idx = tid; idx < kStrCols * Kp; idx += kStrThreads) {
         const int c = idx / Kp, k = idx % Kp;
         const bool okc = c < ncol;
@@ -161,44 +132,30 @@ __global__ void __launch_bounds__(kStrThreads, 1) rank2_stream_kernel(const Rank
     const long long total = (long long)N * 2 * SPH;   // stages of the whole run
     const float* Avs = static_cast<const float*>(a.Avs_rm);
     const float* Asv = static_cast<const float*>(a.Asv_rm);
-    // stage g: half (g / SPH) & 1, pass p, k stage ks of that half: rows
-    // r0 + 64 p .. + 63 and columns 64 ks .. + 63 of the half's operator.
-    // Every thread copies its 16-byte pieces t, t + 256, ... and arrives on
-    // the slot's mbarrier when they have landed; before reusing a slot, each
-    // warp waits until all warps released the stage it last held.
-    long long issued = 0;                             // stages issued by this thread
-    auto issue_upto = [&](long long upto) {
-        while (issued < upto && issued < total) {
-            const int s = (int)(issued % kStrStages);
-            const uint32_t use = (uint32_t)(issued / kStrStages);
-            int ok = 1;
-            if (use > 0 && lane == 0) ok = (*abort_flag == 0) && mbarrier_spin(&empty[s], (use - 1) & 1, limit, abort_flag);
-            ok = __shfl_sync(0xffffffffu, ok, 0);
-            if (!ok) break;
-            const int hh = (int)((issued / SPH) & 1);
-            const int w = (int)(issued % SPH);
-            const int p = w / NKS, ks = w % NKS;
-            const float* src = (hh ? Asv : Avs) + (size_t)(r0 + p * kStrRows) * Kp + ks * kStrKC;
-            float* dst = ring + (size_t)s * kStrStageFloats;
+    // Stage g: half (g / SPH) & 1, pass p, k stage ks of that half; this
+    // thread's part is rows r0 + 64 p + 4 q .. + 3 at k = 64 ks + 4 j .. + 3.
+    // A ring of NKS stages lives in registers: slot ks holds stage g, and is
+    // refilled with stage g + NKS (the same k stage of the next pass or half)
+    // as soon as it has been used, so the loads of NKS stages are in flight.
+    auto load_stage = [&](long long g, float4 (&b)[4]) {
+        const int hh = (int)((g / SPH) & 1);
+        const int w = (int)(g % SPH);
+        const int p = w / NKS, ks = w % NKS;
+        const float* src = (hh ? Asv : Avs) + (size_t)(r0 + p * kStrRows + 4 * q) * Kp + ks * kStrKC + 4 * j;
 #pragma unroll
-            for (int e = tid; e < kPieces; e += kStrThreads) {
-                const int row = e / (kStrKC / 4), c4 = e % (kStrKC / 4);
-                asm volatile("cp.async.cg.shared.global [%0], [%1], 16;"
-                             ::"r"(cvta_shared(dst + row * kStrKC + 4 * c4)),
-                               "l"(src + (size_t)row * Kp + 4 * c4) : "memory");
-            }
-            asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];"
-                         ::"r"(cvta_shared(&full[s])) : "memory");
-            ++issued;
-        }
+        for (int r = 0; r < 4; ++r) b[r] = __ldcg(reinterpret_cast<const float4*>(src + (size_t)r * Kp));
     };
-    issue_upto(kStrStages - 1);
+    float4 ring[NKS][4];
+#pragma unroll
+    for (int ks = 0; ks < NKS; ++ks) {
+        if (ks < total) load_stage(ks, ring[ks]);
+    }
 
     float* traces = static_cast<float*>(a.traces);
     const float* Cp = static_cast<const float*>(a.C_p);
     const int H = Kp / 64;                            // the split kernel's receiver slabs
     const int rpc = (a.R + H - 1) / H;
-    long long gidx = 0;                               // stage being consumed
+    long long g = 0;                                  // stage being consumed
     for (int n = 0; n < N; ++n) {
 #pragma unroll 1
         for (int h = 0; h < 2; ++h) {
@@ -206,17 +163,6 @@ __global__ void __launch_bounds__(kStrThreads, 1) rank2_stream_kernel(const Rank
             float* Y = h ? Sf : Vf;                   // state updated in its own rows
             float* cY = h ? cS : cV;
             const int Kown = h ? a.Ks : a.Kv;
-            // this lane's operand values: k = 64 i + 4 j + t, as in the split kernel
-            float xs[CB][4 * KI];
-#pragma unroll
-            for (int cc = 0; cc < CB; ++cc)
-#pragma unroll
-                for (int i = 0; i < KI; ++i) {
-                    float x4[4];
-                    load4(X + (size_t)cc * Kp + 64 * i + 4 * j, x4);
-#pragma unroll
-                    for (int t = 0; t < 4; ++t) xs[cc][4 * i + t] = x4[t];
-                }
 #pragma unroll 1
             for (int p = 0; p < NP; ++p) {
                 float acc[4][CB];
@@ -225,20 +171,19 @@ __global__ void __launch_bounds__(kStrThreads, 1) rank2_stream_kernel(const Rank
 #pragma unroll
                     for (int cc = 0; cc < CB; ++cc) acc[r][cc] = 0.f;
 #pragma unroll
-                for (int ks = 0; ks < NKS; ++ks, ++gidx) {
-                    issue_upto(gidx + kStrStages);
-                    const int s = (int)(gidx % kStrStages);
-                    const uint32_t use = (uint32_t)(gidx / kStrStages);
-                    int ok = 1;
-                    if (lane == 0) ok = (*abort_flag == 0) && mbarrier_spin(&full[s], use & 1, limit, abort_flag);
-                    ok = __shfl_sync(0xffffffffu, ok, 0);
-                    if (!ok) continue;
-                    const float* st = ring + (size_t)s * kStrStageFloats;
+                for (int ks = 0; ks < NKS; ++ks, ++g) {
                     float op[4][4];
 #pragma unroll
-                    for (int r = 0; r < 4; ++r) load4(st + (4 * q + r) * kStrKC + 4 * j, op[r]);
-                    __syncwarp();
-                    if (lane == 0) mbarrier_arrive(&empty[s]);
+                    for (int r = 0; r < 4; ++r) {
+                        op[r][0] = ring[ks][r].x;
+                        op[r][1] = ring[ks][r].y;
+                        op[r][2] = ring[ks][r].z;
+                        op[r][3] = ring[ks][r].w;
+                    }
+                    if (g + NKS < total) load_stage(g + NKS, ring[ks]);
+                    float x[CB][4];
+#pragma unroll
+                    for (int cc = 0; cc < CB; ++cc) load4(X + (size_t)cc * Kp + 64 * ks + 4 * j, x[cc]);
                     // the split kernel's FMA order: k ascending within the lane's stripe
 #pragma unroll
                     for (int t = 0; t < 4; ++t)
@@ -246,7 +191,7 @@ __global__ void __launch_bounds__(kStrThreads, 1) rank2_stream_kernel(const Rank
                         for (int cc = 0; cc < CB; ++cc)
 #pragma unroll
                             for (int r = 0; r < 4; ++r)
-                                acc[r][cc] = __fmaf_rn(op[r][t], xs[cc][4 * ks + t], acc[r][cc]);
+                                acc[r][cc] = __fmaf_rn(op[r][t], x[cc][t], acc[r][cc]);
                 }
                 // reduce-scatter over the 16 k lanes and the fused epilogue
                 float v[4 * CB];
@@ -259,7 +204,7 @@ __global__ void __launch_bounds__(kStrThreads, 1) rank2_stream_kernel(const Rank
                 const float tot = reduce_scatter16<float, 4 * CB>(v, j, vi, active);
                 const int rl = p * kStrRows + 4 * q + vi / CB;
                 const int c = vi % CB;
-                if (active && c < ncol && r0 + rl < Kown && !*abort_flag) {
+                if (active && c < ncol && r0 + rl < Kown) {
                     float inc = tot;
                     if (h == 0) inc = __fmaf_rn(gown[rl], fcol[c], inc);
                     inc = inc * dt;
@@ -284,17 +229,7 @@ __global__ void __launch_bounds__(kStrThreads, 1) rank2_stream_kernel(const Rank
                 else if (a.Tper) f = wavelet_eval_pre(a.wavelet, (long long)a.n0 + n + 1, a.dt, Tpre[2 * tid], Tpre[2 * tid + 1]);
                 fcol[tid] = f;
             }
-            if (tid == 0) abort_pub[h] = *abort_flag;
             cluster.sync();
-            if (tid == 0) {
-                int any = 0;
-                for (int pp = 0; pp < CSZ; ++pp)
-                    any |= *reinterpret_cast<volatile const int*>(
-                        cluster.map_shared_rank(const_cast<int*>(abort_pub + h), pp));
-                *abort_all = any;
-            }
-            __syncthreads();
-            if (*abort_all) goto done;
             // receiver traces of V^{n+1}: the split kernel's receiver slabs
             // crank, crank + CSZ, ..., each with the same warp tiles
             if (h == 0 && traces && ((n + 1) % a.r) == 0) {
@@ -308,12 +243,6 @@ __global__ void __launch_bounds__(kStrThreads, 1) rank2_stream_kernel(const Rank
             }
         }
     }
-done:
-    // no stage copy may still be landing when the CTA leaves: each thread
-    // waits for its own copies
-    asm volatile("cp.async.wait_all;" ::: "memory");
-    const bool aborted = *abort_flag != 0 || *abort_all != 0;
-    if (aborted && tid == 0 && a.status) atomicCAS(a.status, 0, 5 /* ROM_E_TIMEOUT */);
     // ---- write back the own rows and carries
     int bad = 0;
     for (int idx = tid; idx < ncol * NR; idx += kStrThreads) {
@@ -333,8 +262,6 @@ done:
     }
     bad = __syncthreads_or(bad);
     if (bad && tid == 0 && a.status) atomicCAS(a.status, 0, 6 /* ROM_E_NONFINITE */);
-    // peers may still read this CTA's flags until every CTA is here
-    cluster.sync();
 }
 
 }  // namespace romk
