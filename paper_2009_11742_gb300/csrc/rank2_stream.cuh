@@ -129,33 +129,29 @@ __global__ void __launch_bounds__(kStrThreads, 1) rank2_stream_kernel(const Rank
     cluster.sync();
 
     const int N = a.nsteps;
-    const long long total = (long long)N * 2 * SPH;   // stages of the whole run
     const float* Avs = static_cast<const float*>(a.Avs_rm);
     const float* Asv = static_cast<const float*>(a.Asv_rm);
-    // Stage g: half (g / SPH) & 1, pass p, k stage ks of that half; this
-    // thread's part is rows r0 + 64 p + 4 q .. + 3 at k = 64 ks + 4 j .. + 3.
-    // A ring of NKS stages lives in registers: slot ks holds stage g, and is
-    // refilled with stage g + NKS (the same k stage of the next pass or half)
-    // as soon as it has been used, so the loads of NKS stages are in flight.
-    auto load_stage = [&](long long g, float4 (&b)[4]) {
-        const int hh = (int)((g / SPH) & 1);
-        const int w = (int)(g % SPH);
-        const int p = w / NKS, ks = w % NKS;
-        const float* src = (hh ? Asv : Avs) + (size_t)(r0 + p * kStrRows + 4 * q) * Kp + ks * kStrKC + 4 * j;
-#pragma unroll
-        for (int r = 0; r < 4; ++r) b[r] = __ldcg(reinterpret_cast<const float4*>(src + (size_t)r * Kp));
-    };
+    // Stage (half h, pass p, k stage ks): this thread's part is rows
+    // r0 + 64 p + 4 q .. + 3 of the half's operator at k = 64 ks + 4 j .. + 3.
+    // A ring of NKS stages lives in registers: slot ks holds the current
+    // pass's stage ks and is refilled with the next pass's stage ks (the
+    // next half's first pass after the last one) as soon as it is used, so a
+    // pass worth of loads is always in flight, across half-steps too.
+    const size_t lane_off = (size_t)(r0 + 4 * q) * Kp + 4 * j;
     float4 ring[NKS][4];
+    if (N > 0) {
+        const float* src = Avs + lane_off;
 #pragma unroll
-    for (int ks = 0; ks < NKS; ++ks) {
-        if (ks < total) load_stage(ks, ring[ks]);
+        for (int ks = 0; ks < NKS; ++ks)
+#pragma unroll
+            for (int r = 0; r < 4; ++r)
+                ring[ks][r] = __ldcg(reinterpret_cast<const float4*>(src + (size_t)r * Kp + ks * kStrKC));
     }
 
     float* traces = static_cast<float*>(a.traces);
     const float* Cp = static_cast<const float*>(a.C_p);
     const int H = Kp / 64;                            // the split kernel's receiver slabs
     const int rpc = (a.R + H - 1) / H;
-    long long g = 0;                                  // stage being consumed
     for (int n = 0; n < N; ++n) {
 #pragma unroll 1
         for (int h = 0; h < 2; ++h) {
@@ -165,13 +161,18 @@ __global__ void __launch_bounds__(kStrThreads, 1) rank2_stream_kernel(const Rank
             const int Kown = h ? a.Ks : a.Kv;
 #pragma unroll 1
             for (int p = 0; p < NP; ++p) {
+                // the pass whose stages refill the ring
+                const bool last = p + 1 == NP;
+                const bool has_next = !(last && h == 1 && n + 1 == N);
+                const float* nsrc = (last ? (h ? Avs : Asv) : (h ? Asv : Avs)) +
+                                    (size_t)(last ? 0 : (p + 1) * kStrRows) * Kp + lane_off;
                 float acc[4][CB];
 #pragma unroll
                 for (int r = 0; r < 4; ++r)
 #pragma unroll
                     for (int cc = 0; cc < CB; ++cc) acc[r][cc] = 0.f;
 #pragma unroll
-                for (int ks = 0; ks < NKS; ++ks, ++g) {
+                for (int ks = 0; ks < NKS; ++ks) {
                     float op[4][4];
 #pragma unroll
                     for (int r = 0; r < 4; ++r) {
@@ -180,7 +181,11 @@ __global__ void __launch_bounds__(kStrThreads, 1) rank2_stream_kernel(const Rank
                         op[r][2] = ring[ks][r].z;
                         op[r][3] = ring[ks][r].w;
                     }
-                    if (g + NKS < total) load_stage(g + NKS, ring[ks]);
+                    if (has_next) {
+#pragma unroll
+                        for (int r = 0; r < 4; ++r)
+                            ring[ks][r] = __ldcg(reinterpret_cast<const float4*>(nsrc + (size_t)r * Kp + ks * kStrKC));
+                    }
                     float x[CB][4];
 #pragma unroll
                     for (int cc = 0; cc < CB; ++cc) load4(X + (size_t)cc * Kp + 64 * ks + 4 * j, x[cc]);
