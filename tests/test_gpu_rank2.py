@@ -149,11 +149,12 @@ def test_config1_fp32_sampled_columns(rom):
 
 def test_one_block_and_two_block_kernels_agree(rom):
     """Both FP32 schedules at workload-1 width (K = 512) agree to FP32 rounding
-    and the two-block kernel is what the planner picks."""
+    and the two-block kernel is what the planner picks (with the streaming
+    companion on the SMs its clusters leave idle: variant 4)."""
     p = inputs.make_problem(512, 512, 256, 64, seed=0)
     h = rom.Rom.from_problem(p)
     Z = np.zeros((512, 256))
-    assert h.plan(256)["variant"] == 2
+    assert h.plan(256)["variant"] in (2, 4)
     V1, S1, t1 = gpu_run(rom, h, p, Z, Z, 1000, "fp32", r=10, kernel=1)
     V2, S2, t2 = gpu_run(rom, h, p, Z, Z, 1000, "fp32", r=10, kernel=2)
     V3, S3, t3 = gpu_run(rom, h, p, Z, Z, 1000, "fp32", r=10, kernel=3)
