@@ -478,6 +478,7 @@ def main():
     achieved = flops / (t_dev / args.steps) / 1e12
     plan = h.plan(M, "fp32")
     kname = ("rank2_split_kernel<8>" if plan["variant"] == 2
+             else "rank2_split_kernel<8> + rank2_stream_kernel<8,4>" if plan["variant"] == 4
              else "rank2_simt_kernel<float,8,8,true>")
     traffic = profiled_traffic(kname, N) if (K, M, R, r) == (512, 256, 64, 10) else None
     if "fp32" in mp:
