@@ -240,7 +240,8 @@ def profiled_traffic(kname, nsteps):
     """DRAM bytes (read + write) of one full-size launch, from the committed
     ncu summary of that kernel on this workload, or None."""
     import re
-    stem = kname.split("<")[0]
+    stem = ("rank2_split_and_stream_kernels" if "rank2_stream_kernel" in kname
+            else kname.split("<")[0])
     prof = os.path.join(ROOT, "profiles", f"{stem}_fp32_K512_M256_N{nsteps}.md")
     try:
         m = re.search(r"^dram_bytes_per_launch:\s*(\d+)", open(prof).read(), re.M)

@@ -30,14 +30,23 @@ def test_reference_arm_line_keeps_the_contract():
 
 def test_roofline_traffic_comes_from_the_committed_profile():
     """The headline line's roofline `traffic` is read from the ncu summary of
-    the split kernel on the headline workload; the summary must keep the
-    line the bench parses, with read + write bytes of one full launch."""
+    the kernels of the headline plan; each summary keeps the line the bench
+    parses, equal to the read + write bytes of one full launch (the sum over
+    both kernels of the split + companion pair)."""
     import re
     import bench
-    t = bench.profiled_traffic("rank2_split_kernel<8>", 10000)
-    assert isinstance(t, int) and t > 0
-    text = open(os.path.join(ROOT, "profiles", "rank2_split_kernel_fp32_K512_M256_N10000.md")).read()
-    rd = int(re.search(r"dram__bytes_read\.sum \| ([\d,]+) B", text).group(1).replace(",", ""))
-    wr = int(re.search(r"dram__bytes_write\.sum \| ([\d,]+) B", text).group(1).replace(",", ""))
-    assert t == rd + wr
-    assert bench.profiled_traffic("rank2_split_kernel<8>", 1234) is None
+    cases = [("rank2_split_kernel<8>", "rank2_split_kernel_fp32_K512_M256_N10000.md"),
+             ("rank2_split_kernel<8> + rank2_stream_kernel<8,4>",
+              "rank2_split_and_stream_kernels_fp32_K512_M256_N10000.md")]
+    for kname, fname in cases:
+        t = bench.profiled_traffic(kname, 10000)
+        assert isinstance(t, int) and t > 0
+        text = open(os.path.join(ROOT, "profiles", fname)).read()
+        rd = [int(x.replace(",", "")) for x in re.findall(r"dram__bytes_read\.sum \| ([\d,]+) B", text)]
+        wr = [int(x.replace(",", "")) for x in re.findall(r"dram__bytes_write\.sum \| ([\d,]+) B", text)]
+        if not rd:  # table with one row per kernel
+            rows = re.findall(r"^\| rank2_\w+<[^|]*\| ([\d,]+) B \| ([\d,]+) B \|", text, re.M)
+            rd = [int(a.replace(",", "")) for a, _ in rows]
+            wr = [int(b.replace(",", "")) for _, b in rows]
+        assert rd and t == sum(rd) + sum(wr), (fname, t, rd, wr)
+        assert bench.profiled_traffic(kname, 1234) is None
