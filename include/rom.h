@@ -402,7 +402,9 @@ rom_status rom_autotune_batched(const rom_job* jobs, int njobs, int prec, int pr
  * Outputs: gV0 (Kv x M), gS0 (Ks x M), gT (M) device float; *loss (host).
  * workspace: device, rom_adjoint_workspace_size bytes, or NULL to let the
  * library allocate it for the call.  Device buffers only; FP32 only;
- * Kv, Ks <= 512.  Synchronous on `stream`.
+ * Kv, Ks <= 1024 (above 512 the reverse kernel reads the transposed
+ * operators from L2 every half-step instead of keeping them in registers).
+ * Synchronous on `stream`.
  */
 rom_status rom_adjoint(rom_t h, const void* V0, const void* S0, const void* T, int M, int nsteps,
                        const void* ystar, int ckpt_every, void* gV0, void* gS0, void* gT,

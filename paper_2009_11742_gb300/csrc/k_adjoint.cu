@@ -7,34 +7,36 @@
 namespace romk {
 
 static void* adjoint_kernel(int KI) {
+#define ROM_ADJ_CASE(k) \
+    case k: return (void*)&rank2_adjoint_kernel<k, 8>;
     switch (KI) {
-        case 1: return (void*)&rank2_adjoint_kernel<1, 8>;
-        case 2: return (void*)&rank2_adjoint_kernel<2, 8>;
-        case 3: return (void*)&rank2_adjoint_kernel<3, 8>;
-        case 4: return (void*)&rank2_adjoint_kernel<4, 8>;
-        case 5: return (void*)&rank2_adjoint_kernel<5, 8>;
-        case 6: return (void*)&rank2_adjoint_kernel<6, 8>;
-        case 7: return (void*)&rank2_adjoint_kernel<7, 8>;
-        case 8: return (void*)&rank2_adjoint_kernel<8, 8>;
+        ROM_ADJ_CASE(1) ROM_ADJ_CASE(2) ROM_ADJ_CASE(3) ROM_ADJ_CASE(4)
+        ROM_ADJ_CASE(5) ROM_ADJ_CASE(6) ROM_ADJ_CASE(7) ROM_ADJ_CASE(8)
+        ROM_ADJ_CASE(9) ROM_ADJ_CASE(10) ROM_ADJ_CASE(11) ROM_ADJ_CASE(12)
+        ROM_ADJ_CASE(13) ROM_ADJ_CASE(14) ROM_ADJ_CASE(15) ROM_ADJ_CASE(16)
         default: return nullptr;
     }
+#undef ROM_ADJ_CASE
 }
 
+// Kp <= 512: one 32-row tile per CTA (Kp / 32 CTAs, operators in registers);
+// 512 < Kp <= 1024: two tiles per CTA (Kp / 64 CTAs, operators read from L2).
 bool plan_adjoint(int Kp, int M, int R, AdjPlan* p) {
-    if (Kp <= 0 || Kp % 64 != 0 || Kp > 512 || M <= 0 || R <= 0) return false;
+    if (Kp <= 0 || Kp % 64 != 0 || Kp > 1024 || M <= 0 || R <= 0) return false;
     p->KI = Kp / 64;
-    p->cs = Kp / 32;
+    const int nrt = Kp > 512 ? 2 : 1;
+    p->cs = Kp / (32 * nrt);
     p->cb = 8;
     const int smax = device_smem_optin();
     int wcap = 0;
     for (int w = 8; w <= 2048; w += 8) {
-        if (adj_smem_layout(w, Kp, R).total > (size_t)smax) break;
+        if (adj_smem_layout(w, Kp, R, nrt).total > (size_t)smax) break;
         wcap = w;
     }
     if (wcap == 0) return false;
     void* fn = adjoint_kernel(p->KI);
     if (!fn) return false;
-    const size_t smem_probe = adj_smem_layout(wcap, Kp, R).total;
+    const size_t smem_probe = adj_smem_layout(wcap, Kp, R, nrt).total;
     if (prepare_kernel<float>(fn, smem_probe) != cudaSuccess) return false;
     ClusterLaunch probe(p->cs, 1, kThreads, smem_probe);
     const int nact = probe.max_active(fn);
@@ -45,7 +47,7 @@ bool plan_adjoint(int Kp, int M, int R, AdjPlan* p) {
     p->Wv = wv;
     p->Wa = wv;
     p->nclusters = (M + wv - 1) / wv;
-    p->smem = adj_smem_layout(p->Wa, Kp, R).total;
+    p->smem = adj_smem_layout(p->Wa, Kp, R, nrt).total;
     return true;
 }
 

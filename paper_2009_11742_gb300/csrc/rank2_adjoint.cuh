@@ -12,10 +12,13 @@
 //
 // The kernel is the one-block cluster kernel of rank2_simt.cuh run backwards
 // in time with the transposed operators (the column-major copies of Asv and
-// Avs are the row-major Asv^T and Avs^T) resident in registers; half A's
-// epilogue adds the rank-R source 2 C^T r^{n+1} (C columns of the CTA's rows
-// and the step's residuals staged in shared memory), and a deterministic
-// per-CTA column reduction accumulates the period gradient.
+// Avs are the row-major Asv^T and Avs^T): resident in registers up to
+// Kp = 512 (one 32-row tile per CTA), and for 512 < Kp <= 1024 read from L2
+// for each of the CTA's two 32-row tiles every half-step, as the forward
+// kernel does there.  Half A's epilogue adds the rank-R source 2 C^T r^{n+1}
+// (C columns of the CTA's rows and the step's residuals staged in shared
+// memory), and a deterministic per-CTA column reduction accumulates the
+// period gradient.
 #pragma once
 
 #include <cooperative_groups.h>
@@ -34,16 +37,18 @@ struct AdjSmem {
     size_t Vf, Sf, cV, cS, Ccol, rbuf, g, T, gT, dfT, total;
 };
 
-__host__ __device__ inline AdjSmem adj_smem_layout(int Wa, int Kp, int R) {
+// nrt: 32-row tiles owned per CTA (1 for Kp <= 512, 2 above).
+__host__ __device__ inline AdjSmem adj_smem_layout(int Wa, int Kp, int R, int nrt = 1) {
     AdjSmem s{};
+    const size_t own = (size_t)nrt * kRowsPerCta;
     size_t o = 0;
     s.Vf = o;   o += align16((size_t)Wa * Kp * sizeof(float));
     s.Sf = o;   o += align16((size_t)Wa * Kp * sizeof(float));
-    s.cV = o;   o += align16((size_t)Wa * kRowsPerCta * sizeof(float));
-    s.cS = o;   o += align16((size_t)Wa * kRowsPerCta * sizeof(float));
-    s.Ccol = o; o += align16((size_t)R * kRowsPerCta * sizeof(float));
+    s.cV = o;   o += align16((size_t)Wa * own * sizeof(float));
+    s.cS = o;   o += align16((size_t)Wa * own * sizeof(float));
+    s.Ccol = o; o += align16((size_t)R * own * sizeof(float));
     s.rbuf = o; o += align16((size_t)R * Wa * sizeof(float));
-    s.g = o;    o += align16((size_t)kRowsPerCta * sizeof(float));
+    s.g = o;    o += align16(own * sizeof(float));
     s.T = o;    o += align16((size_t)Wa * sizeof(float));
     s.gT = o;   o += align16((size_t)Wa * sizeof(float));
     s.dfT = o;  o += align16((size_t)kAdjTab * Wa * sizeof(float));
@@ -51,12 +56,15 @@ __host__ __device__ inline AdjSmem adj_smem_layout(int Wa, int Kp, int R) {
     return s;
 }
 
-// Half A of a reverse step on the CTA's 32 rows:
+// Half A of a reverse step on one 32-row tile of the CTA (rows row0 ..):
 //   Y_own += dt (op . X) + 2 C_own^T r   (Kahan-compensated).
+// Ccol points at the tile's first row of the CTA's C columns (row stride
+// cstride floats).
 template <int KI, int CB>
 __device__ __forceinline__ void adj_half_a(const float (&op)[2][4 * KI], const float* __restrict__ X,
                                            float* __restrict__ Y, float* __restrict__ comp,
-                                           const float* __restrict__ Ccol, const float* __restrict__ rbuf,
+                                           const float* __restrict__ Ccol, const int cstride,
+                                           const float* __restrict__ rbuf,
                                            const int R, const float dt, const int Wa, const int Kp,
                                            const int row0, const int rp, const int j) {
     for (int c0 = 0; c0 < Wa; c0 += CB) {
@@ -86,7 +94,7 @@ __device__ __forceinline__ void adj_half_a(const float (&op)[2][4 * KI], const f
             const int rl = 2 * rp + vi / CB;
             const int c = c0 + vi % CB;
             float src = 0.f;
-            for (int jr = 0; jr < R; ++jr) src = __fmaf_rn(Ccol[jr * kRowsPerCta + rl], rbuf[jr * Wa + c], src);
+            for (int jr = 0; jr < R; ++jr) src = __fmaf_rn(Ccol[jr * cstride + rl], rbuf[jr * Wa + c], src);
             const float inc = __fmaf_rn(tot, dt, 2.f * src);
             float* yp = Y + (size_t)c * Kp + row0 + rl;
             *yp = kahan_add(*yp, inc, comp[c * kRowsPerCta + rl]);
@@ -94,8 +102,13 @@ __device__ __forceinline__ void adj_half_a(const float (&op)[2][4 * KI], const f
     }
 }
 
+// KI = Kp / 64 (<= 16); operators resident in registers for KI <= 8 (one
+// 32-row tile per CTA), streamed per tile above (two tiles per CTA).
 template <int KI, int CB>
 __global__ void __launch_bounds__(kThreads, 1) rank2_adjoint_kernel(const AdjArgs a) {
+    constexpr int NRT = KI > 8 ? 2 : 1;
+    constexpr bool RES = NRT == 1;
+    constexpr int OWN = NRT * kRowsPerCta;
     cg::cluster_group cluster = cg::this_cluster();
     const int cs = (int)cluster.num_blocks();
     const int crank = (int)cluster.block_rank();
@@ -106,16 +119,16 @@ __global__ void __launch_bounds__(kThreads, 1) rank2_adjoint_kernel(const AdjArg
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int j = lane & 15;
     const int rp = warp * 2 + (lane >> 4);
-    const int row0 = crank * kRowsPerCta;
+    const int row0 = crank * OWN;
     const float dt = (float)a.dt;
 
     extern __shared__ __align__(16) unsigned char smem[];
-    const AdjSmem L = adj_smem_layout(Wa, Kp, R);
+    const AdjSmem L = adj_smem_layout(Wa, Kp, R, NRT);
     float* Vf = reinterpret_cast<float*>(smem + L.Vf);
     float* Sf = reinterpret_cast<float*>(smem + L.Sf);
     float* cV = reinterpret_cast<float*>(smem + L.cV);
     float* cS = reinterpret_cast<float*>(smem + L.cS);
-    float* Ccol = reinterpret_cast<float*>(smem + L.Ccol);  // [R][32]: C[j][row0 + rl]
+    float* Ccol = reinterpret_cast<float*>(smem + L.Ccol);  // [R][OWN]: C[j][row0 + ro]
     float* rbuf = reinterpret_cast<float*>(smem + L.rbuf);  // [R][Wa]: residual of the step
     float* gown = reinterpret_cast<float*>(smem + L.g);
     float* Tcol = reinterpret_cast<float*>(smem + L.T);
@@ -127,23 +140,28 @@ __global__ void __launch_bounds__(kThreads, 1) rank2_adjoint_kernel(const AdjArg
         Vf[idx] = (c < ncol && k < a.Kv) ? a.lamV[(size_t)(col0 + c) * a.Kv + k] : 0.f;
         Sf[idx] = (c < ncol && k < a.Ks) ? a.lamS[(size_t)(col0 + c) * a.Ks + k] : 0.f;
     }
-    for (int idx = tid; idx < Wa * kRowsPerCta; idx += kThreads) {
-        const int c = idx / kRowsPerCta, rl = idx % kRowsPerCta, row = row0 + rl;
+    // carries: [row tile][column][32 rows]
+    for (int idx = tid; idx < NRT * Wa * kRowsPerCta; idx += kThreads) {
+        const int rt = idx / (Wa * kRowsPerCta);
+        const int rem = idx - rt * Wa * kRowsPerCta;
+        const int c = rem / kRowsPerCta, rl = rem % kRowsPerCta, row = row0 + rt * kRowsPerCta + rl;
         cV[idx] = (c < ncol && row < a.Kv) ? a.compV[(size_t)(col0 + c) * a.Kv + row] : 0.f;
         cS[idx] = (c < ncol && row < a.Ks) ? a.compS[(size_t)(col0 + c) * a.Ks + row] : 0.f;
     }
-    for (int idx = tid; idx < R * kRowsPerCta; idx += kThreads) {
-        const int jr = idx / kRowsPerCta, rl = idx % kRowsPerCta;
-        Ccol[idx] = a.C_rm[(size_t)jr * Kp + row0 + rl];
+    for (int idx = tid; idx < R * OWN; idx += kThreads) {
+        const int jr = idx / OWN, ro = idx % OWN;
+        Ccol[idx] = a.C_rm[(size_t)jr * Kp + row0 + ro];
     }
-    if (tid < kRowsPerCta) gown[tid] = a.g_p[row0 + tid];
+    for (int ro = tid; ro < OWN; ro += kThreads) gown[ro] = a.g_p[row0 + ro];
     for (int c = tid; c < Wa; c += kThreads) {
         Tcol[c] = (c < ncol) ? a.Tper[col0 + c] : 1.f;
         gTacc[c] = (c < ncol) ? a.gTpart[(size_t)crank * a.M + col0 + c] : 0.f;
     }
     float opA[2][4 * KI], opB[2][4 * KI];
-    load_op_rows<float, KI>(opA, a.opA_rm, Kp, row0 + 2 * rp, j);
-    load_op_rows<float, KI>(opB, a.opB_rm, Kp, row0 + 2 * rp, j);
+    if (RES) {
+        load_op_rows<float, KI>(opA, a.opA_rm, Kp, row0 + 2 * rp, j);
+        load_op_rows<float, KI>(opB, a.opB_rm, Kp, row0 + 2 * rp, j);
+    }
     cluster.sync();
 
     for (int n = a.n_hi - 1; n >= a.n_lo; --n) {
@@ -175,37 +193,53 @@ __global__ void __launch_bounds__(kThreads, 1) rank2_adjoint_kernel(const AdjArg
         }
         __syncthreads();
         // ---- half A: lamV <- lamV + 2 C^T r^{n+1} + dt Asv^T lamS
-        adj_half_a<KI, CB>(opA, Sf, Vf, cV, Ccol, rbuf, R, dt, Wa, Kp, row0, rp, j);
+#pragma unroll
+        for (int rt = 0; rt < NRT; ++rt) {
+            const int rowt = row0 + rt * kRowsPerCta;
+            if (!RES) load_op_rows<float, KI>(opA, a.opA_rm, Kp, rowt + 2 * rp, j);
+            adj_half_a<KI, CB>(opA, Sf, Vf, cV + rt * Wa * kRowsPerCta, Ccol + rt * kRowsPerCta, OWN,
+                               rbuf, R, dt, Wa, Kp, rowt, rp, j);
+        }
         __syncthreads();
         // period gradient: dt (g_own . a_V[:, c]) df/dT(t_n; T_c), fixed reduction order
         for (int c = warp; c < ncol; c += kThreads / 32) {
             float s = gown[lane] * Vf[(size_t)c * Kp + row0 + lane];
 #pragma unroll
+            for (int rt = 1; rt < NRT; ++rt)
+                s = __fmaf_rn(gown[rt * kRowsPerCta + lane], Vf[(size_t)c * Kp + row0 + rt * kRowsPerCta + lane], s);
+#pragma unroll
             for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
             if (lane == 0) gTacc[c] = __fmaf_rn(dt * s, dfn[c], gTacc[c]);
         }
-        push_own_rows<float>(cluster, Vf, Wa, Kp, row0, cs, crank, 1);
+        push_own_rows<float>(cluster, Vf, Wa, Kp, row0, cs, crank, NRT);
         cluster.sync();
         // ---- half B: lamS <- lamS + dt Avs^T a_V
-        half_step<float, KI, CB, false>(opB, Vf, Sf, cS, gown, gown, dt, Wa, Kp, row0, rp, j);
+#pragma unroll
+        for (int rt = 0; rt < NRT; ++rt) {
+            const int rowt = row0 + rt * kRowsPerCta;
+            if (!RES) load_op_rows<float, KI>(opB, a.opB_rm, Kp, rowt + 2 * rp, j);
+            half_step<float, KI, CB, false>(opB, Vf, Sf, cS + rt * Wa * kRowsPerCta, gown, gown, dt, Wa,
+                                            Kp, rowt, rp, j);
+        }
         __syncthreads();
-        push_own_rows<float>(cluster, Sf, Wa, Kp, row0, cs, crank, 1);
+        push_own_rows<float>(cluster, Sf, Wa, Kp, row0, cs, crank, NRT);
         cluster.sync();
     }
 
     int bad = 0;
-    for (int idx = tid; idx < ncol * kRowsPerCta; idx += kThreads) {
-        const int c = idx / kRowsPerCta, rl = idx % kRowsPerCta, row = row0 + rl;
+    for (int idx = tid; idx < ncol * OWN; idx += kThreads) {
+        const int c = idx / OWN, ro = idx % OWN, row = row0 + ro;
+        const int ci = (ro / kRowsPerCta) * Wa * kRowsPerCta + c * kRowsPerCta + ro % kRowsPerCta;
         if (row < a.Kv) {
             const float x = Vf[(size_t)c * Kp + row];
             a.lamV[(size_t)(col0 + c) * a.Kv + row] = x;
-            a.compV[(size_t)(col0 + c) * a.Kv + row] = cV[c * kRowsPerCta + rl];
+            a.compV[(size_t)(col0 + c) * a.Kv + row] = cV[ci];
             bad |= !is_finite(x);
         }
         if (row < a.Ks) {
             const float x = Sf[(size_t)c * Kp + row];
             a.lamS[(size_t)(col0 + c) * a.Ks + row] = x;
-            a.compS[(size_t)(col0 + c) * a.Ks + row] = cS[c * kRowsPerCta + rl];
+            a.compS[(size_t)(col0 + c) * a.Ks + row] = cS[ci];
             bad |= !is_finite(x);
         }
     }

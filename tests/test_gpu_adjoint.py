@@ -57,7 +57,11 @@ def gpu_adjoint(R, h, p, V0, S0, ystar, N, ckpt):
 
 
 @pytest.mark.parametrize("Kv,Ks,M,R,N,ckpt", [(64, 64, 7, 3, 60, 0), (64, 64, 7, 3, 60, 16),
-                                               (200, 180, 20, 5, 100, 32), (512, 512, 9, 8, 40, 7)])
+                                               (200, 180, 20, 5, 100, 32), (512, 512, 9, 8, 40, 7),
+                                               # above K = 512: two 32-row tiles per CTA, the
+                                               # transposed operators read from L2
+                                               (640, 600, 11, 5, 36, 0), (1024, 1000, 6, 8, 40, 16),
+                                               (1000, 1024, 17, 3, 25, 9)])
 def test_adjoint_vs_oracle(rom, Kv, Ks, M, R, N, ckpt):
     p, V0, S0, ystar = case(Kv, Ks, M, R, N, seed=Kv + M)
     h = rom.Rom.from_problem(p)
@@ -139,6 +143,41 @@ def test_gradients_vs_fp64_finite_differences_workload4_shape(rom):
         fdS = (misfit(V0, S0 + step * D, T) - misfit(V0, S0 - step * D, T)) / (2 * step)
         assert abs(float(np.sum(gV * D)) - fdV) <= 1e-4 * abs(fdV), (np.sum(gV * D), fdV)
         assert abs(float(np.sum(gS * D)) - fdS) <= 1e-4 * abs(fdS), (np.sum(gS * D), fdS)
+
+
+def test_gradients_vs_fp64_finite_differences_k1024(rom):
+    """K = 1024 (the largest size rom_create takes): dL/dT_m and the V0, S0
+    gradients along a random direction against central differences of the
+    FP64 oracle's misfit, at 1e-4 relative."""
+    Kv = Ks = 1024
+    M, R, N = 3, 8, 60
+    p = inputs.make_problem(Kv, Ks, M, R, seed=77)
+    T = p.T.astype(np.float64)
+    Z = np.zeros((Kv, M))
+    _, _, ys = oracle.forward(p.Avs, p.Asv, p.g, p.C, p.dt, Z, Z, N, T=1.05 * T, r=1)
+    ystar = ys.astype(np.float32)
+    ys64 = ystar.astype(np.float64)
+    V0 = inputs.random_state(Kv, M, seed=5, scale=0.05).astype(np.float32).astype(np.float64)
+    S0 = inputs.random_state(Ks, M, seed=6, scale=0.05).astype(np.float32).astype(np.float64)
+    h = rom.Rom.from_problem(p)
+    loss, gV, gS, gT = gpu_adjoint(rom, h, p, V0, S0, ystar, N, 16)
+
+    def misfit(V0_, S0_, T_):
+        _, _, tr = oracle.forward(p.Avs, p.Asv, p.g, p.C, p.dt, V0_, S0_, N, T=T_, r=1)
+        return float(np.sum((tr - ys64) ** 2))
+
+    step = 1e-3
+    for m in range(M):
+        Tp, Tm = T.copy(), T.copy()
+        Tp[m] += step
+        Tm[m] -= step
+        fd = (misfit(V0, S0, Tp) - misfit(V0, S0, Tm)) / (2 * step)
+        assert abs(gT[m] - fd) <= 1e-4 * abs(fd), (m, gT[m], fd)
+    D = np.random.default_rng(8).standard_normal((Kv, M))
+    fdV = (misfit(V0 + step * D, S0, T) - misfit(V0 - step * D, S0, T)) / (2 * step)
+    fdS = (misfit(V0, S0 + step * D, T) - misfit(V0, S0 - step * D, T)) / (2 * step)
+    assert abs(float(np.sum(gV * D)) - fdV) <= 1e-4 * abs(fdV)
+    assert abs(float(np.sum(gS * D)) - fdS) <= 1e-4 * abs(fdS)
 
 
 def _with_T(p, T):
