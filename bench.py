@@ -511,7 +511,8 @@ def main():
         "cpu_baseline": cpu,
         "e2e": {"value": world * M * N / e2e_t, "unit": "sample-steps/s",
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-        "gpu_launches": args.steps,
+        # one split-kernel launch per step, plus its companion when the plan has one
+        "gpu_launches": args.steps * (2 if plan.get("variant") == 4 else 1),
         "clocks": clocks,
         "wall_s_timed_region": wall,
         "rank1": {"single_sample_steps_s": r1_single, "ensemble_sample_steps_s": r1_ens,
