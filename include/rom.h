@@ -321,9 +321,18 @@ rom_status rom_run_rank1_ensemble(rom_t h, void* V, void* S, const void* T, int 
  * rom_run_batched -- many ensembles at once: job i advances its handle's
  * model (any Kv, Ks <= 1024) for its M columns exactly as rom_run_rank2 would
  * with n0 = 0, and all jobs run in ONE launch of a CUDA graph on `stream`.
- * The scheduler gives every job a share of the GPU proportional to its work
- * per step, 4 K^2 M (the rank-2 GEMM cost of Sec. 2.5), which sets its columns
- * per cluster block, and issues the longest jobs first.  The graph is built
+ * With prec = ROM_FP32 (and no job carrying a reduced reference state) the
+ * graph holds one persistent launch per operator size class (jobs with the
+ * same padded size Kp): its clusters take (job, column block) items from a
+ * device work list, in the order a counter hands them out, until none are
+ * left; each class's block width and cluster count come from a step-time
+ * model, chosen so that the predicted finishing time of the slowest class is
+ * as small as the SMs allow.  Each column's arithmetic is the same as in
+ * rom_run_rank2 (bitwise equal results).  Otherwise, and when
+ * rom_autotune_batched measured it faster, the scheduler gives every job a
+ * share of the GPU proportional to its work per step, 4 K^2 M (the rank-2
+ * GEMM cost of Sec. 2.5), which sets its columns per cluster block, and
+ * issues the longest jobs first, one launch per job.  The graph is built
  * (captured and instantiated) on the first call for a given job list and
  * replayed afterwards.  Requirements: device buffers only, one job per
  * handle, traces (per job, optional) need r > 0 and receiver rows.
@@ -379,7 +388,8 @@ rom_status rom_run_rank3(const rom_t* handles, int nops, void* V, void* S, const
  * tensor-core jobs plan their own widths).  With prec = ROM_AUTO it also
  * tries the size thresholds 0 (every job BF16S), 256, 512 and none (every
  * job FP32), and with tensor-core jobs both the batch widths and the ones
- * the planner picks for a job alone; it keeps the fastest combination.  *best_us (may be
+ * the planner picks for a job alone; with ROM_FP32 it also times the
+ * work-list form; it keeps the fastest combination.  *best_us (may be
  * NULL) receives the chosen schedule's probe time per step.  Synchronous on
  * `stream`.  Errors as for rom_run_batched, plus ROM_E_NOMEM.
  */

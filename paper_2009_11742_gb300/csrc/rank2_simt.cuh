@@ -221,17 +221,14 @@ __device__ __forceinline__ void add_reference(T* __restrict__ Y, float* __restri
     }
 }
 
+// The one-block kernel's work on one column block: columns [gc0, gc0 + ncol)
+// of the caller's arrays, operator `gop` of the table (rank-3 launch) or the
+// launch's own operator (gop null).
 template <typename T, int KI, int CB, bool RESIDENT>
-__global__ void __launch_bounds__(kThreads, 1) rank2_simt_kernel(const Rank2Args a) {
-    cg::cluster_group cluster = cg::this_cluster();
+__device__ __forceinline__ void simt_body(cg::cluster_group& cluster, const Rank2Args& a,
+                                          const GroupOp* gop, const int gc0, const int ncol) {
     const int cs = (int)cluster.num_blocks();
     const int crank = (int)cluster.block_rank();
-    // rank-3 grouped launch: operator `job` of the table, column block `blk` of it
-    const int job = a.group ? (int)(blockIdx.x / cs) / a.group_cpj : 0;
-    const int blk = a.group ? (int)(blockIdx.x / cs) % a.group_cpj : (int)(blockIdx.x / cs);
-    const GroupOp* gop = a.group ? a.group + job : nullptr;
-    const int col0 = blk * a.Wv;                 // first column of this block (within the job)
-    const int ncol = min(a.Wv, a.M - col0);      // valid columns
     const int Wa = a.Wa;
     const int Kp = a.Kp;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -257,7 +254,6 @@ __global__ void __launch_bounds__(kThreads, 1) rank2_simt_kernel(const Rank2Args
 
     const T* __restrict__ Vin = static_cast<const T*>(a.V);
     const T* __restrict__ Sin = static_cast<const T*>(a.S);
-    const int gc0 = a.col_base + job * a.M + col0;  // first column in the caller's arrays
 
     // ---- load the column block (all rows) and the per-CTA constants
     for (int idx = tid; idx < Wa * Kp; idx += kThreads) {
@@ -388,6 +384,65 @@ __global__ void __launch_bounds__(kThreads, 1) rank2_simt_kernel(const Rank2Args
     }
     bad = __syncthreads_or(bad);
     if (bad && tid == 0 && a.status) atomicCAS(a.status, 0, (int)6 /* ROM_E_NONFINITE */);
+}
+
+template <typename T, int KI, int CB, bool RESIDENT>
+__global__ void __launch_bounds__(kThreads, 1) rank2_simt_kernel(const Rank2Args a) {
+    cg::cluster_group cluster = cg::this_cluster();
+    const int cs = (int)cluster.num_blocks();
+    // rank-3 grouped launch: operator `job` of the table, column block `blk` of it
+    const int job = a.group ? (int)(blockIdx.x / cs) / a.group_cpj : 0;
+    const int blk = a.group ? (int)(blockIdx.x / cs) % a.group_cpj : (int)(blockIdx.x / cs);
+    const GroupOp* gop = a.group ? a.group + job : nullptr;
+    const int col0 = blk * a.Wv;                 // first column of this block (within the job)
+    const int ncol = min(a.Wv, a.M - col0);      // valid columns
+    simt_body<T, KI, CB, RESIDENT>(cluster, a, gop, a.col_base + job * a.M + col0, ncol);
+}
+
+// Work-list launch of the batched scheduler (FP32): the clusters take
+// (job, column block) items from a.items in the order a global counter
+// hands them out, each job with its own operator, state, periods, traces
+// and constants from the table a.group, until none are left.
+template <int KI, int CB, bool RESIDENT>
+__global__ void __launch_bounds__(kThreads, 1) rank2_simt_worklist_kernel(const Rank2Args a) {
+    cg::cluster_group cluster = cg::this_cluster();
+    const int cs = (int)cluster.num_blocks();
+    const int crank = (int)cluster.block_rank();
+    __shared__ int s_item;
+    for (;;) {
+        if (crank == 0 && threadIdx.x == 0) {
+            const int k = atomicAdd(a.item_counter, 1);
+            for (int r = 0; r < cs; ++r) *cluster.map_shared_rank(&s_item, r) = k;
+        }
+        cluster.sync();
+        const int k = s_item;
+        if (k >= a.nitems) break;
+        const WorkItem wi = a.items[k];
+        const GroupOp* gop = a.group + wi.job;
+        Rank2Args aj = a;
+        aj.Avs_rm = gop->Avs_rm;
+        aj.Asv_rm = gop->Asv_rm;
+        aj.g_p = gop->g_p;
+        aj.C_p = gop->C_p;
+        aj.V = gop->V;
+        aj.S = gop->S;
+        aj.Tper = gop->Tper;
+        aj.traces = gop->traces;
+        aj.status = gop->status;
+        aj.dt = gop->dt;
+        aj.Kv = gop->Kv;
+        aj.Ks = gop->Ks;
+        aj.R = gop->R;
+        aj.rpc = gop->rpc;
+        aj.M = gop->M;
+        aj.Mtot = gop->M;
+        aj.wavelet = gop->wavelet;
+        aj.col_base = 0;
+        aj.group = nullptr;
+        simt_body<float, KI, CB, RESIDENT>(cluster, aj, nullptr, wi.col0, min(a.Wv, wi.ncol));
+        // every CTA has read the slot and finished the item before the next fetch
+        cluster.sync();
+    }
 }
 
 }  // namespace romk

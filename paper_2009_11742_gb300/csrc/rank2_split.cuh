@@ -212,14 +212,15 @@ __device__ __forceinline__ void split_traces(const float* __restrict__ Cown, con
     }
 }
 
-// MODE: 0 plain; 1 adds the reduced reference state (a.Xv / a.Xs); 2 is the
-// rank-3 grouped launch (operator table a.group).  A template parameter, so
-// that each instance compiles to exactly the code its runs need.
+// The split kernel's work on one item: column blocks A = [gc0_0, gc0_0 + nc0)
+// and B = [gc0_0 + Wv, gc0_0 + Wv + nc1) of the caller's arrays, operator
+// `gop` of the table (MODE 2) or the launch's own operator.
 template <int KI, int MODE>
-__global__ void __launch_bounds__(kThreads, 1) rank2_split_kernel(const Rank2Args a) {
+__device__ __forceinline__ void split_body(cg::cluster_group& cluster, const Rank2Args& a,
+                                           const GroupOp* gop, const int gc0_0, const int nc0,
+                                           const int nc1) {
     constexpr bool XR = MODE == 1;
     constexpr bool GROUPED = MODE == 2;
-    cg::cluster_group cluster = cg::this_cluster();
     const int cs = (int)cluster.num_blocks();
     const int H = cs / 2;
     const int crank = (int)cluster.block_rank();
@@ -227,10 +228,6 @@ __global__ void __launch_bounds__(kThreads, 1) rank2_split_kernel(const Rank2Arg
     const int s = vrole ? crank : crank - H;  // row slab
     const int row0 = s * kSplitRows;
     const int peer0 = vrole ? H : 0;          // first CTA of the other role
-    // rank-3 grouped launch: operator `job` of the table, cluster `clu` of it
-    const int job = GROUPED ? (int)(blockIdx.x / cs) / a.group_cpj : 0;
-    const int clu = GROUPED ? (int)(blockIdx.x / cs) % a.group_cpj : (int)(blockIdx.x / cs);
-    const GroupOp* gop = GROUPED ? a.group + job : nullptr;
     const int Wa = a.Wa, Kp = a.Kp;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int j = lane & 15;
@@ -250,11 +247,7 @@ __global__ void __launch_bounds__(kThreads, 1) rank2_split_kernel(const Rank2Arg
 
     // column ranges of the two blocks, kept in scalars so that runtime block
     // indices do not force a local-memory array
-    const int gc0_0 = a.col_base + job * a.M + (2 * clu) * a.Wv;
     const int gc0_1 = gc0_0 + a.Wv;
-    const int nr0 = a.M - (2 * clu) * a.Wv, nr1 = nr0 - a.Wv;
-    const int nc0 = nr0 < 0 ? 0 : (nr0 > a.Wv ? a.Wv : nr0);
-    const int nc1 = nr1 < 0 ? 0 : (nr1 > a.Wv ? a.Wv : nr1);
     auto gc0 = [&](int b) { return b ? gc0_1 : gc0_0; };
     auto ncol = [&](int b) { return b ? nc1 : nc0; };
 
@@ -384,6 +377,69 @@ __global__ void __launch_bounds__(kThreads, 1) rank2_split_kernel(const Rank2Arg
     }
     bad = __syncthreads_or(bad);
     if (bad && tid == 0 && a.status) atomicCAS(a.status, 0, 6 /* ROM_E_NONFINITE */);
+}
+
+
+// MODE: 0 plain; 1 adds the reduced reference state (a.Xv / a.Xs); 2 is the
+// rank-3 grouped launch (operator table a.group); 3 is the work-list launch
+// of the batched scheduler: the clusters take (job, column range) items from
+// a.items in the order a global counter hands them out, each job with its
+// own operator, state, periods, traces and constants from the table, until
+// none are left.  A template parameter, so that each instance compiles to
+// exactly the code its runs need.
+template <int KI, int MODE>
+__global__ void __launch_bounds__(kThreads, 1) rank2_split_kernel(const Rank2Args a) {
+    cg::cluster_group cluster = cg::this_cluster();
+    const int cs = (int)cluster.num_blocks();
+    if constexpr (MODE == 3) {
+        __shared__ int s_item;
+        const int crank = (int)cluster.block_rank();
+        for (;;) {
+            if (crank == 0 && threadIdx.x == 0) {
+                const int k = atomicAdd(a.item_counter, 1);
+                for (int r = 0; r < cs; ++r) *cluster.map_shared_rank(&s_item, r) = k;
+            }
+            cluster.sync();
+            const int k = s_item;
+            if (k >= a.nitems) break;
+            const WorkItem wi = a.items[k];
+            const GroupOp* gop = a.group + wi.job;
+            Rank2Args aj = a;
+            aj.Avs_rm = gop->Avs_rm;
+            aj.Asv_rm = gop->Asv_rm;
+            aj.g_p = gop->g_p;
+            aj.C_p = gop->C_p;
+            aj.V = gop->V;
+            aj.S = gop->S;
+            aj.Tper = gop->Tper;
+            aj.traces = gop->traces;
+            aj.status = gop->status;
+            aj.dt = gop->dt;
+            aj.Kv = gop->Kv;
+            aj.Ks = gop->Ks;
+            aj.R = gop->R;
+            aj.rpc = gop->rpc;
+            aj.M = gop->M;
+            aj.Mtot = gop->M;
+            aj.wavelet = gop->wavelet;
+            aj.col_base = 0;
+            const int nc0 = min(a.Wv, wi.ncol);
+            const int nc1 = max(0, min(a.Wv, wi.ncol - a.Wv));
+            split_body<KI, 0>(cluster, aj, nullptr, wi.col0, nc0, nc1);
+            // every CTA has read the slot and finished the item before the next fetch
+            cluster.sync();
+        }
+    } else {
+        // rank-3 grouped launch: operator `job` of the table, cluster `clu` of it
+        const int job = MODE == 2 ? (int)(blockIdx.x / cs) / a.group_cpj : 0;
+        const int clu = MODE == 2 ? (int)(blockIdx.x / cs) % a.group_cpj : (int)(blockIdx.x / cs);
+        const GroupOp* gop = MODE == 2 ? a.group + job : nullptr;
+        const int gc0_0 = a.col_base + job * a.M + (2 * clu) * a.Wv;
+        const int nr0 = a.M - (2 * clu) * a.Wv, nr1 = nr0 - a.Wv;
+        const int nc0 = nr0 < 0 ? 0 : (nr0 > a.Wv ? a.Wv : nr0);
+        const int nc1 = nr1 < 0 ? 0 : (nr1 > a.Wv ? a.Wv : nr1);
+        split_body<KI, MODE>(cluster, a, gop, gc0_0, nc0, nc1);
+    }
 }
 
 }  // namespace romk

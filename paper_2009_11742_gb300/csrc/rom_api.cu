@@ -1048,18 +1048,31 @@ struct BatchKey {
     bool operator<(const BatchKey& o) const { return words < o.words; }
 };
 std::mutex g_batch_mu;
-std::map<BatchKey, cudaGraphExec_t> g_batch_graphs;
+// A captured batch: the graph, and the device tables of its work-list
+// launches (operator/job tables, items, counters), freed with it.
+struct BatchGraph {
+    cudaGraphExec_t exec = nullptr;
+    void* tables = nullptr;
+};
+void free_batch_graph(BatchGraph& g) {
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+    if (g.tables) cudaFree(g.tables);
+    g = BatchGraph{};
+}
+std::map<BatchKey, BatchGraph> g_batch_graphs;
 std::vector<cudaStream_t> g_batch_streams;
 std::vector<cudaEvent_t> g_batch_events;
 cudaStream_t g_capture_stream = nullptr;  // private: the caller's stream may be the legacy one
 
-// Cluster-budget scale (and, for ROM_AUTO, the size threshold) chosen by
-// rom_autotune_batched, per job list (handles and widths; buffers and step
-// counts do not change the choice).  Keys: (njobs, prec, device), then
-// (handle, M) per job.
+// Cluster-budget scale (and, for ROM_AUTO, the size threshold; for
+// ROM_FP32 the choice between the work-list form, 1, and one launch per job,
+// 0) chosen by rom_autotune_batched, per job list (handles and widths;
+// buffers and step counts do not change the choice).  Keys: (njobs, prec,
+// device), then (handle, M) per job.
 std::map<std::vector<uintptr_t>, double> g_batch_scale;
 std::map<std::vector<uintptr_t>, int> g_batch_kthr;
 std::map<std::vector<uintptr_t>, int> g_batch_tcw;
+std::map<std::vector<uintptr_t>, int> g_batch_wl;
 
 void drop_batch_graphs(rom_s* h) {
     std::lock_guard<std::mutex> lk(g_batch_mu);
@@ -1074,12 +1087,14 @@ void drop_batch_graphs(rom_s* h) {
         it = tuned_for_h(it->first) ? g_batch_kthr.erase(it) : std::next(it);
     for (auto it = g_batch_tcw.begin(); it != g_batch_tcw.end();)
         it = tuned_for_h(it->first) ? g_batch_tcw.erase(it) : std::next(it);
+    for (auto it = g_batch_wl.begin(); it != g_batch_wl.end();)
+        it = tuned_for_h(it->first) ? g_batch_wl.erase(it) : std::next(it);
     for (auto it = g_batch_graphs.begin(); it != g_batch_graphs.end();) {
         bool uses = false;
         const auto& w = it->first.words;
         for (size_t k = 6; k < w.size(); k += 6) uses |= (w[k] == (uintptr_t)h);
         if (uses) {
-            cudaGraphExecDestroy(it->second);
+            free_batch_graph(it->second);
             it = g_batch_graphs.erase(it);
         } else {
             ++it;
@@ -1127,9 +1142,244 @@ static int batch_tc_width(int prec, int M) {
     return M <= 64 ? 64 : 128;
 }
 
+// ---- work-list batched launch (FP32): one persistent launch per operator
+// size class.  Jobs are grouped by padded size Kp (the split kernel for
+// Kp <= 512, the one-block kernel above); a class's clusters take
+// (job, column range) items from a device list in the order a counter hands
+// them out, so no cluster idles while items are left.  Widths and cluster
+// counts come from a step-time model, microseconds per leapfrog step of one
+// item: split kernel 2.24 + 0.466 W Kp/512 (two W-column blocks per item),
+// one-block kernel 3.5 + 1.39 W Kp/1024 (one block per item), fitted on
+// GB300.  A binary search finds the smallest predicted makespan T for which
+// every class, at its best width, needs at most the device's SMs in total:
+// a class with items(W) items of time t(W) needs ceil(items / floor(T / t))
+// clusters.
+struct WLClass {
+    int Kp = 0;
+    bool split = true;
+    std::vector<int> jobs;
+    int rpc_max = 0;
+    int W = 0, ncl = 0, nitems = 0;
+    Rank2Plan plan;
+};
+
+static double wl_step_us(bool split, int Kp, int W) {
+    return split ? 2.24 + 0.466 * W * (Kp / 512.0) : 3.5 + 1.39 * W * (Kp / 1024.0);
+}
+
+static int wl_items(const WLClass& c, const rom_job* jobs, int W) {
+    const int per = c.split ? 2 * W : W;
+    int n = 0;
+    for (int i : c.jobs) n += (jobs[i].M + per - 1) / per;
+    return n;
+}
+
+static rom_status run_batched_worklist(const rom_job* jobs, int njobs, int nsteps, int r,
+                                       cudaStream_t st, int dev, int nsm) {
+    BatchKey key;
+    key.words = {(uintptr_t)njobs, (uintptr_t)nsteps, (uintptr_t)r, (uintptr_t)ROM_FP32, (uintptr_t)st,
+                 (uintptr_t)dev};
+    for (int i = 0; i < njobs; ++i) {
+        const rom_job& j = jobs[i];
+        key.words.insert(key.words.end(), {(uintptr_t)j.h, (uintptr_t)j.V, (uintptr_t)j.S,
+                                           (uintptr_t)j.T, (uintptr_t)j.M, (uintptr_t)j.traces});
+    }
+    key.words.push_back((uintptr_t)0x574c);  // work-list form
+    std::lock_guard<std::mutex> lk(g_batch_mu);
+    auto it = g_batch_graphs.find(key);
+    if (it == g_batch_graphs.end()) {
+        // ---- size classes
+        std::map<int, WLClass> byK;
+        for (int i = 0; i < njobs; ++i) {
+            const rom_s* h = jobs[i].h;
+            WLClass& c = byK[h->Kp];
+            c.Kp = h->Kp;
+            c.split = h->Kp <= 512;
+            c.jobs.push_back(i);
+            const int cs = c.split ? h->Kp / 32 : h->Kp / 64;
+            const int H = c.split ? cs / 2 : cs;
+            const int rpc = (h->R + H - 1) / H;
+            c.rpc_max = rpc > c.rpc_max ? rpc : c.rpc_max;
+        }
+        std::vector<WLClass> cls;
+        for (auto& kv : byK) cls.push_back(kv.second);
+        // widths each class can take, with their co-resident cluster limits
+        struct Cand { int W, items, maxact; double t; };
+        std::vector<std::vector<Cand>> cands(cls.size());
+        for (size_t c = 0; c < cls.size(); ++c) {
+            const int step = cls[c].split ? 4 : 8;
+            for (int W = step; W <= 256; W += step) {
+                Rank2Plan p;
+                const bool ok = cls[c].split ? plan_worklist_split(cls[c].Kp, cls[c].rpc_max, W, 1, &p)
+                                             : plan_worklist_simt(cls[c].Kp, cls[c].rpc_max, W, 1, &p);
+                if (!ok) break;
+                cands[c].push_back({W, wl_items(cls[c], jobs, W), p.max_active_clusters,
+                                    wl_step_us(cls[c].split, cls[c].Kp, W)});
+                cls[c].plan = p;  // cluster size and kernel (the width is set below)
+            }
+            if (cands[c].empty()) {
+                snprintf(g_last_error, sizeof(g_last_error), "no work-list plan for Kp=%d", cls[c].Kp);
+                return ROM_E_UNSUPPORTED;
+            }
+        }
+        // the fewest SMs class c needs to finish within T (INT_MAX: cannot)
+        auto need = [&](size_t c, double T, int* Wout, int* nout) {
+            long best = 1L << 40;
+            for (const Cand& k : cands[c]) {
+                if (k.t > T) continue;
+                const long rounds = (long)(T / k.t);
+                long n = (k.items + rounds - 1) / rounds;
+                if (n < 1) n = 1;
+                if (n > k.maxact || n > k.items) continue;
+                const long sms = n * (long)cls[c].plan.cs;
+                if (sms < best) {
+                    best = sms;
+                    *Wout = k.W;
+                    *nout = (int)n;
+                }
+            }
+            return best;
+        };
+        double lo = 0.0, hi = 1e9;
+        for (int iter = 0; iter < 60; ++iter) {
+            const double mid = 0.5 * (lo + hi);
+            long tot = 0;
+            int w, n;
+            for (size_t c = 0; c < cls.size(); ++c) tot += need(c, mid, &w, &n);
+            if (tot <= nsm) hi = mid;
+            else lo = mid;
+        }
+        for (size_t c = 0; c < cls.size(); ++c) {
+            int w = 0, n = 0;
+            if (need(c, hi, &w, &n) >= (1L << 40)) return ROM_E_UNSUPPORTED;
+            cls[c].W = w;
+            cls[c].ncl = n;
+            cls[c].nitems = wl_items(cls[c], jobs, w);
+            Rank2Plan p;
+            const bool ok = cls[c].split ? plan_worklist_split(cls[c].Kp, cls[c].rpc_max, w, n, &p)
+                                         : plan_worklist_simt(cls[c].Kp, cls[c].rpc_max, w, n, &p);
+            if (!ok) return ROM_E_UNSUPPORTED;
+            cls[c].plan = p;
+        }
+        // ---- device tables: counters, then per class its job table and items
+        size_t bytes = 256;
+        std::vector<size_t> off_ops(cls.size()), off_items(cls.size());
+        for (size_t c = 0; c < cls.size(); ++c) {
+            off_ops[c] = bytes;
+            bytes += ((sizeof(GroupOp) * cls[c].jobs.size() + 255) / 256) * 256;
+            off_items[c] = bytes;
+            bytes += ((sizeof(WorkItem) * cls[c].nitems + 255) / 256) * 256;
+        }
+        std::vector<unsigned char> host(bytes, 0);
+        for (size_t c = 0; c < cls.size(); ++c) {
+            GroupOp* ops = reinterpret_cast<GroupOp*>(host.data() + off_ops[c]);
+            WorkItem* items = reinterpret_cast<WorkItem*>(host.data() + off_items[c]);
+            const int cs = cls[c].plan.cs;
+            const int H = cls[c].split ? cs / 2 : cs;
+            const int per = cls[c].split ? 2 * cls[c].W : cls[c].W;
+            int n = 0;
+            for (size_t q = 0; q < cls[c].jobs.size(); ++q) {
+                const rom_job& j = jobs[cls[c].jobs[q]];
+                rom_s* h = j.h;
+                GroupOp& g = ops[q];
+                g.Avs_rm = h->Avs_rm[1];
+                g.Asv_rm = h->Asv_rm[1];
+                g.g_p = h->g_p[1];
+                g.C_p = h->C_rm[1];
+                g.V = j.V;
+                g.S = j.S;
+                g.Tper = j.T;
+                g.traces = j.traces;
+                g.status = h->status;
+                g.dt = h->dt;
+                g.Kv = h->Kv;
+                g.Ks = h->Ks;
+                g.R = h->R;
+                g.M = j.M;
+                g.wavelet = h->wavelet;
+                g.rpc = (h->R + H - 1) / H;
+                for (int col = 0; col < j.M; col += per)
+                    items[n++] = {(int)q, col, j.M - col < per ? j.M - col : per, 0};
+            }
+        }
+        void* tables = nullptr;
+        ROM_CUDA(cudaMalloc(&tables, bytes));
+        cudaError_t e = cudaMemcpy(tables, host.data(), bytes, cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) {
+            cudaFree(tables);
+            return cuda_fail(e, "rom_run_batched work list");
+        }
+        // ---- capture: reset the counters, then every class on its own stream,
+        // the classes with the largest clusters issued first
+        std::vector<size_t> order(cls.size());
+        for (size_t c = 0; c < cls.size(); ++c) order[c] = c;
+        std::sort(order.begin(), order.end(), [&](size_t x, size_t y) { return cls[x].plan.cs > cls[y].plan.cs; });
+        const size_t npool = cls.size() < 32 ? cls.size() : 32;
+        rom_status s = batch_streams(npool);
+        if (s != ROM_OK) {
+            cudaFree(tables);
+            return s;
+        }
+        cudaGraph_t graph = nullptr;
+        cudaStream_t cap = g_capture_stream;
+        e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeRelaxed);
+        if (e == cudaSuccess) e = cudaMemsetAsync(tables, 0, 256, cap);
+        cudaEvent_t fork = g_batch_events[npool];
+        if (e == cudaSuccess) e = cudaEventRecord(fork, cap);
+        for (size_t k = 0; k < npool && e == cudaSuccess; ++k) e = cudaStreamWaitEvent(g_batch_streams[k], fork, 0);
+        for (size_t oi = 0; oi < order.size() && e == cudaSuccess; ++oi) {
+            const size_t c = order[oi];
+            const rom_s* h0 = jobs[cls[c].jobs[0]].h;
+            Rank2Args a = {};
+            a.Avs_rm = h0->Avs_rm[1];
+            a.Asv_rm = h0->Asv_rm[1];
+            a.g_p = h0->g_p[1];
+            a.C_p = h0->C_rm[1];
+            a.status = h0->status;
+            a.dt = h0->dt;
+            a.Kv = h0->Kv;
+            a.Ks = h0->Ks;
+            a.Kp = cls[c].Kp;
+            a.R = h0->R;
+            a.M = jobs[cls[c].jobs[0]].M;
+            a.Mtot = a.M;
+            a.nsteps = nsteps;
+            a.r = r > 0 ? r : 1;
+            a.rpc = cls[c].rpc_max;
+            a.spin_limit = h0->wait_limit;
+            a.group = reinterpret_cast<const GroupOp*>(static_cast<unsigned char*>(tables) + off_ops[c]);
+            a.items = reinterpret_cast<const WorkItem*>(static_cast<unsigned char*>(tables) + off_items[c]);
+            a.nitems = cls[c].nitems;
+            a.item_counter = static_cast<int*>(tables) + c;
+            cudaStream_t ss = g_batch_streams[oi % npool];
+            e = cls[c].split ? launch_rank2_split_f32(a, cls[c].plan, ss)
+                             : launch_rank2_simt_worklist_f32(a, cls[c].plan, ss);
+        }
+        for (size_t k = 0; k < npool && e == cudaSuccess; ++k) {
+            e = cudaEventRecord(g_batch_events[k], g_batch_streams[k]);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(cap, g_batch_events[k], 0);
+        }
+        cudaError_t e2 = cudaStreamEndCapture(cap, &graph);
+        if (e == cudaSuccess) e = e2;
+        cudaGraphExec_t exec = nullptr;
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
+        if (graph) cudaGraphDestroy(graph);
+        if (e != cudaSuccess) {
+            cudaFree(tables);
+            return cuda_fail(e, "rom_run_batched work-list capture");
+        }
+        it = g_batch_graphs.emplace(key, BatchGraph{exec, tables}).first;
+    }
+    ROM_CUDA(cudaGraphLaunch(it->second.exec, st));
+    return ROM_OK;
+}
+
 // tcw: tensor-core block widths, 1 = batch_tc_width, 0 = the planner's.
+// wl: 1 = FP32 batches run as work-list launches (one per size class), 0 =
+// one launch per job.
 static rom_status run_batched_impl(const rom_job* jobs, int njobs, int nsteps, int r, int prec,
-                                   void* stream, double scale, int kthr = kAutoKthr, int tcw = 1) {
+                                   void* stream, double scale, int kthr = kAutoKthr, int tcw = 1,
+                                   int wl = 1) {
     if (!jobs || njobs < 1 || nsteps < 0 || r < 0 || !batch_prec(prec)) return ROM_E_INVAL;
     for (int i = 0; i < njobs; ++i) {
         const rom_job& j = jobs[i];
@@ -1152,6 +1402,11 @@ static rom_status run_batched_impl(const rom_job* jobs, int njobs, int nsteps, i
     int dev = 0, nsm = 0;
     ROM_CUDA(cudaGetDevice(&dev));
     ROM_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    if (wl && prec == ROM_FP32) {
+        bool ok = true;
+        for (int i = 0; i < njobs; ++i) ok = ok && jobs[i].h->xref_M == 0 && jobs[i].h->Kp <= 1024;
+        if (ok) return run_batched_worklist(jobs, njobs, nsteps, r, st, dev, nsm);
+    }
     // share of the SMs per job, proportional to its work per step
     std::vector<double> cost(njobs);
     double total = 0.0;
@@ -1250,16 +1505,16 @@ static rom_status run_batched_impl(const rom_job* jobs, int njobs, int nsteps, i
         e = cudaGraphInstantiate(&exec, graph, 0);
         cudaGraphDestroy(graph);
         if (e != cudaSuccess) return cuda_fail(e, "rom_run_batched instantiate");
-        it = g_batch_graphs.emplace(key, exec).first;
+        it = g_batch_graphs.emplace(key, BatchGraph{exec, nullptr}).first;
     }
-    ROM_CUDA(cudaGraphLaunch(it->second, st));
+    ROM_CUDA(cudaGraphLaunch(it->second.exec, st));
     if (any_tc) {
         // tensor-core jobs use per-handle workspaces that a later call may
         // reallocate: their graphs are not kept
-        cudaGraphExec_t exec = it->second;
+        BatchGraph g = it->second;
         g_batch_graphs.erase(it);
         ROM_CUDA(cudaStreamSynchronize(st));
-        cudaGraphExecDestroy(exec);
+        free_batch_graph(g);
     }
     return ROM_OK;
 }
@@ -1277,7 +1532,7 @@ static std::vector<uintptr_t> batch_tune_key(const rom_job* jobs, int njobs, int
 
 rom_status rom_run_batched(const rom_job* jobs, int njobs, int nsteps, int r, int prec, void* stream) {
     double scale = 1.0;
-    int kthr = kAutoKthr, tcw = 1;
+    int kthr = kAutoKthr, tcw = 1, wl = 1;
     if (jobs && njobs > 0) {
         for (int i = 0; i < njobs; ++i)
             if (!jobs[i].h) return ROM_E_INVAL;
@@ -1289,8 +1544,10 @@ rom_status rom_run_batched(const rom_job* jobs, int njobs, int nsteps, int r, in
         if (kt != g_batch_kthr.end()) kthr = kt->second;
         auto tw = g_batch_tcw.find(key);
         if (tw != g_batch_tcw.end()) tcw = tw->second;
+        auto wt = g_batch_wl.find(key);
+        if (wt != g_batch_wl.end()) wl = wt->second;
     }
-    return run_batched_impl(jobs, njobs, nsteps, r, prec, stream, scale, kthr, tcw);
+    return run_batched_impl(jobs, njobs, nsteps, r, prec, stream, scale, kthr, tcw, wl);
 }
 
 rom_status rom_autotune_batched(const rom_job* jobs, int njobs, int prec, int probe_steps,
@@ -1335,19 +1592,22 @@ rom_status rom_autotune_batched(const rom_job* jobs, int njobs, int prec, int pr
     // tensor-core block widths: the batch rule (1) and the planner's (0)
     const int ntw = (prec == ROM_AUTO || tc_prec(prec)) ? 2 : 1;
     double best = -1.0, best_scale = 1.0;
-    int best_kthr = kAutoKthr, best_tcw = 1;
+    int best_kthr = kAutoKthr, best_tcw = 1, best_wl = 0;
     rom_status rs = ROM_OK;
+    // FP32: the work-list form (one candidate) besides one launch per job
+    const int nwl = prec == ROM_FP32 ? 2 : 1;
+    for (int wl = nwl - 1; wl >= 0 && e == cudaSuccess && rs == ROM_OK; --wl)
     for (int t = 0; t < nk && e == cudaSuccess && rs == ROM_OK; ++t) {
         for (int tw = 0; tw < ntw && e == cudaSuccess && rs == ROM_OK; ++tw) {
             const int tcw = 1 - tw;
-            for (int c = 0; c < 4 && e == cudaSuccess && rs == ROM_OK; ++c) {
+            for (int c = 0; c < (wl ? 1 : 4) && e == cudaSuccess && rs == ROM_OK; ++c) {
                 float ms = 0.f;
                 for (int pass = 0; pass < 2 && e == cudaSuccess && rs == ROM_OK; ++pass) {  // warm-up, timed
                     const int n = pass == 0 ? (probe_steps < 20 ? probe_steps : 20) : probe_steps;
                     e = cudaEventRecord(e0, st);
                     if (e == cudaSuccess)
                         rs = run_batched_impl(sj.data(), njobs, n, 0, prec, stream, scales[c],
-                                              prec == ROM_AUTO ? kthrs[t] : kAutoKthr, tcw);
+                                              prec == ROM_AUTO ? kthrs[t] : kAutoKthr, tcw, wl);
                     if (e == cudaSuccess && rs == ROM_OK) e = cudaEventRecord(e1, st);
                     if (e == cudaSuccess && rs == ROM_OK) e = cudaEventSynchronize(e1);
                     if (e == cudaSuccess && rs == ROM_OK) e = cudaEventElapsedTime(&ms, e0, e1);
@@ -1359,6 +1619,7 @@ rom_status rom_autotune_batched(const rom_job* jobs, int njobs, int prec, int pr
                         best_scale = scales[c];
                         best_kthr = prec == ROM_AUTO ? kthrs[t] : kAutoKthr;
                         best_tcw = tcw;
+                        best_wl = wl;
                     }
                 }
             }
@@ -1374,7 +1635,7 @@ rom_status rom_autotune_batched(const rom_job* jobs, int njobs, int prec, int pr
             for (uintptr_t w : it->first.words)
                 for (void* b : bufs) uses |= (w == (uintptr_t)b);
             if (uses) {
-                cudaGraphExecDestroy(it->second);
+                free_batch_graph(it->second);
                 it = g_batch_graphs.erase(it);
             } else {
                 ++it;
@@ -1389,6 +1650,7 @@ rom_status rom_autotune_batched(const rom_job* jobs, int njobs, int prec, int pr
         g_batch_scale[batch_tune_key(jobs, njobs, prec)] = best_scale;
         if (prec == ROM_AUTO) g_batch_kthr[batch_tune_key(jobs, njobs, prec)] = best_kthr;
         g_batch_tcw[batch_tune_key(jobs, njobs, prec)] = best_tcw;
+        g_batch_wl[batch_tune_key(jobs, njobs, prec)] = best_wl;
     }
     if (best_us) *best_us = best;
     return ROM_OK;

@@ -22,6 +22,22 @@ struct GroupOp {
     const void* Asv_rm;
     const void* g_p;
     const void* C_p;
+    // work-list launches only (the batched scheduler): the job's own state,
+    // periods, traces, status word and constants
+    void* V;
+    void* S;
+    const void* Tper;
+    void* traces;
+    int* status;
+    double dt;
+    int Kv, Ks, R, M, wavelet, rpc;
+};
+
+// One item of a work-list launch: columns [col0, col0 + ncol) of job `job` of
+// the operator table (the split kernel's two column blocks, or the one-block
+// kernel's one).
+struct WorkItem {
+    int job, col0, ncol, pad;
 };
 
 struct Rank2Args {
@@ -61,6 +77,12 @@ struct Rank2Args {
     const GroupOp* group;
     int group_cpj;
     int c_global;          // one-block kernel: read receiver rows from C_p instead of shared memory
+    // work-list launch: clusters take items from `items` (nitems of them) in
+    // the order a global counter hands them out; the operator table `group`
+    // then also carries each job's state and constants.  Null: off.
+    const WorkItem* items;
+    int nitems;
+    int* item_counter;
 };
 
 // Launch plan chosen by the host for a rank-2 call.
@@ -96,6 +118,15 @@ bool plan_rank2_simt_f64(int Kp, int M, int R, bool rank1, Rank2Plan* plan, int 
 bool plan_rank2_split_f32(int Kp, int M, int R, Rank2Plan* plan, int cluster_budget = 0);
 bool plan_rank2_dataflow_f32(int Kp, int M, int R, Rank2Plan* plan);
 cudaError_t launch_rank2_split_f32(const Rank2Args& a, const Rank2Plan& plan, cudaStream_t st);
+// Work-list launch of the one-block kernel (FP32, the batched scheduler);
+// the split kernel's work-list form is launched by launch_rank2_split_f32
+// when a.items is set.  a.rpc: the jobs' largest rows of C per CTA.
+cudaError_t launch_rank2_simt_worklist_f32(const Rank2Args& a, const Rank2Plan& plan, cudaStream_t st);
+// Work-list plans with W columns per column block and ncl clusters (false if
+// the width does not fit): the split kernel (Kp <= 512) and the one-block
+// kernel (512 < Kp <= 1024); rpc_max sizes the receiver-row staging.
+bool plan_worklist_split(int Kp, int rpc_max, int W, int ncl, Rank2Plan* plan);
+bool plan_worklist_simt(int Kp, int rpc_max, int W, int ncl, Rank2Plan* plan);
 
 // Streaming companion of the split kernel (FP32, Kp <= 512, clusters of 2
 // or 4 CTAs, at most 4 columns per cluster; operators streamed from L2).
