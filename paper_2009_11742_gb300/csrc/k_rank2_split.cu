@@ -9,15 +9,14 @@
 namespace romk {
 
 // mode: the split kernel instance (0 plain, 1 with the reduced reference
-// state, 2 rank-3 grouped, 3 work list); the dataflow kernel tests for the
-// reference state at run time and has neither a grouped nor a work-list form.
+// state, 2 rank-3 grouped); the dataflow kernel tests for the reference
+// state at run time and has no grouped form.
 template <bool DF>
 static void* two_block_kernel(int KI, int mode = 0) {
 #define ROM_TB_CASE(k)                                                              \
     case k:                                                                         \
         return DF ? (void*)&rank2_dataflow_kernel<k>                                \
-                  : (mode == 3   ? (void*)&rank2_split_kernel<k, 3>                 \
-                     : mode == 2 ? (void*)&rank2_split_kernel<k, 2>                 \
+                  : (mode == 2   ? (void*)&rank2_split_kernel<k, 2>                 \
                      : mode == 1 ? (void*)&rank2_split_kernel<k, 1>                 \
                                  : (void*)&rank2_split_kernel<k, 0>);
     switch (KI) {
@@ -79,9 +78,8 @@ static cudaError_t launch_two_block(const Rank2Args& a_in, const Rank2Plan& p, c
     const int H = p.cs / 2;
     a.rpc = (a.R + H - 1) / H;
     if (DF && a.group) return cudaErrorInvalidValue;
-    const int mode = a.items ? 3 : a.group ? 2 : (a.Xv != nullptr || a.Xs != nullptr ? 1 : 0);
-    if (a.group && mode >= 2 && (a.Xv || a.Xs)) return cudaErrorInvalidValue;
-    if (mode == 3) a.rpc = a_in.rpc;  // the work list's largest rpc, set by the caller
+    const int mode = a.group ? 2 : (a.Xv != nullptr || a.Xs != nullptr ? 1 : 0);
+    if (a.group && (a.Xv || a.Xs)) return cudaErrorInvalidValue;
     void* fn = two_block_kernel<DF>(p.KI, mode);
     if (!fn) return cudaErrorInvalidValue;
     cudaError_t e = prepare_kernel<float>(fn, p.smem);
@@ -93,29 +91,6 @@ static cudaError_t launch_two_block(const Rank2Args& a_in, const Rank2Plan& p, c
 
 bool plan_rank2_split_f32(int Kp, int M, int R, Rank2Plan* p, int budget) { return plan_two_block<false>(Kp, M, R, p, budget); }
 
-// Work-list plan of the split kernel: W columns per column block (two
-// blocks per item), ncl clusters; shared memory sized for rpc_max receiver
-// rows per CTA, with 1 KB left for the kernel's static shared memory.
-bool plan_worklist_split(int Kp, int rpc_max, int W, int ncl, Rank2Plan* p) {
-    if (Kp <= 0 || Kp % 64 != 0 || Kp > 512 || W < kSplitCB || W % kSplitCB != 0 || ncl < 1) return false;
-    const size_t smem = split_smem_layout(W, Kp, rpc_max).total;
-    if (smem + 1024 > (size_t)device_smem_optin()) return false;
-    void* fn = two_block_kernel<false>(Kp / 64, 3);
-    if (!fn || prepare_kernel<float>(fn, smem) != cudaSuccess) return false;
-    p->KI = Kp / 64;
-    p->cs = Kp / 32;
-    p->cb = kSplitCB;
-    p->Wv = p->Wa = W;
-    p->nclusters = ncl;
-    p->smem = smem;
-    p->resident = true;
-    p->variant = 2;
-    p->nrt = 1;
-    p->c_global = false;
-    ClusterLaunch probe(p->cs, 1, kThreads, smem);
-    p->max_active_clusters = probe.max_active(fn);
-    return p->max_active_clusters > 0;
-}
 bool plan_rank2_dataflow_f32(int Kp, int M, int R, Rank2Plan* p) { return plan_two_block<true>(Kp, M, R, p); }
 cudaError_t launch_rank2_split_f32(const Rank2Args& a, const Rank2Plan& p, cudaStream_t st) {
     return p.variant == 3 ? launch_two_block<true>(a, p, st) : launch_two_block<false>(a, p, st);

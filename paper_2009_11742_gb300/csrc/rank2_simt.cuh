@@ -39,7 +39,8 @@ struct Rank2Smem {
     size_t Vf, Sf, C, f, T, g, cV, cS, total;
 };
 
-// nrt: 32-row tiles owned per CTA (1, or 2 with operators streamed from L2).
+// nrt: 32-row tiles owned per CTA (1, or 2 with operators streamed from L2;
+// the work-list launch: the most any CTA of the cluster owns).
 template <typename T>
 __host__ __device__ inline Rank2Smem rank2_smem_layout(int Wa, int Kp, int rpc, int nrt = 1) {
     Rank2Smem s{};
@@ -106,18 +107,20 @@ __device__ __forceinline__ T reduce_scatter16(T (&v)[NV], int j, int& vi, bool& 
 }
 
 // One half-step on the CTA's own 32 rows:  Y_own += dt (op . X [+ g f^T]).
-template <typename T, int KI, int CB, bool FORCED>
+// GUARD: only the first ki of the KI 64-wide k groups exist (Kp = 64 ki).
+template <typename T, int KI, int CB, bool FORCED, bool GUARD = false>
 __device__ __forceinline__ void half_step(const T (&op)[2][4 * KI], const T* __restrict__ X,
                                           T* __restrict__ Y, float* __restrict__ comp,
                                           const T* __restrict__ gown, const T* __restrict__ fcol,
                                           const T dt, const int Wa, const int Kp, const int row0,
-                                          const int rp, const int j) {
+                                          const int rp, const int j, const int ki = KI) {
     for (int c0 = 0; c0 < Wa; c0 += CB) {
         T acc[2][CB];
 #pragma unroll
         for (int cc = 0; cc < CB; ++cc) { acc[0][cc] = T(0); acc[1][cc] = T(0); }
 #pragma unroll
         for (int i = 0; i < KI; ++i) {
+            if (GUARD && i >= ki) continue;
             T x[CB][4];
 #pragma unroll
             for (int cc = 0; cc < CB; ++cc) load4(X + (size_t)(c0 + cc) * Kp + 64 * i + 4 * j, x[cc]);
@@ -172,15 +175,15 @@ __device__ __forceinline__ void push_own_rows(cg::cluster_group& cluster, T* Y, 
     }
 }
 
-template <typename T, int KI>
+template <typename T, int KI, bool GUARD = false>
 __device__ __forceinline__ void load_op_rows(T (&op)[2][4 * KI], const T* __restrict__ A, int Kp,
-                                             int row, int j) {
+                                             int row, int j, int ki = KI) {
 #pragma unroll
     for (int rr = 0; rr < 2; ++rr) {
 #pragma unroll
         for (int i = 0; i < KI; ++i) {
-            T x[4];
-            load4_ro(A + (size_t)(row + rr) * Kp + 64 * i + 4 * j, x);
+            T x[4] = {T(0), T(0), T(0), T(0)};  // groups past ki: never used
+            if (!GUARD || i < ki) load4_ro(A + (size_t)(row + rr) * Kp + 64 * i + 4 * j, x);
 #pragma unroll
             for (int q = 0; q < 4; ++q) op[rr][4 * i + q] = x[q];
         }
@@ -224,19 +227,30 @@ __device__ __forceinline__ void add_reference(T* __restrict__ Y, float* __restri
 // The one-block kernel's work on one column block: columns [gc0, gc0 + ncol)
 // of the caller's arrays, operator `gop` of the table (rank-3 launch) or the
 // launch's own operator (gop null).
-template <typename T, int KI, int CB, bool RESIDENT>
+// GEN (work-list launch, operators streamed from L2): the Kp / 32 row tiles
+// are dealt out to the cluster's CTAs as evenly as they go (the first
+// Kp/32 mod cs CTAs take one more; a CTA may own none), a.nrt is the most
+// any CTA owns, and the k loops stop after Kp / 64 of their KI groups.
+// Otherwise every CTA owns a.nrt tiles and Kp = 64 KI.
+template <typename T, int KI, int CB, bool RESIDENT, bool GEN = false>
 __device__ __forceinline__ void simt_body(cg::cluster_group& cluster, const Rank2Args& a,
                                           const GroupOp* gop, const int gc0, const int ncol) {
     const int cs = (int)cluster.num_blocks();
     const int crank = (int)cluster.block_rank();
     const int Wa = a.Wa;
     const int Kp = a.Kp;
+    const int ki = GEN ? Kp / 64 : KI;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int j = lane & 15;
     const int rp = warp * 2 + (lane >> 4);
-    const int nrt = a.nrt;
-    const int own_rows = nrt * kRowsPerCta;
-    const int row0 = crank * own_rows;
+    const int nrt = a.nrt;  // tiles the layout holds per CTA
+    int nrt_own = nrt, row0 = crank * nrt * kRowsPerCta;
+    if (GEN) {
+        const int tiles = Kp / kRowsPerCta, base = tiles / cs, rem = tiles % cs;
+        nrt_own = base + (crank < rem ? 1 : 0);
+        row0 = (crank * base + (crank < rem ? crank : rem)) * kRowsPerCta;
+    }
+    const int own_rows = nrt_own * kRowsPerCta;
     const T dt = (T)a.dt;
 
     extern __shared__ __align__(16) unsigned char smem[];
@@ -262,7 +276,7 @@ __device__ __forceinline__ void simt_body(cg::cluster_group& cluster, const Rank
         Sf[idx] = (c < ncol && k < a.Ks) ? Sin[(size_t)(gc0 + c) * a.Ks + k] : T(0);
     }
     // carries: [row tile][column][32 rows]
-    for (int idx = tid; idx < nrt * Wa * kRowsPerCta; idx += kThreads) {
+    for (int idx = tid; idx < nrt_own * Wa * kRowsPerCta; idx += kThreads) {
         const int rt = idx / (Wa * kRowsPerCta);
         const int rem = idx - rt * Wa * kRowsPerCta;
         const int c = rem / kRowsPerCta, rl = rem % kRowsPerCta, row = row0 + rt * kRowsPerCta + rl;
@@ -289,7 +303,7 @@ __device__ __forceinline__ void simt_body(cg::cluster_group& cluster, const Rank
     T opB[2][4 * KI];
     const T* __restrict__ Avs = static_cast<const T*>(gop ? gop->Avs_rm : a.Avs_rm);
     const T* __restrict__ Asv = static_cast<const T*>(gop ? gop->Asv_rm : a.Asv_rm);
-    if (RESIDENT) {
+    if (RESIDENT && nrt_own > 0) {
         load_op_rows<T, KI>(opA, Avs, Kp, row0 + 2 * rp, j);
         load_op_rows<T, KI>(opB, Asv, Kp, row0 + 2 * rp, j);
     }
@@ -299,32 +313,32 @@ __device__ __forceinline__ void simt_body(cg::cluster_group& cluster, const Rank
     T* traces = static_cast<T*>(a.traces);
     for (int n = 0; n < a.nsteps; ++n) {
         // ---- velocity half-step: V_own += dt (Avs_own S + g f_n^T [+ Xv])
-        for (int rt = 0; rt < nrt; ++rt) {
+        for (int rt = 0; rt < nrt_own; ++rt) {
             const int rowt = row0 + rt * kRowsPerCta;
-            if (!RESIDENT) load_op_rows<T, KI>(opA, Avs, Kp, rowt + 2 * rp, j);
-            half_step<T, KI, CB, true>(opA, Sf, Vf, cV + rt * Wa * kRowsPerCta, gown + rt * kRowsPerCta,
-                                       fcol, dt, Wa, Kp, rowt, rp, j);
+            if (!RESIDENT) load_op_rows<T, KI, GEN>(opA, Avs, Kp, rowt + 2 * rp, j, ki);
+            half_step<T, KI, CB, true, GEN>(opA, Sf, Vf, cV + rt * Wa * kRowsPerCta,
+                                            gown + rt * kRowsPerCta, fcol, dt, Wa, Kp, rowt, rp, j, ki);
         }
         if (a.Xv) {  // kernel parameters, read where used: no register held across the loop
             __syncthreads();
             add_reference<T>(Vf, cV, static_cast<const T*>(a.Xv) + (size_t)gc0 * a.Kv,
-                             a.Kv, ncol, dt, Wa, Kp, row0, nrt);
+                             a.Kv, ncol, dt, Wa, Kp, row0, nrt_own);
         }
         __syncthreads();
-        push_own_rows<T>(cluster, Vf, Wa, Kp, row0, cs, crank, nrt);
+        push_own_rows<T>(cluster, Vf, Wa, Kp, row0, cs, crank, nrt_own);
         cluster.sync();
 
         // ---- stress half-step with the new velocity: S_own += dt (Asv_own V [+ Xs])
-        for (int rt = 0; rt < nrt; ++rt) {
+        for (int rt = 0; rt < nrt_own; ++rt) {
             const int rowt = row0 + rt * kRowsPerCta;
-            if (!RESIDENT) load_op_rows<T, KI>(opB, Asv, Kp, rowt + 2 * rp, j);
-            half_step<T, KI, CB, false>(opB, Vf, Sf, cS + rt * Wa * kRowsPerCta, gown, fcol, dt, Wa, Kp,
-                                        rowt, rp, j);
+            if (!RESIDENT) load_op_rows<T, KI, GEN>(opB, Asv, Kp, rowt + 2 * rp, j, ki);
+            half_step<T, KI, CB, false, GEN>(opB, Vf, Sf, cS + rt * Wa * kRowsPerCta, gown, fcol, dt, Wa,
+                                             Kp, rowt, rp, j, ki);
         }
         if (a.Xs) {
             __syncthreads();
             add_reference<T>(Sf, cS, static_cast<const T*>(a.Xs) + (size_t)gc0 * a.Ks,
-                             a.Ks, ncol, dt, Wa, Kp, row0, nrt);
+                             a.Ks, ncol, dt, Wa, Kp, row0, nrt_own);
             __syncthreads();
         }
 
@@ -356,7 +370,7 @@ __device__ __forceinline__ void simt_body(cg::cluster_group& cluster, const Rank
             }
         }
         __syncthreads();
-        push_own_rows<T>(cluster, Sf, Wa, Kp, row0, cs, crank, nrt);
+        push_own_rows<T>(cluster, Sf, Wa, Kp, row0, cs, crank, nrt_own);
         cluster.sync();
     }
 
@@ -399,12 +413,15 @@ __global__ void __launch_bounds__(kThreads, 1) rank2_simt_kernel(const Rank2Args
     simt_body<T, KI, CB, RESIDENT>(cluster, a, gop, a.col_base + job * a.M + col0, ncol);
 }
 
-// Work-list launch of the batched scheduler (FP32): the clusters take
-// (job, column block) items from a.items in the order a global counter
-// hands them out, each job with its own operator, state, periods, traces
-// and constants from the table a.group, until none are left.
-template <int KI, int CB, bool RESIDENT>
-__global__ void __launch_bounds__(kThreads, 1) rank2_simt_worklist_kernel(const Rank2Args a) {
+// Work-list launch of the batched scheduler (FP32): one persistent launch
+// for jobs of any Kp <= 64 KI.  The clusters take (job, column block) items
+// from a.items in the order a global counter hands them out, each job with
+// its own operator, state, periods, traces, constants, width and Kp from the
+// table a.group, until none are left.  The cluster size is the launch's:
+// a job's rows are dealt out to its CTAs (simt_body, GEN) and its receiver
+// rows split ceil(R / cs) per CTA, so one instance serves every job.
+template <int KI, int CB>
+__global__ void __launch_bounds__(kThreads, 1) rank2_wl_kernel(const Rank2Args a) {
     cg::cluster_group cluster = cg::this_cluster();
     const int cs = (int)cluster.num_blocks();
     const int crank = (int)cluster.block_rank();
@@ -432,14 +449,18 @@ __global__ void __launch_bounds__(kThreads, 1) rank2_simt_worklist_kernel(const 
         aj.dt = gop->dt;
         aj.Kv = gop->Kv;
         aj.Ks = gop->Ks;
+        aj.Kp = gop->Kp;
         aj.R = gop->R;
-        aj.rpc = gop->rpc;
         aj.M = gop->M;
         aj.Mtot = gop->M;
         aj.wavelet = gop->wavelet;
+        aj.Wv = aj.Wa = gop->Wa;
+        aj.nrt = (gop->Kp / kRowsPerCta + cs - 1) / cs;
+        aj.rpc = (gop->R + cs - 1) / cs;
+        aj.c_global = gop->c_global;
         aj.col_base = 0;
         aj.group = nullptr;
-        simt_body<float, KI, CB, RESIDENT>(cluster, aj, nullptr, wi.col0, min(a.Wv, wi.ncol));
+        simt_body<float, KI, CB, false, true>(cluster, aj, nullptr, wi.col0, min(aj.Wv, wi.ncol));
         // every CTA has read the slot and finished the item before the next fetch
         cluster.sync();
     }

@@ -381,65 +381,21 @@ __device__ __forceinline__ void split_body(cg::cluster_group& cluster, const Ran
 
 
 // MODE: 0 plain; 1 adds the reduced reference state (a.Xv / a.Xs); 2 is the
-// rank-3 grouped launch (operator table a.group); 3 is the work-list launch
-// of the batched scheduler: the clusters take (job, column range) items from
-// a.items in the order a global counter hands them out, each job with its
-// own operator, state, periods, traces and constants from the table, until
-// none are left.  A template parameter, so that each instance compiles to
-// exactly the code its runs need.
+// rank-3 grouped launch (operator table a.group).  A template parameter, so
+// that each instance compiles to exactly the code its runs need.
 template <int KI, int MODE>
 __global__ void __launch_bounds__(kThreads, 1) rank2_split_kernel(const Rank2Args a) {
     cg::cluster_group cluster = cg::this_cluster();
     const int cs = (int)cluster.num_blocks();
-    if constexpr (MODE == 3) {
-        __shared__ int s_item;
-        const int crank = (int)cluster.block_rank();
-        for (;;) {
-            if (crank == 0 && threadIdx.x == 0) {
-                const int k = atomicAdd(a.item_counter, 1);
-                for (int r = 0; r < cs; ++r) *cluster.map_shared_rank(&s_item, r) = k;
-            }
-            cluster.sync();
-            const int k = s_item;
-            if (k >= a.nitems) break;
-            const WorkItem wi = a.items[k];
-            const GroupOp* gop = a.group + wi.job;
-            Rank2Args aj = a;
-            aj.Avs_rm = gop->Avs_rm;
-            aj.Asv_rm = gop->Asv_rm;
-            aj.g_p = gop->g_p;
-            aj.C_p = gop->C_p;
-            aj.V = gop->V;
-            aj.S = gop->S;
-            aj.Tper = gop->Tper;
-            aj.traces = gop->traces;
-            aj.status = gop->status;
-            aj.dt = gop->dt;
-            aj.Kv = gop->Kv;
-            aj.Ks = gop->Ks;
-            aj.R = gop->R;
-            aj.rpc = gop->rpc;
-            aj.M = gop->M;
-            aj.Mtot = gop->M;
-            aj.wavelet = gop->wavelet;
-            aj.col_base = 0;
-            const int nc0 = min(a.Wv, wi.ncol);
-            const int nc1 = max(0, min(a.Wv, wi.ncol - a.Wv));
-            split_body<KI, 0>(cluster, aj, nullptr, wi.col0, nc0, nc1);
-            // every CTA has read the slot and finished the item before the next fetch
-            cluster.sync();
-        }
-    } else {
-        // rank-3 grouped launch: operator `job` of the table, cluster `clu` of it
-        const int job = MODE == 2 ? (int)(blockIdx.x / cs) / a.group_cpj : 0;
-        const int clu = MODE == 2 ? (int)(blockIdx.x / cs) % a.group_cpj : (int)(blockIdx.x / cs);
-        const GroupOp* gop = MODE == 2 ? a.group + job : nullptr;
-        const int gc0_0 = a.col_base + job * a.M + (2 * clu) * a.Wv;
-        const int nr0 = a.M - (2 * clu) * a.Wv, nr1 = nr0 - a.Wv;
-        const int nc0 = nr0 < 0 ? 0 : (nr0 > a.Wv ? a.Wv : nr0);
-        const int nc1 = nr1 < 0 ? 0 : (nr1 > a.Wv ? a.Wv : nr1);
-        split_body<KI, MODE>(cluster, a, gop, gc0_0, nc0, nc1);
-    }
+    // rank-3 grouped launch: operator `job` of the table, cluster `clu` of it
+    const int job = MODE == 2 ? (int)(blockIdx.x / cs) / a.group_cpj : 0;
+    const int clu = MODE == 2 ? (int)(blockIdx.x / cs) % a.group_cpj : (int)(blockIdx.x / cs);
+    const GroupOp* gop = MODE == 2 ? a.group + job : nullptr;
+    const int gc0_0 = a.col_base + job * a.M + (2 * clu) * a.Wv;
+    const int nr0 = a.M - (2 * clu) * a.Wv, nr1 = nr0 - a.Wv;
+    const int nc0 = nr0 < 0 ? 0 : (nr0 > a.Wv ? a.Wv : nr0);
+    const int nc1 = nr1 < 0 ? 0 : (nr1 > a.Wv ? a.Wv : nr1);
+    split_body<KI, MODE>(cluster, a, gop, gc0_0, nc0, nc1);
 }
 
 }  // namespace romk

@@ -1142,40 +1142,34 @@ static int batch_tc_width(int prec, int M) {
     return M <= 64 ? 64 : 128;
 }
 
-// ---- work-list batched launch (FP32): one persistent launch per operator
-// size class.  Jobs are grouped by padded size Kp (the split kernel for
-// Kp <= 512, the one-block kernel above); a class's clusters take
-// (job, column range) items from a device list in the order a counter hands
-// them out, so no cluster idles while items are left.  Widths and cluster
-// counts come from a step-time model, microseconds per leapfrog step of one
-// item: split kernel 2.24 + 0.466 W Kp/512 (two W-column blocks per item),
-// one-block kernel 3.5 + 1.39 W Kp/1024 (one block per item), fitted on
-// GB300.  A binary search finds the smallest predicted makespan T for which
-// every class, at its best width, needs at most the device's SMs in total:
-// a class with items(W) items of time t(W) needs ceil(items / floor(T / t))
-// clusters.
-struct WLClass {
-    int Kp = 0;
-    bool split = true;
-    std::vector<int> jobs;
-    int rpc_max = 0;
-    int W = 0, ncl = 0, nitems = 0;
-    Rank2Plan plan;
-};
+// ---- work-list batched launch (FP32): ONE persistent launch of the
+// work-list kernel for every job of the batch.  All clusters have the same
+// size cs (2: 76 co-resident clusters cover all 152 SMs of a GB300; 4: 36
+// clusters, 144 SMs); a job's Kp / 32 row tiles are dealt out to the CTAs of
+// whichever cluster takes one of its items, so jobs of every size share one
+// kernel and one device work list.  Job j is cut into column blocks of width
+// W_j: the widest that fits the shared memory (and the cap `wcap`), then
+// narrowed to spread M_j evenly over that many blocks.  The items are
+// ordered longest first (a step of an item costs about its busiest CTA's
+// rows x Kp x W_j multiply-adds plus a fixed part), so the clusters, which
+// take the next item whenever they finish one, end within about one short
+// item of each other (list scheduling, longest processing time first).
+// Receiver rows are staged in shared memory when a CTA's share is at most
+// 16 KB, else read from global memory.
+//
+// `wl` encodes the form: cs * 1000 + wcap.
+constexpr int kWlDefault = 2 * 1000 + 32;
 
-static double wl_step_us(bool split, int Kp, int W) {
-    return split ? 2.24 + 0.466 * W * (Kp / 512.0) : 3.5 + 1.39 * W * (Kp / 1024.0);
-}
-
-static int wl_items(const WLClass& c, const rom_job* jobs, int W) {
-    const int per = c.split ? 2 * W : W;
-    int n = 0;
-    for (int i : c.jobs) n += (jobs[i].M + per - 1) / per;
-    return n;
+static bool wl_decode(int wl, int* cs, int* wcap) {
+    *cs = wl / 1000;
+    *wcap = wl % 1000;
+    return (*cs == 2 || *cs == 4 || *cs == 8) && *wcap >= 8 && *wcap % 8 == 0 && *wcap <= 256;
 }
 
 static rom_status run_batched_worklist(const rom_job* jobs, int njobs, int nsteps, int r,
-                                       cudaStream_t st, int dev, int nsm) {
+                                       cudaStream_t st, int dev, int wl) {
+    int cs = 0, wcap = 0;
+    if (!wl_decode(wl, &cs, &wcap)) return ROM_E_INVAL;
     BatchKey key;
     key.words = {(uintptr_t)njobs, (uintptr_t)nsteps, (uintptr_t)r, (uintptr_t)ROM_FP32, (uintptr_t)st,
                  (uintptr_t)dev};
@@ -1184,124 +1178,81 @@ static rom_status run_batched_worklist(const rom_job* jobs, int njobs, int nstep
         key.words.insert(key.words.end(), {(uintptr_t)j.h, (uintptr_t)j.V, (uintptr_t)j.S,
                                            (uintptr_t)j.T, (uintptr_t)j.M, (uintptr_t)j.traces});
     }
-    key.words.push_back((uintptr_t)0x574c);  // work-list form
+    key.words.push_back((uintptr_t)0x574c0000 + (uintptr_t)wl);  // work-list form
     std::lock_guard<std::mutex> lk(g_batch_mu);
     auto it = g_batch_graphs.find(key);
     if (it == g_batch_graphs.end()) {
-        // ---- size classes
-        std::map<int, WLClass> byK;
+        int optin = 0;
+        ROM_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+        const size_t budget = (size_t)optin - 1024;
+        // ---- per job: tiles per CTA, receiver rows, width
+        std::vector<GroupOp> ops(njobs);
+        std::vector<double> cost(njobs);
+        size_t smem = 0;
+        int nitems = 0;
         for (int i = 0; i < njobs; ++i) {
             const rom_s* h = jobs[i].h;
-            WLClass& c = byK[h->Kp];
-            c.Kp = h->Kp;
-            c.split = h->Kp <= 512;
-            c.jobs.push_back(i);
-            const int cs = c.split ? h->Kp / 32 : h->Kp / 64;
-            const int H = c.split ? cs / 2 : cs;
-            const int rpc = (h->R + H - 1) / H;
-            c.rpc_max = rpc > c.rpc_max ? rpc : c.rpc_max;
-        }
-        std::vector<WLClass> cls;
-        for (auto& kv : byK) cls.push_back(kv.second);
-        // widths each class can take, with their co-resident cluster limits
-        struct Cand { int W, items, maxact; double t; };
-        std::vector<std::vector<Cand>> cands(cls.size());
-        for (size_t c = 0; c < cls.size(); ++c) {
-            const int step = cls[c].split ? 4 : 8;
-            for (int W = step; W <= 256; W += step) {
-                Rank2Plan p;
-                const bool ok = cls[c].split ? plan_worklist_split(cls[c].Kp, cls[c].rpc_max, W, 1, &p)
-                                             : plan_worklist_simt(cls[c].Kp, cls[c].rpc_max, W, 1, &p);
-                if (!ok) break;
-                cands[c].push_back({W, wl_items(cls[c], jobs, W), p.max_active_clusters,
-                                    wl_step_us(cls[c].split, cls[c].Kp, W)});
-                cls[c].plan = p;  // cluster size and kernel (the width is set below)
+            const int Kp = h->Kp, M = jobs[i].M;
+            const int nrt = (Kp / 32 + cs - 1) / cs;
+            const int rpc = (h->R + cs - 1) / cs;
+            const int cglob = (size_t)rpc * Kp * sizeof(float) > 16384 ? 1 : 0;
+            const int rst = cglob ? 0 : rpc;
+            int wmax = 0;
+            for (int w = 8; w <= wcap; w += 8) {
+                if (worklist_smem(w, Kp, rst, nrt) > budget) break;
+                wmax = w;
             }
-            if (cands[c].empty()) {
-                snprintf(g_last_error, sizeof(g_last_error), "no work-list plan for Kp=%d", cls[c].Kp);
+            if (wmax == 0) {
+                snprintf(g_last_error, sizeof(g_last_error), "no work-list width for Kp=%d", Kp);
                 return ROM_E_UNSUPPORTED;
             }
+            const int nb = (M + wmax - 1) / wmax;
+            const int W = (((M + nb - 1) / nb) + 7) / 8 * 8;
+            const size_t sm = worklist_smem(W, Kp, rst, nrt);
+            smem = sm > smem ? sm : smem;
+            GroupOp& g = ops[i];
+            g.Avs_rm = h->Avs_rm[1];
+            g.Asv_rm = h->Asv_rm[1];
+            g.g_p = h->g_p[1];
+            g.C_p = h->C_rm[1];
+            g.V = jobs[i].V;
+            g.S = jobs[i].S;
+            g.Tper = jobs[i].T;
+            g.traces = jobs[i].traces;
+            g.status = h->status;
+            g.dt = h->dt;
+            g.Kv = h->Kv;
+            g.Ks = h->Ks;
+            g.R = h->R;
+            g.M = M;
+            g.wavelet = h->wavelet;
+            g.Kp = Kp;
+            g.Wa = W;
+            g.c_global = cglob;
+            cost[i] = 3.5 + 1.39 * W * (Kp / 1024.0) * nrt / 2.0;
+            nitems += nb;
         }
-        // the fewest SMs class c needs to finish within T (INT_MAX: cannot)
-        auto need = [&](size_t c, double T, int* Wout, int* nout) {
-            long best = 1L << 40;
-            for (const Cand& k : cands[c]) {
-                if (k.t > T) continue;
-                const long rounds = (long)(T / k.t);
-                long n = (k.items + rounds - 1) / rounds;
-                if (n < 1) n = 1;
-                if (n > k.maxact || n > k.items) continue;
-                const long sms = n * (long)cls[c].plan.cs;
-                if (sms < best) {
-                    best = sms;
-                    *Wout = k.W;
-                    *nout = (int)n;
-                }
-            }
-            return best;
-        };
-        double lo = 0.0, hi = 1e9;
-        for (int iter = 0; iter < 60; ++iter) {
-            const double mid = 0.5 * (lo + hi);
-            long tot = 0;
-            int w, n;
-            for (size_t c = 0; c < cls.size(); ++c) tot += need(c, mid, &w, &n);
-            if (tot <= nsm) hi = mid;
-            else lo = mid;
+        // ---- the item list, longest first (ties: job order, then columns)
+        std::vector<WorkItem> items;
+        items.reserve(nitems);
+        for (int i = 0; i < njobs; ++i)
+            for (int col = 0; col < jobs[i].M; col += ops[i].Wa)
+                items.push_back({i, col, jobs[i].M - col < ops[i].Wa ? jobs[i].M - col : ops[i].Wa, 0});
+        std::stable_sort(items.begin(), items.end(),
+                         [&](const WorkItem& x, const WorkItem& y) { return cost[x.job] > cost[y.job]; });
+        int ncl = worklist_max_clusters(cs, smem);
+        if (ncl <= 0) {
+            snprintf(g_last_error, sizeof(g_last_error), "work-list kernel does not fit (cs=%d, %zu B)", cs, smem);
+            return ROM_E_UNSUPPORTED;
         }
-        for (size_t c = 0; c < cls.size(); ++c) {
-            int w = 0, n = 0;
-            if (need(c, hi, &w, &n) >= (1L << 40)) return ROM_E_UNSUPPORTED;
-            cls[c].W = w;
-            cls[c].ncl = n;
-            cls[c].nitems = wl_items(cls[c], jobs, w);
-            Rank2Plan p;
-            const bool ok = cls[c].split ? plan_worklist_split(cls[c].Kp, cls[c].rpc_max, w, n, &p)
-                                         : plan_worklist_simt(cls[c].Kp, cls[c].rpc_max, w, n, &p);
-            if (!ok) return ROM_E_UNSUPPORTED;
-            cls[c].plan = p;
-        }
-        // ---- device tables: counters, then per class its job table and items
-        size_t bytes = 256;
-        std::vector<size_t> off_ops(cls.size()), off_items(cls.size());
-        for (size_t c = 0; c < cls.size(); ++c) {
-            off_ops[c] = bytes;
-            bytes += ((sizeof(GroupOp) * cls[c].jobs.size() + 255) / 256) * 256;
-            off_items[c] = bytes;
-            bytes += ((sizeof(WorkItem) * cls[c].nitems + 255) / 256) * 256;
-        }
+        if (ncl > nitems) ncl = nitems;
+        // ---- device tables: counter, job table, items
+        const size_t off_ops = 256;
+        const size_t off_items = off_ops + ((sizeof(GroupOp) * njobs + 255) / 256) * 256;
+        const size_t bytes = off_items + sizeof(WorkItem) * items.size();
         std::vector<unsigned char> host(bytes, 0);
-        for (size_t c = 0; c < cls.size(); ++c) {
-            GroupOp* ops = reinterpret_cast<GroupOp*>(host.data() + off_ops[c]);
-            WorkItem* items = reinterpret_cast<WorkItem*>(host.data() + off_items[c]);
-            const int cs = cls[c].plan.cs;
-            const int H = cls[c].split ? cs / 2 : cs;
-            const int per = cls[c].split ? 2 * cls[c].W : cls[c].W;
-            int n = 0;
-            for (size_t q = 0; q < cls[c].jobs.size(); ++q) {
-                const rom_job& j = jobs[cls[c].jobs[q]];
-                rom_s* h = j.h;
-                GroupOp& g = ops[q];
-                g.Avs_rm = h->Avs_rm[1];
-                g.Asv_rm = h->Asv_rm[1];
-                g.g_p = h->g_p[1];
-                g.C_p = h->C_rm[1];
-                g.V = j.V;
-                g.S = j.S;
-                g.Tper = j.T;
-                g.traces = j.traces;
-                g.status = h->status;
-                g.dt = h->dt;
-                g.Kv = h->Kv;
-                g.Ks = h->Ks;
-                g.R = h->R;
-                g.M = j.M;
-                g.wavelet = h->wavelet;
-                g.rpc = (h->R + H - 1) / H;
-                for (int col = 0; col < j.M; col += per)
-                    items[n++] = {(int)q, col, j.M - col < per ? j.M - col : per, 0};
-            }
-        }
+        memcpy(host.data() + off_ops, ops.data(), sizeof(GroupOp) * njobs);
+        memcpy(host.data() + off_items, items.data(), sizeof(WorkItem) * items.size());
         void* tables = nullptr;
         ROM_CUDA(cudaMalloc(&tables, bytes));
         cudaError_t e = cudaMemcpy(tables, host.data(), bytes, cudaMemcpyHostToDevice);
@@ -1309,13 +1260,17 @@ static rom_status run_batched_worklist(const rom_job* jobs, int njobs, int nstep
             cudaFree(tables);
             return cuda_fail(e, "rom_run_batched work list");
         }
-        // ---- capture: reset the counters, then every class on its own stream,
-        // the classes with the largest clusters issued first
-        std::vector<size_t> order(cls.size());
-        for (size_t c = 0; c < cls.size(); ++c) order[c] = c;
-        std::sort(order.begin(), order.end(), [&](size_t x, size_t y) { return cls[x].plan.cs > cls[y].plan.cs; });
-        const size_t npool = cls.size() < 32 ? cls.size() : 32;
-        rom_status s = batch_streams(npool);
+        const rom_s* h0 = jobs[0].h;
+        Rank2Args a = {};
+        a.nsteps = nsteps;
+        a.r = r > 0 ? r : 1;
+        a.spin_limit = h0->wait_limit;
+        a.group = reinterpret_cast<const GroupOp*>(static_cast<unsigned char*>(tables) + off_ops);
+        a.items = reinterpret_cast<const WorkItem*>(static_cast<unsigned char*>(tables) + off_items);
+        a.nitems = nitems;
+        a.item_counter = static_cast<int*>(tables);
+        // ---- capture: reset the counter, then the one launch
+        rom_status s = batch_streams(1);
         if (s != ROM_OK) {
             cudaFree(tables);
             return s;
@@ -1323,42 +1278,8 @@ static rom_status run_batched_worklist(const rom_job* jobs, int njobs, int nstep
         cudaGraph_t graph = nullptr;
         cudaStream_t cap = g_capture_stream;
         e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeRelaxed);
-        if (e == cudaSuccess) e = cudaMemsetAsync(tables, 0, 256, cap);
-        cudaEvent_t fork = g_batch_events[npool];
-        if (e == cudaSuccess) e = cudaEventRecord(fork, cap);
-        for (size_t k = 0; k < npool && e == cudaSuccess; ++k) e = cudaStreamWaitEvent(g_batch_streams[k], fork, 0);
-        for (size_t oi = 0; oi < order.size() && e == cudaSuccess; ++oi) {
-            const size_t c = order[oi];
-            const rom_s* h0 = jobs[cls[c].jobs[0]].h;
-            Rank2Args a = {};
-            a.Avs_rm = h0->Avs_rm[1];
-            a.Asv_rm = h0->Asv_rm[1];
-            a.g_p = h0->g_p[1];
-            a.C_p = h0->C_rm[1];
-            a.status = h0->status;
-            a.dt = h0->dt;
-            a.Kv = h0->Kv;
-            a.Ks = h0->Ks;
-            a.Kp = cls[c].Kp;
-            a.R = h0->R;
-            a.M = jobs[cls[c].jobs[0]].M;
-            a.Mtot = a.M;
-            a.nsteps = nsteps;
-            a.r = r > 0 ? r : 1;
-            a.rpc = cls[c].rpc_max;
-            a.spin_limit = h0->wait_limit;
-            a.group = reinterpret_cast<const GroupOp*>(static_cast<unsigned char*>(tables) + off_ops[c]);
-            a.items = reinterpret_cast<const WorkItem*>(static_cast<unsigned char*>(tables) + off_items[c]);
-            a.nitems = cls[c].nitems;
-            a.item_counter = static_cast<int*>(tables) + c;
-            cudaStream_t ss = g_batch_streams[oi % npool];
-            e = cls[c].split ? launch_rank2_split_f32(a, cls[c].plan, ss)
-                             : launch_rank2_simt_worklist_f32(a, cls[c].plan, ss);
-        }
-        for (size_t k = 0; k < npool && e == cudaSuccess; ++k) {
-            e = cudaEventRecord(g_batch_events[k], g_batch_streams[k]);
-            if (e == cudaSuccess) e = cudaStreamWaitEvent(cap, g_batch_events[k], 0);
-        }
+        if (e == cudaSuccess) e = cudaMemsetAsync(tables, 0, sizeof(int), cap);
+        if (e == cudaSuccess) e = launch_rank2_worklist_f32(a, cs, ncl, smem, cap);
         cudaError_t e2 = cudaStreamEndCapture(cap, &graph);
         if (e == cudaSuccess) e = e2;
         cudaGraphExec_t exec = nullptr;
@@ -1375,11 +1296,11 @@ static rom_status run_batched_worklist(const rom_job* jobs, int njobs, int nstep
 }
 
 // tcw: tensor-core block widths, 1 = batch_tc_width, 0 = the planner's.
-// wl: 1 = FP32 batches run as work-list launches (one per size class), 0 =
-// one launch per job.
+// wl: FP32 batches run as one work-list launch of that form (cs * 1000 +
+// wcap), 0 = one launch per job.
 static rom_status run_batched_impl(const rom_job* jobs, int njobs, int nsteps, int r, int prec,
                                    void* stream, double scale, int kthr = kAutoKthr, int tcw = 1,
-                                   int wl = 1) {
+                                   int wl = kWlDefault) {
     if (!jobs || njobs < 1 || nsteps < 0 || r < 0 || !batch_prec(prec)) return ROM_E_INVAL;
     for (int i = 0; i < njobs; ++i) {
         const rom_job& j = jobs[i];
@@ -1405,7 +1326,7 @@ static rom_status run_batched_impl(const rom_job* jobs, int njobs, int nsteps, i
     if (wl && prec == ROM_FP32) {
         bool ok = true;
         for (int i = 0; i < njobs; ++i) ok = ok && jobs[i].h->xref_M == 0 && jobs[i].h->Kp <= 1024;
-        if (ok) return run_batched_worklist(jobs, njobs, nsteps, r, st, dev, nsm);
+        if (ok) return run_batched_worklist(jobs, njobs, nsteps, r, st, dev, wl);
     }
     // share of the SMs per job, proportional to its work per step
     std::vector<double> cost(njobs);
@@ -1532,7 +1453,7 @@ static std::vector<uintptr_t> batch_tune_key(const rom_job* jobs, int njobs, int
 
 rom_status rom_run_batched(const rom_job* jobs, int njobs, int nsteps, int r, int prec, void* stream) {
     double scale = 1.0;
-    int kthr = kAutoKthr, tcw = 1, wl = 1;
+    int kthr = kAutoKthr, tcw = 1, wl = kWlDefault;
     if (jobs && njobs > 0) {
         for (int i = 0; i < njobs; ++i)
             if (!jobs[i].h) return ROM_E_INVAL;
@@ -1594,10 +1515,13 @@ rom_status rom_autotune_batched(const rom_job* jobs, int njobs, int prec, int pr
     double best = -1.0, best_scale = 1.0;
     int best_kthr = kAutoKthr, best_tcw = 1, best_wl = 0;
     rom_status rs = ROM_OK;
-    // FP32: the work-list form (one candidate) besides one launch per job
-    const int nwl = prec == ROM_FP32 ? 2 : 1;
-    for (int wl = nwl - 1; wl >= 0 && e == cudaSuccess && rs == ROM_OK; --wl)
+    // FP32: work-list forms (clusters of 2 or 4 CTAs, width caps 16 / 32 /
+    // 64) besides one launch per job (0)
+    const int wls[7] = {kWlDefault, 2016, 2064, 4016, 4032, 4064, 0};
+    const int nwl = prec == ROM_FP32 ? 7 : 1;
+    for (int iw = 0; iw < nwl && e == cudaSuccess && rs == ROM_OK; ++iw)
     for (int t = 0; t < nk && e == cudaSuccess && rs == ROM_OK; ++t) {
+        const int wl = prec == ROM_FP32 ? wls[iw] : 0;
         for (int tw = 0; tw < ntw && e == cudaSuccess && rs == ROM_OK; ++tw) {
             const int tcw = 1 - tw;
             for (int c = 0; c < (wl ? 1 : 4) && e == cudaSuccess && rs == ROM_OK; ++c) {
@@ -1611,6 +1535,10 @@ rom_status rom_autotune_batched(const rom_job* jobs, int njobs, int prec, int pr
                     if (e == cudaSuccess && rs == ROM_OK) e = cudaEventRecord(e1, st);
                     if (e == cudaSuccess && rs == ROM_OK) e = cudaEventSynchronize(e1);
                     if (e == cudaSuccess && rs == ROM_OK) e = cudaEventElapsedTime(&ms, e0, e1);
+                }
+                if (wl && rs == ROM_E_UNSUPPORTED) {  // a form that does not fit: next candidate
+                    rs = ROM_OK;
+                    continue;
                 }
                 if (e == cudaSuccess && rs == ROM_OK) {
                     const double us = 1e3 * ms / probe_steps;

@@ -23,19 +23,20 @@ struct GroupOp {
     const void* g_p;
     const void* C_p;
     // work-list launches only (the batched scheduler): the job's own state,
-    // periods, traces, status word and constants
+    // periods, traces, status word and constants, its padded size Kp, the
+    // columns of one item (Wa, a multiple of 8), and whether its receiver
+    // rows are read from C_p rather than staged in shared memory
     void* V;
     void* S;
     const void* Tper;
     void* traces;
     int* status;
     double dt;
-    int Kv, Ks, R, M, wavelet, rpc;
+    int Kv, Ks, R, M, wavelet, Kp, Wa, c_global;
 };
 
 // One item of a work-list launch: columns [col0, col0 + ncol) of job `job` of
-// the operator table (the split kernel's two column blocks, or the one-block
-// kernel's one).
+// the operator table.
 struct WorkItem {
     int job, col0, ncol, pad;
 };
@@ -118,15 +119,13 @@ bool plan_rank2_simt_f64(int Kp, int M, int R, bool rank1, Rank2Plan* plan, int 
 bool plan_rank2_split_f32(int Kp, int M, int R, Rank2Plan* plan, int cluster_budget = 0);
 bool plan_rank2_dataflow_f32(int Kp, int M, int R, Rank2Plan* plan);
 cudaError_t launch_rank2_split_f32(const Rank2Args& a, const Rank2Plan& plan, cudaStream_t st);
-// Work-list launch of the one-block kernel (FP32, the batched scheduler);
-// the split kernel's work-list form is launched by launch_rank2_split_f32
-// when a.items is set.  a.rpc: the jobs' largest rows of C per CTA.
-cudaError_t launch_rank2_simt_worklist_f32(const Rank2Args& a, const Rank2Plan& plan, cudaStream_t st);
-// Work-list plans with W columns per column block and ncl clusters (false if
-// the width does not fit): the split kernel (Kp <= 512) and the one-block
-// kernel (512 < Kp <= 1024); rpc_max sizes the receiver-row staging.
-bool plan_worklist_split(int Kp, int rpc_max, int W, int ncl, Rank2Plan* plan);
-bool plan_worklist_simt(int Kp, int rpc_max, int W, int ncl, Rank2Plan* plan);
+// The work-list kernel (FP32, any Kp <= 1024, clusters of cs CTAs): the
+// co-resident clusters at `smem` bytes of dynamic shared memory (0: the
+// size does not fit), and the launch of ncl clusters (a.group / items /
+// nitems / item_counter set).
+int worklist_max_clusters(int cs, size_t smem);
+size_t worklist_smem(int W, int Kp, int rpc, int nrt);
+cudaError_t launch_rank2_worklist_f32(const Rank2Args& a, int cs, int ncl, size_t smem, cudaStream_t st);
 
 // Streaming companion of the split kernel (FP32, Kp <= 512, clusters of 2
 // or 4 CTAs, at most 4 columns per cluster; operators streamed from L2).
