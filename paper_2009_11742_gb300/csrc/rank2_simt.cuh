@@ -107,20 +107,18 @@ __device__ __forceinline__ T reduce_scatter16(T (&v)[NV], int j, int& vi, bool& 
 }
 
 // One half-step on the CTA's own 32 rows:  Y_own += dt (op . X [+ g f^T]).
-// GUARD: only the first ki of the KI 64-wide k groups exist (Kp = 64 ki).
-template <typename T, int KI, int CB, bool FORCED, bool GUARD = false>
+template <typename T, int KI, int CB, bool FORCED>
 __device__ __forceinline__ void half_step(const T (&op)[2][4 * KI], const T* __restrict__ X,
                                           T* __restrict__ Y, float* __restrict__ comp,
                                           const T* __restrict__ gown, const T* __restrict__ fcol,
                                           const T dt, const int Wa, const int Kp, const int row0,
-                                          const int rp, const int j, const int ki = KI) {
+                                          const int rp, const int j) {
     for (int c0 = 0; c0 < Wa; c0 += CB) {
         T acc[2][CB];
 #pragma unroll
         for (int cc = 0; cc < CB; ++cc) { acc[0][cc] = T(0); acc[1][cc] = T(0); }
 #pragma unroll
         for (int i = 0; i < KI; ++i) {
-            if (GUARD && i >= ki) continue;
             T x[CB][4];
 #pragma unroll
             for (int cc = 0; cc < CB; ++cc) load4(X + (size_t)(c0 + cc) * Kp + 64 * i + 4 * j, x[cc]);
@@ -175,18 +173,105 @@ __device__ __forceinline__ void push_own_rows(cg::cluster_group& cluster, T* Y, 
     }
 }
 
-template <typename T, int KI, bool GUARD = false>
+template <typename T, int KI>
 __device__ __forceinline__ void load_op_rows(T (&op)[2][4 * KI], const T* __restrict__ A, int Kp,
-                                             int row, int j, int ki = KI) {
+                                             int row, int j) {
 #pragma unroll
     for (int rr = 0; rr < 2; ++rr) {
 #pragma unroll
         for (int i = 0; i < KI; ++i) {
-            T x[4] = {T(0), T(0), T(0), T(0)};  // groups past ki: never used
-            if (!GUARD || i < ki) load4_ro(A + (size_t)(row + rr) * Kp + 64 * i + 4 * j, x);
+            T x[4];
+            load4_ro(A + (size_t)(row + rr) * Kp + 64 * i + 4 * j, x);
 #pragma unroll
             for (int q = 0; q < 4; ++q) op[rr][4 * i + q] = x[q];
         }
+    }
+}
+
+// ---- the work-list kernel's half-step (FP32, operators streamed from L2):
+// warp w holds rows 4w .. 4w + 3 of a 32-row tile and lane l the k values
+// 128 i + 4 l + q, so each 16-byte read of the state feeds 16 multiply-adds
+// (4 rows x 4 k) and the partial sums meet in a 32-lane reduce-scatter.
+// Only k < Kp exist (Kp a multiple of 64: the last group may be half full).
+
+// Butterfly reduce-scatter of 32 partial sums over the 32 lanes of a warp:
+// afterwards lane l holds the full sum of value index `vi`.
+__device__ __forceinline__ float reduce_scatter32(float (&v)[32], int lane, int& vi) {
+    int base = 0;
+#pragma unroll
+    for (int s = 0; s < 5; ++s) {
+        const int o = 16 >> s;
+        const int half = 16 >> s;  // values kept after this stage
+        const bool up = (lane & o) != 0;
+#pragma unroll
+        for (int k = 0; k < half; ++k) {
+            const float send = up ? v[k] : v[k + half];
+            const float keep = up ? v[k + half] : v[k];
+            v[k] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+        }
+        base += up ? half : 0;
+    }
+    vi = base;
+    return v[0];
+}
+
+template <int KQ>
+__device__ __forceinline__ void wl_load_op(float (&op)[4][4 * KQ], const float* __restrict__ A, int Kp,
+                                             int row, int lane) {
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+#pragma unroll
+        for (int i = 0; i < KQ; ++i) {
+            float x[4] = {0.f, 0.f, 0.f, 0.f};  // k >= Kp: never used
+            if (128 * i + 4 * lane < Kp) load4_ro(A + (size_t)(row + r) * Kp + 128 * i + 4 * lane, x);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) op[r][4 * i + q] = x[q];
+        }
+    }
+}
+
+// Y_own += dt (op . X [+ g f^T]) on the tile starting at row0 (8 columns a pass).
+template <int KQ, bool FORCED>
+__device__ __forceinline__ void wl_half_step(const float (&op)[4][4 * KQ], const float* __restrict__ X,
+                                               float* __restrict__ Y, float* __restrict__ comp,
+                                               const float* __restrict__ gown,
+                                               const float* __restrict__ fcol, const float dt,
+                                               const int Wa, const int Kp, const int row0,
+                                               const int warp, const int lane) {
+    constexpr int CB = 8;
+    for (int c0 = 0; c0 < Wa; c0 += CB) {
+        float acc[4][CB];
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+#pragma unroll
+            for (int cc = 0; cc < CB; ++cc) acc[r][cc] = 0.f;
+#pragma unroll
+        for (int i = 0; i < KQ; ++i) {
+            if (128 * i + 4 * lane >= Kp) continue;
+            float x[CB][4];
+#pragma unroll
+            for (int cc = 0; cc < CB; ++cc) load4(X + (size_t)(c0 + cc) * Kp + 128 * i + 4 * lane, x[cc]);
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+#pragma unroll
+                for (int cc = 0; cc < CB; ++cc)
+#pragma unroll
+                    for (int r = 0; r < 4; ++r) acc[r][cc] = fmadd(op[r][4 * i + q], x[cc][q], acc[r][cc]);
+        }
+        float v[4 * CB];
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+#pragma unroll
+            for (int cc = 0; cc < CB; ++cc) v[r * CB + cc] = acc[r][cc];
+        int vi;
+        const float tot = reduce_scatter32(v, lane, vi);
+        const int rl = 4 * warp + vi / CB;
+        const int c = c0 + vi % CB;
+        float inc = tot;
+        if (FORCED) inc = fmadd(gown[rl], fcol[c], inc);
+        inc = inc * dt;
+        float* yp = Y + (size_t)c * Kp + row0 + rl;
+        *yp = kahan_add(*yp, inc, comp[c * kRowsPerCta + rl]);
     }
 }
 
@@ -227,11 +312,11 @@ __device__ __forceinline__ void add_reference(T* __restrict__ Y, float* __restri
 // The one-block kernel's work on one column block: columns [gc0, gc0 + ncol)
 // of the caller's arrays, operator `gop` of the table (rank-3 launch) or the
 // launch's own operator (gop null).
-// GEN (work-list launch, operators streamed from L2): the Kp / 32 row tiles
-// are dealt out to the cluster's CTAs as evenly as they go (the first
+// GEN (work-list launch, operators streamed from L2, FP32): the Kp / 32 row
+// tiles are dealt out to the cluster's CTAs as evenly as they go (the first
 // Kp/32 mod cs CTAs take one more; a CTA may own none), a.nrt is the most
-// any CTA owns, and the k loops stop after Kp / 64 of their KI groups.
-// Otherwise every CTA owns a.nrt tiles and Kp = 64 KI.
+// any CTA owns, and the products run on the 4-row half-step above for any
+// Kp <= 64 KI.  Otherwise every CTA owns a.nrt tiles and Kp = 64 KI.
 template <typename T, int KI, int CB, bool RESIDENT, bool GEN = false>
 __device__ __forceinline__ void simt_body(cg::cluster_group& cluster, const Rank2Args& a,
                                           const GroupOp* gop, const int gc0, const int ncol) {
@@ -239,7 +324,6 @@ __device__ __forceinline__ void simt_body(cg::cluster_group& cluster, const Rank
     const int crank = (int)cluster.block_rank();
     const int Wa = a.Wa;
     const int Kp = a.Kp;
-    const int ki = GEN ? Kp / 64 : KI;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int j = lane & 15;
     const int rp = warp * 2 + (lane >> 4);
@@ -301,6 +385,7 @@ __device__ __forceinline__ void simt_body(cg::cluster_group& cluster, const Rank
 
     T opA[2][4 * KI];
     T opB[2][4 * KI];
+    float opQ[GEN ? 4 : 1][GEN ? 2 * KI : 1];  // GEN: 4 rows, k groups of 128 (KI / 2 of them)
     const T* __restrict__ Avs = static_cast<const T*>(gop ? gop->Avs_rm : a.Avs_rm);
     const T* __restrict__ Asv = static_cast<const T*>(gop ? gop->Asv_rm : a.Asv_rm);
     if (RESIDENT && nrt_own > 0) {
@@ -315,9 +400,15 @@ __device__ __forceinline__ void simt_body(cg::cluster_group& cluster, const Rank
         // ---- velocity half-step: V_own += dt (Avs_own S + g f_n^T [+ Xv])
         for (int rt = 0; rt < nrt_own; ++rt) {
             const int rowt = row0 + rt * kRowsPerCta;
-            if (!RESIDENT) load_op_rows<T, KI, GEN>(opA, Avs, Kp, rowt + 2 * rp, j, ki);
-            half_step<T, KI, CB, true, GEN>(opA, Sf, Vf, cV + rt * Wa * kRowsPerCta,
-                                            gown + rt * kRowsPerCta, fcol, dt, Wa, Kp, rowt, rp, j, ki);
+            if constexpr (GEN) {
+                wl_load_op<KI / 2>(opQ, Avs, Kp, rowt + 4 * warp, lane);
+                wl_half_step<KI / 2, true>(opQ, Sf, Vf, cV + rt * Wa * kRowsPerCta,
+                                             gown + rt * kRowsPerCta, fcol, dt, Wa, Kp, rowt, warp, lane);
+            } else {
+                if (!RESIDENT) load_op_rows<T, KI>(opA, Avs, Kp, rowt + 2 * rp, j);
+                half_step<T, KI, CB, true>(opA, Sf, Vf, cV + rt * Wa * kRowsPerCta,
+                                           gown + rt * kRowsPerCta, fcol, dt, Wa, Kp, rowt, rp, j);
+            }
         }
         if (a.Xv) {  // kernel parameters, read where used: no register held across the loop
             __syncthreads();
@@ -331,9 +422,15 @@ __device__ __forceinline__ void simt_body(cg::cluster_group& cluster, const Rank
         // ---- stress half-step with the new velocity: S_own += dt (Asv_own V [+ Xs])
         for (int rt = 0; rt < nrt_own; ++rt) {
             const int rowt = row0 + rt * kRowsPerCta;
-            if (!RESIDENT) load_op_rows<T, KI, GEN>(opB, Asv, Kp, rowt + 2 * rp, j, ki);
-            half_step<T, KI, CB, false, GEN>(opB, Vf, Sf, cS + rt * Wa * kRowsPerCta, gown, fcol, dt, Wa,
-                                             Kp, rowt, rp, j, ki);
+            if constexpr (GEN) {
+                wl_load_op<KI / 2>(opQ, Asv, Kp, rowt + 4 * warp, lane);
+                wl_half_step<KI / 2, false>(opQ, Vf, Sf, cS + rt * Wa * kRowsPerCta, gown, fcol, dt, Wa,
+                                              Kp, rowt, warp, lane);
+            } else {
+                if (!RESIDENT) load_op_rows<T, KI>(opB, Asv, Kp, rowt + 2 * rp, j);
+                half_step<T, KI, CB, false>(opB, Vf, Sf, cS + rt * Wa * kRowsPerCta, gown, fcol, dt, Wa,
+                                            Kp, rowt, rp, j);
+            }
         }
         if (a.Xs) {
             __syncthreads();

@@ -64,15 +64,20 @@ def test_batched_vs_oracle_and_individual(rom):
         Z = np.zeros((p.Kv, p.M))
         Vo, So, tro = oracle.forward(p.Avs, p.Asv, p.g, p.C if p.R else None, p.dt, Z, Z, N,
                                      T=p.T, r=r if p.R else 0)
-        assert rel(V.cpu().numpy(), Vo) <= 1e-4 and rel(S.cpu().numpy(), So) <= 1e-4
+        assert colmax_rel(V.cpu().numpy(), Vo) <= 1e-4 and colmax_rel(S.cpu().numpy(), So) <= 1e-4
         if tr is not None:
-            assert rel(tr.transpose(1, 2).cpu().numpy(), tro) <= 1e-4
-        # the same job alone through rom_run_rank2 gives the same bits
+            # per realization m: every record of every receiver (oracle: nrec x R x M)
+            trg = tr.transpose(1, 2).cpu().numpy().reshape(-1, p.M)
+            assert colmax_rel(trg, np.asarray(tro).reshape(-1, p.M)) <= 1e-4
+        # the same job alone through rom_run_rank2: the work-list kernel sums
+        # in another order (32 k lanes, 4 rows a thread), so the two FP32
+        # results agree to rounding, column by column
         V1 = rom.Rom.new_state(p.Kv, p.M, "fp32")
         S1 = rom.Rom.new_state(p.Ks, p.M, "fp32")
         h.run_rank2(V1, S1, T, N, prec="fp32")
         torch.cuda.synchronize()
-        assert torch.equal(V1, V) and torch.equal(S1, S)
+        assert colmax_rel(V.cpu().numpy(), V1.cpu().numpy()) <= 2e-5
+        assert colmax_rel(S.cpu().numpy(), S1.cpu().numpy()) <= 2e-5
 
 
 def test_batched_graph_replay(rom):
