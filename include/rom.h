@@ -409,11 +409,14 @@ rom_status rom_autotune_batched(const rom_job* jobs, int njobs, int prec, int pr
  * sweep that keeps a checkpoint (V, S and their Kahan carries) every
  * ckpt_every steps (0: keep every trace, one segment) and recomputes each
  * segment's traces, bit for bit, before reversing it.
- * Outputs: gV0 (Kv x M), gS0 (Ks x M), gT (M) device float; *loss (host).
- * workspace: device, rom_adjoint_workspace_size bytes, or NULL to let the
- * library allocate it for the call.  Device buffers only; FP32 only;
- * Kv, Ks <= 1024 (above 512 the reverse kernel reads the transposed
- * operators from L2 every half-step instead of keeping them in registers).
+ * Outputs: gV0 (Kv x M), gS0 (Ks x M), gT (M) on the device; *loss (host).
+ * prec: ROM_FP32 (V0, S0, T, ystar and the outputs float; the adjoint state
+ * Kahan-compensated; Kv, Ks <= 1024, and above 512 the reverse kernel reads
+ * the transposed operators from L2 every half-step instead of keeping them
+ * in registers) or ROM_FP64 (the check path: all of them double, plain
+ * FP64 sums; Kv, Ks <= 512); other precisions: ROM_E_UNSUPPORTED.
+ * workspace: device, rom_adjoint_workspace_size bytes for the same prec, or
+ * NULL to let the library allocate it for the call.  Device buffers only.
  * Synchronous on `stream`.
  */
 rom_status rom_adjoint(rom_t h, const void* V0, const void* S0, const void* T, int M, int nsteps,

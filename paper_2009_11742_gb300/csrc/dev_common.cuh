@@ -35,6 +35,13 @@ __device__ __forceinline__ float ricker_dT_eval(long long step, double dt, float
                                ((double)T * (double)T * (double)T));
     return (2.0f * u - 3.0f) * expf(-u) * dudT;
 }
+__device__ __forceinline__ double ricker_dT_eval(long long step, double dt, double T) {
+    const double tau = (double)step * dt - 1.5 * T;
+    const double a = 3.14159265358979323846 * tau / T;
+    const double u = a * a;
+    const double dudT = -9.8696044010893586188 * tau * (3.0 * T + 2.0 * tau) / (T * T * T);
+    return (2.0 * u - 3.0) * exp(-u) * dudT;
+}
 
 // First derivative of a Gaussian (the paper's second source signal, Sec.
 // 3.2): the tau-derivative of the Ricker's envelope exp(-pi^2 tau^2 / T^2),
@@ -60,6 +67,13 @@ __device__ __forceinline__ float gauss1_dT_eval(long long step, double dt, float
     const float dadT = (float)(-3.14159265358979323846 * t / ((double)T * (double)T));
     return -(float)kSqrt2e * (1.0f - 2.0f * a * a) * expf(-a * a) * dadT;
 }
+__device__ __forceinline__ double gauss1_dT_eval(long long step, double dt, double T) {
+    const double t = (double)step * dt;
+    const double tau = t - 1.5 * T;
+    const double a = 3.14159265358979323846 * tau / T;
+    const double dadT = -3.14159265358979323846 * t / (T * T);
+    return -kSqrt2e * (1.0 - 2.0 * a * a) * exp(-a * a) * dadT;
+}
 
 // The FP32 source signal of kind `wavelet` from per-column FP64 constants
 // m15T = -1.5 T and piT = pi / T set once per run: a = (t - 1.5 T) pi / T
@@ -78,8 +92,9 @@ template <typename T>
 __device__ __forceinline__ T wavelet_eval(int wavelet, long long step, double dt, T period) {
     return wavelet == 1 ? gauss1_eval(step, dt, period) : ricker_eval(step, dt, period);
 }
-__device__ __forceinline__ float wavelet_dT_eval(int wavelet, long long step, double dt, float T) {
-    return wavelet == 1 ? gauss1_dT_eval(step, dt, T) : ricker_dT_eval(step, dt, T);
+template <typename T>
+__device__ __forceinline__ T wavelet_dT_eval(int wavelet, long long step, double dt, T period) {
+    return wavelet == 1 ? gauss1_dT_eval(step, dt, period) : ricker_dT_eval(step, dt, period);
 }
 
 // Four consecutive elements from shared or global memory (16-byte aligned).

@@ -6,9 +6,9 @@
 
 namespace romk {
 
-static void* adjoint_kernel(int KI) {
+static void* adjoint_kernel_f32(int KI) {
 #define ROM_ADJ_CASE(k) \
-    case k: return (void*)&rank2_adjoint_kernel<k, 8>;
+    case k: return (void*)&rank2_adjoint_kernel<float, k, 8>;
     switch (KI) {
         ROM_ADJ_CASE(1) ROM_ADJ_CASE(2) ROM_ADJ_CASE(3) ROM_ADJ_CASE(4)
         ROM_ADJ_CASE(5) ROM_ADJ_CASE(6) ROM_ADJ_CASE(7) ROM_ADJ_CASE(8)
@@ -19,24 +19,45 @@ static void* adjoint_kernel(int KI) {
 #undef ROM_ADJ_CASE
 }
 
-// Kp <= 512: one 32-row tile per CTA (Kp / 32 CTAs, operators in registers);
-// 512 < Kp <= 1024: two tiles per CTA (Kp / 64 CTAs, operators read from L2).
-bool plan_adjoint(int Kp, int M, int R, AdjPlan* p) {
-    if (Kp <= 0 || Kp % 64 != 0 || Kp > 1024 || M <= 0 || R <= 0) return false;
+// FP64: 4 columns a pass (the register budget of the double operator rows).
+static void* adjoint_kernel_f64(int KI) {
+#define ROM_ADJ_CASE(k) \
+    case k: return (void*)&rank2_adjoint_kernel<double, k, 4>;
+    switch (KI) {
+        ROM_ADJ_CASE(1) ROM_ADJ_CASE(2) ROM_ADJ_CASE(3) ROM_ADJ_CASE(4)
+        ROM_ADJ_CASE(5) ROM_ADJ_CASE(6) ROM_ADJ_CASE(7) ROM_ADJ_CASE(8)
+        default: return nullptr;
+    }
+#undef ROM_ADJ_CASE
+}
+
+static void* adjoint_kernel(const AdjPlan& p) { return p.f64 ? adjoint_kernel_f64(p.KI) : adjoint_kernel_f32(p.KI); }
+
+static size_t adjoint_smem(bool f64, int W, int Kp, int R, int nrt) {
+    return f64 ? adj_smem_layout<double>(W, Kp, R, nrt).total : adj_smem_layout<float>(W, Kp, R, nrt).total;
+}
+
+// FP32, Kp <= 512: one 32-row tile per CTA (Kp / 32 CTAs, operators in
+// registers); 512 < Kp <= 1024: two tiles per CTA (Kp / 64 CTAs, operators
+// read from L2).  FP64: Kp <= 512, one tile per CTA.  Widths are multiples of
+// the kernel's columns per pass.
+bool plan_adjoint(int Kp, int M, int R, AdjPlan* p, bool f64) {
+    if (Kp <= 0 || Kp % 64 != 0 || Kp > (f64 ? 512 : 1024) || M <= 0 || R <= 0) return false;
+    p->f64 = f64;
     p->KI = Kp / 64;
     const int nrt = Kp > 512 ? 2 : 1;
     p->cs = Kp / (32 * nrt);
-    p->cb = 8;
+    p->cb = f64 ? 4 : 8;
     const int smax = device_smem_optin();
     int wcap = 0;
     for (int w = 8; w <= 2048; w += 8) {
-        if (adj_smem_layout(w, Kp, R, nrt).total > (size_t)smax) break;
+        if (adjoint_smem(f64, w, Kp, R, nrt) > (size_t)smax) break;
         wcap = w;
     }
     if (wcap == 0) return false;
-    void* fn = adjoint_kernel(p->KI);
+    void* fn = adjoint_kernel(*p);
     if (!fn) return false;
-    const size_t smem_probe = adj_smem_layout(wcap, Kp, R, nrt).total;
+    const size_t smem_probe = adjoint_smem(f64, wcap, Kp, R, nrt);
     if (prepare_kernel<float>(fn, smem_probe) != cudaSuccess) return false;
     ClusterLaunch probe(p->cs, 1, kThreads, smem_probe);
     const int nact = probe.max_active(fn);
@@ -47,15 +68,17 @@ bool plan_adjoint(int Kp, int M, int R, AdjPlan* p) {
     p->Wv = wv;
     p->Wa = wv;
     p->nclusters = (M + wv - 1) / wv;
-    p->smem = adj_smem_layout(p->Wa, Kp, R, nrt).total;
+    p->smem = adjoint_smem(f64, p->Wa, Kp, R, nrt);
     return true;
 }
 
-cudaError_t launch_adjoint(const AdjArgs& a_in, const AdjPlan& p, cudaStream_t st) {
-    AdjArgs a = a_in;
+template <typename T>
+static cudaError_t launch_adjoint_t(const AdjArgsT<T>& a_in, const AdjPlan& p, cudaStream_t st) {
+    if (p.f64 != (sizeof(T) == 8)) return cudaErrorInvalidValue;
+    AdjArgsT<T> a = a_in;
     a.Wv = p.Wv;
     a.Wa = p.Wa;
-    void* fn = adjoint_kernel(p.KI);
+    void* fn = adjoint_kernel(p);
     if (!fn) return cudaErrorInvalidValue;
     cudaError_t e = prepare_kernel<float>(fn, p.smem);
     if (e != cudaSuccess) return e;
@@ -64,17 +87,29 @@ cudaError_t launch_adjoint(const AdjArgs& a_in, const AdjPlan& p, cudaStream_t s
     return L.launch(fn, args);
 }
 
+cudaError_t launch_adjoint(const AdjArgsT<float>& a, const AdjPlan& p, cudaStream_t st) {
+    return launch_adjoint_t<float>(a, p, st);
+}
+cudaError_t launch_adjoint(const AdjArgsT<double>& a, const AdjPlan& p, cudaStream_t st) {
+    return launch_adjoint_t<double>(a, p, st);
+}
+
 // out[m] = sum over CTAs (in rank order) of part[rank][m].
-__global__ void sum_partials_kernel(const float* __restrict__ part, int cs, int M, float* __restrict__ out) {
+template <typename T>
+__global__ void sum_partials_kernel(const T* __restrict__ part, int cs, int M, T* __restrict__ out) {
     const int m = blockIdx.x * blockDim.x + threadIdx.x;
     if (m >= M) return;
-    float s = 0.f;
+    T s = T(0);
     for (int k = 0; k < cs; ++k) s += part[(size_t)k * M + m];
     out[m] = s;
 }
 
 cudaError_t launch_sum_partials(const float* part, int cs, int M, float* out, cudaStream_t st) {
-    sum_partials_kernel<<<(M + 255) / 256, 256, 0, st>>>(part, cs, M, out);
+    sum_partials_kernel<float><<<(M + 255) / 256, 256, 0, st>>>(part, cs, M, out);
+    return cudaGetLastError();
+}
+cudaError_t launch_sum_partials(const double* part, int cs, int M, double* out, cudaStream_t st) {
+    sum_partials_kernel<double><<<(M + 255) / 256, 256, 0, st>>>(part, cs, M, out);
     return cudaGetLastError();
 }
 

@@ -12,13 +12,15 @@
 //
 // The kernel is the one-block cluster kernel of rank2_simt.cuh run backwards
 // in time with the transposed operators (the column-major copies of Asv and
-// Avs are the row-major Asv^T and Avs^T): resident in registers up to
+// Avs are the row-major Asv^T and Avs^T).  FP32: resident in registers up to
 // Kp = 512 (one 32-row tile per CTA), and for 512 < Kp <= 1024 read from L2
 // for each of the CTA's two 32-row tiles every half-step, as the forward
-// kernel does there.  Half A's epilogue adds the rank-R source 2 C^T r^{n+1}
-// (C columns of the CTA's rows and the step's residuals staged in shared
-// memory), and a deterministic per-CTA column reduction accumulates the
-// period gradient.
+// kernel does there; the adjoint state is Kahan-compensated.  FP64 (the
+// check path, Kp <= 512, one tile per CTA): resident up to Kp = 256 and
+// read from L2 per half-step above, plain sums, as the FP64 forward kernel.
+// Half A's epilogue adds the rank-R source 2 C^T r^{n+1} (C columns of the
+// CTA's rows and the step's residuals staged in shared memory), and a
+// deterministic per-CTA column reduction accumulates the period gradient.
 #pragma once
 
 #include <cooperative_groups.h>
@@ -30,84 +32,94 @@
 
 namespace romk {
 
-// Steps of df/dT tabulated at a time (shared memory, kAdjTab x Wa floats).
+// Steps of df/dT tabulated at a time (shared memory, kAdjTab x Wa values).
 constexpr int kAdjTab = 64;
 
 struct AdjSmem {
     size_t Vf, Sf, cV, cS, Ccol, rbuf, g, T, gT, dfT, total;
 };
 
-// nrt: 32-row tiles owned per CTA (1 for Kp <= 512, 2 above).
+// nrt: 32-row tiles owned per CTA (1 for Kp <= 512, 2 above); T the element
+// type (the carries are FP32 and only the FP32 path has them).
+template <typename T>
 __host__ __device__ inline AdjSmem adj_smem_layout(int Wa, int Kp, int R, int nrt = 1) {
     AdjSmem s{};
     const size_t own = (size_t)nrt * kRowsPerCta;
+    const size_t ncarry = sizeof(T) == 4 ? (size_t)Wa * own : 0;
     size_t o = 0;
-    s.Vf = o;   o += align16((size_t)Wa * Kp * sizeof(float));
-    s.Sf = o;   o += align16((size_t)Wa * Kp * sizeof(float));
-    s.cV = o;   o += align16((size_t)Wa * own * sizeof(float));
-    s.cS = o;   o += align16((size_t)Wa * own * sizeof(float));
-    s.Ccol = o; o += align16((size_t)R * own * sizeof(float));
-    s.rbuf = o; o += align16((size_t)R * Wa * sizeof(float));
-    s.g = o;    o += align16(own * sizeof(float));
-    s.T = o;    o += align16((size_t)Wa * sizeof(float));
-    s.gT = o;   o += align16((size_t)Wa * sizeof(float));
-    s.dfT = o;  o += align16((size_t)kAdjTab * Wa * sizeof(float));
+    s.Vf = o;   o += align16((size_t)Wa * Kp * sizeof(T));
+    s.Sf = o;   o += align16((size_t)Wa * Kp * sizeof(T));
+    s.cV = o;   o += align16(ncarry * sizeof(float));
+    s.cS = o;   o += align16(ncarry * sizeof(float));
+    s.Ccol = o; o += align16((size_t)R * own * sizeof(T));
+    s.rbuf = o; o += align16((size_t)R * Wa * sizeof(T));
+    s.g = o;    o += align16(own * sizeof(T));
+    s.T = o;    o += align16((size_t)Wa * sizeof(T));
+    s.gT = o;   o += align16((size_t)Wa * sizeof(T));
+    s.dfT = o;  o += align16((size_t)kAdjTab * Wa * sizeof(T));
     s.total = o;
     return s;
 }
 
 // Half A of a reverse step on one 32-row tile of the CTA (rows row0 ..):
-//   Y_own += dt (op . X) + 2 C_own^T r   (Kahan-compensated).
+//   Y_own += dt (op . X) + 2 C_own^T r   (Kahan-compensated in FP32).
 // Ccol points at the tile's first row of the CTA's C columns (row stride
-// cstride floats).
-template <int KI, int CB>
-__device__ __forceinline__ void adj_half_a(const float (&op)[2][4 * KI], const float* __restrict__ X,
-                                           float* __restrict__ Y, float* __restrict__ comp,
-                                           const float* __restrict__ Ccol, const int cstride,
-                                           const float* __restrict__ rbuf,
-                                           const int R, const float dt, const int Wa, const int Kp,
+// cstride values).
+template <typename T, int KI, int CB>
+__device__ __forceinline__ void adj_half_a(const T (&op)[2][4 * KI], const T* __restrict__ X,
+                                           T* __restrict__ Y, float* __restrict__ comp,
+                                           const T* __restrict__ Ccol, const int cstride,
+                                           const T* __restrict__ rbuf,
+                                           const int R, const T dt, const int Wa, const int Kp,
                                            const int row0, const int rp, const int j) {
     for (int c0 = 0; c0 < Wa; c0 += CB) {
-        float acc[2][CB];
+        T acc[2][CB];
 #pragma unroll
-        for (int cc = 0; cc < CB; ++cc) { acc[0][cc] = 0.f; acc[1][cc] = 0.f; }
+        for (int cc = 0; cc < CB; ++cc) { acc[0][cc] = T(0); acc[1][cc] = T(0); }
 #pragma unroll
         for (int i = 0; i < KI; ++i) {
-            float x[CB][4];
+            T x[CB][4];
 #pragma unroll
             for (int cc = 0; cc < CB; ++cc) load4(X + (size_t)(c0 + cc) * Kp + 64 * i + 4 * j, x[cc]);
 #pragma unroll
             for (int q = 0; q < 4; ++q)
 #pragma unroll
                 for (int cc = 0; cc < CB; ++cc) {
-                    acc[0][cc] = __fmaf_rn(op[0][4 * i + q], x[cc][q], acc[0][cc]);
-                    acc[1][cc] = __fmaf_rn(op[1][4 * i + q], x[cc][q], acc[1][cc]);
+                    acc[0][cc] = fmadd(op[0][4 * i + q], x[cc][q], acc[0][cc]);
+                    acc[1][cc] = fmadd(op[1][4 * i + q], x[cc][q], acc[1][cc]);
                 }
         }
-        float v[2 * CB];
+        T v[2 * CB];
 #pragma unroll
         for (int cc = 0; cc < CB; ++cc) { v[cc] = acc[0][cc]; v[CB + cc] = acc[1][cc]; }
         int vi;
         bool active;
-        const float tot = reduce_scatter16<float, 2 * CB>(v, j, vi, active);
+        const T tot = reduce_scatter16<T, 2 * CB>(v, j, vi, active);
         if (active) {
             const int rl = 2 * rp + vi / CB;
             const int c = c0 + vi % CB;
-            float src = 0.f;
-            for (int jr = 0; jr < R; ++jr) src = __fmaf_rn(Ccol[jr * cstride + rl], rbuf[jr * Wa + c], src);
-            const float inc = __fmaf_rn(tot, dt, 2.f * src);
-            float* yp = Y + (size_t)c * Kp + row0 + rl;
-            *yp = kahan_add(*yp, inc, comp[c * kRowsPerCta + rl]);
+            T src = T(0);
+            for (int jr = 0; jr < R; ++jr) src = fmadd(Ccol[jr * cstride + rl], rbuf[jr * Wa + c], src);
+            const T inc = fmadd(tot, dt, T(2) * src);
+            T* yp = Y + (size_t)c * Kp + row0 + rl;
+            if constexpr (sizeof(T) == 4) {
+                *yp = kahan_add(*yp, inc, comp[c * kRowsPerCta + rl]);
+            } else {
+                *yp = *yp + inc;
+            }
         }
     }
 }
 
-// KI = Kp / 64 (<= 16); operators resident in registers for KI <= 8 (one
-// 32-row tile per CTA), streamed per tile above (two tiles per CTA).
-template <int KI, int CB>
-__global__ void __launch_bounds__(kThreads, 1) rank2_adjoint_kernel(const AdjArgs a) {
+// KI = Kp / 64.  FP32 (KI <= 16): operators resident in registers for
+// KI <= 8 (one 32-row tile per CTA), streamed per tile above (two tiles per
+// CTA).  FP64 (KI <= 8): one tile per CTA, resident for KI <= 4.
+template <typename T, int KI, int CB>
+__global__ void __launch_bounds__(kThreads, 1) rank2_adjoint_kernel(const AdjArgsT<T> a) {
+    constexpr bool F32 = sizeof(T) == 4;
+    static_assert(F32 ? KI <= 16 : KI <= 8, "unsupported size");
     constexpr int NRT = KI > 8 ? 2 : 1;
-    constexpr bool RES = NRT == 1;
+    constexpr bool RES = F32 ? NRT == 1 : KI <= 4;
     constexpr int OWN = NRT * kRowsPerCta;
     cg::cluster_group cluster = cg::this_cluster();
     const int cs = (int)cluster.num_blocks();
@@ -120,28 +132,28 @@ __global__ void __launch_bounds__(kThreads, 1) rank2_adjoint_kernel(const AdjArg
     const int j = lane & 15;
     const int rp = warp * 2 + (lane >> 4);
     const int row0 = crank * OWN;
-    const float dt = (float)a.dt;
+    const T dt = (T)a.dt;
 
     extern __shared__ __align__(16) unsigned char smem[];
-    const AdjSmem L = adj_smem_layout(Wa, Kp, R, NRT);
-    float* Vf = reinterpret_cast<float*>(smem + L.Vf);
-    float* Sf = reinterpret_cast<float*>(smem + L.Sf);
+    const AdjSmem L = adj_smem_layout<T>(Wa, Kp, R, NRT);
+    T* Vf = reinterpret_cast<T*>(smem + L.Vf);
+    T* Sf = reinterpret_cast<T*>(smem + L.Sf);
     float* cV = reinterpret_cast<float*>(smem + L.cV);
     float* cS = reinterpret_cast<float*>(smem + L.cS);
-    float* Ccol = reinterpret_cast<float*>(smem + L.Ccol);  // [R][OWN]: C[j][row0 + ro]
-    float* rbuf = reinterpret_cast<float*>(smem + L.rbuf);  // [R][Wa]: residual of the step
-    float* gown = reinterpret_cast<float*>(smem + L.g);
-    float* Tcol = reinterpret_cast<float*>(smem + L.T);
-    float* gTacc = reinterpret_cast<float*>(smem + L.gT);
-    float* dfT = reinterpret_cast<float*>(smem + L.dfT);    // [kAdjTab][Wa]: df/dT of the chunk
+    T* Ccol = reinterpret_cast<T*>(smem + L.Ccol);  // [R][OWN]: C[j][row0 + ro]
+    T* rbuf = reinterpret_cast<T*>(smem + L.rbuf);  // [R][Wa]: residual of the step
+    T* gown = reinterpret_cast<T*>(smem + L.g);
+    T* Tcol = reinterpret_cast<T*>(smem + L.T);
+    T* gTacc = reinterpret_cast<T*>(smem + L.gT);
+    T* dfT = reinterpret_cast<T*>(smem + L.dfT);    // [kAdjTab][Wa]: df/dT of the chunk
 
     for (int idx = tid; idx < Wa * Kp; idx += kThreads) {
         const int c = idx / Kp, k = idx % Kp;
-        Vf[idx] = (c < ncol && k < a.Kv) ? a.lamV[(size_t)(col0 + c) * a.Kv + k] : 0.f;
-        Sf[idx] = (c < ncol && k < a.Ks) ? a.lamS[(size_t)(col0 + c) * a.Ks + k] : 0.f;
+        Vf[idx] = (c < ncol && k < a.Kv) ? a.lamV[(size_t)(col0 + c) * a.Kv + k] : T(0);
+        Sf[idx] = (c < ncol && k < a.Ks) ? a.lamS[(size_t)(col0 + c) * a.Ks + k] : T(0);
     }
-    // carries: [row tile][column][32 rows]
-    for (int idx = tid; idx < NRT * Wa * kRowsPerCta; idx += kThreads) {
+    // carries (FP32): [row tile][column][32 rows]
+    for (int idx = tid; idx < (F32 ? NRT * Wa * kRowsPerCta : 0); idx += kThreads) {
         const int rt = idx / (Wa * kRowsPerCta);
         const int rem = idx - rt * Wa * kRowsPerCta;
         const int c = rem / kRowsPerCta, rl = rem % kRowsPerCta, row = row0 + rt * kRowsPerCta + rl;
@@ -154,13 +166,13 @@ __global__ void __launch_bounds__(kThreads, 1) rank2_adjoint_kernel(const AdjArg
     }
     for (int ro = tid; ro < OWN; ro += kThreads) gown[ro] = a.g_p[row0 + ro];
     for (int c = tid; c < Wa; c += kThreads) {
-        Tcol[c] = (c < ncol) ? a.Tper[col0 + c] : 1.f;
-        gTacc[c] = (c < ncol) ? a.gTpart[(size_t)crank * a.M + col0 + c] : 0.f;
+        Tcol[c] = (c < ncol) ? a.Tper[col0 + c] : T(1);
+        gTacc[c] = (c < ncol) ? a.gTpart[(size_t)crank * a.M + col0 + c] : T(0);
     }
-    float opA[2][4 * KI], opB[2][4 * KI];
+    T opA[2][4 * KI], opB[2][4 * KI];
     if (RES) {
-        load_op_rows<float, KI>(opA, a.opA_rm, Kp, row0 + 2 * rp, j);
-        load_op_rows<float, KI>(opB, a.opB_rm, Kp, row0 + 2 * rp, j);
+        load_op_rows<T, KI>(opA, a.opA_rm, Kp, row0 + 2 * rp, j);
+        load_op_rows<T, KI>(opB, a.opB_rm, Kp, row0 + 2 * rp, j);
     }
     cluster.sync();
 
@@ -175,15 +187,15 @@ __global__ void __launch_bounds__(kThreads, 1) rank2_adjoint_kernel(const AdjArg
             for (int idx = tid; idx < kAdjTab * ncol; idx += kThreads) {
                 const int i = idx / ncol, c = idx % ncol;
                 if (n - i >= a.n_lo)
-                    dfT[i * Wa + c] = wavelet_dT_eval(a.wavelet, (long long)a.n0 + n - i, a.dt, Tcol[c]);
+                    dfT[i * Wa + c] = wavelet_dT_eval<T>(a.wavelet, (long long)a.n0 + n - i, a.dt, Tcol[c]);
             }
         }
-        const float* dfn = dfT + (done % kAdjTab) * Wa;
+        const T* dfn = dfT + (done % kAdjTab) * Wa;
         // residual r^{n+1} = C V^{n+1} - ystar^{n+1} of this block's columns
         const int rec = n + 1 - a.rec_base;  // trace record holding C V^{n+1}
         for (int idx = tid; idx < R * Wa; idx += kThreads) {
             const int jr = idx / Wa, c = idx % Wa;
-            float rv = 0.f;
+            T rv = T(0);
             if (c < ncol) {
                 const size_t o = ((size_t)rec * a.M + col0 + c) * R + jr;
                 const size_t oy = ((size_t)n * a.M + col0 + c) * R + jr;  // ystar record of V^{n+1}
@@ -196,33 +208,33 @@ __global__ void __launch_bounds__(kThreads, 1) rank2_adjoint_kernel(const AdjArg
 #pragma unroll
         for (int rt = 0; rt < NRT; ++rt) {
             const int rowt = row0 + rt * kRowsPerCta;
-            if (!RES) load_op_rows<float, KI>(opA, a.opA_rm, Kp, rowt + 2 * rp, j);
-            adj_half_a<KI, CB>(opA, Sf, Vf, cV + rt * Wa * kRowsPerCta, Ccol + rt * kRowsPerCta, OWN,
-                               rbuf, R, dt, Wa, Kp, rowt, rp, j);
+            if (!RES) load_op_rows<T, KI>(opA, a.opA_rm, Kp, rowt + 2 * rp, j);
+            adj_half_a<T, KI, CB>(opA, Sf, Vf, cV + rt * Wa * kRowsPerCta, Ccol + rt * kRowsPerCta, OWN,
+                                  rbuf, R, dt, Wa, Kp, rowt, rp, j);
         }
         __syncthreads();
         // period gradient: dt (g_own . a_V[:, c]) df/dT(t_n; T_c), fixed reduction order
         for (int c = warp; c < ncol; c += kThreads / 32) {
-            float s = gown[lane] * Vf[(size_t)c * Kp + row0 + lane];
+            T s = gown[lane] * Vf[(size_t)c * Kp + row0 + lane];
 #pragma unroll
             for (int rt = 1; rt < NRT; ++rt)
-                s = __fmaf_rn(gown[rt * kRowsPerCta + lane], Vf[(size_t)c * Kp + row0 + rt * kRowsPerCta + lane], s);
+                s = fmadd(gown[rt * kRowsPerCta + lane], Vf[(size_t)c * Kp + row0 + rt * kRowsPerCta + lane], s);
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-            if (lane == 0) gTacc[c] = __fmaf_rn(dt * s, dfn[c], gTacc[c]);
+            if (lane == 0) gTacc[c] = fmadd(dt * s, dfn[c], gTacc[c]);
         }
-        push_own_rows<float>(cluster, Vf, Wa, Kp, row0, cs, crank, NRT);
+        push_own_rows<T>(cluster, Vf, Wa, Kp, row0, cs, crank, NRT);
         cluster.sync();
         // ---- half B: lamS <- lamS + dt Avs^T a_V
 #pragma unroll
         for (int rt = 0; rt < NRT; ++rt) {
             const int rowt = row0 + rt * kRowsPerCta;
-            if (!RES) load_op_rows<float, KI>(opB, a.opB_rm, Kp, rowt + 2 * rp, j);
-            half_step<float, KI, CB, false>(opB, Vf, Sf, cS + rt * Wa * kRowsPerCta, gown, gown, dt, Wa,
-                                            Kp, rowt, rp, j);
+            if (!RES) load_op_rows<T, KI>(opB, a.opB_rm, Kp, rowt + 2 * rp, j);
+            half_step<T, KI, CB, false>(opB, Vf, Sf, cS + rt * Wa * kRowsPerCta, gown, gown, dt, Wa,
+                                        Kp, rowt, rp, j);
         }
         __syncthreads();
-        push_own_rows<float>(cluster, Sf, Wa, Kp, row0, cs, crank, NRT);
+        push_own_rows<T>(cluster, Sf, Wa, Kp, row0, cs, crank, NRT);
         cluster.sync();
     }
 
@@ -231,15 +243,15 @@ __global__ void __launch_bounds__(kThreads, 1) rank2_adjoint_kernel(const AdjArg
         const int c = idx / OWN, ro = idx % OWN, row = row0 + ro;
         const int ci = (ro / kRowsPerCta) * Wa * kRowsPerCta + c * kRowsPerCta + ro % kRowsPerCta;
         if (row < a.Kv) {
-            const float x = Vf[(size_t)c * Kp + row];
+            const T x = Vf[(size_t)c * Kp + row];
             a.lamV[(size_t)(col0 + c) * a.Kv + row] = x;
-            a.compV[(size_t)(col0 + c) * a.Kv + row] = cV[ci];
+            if (F32) a.compV[(size_t)(col0 + c) * a.Kv + row] = cV[ci];
             bad |= !is_finite(x);
         }
         if (row < a.Ks) {
-            const float x = Sf[(size_t)c * Kp + row];
+            const T x = Sf[(size_t)c * Kp + row];
             a.lamS[(size_t)(col0 + c) * a.Ks + row] = x;
-            a.compS[(size_t)(col0 + c) * a.Ks + row] = cS[ci];
+            if (F32) a.compS[(size_t)(col0 + c) * a.Ks + row] = cS[ci];
             bad |= !is_finite(x);
         }
     }

@@ -1742,50 +1742,35 @@ struct AdjLayout {
     int seg, nseg;
 };
 
-AdjLayout adjoint_layout(const rom_s* h, int M, int nsteps, int ckpt_every) {
+// es: bytes of an element (4 FP32, 8 FP64).  The FP32 path also checkpoints
+// and reverses Kahan carries; the FP64 path keeps the same slots, unused.
+AdjLayout adjoint_layout(const rom_s* h, int M, int nsteps, int ckpt_every, size_t es) {
     AdjLayout L{};
     auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
     L.seg = ckpt_every > 0 && ckpt_every < nsteps ? ckpt_every : nsteps;
     L.nseg = (nsteps + L.seg - 1) / L.seg;
     const size_t kvm = (size_t)(h->Kv + h->Ks) * M;  // one (V, S) pair
     size_t o = 0;
-    L.traces = o; o += al(sizeof(float) * (size_t)L.seg * h->R * M);
-    L.ckpt = o;   o += al(sizeof(float) * 2 * kvm * (size_t)L.nseg);   // state + Kahan carries
-    L.work = o;   o += al(sizeof(float) * 2 * kvm);
+    L.traces = o; o += al(es * (size_t)L.seg * h->R * M);
+    L.ckpt = o;   o += al(es * 2 * kvm * (size_t)L.nseg);   // state + Kahan carries
+    L.work = o;   o += al(es * 2 * kvm);
     L.acomp = o;  o += al(sizeof(float) * kvm);
-    L.gtp = o;    o += al(sizeof(float) * 16 * (size_t)M);
+    L.gtp = o;    o += al(es * 16 * (size_t)M);
     L.acc = o;    o += al(sizeof(double) * 2);
     L.total = o;
     return L;
 }
 
-}  // namespace
-
-extern "C" {
-
-size_t rom_adjoint_workspace_size(rom_t h, int M, int nsteps, int ckpt_every, int prec) {
-    if (!h || M < 1 || nsteps < 1 || ckpt_every < 0 || prec != ROM_FP32) return 0;
-    return adjoint_layout(h, M, nsteps, ckpt_every).total;
-}
-
-rom_status rom_adjoint(rom_t h, const void* V0, const void* S0, const void* T, int M, int nsteps,
-                       const void* ystar, int ckpt_every, void* gV0, void* gS0, void* gT,
-                       double* loss, void* workspace, size_t ws_bytes, int prec, void* stream) {
-    if (!h || !V0 || !S0 || !T || !ystar || !gV0 || !gS0 || !gT || M < 1 || nsteps < 1 ||
-        ckpt_every < 0 || h->R < 1)
-        return ROM_E_INVAL;
-    if (prec != ROM_FP32) return ROM_E_UNSUPPORTED;
-    if (h->xref_M != 0 && h->xref_M != M) return ROM_E_INVAL;  // reference state of another ensemble
-    const void* ptrs[] = {V0, S0, T, ystar, gV0, gS0, gT};
-    for (const void* p : ptrs)
-        if (!is_device_ptr(p)) return ROM_E_INVAL;
-    AdjPlan ap;
-    if (!plan_adjoint(h->Kp, M, h->R, &ap)) {
-        snprintf(g_last_error, sizeof(g_last_error), "no adjoint plan for Kp=%d M=%d", h->Kp, M);
-        return ROM_E_UNSUPPORTED;
-    }
-    cudaStream_t st = static_cast<cudaStream_t>(stream);
-    const AdjLayout L = adjoint_layout(h, M, nsteps, ckpt_every);
+// The forward sweep with checkpoints, then the reverse sweep segment by
+// segment, in element type T (float: ROM_FP32, double: ROM_FP64).
+template <typename T>
+rom_status adjoint_run(rom_s* h, const void* V0, const void* S0, const void* Tp, int M, int nsteps,
+                       const void* ystar, int ckpt_every, void* gV0, void* gS0, void* gT, double* loss,
+                       void* workspace, size_t ws_bytes, const AdjPlan& ap, cudaStream_t st) {
+    constexpr bool F32 = sizeof(T) == 4;
+    constexpr int prec = F32 ? ROM_FP32 : ROM_FP64;
+    constexpr int t = F32 ? 1 : 0;  // index of the handle's operator copies
+    const AdjLayout L = adjoint_layout(h, M, nsteps, ckpt_every, sizeof(T));
     void* own_ws = nullptr;
     if (!workspace) {
         ROM_CUDA(cudaMalloc(&own_ws, L.total));
@@ -1794,68 +1779,67 @@ rom_status rom_adjoint(rom_t h, const void* V0, const void* S0, const void* T, i
         return ROM_E_INVAL;
     }
     char* ws = static_cast<char*>(workspace);
-    float* traces = reinterpret_cast<float*>(ws + L.traces);
-    float* ckpt = reinterpret_cast<float*>(ws + L.ckpt);
-    float* work = reinterpret_cast<float*>(ws + L.work);
+    T* traces = reinterpret_cast<T*>(ws + L.traces);
+    T* ckpt = reinterpret_cast<T*>(ws + L.ckpt);
+    T* work = reinterpret_cast<T*>(ws + L.work);
     float* acomp = reinterpret_cast<float*>(ws + L.acomp);
-    float* gtp = reinterpret_cast<float*>(ws + L.gtp);
+    T* gtp = reinterpret_cast<T*>(ws + L.gtp);
     double* acc = reinterpret_cast<double*>(ws + L.acc);
     const size_t nv = (size_t)h->Kv * M, ns = (size_t)h->Ks * M, kvm = nv + ns;
-    float* wV = work;
-    float* wS = work + nv;
-    float* wcV = work + kvm;
-    float* wcS = work + kvm + nv;
+    T* wV = work;
+    T* wS = work + nv;
+    T* wcV = work + kvm;  // FP32 carries (FP32 path only)
+    T* wcS = work + kvm + nv;
     const size_t rec = (size_t)h->R * M;
-    const float* ys = static_cast<const float*>(ystar);
+    const T* ys = static_cast<const T*>(ystar);
     rom_status s = ROM_OK;
     cudaError_t e = cudaSuccess;
-    auto fail = [&](cudaError_t err, const char* where) {
-        s = cuda_fail(err, where);
-        return s;
-    };
     auto forward = [&](int n_start, int len) -> rom_status {
-        RunBufs b = {wV, wS, const_cast<void*>(T), nullptr, wcV, wcS, traces};
-        return run_rank2_device(h, b, M, len, n_start, 1, ROM_FP32, false, st);
+        RunBufs b = {wV, wS, const_cast<void*>(Tp), nullptr, F32 ? (void*)wcV : nullptr,
+                     F32 ? (void*)wcS : nullptr, traces};
+        return run_rank2_device(h, b, M, len, n_start, 1, prec, false, st);
     };
     // ---- forward sweep: checkpoints, traces, misfit
-    e = cudaMemcpyAsync(wV, V0, sizeof(float) * nv, cudaMemcpyDeviceToDevice, st);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(wS, S0, sizeof(float) * ns, cudaMemcpyDeviceToDevice, st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(wcV, 0, sizeof(float) * kvm, st);
+    e = cudaMemcpyAsync(wV, V0, sizeof(T) * nv, cudaMemcpyDeviceToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(wS, S0, sizeof(T) * ns, cudaMemcpyDeviceToDevice, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(wcV, 0, sizeof(T) * kvm, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(acc, 0, sizeof(double) * 2, st);
+    const int dt_code = F32 ? 1 : 0;  // element type codes of launch_rel_l2
     for (int k = 0; k < L.nseg && e == cudaSuccess && s == ROM_OK; ++k) {
         const int n_start = k * L.seg, len = nsteps - n_start < L.seg ? nsteps - n_start : L.seg;
-        e = cudaMemcpyAsync(ckpt + (size_t)k * 2 * kvm, work, sizeof(float) * 2 * kvm,
+        e = cudaMemcpyAsync(ckpt + (size_t)k * 2 * kvm, work, sizeof(T) * 2 * kvm,
                             cudaMemcpyDeviceToDevice, st);
         if (e != cudaSuccess) break;
         s = forward(n_start, len);
-        if (s == ROM_OK) e = launch_rel_l2(traces, 1, ys + (size_t)n_start * rec, 1, (size_t)len * rec, acc, st);
+        if (s == ROM_OK)
+            e = launch_rel_l2(traces, dt_code, ys + (size_t)n_start * rec, dt_code, (size_t)len * rec, acc, st);
     }
     // ---- reverse sweep, segment by segment (recomputing each one's traces)
     if (e == cudaSuccess && s == ROM_OK) {
-        e = cudaMemsetAsync(gV0, 0, sizeof(float) * nv, st);
-        if (e == cudaSuccess) e = cudaMemsetAsync(gS0, 0, sizeof(float) * ns, st);
+        e = cudaMemsetAsync(gV0, 0, sizeof(T) * nv, st);
+        if (e == cudaSuccess) e = cudaMemsetAsync(gS0, 0, sizeof(T) * ns, st);
         if (e == cudaSuccess) e = cudaMemsetAsync(acomp, 0, sizeof(float) * kvm, st);
-        if (e == cudaSuccess) e = cudaMemsetAsync(gtp, 0, sizeof(float) * 16 * (size_t)M, st);
+        if (e == cudaSuccess) e = cudaMemsetAsync(gtp, 0, sizeof(T) * 16 * (size_t)M, st);
     }
     for (int k = L.nseg - 1; k >= 0 && e == cudaSuccess && s == ROM_OK; --k) {
         const int n_start = k * L.seg, len = nsteps - n_start < L.seg ? nsteps - n_start : L.seg;
         if (k != L.nseg - 1) {  // the last segment's traces are still in place
-            e = cudaMemcpyAsync(work, ckpt + (size_t)k * 2 * kvm, sizeof(float) * 2 * kvm,
+            e = cudaMemcpyAsync(work, ckpt + (size_t)k * 2 * kvm, sizeof(T) * 2 * kvm,
                                 cudaMemcpyDeviceToDevice, st);
             if (e != cudaSuccess) break;
             s = forward(n_start, len);
             if (s != ROM_OK) break;
         }
-        AdjArgs aa = {};
-        aa.opA_rm = static_cast<const float*>(h->Asv_cm[1]);
-        aa.opB_rm = static_cast<const float*>(h->Avs_cm[1]);
-        aa.g_p = static_cast<const float*>(h->g_p[1]);
-        aa.C_rm = static_cast<const float*>(h->C_rm[1]);
-        aa.lamV = static_cast<float*>(gV0);
-        aa.lamS = static_cast<float*>(gS0);
-        aa.compV = acomp;
-        aa.compS = acomp + nv;
-        aa.Tper = static_cast<const float*>(T);
+        AdjArgsT<T> aa = {};
+        aa.opA_rm = static_cast<const T*>(h->Asv_cm[t]);
+        aa.opB_rm = static_cast<const T*>(h->Avs_cm[t]);
+        aa.g_p = static_cast<const T*>(h->g_p[t]);
+        aa.C_rm = static_cast<const T*>(h->C_rm[t]);
+        aa.lamV = static_cast<T*>(gV0);
+        aa.lamS = static_cast<T*>(gS0);
+        aa.compV = F32 ? acomp : nullptr;
+        aa.compS = F32 ? acomp + nv : nullptr;
+        aa.Tper = static_cast<const T*>(Tp);
         aa.traces = traces;
         aa.ystar = ys;
         aa.gTpart = gtp;
@@ -1873,15 +1857,48 @@ rom_status rom_adjoint(rom_t h, const void* V0, const void* S0, const void* T, i
         aa.M = M;
         e = launch_adjoint(aa, ap, st);
     }
-    if (e == cudaSuccess && s == ROM_OK) e = launch_sum_partials(gtp, ap.cs, M, static_cast<float*>(gT), st);
+    if (e == cudaSuccess && s == ROM_OK) e = launch_sum_partials(gtp, ap.cs, M, static_cast<T*>(gT), st);
     double hacc[2] = {0.0, 0.0};
     if (e == cudaSuccess && s == ROM_OK) e = cudaMemcpyAsync(hacc, acc, sizeof(hacc), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess && s == ROM_OK) e = cudaStreamSynchronize(st);
     if (own_ws) cudaFree(own_ws);
     if (s != ROM_OK) return s;
-    if (e != cudaSuccess) return fail(e, "rom_adjoint");
+    if (e != cudaSuccess) return cuda_fail(e, "rom_adjoint");
     if (loss) *loss = hacc[0];
     return ROM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t rom_adjoint_workspace_size(rom_t h, int M, int nsteps, int ckpt_every, int prec) {
+    if (!h || M < 1 || nsteps < 1 || ckpt_every < 0 || (prec != ROM_FP32 && prec != ROM_FP64)) return 0;
+    return adjoint_layout(h, M, nsteps, ckpt_every, prec == ROM_FP64 ? 8 : 4).total;
+}
+
+rom_status rom_adjoint(rom_t h, const void* V0, const void* S0, const void* T, int M, int nsteps,
+                       const void* ystar, int ckpt_every, void* gV0, void* gS0, void* gT,
+                       double* loss, void* workspace, size_t ws_bytes, int prec, void* stream) {
+    if (!h || !V0 || !S0 || !T || !ystar || !gV0 || !gS0 || !gT || M < 1 || nsteps < 1 ||
+        ckpt_every < 0 || h->R < 1)
+        return ROM_E_INVAL;
+    if (prec != ROM_FP32 && prec != ROM_FP64) return ROM_E_UNSUPPORTED;
+    if (h->xref_M != 0 && h->xref_M != M) return ROM_E_INVAL;  // reference state of another ensemble
+    const void* ptrs[] = {V0, S0, T, ystar, gV0, gS0, gT};
+    for (const void* p : ptrs)
+        if (!is_device_ptr(p)) return ROM_E_INVAL;
+    AdjPlan ap;
+    if (!plan_adjoint(h->Kp, M, h->R, &ap, prec == ROM_FP64)) {
+        snprintf(g_last_error, sizeof(g_last_error), "no adjoint plan for Kp=%d M=%d (prec %d)", h->Kp, M, prec);
+        return ROM_E_UNSUPPORTED;
+    }
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    return prec == ROM_FP64
+               ? adjoint_run<double>(h, V0, S0, T, M, nsteps, ystar, ckpt_every, gV0, gS0, gT, loss,
+                                     workspace, ws_bytes, ap, st)
+               : adjoint_run<float>(h, V0, S0, T, M, nsteps, ystar, ckpt_every, gV0, gS0, gT, loss,
+                                    workspace, ws_bytes, ap, st);
 }
 
 rom_status rom_rel_l2(const void* x, int x_dtype, const void* ref, int ref_dtype, size_t n,

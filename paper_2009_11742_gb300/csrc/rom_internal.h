@@ -179,19 +179,23 @@ bool plan_rank2_tc(int prec, int Kp, int M, int R, int Wforce, TcPlan* plan);
 cudaError_t launch_rank2_tc(const TcArgs& a, const TcPlan& plan, cudaStream_t st);
 
 // Reverse-time adjoint kernel (FP32, K <= 512).
-struct AdjArgs {
-    const float* opA_rm;  // Asv^T as Kp x Kp row-major (the column-major copy of Asv)
-    const float* opB_rm;  // Avs^T as Kp x Kp row-major
-    const float* g_p;     // Kp
-    const float* C_rm;    // R x Kp row-major
-    float* lamV;          // Kv x M adjoint of V (in: running value, out: after the range)
-    float* lamS;          // Ks x M
-    float* compV;         // Kahan carries of lamV / lamS
+// Arguments of the reverse sweep, element type T (float: the FP32 path with
+// Kahan-compensated adjoint state; double: the FP64 path, plain sums, the
+// carries unused and may be null).
+template <typename T>
+struct AdjArgsT {
+    const T* opA_rm;  // Asv^T as Kp x Kp row-major (the column-major copy of Asv)
+    const T* opB_rm;  // Avs^T as Kp x Kp row-major
+    const T* g_p;     // Kp
+    const T* C_rm;    // R x Kp row-major
+    T* lamV;          // Kv x M adjoint of V (in: running value, out: after the range)
+    T* lamS;          // Ks x M
+    float* compV;     // Kahan carries of lamV / lamS (FP32 path)
     float* compS;
-    const float* Tper;    // M periods
-    const float* traces;  // forward records: record k = C V^{rec_base + k}, [k][m][j]
-    const float* ystar;   // targets: record n = ystar^{n+1}, [n][m][j]
-    float* gTpart;        // cs x M per-CTA partial dL/dT (in/out)
+    const T* Tper;    // M periods
+    const T* traces;  // forward records: record k = C V^{rec_base + k}, [k][m][j]
+    const T* ystar;   // targets: record n = ystar^{n+1}, [n][m][j]
+    T* gTpart;        // cs x M per-CTA partial dL/dT (in/out)
     int* status;
     double dt;
     long long n0;
@@ -200,13 +204,17 @@ struct AdjArgs {
     int Kv, Ks, Kp, R, M, Wv, Wa;
     int wavelet;          // source signal of the periods (see Rank2Args)
 };
+using AdjArgs = AdjArgsT<float>;
 struct AdjPlan {
     int cs, KI, cb, Wv, Wa, nclusters;
     size_t smem;
+    bool f64;  // the FP64 instance (Kp <= 512)
 };
-bool plan_adjoint(int Kp, int M, int R, AdjPlan* p);
-cudaError_t launch_adjoint(const AdjArgs& a, const AdjPlan& p, cudaStream_t st);
+bool plan_adjoint(int Kp, int M, int R, AdjPlan* p, bool f64 = false);
+cudaError_t launch_adjoint(const AdjArgsT<float>& a, const AdjPlan& p, cudaStream_t st);
+cudaError_t launch_adjoint(const AdjArgsT<double>& a, const AdjPlan& p, cudaStream_t st);
 cudaError_t launch_sum_partials(const float* part, int cs, int M, float* out, cudaStream_t st);
+cudaError_t launch_sum_partials(const double* part, int cs, int M, double* out, cudaStream_t st);
 
 // Rank-1 ensemble (one realization per CTA, operators streamed every step).
 struct Rank1EnsArgs {

@@ -632,21 +632,26 @@ class Rom:
 
 
 def adjoint(h, V0, S0, T, ystar, nsteps, ckpt_every=0, stream=None):
-    """Loss and gradients of sum_n ||C V^n - ystar^n||^2 (FP32, device tensors).
+    """Loss and gradients of sum_n ||C V^n - ystar^n||^2 (device tensors).
     V0 (Kv, M) and S0 (Ks, M) column-major; ystar a contiguous (nsteps, M, R)
-    tensor (record n-1 = ystar^n).  Returns (loss, gV0, gS0, gT)."""
+    tensor (record n-1 = ystar^n).  float32 inputs run the FP32 path, float64
+    inputs the FP64 one (Kv, Ks <= 512).  Returns (loss, gV0, gS0, gT) in the
+    inputs' type."""
     torch = _torch()
     M = V0.shape[1]
-    _check_colmajor(V0, h.Kv, M, "V0", np.float32)
-    _check_colmajor(S0, h.Ks, M, "S0", np.float32)
-    _check_vec(T, M, "T", np.float32)
-    _check_vec(ystar, nsteps * M * h.R, "ystar", np.float32)
-    gV = Rom.new_state(h.Kv, M, "fp32", device=V0.device)
-    gS = Rom.new_state(h.Ks, M, "fp32", device=V0.device)
-    gT = torch.zeros(M, dtype=torch.float32, device=V0.device)
+    f64 = V0.dtype == torch.float64
+    dt = np.float64 if f64 else np.float32
+    _check_colmajor(V0, h.Kv, M, "V0", dt)
+    _check_colmajor(S0, h.Ks, M, "S0", dt)
+    _check_vec(T, M, "T", dt)
+    _check_vec(ystar, nsteps * M * h.R, "ystar", dt)
+    name = "fp64" if f64 else "fp32"
+    gV = Rom.new_state(h.Kv, M, name, device=V0.device)
+    gS = Rom.new_state(h.Ks, M, name, device=V0.device)
+    gT = torch.zeros(M, dtype=V0.dtype, device=V0.device)
     st, loss = rom_adjoint(h.h, _ptr(V0), _ptr(S0), _ptr(T), M, int(nsteps), _ptr(ystar),
-                           int(ckpt_every), _ptr(gV), _ptr(gS), _ptr(gT), None, 0, ROM_FP32,
-                           _stream_handle(stream))
+                           int(ckpt_every), _ptr(gV), _ptr(gS), _ptr(gT), None, 0,
+                           ROM_FP64 if f64 else ROM_FP32, _stream_handle(stream))
     _chk(st, "rom_adjoint")
     return loss, gV, gS, gT
 
@@ -669,7 +674,7 @@ def _adjoint_function():
         @staticmethod
         def backward(ctx, gout):
             gV, gS, gT = ctx.saved_tensors
-            s = gout.to(torch.float32)
+            s = gout.to(gV.dtype)
             return s * gV, s * gS, s * gT, None, None, None, None
 
     return RomAdjointFn

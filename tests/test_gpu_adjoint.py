@@ -208,3 +208,110 @@ def test_adjoint_workload4_full_size_sampled(rom):
     assert colmax_rel(gV[:, cols], gVo) <= 1e-4
     assert colmax_rel(gS[:, cols], gSo) <= 1e-4
     assert np.max(np.abs(gT[cols] - gTo) / np.abs(gTo)) <= 1e-4
+
+
+# ---------------------------------------------------------------- FP64 path
+
+def gpu_adjoint64(R, h, p, V0, S0, ystar, N, ckpt, T=None):
+    M = V0.shape[1]
+    V0t = R.Rom.new_state(p.Kv, M, "fp64", fill=V0)
+    S0t = R.Rom.new_state(p.Ks, M, "fp64", fill=S0)
+    Tt = torch.as_tensor(np.asarray(p.T if T is None else T, np.float64), device="cuda")
+    ys = torch.as_tensor(np.ascontiguousarray(np.transpose(ystar, (0, 2, 1))), dtype=torch.float64,
+                         device="cuda")
+    loss, gV, gS, gT = R.adjoint(h, V0t, S0t, Tt, ys, N, ckpt_every=ckpt)
+    torch.cuda.synchronize()
+    assert h.sync_status() == 0
+    assert gV.dtype == torch.float64 and gT.dtype == torch.float64
+    return loss, gV.cpu().numpy(), gS.cpu().numpy(), gT.cpu().numpy()
+
+
+@pytest.mark.parametrize("Kv,Ks,M,R,N,ckpt", [(64, 64, 7, 3, 60, 0), (200, 180, 20, 5, 100, 32),
+                                               # Kp = 320 and 512: the FP64 kernel reads the
+                                               # transposed operators from L2 every half-step
+                                               (320, 300, 9, 4, 50, 16), (512, 512, 9, 8, 40, 7)])
+def test_adjoint_fp64_vs_oracle(rom, Kv, Ks, M, R, N, ckpt):
+    """The FP64 reverse sweep against the FP64 oracle adjoint: the two differ
+    only in summation order, so they agree to 1e-10 relative."""
+    p, V0, S0, ystar = case(Kv, Ks, M, R, N, seed=Kv + M + 1)
+    V0 = V0.astype(np.float64)
+    S0 = S0.astype(np.float64)
+    ys64 = ystar.astype(np.float64)
+    h = rom.Rom.from_problem(p)
+    T = p.T.astype(np.float64)
+    loss, gV, gS, gT = gpu_adjoint64(rom, h, p, V0, S0, ys64, N, ckpt, T=T)
+    Lo, gVo, gSo, gTo = oracle.adjoint(p.Avs, p.Asv, p.g, p.C, p.dt, V0, S0, T, N, ys64)
+    assert abs(loss - Lo) <= 1e-10 * abs(Lo)
+    assert colmax_rel(gV, gVo) <= 1e-10 and colmax_rel(gS, gSo) <= 1e-10
+    assert np.max(np.abs(gT - gTo) / np.abs(gTo)) <= 1e-10
+
+
+def test_adjoint_fp64_vs_finite_differences(rom):
+    """dL/dT_m and the V0, S0 gradients along random directions of the FP64
+    path against central differences of the FP64 oracle's misfit, at 1e-6
+    relative.  The state differences are exact up to rounding (the misfit is
+    quadratic in V0, S0); the period differences' own error is O(h^2)."""
+    Kv, Ks, M, R, N = 256, 240, 4, 6, 200
+    p = inputs.make_problem(Kv, Ks, M, R, seed=91)
+    T = p.T.astype(np.float64)
+    _, _, ys = oracle.forward(p.Avs, p.Asv, p.g, p.C, p.dt, np.zeros((Kv, M)), np.zeros((Ks, M)), N,
+                              T=1.05 * T, r=1)
+    V0 = inputs.random_state(Kv, M, seed=92, scale=0.05).astype(np.float64)
+    S0 = inputs.random_state(Ks, M, seed=93, scale=0.05).astype(np.float64)
+    h = rom.Rom.from_problem(p)
+    loss, gV, gS, gT = gpu_adjoint64(rom, h, p, V0, S0, ys, N, 32, T=T)
+
+    def misfit(V0_, S0_, T_):
+        _, _, tr = oracle.forward(p.Avs, p.Asv, p.g, p.C, p.dt, V0_, S0_, N, T=T_, r=1)
+        return float(np.sum((tr - ys) ** 2))
+
+    assert abs(loss - misfit(V0, S0, T)) <= 1e-12 * loss
+    step = 1e-3
+    for m in range(M):
+        Tp, Tm = T.copy(), T.copy()
+        Tp[m] += step
+        Tm[m] -= step
+        fd = (misfit(V0, S0, Tp) - misfit(V0, S0, Tm)) / (2 * step)
+        assert abs(gT[m] - fd) <= 1e-6 * abs(fd), (m, gT[m], fd)
+    rng = np.random.default_rng(94)
+    for _ in range(2):
+        DV = rng.standard_normal((Kv, M))
+        DS = rng.standard_normal((Ks, M))
+        fdV = (misfit(V0 + step * DV, S0, T) - misfit(V0 - step * DV, S0, T)) / (2 * step)
+        fdS = (misfit(V0, S0 + step * DS, T) - misfit(V0, S0 - step * DS, T)) / (2 * step)
+        assert abs(float(np.sum(gV * DV)) - fdV) <= 1e-6 * abs(fdV), (np.sum(gV * DV), fdV)
+        assert abs(float(np.sum(gS * DS)) - fdS) <= 1e-6 * abs(fdS), (np.sum(gS * DS), fdS)
+
+
+def test_adjoint_fp64_checkpoints_and_autograd(rom):
+    """FP64: the gradients do not depend on the checkpoint interval (the
+    recomputed segments repeat the forward sweep bit for bit), and the
+    autograd function returns them for float64 leaves."""
+    p, V0, S0, ystar = case(128, 128, 6, 4, 70, seed=17)
+    V0 = V0.astype(np.float64)
+    S0 = S0.astype(np.float64)
+    ys64 = ystar.astype(np.float64)
+    h = rom.Rom.from_problem(p)
+    T = p.T.astype(np.float64)
+    a = gpu_adjoint64(rom, h, p, V0, S0, ys64, 70, 0, T=T)
+    b = gpu_adjoint64(rom, h, p, V0, S0, ys64, 70, 15, T=T)
+    assert abs(a[0] - b[0]) <= 1e-13 * abs(a[0])
+    for x, y in zip(a[1:], b[1:]):
+        np.testing.assert_array_equal(x, y)
+    V0t = rom.Rom.new_state(128, 6, "fp64", fill=V0).requires_grad_(True)
+    S0t = rom.Rom.new_state(128, 6, "fp64", fill=S0).requires_grad_(True)
+    Tt = torch.as_tensor(T, device="cuda").requires_grad_(True)
+    ys = torch.as_tensor(np.ascontiguousarray(np.transpose(ys64, (0, 2, 1))), device="cuda")
+    L = rom.rom_loss(h, V0t, S0t, Tt, ys, 70)
+    L.backward()
+    np.testing.assert_array_equal(V0t.grad.cpu().numpy(), a[1])
+    np.testing.assert_array_equal(S0t.grad.cpu().numpy(), a[2])
+    np.testing.assert_array_equal(Tt.grad.cpu().numpy(), a[3])
+
+
+def test_adjoint_fp64_refuses_above_512(rom):
+    p, V0, S0, ystar = case(576, 576, 2, 2, 5, seed=3)
+    h = rom.Rom.from_problem(p)
+    with pytest.raises(rom.RomError):
+        gpu_adjoint64(rom, h, p, V0.astype(np.float64), S0.astype(np.float64),
+                      ystar.astype(np.float64), 5, 0, T=p.T.astype(np.float64))
