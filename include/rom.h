@@ -397,6 +397,19 @@ rom_status rom_autotune_batched(const rom_job* jobs, int njobs, int prec, int pr
                                 double* best_us, void* stream);
 
 /*
+ * rom_set_batched_form -- pin how rom_run_batched runs this FP32 job list
+ * (the same handles and widths; buffers and step counts may change), as
+ * rom_autotune_batched would: cluster_size 2, 4 or 8 with width_cap a
+ * multiple of 8 in [8, 256] selects the work-list launch with clusters of
+ * that many CTAs and at most width_cap columns per item; cluster_size 0
+ * selects one launch per job (width_cap ignored).  Without a pinned or
+ * tuned form, FP32 lists run the work-list launch with clusters of 2 and a
+ * cap of 32.  prec must be ROM_FP32.  Errors: ROM_E_INVAL (null or empty
+ * list, a null handle, M < 1, another precision, a form outside the above).
+ */
+rom_status rom_set_batched_form(const rom_job* jobs, int njobs, int prec, int cluster_size, int width_cap);
+
+/*
  * rom_adjoint -- gradients of the receiver-trace misfit
  *     L = sum_{n=1..N} sum_m || C V_m^n - ystar_m^n ||^2
  * with respect to the initial state (V0, S0) and the Ricker periods T, by a

@@ -1471,6 +1471,21 @@ rom_status rom_run_batched(const rom_job* jobs, int njobs, int nsteps, int r, in
     return run_batched_impl(jobs, njobs, nsteps, r, prec, stream, scale, kthr, tcw, wl);
 }
 
+rom_status rom_set_batched_form(const rom_job* jobs, int njobs, int prec, int cluster_size, int width_cap) {
+    if (!jobs || njobs < 1 || prec != ROM_FP32) return ROM_E_INVAL;
+    for (int i = 0; i < njobs; ++i)
+        if (!jobs[i].h || jobs[i].M < 1) return ROM_E_INVAL;
+    int wl = 0;
+    if (cluster_size != 0) {
+        int cs = 0, wcap = 0;
+        wl = cluster_size * 1000 + width_cap;
+        if (width_cap < 0 || width_cap >= 1000 || !wl_decode(wl, &cs, &wcap)) return ROM_E_INVAL;
+    }
+    std::lock_guard<std::mutex> lk(g_batch_mu);
+    g_batch_wl[batch_tune_key(jobs, njobs, prec)] = wl;
+    return ROM_OK;
+}
+
 rom_status rom_autotune_batched(const rom_job* jobs, int njobs, int prec, int probe_steps,
                                 double* best_us, void* stream) {
     if (!jobs || njobs < 1 || probe_steps < 1 || !batch_prec(prec)) return ROM_E_INVAL;

@@ -35,7 +35,7 @@ PRECISIONS = {"fp64": ROM_FP64, "fp32": ROM_FP32, "tf32x3": ROM_TF32X3,
               "bf16x3": ROM_BF16X3, "bf16": ROM_BF16, "bf16s": ROM_BF16S, "auto": ROM_AUTO}
 
 EXPORTED = ["rom_create", "rom_destroy", "rom_spectral_radius", "rom_sync_status",
-            "rom_get_dims", "rom_set_kernel", "rom_get_plan", "rom_set_tc_columns", "rom_set_wavelet", "rom_set_reference", "rom_autotune", "rom_autotune_batched", "rom_set_wait_limit",
+            "rom_get_dims", "rom_set_kernel", "rom_get_plan", "rom_set_tc_columns", "rom_set_wavelet", "rom_set_reference", "rom_autotune", "rom_autotune_batched", "rom_set_batched_form", "rom_set_wait_limit",
             "rom_debug_inject_stall", "rom_run_rank2", "rom_run_rank2_ex", "rom_run_rank1",
             "rom_run_rank1_ensemble", "rom_run_batched", "rom_run_rank3", "rom_adjoint",
             "rom_adjoint_workspace_size", "rom_rel_l2", "rom_spectral_radius_noalloc",
@@ -74,6 +74,7 @@ def _signatures(lib):
         "rom_set_reference": (_i, [_vp, _vp, _vp, _i, _i]),
         "rom_autotune": (_i, [_vp, _i, _i, _i, ctypes.POINTER(_d), _vp]),
         "rom_autotune_batched": (_i, [_vp, _i, _i, _i, ctypes.POINTER(_d), _vp]),
+        "rom_set_batched_form": (_i, [_vp, _i, _i, _i, _i]),
         "rom_debug_inject_stall": (_i, [_vp, _i]),
         "rom_get_plan": (_i, [_vp, _i, _i, ctypes.POINTER(_i), ctypes.POINTER(_i),
                               ctypes.POINTER(_i), ctypes.POINTER(_i)]),
@@ -315,6 +316,21 @@ def rom_autotune_batched(jobs, njobs, prec, probe_steps, stream=None):
     us = _d(0.0)
     st = load().rom_autotune_batched(jobs, int(njobs), int(prec), int(probe_steps), ctypes.byref(us), stream)
     return st, us.value
+
+
+def rom_set_batched_form(jobs, njobs, prec, cluster_size, width_cap):
+    return load().rom_set_batched_form(jobs, int(njobs), int(prec), int(cluster_size), int(width_cap))
+
+
+def set_batched_form(items, cluster_size, width_cap=32, prec="fp32"):
+    """Pin how run_batched runs `items` (as for run_batched; FP32): the
+    work-list launch with clusters of 2, 4 or 8 CTAs and at most width_cap
+    columns per item, or cluster_size 0 for one launch per job."""
+    p = PRECISIONS.get(prec, prec)
+    arr = (rom_job * len(items))()
+    for i, (h, V, S, T, tr) in enumerate(items):
+        arr[i] = rom_job(h.h, _ptr(V), _ptr(S), _ptr(T), V.shape[1], None)
+    _chk(rom_set_batched_form(arr, len(items), p, cluster_size, width_cap), "rom_set_batched_form")
 
 
 def autotune_batched(items, prec="fp32", probe_steps=200, stream=None):

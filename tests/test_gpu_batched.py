@@ -80,6 +80,36 @@ def test_batched_vs_oracle_and_individual(rom):
         assert colmax_rel(S.cpu().numpy(), S1.cpu().numpy()) <= 2e-5
 
 
+@pytest.mark.parametrize("form", [None, (4, 16), (8, 64), (2, 8), (0, 0)])
+def test_batched_worklist_edge_cases(rom, form):
+    """The work-list launch on the cases its layout branches on, in the
+    default form (clusters of 2, width cap 32) and pinned ones:
+    - a one-column job at Kp = 1024, and ragged K (1000 -> Kp = 1024);
+    - receiver rows too many to stage in shared memory (K = 640, R = 48:
+      24 rows of C per CTA of a pair, 61 KB, read from L2);
+    - Kp = 576 (18 row tiles: 5, 5, 4, 4 over a cluster of 4, and 3 or 2
+      over one of 8), Kp = 320 (10 tiles: 3, 3, 2, 2 over 4);
+    - Kp = 64 (2 tiles: over a cluster of 4 or 8 most CTAs own none);
+    - (0, 0): one launch per job.
+    Every column of state and traces is held to the FP64 oracle."""
+    sizes = [(1024, 1, 3), (1000, 9, 40), (640, 20, 48), (576, 13, 5), (320, 30, 6), (64, 3, 0)]
+    N, r = 40, 4
+    jobs, probs = make_jobs(rom, sizes, with_traces=N // r, seed0=400)
+    if form is not None:
+        rom.set_batched_form(jobs, *form)
+    rom.run_batched(jobs, N, r=r, prec="fp32")
+    torch.cuda.synchronize()
+    for (h, V, S, T, tr), p in zip(jobs, probs):
+        assert h.sync_status() == 0
+        Z = np.zeros((p.Kv, p.M))
+        Vo, So, tro = oracle.forward(p.Avs, p.Asv, p.g, p.C if p.R else None, p.dt, Z, Z, N,
+                                     T=p.T, r=r if p.R else 0)
+        assert colmax_rel(V.cpu().numpy(), Vo) <= 1e-4 and colmax_rel(S.cpu().numpy(), So) <= 1e-4
+        if tr is not None:
+            trg = tr.transpose(1, 2).cpu().numpy().reshape(-1, p.M)
+            assert colmax_rel(trg, np.asarray(tro).reshape(-1, p.M)) <= 1e-4
+
+
 def test_batched_graph_replay(rom):
     """The second call replays the cached graph: the state advances by
     another nsteps (forcing restarts at t = 0 for every call)."""
@@ -101,6 +131,11 @@ def test_batched_rejects_bad_jobs(rom):
     dup = [jobs[0], jobs[0]]
     with pytest.raises(rom.RomError):
         rom.run_batched(dup, 10, prec="fp32")
+    for bad in [(3, 32), (2, 12), (2, 0), (4, 264), (16, 32), (-2, 32)]:
+        with pytest.raises(rom.RomError):
+            rom.set_batched_form(jobs, *bad)
+    with pytest.raises(rom.RomError):
+        rom.set_batched_form(jobs, 2, 32, prec="fp64")
 
 
 def test_batched_workload3_full_size_sampled(rom):
