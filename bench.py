@@ -187,15 +187,23 @@ def run_reference(args):
     return 0
 
 
-def cpu_baseline_sample(p, target_s=12.0):
+def cpu_baseline_sample(p, target_s=16.0):
     """Oracle throughput on a bounded sample (all host cores)."""
     import oracle
     cores = oracle.max_threads()
     ncol = min(WORKLOAD["M"], 2 * cores)
     cols = np.linspace(0, WORKLOAD["M"] - 1, ncol).astype(int)
+    oracle.problem_forward(p, nsteps=WORKLOAD["r"], r=WORKLOAD["r"], columns=cols)  # threads up
     t0 = time.perf_counter()
-    oracle.problem_forward(p, nsteps=50, r=WORKLOAD["r"], columns=cols)
-    per_step = (time.perf_counter() - t0) / 50
+    oracle.problem_forward(p, nsteps=100, r=WORKLOAD["r"], columns=cols)
+    per_step = (time.perf_counter() - t0) / 100
+    full = per_step * WORKLOAD["nsteps"]
+    if full < target_s and ncol < WORKLOAD["M"]:
+        # every step fits: widen the column sample (whole multiples of the cores)
+        ncol0 = ncol
+        ncol = min(WORKLOAD["M"], max(ncol0, int(ncol0 * target_s / max(full, 1e-9)) // cores * cores))
+        cols = np.linspace(0, WORKLOAD["M"] - 1, ncol).astype(int)
+        per_step *= ncol / ncol0
     nst = int(max(100, min(WORKLOAD["nsteps"], target_s / max(per_step, 1e-9))))
     nst -= nst % WORKLOAD["r"]
     t0 = time.perf_counter()
@@ -203,6 +211,7 @@ def cpu_baseline_sample(p, target_s=12.0):
     dt = time.perf_counter() - t0
     # the same oracle on one thread (a few columns, a few seconds)
     c1 = cols[:2]
+    oracle.problem_forward(p, nsteps=WORKLOAD["r"], r=WORKLOAD["r"], columns=c1, threads=1)
     t0 = time.perf_counter()
     oracle.problem_forward(p, nsteps=100, r=WORKLOAD["r"], columns=c1, threads=1)
     per1 = (time.perf_counter() - t0) / 100
