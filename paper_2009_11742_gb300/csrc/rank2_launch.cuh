@@ -42,9 +42,12 @@ struct ClusterLaunch {
     cudaError_t launch(const void* fn, void** args) { return cudaLaunchKernelExC(&cfg, fn, args); }
 };
 
+// FP32 with operators streamed from L2 (KI > 8) in 8-column groups runs the
+// 4-row, 32-lane half-step (GEN).
 template <typename T, int KI, int CB, bool RES>
 struct Rank2Kernel {
-    static void* fn() { return (void*)&rank2_simt_kernel<T, KI, CB, RES>; }
+    static constexpr bool GEN = sizeof(T) == 4 && CB == 8 && KI > 8 && !RES;
+    static void* fn() { return (void*)&rank2_simt_kernel<T, KI, CB, RES, GEN>; }
 };
 
 // Kernel entry for (KI, CB) with the residency rule of the element type:
@@ -52,7 +55,8 @@ struct Rank2Kernel {
 // KI = 4 (K <= 256) and re-reads its 32-row operator slab from L2 each
 // half-step beyond that.
 // FP32 beyond KI = 8 (K > 512) streams two 32-row operator tiles per CTA per
-// half-step (one-block kernel with nrt = 2); FP64 stops at K = 512.
+// half-step (one-block kernel with nrt = 2; in 8-column groups with the 4-row
+// half-step); FP64 stops at K = 512.
 template <typename T, int CB>
 static void* rank2_kernel_for(int KI, bool* resident) {
     constexpr bool f64 = sizeof(T) == 8;
@@ -107,16 +111,24 @@ static cudaError_t prepare_kernel(void* fn, size_t smem) {
     return cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
 }
 
-// cluster_budget > 0 caps the clusters the plan assumes it may keep busy (the
-// batched scheduler hands each ROM its share of the GPU).
+// The plan for clusters of cs CTAs owning at most nrt 32-row tiles each
+// (cs = 0: the kernel's own, Kp / 32 CTAs of one tile up to Kp = 512 and
+// Kp / 64 of two above).  cluster_budget > 0 caps the clusters the plan
+// assumes it may keep busy (the batched scheduler hands each ROM its share
+// of the GPU).
 template <typename T>
-static bool plan_rank2(int Kp, int M, int R, bool rank1, Rank2Plan* p, int cluster_budget = 0) {
+static bool plan_rank2_cs(int Kp, int M, int R, bool rank1, Rank2Plan* p, int cluster_budget, int cs) {
     const int kmax = sizeof(T) == 4 ? 1024 : 512;
     if (Kp <= 0 || Kp % 64 != 0 || Kp > kmax || M <= 0) return false;
     constexpr int CBW = 8;  // wide column group (FP32)
     p->KI = Kp / 64;
-    p->nrt = Kp > 512 ? 2 : 1;
-    p->cs = Kp / (32 * p->nrt);
+    if (cs == 0) {
+        p->nrt = Kp > 512 ? 2 : 1;
+        p->cs = Kp / (32 * p->nrt);
+    } else {
+        p->cs = cs;
+        p->nrt = (Kp / 32 + cs - 1) / cs;
+    }
     // FP64 runs one-column groups: it is bound by the SMs' few FP64 units,
     // not by the shuffles and loads a wider group saves, and a narrow group
     // lets a small ensemble spread one column per cluster.
@@ -156,6 +168,37 @@ static bool plan_rank2(int Kp, int M, int R, bool rank1, Rank2Plan* p, int clust
     p->nclusters = (M + wv - 1) / wv;
     p->smem = rank2_smem_layout<T>(p->Wa, Kp, rpc_smem, p->nrt).total;
     p->variant = 1;
+    return true;
+}
+
+// Wave count x step time of a plan (µs per step): a wave of clusters takes
+// about 3.5 µs plus 0.71 µs per 32-row tile and column at Kp = 1024, scaled
+// by Kp (the streamed-operator kernel measured on GB300).
+static double rank2_plan_model_us(const Rank2Plan& p, int Kp) {
+    const int act = p.max_active_clusters > 0 ? p.max_active_clusters : 1;
+    const int waves = (p.nclusters + act - 1) / act;
+    return waves * (3.5 + 0.71 * p.nrt * p.Wa * (Kp / 1024.0));
+}
+
+// FP32 above Kp = 512 in 8-column groups (the 4-row half-step, which deals
+// a job's row tiles to any cluster size) also tries clusters of 4 and 2:
+// at most 7 clusters of Kp / 64 > 8 CTAs are co-resident, against 36 of 4
+// and 76 of 2, and the shared memory caps the columns per cluster whatever
+// its size.  The plan with the fewest modelled µs per step wins.
+template <typename T>
+static bool plan_rank2(int Kp, int M, int R, bool rank1, Rank2Plan* p, int cluster_budget = 0) {
+    if (!plan_rank2_cs<T>(Kp, M, R, rank1, p, cluster_budget, 0)) return false;
+    if (sizeof(T) != 4 || rank1 || cluster_budget > 0 || Kp <= 512 || p->cb != 8) return true;
+    double best = rank2_plan_model_us(*p, Kp);
+    for (int cs : {4, 2}) {
+        Rank2Plan q{};
+        if (!plan_rank2_cs<T>(Kp, M, R, rank1, &q, 0, cs)) continue;
+        const double t = rank2_plan_model_us(q, Kp);
+        if (t < best) {
+            best = t;
+            *p = q;
+        }
+    }
     return true;
 }
 

@@ -385,7 +385,8 @@ __device__ __forceinline__ void simt_body(cg::cluster_group& cluster, const Rank
 
     T opA[2][4 * KI];
     T opB[2][4 * KI];
-    float opQ[GEN ? 4 : 1][GEN ? 2 * KI : 1];  // GEN: 4 rows, k groups of 128 (KI / 2 of them)
+    constexpr int KQ = (KI + 1) / 2;  // GEN: k groups of 128 covering 64 KI
+    float opQ[GEN ? 4 : 1][GEN ? 4 * KQ : 1];  // GEN: 4 rows of them
     const T* __restrict__ Avs = static_cast<const T*>(gop ? gop->Avs_rm : a.Avs_rm);
     const T* __restrict__ Asv = static_cast<const T*>(gop ? gop->Asv_rm : a.Asv_rm);
     if (RESIDENT && nrt_own > 0) {
@@ -401,8 +402,8 @@ __device__ __forceinline__ void simt_body(cg::cluster_group& cluster, const Rank
         for (int rt = 0; rt < nrt_own; ++rt) {
             const int rowt = row0 + rt * kRowsPerCta;
             if constexpr (GEN) {
-                wl_load_op<KI / 2>(opQ, Avs, Kp, rowt + 4 * warp, lane);
-                wl_half_step<KI / 2, true>(opQ, Sf, Vf, cV + rt * Wa * kRowsPerCta,
+                wl_load_op<KQ>(opQ, Avs, Kp, rowt + 4 * warp, lane);
+                wl_half_step<KQ, true>(opQ, Sf, Vf, cV + rt * Wa * kRowsPerCta,
                                              gown + rt * kRowsPerCta, fcol, dt, Wa, Kp, rowt, warp, lane);
             } else {
                 if (!RESIDENT) load_op_rows<T, KI>(opA, Avs, Kp, rowt + 2 * rp, j);
@@ -423,8 +424,8 @@ __device__ __forceinline__ void simt_body(cg::cluster_group& cluster, const Rank
         for (int rt = 0; rt < nrt_own; ++rt) {
             const int rowt = row0 + rt * kRowsPerCta;
             if constexpr (GEN) {
-                wl_load_op<KI / 2>(opQ, Asv, Kp, rowt + 4 * warp, lane);
-                wl_half_step<KI / 2, false>(opQ, Vf, Sf, cS + rt * Wa * kRowsPerCta, gown, fcol, dt, Wa,
+                wl_load_op<KQ>(opQ, Asv, Kp, rowt + 4 * warp, lane);
+                wl_half_step<KQ, false>(opQ, Vf, Sf, cS + rt * Wa * kRowsPerCta, gown, fcol, dt, Wa,
                                               Kp, rowt, warp, lane);
             } else {
                 if (!RESIDENT) load_op_rows<T, KI>(opB, Asv, Kp, rowt + 2 * rp, j);
@@ -497,8 +498,11 @@ __device__ __forceinline__ void simt_body(cg::cluster_group& cluster, const Rank
     if (bad && tid == 0 && a.status) atomicCAS(a.status, 0, (int)6 /* ROM_E_NONFINITE */);
 }
 
-template <typename T, int KI, int CB, bool RESIDENT>
+// GEN: the 4-row half-step of the work-list kernel (FP32 with operators
+// streamed from L2 and 8-column groups only).
+template <typename T, int KI, int CB, bool RESIDENT, bool GEN = false>
 __global__ void __launch_bounds__(kThreads, 1) rank2_simt_kernel(const Rank2Args a) {
+    static_assert(!GEN || (sizeof(T) == 4 && CB == 8 && !RESIDENT), "GEN: FP32, 8-column groups, streamed");
     cg::cluster_group cluster = cg::this_cluster();
     const int cs = (int)cluster.num_blocks();
     // rank-3 grouped launch: operator `job` of the table, column block `blk` of it
@@ -507,7 +511,7 @@ __global__ void __launch_bounds__(kThreads, 1) rank2_simt_kernel(const Rank2Args
     const GroupOp* gop = a.group ? a.group + job : nullptr;
     const int col0 = blk * a.Wv;                 // first column of this block (within the job)
     const int ncol = min(a.Wv, a.M - col0);      // valid columns
-    simt_body<T, KI, CB, RESIDENT>(cluster, a, gop, a.col_base + job * a.M + col0, ncol);
+    simt_body<T, KI, CB, RESIDENT, GEN>(cluster, a, gop, a.col_base + job * a.M + col0, ncol);
 }
 
 // Work-list launch of the batched scheduler (FP32): one persistent launch
