@@ -322,17 +322,20 @@ rom_status rom_run_rank1_ensemble(rom_t h, void* V, void* S, const void* T, int 
  * model (any Kv, Ks <= 1024) for its M columns exactly as rom_run_rank2 would
  * with n0 = 0, and all jobs run in ONE launch of a CUDA graph on `stream`.
  * With prec = ROM_FP32 (and no job carrying a reduced reference state) the
- * graph holds one persistent launch per operator size class (jobs with the
- * same padded size Kp): its clusters take (job, column block) items from a
- * device work list, in the order a counter hands them out, until none are
- * left; each class's block width and cluster count come from a step-time
- * model, chosen so that the predicted finishing time of the slowest class is
- * as small as the SMs allow.  Each column's arithmetic is the same as in
- * rom_run_rank2 (bitwise equal results).  Otherwise, and when
- * rom_autotune_batched measured it faster, the scheduler gives every job a
- * share of the GPU proportional to its work per step, 4 K^2 M (the rank-2
- * GEMM cost of Sec. 2.5), which sets its columns per cluster block, and
- * issues the longest jobs first, one launch per job.  The graph is built
+ * graph can hold ONE persistent launch for all jobs: co-resident clusters of
+ * 2 CTAs (by default) take (job, column block) items from a device work
+ * list, longest first, in the order a counter hands them out, until none
+ * are left; a job's rows are dealt out to the CTAs of whichever cluster
+ * takes one of its items, and its operators are read from L2.  The
+ * summation order differs from rom_run_rank2's (the results agree to FP32
+ * rounding, column by column).  The alternative is one launch per job:
+ * every job gets a share of the GPU proportional to its work per step,
+ * 4 K^2 M (the rank-2 GEMM cost of Sec. 2.5), which sets its columns per
+ * cluster block, and the longest jobs are issued first; each column's
+ * arithmetic is then rom_run_rank2's (bitwise equal results).  FP32 lists
+ * take the form pinned with rom_set_batched_form or measured by
+ * rom_autotune_batched, else the one the step-time models predict faster
+ * (see rom_set_batched_form); other precisions run one launch per job.  The graph is built
  * (captured and instantiated) on the first call for a given job list and
  * replayed afterwards.  Requirements: device buffers only, one job per
  * handle, traces (per job, optional) need r > 0 and receiver rows.
@@ -403,8 +406,10 @@ rom_status rom_autotune_batched(const rom_job* jobs, int njobs, int prec, int pr
  * multiple of 8 in [8, 256] selects the work-list launch with clusters of
  * that many CTAs and at most width_cap columns per item; cluster_size 0
  * selects one launch per job (width_cap ignored).  Without a pinned or
- * tuned form, FP32 lists run the work-list launch with clusters of 2 and a
- * cap of 32.  prec must be ROM_FP32.  Errors: ROM_E_INVAL (null or empty
+ * tuned form, an FP32 list runs the form that the library's step-time
+ * models predict faster for it: the work-list launch with clusters of 2
+ * and a cap of 32, or one launch per job (chosen at the list's first call
+ * and kept).  prec must be ROM_FP32.  Errors: ROM_E_INVAL (null or empty
  * list, a null handle, M < 1, another precision, a form outside the above).
  */
 rom_status rom_set_batched_form(const rom_job* jobs, int njobs, int prec, int cluster_size, int width_cap);

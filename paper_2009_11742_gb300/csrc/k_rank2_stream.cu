@@ -62,7 +62,7 @@ cudaError_t launch_rank2_stream_f32(const Rank2Args& a_in, int csz, int cols_per
 // from L2 at about 71 GB/s per SM and spends about 3 us per step on its two
 // cluster barriers, the row exchange and the epilogues (measured: 10.0 us
 // with clusters of 4, 17.1 us with clusters of 2).
-static double model_main_us(int Kp, int W) { return 2.24 + 0.466 * W * (Kp / 512.0); }
+static double model_main_us(int Kp, int W) { return model_split_us(Kp, W); }
 static double model_comp_us(int Kp, int csz) {
     return 2.0 * (Kp / (double)csz) * Kp * 4.0 / 71e3 + 3.0;
 }

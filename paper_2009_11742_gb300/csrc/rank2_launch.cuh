@@ -171,13 +171,11 @@ static bool plan_rank2_cs(int Kp, int M, int R, bool rank1, Rank2Plan* p, int cl
     return true;
 }
 
-// Wave count x step time of a plan (µs per step): a wave of clusters takes
-// about 3.5 µs plus 0.71 µs per 32-row tile and column at Kp = 1024, scaled
-// by Kp (the streamed-operator kernel measured on GB300).
-static double rank2_plan_model_us(const Rank2Plan& p, int Kp) {
+// Wave count x step time of a plan with streamed operators (µs per step).
+inline double rank2_plan_model_us(const Rank2Plan& p, int Kp) {
     const int act = p.max_active_clusters > 0 ? p.max_active_clusters : 1;
     const int waves = (p.nclusters + act - 1) / act;
-    return waves * (3.5 + 0.71 * p.nrt * p.Wa * (Kp / 1024.0));
+    return waves * model_streamed_us(Kp, p.nrt, p.Wa);
 }
 
 // FP32 above Kp = 512 in 8-column groups (the 4-row half-step, which deals

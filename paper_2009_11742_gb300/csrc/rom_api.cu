@@ -833,6 +833,9 @@ rom_status rom_autotune(rom_t h, int prec, int M, int probe_steps, double* best_
             if (plan_rank2_split_f32(h->Kp, M, h->R, &p, b)) { p.variant = 2; simt.push_back(p); }
             if (plan_rank2_simt_f32(h->Kp, M, h->R, false, &p, b)) { p.variant = 1; simt.push_back(p); }
         }
+        // above Kp = 512 the planner's own choice (clusters of Kp/64, 4 or 2
+        // CTAs; the budgeted plans above keep Kp/64)
+        if (h->Kp > 512 && nact > 0 && p0.variant == 1) simt.push_back(p0);
         // the saturated split kernel with 4, 8 or 12 fewer columns per block,
         // the freed columns on the streaming companion (clusters of 2 or 4)
         Rank2Plan ps;
@@ -1166,6 +1169,87 @@ static bool wl_decode(int wl, int* cs, int* wcap) {
     return (*cs == 2 || *cs == 4 || *cs == 8) && *wcap >= 8 && *wcap % 8 == 0 && *wcap <= 256;
 }
 
+// A job's layout in the work-list form with clusters of cs CTAs: tiles per
+// CTA, whether its receiver rows are read from global memory, the widest
+// multiple of 8 (<= wcap) that fits `budget` bytes of shared memory narrowed
+// to spread M evenly over that many blocks, and that width's shared memory.
+struct WlJob {
+    int nrt = 0, cglob = 0, W = 0, nblocks = 0;
+    size_t smem = 0;
+};
+static bool wl_job_layout(const rom_s* h, int M, int cs, int wcap, size_t budget, WlJob* L) {
+    const int Kp = h->Kp;
+    L->nrt = (Kp / 32 + cs - 1) / cs;
+    const int rpc = (h->R + cs - 1) / cs;
+    L->cglob = (size_t)rpc * Kp * sizeof(float) > 16384 ? 1 : 0;
+    const int rst = L->cglob ? 0 : rpc;
+    int wmax = 0;
+    for (int w = 8; w <= wcap; w += 8) {
+        if (worklist_smem(w, Kp, rst, L->nrt) > budget) break;
+        wmax = w;
+    }
+    if (wmax == 0) return false;
+    L->nblocks = (M + wmax - 1) / wmax;
+    L->W = (((M + L->nblocks - 1) / L->nblocks) + 7) / 8 * 8;
+    L->smem = worklist_smem(L->W, Kp, rst, L->nrt);
+    return true;
+}
+
+// The form an FP32 job list runs in when nothing pinned or tuned one: the
+// work-list launch (kWlDefault) or one launch per job (0), whichever the
+// step-time models predict faster.  Work list: its items run longest first
+// on the co-resident clusters, so a step lasts about max(longest item,
+// sum of item times / clusters).  Per job: each job on its own plan, the
+// jobs side by side, so about max(slowest job, sum of job time x SMs / SMs
+// of the GPU).  Few items (small M, say 16 operators of 16 columns) leave
+// the work list's clusters idle while the split kernel keeps its operators
+// in registers; many uneven jobs favour the list.
+static int batched_default_form(const rom_job* jobs, int njobs, int dev, int nsm) {
+    int optin = 0;
+    if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) {
+        cudaGetLastError();
+        return kWlDefault;
+    }
+    const size_t budget = (size_t)optin - 1024;
+    int cs = 0, wcap = 0;
+    wl_decode(kWlDefault, &cs, &wcap);
+    double sum = 0.0, cmax = 0.0;
+    long nitems = 0;
+    size_t smem = 0;
+    for (int i = 0; i < njobs; ++i) {
+        WlJob L;
+        if (!wl_job_layout(jobs[i].h, jobs[i].M, cs, wcap, budget, &L)) return 0;
+        const double c = model_streamed_us(jobs[i].h->Kp, L.nrt, L.W);
+        sum += c * L.nblocks;
+        cmax = c > cmax ? c : cmax;
+        nitems += L.nblocks;
+        smem = L.smem > smem ? L.smem : smem;
+    }
+    int P = worklist_max_clusters(cs, smem);
+    if (P <= 0) return 0;
+    if (P > nitems) P = (int)nitems;
+    const double t_wl = fmax(cmax, sum / P);
+    double tmax = 0.0, sm_us = 0.0;
+    for (int i = 0; i < njobs; ++i) {
+        const rom_s* h = jobs[i].h;
+        Rank2Plan p;
+        double t = 0.0;
+        if (plan_rank2_split_f32(h->Kp, jobs[i].M, h->R, &p)) {
+            t = model_split_us(h->Kp, p.Wa);
+        } else if (plan_rank2_simt_f32(h->Kp, jobs[i].M, h->R, false, &p)) {
+            const int act = p.max_active_clusters > 0 ? p.max_active_clusters : 1;
+            t = ((p.nclusters + act - 1) / act) * model_streamed_us(h->Kp, p.nrt, p.Wa);
+        } else {
+            return kWlDefault;
+        }
+        const int busy = p.nclusters < p.max_active_clusters ? p.nclusters : p.max_active_clusters;
+        tmax = t > tmax ? t : tmax;
+        sm_us += t * busy * p.cs;
+    }
+    const double t_pj = fmax(tmax, sm_us / nsm);
+    return t_pj < t_wl ? 0 : kWlDefault;
+}
+
 static rom_status run_batched_worklist(const rom_job* jobs, int njobs, int nsteps, int r,
                                        cudaStream_t st, int dev, int wl) {
     int cs = 0, wcap = 0;
@@ -1193,23 +1277,13 @@ static rom_status run_batched_worklist(const rom_job* jobs, int njobs, int nstep
         for (int i = 0; i < njobs; ++i) {
             const rom_s* h = jobs[i].h;
             const int Kp = h->Kp, M = jobs[i].M;
-            const int nrt = (Kp / 32 + cs - 1) / cs;
-            const int rpc = (h->R + cs - 1) / cs;
-            const int cglob = (size_t)rpc * Kp * sizeof(float) > 16384 ? 1 : 0;
-            const int rst = cglob ? 0 : rpc;
-            int wmax = 0;
-            for (int w = 8; w <= wcap; w += 8) {
-                if (worklist_smem(w, Kp, rst, nrt) > budget) break;
-                wmax = w;
-            }
-            if (wmax == 0) {
+            WlJob L;
+            if (!wl_job_layout(h, M, cs, wcap, budget, &L)) {
                 snprintf(g_last_error, sizeof(g_last_error), "no work-list width for Kp=%d", Kp);
                 return ROM_E_UNSUPPORTED;
             }
-            const int nb = (M + wmax - 1) / wmax;
-            const int W = (((M + nb - 1) / nb) + 7) / 8 * 8;
-            const size_t sm = worklist_smem(W, Kp, rst, nrt);
-            smem = sm > smem ? sm : smem;
+            const int nrt = L.nrt, cglob = L.cglob, W = L.W, nb = L.nblocks;
+            smem = L.smem > smem ? L.smem : smem;
             GroupOp& g = ops[i];
             g.Avs_rm = h->Avs_rm[1];
             g.Asv_rm = h->Asv_rm[1];
@@ -1229,7 +1303,7 @@ static rom_status run_batched_worklist(const rom_job* jobs, int njobs, int nstep
             g.Kp = Kp;
             g.Wa = W;
             g.c_global = cglob;
-            cost[i] = 3.5 + 1.39 * W * (Kp / 1024.0) * nrt / 2.0;
+            cost[i] = model_streamed_us(Kp, nrt, W);
             nitems += nb;
         }
         // ---- the item list, longest first (ties: job order, then columns)
@@ -1454,9 +1528,13 @@ static std::vector<uintptr_t> batch_tune_key(const rom_job* jobs, int njobs, int
 rom_status rom_run_batched(const rom_job* jobs, int njobs, int nsteps, int r, int prec, void* stream) {
     double scale = 1.0;
     int kthr = kAutoKthr, tcw = 1, wl = kWlDefault;
+    bool model_form = false;
     if (jobs && njobs > 0) {
-        for (int i = 0; i < njobs; ++i)
+        bool valid = true;
+        for (int i = 0; i < njobs; ++i) {
             if (!jobs[i].h) return ROM_E_INVAL;
+            valid = valid && jobs[i].M >= 1;
+        }
         std::lock_guard<std::mutex> lk(g_batch_mu);
         const auto key = batch_tune_key(jobs, njobs, prec);
         auto it = g_batch_scale.find(key);
@@ -1467,6 +1545,16 @@ rom_status rom_run_batched(const rom_job* jobs, int njobs, int nsteps, int r, in
         if (tw != g_batch_tcw.end()) tcw = tw->second;
         auto wt = g_batch_wl.find(key);
         if (wt != g_batch_wl.end()) wl = wt->second;
+        else model_form = prec == ROM_FP32 && valid;
+    }
+    if (model_form) {
+        // neither pinned nor tuned: the models' choice, kept for this list
+        int dev = 0, nsm = 0;
+        ROM_CUDA(cudaGetDevice(&dev));
+        ROM_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+        wl = batched_default_form(jobs, njobs, dev, nsm);
+        std::lock_guard<std::mutex> lk(g_batch_mu);
+        g_batch_wl.emplace(batch_tune_key(jobs, njobs, prec), wl);
     }
     return run_batched_impl(jobs, njobs, nsteps, r, prec, stream, scale, kthr, tcw, wl);
 }

@@ -86,6 +86,14 @@ struct Rank2Args {
     int* item_counter;
 };
 
+// Step-time models, microseconds per leapfrog step of one cluster, fitted on
+// GB300: the two-block split kernel with W columns per block (operators in
+// registers), and a kernel that streams its operators from L2 with nrt
+// 32-row tiles per CTA and W columns (one-block kernel above Kp = 512, the
+// work-list kernel).
+inline double model_split_us(int Kp, int W) { return 2.24 + 0.466 * W * (Kp / 512.0); }
+inline double model_streamed_us(int Kp, int nrt, int W) { return 3.5 + 0.71 * nrt * W * (Kp / 1024.0); }
+
 // Launch plan chosen by the host for a rank-2 call.
 struct Rank2Plan {
     int cs;        // cluster size (CTAs)

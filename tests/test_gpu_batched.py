@@ -204,6 +204,30 @@ def test_autotune_single_handle(rom):
     assert np.linalg.norm(V3.cpu().numpy() - a) <= 1e-4 * np.linalg.norm(a)
 
 
+def test_autotune_single_handle_above_512(rom):
+    """K = 768: the planner picks clusters of 4 or 2 for the streamed
+    operators; the tuner, which also times that plan, keeps one of the
+    one-block cluster sizes, and its result holds the sampled columns to the
+    oracle."""
+    K, M, N = 768, 256, 120
+    p = inputs.make_problem(K, K, M, 8, seed=21)
+    h = rom.Rom.from_problem(p)
+    T = torch.as_tensor(p.T, device="cuda")
+    planned = h.plan(M)
+    us = h.autotune(M, "fp32", probe_steps=100)
+    assert us > 0
+    tuned = h.plan(M)
+    assert tuned["cluster_size"] in (2, 4, K // 64)
+    V, S = rom.Rom.new_state(K, M, "fp32"), rom.Rom.new_state(K, M, "fp32")
+    h.run_rank2(V, S, T, N, prec="fp32")
+    torch.cuda.synchronize()
+    cols = np.array([0, 100, 255])
+    Vo, So, _ = oracle.problem_forward(p, nsteps=N, r=0, columns=cols)
+    assert colmax_rel(V.cpu().numpy()[:, cols], Vo) <= 1e-4
+    assert colmax_rel(S.cpu().numpy()[:, cols], So) <= 1e-4
+    assert planned["cluster_size"] in (2, 4)  # the model's choice at this size
+
+
 def test_batched_auto_precision(rom):
     """prec="auto": jobs with max(Kv, Ks) >= 256 take the exact-slice BF16
     tensor-core path, the others FP32; every result meets the FP32 bar
