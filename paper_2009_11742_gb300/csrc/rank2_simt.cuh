@@ -17,6 +17,15 @@
 //  * The epilogue fuses the point-source forcing g f_n^T (Sec. 2.2, 3.2), the
 //    Kahan-compensated FP32 state update, and every r steps the receiver traces
 //    y = C V (Sec. 4.5.2, rows of C split across the cluster).
+// Variants of the same body:
+//  * FP64 beyond Kp = 256 and FP32 beyond Kp = 512 re-read each CTA's operator
+//    rows from L2 every half-step instead of holding them (FP32: two 32-row
+//    tiles per CTA, or more on smaller clusters).
+//  * GEN (FP32 with streamed operators): the row tiles are dealt out to any
+//    cluster size and the products run on a 4-row, 32-lane half-step, which
+//    feeds 16 multiply-adds from each 16-byte state read instead of 8.
+//  * rank2_wl_kernel: the batched work list, one persistent launch whose
+//    clusters take (job, column block) items of jobs of any Kp <= 1024.
 #pragma once
 
 #include <cooperative_groups.h>
