@@ -37,27 +37,29 @@ static size_t adjoint_smem(bool f64, int W, int Kp, int R, int nrt) {
     return f64 ? adj_smem_layout<double>(W, Kp, R, nrt).total : adj_smem_layout<float>(W, Kp, R, nrt).total;
 }
 
-// FP32, Kp <= 512: one 32-row tile per CTA (Kp / 32 CTAs, operators in
-// registers); 512 < Kp <= 1024: two tiles per CTA (Kp / 64 CTAs, operators
-// read from L2).  FP64: Kp <= 512, one tile per CTA.  Widths are multiples of
-// the kernel's columns per pass.
-bool plan_adjoint(int Kp, int M, int R, AdjPlan* p, bool f64) {
-    if (Kp <= 0 || Kp % 64 != 0 || Kp > (f64 ? 512 : 1024) || M <= 0 || R <= 0) return false;
+// The plan for clusters of cs CTAs (cs = 0: Kp / 32 CTAs of one tile up to
+// Kp = 512, Kp / 64 of two above).  Widths are multiples of 8.
+static bool plan_adjoint_cs(int Kp, int M, int R, AdjPlan* p, bool f64, int cs) {
     p->f64 = f64;
     p->KI = Kp / 64;
-    const int nrt = Kp > 512 ? 2 : 1;
-    p->cs = Kp / (32 * nrt);
+    if (cs == 0) {
+        p->nrt = Kp > 512 ? 2 : 1;
+        p->cs = Kp / (32 * p->nrt);
+    } else {
+        p->cs = cs;
+        p->nrt = (Kp / 32 + cs - 1) / cs;
+    }
     p->cb = f64 ? 4 : 8;
     const int smax = device_smem_optin();
     int wcap = 0;
     for (int w = 8; w <= 2048; w += 8) {
-        if (adjoint_smem(f64, w, Kp, R, nrt) > (size_t)smax) break;
+        if (adjoint_smem(f64, w, Kp, R, p->nrt) > (size_t)smax) break;
         wcap = w;
     }
     if (wcap == 0) return false;
     void* fn = adjoint_kernel(*p);
     if (!fn) return false;
-    const size_t smem_probe = adjoint_smem(f64, wcap, Kp, R, nrt);
+    const size_t smem_probe = adjoint_smem(f64, wcap, Kp, R, p->nrt);
     if (prepare_kernel<float>(fn, smem_probe) != cudaSuccess) return false;
     ClusterLaunch probe(p->cs, 1, kThreads, smem_probe);
     const int nact = probe.max_active(fn);
@@ -68,7 +70,26 @@ bool plan_adjoint(int Kp, int M, int R, AdjPlan* p, bool f64) {
     p->Wv = wv;
     p->Wa = wv;
     p->nclusters = (M + wv - 1) / wv;
-    p->smem = adjoint_smem(f64, p->Wa, Kp, R, nrt);
+    p->smem = adjoint_smem(f64, p->Wa, Kp, R, p->nrt);
+    // waves x step-time model, to compare cluster sizes
+    const int waves = (p->nclusters + nact - 1) / nact;
+    p->model_us = waves * model_streamed_us(Kp, p->nrt, p->Wa);
+    return true;
+}
+
+// FP32, Kp <= 512: one 32-row tile per CTA (Kp / 32 CTAs, operators in
+// registers).  FP32 above: the operators are read from L2 and the row tiles
+// dealt out to any cluster size, so Kp / 64 CTAs (7 co-resident), 4 (36) and
+// 2 (76) are priced with the step-time model and the fastest kept.  FP64:
+// Kp <= 512, one tile per CTA.
+bool plan_adjoint(int Kp, int M, int R, AdjPlan* p, bool f64) {
+    if (Kp <= 0 || Kp % 64 != 0 || Kp > (f64 ? 512 : 1024) || M <= 0 || R <= 0) return false;
+    if (!plan_adjoint_cs(Kp, M, R, p, f64, 0)) return false;
+    if (f64 || Kp <= 512) return true;
+    for (int cs : {4, 2}) {
+        AdjPlan q{};
+        if (plan_adjoint_cs(Kp, M, R, &q, f64, cs) && q.model_us < p->model_us) *p = q;
+    }
     return true;
 }
 
@@ -78,6 +99,7 @@ static cudaError_t launch_adjoint_t(const AdjArgsT<T>& a_in, const AdjPlan& p, c
     AdjArgsT<T> a = a_in;
     a.Wv = p.Wv;
     a.Wa = p.Wa;
+    a.nrt = p.nrt;
     void* fn = adjoint_kernel(p);
     if (!fn) return cudaErrorInvalidValue;
     cudaError_t e = prepare_kernel<float>(fn, p.smem);

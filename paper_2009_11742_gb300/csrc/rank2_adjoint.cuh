@@ -111,16 +111,68 @@ __device__ __forceinline__ void adj_half_a(const T (&op)[2][4 * KI], const T* __
     }
 }
 
+// Half A in the 4-row, 32-lane form of the work-list kernel (FP32 with the
+// operators streamed from L2): warp w holds rows 4w .. 4w + 3 of the tile,
+// lane l the k values 128 i + 4 l + q (k < Kp); the epilogue adds
+// 2 C_own^T r as above.
+template <int KQ>
+__device__ __forceinline__ void wl_adj_half_a(const float (&op)[4][4 * KQ], const float* __restrict__ X,
+                                              float* __restrict__ Y, float* __restrict__ comp,
+                                              const float* __restrict__ Ccol, const int cstride,
+                                              const float* __restrict__ rbuf, const int R, const float dt,
+                                              const int Wa, const int Kp, const int row0, const int warp,
+                                              const int lane) {
+    constexpr int CB = 8;
+    for (int c0 = 0; c0 < Wa; c0 += CB) {
+        float acc[4][CB];
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+#pragma unroll
+            for (int cc = 0; cc < CB; ++cc) acc[r][cc] = 0.f;
+#pragma unroll
+        for (int i = 0; i < KQ; ++i) {
+            if (128 * i + 4 * lane >= Kp) continue;
+            float x[CB][4];
+#pragma unroll
+            for (int cc = 0; cc < CB; ++cc) load4(X + (size_t)(c0 + cc) * Kp + 128 * i + 4 * lane, x[cc]);
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+#pragma unroll
+                for (int cc = 0; cc < CB; ++cc)
+#pragma unroll
+                    for (int r = 0; r < 4; ++r) acc[r][cc] = __fmaf_rn(op[r][4 * i + q], x[cc][q], acc[r][cc]);
+        }
+        float v[4 * CB];
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+#pragma unroll
+            for (int cc = 0; cc < CB; ++cc) v[r * CB + cc] = acc[r][cc];
+        int vi;
+        const float tot = reduce_scatter32(v, lane, vi);
+        const int rl = 4 * warp + vi / CB;
+        const int c = c0 + vi % CB;
+        float src = 0.f;
+        for (int jr = 0; jr < R; ++jr) src = __fmaf_rn(Ccol[jr * cstride + rl], rbuf[jr * Wa + c], src);
+        const float inc = __fmaf_rn(tot, dt, 2.f * src);
+        float* yp = Y + (size_t)c * Kp + row0 + rl;
+        *yp = kahan_add(*yp, inc, comp[c * kRowsPerCta + rl]);
+    }
+}
+
 // KI = Kp / 64.  FP32 (KI <= 16): operators resident in registers for
-// KI <= 8 (one 32-row tile per CTA), streamed per tile above (two tiles per
-// CTA).  FP64 (KI <= 8): one tile per CTA, resident for KI <= 4.
+// KI <= 8 (one 32-row tile per CTA); above that (GEN) the Kp / 32 row tiles
+// are dealt out to the cluster's CTAs (the first Kp/32 mod cs take one more;
+// a.nrt is the most any CTA owns), the operators are streamed per tile, and
+// both halves run in the 4-row form.  FP64 (KI <= 8): one tile per CTA,
+// resident for KI <= 4.
 template <typename T, int KI, int CB>
 __global__ void __launch_bounds__(kThreads, 1) rank2_adjoint_kernel(const AdjArgsT<T> a) {
     constexpr bool F32 = sizeof(T) == 4;
     static_assert(F32 ? KI <= 16 : KI <= 8, "unsupported size");
-    constexpr int NRT = KI > 8 ? 2 : 1;
-    constexpr bool RES = F32 ? NRT == 1 : KI <= 4;
-    constexpr int OWN = NRT * kRowsPerCta;
+    constexpr bool GEN = F32 && KI > 8;
+    static_assert(!GEN || CB == 8, "the 4-row form runs 8-column groups");
+    constexpr bool RES = F32 ? !GEN : KI <= 4;
+    constexpr int KQ = (KI + 1) / 2;  // GEN: k groups of 128
     cg::cluster_group cluster = cg::this_cluster();
     const int cs = (int)cluster.num_blocks();
     const int crank = (int)cluster.block_rank();
@@ -131,7 +183,16 @@ __global__ void __launch_bounds__(kThreads, 1) rank2_adjoint_kernel(const AdjArg
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int j = lane & 15;
     const int rp = warp * 2 + (lane >> 4);
-    const int row0 = crank * OWN;
+    // row tiles: the layout holds NRT per CTA, this CTA owns nrt_own from row0
+    const int NRT = GEN ? a.nrt : 1;
+    const int OWN = NRT * kRowsPerCta;
+    int nrt_own = NRT, row0 = crank * OWN;
+    if (GEN) {
+        const int tiles = Kp / kRowsPerCta, base = tiles / cs, rem = tiles % cs;
+        nrt_own = base + (crank < rem ? 1 : 0);
+        row0 = (crank * base + (crank < rem ? crank : rem)) * kRowsPerCta;
+    }
+    const int own_rows = nrt_own * kRowsPerCta;
     const T dt = (T)a.dt;
 
     extern __shared__ __align__(16) unsigned char smem[];
@@ -153,7 +214,7 @@ __global__ void __launch_bounds__(kThreads, 1) rank2_adjoint_kernel(const AdjArg
         Sf[idx] = (c < ncol && k < a.Ks) ? a.lamS[(size_t)(col0 + c) * a.Ks + k] : T(0);
     }
     // carries (FP32): [row tile][column][32 rows]
-    for (int idx = tid; idx < (F32 ? NRT * Wa * kRowsPerCta : 0); idx += kThreads) {
+    for (int idx = tid; idx < (F32 ? nrt_own * Wa * kRowsPerCta : 0); idx += kThreads) {
         const int rt = idx / (Wa * kRowsPerCta);
         const int rem = idx - rt * Wa * kRowsPerCta;
         const int c = rem / kRowsPerCta, rl = rem % kRowsPerCta, row = row0 + rt * kRowsPerCta + rl;
@@ -162,14 +223,15 @@ __global__ void __launch_bounds__(kThreads, 1) rank2_adjoint_kernel(const AdjArg
     }
     for (int idx = tid; idx < R * OWN; idx += kThreads) {
         const int jr = idx / OWN, ro = idx % OWN;
-        Ccol[idx] = a.C_rm[(size_t)jr * Kp + row0 + ro];
+        Ccol[idx] = ro < own_rows ? a.C_rm[(size_t)jr * Kp + row0 + ro] : T(0);
     }
-    for (int ro = tid; ro < OWN; ro += kThreads) gown[ro] = a.g_p[row0 + ro];
+    for (int ro = tid; ro < OWN; ro += kThreads) gown[ro] = ro < own_rows ? a.g_p[row0 + ro] : T(0);
     for (int c = tid; c < Wa; c += kThreads) {
         Tcol[c] = (c < ncol) ? a.Tper[col0 + c] : T(1);
         gTacc[c] = (c < ncol) ? a.gTpart[(size_t)crank * a.M + col0 + c] : T(0);
     }
     T opA[2][4 * KI], opB[2][4 * KI];
+    float opQ[GEN ? 4 : 1][GEN ? 4 * KQ : 1];
     if (RES) {
         load_op_rows<T, KI>(opA, a.opA_rm, Kp, row0 + 2 * rp, j);
         load_op_rows<T, KI>(opB, a.opB_rm, Kp, row0 + 2 * rp, j);
@@ -205,42 +267,52 @@ __global__ void __launch_bounds__(kThreads, 1) rank2_adjoint_kernel(const AdjArg
         }
         __syncthreads();
         // ---- half A: lamV <- lamV + 2 C^T r^{n+1} + dt Asv^T lamS
-#pragma unroll
-        for (int rt = 0; rt < NRT; ++rt) {
+        for (int rt = 0; rt < nrt_own; ++rt) {
             const int rowt = row0 + rt * kRowsPerCta;
-            if (!RES) load_op_rows<T, KI>(opA, a.opA_rm, Kp, rowt + 2 * rp, j);
-            adj_half_a<T, KI, CB>(opA, Sf, Vf, cV + rt * Wa * kRowsPerCta, Ccol + rt * kRowsPerCta, OWN,
-                                  rbuf, R, dt, Wa, Kp, rowt, rp, j);
+            if constexpr (GEN) {
+                wl_load_op<KQ>(opQ, a.opA_rm, Kp, rowt + 4 * warp, lane);
+                wl_adj_half_a<KQ>(opQ, Sf, Vf, cV + rt * Wa * kRowsPerCta, Ccol + rt * kRowsPerCta, OWN,
+                                  rbuf, R, dt, Wa, Kp, rowt, warp, lane);
+            } else {
+                if (!RES) load_op_rows<T, KI>(opA, a.opA_rm, Kp, rowt + 2 * rp, j);
+                adj_half_a<T, KI, CB>(opA, Sf, Vf, cV + rt * Wa * kRowsPerCta, Ccol + rt * kRowsPerCta, OWN,
+                                      rbuf, R, dt, Wa, Kp, rowt, rp, j);
+            }
         }
         __syncthreads();
         // period gradient: dt (g_own . a_V[:, c]) df/dT(t_n; T_c), fixed reduction order
         for (int c = warp; c < ncol; c += kThreads / 32) {
-            T s = gown[lane] * Vf[(size_t)c * Kp + row0 + lane];
-#pragma unroll
-            for (int rt = 1; rt < NRT; ++rt)
+            T s = T(0);
+            if (nrt_own > 0) s = gown[lane] * Vf[(size_t)c * Kp + row0 + lane];
+            for (int rt = 1; rt < nrt_own; ++rt)
                 s = fmadd(gown[rt * kRowsPerCta + lane], Vf[(size_t)c * Kp + row0 + rt * kRowsPerCta + lane], s);
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
             if (lane == 0) gTacc[c] = fmadd(dt * s, dfn[c], gTacc[c]);
         }
-        push_own_rows<T>(cluster, Vf, Wa, Kp, row0, cs, crank, NRT);
+        push_own_rows<T>(cluster, Vf, Wa, Kp, row0, cs, crank, nrt_own);
         cluster.sync();
         // ---- half B: lamS <- lamS + dt Avs^T a_V
-#pragma unroll
-        for (int rt = 0; rt < NRT; ++rt) {
+        for (int rt = 0; rt < nrt_own; ++rt) {
             const int rowt = row0 + rt * kRowsPerCta;
-            if (!RES) load_op_rows<T, KI>(opB, a.opB_rm, Kp, rowt + 2 * rp, j);
-            half_step<T, KI, CB, false>(opB, Vf, Sf, cS + rt * Wa * kRowsPerCta, gown, gown, dt, Wa,
-                                        Kp, rowt, rp, j);
+            if constexpr (GEN) {
+                wl_load_op<KQ>(opQ, a.opB_rm, Kp, rowt + 4 * warp, lane);
+                wl_half_step<KQ, false>(opQ, Vf, Sf, cS + rt * Wa * kRowsPerCta, gown, gown, dt, Wa, Kp, rowt,
+                                        warp, lane);
+            } else {
+                if (!RES) load_op_rows<T, KI>(opB, a.opB_rm, Kp, rowt + 2 * rp, j);
+                half_step<T, KI, CB, false>(opB, Vf, Sf, cS + rt * Wa * kRowsPerCta, gown, gown, dt, Wa,
+                                            Kp, rowt, rp, j);
+            }
         }
         __syncthreads();
-        push_own_rows<T>(cluster, Sf, Wa, Kp, row0, cs, crank, NRT);
+        push_own_rows<T>(cluster, Sf, Wa, Kp, row0, cs, crank, nrt_own);
         cluster.sync();
     }
 
     int bad = 0;
-    for (int idx = tid; idx < ncol * OWN; idx += kThreads) {
-        const int c = idx / OWN, ro = idx % OWN, row = row0 + ro;
+    for (int idx = tid; idx < ncol * own_rows; idx += kThreads) {
+        const int c = idx / own_rows, ro = idx % own_rows, row = row0 + ro;
         const int ci = (ro / kRowsPerCta) * Wa * kRowsPerCta + c * kRowsPerCta + ro % kRowsPerCta;
         if (row < a.Kv) {
             const T x = Vf[(size_t)c * Kp + row];

@@ -210,13 +210,15 @@ struct AdjArgsT {
     int n_lo, n_hi;       // reverse steps n_hi-1 .. n_lo
     int rec_base;
     int Kv, Ks, Kp, R, M, Wv, Wa;
+    int nrt;              // 32-row tiles the layout holds per CTA (FP32 above Kp = 512)
     int wavelet;          // source signal of the periods (see Rank2Args)
 };
 using AdjArgs = AdjArgsT<float>;
 struct AdjPlan {
-    int cs, KI, cb, Wv, Wa, nclusters;
+    int cs, KI, cb, Wv, Wa, nclusters, nrt;
     size_t smem;
-    bool f64;  // the FP64 instance (Kp <= 512)
+    bool f64;         // the FP64 instance (Kp <= 512)
+    double model_us;  // modelled µs per reverse step (cluster-size choice)
 };
 bool plan_adjoint(int Kp, int M, int R, AdjPlan* p, bool f64 = false);
 cudaError_t launch_adjoint(const AdjArgsT<float>& a, const AdjPlan& p, cudaStream_t st);

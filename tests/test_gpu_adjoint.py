@@ -61,7 +61,10 @@ def gpu_adjoint(R, h, p, V0, S0, ystar, N, ckpt):
                                                # above K = 512: two 32-row tiles per CTA, the
                                                # transposed operators read from L2
                                                (640, 600, 11, 5, 36, 0), (1024, 1000, 6, 8, 40, 16),
-                                               (1000, 1024, 17, 3, 25, 9)])
+                                               (1000, 1024, 17, 3, 25, 9),
+                                               # enough columns for the planner to take clusters
+                                               # of 4: 22 row tiles dealt 6, 6, 5, 5
+                                               (704, 680, 256, 8, 20, 0)])
 def test_adjoint_vs_oracle(rom, Kv, Ks, M, R, N, ckpt):
     p, V0, S0, ystar = case(Kv, Ks, M, R, N, seed=Kv + M)
     h = rom.Rom.from_problem(p)
