@@ -1314,6 +1314,7 @@ static rom_status run_batched_worklist(const rom_job* jobs, int njobs, int nstep
                 items.push_back({i, col, jobs[i].M - col < ops[i].Wa ? jobs[i].M - col : ops[i].Wa, 0});
         std::stable_sort(items.begin(), items.end(),
                          [&](const WorkItem& x, const WorkItem& y) { return cost[x.job] > cost[y.job]; });
+        nitems = (int)items.size();  // the list as built (equal to the blocks counted above)
         int ncl = worklist_max_clusters(cs, smem);
         if (ncl <= 0) {
             snprintf(g_last_error, sizeof(g_last_error), "work-list kernel does not fit (cs=%d, %zu B)", cs, smem);
