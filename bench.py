@@ -194,9 +194,11 @@ def cpu_baseline_sample(p, target_s=16.0):
     ncol = min(WORKLOAD["M"], 2 * cores)
     cols = np.linspace(0, WORKLOAD["M"] - 1, ncol).astype(int)
     oracle.problem_forward(p, nsteps=WORKLOAD["r"], r=WORKLOAD["r"], columns=cols)  # threads up
+    # long enough that the call's fixed cost (buffers, thread start) is small
+    ncal = min(WORKLOAD["nsteps"], 1000)
     t0 = time.perf_counter()
-    oracle.problem_forward(p, nsteps=100, r=WORKLOAD["r"], columns=cols)
-    per_step = (time.perf_counter() - t0) / 100
+    oracle.problem_forward(p, nsteps=ncal, r=WORKLOAD["r"], columns=cols)
+    per_step = (time.perf_counter() - t0) / ncal
     full = per_step * WORKLOAD["nsteps"]
     if full < target_s and ncol < WORKLOAD["M"]:
         # every step fits: widen the column sample (whole multiples of the cores)
