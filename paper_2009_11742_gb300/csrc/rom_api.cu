@@ -25,6 +25,9 @@ void romk::set_last_error(const char* msg) { snprintf(g_last_error, sizeof(g_las
 
 rom_status romk::cuda_fail(cudaError_t e, const char* where) {
     snprintf(g_last_error, sizeof(g_last_error), "%s: %s", where, cudaGetErrorString(e));
+    // clear the runtime's record of a non-sticky error (a failed allocation),
+    // so that a later call's launch check does not report it again
+    (void)cudaGetLastError();
     return e == cudaErrorMemoryAllocation ? ROM_E_NOMEM : ROM_E_CUDA;
 }
 

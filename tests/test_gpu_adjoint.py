@@ -318,3 +318,28 @@ def test_adjoint_fp64_refuses_above_512(rom):
     with pytest.raises(rom.RomError):
         gpu_adjoint64(rom, h, p, V0.astype(np.float64), S0.astype(np.float64),
                       ystar.astype(np.float64), 5, 0, T=p.T.astype(np.float64))
+
+
+def test_adjoint_allocation_failure_is_reported(rom):
+    """A workspace the GPU cannot hold (every trace of 10^7 steps kept:
+    10^7 x 64 x 256 x 4 B = 655 GB) is refused with ROM_E_NOMEM before any
+    kernel runs, and the next call on the same handle succeeds."""
+    K, M, R = 64, 256, 64
+    p, V0, S0, ystar = case(K, K, M, R, 10, seed=31)
+    h = rom.Rom.from_problem(p)
+    need = rom.rom_adjoint_workspace_size(h.h, M, 10 ** 7, 0, rom.ROM_FP32)
+    assert need > 600 * 10 ** 9
+    V0t = rom.Rom.new_state(K, M, "fp32", fill=V0)
+    S0t = rom.Rom.new_state(K, M, "fp32", fill=S0)
+    T = torch.as_tensor(p.T, device="cuda")
+    ys = torch.zeros((10, M, R), device="cuda")  # never read: the allocation fails first
+    gV = rom.Rom.new_state(K, M, "fp32")
+    gS = rom.Rom.new_state(K, M, "fp32")
+    gT = torch.zeros(M, device="cuda")
+    st, _ = rom.rom_adjoint(h.h, V0t.data_ptr(), S0t.data_ptr(), T.data_ptr(), M, 10 ** 7,
+                            ys.data_ptr(), 0, gV.data_ptr(), gS.data_ptr(), gT.data_ptr(), None, 0,
+                            rom.ROM_FP32, None)
+    assert st == rom.ROM_E_NOMEM
+    loss, gV2, gS2, gT2 = gpu_adjoint(rom, h, p, V0, S0, ystar, 10, 0)
+    Lo, gVo, _, _ = oracle.adjoint(p.Avs, p.Asv, p.g, p.C, p.dt, V0, S0, p.T, 10, ystar)
+    assert abs(loss - Lo) <= 1e-4 * abs(Lo) and rel(gV2, gVo) <= 1e-4
