@@ -614,6 +614,8 @@ def bench_uq(args, torch, dev, inputs, rom):
                                 "probs": list(c["probs"])},
                       "rank1_ensemble_sample_steps_s": r1,
                       "rank2_over_rank1_ensemble": (M * N / tr_run) / r1,
+                      "tflops_useful": 4.0 * Kv * Ks * M * N / tr_run / 1e12,
+                      "plan": h.plan(M),
                       "rel_err_traces_vs_oracle": {"value": err, "columns": cols.tolist(), "steps": Na}}),
           flush=True)
     return 0

@@ -10,30 +10,23 @@
 
 namespace romk {
 
-// Instances whose owned rows (Kp / csz) are whole 64-row passes.
+// Instances for clusters of 2 and 4 CTAs, Kp = 64 .. 512 (the owned rows
+// Kp / csz are whole 16-row groups; the last 64-row pass may be partial).
 static void* stream_kernel(int KI, int csz) {
-    if (csz == 2) {
-        switch (KI) {
-            case 2: return (void*)&rank2_stream_kernel<2, 2>;
-            case 4: return (void*)&rank2_stream_kernel<4, 2>;
-            case 6: return (void*)&rank2_stream_kernel<6, 2>;
-            case 8: return (void*)&rank2_stream_kernel<8, 2>;
-            default: return nullptr;
-        }
+#define ROM_STR_CASE(k)                                                          \
+    case k: return csz == 2 ? (void*)&rank2_stream_kernel<k, 2> : (void*)&rank2_stream_kernel<k, 4>;
+    if (csz != 2 && csz != 4) return nullptr;
+    switch (KI) {
+        ROM_STR_CASE(1) ROM_STR_CASE(2) ROM_STR_CASE(3) ROM_STR_CASE(4)
+        ROM_STR_CASE(5) ROM_STR_CASE(6) ROM_STR_CASE(7) ROM_STR_CASE(8)
+        default: return nullptr;
     }
-    if (csz == 4) {
-        switch (KI) {
-            case 4: return (void*)&rank2_stream_kernel<4, 4>;
-            case 8: return (void*)&rank2_stream_kernel<8, 4>;
-            default: return nullptr;
-        }
-    }
-    return nullptr;
+#undef ROM_STR_CASE
 }
 
 bool stream_supported(int Kp, int csz) {
     return Kp > 0 && Kp % 64 == 0 && Kp <= 512 && (csz == 2 || csz == 4) &&
-           (Kp / csz) % kStrRows == 0 && stream_smem_layout(Kp, csz).total <= (size_t)device_smem_optin();
+           (Kp / csz) % 16 == 0 && stream_smem_layout(Kp, csz).total <= (size_t)device_smem_optin();
 }
 
 int stream_max_columns_per_cluster() { return kStrCols; }

@@ -65,15 +65,16 @@ __host__ __device__ inline StreamSmem stream_smem_layout(int Kp, int csz) {
     return s;
 }
 
-// KI = Kp / 64 (Kp <= 512); CSZ CTAs per cluster; Kp / CSZ a multiple of 64.
+// KI = Kp / 64 (Kp <= 512); CSZ CTAs per cluster; Kp / CSZ a multiple of 16
+// (a last pass of fewer than 64 rows leaves the row quads beyond the CTA's
+// rows idle: they load nothing and write nothing).
 template <int KI, int CSZ>
 __global__ void __launch_bounds__(kStrThreads, 1) rank2_stream_kernel(const Rank2Args a) {
     constexpr int Kp = 64 * KI;
     constexpr int NR = Kp / CSZ;               // rows owned per CTA
-    constexpr int NP = NR / kStrRows;          // 64-row passes per half-step
+    constexpr int NP = (NR + kStrRows - 1) / kStrRows;  // 64-row passes per half-step
     constexpr int NKS = Kp / kStrKC;           // k stages per pass (= KI)
-    constexpr int SPH = NP * NKS;              // stages per half-step
-    static_assert(NR % kStrRows == 0, "owned rows must be whole 64-row passes");
+    static_assert(NR % 16 == 0, "owned rows must be whole 16-row groups");
     constexpr int CB = kStrCols;
     cg::cluster_group cluster = cg::this_cluster();
     const int crank = (int)cluster.block_rank();
@@ -138,8 +139,18 @@ __global__ void __launch_bounds__(kStrThreads, 1) rank2_stream_kernel(const Rank
     // next half's first pass after the last one) as soon as it is used, so a
     // pass worth of loads is always in flight, across half-steps too.
     const size_t lane_off = (size_t)(r0 + 4 * q) * Kp + 4 * j;
+    // this thread's row quad exists in pass p (only a partial last pass,
+    // NR not a multiple of 64, leaves quads out)
+    constexpr bool WHOLE = NR % kStrRows == 0;
+    auto quad_in = [&](int p) { return WHOLE || kStrRows * p + 4 * q < NR; };
     float4 ring[NKS][4];
-    if (N > 0) {
+    if (!WHOLE) {  // quads absent from the first pass never load theirs
+#pragma unroll
+        for (int ks = 0; ks < NKS; ++ks)
+#pragma unroll
+            for (int r = 0; r < 4; ++r) ring[ks][r] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    if (N > 0 && quad_in(0)) {
         const float* src = Avs + lane_off;
 #pragma unroll
         for (int ks = 0; ks < NKS; ++ks)
@@ -163,7 +174,7 @@ __global__ void __launch_bounds__(kStrThreads, 1) rank2_stream_kernel(const Rank
             for (int p = 0; p < NP; ++p) {
                 // the pass whose stages refill the ring
                 const bool last = p + 1 == NP;
-                const bool has_next = !(last && h == 1 && n + 1 == N);
+                const bool has_next = !(last && h == 1 && n + 1 == N) && quad_in(last ? 0 : p + 1);
                 const float* nsrc = (last ? (h ? Avs : Asv) : (h ? Asv : Avs)) +
                                     (size_t)(last ? 0 : (p + 1) * kStrRows) * Kp + lane_off;
                 float acc[4][CB];
@@ -209,7 +220,7 @@ __global__ void __launch_bounds__(kStrThreads, 1) rank2_stream_kernel(const Rank
                 const float tot = reduce_scatter16<float, 4 * CB>(v, j, vi, active);
                 const int rl = p * kStrRows + 4 * q + vi / CB;
                 const int c = vi % CB;
-                if (active && c < ncol && r0 + rl < Kown) {
+                if (active && quad_in(p) && c < ncol && r0 + rl < Kown) {
                     float inc = tot;
                     if (h == 0) inc = __fmaf_rn(gown[rl], fcol[c], inc);
                     inc = inc * dt;

@@ -55,6 +55,10 @@ def run(R, h, p, V0, S0, N, r=0, n0=0, ftab=None):
     (200, 180, 37, 6, 150, 7, 9),      # ragged rows (Kp = 256), 3 companion clusters
     (256, 256, 6, 3, 200, 10, 6),      # every column on the companion, one 64-row pass per CTA
     (512, 500, 40, 64, 90, 3, 13),     # Ks < Kv, ragged last companion cluster, many receivers
+    # partial last 64-row pass: Kp = 448 owns 224 / 112 rows per CTA (3.5 /
+    # 1.75 passes), Kp = 192 owns 96 / 48 (1.5 passes / one partial pass)
+    (436, 417, 33, 8, 80, 4, 11),
+    (192, 170, 21, 5, 100, 5, 9),
 ])
 def test_companion_vs_oracle(rom, csz, Kv, Ks, M, R, N, r, cols):
     p = inputs.make_problem(Kv, Ks, M, R, seed=Kv + M + csz)
@@ -72,10 +76,12 @@ def test_companion_vs_oracle(rom, csz, Kv, Ks, M, R, N, r, cols):
 
 
 @pytest.mark.parametrize("csz", [2, 4])
-def test_companion_bitwise_equals_two_block_kernel(rom, csz):
+@pytest.mark.parametrize("Kv", [512, 448])
+def test_companion_bitwise_equals_two_block_kernel(rom, csz, Kv):
     """The companion's columns (state and traces) are bit for bit what the
-    two-block kernel alone computes for them."""
-    Kv, M, N, r = 512, 40, 150, 5
+    two-block kernel alone computes for them (Kp = 448: a partial last
+    pass per CTA)."""
+    M, N, r = 40, 150, 5
     p = inputs.make_problem(Kv, Kv, M, 64, seed=31)
     V0 = inputs.random_state(Kv, M, seed=1, scale=0.1)
     S0 = inputs.random_state(Kv, M, seed=2, scale=0.1)
