@@ -83,6 +83,17 @@ def measured_pipe_peaks(rom):
     return out
 
 
+def fp32_roofline(rom, tflops):
+    """The FP32 FMA roofline of a secondary workload: the achieved useful
+    rate against the FP32 peak measured live (rom_measure_peak)."""
+    try:
+        pk = rom.measure_peak("fp32")[0]
+    except Exception as exc:  # no denominator: report the rate alone
+        return {"bound": "alu", "achieved": tflops, "unit": "TFLOP/s", "peak_error": str(exc)}
+    return {"bound": "alu", "achieved": tflops, "peak": pk, "unit": "TFLOP/s", "frac": tflops / pk,
+            "peak_kind": "FP32 FMA microbenchmark (rom_measure_peak), this run"}
+
+
 class ClockSampler:
     """nvidia-smi samples of SM clock and throttle reasons during a region."""
 
@@ -385,6 +396,9 @@ def main():
             out = {"only_rank2": True, "workload": W["name"], "prec": prec, "value": value,
                    "unit": "sample-steps/s", "ms_per_step": ms_per_step, "nsteps": N,
                    "tflops_useful": world * flops * args.steps / t_dev / 1e12, "clocks": clocks}
+            if prec == "fp32":
+                out["roofline"] = fp32_roofline(rom, out["tflops_useful"])
+                out["plan"] = h.plan(M)
             if prec in TC_RATIO:
                 pk, pk_kind = peaks()
                 mp = measured_pipe_peaks(rom)
@@ -615,6 +629,7 @@ def bench_uq(args, torch, dev, inputs, rom):
                       "rank1_ensemble_sample_steps_s": r1,
                       "rank2_over_rank1_ensemble": (M * N / tr_run) / r1,
                       "tflops_useful": 4.0 * Kv * Ks * M * N / tr_run / 1e12,
+                      "roofline": fp32_roofline(rom, 4.0 * Kv * Ks * M * N / tr_run / 1e12),
                       "plan": h.plan(M),
                       "rel_err_traces_vs_oracle": {"value": err, "columns": cols.tolist(), "steps": Na}}),
           flush=True)
@@ -796,7 +811,9 @@ def bench_batched(args, torch, dev, inputs, rom):
                       "ms_per_step": 1e3 * t, "tflops_useful": fl / t / 1e12,
                       "untuned": {"value": ss / t0, "ms_per_step": 1e3 * t0},
                       "autotune_probe_us_per_step": probe_us,
-                      "columns_total": sum(p.M for p in probs)}), flush=True)
+                      "columns_total": sum(p.M for p in probs),
+                      **({"roofline": fp32_roofline(rom, fl / t / 1e12)} if prec == "fp32" else {})}),
+          flush=True)
     return 0
 
 
