@@ -130,4 +130,24 @@ __device__ __forceinline__ float kahan_add(float v, float inc, float& c) {
     return t;
 }
 
+// Asynchronous global -> shared copy of one 4- or 8-byte element (zero fill
+// when src_bytes is 0; gsrc must still be a valid address), and the wait for
+// all of this thread's outstanding ones.
+__device__ __forceinline__ void cp_async4(void* sdst, const void* gsrc, int src_bytes) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;"
+                 ::"r"((uint32_t)__cvta_generic_to_shared(sdst)), "l"(gsrc), "r"(src_bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async8(void* sdst, const void* gsrc, int src_bytes) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;"
+                 ::"r"((uint32_t)__cvta_generic_to_shared(sdst)), "l"(gsrc), "r"(src_bytes) : "memory");
+}
+template <typename T>
+__device__ __forceinline__ void cp_async_elem(T* sdst, const T* gsrc, bool ok) {
+    if constexpr (sizeof(T) == 4) cp_async4(sdst, gsrc, ok ? 4 : 0);
+    else cp_async8(sdst, gsrc, ok ? 8 : 0);
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+    asm volatile("cp.async.wait_all;" ::: "memory");
+}
+
 }  // namespace romk

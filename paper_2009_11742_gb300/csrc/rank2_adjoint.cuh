@@ -36,7 +36,7 @@ namespace romk {
 constexpr int kAdjTab = 64;
 
 struct AdjSmem {
-    size_t Vf, Sf, cV, cS, Ccol, rbuf, g, T, gT, dfT, total;
+    size_t Vf, Sf, cV, cS, Ccol, rbuf, trS, ysS, g, T, gT, dfT, total;
 };
 
 // nrt: 32-row tiles owned per CTA (1 for Kp <= 512, 2 above); T the element
@@ -53,6 +53,8 @@ __host__ __device__ inline AdjSmem adj_smem_layout(int Wa, int Kp, int R, int nr
     s.cS = o;   o += align16(ncarry * sizeof(float));
     s.Ccol = o; o += align16((size_t)R * own * sizeof(T));
     s.rbuf = o; o += align16((size_t)R * Wa * sizeof(T));
+    s.trS = o;  o += align16((size_t)R * Wa * sizeof(T));   // next step's traces, in flight
+    s.ysS = o;  o += align16((size_t)R * Wa * sizeof(T));   // and targets
     s.g = o;    o += align16(own * sizeof(T));
     s.T = o;    o += align16((size_t)Wa * sizeof(T));
     s.gT = o;   o += align16((size_t)Wa * sizeof(T));
@@ -159,19 +161,19 @@ __device__ __forceinline__ void wl_adj_half_a(const float (&op)[4][4 * KQ], cons
     }
 }
 
-// KI = Kp / 64.  FP32 (KI <= 16): operators resident in registers for
-// KI <= 8 (one 32-row tile per CTA); above that (GEN) the Kp / 32 row tiles
-// are dealt out to the cluster's CTAs (the first Kp/32 mod cs take one more;
-// a.nrt is the most any CTA owns), the operators are streamed per tile, and
-// both halves run in the 4-row form.  FP64 (KI <= 8): one tile per CTA,
-// resident for KI <= 4.
+// KI = Kp / 64.  FP32 (GEN, KI <= 16): both halves run in the 4-row form;
+// for KI <= 8 each CTA owns one 32-row tile and keeps its rows of both
+// transposed operators in registers, above that the Kp / 32 row tiles are
+// dealt out to the cluster's CTAs (the first Kp/32 mod cs take one more;
+// a.nrt is the most any CTA owns) and the operators are streamed per tile.
+// FP64 (KI <= 8): the 2-row form, one tile per CTA, resident for KI <= 4.
 template <typename T, int KI, int CB>
 __global__ void __launch_bounds__(kThreads, 1) rank2_adjoint_kernel(const AdjArgsT<T> a) {
     constexpr bool F32 = sizeof(T) == 4;
     static_assert(F32 ? KI <= 16 : KI <= 8, "unsupported size");
-    constexpr bool GEN = F32 && KI > 8;
+    constexpr bool GEN = F32;
     static_assert(!GEN || CB == 8, "the 4-row form runs 8-column groups");
-    constexpr bool RES = F32 ? !GEN : KI <= 4;
+    constexpr bool RES = F32 ? KI <= 8 : KI <= 4;
     constexpr int KQ = (KI + 1) / 2;  // GEN: k groups of 128
     cg::cluster_group cluster = cg::this_cluster();
     const int cs = (int)cluster.num_blocks();
@@ -203,6 +205,8 @@ __global__ void __launch_bounds__(kThreads, 1) rank2_adjoint_kernel(const AdjArg
     float* cS = reinterpret_cast<float*>(smem + L.cS);
     T* Ccol = reinterpret_cast<T*>(smem + L.Ccol);  // [R][OWN]: C[j][row0 + ro]
     T* rbuf = reinterpret_cast<T*>(smem + L.rbuf);  // [R][Wa]: residual of the step
+    T* trS = reinterpret_cast<T*>(smem + L.trS);    // [R][Wa]: C V^{n+1} of the next step
+    T* ysS = reinterpret_cast<T*>(smem + L.ysS);    // [R][Wa]: its target
     T* gown = reinterpret_cast<T*>(smem + L.g);
     T* Tcol = reinterpret_cast<T*>(smem + L.T);
     T* gTacc = reinterpret_cast<T*>(smem + L.gT);
@@ -230,12 +234,30 @@ __global__ void __launch_bounds__(kThreads, 1) rank2_adjoint_kernel(const AdjArg
         Tcol[c] = (c < ncol) ? a.Tper[col0 + c] : T(1);
         gTacc[c] = (c < ncol) ? a.gTpart[(size_t)crank * a.M + col0 + c] : T(0);
     }
-    T opA[2][4 * KI], opB[2][4 * KI];
-    float opQ[GEN ? 4 : 1][GEN ? 4 * KQ : 1];
-    if (RES) {
+    T opA[GEN ? 1 : 2][GEN ? 1 : 4 * KI], opB[GEN ? 1 : 2][GEN ? 1 : 4 * KI];
+    float opQA[GEN ? 4 : 1][GEN ? 4 * KQ : 1], opQB[GEN ? 4 : 1][GEN ? 4 * KQ : 1];
+    if constexpr (GEN) {
+        if (RES && nrt_own > 0) {
+            wl_load_op<KQ>(opQA, a.opA_rm, Kp, row0 + 4 * warp, lane);
+            wl_load_op<KQ>(opQB, a.opB_rm, Kp, row0 + 4 * warp, lane);
+        }
+    } else if (RES) {
         load_op_rows<T, KI>(opA, a.opA_rm, Kp, row0 + 2 * rp, j);
         load_op_rows<T, KI>(opB, a.opB_rm, Kp, row0 + 2 * rp, j);
     }
+    // the trace record C V^{n+1} and target y*^{n+1} of reverse step n, copied
+    // asynchronously into trS / ysS while the step before it computes
+    auto prefetch_residual = [&](int n) {
+        const int rec = n + 1 - a.rec_base;  // trace record holding C V^{n+1}
+        for (int idx = tid; idx < R * Wa; idx += kThreads) {
+            const int jr = idx / Wa, c = idx % Wa;
+            const bool ok = c < ncol;
+            const int cc = ok ? c : 0;  // a valid address for the zero fill
+            cp_async_elem<T>(trS + idx, a.traces + ((size_t)rec * a.M + col0 + cc) * R + jr, ok);
+            cp_async_elem<T>(ysS + idx, a.ystar + ((size_t)n * a.M + col0 + cc) * R + jr, ok);
+        }
+    };
+    if (a.n_hi > a.n_lo) prefetch_residual(a.n_hi - 1);
     cluster.sync();
 
     for (int n = a.n_hi - 1; n >= a.n_lo; --n) {
@@ -254,24 +276,19 @@ __global__ void __launch_bounds__(kThreads, 1) rank2_adjoint_kernel(const AdjArg
         }
         const T* dfn = dfT + (done % kAdjTab) * Wa;
         // residual r^{n+1} = C V^{n+1} - ystar^{n+1} of this block's columns
-        const int rec = n + 1 - a.rec_base;  // trace record holding C V^{n+1}
-        for (int idx = tid; idx < R * Wa; idx += kThreads) {
-            const int jr = idx / Wa, c = idx % Wa;
-            T rv = T(0);
-            if (c < ncol) {
-                const size_t o = ((size_t)rec * a.M + col0 + c) * R + jr;
-                const size_t oy = ((size_t)n * a.M + col0 + c) * R + jr;  // ystar record of V^{n+1}
-                rv = a.traces[o] - a.ystar[oy];
-            }
-            rbuf[idx] = rv;
-        }
+        // (zero past ncol), from the copies issued one step earlier; then the
+        // next step's copies start
+        cp_async_wait_all();
         __syncthreads();
+        for (int idx = tid; idx < R * Wa; idx += kThreads) rbuf[idx] = trS[idx] - ysS[idx];
+        __syncthreads();
+        if (n > a.n_lo) prefetch_residual(n - 1);
         // ---- half A: lamV <- lamV + 2 C^T r^{n+1} + dt Asv^T lamS
         for (int rt = 0; rt < nrt_own; ++rt) {
             const int rowt = row0 + rt * kRowsPerCta;
             if constexpr (GEN) {
-                wl_load_op<KQ>(opQ, a.opA_rm, Kp, rowt + 4 * warp, lane);
-                wl_adj_half_a<KQ>(opQ, Sf, Vf, cV + rt * Wa * kRowsPerCta, Ccol + rt * kRowsPerCta, OWN,
+                if (!RES) wl_load_op<KQ>(opQA, a.opA_rm, Kp, rowt + 4 * warp, lane);
+                wl_adj_half_a<KQ>(opQA, Sf, Vf, cV + rt * Wa * kRowsPerCta, Ccol + rt * kRowsPerCta, OWN,
                                   rbuf, R, dt, Wa, Kp, rowt, warp, lane);
             } else {
                 if (!RES) load_op_rows<T, KI>(opA, a.opA_rm, Kp, rowt + 2 * rp, j);
@@ -296,8 +313,8 @@ __global__ void __launch_bounds__(kThreads, 1) rank2_adjoint_kernel(const AdjArg
         for (int rt = 0; rt < nrt_own; ++rt) {
             const int rowt = row0 + rt * kRowsPerCta;
             if constexpr (GEN) {
-                wl_load_op<KQ>(opQ, a.opB_rm, Kp, rowt + 4 * warp, lane);
-                wl_half_step<KQ, false>(opQ, Vf, Sf, cS + rt * Wa * kRowsPerCta, gown, gown, dt, Wa, Kp, rowt,
+                if (!RES) wl_load_op<KQ>(opQB, a.opB_rm, Kp, rowt + 4 * warp, lane);
+                wl_half_step<KQ, false>(opQB, Vf, Sf, cS + rt * Wa * kRowsPerCta, gown, gown, dt, Wa, Kp, rowt,
                                         warp, lane);
             } else {
                 if (!RES) load_op_rows<T, KI>(opB, a.opB_rm, Kp, rowt + 2 * rp, j);

@@ -197,15 +197,6 @@ __device__ __forceinline__ unsigned colmax8(unsigned (&v)[8], int lane, int& col
     return v[0];
 }
 
-// 4-byte asynchronous global -> shared copy (zero fill when src_bytes is 0),
-// and the wait for all of this thread's outstanding ones.
-__device__ __forceinline__ void cp_async4(void* sdst, const void* gsrc, int src_bytes) {
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;"
-                 ::"r"(cvta_shared(sdst)), "l"(gsrc), "r"(src_bytes) : "memory");
-}
-__device__ __forceinline__ void cp_async_wait_all() {
-    asm volatile("cp.async.wait_all;" ::: "memory");
-}
 
 // Shared memory for the reduced reference state of one half-step: WH values
 // per reader thread, [WH][256] so that a warp's accesses are consecutive.
