@@ -110,6 +110,29 @@ def test_batched_worklist_edge_cases(rom, form):
             assert colmax_rel(trg, np.asarray(tro).reshape(-1, p.M)) <= 1e-4
 
 
+@pytest.mark.parametrize("form", [None, (0, 0)])
+def test_batched_nonfinite_job_flags_its_own_handle(rom, form):
+    """A job whose state holds a NaN ends non-finite and its handle reports
+    ROM_E_NONFINITE; the other jobs of the same launch (work list or one
+    launch per job) are untouched and meet the oracle."""
+    sizes = [(192, 24, 0), (640, 16, 0), (320, 40, 0)]
+    jobs, probs = make_jobs(rom, sizes, with_traces=0, seed0=500)
+    jobs[1][1][5, 3] = float("nan")
+    if form is not None:
+        rom.set_batched_form(jobs, *form)
+    N = 30
+    rom.run_batched(jobs, N, prec="fp32")
+    torch.cuda.synchronize()
+    for k, ((h, V, S, T, _), p) in enumerate(zip(jobs, probs)):
+        if k == 1:
+            assert h.sync_status() == rom.ROM_E_NONFINITE
+            continue
+        assert h.sync_status() == 0
+        Z = np.zeros((p.Kv, p.M))
+        Vo, So, _ = oracle.forward(p.Avs, p.Asv, p.g, None, p.dt, Z, Z, N, T=p.T)
+        assert colmax_rel(V.cpu().numpy(), Vo) <= 1e-4 and colmax_rel(S.cpu().numpy(), So) <= 1e-4
+
+
 def test_batched_graph_replay(rom):
     """The second call replays the cached graph: the state advances by
     another nsteps (forcing restarts at t = 0 for every call)."""
