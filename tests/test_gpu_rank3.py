@@ -14,6 +14,14 @@ pytestmark = pytest.mark.gpu
 TOL = {"fp64": 1e-12, "fp32": 1e-4}
 
 
+def colmax_rel(a, b):
+    """Largest per-column relative L2 error (columns are realizations)."""
+    a = np.asarray(a, np.float64)
+    b = np.asarray(b, np.float64)
+    num = np.linalg.norm(a - b, axis=0)
+    return float(np.max(num / np.maximum(np.linalg.norm(b, axis=0), 1e-300)))
+
+
 def rel(a, b):
     a = np.asarray(a, np.float64)
     b = np.asarray(b, np.float64)
@@ -56,6 +64,9 @@ def rank3_run(rom, probs, V0, S0, N, prec, r):
     ("fp32", 3, 512, 512, 40, 200),   # split kernel, one wave
     ("fp32", 9, 512, 448, 8, 120),    # more operators than co-resident clusters
     ("fp32", 2, 640, 600, 24, 100),   # one-block kernel (K > 512)
+    # enough columns for the planner to take clusters of 4 (22 row tiles
+    # dealt 6, 6, 5, 5), 32 clusters per operator in two waves
+    ("fp32", 2, 704, 680, 256, 40),
     ("fp64", 4, 192, 160, 10, 200),   # FP64 one-block kernel
     ("fp32", 1, 256, 256, 10, 100),   # one operator: the rank-2 run
 ])
@@ -70,8 +81,9 @@ def test_rank3_vs_oracle(rom, prec, nops, Kv, Ks, M, N):
         sl = slice(i * M, (i + 1) * M)
         Vo, So, tro = oracle.forward(p.Avs, p.Asv, p.g, p.C, p.dt, V0[:, sl], S0[:, sl], N,
                                      T=p.T, r=r)
-        assert rel(V[:, sl], Vo) <= tol and rel(S[:, sl], So) <= tol, i
-        assert rel(tr[:, sl, :].transpose(0, 2, 1), tro) <= tol, i
+        assert colmax_rel(V[:, sl], Vo) <= tol and colmax_rel(S[:, sl], So) <= tol, i
+        trg = tr[:, sl, :].transpose(0, 2, 1)  # records x receivers x columns
+        assert colmax_rel(trg.reshape(-1, M), np.asarray(tro).reshape(-1, M)) <= tol, i
 
 
 @pytest.mark.parametrize("prec,kernel", [("fp32", 2), ("fp64", 0)])
