@@ -17,11 +17,16 @@ def rel(a, b):
 
 
 def colmax_rel(a, b):
-    """Largest per-column relative L2 error (columns are realizations)."""
+    """Largest per-realization relative L2 error (Eq. (errors), Sec. 4.4):
+    the last axis indexes the realizations (columns), every other axis is
+    one realization's values.  One bad column cannot hide among good ones."""
     a = np.asarray(a, np.float64)
     b = np.asarray(b, np.float64)
+    a = a.reshape(-1, a.shape[-1])
+    b = b.reshape(-1, b.shape[-1])
     num = np.linalg.norm(a - b, axis=0)
-    return float(np.max(num / np.maximum(np.linalg.norm(b, axis=0), 1e-300)))
+    den = np.maximum(np.linalg.norm(b, axis=0), 1e-300)
+    return float(np.max(num / den))
 
 
 @pytest.fixture(scope="module")
@@ -71,7 +76,7 @@ def test_adjoint_vs_oracle(rom, Kv, Ks, M, R, N, ckpt):
     loss, gV, gS, gT = gpu_adjoint(rom, h, p, V0, S0, ystar, N, ckpt)
     Lo, gVo, gSo, gTo = oracle.adjoint(p.Avs, p.Asv, p.g, p.C, p.dt, V0, S0, p.T, N, ystar)
     assert abs(loss - Lo) <= 1e-4 * abs(Lo)
-    assert rel(gV, gVo) <= 1e-4 and rel(gS, gSo) <= 1e-4 and rel(gT, gTo) <= 1e-4
+    assert colmax_rel(gV, gVo) <= 1e-4 and colmax_rel(gS, gSo) <= 1e-4 and rel(gT, gTo) <= 1e-4
 
 
 def test_checkpointed_equals_stored_traces_bitwise(rom):

@@ -29,14 +29,16 @@ TOL = {"tf32x3": 1e-4, "bf16x3": 1e-3, "bf16": 5e-2, "bf16s": 1e-5}
 
 
 def colmax_rel(a, b):
-    """Largest per-realization relative L2 error: the last axis indexes the
-    realizations, every other axis is one realization's values."""
+    """Largest per-realization relative L2 error (Eq. (errors), Sec. 4.4):
+    the last axis indexes the realizations (columns), every other axis is
+    one realization's values.  One bad column cannot hide among good ones."""
     a = np.asarray(a, np.float64)
     b = np.asarray(b, np.float64)
     a = a.reshape(-1, a.shape[-1])
     b = b.reshape(-1, b.shape[-1])
     num = np.linalg.norm(a - b, axis=0)
-    return float(np.max(num / np.maximum(np.linalg.norm(b, axis=0), 1e-300)))
+    den = np.maximum(np.linalg.norm(b, axis=0), 1e-300)
+    return float(np.max(num / den))
 
 
 def rel(a, b):
@@ -134,7 +136,7 @@ def test_tc_k1024_tf32x3(rom, cols):
     Z = np.zeros((1024, 96))
     V, S, tr = run_tc(rom, h, p, Z, Z, 120, "tf32x3", r=10)
     Vo, So, tro = oracle.forward(p.Avs, p.Asv, p.g, p.C, p.dt, Z, Z, 120, T=p.T, r=10)
-    assert rel(V, Vo) <= 1e-4 and rel(S, So) <= 1e-4 and rel(tr, tro) <= 1e-4
+    assert colmax_rel(V, Vo) <= 1e-4 and colmax_rel(S, So) <= 1e-4 and colmax_rel(tr, tro) <= 1e-4
 
 
 def test_tc_zero_in_zero_out(rom):

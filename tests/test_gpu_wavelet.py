@@ -22,6 +22,19 @@ def rom():
     return R
 
 
+def colmax_rel(a, b):
+    """Largest per-realization relative L2 error (Eq. (errors), Sec. 4.4):
+    the last axis indexes the realizations (columns), every other axis is
+    one realization's values.  One bad column cannot hide among good ones."""
+    a = np.asarray(a, np.float64)
+    b = np.asarray(b, np.float64)
+    a = a.reshape(-1, a.shape[-1])
+    b = b.reshape(-1, b.shape[-1])
+    num = np.linalg.norm(a - b, axis=0)
+    den = np.maximum(np.linalg.norm(b, axis=0), 1e-300)
+    return float(np.max(num / den))
+
+
 def rel(a, b):
     a = np.asarray(a, np.float64)
     b = np.asarray(b, np.float64)
@@ -73,7 +86,7 @@ def test_gaussian_source_rank1(rom):
     h.run_rank1_ensemble(Ve, Se, torch.as_tensor(p.T, device="cuda"), N, prec="fp32")
     torch.cuda.synchronize()
     assert rel(v.cpu().numpy(), Vo[:, 2]) <= 1e-4
-    assert rel(Ve.cpu().numpy(), Vo) <= 1e-4 and rel(Se.cpu().numpy(), So) <= 1e-4
+    assert colmax_rel(Ve.cpu().numpy(), Vo) <= 1e-4 and colmax_rel(Se.cpu().numpy(), So) <= 1e-4
 
 
 def test_gaussian_source_adjoint_period_gradient(rom):

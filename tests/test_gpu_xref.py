@@ -15,6 +15,19 @@ pytestmark = pytest.mark.gpu
 TOL = {"fp64": 1e-12, "fp32": 1e-4, "bf16s": 1e-4, "tf32x3": 1e-4}
 
 
+def colmax_rel(a, b):
+    """Largest per-realization relative L2 error (Eq. (errors), Sec. 4.4):
+    the last axis indexes the realizations (columns), every other axis is
+    one realization's values.  One bad column cannot hide among good ones."""
+    a = np.asarray(a, np.float64)
+    b = np.asarray(b, np.float64)
+    a = a.reshape(-1, a.shape[-1])
+    b = b.reshape(-1, b.shape[-1])
+    num = np.linalg.norm(a - b, axis=0)
+    den = np.maximum(np.linalg.norm(b, axis=0), 1e-300)
+    return float(np.max(num / den))
+
+
 def rel(a, b):
     a = np.asarray(a, np.float64)
     b = np.asarray(b, np.float64)
@@ -78,7 +91,7 @@ def test_reference_state_vs_oracle(rom, prec, kernel, Kv, Ks, M, N):
     Vo, So, tro = oracle.forward(p.Avs, p.Asv, p.g, p.C, p.dt, V0, S0, N, T=p.T, r=r,
                                  xref=(Xv, Xs))
     tol = TOL[prec]
-    assert rel(V, Vo) <= tol and rel(S, So) <= tol and rel(tr, tro) <= tol
+    assert colmax_rel(V, Vo) <= tol and colmax_rel(S, So) <= tol and colmax_rel(tr, tro) <= tol
     # the term is not negligible in this case
     Vn, _, _ = oracle.forward(p.Avs, p.Asv, p.g, p.C, p.dt, V0, S0, N, T=p.T)
     assert rel(Vn, Vo) > 100 * tol
@@ -109,7 +122,7 @@ def test_reference_state_one_part_and_clear(rom):
     h.set_reference(None, Xs)
     V, S, _ = run(rom, h, p, V0, S0, N, "fp32")
     Vo, So, _ = oracle.forward(p.Avs, p.Asv, p.g, None, p.dt, V0, S0, N, T=p.T, xref=(None, Xs))
-    assert rel(V, Vo) <= 1e-4 and rel(S, So) <= 1e-4
+    assert colmax_rel(V, Vo) <= 1e-4 and colmax_rel(S, So) <= 1e-4
     h.set_reference(None, None)
     V1, S1, _ = run(rom, h, p, V0, S0, N, "fp32")
     h2 = rom.Rom.from_problem(p)
@@ -143,7 +156,7 @@ def test_reference_state_rank1_paths(rom, prec):
     h.run_rank1_ensemble(V, S, T, N, prec=prec)
     assert h.sync_status() == rom.ROM_OK
     tol = TOL[prec]
-    assert rel(V.cpu().numpy(), Vo) <= tol and rel(S.cpu().numpy(), So) <= tol
+    assert colmax_rel(V.cpu().numpy(), Vo) <= tol and colmax_rel(S.cpu().numpy(), So) <= tol
     m = 4
     h1 = rom.Rom.from_problem(p)
     h1.set_reference(Xv[:, m:m + 1], Xs[:, m:m + 1])
