@@ -31,7 +31,22 @@ static void* adjoint_kernel_f64(int KI) {
 #undef ROM_ADJ_CASE
 }
 
-static void* adjoint_kernel(const AdjPlan& p) { return p.f64 ? adjoint_kernel_f64(p.KI) : adjoint_kernel_f32(p.KI); }
+// The split-role reverse kernel (FP32, Kp <= 512).
+static void* adjoint_split_kernel(int KI) {
+#define ROM_ADJ_CASE(k) \
+    case k: return (void*)&rank2_adjoint_split_kernel<k>;
+    switch (KI) {
+        ROM_ADJ_CASE(1) ROM_ADJ_CASE(2) ROM_ADJ_CASE(3) ROM_ADJ_CASE(4)
+        ROM_ADJ_CASE(5) ROM_ADJ_CASE(6) ROM_ADJ_CASE(7) ROM_ADJ_CASE(8)
+        default: return nullptr;
+    }
+#undef ROM_ADJ_CASE
+}
+
+static void* adjoint_kernel(const AdjPlan& p) {
+    if (p.split) return adjoint_split_kernel(p.KI);
+    return p.f64 ? adjoint_kernel_f64(p.KI) : adjoint_kernel_f32(p.KI);
+}
 
 static size_t adjoint_smem(bool f64, int W, int Kp, int R, int nrt) {
     return f64 ? adj_smem_layout<double>(W, Kp, R, nrt).total : adj_smem_layout<float>(W, Kp, R, nrt).total;
@@ -41,6 +56,7 @@ static size_t adjoint_smem(bool f64, int W, int Kp, int R, int nrt) {
 // Kp = 512, Kp / 64 of two above).  Widths are multiples of 8.
 static bool plan_adjoint_cs(int Kp, int M, int R, AdjPlan* p, bool f64, int cs) {
     p->f64 = f64;
+    p->split = false;
     p->KI = Kp / 64;
     if (cs == 0) {
         p->nrt = Kp > 512 ? 2 : 1;
@@ -77,13 +93,50 @@ static bool plan_adjoint_cs(int Kp, int M, int R, AdjPlan* p, bool f64, int cs) 
     return true;
 }
 
-// FP32, Kp <= 512: one 32-row tile per CTA (Kp / 32 CTAs, operators in
-// registers).  FP32 above: the operators are read from L2 and the row tiles
-// dealt out to any cluster size, so Kp / 64 CTAs (7 co-resident), 4 (36) and
-// 2 (76) are priced with the step-time model and the fastest kept.  FP64:
-// Kp <= 512, one tile per CTA.
+// The split-role plan (FP32, Kp <= 512): Kp / 32 CTAs, Wv columns per block
+// (a multiple of 4), two blocks per cluster, spread over the co-resident
+// clusters.
+static bool plan_adjoint_split(int Kp, int M, int R, AdjPlan* p) {
+    p->f64 = false;
+    p->split = true;
+    p->KI = Kp / 64;
+    p->cs = Kp / 32;
+    p->nrt = 1;
+    p->cb = kSplitCB;
+    const int smax = device_smem_optin();
+    int wcap = 0;
+    for (int w = kSplitCB; w <= 2048; w += kSplitCB) {
+        if (adj_split_smem_layout(w, Kp, R).total > (size_t)smax) break;
+        wcap = w;
+    }
+    if (wcap == 0) return false;
+    void* fn = adjoint_split_kernel(p->KI);
+    if (!fn) return false;
+    const size_t smem_probe = adj_split_smem_layout(wcap, Kp, R).total;
+    if (prepare_kernel<float>(fn, smem_probe) != cudaSuccess) return false;
+    ClusterLaunch probe(p->cs, 1, kThreads, smem_probe);
+    const int nact = probe.max_active(fn);
+    if (nact <= 0) return false;
+    int wv = (M + 2 * nact - 1) / (2 * nact);
+    wv = ((wv + kSplitCB - 1) / kSplitCB) * kSplitCB;
+    if (wv > wcap) wv = wcap;
+    p->Wv = wv;
+    p->Wa = wv;
+    p->nclusters = ((M + wv - 1) / wv + 1) / 2;
+    p->smem = adj_split_smem_layout(wv, Kp, R).total;
+    p->model_us = 0.0;
+    return true;
+}
+
+// FP32, Kp <= 512: the split-role kernel (both roles busy in every phase),
+// else one 32-row tile per CTA (Kp / 32 CTAs, operators in registers).
+// FP32 above: the operators are read from L2 and the row tiles dealt out to
+// any cluster size, so Kp / 64 CTAs (7 co-resident), 4 (36) and 2 (76) are
+// priced with the step-time model and the fastest kept.  FP64: Kp <= 512,
+// one tile per CTA.
 bool plan_adjoint(int Kp, int M, int R, AdjPlan* p, bool f64) {
     if (Kp <= 0 || Kp % 64 != 0 || Kp > (f64 ? 512 : 1024) || M <= 0 || R <= 0) return false;
+    if (!f64 && Kp <= 512 && plan_adjoint_split(Kp, M, R, p)) return true;
     if (!plan_adjoint_cs(Kp, M, R, p, f64, 0)) return false;
     if (f64 || Kp <= 512) return true;
     for (int cs : {4, 2}) {

@@ -28,6 +28,7 @@
 
 #include "dev_common.cuh"
 #include "rank2_simt.cuh"
+#include "rank2_split.cuh"
 #include "rom_internal.h"
 
 namespace romk {
@@ -345,6 +346,198 @@ __global__ void __launch_bounds__(kThreads, 1) rank2_adjoint_kernel(const AdjArg
         }
     }
     for (int c = tid; c < ncol; c += kThreads) a.gTpart[(size_t)crank * a.M + col0 + c] = gTacc[c];
+    bad = __syncthreads_or(bad);
+    if (bad && tid == 0 && a.status) atomicCAS(a.status, 0, 6 /* ROM_E_NONFINITE */);
+}
+
+// ---- split-role reverse kernel (FP32, Kp <= 512).  The reverse step has
+// the forward step's shape: half A updates lamV from lamS, half B updates
+// lamS from the new lamV.  So the forward split kernel's schedule
+// (rank2_split.cuh) carries over: two column blocks half a step apart,
+// V-role CTAs holding their 64 rows of Asv^T in registers and owning those
+// rows of lamV, S-role CTAs doing the same with Avs^T and lamS, each finished
+// tile pushed into the other role's operand copy, one cluster barrier per
+// phase.  Time runs backwards: block A takes reverse step n = n_hi - 1 - k in
+// phase 2k, block B in phase 2k + 1.  The V role's epilogue adds 2 C^T r
+// (its C columns and the block's residual in shared memory; the residual's
+// inputs are copied one phase ahead).  After each of its phases it adds its
+// own rows' share of the period gradient to a per-CTA partial.
+struct AdjSplitSmem {
+    size_t X, own, comp, Ccol, rbuf, trS, ysS, g, T, gT, dfT, total;
+};
+
+__host__ __device__ inline AdjSplitSmem adj_split_smem_layout(int Wa, int Kp, int R) {
+    AdjSplitSmem s{};
+    size_t o = 0;
+    s.X = o;    o += align16((size_t)2 * Wa * Kp * sizeof(float));
+    s.own = o;  o += align16((size_t)2 * Wa * kOwnStride * sizeof(float));
+    s.comp = o; o += align16((size_t)2 * Wa * kOwnStride * sizeof(float));
+    s.Ccol = o; o += align16((size_t)R * kSplitRows * sizeof(float));
+    s.rbuf = o; o += align16((size_t)R * Wa * sizeof(float));
+    s.trS = o;  o += align16((size_t)R * Wa * sizeof(float));
+    s.ysS = o;  o += align16((size_t)R * Wa * sizeof(float));
+    s.g = o;    o += align16((size_t)kSplitRows * sizeof(float));
+    s.T = o;    o += align16((size_t)2 * Wa * sizeof(float));
+    s.gT = o;   o += align16((size_t)2 * Wa * sizeof(float));
+    s.dfT = o;  o += align16((size_t)2 * kAdjTab * Wa * sizeof(float));
+    s.total = o;
+    return s;
+}
+
+template <int KI>
+__global__ void __launch_bounds__(kThreads, 1) rank2_adjoint_split_kernel(const AdjArgsT<float> a) {
+    cg::cluster_group cluster = cg::this_cluster();
+    const int cs = (int)cluster.num_blocks();
+    const int H = cs / 2;
+    const int crank = (int)cluster.block_rank();
+    const bool vrole = crank < H;
+    const int sl = vrole ? crank : crank - H;  // row slab
+    const int row0 = sl * kSplitRows;
+    const int peer0 = vrole ? H : 0;           // first CTA of the other role
+    const int clu = blockIdx.x / cs;
+    const int Wa = a.Wa, Kp = a.Kp, R = a.R, M = a.M;
+    const int gc0_0 = 2 * clu * a.Wv, gc0_1 = gc0_0 + a.Wv;
+    const int nc0 = max(0, min(a.Wv, M - gc0_0)), nc1 = max(0, min(a.Wv, M - gc0_1));
+    auto gc0 = [&](int b) { return b ? gc0_1 : gc0_0; };
+    auto ncol = [&](int b) { return b ? nc1 : nc0; };
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int j = lane & 15;
+    const int q = warp * 2 + (lane >> 4);      // row quad
+    const float dt = (float)a.dt;
+
+    extern __shared__ __align__(16) unsigned char smem[];
+    const AdjSplitSmem L = adj_split_smem_layout(Wa, Kp, R);
+    float* X = reinterpret_cast<float*>(smem + L.X);         // [2][Wa][Kp] operand copies
+    float* own = reinterpret_cast<float*>(smem + L.own);     // [2][Wa][72] owned rows
+    float* comp = reinterpret_cast<float*>(smem + L.comp);   // [2][Wa][72] Kahan carries
+    float* Ccol = reinterpret_cast<float*>(smem + L.Ccol);   // [R][64]: C[jr][row0 + rl]
+    float* rbuf = reinterpret_cast<float*>(smem + L.rbuf);   // [R][Wa] residual of the phase's block
+    float* trS = reinterpret_cast<float*>(smem + L.trS);     // [R][Wa] next phase's records
+    float* ysS = reinterpret_cast<float*>(smem + L.ysS);     // [R][Wa] and targets
+    float* gown = reinterpret_cast<float*>(smem + L.g);      // [64]
+    float* Tcol = reinterpret_cast<float*>(smem + L.T);      // [2][Wa]
+    float* gTacc = reinterpret_cast<float*>(smem + L.gT);    // [2][Wa] period-gradient partials
+    float* dfT = reinterpret_cast<float*>(smem + L.dfT);     // [2][kAdjTab][Wa] df/dT per block
+
+    const int Kown = vrole ? a.Kv : a.Ks;
+    const float* own_in = vrole ? a.lamV : a.lamS;
+    const float* comp_in = vrole ? a.compV : a.compS;
+    // operand copies: V role = the full lamS of each block; the S role's are
+    // filled by the first V-role pushes
+    for (int idx = tid; idx < 2 * Wa * Kp; idx += kThreads) {
+        const int b = idx / (Wa * Kp);
+        const int rem = idx - b * Wa * Kp;
+        const int c = rem / Kp, k = rem - (rem / Kp) * Kp;
+        X[idx] = (vrole && c < ncol(b) && k < a.Ks) ? a.lamS[(size_t)(gc0(b) + c) * a.Ks + k] : 0.f;
+    }
+    for (int idx = tid; idx < 2 * Wa * kOwnStride; idx += kThreads) {
+        const int b = idx / (Wa * kOwnStride);
+        const int rem = idx - b * Wa * kOwnStride;
+        const int c = rem / kOwnStride, rl = rem % kOwnStride, row = row0 + rl;
+        const bool ok = rl < kSplitRows && c < ncol(b) && row < Kown;
+        own[idx] = ok ? own_in[(size_t)(gc0(b) + c) * Kown + row] : 0.f;
+        comp[idx] = ok ? comp_in[(size_t)(gc0(b) + c) * Kown + row] : 0.f;
+    }
+    for (int idx = tid; idx < (vrole ? R * kSplitRows : 0); idx += kThreads) {
+        const int jr = idx / kSplitRows, rl = idx % kSplitRows;
+        Ccol[idx] = a.C_rm[(size_t)jr * Kp + row0 + rl];
+    }
+    if (tid < kSplitRows) gown[tid] = vrole ? a.g_p[row0 + tid] : 0.f;
+    for (int idx = tid; idx < 2 * Wa; idx += kThreads) {
+        const int b = idx / Wa, c = idx % Wa;
+        const bool ok = c < ncol(b);
+        Tcol[idx] = ok ? a.Tper[gc0(b) + c] : 1.f;
+        gTacc[idx] = ok ? a.gTpart[(size_t)crank * M + gc0(b) + c] : 0.f;
+    }
+    float op[4][4 * KI];
+    load_op_quad<KI>(op, vrole ? a.opA_rm : a.opB_rm, Kp, row0 + 4 * q, j);
+
+    // the trace records C V^{n+1} and targets y*^{n+1} of block b, reverse step n
+    auto prefetch_residual = [&](int b, int n) {
+        const int rec = n + 1 - a.rec_base;
+        for (int idx = tid; idx < R * Wa; idx += kThreads) {
+            const int jr = idx / Wa, c = idx % Wa;
+            const bool ok = c < ncol(b);
+            const int cc = ok ? c : 0;  // a valid address for the zero fill
+            cp_async4(trS + idx, a.traces + ((size_t)rec * M + gc0(b) + cc) * R + jr, ok ? 4 : 0);
+            cp_async4(ysS + idx, a.ystar + ((size_t)n * M + gc0(b) + cc) * R + jr, ok ? 4 : 0);
+        }
+    };
+    const int NR = a.n_hi - a.n_lo;  // reverse steps of this segment
+    if (vrole && NR > 0 && ncol(0) > 0) prefetch_residual(0, a.n_hi - 1);
+    // every CTA's copies must be initialised before any peer pushes into them
+    cluster.sync();
+
+    const int nphase = 2 * NR + 1;
+    for (int p = 0; p < nphase; ++p) {
+        int b, k;
+        if (vrole) { b = p & 1; k = (p - b) >> 1; }
+        else { b = (p & 1) ^ 1; k = (p - 1 - b) >> 1; }
+        const bool work = k >= 0 && k < NR && ncol(b) > 0;
+        const int n = a.n_hi - 1 - k;
+        float* Xb = X + (size_t)b * Wa * Kp;
+        float* ownb = own + (size_t)b * Wa * kOwnStride;
+        float* compb = comp + (size_t)b * Wa * kOwnStride;
+        if (vrole) {
+            // this phase's residual (copied during the previous phase), the
+            // block's df/dT table every kAdjTab of its steps, then the next
+            // phase's copies
+            cp_async_wait_all();
+            __syncthreads();
+            if (work) {
+                for (int idx = tid; idx < R * Wa; idx += kThreads) rbuf[idx] = trS[idx] - ysS[idx];
+                if (k % kAdjTab == 0) {
+                    for (int idx = tid; idx < kAdjTab * ncol(b); idx += kThreads) {
+                        const int i = idx / ncol(b), c = idx % ncol(b);
+                        if (n - i >= a.n_lo)
+                            dfT[(b * kAdjTab + i) * Wa + c] =
+                                wavelet_dT_eval<float>(a.wavelet, (long long)a.n0 + n - i, a.dt, Tcol[b * Wa + c]);
+                    }
+                }
+            }
+            __syncthreads();
+            const int b2 = (p + 1) & 1, k2 = (p + 1 - b2) >> 1;
+            if (k2 < NR && ncol(b2) > 0) prefetch_residual(b2, a.n_hi - 1 - k2);
+            if (work) {
+                // half A: lamV <- lamV + dt Asv^T lamS + 2 C^T r^{n+1}
+                split_phase<KI, false, false, true>(cluster, op, Xb, ownb, compb, gown, gown, Xb, dt, Wa, Kp,
+                                                    row0, H, peer0, q, j, warp, lane, nullptr, Kown, ncol(b),
+                                                    Ccol, kSplitRows, rbuf, R);
+                __syncthreads();
+                // period gradient: dt (g_own . a_V[:, c]) df/dT(t_n; T_c), fixed order
+                const float* dfn = dfT + (b * kAdjTab + (k % kAdjTab)) * Wa;
+                for (int c = warp; c < ncol(b); c += kSplitWarps) {
+                    float sg = gown[lane] * ownb[c * kOwnStride + lane];
+                    sg = __fmaf_rn(gown[lane + 32], ownb[c * kOwnStride + lane + 32], sg);
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) sg += __shfl_xor_sync(0xffffffffu, sg, o);
+                    if (lane == 0) gTacc[b * Wa + c] = __fmaf_rn(dt * sg, dfn[c], gTacc[b * Wa + c]);
+                }
+            }
+        } else if (work) {
+            // half B: lamS <- lamS + dt Avs^T lamV (the new lamV of block b)
+            split_phase<KI, false, false>(cluster, op, Xb, ownb, compb, gown, gown, Xb, dt, Wa, Kp, row0, H,
+                                          peer0, q, j, warp, lane, nullptr, Kown, ncol(b));
+        }
+        cluster.sync();
+    }
+
+    // ---- write back the owned rows, carries and the period-gradient partials
+    float* out = vrole ? a.lamV : a.lamS;
+    float* cout_ = vrole ? a.compV : a.compS;
+    int bad = 0;
+    for (int b = 0; b < 2; ++b) {
+        for (int idx = tid; idx < ncol(b) * kSplitRows; idx += kThreads) {
+            const int c = idx / kSplitRows, rl = idx % kSplitRows, row = row0 + rl;
+            if (row < Kown) {
+                const float x = own[(size_t)b * Wa * kOwnStride + c * kOwnStride + rl];
+                out[(size_t)(gc0(b) + c) * Kown + row] = x;
+                cout_[(size_t)(gc0(b) + c) * Kown + row] = comp[(size_t)b * Wa * kOwnStride + c * kOwnStride + rl];
+                bad |= !is_finite(x);
+            }
+        }
+        for (int c = tid; c < ncol(b); c += kThreads) a.gTpart[(size_t)crank * M + gc0(b) + c] = gTacc[b * Wa + c];
+    }
     bad = __syncthreads_or(bad);
     if (bad && tid == 0 && a.status) atomicCAS(a.status, 0, 6 /* ROM_E_NONFINITE */);
 }

@@ -83,8 +83,10 @@ __device__ __forceinline__ void load_op_quad(float (&op)[4][4 * KI], const float
 // With XR, Xref points at block b's first column of the role's reduced
 // reference state (Krows x columns); each lane fetches its epilogue's value
 // before the products.  XR is a template flag so that runs without the term
-// compile to exactly the code they had without it.
-template <int KI, bool FORCED, bool XR>
+// compile to exactly the code they had without it.  ADJ (the reverse-time
+// adjoint's half A): own rows += dt (op . X_b) + 2 C_own^T r, with Ccol the
+// CTA's C columns ([R][cstride]) and rbuf block b's residual ([R][Wa]).
+template <int KI, bool FORCED, bool XR, bool ADJ = false>
 __device__ __forceinline__ void split_phase(cg::cluster_group& cluster, const float (&op)[4][4 * KI],
                                             const float* __restrict__ X, float* __restrict__ own,
                                             float* __restrict__ comp, const float* __restrict__ gown,
@@ -93,7 +95,9 @@ __device__ __forceinline__ void split_phase(cg::cluster_group& cluster, const fl
                                             const int row0, const int H, const int peer0,
                                             const int q, const int j, const int warp,
                                             const int lane, const float* __restrict__ Xref,
-                                            const int Krows, const int ncol) {
+                                            const int Krows, const int ncol,
+                                            const float* __restrict__ Ccol = nullptr, const int cstride = 0,
+                                            const float* __restrict__ rbuf = nullptr, const int R = 0) {
     constexpr int CB = kSplitCB;
     for (int c0 = 0; c0 < Wa; c0 += CB) {
         float xr = 0.f;
@@ -133,9 +137,23 @@ __device__ __forceinline__ void split_phase(cg::cluster_group& cluster, const fl
             const int rl = 4 * q + vi / CB;
             const int c = c0 + vi % CB;
             float inc = tot;
-            if (FORCED) inc = __fmaf_rn(gown[rl], fcol[c], inc);
-            if constexpr (XR) inc = inc + xr;
-            inc = inc * dt;
+            if constexpr (ADJ) {
+                // four independent chains (receivers jr = 4 u + e), summed in a fixed order
+                float s4[4] = {0.f, 0.f, 0.f, 0.f};
+                int jr = 0;
+                for (; jr + 4 <= R; jr += 4) {
+#pragma unroll
+                    for (int e = 0; e < 4; ++e)
+                        s4[e] = __fmaf_rn(Ccol[(jr + e) * cstride + rl], rbuf[(jr + e) * Wa + c], s4[e]);
+                }
+                for (; jr < R; ++jr) s4[0] = __fmaf_rn(Ccol[jr * cstride + rl], rbuf[jr * Wa + c], s4[0]);
+                const float src = (s4[0] + s4[1]) + (s4[2] + s4[3]);
+                inc = __fmaf_rn(tot, dt, 2.f * src);
+            } else {
+                if (FORCED) inc = __fmaf_rn(gown[rl], fcol[c], inc);
+                if constexpr (XR) inc = inc + xr;
+                inc = inc * dt;
+            }
             float* yp = own + c * kOwnStride + rl;
             *yp = kahan_add(*yp, inc, comp[c * kOwnStride + rl]);
         }

@@ -219,6 +219,7 @@ struct AdjPlan {
     size_t smem;
     bool f64;         // the FP64 instance (Kp <= 512)
     double model_us;  // modelled µs per reverse step (cluster-size choice)
+    bool split;       // the split-role kernel (FP32, Kp <= 512): Wv columns per block, two blocks per cluster
 };
 bool plan_adjoint(int Kp, int M, int R, AdjPlan* p, bool f64 = false);
 cudaError_t launch_adjoint(const AdjArgsT<float>& a, const AdjPlan& p, cudaStream_t st);
