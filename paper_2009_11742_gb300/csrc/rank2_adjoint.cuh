@@ -366,16 +366,26 @@ struct AdjSplitSmem {
     size_t X, own, comp, Ccol, rbuf, trS, ysS, g, T, gT, dfT, total;
 };
 
+// Row stride (floats) of the receiver-indexed buffers of the split reverse
+// kernel: R rounded up to a multiple of 4 (zero-padded), plus 4 when that is
+// an even number of 16-byte groups, so that the rows read by the eight lanes
+// of a quarter warp fall in distinct bank groups.
+__host__ __device__ inline int adj_rstride(int R) {
+    const int rp = (R + 3) / 4 * 4;
+    return (rp / 4) % 2 == 0 ? rp + 4 : rp;
+}
+
 __host__ __device__ inline AdjSplitSmem adj_split_smem_layout(int Wa, int Kp, int R) {
     AdjSplitSmem s{};
+    const int rs = adj_rstride(R);
     size_t o = 0;
     s.X = o;    o += align16((size_t)2 * Wa * Kp * sizeof(float));
     s.own = o;  o += align16((size_t)2 * Wa * kOwnStride * sizeof(float));
     s.comp = o; o += align16((size_t)2 * Wa * kOwnStride * sizeof(float));
-    s.Ccol = o; o += align16((size_t)R * kSplitRows * sizeof(float));
-    s.rbuf = o; o += align16((size_t)R * Wa * sizeof(float));
-    s.trS = o;  o += align16((size_t)R * Wa * sizeof(float));
-    s.ysS = o;  o += align16((size_t)R * Wa * sizeof(float));
+    s.Ccol = o; o += align16((size_t)kSplitRows * rs * sizeof(float));
+    s.rbuf = o; o += align16((size_t)Wa * rs * sizeof(float));
+    s.trS = o;  o += align16((size_t)Wa * rs * sizeof(float));
+    s.ysS = o;  o += align16((size_t)Wa * rs * sizeof(float));
     s.g = o;    o += align16((size_t)kSplitRows * sizeof(float));
     s.T = o;    o += align16((size_t)2 * Wa * sizeof(float));
     s.gT = o;   o += align16((size_t)2 * Wa * sizeof(float));
@@ -410,10 +420,12 @@ __global__ void __launch_bounds__(kThreads, 1) rank2_adjoint_split_kernel(const 
     float* X = reinterpret_cast<float*>(smem + L.X);         // [2][Wa][Kp] operand copies
     float* own = reinterpret_cast<float*>(smem + L.own);     // [2][Wa][72] owned rows
     float* comp = reinterpret_cast<float*>(smem + L.comp);   // [2][Wa][72] Kahan carries
-    float* Ccol = reinterpret_cast<float*>(smem + L.Ccol);   // [R][64]: C[jr][row0 + rl]
-    float* rbuf = reinterpret_cast<float*>(smem + L.rbuf);   // [R][Wa] residual of the phase's block
-    float* trS = reinterpret_cast<float*>(smem + L.trS);     // [R][Wa] next phase's records
-    float* ysS = reinterpret_cast<float*>(smem + L.ysS);     // [R][Wa] and targets
+    // receiver-indexed buffers, jr contiguous (stride rs, zero beyond R)
+    const int rs = adj_rstride(R);
+    float* Ccol = reinterpret_cast<float*>(smem + L.Ccol);   // [64][rs]: C[jr][row0 + rl]
+    float* rbuf = reinterpret_cast<float*>(smem + L.rbuf);   // [Wa][rs] residual of the phase's block
+    float* trS = reinterpret_cast<float*>(smem + L.trS);     // [Wa][rs] next phase's records
+    float* ysS = reinterpret_cast<float*>(smem + L.ysS);     // [Wa][rs] and targets
     float* gown = reinterpret_cast<float*>(smem + L.g);      // [64]
     float* Tcol = reinterpret_cast<float*>(smem + L.T);      // [2][Wa]
     float* gTacc = reinterpret_cast<float*>(smem + L.gT);    // [2][Wa] period-gradient partials
@@ -438,9 +450,9 @@ __global__ void __launch_bounds__(kThreads, 1) rank2_adjoint_split_kernel(const 
         own[idx] = ok ? own_in[(size_t)(gc0(b) + c) * Kown + row] : 0.f;
         comp[idx] = ok ? comp_in[(size_t)(gc0(b) + c) * Kown + row] : 0.f;
     }
-    for (int idx = tid; idx < (vrole ? R * kSplitRows : 0); idx += kThreads) {
-        const int jr = idx / kSplitRows, rl = idx % kSplitRows;
-        Ccol[idx] = a.C_rm[(size_t)jr * Kp + row0 + rl];
+    for (int idx = tid; idx < (vrole ? kSplitRows * rs : 0); idx += kThreads) {
+        const int rl = idx / rs, jr = idx % rs;
+        Ccol[idx] = jr < R ? a.C_rm[(size_t)jr * Kp + row0 + rl] : 0.f;
     }
     if (tid < kSplitRows) gown[tid] = vrole ? a.g_p[row0 + tid] : 0.f;
     for (int idx = tid; idx < 2 * Wa; idx += kThreads) {
@@ -455,12 +467,12 @@ __global__ void __launch_bounds__(kThreads, 1) rank2_adjoint_split_kernel(const 
     // the trace records C V^{n+1} and targets y*^{n+1} of block b, reverse step n
     auto prefetch_residual = [&](int b, int n) {
         const int rec = n + 1 - a.rec_base;
-        for (int idx = tid; idx < R * Wa; idx += kThreads) {
-            const int jr = idx / Wa, c = idx % Wa;
-            const bool ok = c < ncol(b);
-            const int cc = ok ? c : 0;  // a valid address for the zero fill
-            cp_async4(trS + idx, a.traces + ((size_t)rec * M + gc0(b) + cc) * R + jr, ok ? 4 : 0);
-            cp_async4(ysS + idx, a.ystar + ((size_t)n * M + gc0(b) + cc) * R + jr, ok ? 4 : 0);
+        for (int idx = tid; idx < Wa * rs; idx += kThreads) {
+            const int c = idx / rs, jr = idx % rs;
+            const bool ok = c < ncol(b) && jr < R;
+            const int cc = ok ? c : 0, jj = ok ? jr : 0;  // a valid address for the zero fill
+            cp_async4(trS + idx, a.traces + ((size_t)rec * M + gc0(b) + cc) * R + jj, ok ? 4 : 0);
+            cp_async4(ysS + idx, a.ystar + ((size_t)n * M + gc0(b) + cc) * R + jj, ok ? 4 : 0);
         }
     };
     const int NR = a.n_hi - a.n_lo;  // reverse steps of this segment
@@ -485,7 +497,7 @@ __global__ void __launch_bounds__(kThreads, 1) rank2_adjoint_split_kernel(const 
             cp_async_wait_all();
             __syncthreads();
             if (work) {
-                for (int idx = tid; idx < R * Wa; idx += kThreads) rbuf[idx] = trS[idx] - ysS[idx];
+                for (int idx = tid; idx < Wa * rs; idx += kThreads) rbuf[idx] = trS[idx] - ysS[idx];
                 if (k % kAdjTab == 0) {
                     for (int idx = tid; idx < kAdjTab * ncol(b); idx += kThreads) {
                         const int i = idx / ncol(b), c = idx % ncol(b);
@@ -502,7 +514,7 @@ __global__ void __launch_bounds__(kThreads, 1) rank2_adjoint_split_kernel(const 
                 // half A: lamV <- lamV + dt Asv^T lamS + 2 C^T r^{n+1}
                 split_phase<KI, false, false, true>(cluster, op, Xb, ownb, compb, gown, gown, Xb, dt, Wa, Kp,
                                                     row0, H, peer0, q, j, warp, lane, nullptr, Kown, ncol(b),
-                                                    Ccol, kSplitRows, rbuf, R);
+                                                    Ccol, rbuf, rs, (R + 3) / 4);
                 __syncthreads();
                 // period gradient: dt (g_own . a_V[:, c]) df/dT(t_n; T_c), fixed order
                 const float* dfn = dfT + (b * kAdjTab + (k % kAdjTab)) * Wa;

@@ -85,7 +85,8 @@ __device__ __forceinline__ void load_op_quad(float (&op)[4][4 * KI], const float
 // before the products.  XR is a template flag so that runs without the term
 // compile to exactly the code they had without it.  ADJ (the reverse-time
 // adjoint's half A): own rows += dt (op . X_b) + 2 C_own^T r, with Ccol the
-// CTA's C columns ([R][cstride]) and rbuf block b's residual ([R][Wa]).
+// CTA's C columns ([64 rows][rstride], receiver index contiguous) and rbuf
+// block b's residual ([Wa][rstride]), both zero from R up to 4 nr4.
 template <int KI, bool FORCED, bool XR, bool ADJ = false>
 __device__ __forceinline__ void split_phase(cg::cluster_group& cluster, const float (&op)[4][4 * KI],
                                             const float* __restrict__ X, float* __restrict__ own,
@@ -96,8 +97,9 @@ __device__ __forceinline__ void split_phase(cg::cluster_group& cluster, const fl
                                             const int q, const int j, const int warp,
                                             const int lane, const float* __restrict__ Xref,
                                             const int Krows, const int ncol,
-                                            const float* __restrict__ Ccol = nullptr, const int cstride = 0,
-                                            const float* __restrict__ rbuf = nullptr, const int R = 0) {
+                                            const float* __restrict__ Ccol = nullptr,
+                                            const float* __restrict__ rbuf = nullptr, const int rstride = 0,
+                                            const int nr4 = 0) {
     constexpr int CB = kSplitCB;
     for (int c0 = 0; c0 < Wa; c0 += CB) {
         float xr = 0.f;
@@ -138,15 +140,20 @@ __device__ __forceinline__ void split_phase(cg::cluster_group& cluster, const fl
             const int c = c0 + vi % CB;
             float inc = tot;
             if constexpr (ADJ) {
-                // four independent chains (receivers jr = 4 u + e), summed in a fixed order
+                // four independent chains (receivers jr = 4 u + e), summed in a
+                // fixed order; both buffers are receiver-contiguous and zero
+                // beyond R, so each 16-byte read feeds one step of all four
+                const float4* cr = reinterpret_cast<const float4*>(Ccol + (size_t)rl * rstride);
+                const float4* rr = reinterpret_cast<const float4*>(rbuf + (size_t)c * rstride);
                 float s4[4] = {0.f, 0.f, 0.f, 0.f};
-                int jr = 0;
-                for (; jr + 4 <= R; jr += 4) {
-#pragma unroll
-                    for (int e = 0; e < 4; ++e)
-                        s4[e] = __fmaf_rn(Ccol[(jr + e) * cstride + rl], rbuf[(jr + e) * Wa + c], s4[e]);
+#pragma unroll 4
+                for (int u = 0; u < nr4; ++u) {
+                    const float4 cv = cr[u], rv = rr[u];
+                    s4[0] = __fmaf_rn(cv.x, rv.x, s4[0]);
+                    s4[1] = __fmaf_rn(cv.y, rv.y, s4[1]);
+                    s4[2] = __fmaf_rn(cv.z, rv.z, s4[2]);
+                    s4[3] = __fmaf_rn(cv.w, rv.w, s4[3]);
                 }
-                for (; jr < R; ++jr) s4[0] = __fmaf_rn(Ccol[jr * cstride + rl], rbuf[jr * Wa + c], s4[0]);
                 const float src = (s4[0] + s4[1]) + (s4[2] + s4[3]);
                 inc = __fmaf_rn(tot, dt, 2.f * src);
             } else {
