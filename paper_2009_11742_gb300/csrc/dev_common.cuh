@@ -141,6 +141,12 @@ __device__ __forceinline__ void cp_async8(void* sdst, const void* gsrc, int src_
     asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;"
                  ::"r"((uint32_t)__cvta_generic_to_shared(sdst)), "l"(gsrc), "r"(src_bytes) : "memory");
 }
+// 16 bytes (both addresses 16-byte aligned), bypassing L1; src_bytes = 0
+// zero-fills the destination.
+__device__ __forceinline__ void cp_async16(void* sdst, const void* gsrc, int src_bytes) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;"
+                 ::"r"((uint32_t)__cvta_generic_to_shared(sdst)), "l"(gsrc), "r"(src_bytes) : "memory");
+}
 template <typename T>
 __device__ __forceinline__ void cp_async_elem(T* sdst, const T* gsrc, bool ok) {
     if constexpr (sizeof(T) == 4) cp_async4(sdst, gsrc, ok ? 4 : 0);

@@ -169,6 +169,75 @@ cudaError_t launch_adjoint(const AdjArgsT<double>& a, const AdjPlan& p, cudaStre
     return launch_adjoint_t<double>(a, p, st);
 }
 
+// The reverse step's source term for a range of steps (Sec. 3.1: the
+// misfit's derivative enters the adjoint of V through C^T):
+//   src[s][m][k] = sum_jr C[jr][k] (traces[n + 1 - rec_base][m][jr] - ystar[n][m][jr]),
+// n = n_lo + s.  It does not depend on the adjoint state, so the split-role
+// kernel reads it instead of forming it on its critical path.  Four chains
+// over jr = 4 u + e, summed as (c0 + c1) + (c2 + c3): the order the reverse
+// kernels use.  Block: 64 rows k x 16 columns m of one step; thread t takes
+// row t % 64 and columns 4 (t / 64) + 0..3; the block's residuals sit in
+// shared memory, receiver-contiguous and zero-padded to a multiple of 4.
+constexpr int kSrcRows = 64, kSrcCols = 16;
+
+__global__ void __launch_bounds__(256) adj_source_kernel(const float* __restrict__ C_rm,
+                                                         const float* __restrict__ traces,
+                                                         const float* __restrict__ ystar, int n_lo,
+                                                         int rec_base, int M, int R, int Kp,
+                                                         float* __restrict__ src) {
+    extern __shared__ float4 res4[];  // [kSrcCols][R4]
+    float* res = reinterpret_cast<float*>(res4);
+    const int R4 = (R + 3) / 4, RP = 4 * R4;
+    const int k0 = blockIdx.x * kSrcRows, m0 = blockIdx.y * kSrcCols, s = blockIdx.z;
+    const int n = n_lo + s, rec = n + 1 - rec_base;
+    for (int idx = threadIdx.x; idx < kSrcCols * RP; idx += blockDim.x) {
+        const int c = idx / RP, jr = idx % RP, m = m0 + c;
+        float v = 0.f;
+        if (m < M && jr < R)
+            v = traces[((size_t)rec * M + m) * R + jr] - ystar[((size_t)n * M + m) * R + jr];
+        res[idx] = v;
+    }
+    __syncthreads();
+    const int k = k0 + (threadIdx.x % kSrcRows), cg4 = 4 * (threadIdx.x / kSrcRows);
+    float acc[4][4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c)
+#pragma unroll
+        for (int e = 0; e < 4; ++e) acc[c][e] = 0.f;
+    for (int u = 0; u < R4; ++u) {
+        float cv[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) cv[e] = 4 * u + e < R ? C_rm[(size_t)(4 * u + e) * Kp + k] : 0.f;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const float4 r4 = res4[(cg4 + c) * R4 + u];
+            acc[c][0] = __fmaf_rn(cv[0], r4.x, acc[c][0]);
+            acc[c][1] = __fmaf_rn(cv[1], r4.y, acc[c][1]);
+            acc[c][2] = __fmaf_rn(cv[2], r4.z, acc[c][2]);
+            acc[c][3] = __fmaf_rn(cv[3], r4.w, acc[c][3]);
+        }
+    }
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        const int m = m0 + cg4 + c;
+        if (m < M) src[((size_t)s * M + m) * Kp + k] = (acc[c][0] + acc[c][1]) + (acc[c][2] + acc[c][3]);
+    }
+}
+
+cudaError_t launch_adj_source(const float* C_rm, const float* traces, const float* ystar, int n_lo, int ns,
+                              int rec_base, int M, int R, int Kp, float* src, cudaStream_t st) {
+    if (ns < 1 || M < 1 || R < 1 || Kp < kSrcRows || Kp % kSrcRows != 0) return cudaErrorInvalidValue;
+    const size_t smem = (size_t)kSrcCols * ((R + 3) / 4) * sizeof(float4);
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(adj_source_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    const dim3 grid(Kp / kSrcRows, (M + kSrcCols - 1) / kSrcCols, ns);
+    adj_source_kernel<<<grid, 256, smem, st>>>(C_rm, traces, ystar, n_lo, rec_base, M, R, Kp, src);
+    return cudaGetLastError();
+}
+
 // out[m] = sum over CTAs (in rank order) of part[rank][m].
 template <typename T>
 __global__ void sum_partials_kernel(const T* __restrict__ part, int cs, int M, T* __restrict__ out) {

@@ -21,6 +21,7 @@
 // Half A's epilogue adds the rank-R source 2 C^T r^{n+1} (C columns of the
 // CTA's rows and the step's residuals staged in shared memory), and a
 // deterministic per-CTA column reduction accumulates the period gradient.
+// The split-role kernel below (FP32, Kp <= 512) is the faster form there.
 #pragma once
 
 #include <cooperative_groups.h>
@@ -358,34 +359,23 @@ __global__ void __launch_bounds__(kThreads, 1) rank2_adjoint_kernel(const AdjArg
 // rows of lamV, S-role CTAs doing the same with Avs^T and lamS, each finished
 // tile pushed into the other role's operand copy, one cluster barrier per
 // phase.  Time runs backwards: block A takes reverse step n = n_hi - 1 - k in
-// phase 2k, block B in phase 2k + 1.  The V role's epilogue adds 2 C^T r
-// (its C columns and the block's residual in shared memory; the residual's
-// inputs are copied one phase ahead).  After each of its phases it adds its
+// phase 2k, block B in phase 2k + 1.  The V role's epilogue adds 2 C^T r,
+// which does not depend on the adjoint state: adj_source_kernel forms it for
+// the launch's range of steps beforehand, and each V-role CTA copies its own
+// rows of it one phase ahead.  After each of its phases the V role adds its
 // own rows' share of the period gradient to a per-CTA partial.
 struct AdjSplitSmem {
-    size_t X, own, comp, Ccol, rbuf, trS, ysS, g, T, gT, dfT, total;
+    size_t X, own, comp, src, g, T, gT, dfT, total;
 };
 
-// Row stride (floats) of the receiver-indexed buffers of the split reverse
-// kernel: R rounded up to a multiple of 4 (zero-padded), plus 4 when that is
-// an even number of 16-byte groups, so that the rows read by the eight lanes
-// of a quarter warp fall in distinct bank groups.
-__host__ __device__ inline int adj_rstride(int R) {
-    const int rp = (R + 3) / 4 * 4;
-    return (rp / 4) % 2 == 0 ? rp + 4 : rp;
-}
-
 __host__ __device__ inline AdjSplitSmem adj_split_smem_layout(int Wa, int Kp, int R) {
+    (void)R;  // the source term arrives precomputed, so the layout does not depend on R
     AdjSplitSmem s{};
-    const int rs = adj_rstride(R);
     size_t o = 0;
     s.X = o;    o += align16((size_t)2 * Wa * Kp * sizeof(float));
     s.own = o;  o += align16((size_t)2 * Wa * kOwnStride * sizeof(float));
     s.comp = o; o += align16((size_t)2 * Wa * kOwnStride * sizeof(float));
-    s.Ccol = o; o += align16((size_t)kSplitRows * rs * sizeof(float));
-    s.rbuf = o; o += align16((size_t)Wa * rs * sizeof(float));
-    s.trS = o;  o += align16((size_t)Wa * rs * sizeof(float));
-    s.ysS = o;  o += align16((size_t)Wa * rs * sizeof(float));
+    s.src = o;  o += align16((size_t)2 * Wa * kOwnStride * sizeof(float));
     s.g = o;    o += align16((size_t)kSplitRows * sizeof(float));
     s.T = o;    o += align16((size_t)2 * Wa * sizeof(float));
     s.gT = o;   o += align16((size_t)2 * Wa * sizeof(float));
@@ -420,12 +410,7 @@ __global__ void __launch_bounds__(kThreads, 1) rank2_adjoint_split_kernel(const 
     float* X = reinterpret_cast<float*>(smem + L.X);         // [2][Wa][Kp] operand copies
     float* own = reinterpret_cast<float*>(smem + L.own);     // [2][Wa][72] owned rows
     float* comp = reinterpret_cast<float*>(smem + L.comp);   // [2][Wa][72] Kahan carries
-    // receiver-indexed buffers, jr contiguous (stride rs, zero beyond R)
-    const int rs = adj_rstride(R);
-    float* Ccol = reinterpret_cast<float*>(smem + L.Ccol);   // [64][rs]: C[jr][row0 + rl]
-    float* rbuf = reinterpret_cast<float*>(smem + L.rbuf);   // [Wa][rs] residual of the phase's block
-    float* trS = reinterpret_cast<float*>(smem + L.trS);     // [Wa][rs] next phase's records
-    float* ysS = reinterpret_cast<float*>(smem + L.ysS);     // [Wa][rs] and targets
+    float* srcS = reinterpret_cast<float*>(smem + L.src);    // [2][Wa][72] C^T r, by phase parity
     float* gown = reinterpret_cast<float*>(smem + L.g);      // [64]
     float* Tcol = reinterpret_cast<float*>(smem + L.T);      // [2][Wa]
     float* gTacc = reinterpret_cast<float*>(smem + L.gT);    // [2][Wa] period-gradient partials
@@ -450,10 +435,6 @@ __global__ void __launch_bounds__(kThreads, 1) rank2_adjoint_split_kernel(const 
         own[idx] = ok ? own_in[(size_t)(gc0(b) + c) * Kown + row] : 0.f;
         comp[idx] = ok ? comp_in[(size_t)(gc0(b) + c) * Kown + row] : 0.f;
     }
-    for (int idx = tid; idx < (vrole ? kSplitRows * rs : 0); idx += kThreads) {
-        const int rl = idx / rs, jr = idx % rs;
-        Ccol[idx] = jr < R ? a.C_rm[(size_t)jr * Kp + row0 + rl] : 0.f;
-    }
     if (tid < kSplitRows) gown[tid] = vrole ? a.g_p[row0 + tid] : 0.f;
     for (int idx = tid; idx < 2 * Wa; idx += kThreads) {
         const int b = idx / Wa, c = idx % Wa;
@@ -464,19 +445,19 @@ __global__ void __launch_bounds__(kThreads, 1) rank2_adjoint_split_kernel(const 
     float op[4][4 * KI];
     load_op_quad<KI>(op, vrole ? a.opA_rm : a.opB_rm, Kp, row0 + 4 * q, j);
 
-    // the trace records C V^{n+1} and targets y*^{n+1} of block b, reverse step n
-    auto prefetch_residual = [&](int b, int n) {
-        const int rec = n + 1 - a.rec_base;
-        for (int idx = tid; idx < Wa * rs; idx += kThreads) {
-            const int c = idx / rs, jr = idx % rs;
-            const bool ok = c < ncol(b) && jr < R;
-            const int cc = ok ? c : 0, jj = ok ? jr : 0;  // a valid address for the zero fill
-            cp_async4(trS + idx, a.traces + ((size_t)rec * M + gc0(b) + cc) * R + jj, ok ? 4 : 0);
-            cp_async4(ysS + idx, a.ystar + ((size_t)n * M + gc0(b) + cc) * R + jj, ok ? 4 : 0);
+    // the own rows' C^T r of block b, reverse step n (precomputed for the
+    // range), into parity buffer pb: 16 bytes per copy, zero for absent columns
+    auto prefetch_src = [&](int b, int n, int pb) {
+        float* dst = srcS + (size_t)pb * Wa * kOwnStride;
+        for (int idx = tid; idx < Wa * (kSplitRows / 4); idx += kThreads) {
+            const int c = idx / (kSplitRows / 4), piece = idx % (kSplitRows / 4);
+            const bool ok = c < ncol(b);
+            const float* gsrc = a.src + ((size_t)(n - a.n_lo) * M + gc0(b) + (ok ? c : 0)) * Kp + row0 + 4 * piece;
+            cp_async16(dst + (size_t)c * kOwnStride + 4 * piece, gsrc, ok ? 16 : 0);
         }
     };
     const int NR = a.n_hi - a.n_lo;  // reverse steps of this segment
-    if (vrole && NR > 0 && ncol(0) > 0) prefetch_residual(0, a.n_hi - 1);
+    if (vrole && NR > 0 && ncol(0) > 0) prefetch_src(0, a.n_hi - 1, 0);
     // every CTA's copies must be initialised before any peer pushes into them
     cluster.sync();
 
@@ -491,30 +472,27 @@ __global__ void __launch_bounds__(kThreads, 1) rank2_adjoint_split_kernel(const 
         float* ownb = own + (size_t)b * Wa * kOwnStride;
         float* compb = comp + (size_t)b * Wa * kOwnStride;
         if (vrole) {
-            // this phase's residual (copied during the previous phase), the
-            // block's df/dT table every kAdjTab of its steps, then the next
-            // phase's copies
+            // this phase's source term (copied during the previous phase into
+            // parity buffer p & 1), the block's df/dT table every kAdjTab of
+            // its steps, then the next phase's copies into the other buffer
+            // (read last in phase p - 1, which a cluster barrier has closed)
             cp_async_wait_all();
             __syncthreads();
-            if (work) {
-                for (int idx = tid; idx < Wa * rs; idx += kThreads) rbuf[idx] = trS[idx] - ysS[idx];
-                if (k % kAdjTab == 0) {
-                    for (int idx = tid; idx < kAdjTab * ncol(b); idx += kThreads) {
-                        const int i = idx / ncol(b), c = idx % ncol(b);
-                        if (n - i >= a.n_lo)
-                            dfT[(b * kAdjTab + i) * Wa + c] =
-                                wavelet_dT_eval<float>(a.wavelet, (long long)a.n0 + n - i, a.dt, Tcol[b * Wa + c]);
-                    }
+            if (work && k % kAdjTab == 0) {
+                for (int idx = tid; idx < kAdjTab * ncol(b); idx += kThreads) {
+                    const int i = idx / ncol(b), c = idx % ncol(b);
+                    if (n - i >= a.n_lo)
+                        dfT[(b * kAdjTab + i) * Wa + c] =
+                            wavelet_dT_eval<float>(a.wavelet, (long long)a.n0 + n - i, a.dt, Tcol[b * Wa + c]);
                 }
             }
-            __syncthreads();
             const int b2 = (p + 1) & 1, k2 = (p + 1 - b2) >> 1;
-            if (k2 < NR && ncol(b2) > 0) prefetch_residual(b2, a.n_hi - 1 - k2);
+            if (k2 < NR && ncol(b2) > 0) prefetch_src(b2, a.n_hi - 1 - k2, (p + 1) & 1);
             if (work) {
                 // half A: lamV <- lamV + dt Asv^T lamS + 2 C^T r^{n+1}
                 split_phase<KI, false, false, true>(cluster, op, Xb, ownb, compb, gown, gown, Xb, dt, Wa, Kp,
                                                     row0, H, peer0, q, j, warp, lane, nullptr, Kown, ncol(b),
-                                                    Ccol, rbuf, rs, (R + 3) / 4);
+                                                    srcS + (size_t)(p & 1) * Wa * kOwnStride);
                 __syncthreads();
                 // period gradient: dt (g_own . a_V[:, c]) df/dT(t_n; T_c), fixed order
                 const float* dfn = dfT + (b * kAdjTab + (k % kAdjTab)) * Wa;

@@ -84,9 +84,8 @@ __device__ __forceinline__ void load_op_quad(float (&op)[4][4 * KI], const float
 // reference state (Krows x columns); each lane fetches its epilogue's value
 // before the products.  XR is a template flag so that runs without the term
 // compile to exactly the code they had without it.  ADJ (the reverse-time
-// adjoint's half A): own rows += dt (op . X_b) + 2 C_own^T r, with Ccol the
-// CTA's C columns ([64 rows][rstride], receiver index contiguous) and rbuf
-// block b's residual ([Wa][rstride]), both zero from R up to 4 nr4.
+// adjoint's half A): own rows += dt (op . X_b) + 2 C_own^T r, with asrc
+// block b's C_own^T r for this step ([Wa][kOwnStride], precomputed).
 template <int KI, bool FORCED, bool XR, bool ADJ = false>
 __device__ __forceinline__ void split_phase(cg::cluster_group& cluster, const float (&op)[4][4 * KI],
                                             const float* __restrict__ X, float* __restrict__ own,
@@ -97,9 +96,7 @@ __device__ __forceinline__ void split_phase(cg::cluster_group& cluster, const fl
                                             const int q, const int j, const int warp,
                                             const int lane, const float* __restrict__ Xref,
                                             const int Krows, const int ncol,
-                                            const float* __restrict__ Ccol = nullptr,
-                                            const float* __restrict__ rbuf = nullptr, const int rstride = 0,
-                                            const int nr4 = 0) {
+                                            const float* __restrict__ asrc = nullptr) {
     constexpr int CB = kSplitCB;
     for (int c0 = 0; c0 < Wa; c0 += CB) {
         float xr = 0.f;
@@ -140,21 +137,7 @@ __device__ __forceinline__ void split_phase(cg::cluster_group& cluster, const fl
             const int c = c0 + vi % CB;
             float inc = tot;
             if constexpr (ADJ) {
-                // four independent chains (receivers jr = 4 u + e), summed in a
-                // fixed order; both buffers are receiver-contiguous and zero
-                // beyond R, so each 16-byte read feeds one step of all four
-                const float4* cr = reinterpret_cast<const float4*>(Ccol + (size_t)rl * rstride);
-                const float4* rr = reinterpret_cast<const float4*>(rbuf + (size_t)c * rstride);
-                float s4[4] = {0.f, 0.f, 0.f, 0.f};
-#pragma unroll 4
-                for (int u = 0; u < nr4; ++u) {
-                    const float4 cv = cr[u], rv = rr[u];
-                    s4[0] = __fmaf_rn(cv.x, rv.x, s4[0]);
-                    s4[1] = __fmaf_rn(cv.y, rv.y, s4[1]);
-                    s4[2] = __fmaf_rn(cv.z, rv.z, s4[2]);
-                    s4[3] = __fmaf_rn(cv.w, rv.w, s4[3]);
-                }
-                const float src = (s4[0] + s4[1]) + (s4[2] + s4[3]);
+                const float src = asrc[c * kOwnStride + rl];
                 inc = __fmaf_rn(tot, dt, 2.f * src);
             } else {
                 if (FORCED) inc = __fmaf_rn(gown[rl], fcol[c], inc);

@@ -1845,7 +1845,7 @@ rom_status rom_run_rank3(const rom_t* hs, int nops, void* V, void* S, const void
 namespace {
 
 struct AdjLayout {
-    size_t traces, ckpt, work, acomp, gtp, acc, total;
+    size_t traces, ckpt, work, acomp, gtp, acc, src, total;
     int seg, nseg;
 };
 
@@ -1864,6 +1864,11 @@ AdjLayout adjoint_layout(const rom_s* h, int M, int nsteps, int ckpt_every, size
     L.acomp = o;  o += al(sizeof(float) * kvm);
     L.gtp = o;    o += al(es * 16 * (size_t)M);
     L.acc = o;    o += al(sizeof(double) * 2);
+    // FP32 up to Kp = 512 (the split-role reverse kernel): the source term of
+    // up to kAdjSrcSteps reverse steps
+    L.src = o;
+    if (es == 4 && h->Kp <= 512)
+        o += al(sizeof(float) * (size_t)(L.seg < kAdjSrcSteps ? L.seg : kAdjSrcSteps) * M * h->Kp);
     L.total = o;
     return L;
 }
@@ -1892,6 +1897,7 @@ rom_status adjoint_run(rom_s* h, const void* V0, const void* S0, const void* Tp,
     float* acomp = reinterpret_cast<float*>(ws + L.acomp);
     T* gtp = reinterpret_cast<T*>(ws + L.gtp);
     double* acc = reinterpret_cast<double*>(ws + L.acc);
+    float* asrc = reinterpret_cast<float*>(ws + L.src);
     const size_t nv = (size_t)h->Kv * M, ns = (size_t)h->Ks * M, kvm = nv + ns;
     T* wV = work;
     T* wS = work + nv;
@@ -1962,7 +1968,23 @@ rom_status adjoint_run(rom_s* h, const void* V0, const void* S0, const void* Tp,
         aa.Kp = h->Kp;
         aa.R = h->R;
         aa.M = M;
-        e = launch_adjoint(aa, ap, st);
+        if (F32 && ap.split) {
+            // the split-role kernel reads the source term precomputed for at
+            // most kAdjSrcSteps steps: the segment's latest steps first
+            for (int hi = n_start + len; hi > n_start && e == cudaSuccess;) {
+                const int lo = hi - kAdjSrcSteps > n_start ? hi - kAdjSrcSteps : n_start;
+                e = launch_adj_source(static_cast<const float*>(h->C_rm[1]), reinterpret_cast<const float*>(traces),
+                                      reinterpret_cast<const float*>(ys), lo, hi - lo, aa.rec_base, M, h->R,
+                                      h->Kp, asrc, st);
+                aa.src = asrc;
+                aa.n_lo = lo;
+                aa.n_hi = hi;
+                if (e == cudaSuccess) e = launch_adjoint(aa, ap, st);
+                hi = lo;
+            }
+        } else {
+            e = launch_adjoint(aa, ap, st);
+        }
     }
     if (e == cudaSuccess && s == ROM_OK) e = launch_sum_partials(gtp, ap.cs, M, static_cast<T*>(gT), st);
     double hacc[2] = {0.0, 0.0};

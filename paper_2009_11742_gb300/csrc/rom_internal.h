@@ -204,6 +204,7 @@ struct AdjArgsT {
     const T* traces;  // forward records: record k = C V^{rec_base + k}, [k][m][j]
     const T* ystar;   // targets: record n = ystar^{n+1}, [n][m][j]
     T* gTpart;        // cs x M per-CTA partial dL/dT (in/out)
+    const float* src; // split-role kernel: C^T r of the range's steps, [n - n_lo][m][Kp]
     int* status;
     double dt;
     long long n0;
@@ -224,6 +225,12 @@ struct AdjPlan {
 bool plan_adjoint(int Kp, int M, int R, AdjPlan* p, bool f64 = false);
 cudaError_t launch_adjoint(const AdjArgsT<float>& a, const AdjPlan& p, cudaStream_t st);
 cudaError_t launch_adjoint(const AdjArgsT<double>& a, const AdjPlan& p, cudaStream_t st);
+// The reverse step's source term, hoisted out of the recurrence for the
+// split-role kernel: src[s][m][k] = sum_jr C[jr][k] r[jr] with r = traces of
+// record n + 1 - rec_base minus ystar of step n, n = n_lo + s, s < ns.
+constexpr int kAdjSrcSteps = 64;  // reverse steps per launch of the split-role kernel
+cudaError_t launch_adj_source(const float* C_rm, const float* traces, const float* ystar, int n_lo, int ns,
+                              int rec_base, int M, int R, int Kp, float* src, cudaStream_t st);
 cudaError_t launch_sum_partials(const float* part, int cs, int M, float* out, cudaStream_t st);
 cudaError_t launch_sum_partials(const double* part, int cs, int M, double* out, cudaStream_t st);
 

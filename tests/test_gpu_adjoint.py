@@ -63,6 +63,9 @@ def gpu_adjoint(R, h, p, V0, S0, ystar, N, ckpt):
 
 @pytest.mark.parametrize("Kv,Ks,M,R,N,ckpt", [(64, 64, 7, 3, 60, 0), (64, 64, 7, 3, 60, 16),
                                                (200, 180, 20, 5, 100, 32), (512, 512, 9, 8, 40, 7),
+                                               # one receiver, and more receivers than rows per CTA
+                                               # (receiver-contiguous buffers of stride 4 and 100)
+                                               (128, 96, 5, 1, 30, 0), (256, 256, 10, 100, 30, 8),
                                                # above K = 512: two 32-row tiles per CTA, the
                                                # transposed operators read from L2
                                                (640, 600, 11, 5, 36, 0), (1024, 1000, 6, 8, 40, 16),
