@@ -362,8 +362,9 @@ __global__ void __launch_bounds__(kThreads, 1) rank2_adjoint_kernel(const AdjArg
 // phase 2k, block B in phase 2k + 1.  The V role's epilogue adds 2 C^T r,
 // which does not depend on the adjoint state: adj_source_kernel forms it for
 // the launch's range of steps beforehand, and each V-role CTA copies its own
-// rows of it one phase ahead.  After each of its phases the V role adds its
-// own rows' share of the period gradient to a per-CTA partial.
+// rows of it one phase ahead.  The S role, whose operand copy holds the same
+// new lamV, adds its slab's share of the period gradient to a per-CTA
+// partial after each of its phases.
 struct AdjSplitSmem {
     size_t X, own, comp, src, g, T, gT, dfT, total;
 };
@@ -435,7 +436,7 @@ __global__ void __launch_bounds__(kThreads, 1) rank2_adjoint_split_kernel(const 
         own[idx] = ok ? own_in[(size_t)(gc0(b) + c) * Kown + row] : 0.f;
         comp[idx] = ok ? comp_in[(size_t)(gc0(b) + c) * Kown + row] : 0.f;
     }
-    if (tid < kSplitRows) gown[tid] = vrole ? a.g_p[row0 + tid] : 0.f;
+    if (tid < kSplitRows) gown[tid] = a.g_p[row0 + tid];  // the S role's gradient slab
     for (int idx = tid; idx < 2 * Wa; idx += kThreads) {
         const int b = idx / Wa, c = idx % Wa;
         const bool ok = c < ncol(b);
@@ -473,19 +474,10 @@ __global__ void __launch_bounds__(kThreads, 1) rank2_adjoint_split_kernel(const 
         float* compb = comp + (size_t)b * Wa * kOwnStride;
         if (vrole) {
             // this phase's source term (copied during the previous phase into
-            // parity buffer p & 1), the block's df/dT table every kAdjTab of
-            // its steps, then the next phase's copies into the other buffer
-            // (read last in phase p - 1, which a cluster barrier has closed)
+            // parity buffer p & 1), then the next phase's copies into the other
+            // buffer (read last in phase p - 1, which a cluster barrier has closed)
             cp_async_wait_all();
             __syncthreads();
-            if (work && k % kAdjTab == 0) {
-                for (int idx = tid; idx < kAdjTab * ncol(b); idx += kThreads) {
-                    const int i = idx / ncol(b), c = idx % ncol(b);
-                    if (n - i >= a.n_lo)
-                        dfT[(b * kAdjTab + i) * Wa + c] =
-                            wavelet_dT_eval<float>(a.wavelet, (long long)a.n0 + n - i, a.dt, Tcol[b * Wa + c]);
-                }
-            }
             const int b2 = (p + 1) & 1, k2 = (p + 1 - b2) >> 1;
             if (k2 < NR && ncol(b2) > 0) prefetch_src(b2, a.n_hi - 1 - k2, (p + 1) & 1);
             if (work) {
@@ -493,21 +485,32 @@ __global__ void __launch_bounds__(kThreads, 1) rank2_adjoint_split_kernel(const 
                 split_phase<KI, false, false, true>(cluster, op, Xb, ownb, compb, gown, gown, Xb, dt, Wa, Kp,
                                                     row0, H, peer0, q, j, warp, lane, nullptr, Kown, ncol(b),
                                                     srcS + (size_t)(p & 1) * Wa * kOwnStride);
-                __syncthreads();
-                // period gradient: dt (g_own . a_V[:, c]) df/dT(t_n; T_c), fixed order
-                const float* dfn = dfT + (b * kAdjTab + (k % kAdjTab)) * Wa;
-                for (int c = warp; c < ncol(b); c += kSplitWarps) {
-                    float sg = gown[lane] * ownb[c * kOwnStride + lane];
-                    sg = __fmaf_rn(gown[lane + 32], ownb[c * kOwnStride + lane + 32], sg);
-#pragma unroll
-                    for (int o = 16; o > 0; o >>= 1) sg += __shfl_xor_sync(0xffffffffu, sg, o);
-                    if (lane == 0) gTacc[b * Wa + c] = __fmaf_rn(dt * sg, dfn[c], gTacc[b * Wa + c]);
-                }
             }
         } else if (work) {
+            // the block's df/dT table every kAdjTab of its steps
+            if (k % kAdjTab == 0) {
+                for (int idx = tid; idx < kAdjTab * ncol(b); idx += kThreads) {
+                    const int i = idx / ncol(b), c = idx % ncol(b);
+                    if (n - i >= a.n_lo)
+                        dfT[(b * kAdjTab + i) * Wa + c] =
+                            wavelet_dT_eval<float>(a.wavelet, (long long)a.n0 + n - i, a.dt, Tcol[b * Wa + c]);
+                }
+                __syncthreads();
+            }
             // half B: lamS <- lamS + dt Avs^T lamV (the new lamV of block b)
             split_phase<KI, false, false>(cluster, op, Xb, ownb, compb, gown, gown, Xb, dt, Wa, Kp, row0, H,
                                           peer0, q, j, warp, lane, nullptr, Kown, ncol(b));
+            // period gradient of step n over this slab's rows of the same new
+            // lamV: dt (g_slab . a_V[:, c]) df/dT(t_n; T_c), fixed order
+            const float* dfn = dfT + (b * kAdjTab + (k % kAdjTab)) * Wa;
+            for (int c = warp; c < ncol(b); c += kSplitWarps) {
+                const float* av = Xb + (size_t)c * Kp + row0;
+                float sg = gown[lane] * av[lane];
+                sg = __fmaf_rn(gown[lane + 32], av[lane + 32], sg);
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) sg += __shfl_xor_sync(0xffffffffu, sg, o);
+                if (lane == 0) gTacc[b * Wa + c] = __fmaf_rn(dt * sg, dfn[c], gTacc[b * Wa + c]);
+            }
         }
         cluster.sync();
     }
