@@ -171,70 +171,89 @@ cudaError_t launch_adjoint(const AdjArgsT<double>& a, const AdjPlan& p, cudaStre
 
 // The reverse step's source term for a range of steps (Sec. 3.1: the
 // misfit's derivative enters the adjoint of V through C^T):
-//   src[s][m][k] = sum_jr C[jr][k] (traces[n + 1 - rec_base][m][jr] - ystar[n][m][jr]),
-// n = n_lo + s.  It does not depend on the adjoint state, so the split-role
-// kernel reads it instead of forming it on its critical path.  Four chains
-// over jr = 4 u + e, summed as (c0 + c1) + (c2 + c3): the order the reverse
-// kernels use.  Block: 64 rows k x 16 columns m of one step; thread t takes
-// row t % 64 and columns 4 (t / 64) + 0..3; the block's residuals sit in
-// shared memory, receiver-contiguous and zero-padded to a multiple of 4.
-constexpr int kSrcRows = 64, kSrcCols = 16;
+//   src[q][k] = sum_jr C[jr][k] (traces[n + 1 - rec_base][m][jr] - ystar[n][m][jr]),
+// q = s M + m, n = n_lo + s.  It does not depend on the adjoint state, so the
+// split-role kernel reads it instead of forming it on its critical path.
+// Four chains over jr = 4 u + e, summed as (c0 + c1) + (c2 + c3): the order
+// the reverse kernels use.  It is a (ns M) x Kp x R product, tiled as one:
+// a block takes 64 rows q x 64 columns k, stages 64 receivers at a time of
+// the residual rows and of C (k-major) in shared memory, and thread
+// (tq, tk) = (t / 16, t % 16) accumulates rows 4 tq + i and columns
+// tk + 16 j (i, j < 4), so that one 16-byte read of each operand feeds 16
+// multiply-adds and the C reads of a quarter warp fall in distinct banks.
+constexpr int kSrcT = 64;                // rows q and columns k per block
+constexpr int kSrcJ = 64;                // receivers per shared-memory chunk
+constexpr int kSrcStride = kSrcJ + 4;    // 17 16-byte groups per row (odd)
 
 __global__ void __launch_bounds__(256) adj_source_kernel(const float* __restrict__ C_rm,
                                                          const float* __restrict__ traces,
-                                                         const float* __restrict__ ystar, int n_lo,
+                                                         const float* __restrict__ ystar, int n_lo, int ns,
                                                          int rec_base, int M, int R, int Kp,
                                                          float* __restrict__ src) {
-    extern __shared__ float4 res4[];  // [kSrcCols][R4]
-    float* res = reinterpret_cast<float*>(res4);
-    const int R4 = (R + 3) / 4, RP = 4 * R4;
-    const int k0 = blockIdx.x * kSrcRows, m0 = blockIdx.y * kSrcCols, s = blockIdx.z;
-    const int n = n_lo + s, rec = n + 1 - rec_base;
-    for (int idx = threadIdx.x; idx < kSrcCols * RP; idx += blockDim.x) {
-        const int c = idx / RP, jr = idx % RP, m = m0 + c;
-        float v = 0.f;
-        if (m < M && jr < R)
-            v = traces[((size_t)rec * M + m) * R + jr] - ystar[((size_t)n * M + m) * R + jr];
-        res[idx] = v;
-    }
-    __syncthreads();
-    const int k = k0 + (threadIdx.x % kSrcRows), cg4 = 4 * (threadIdx.x / kSrcRows);
-    float acc[4][4];
+    __shared__ __align__(16) float Rs[kSrcT * kSrcStride];  // [q][jr] residual rows
+    __shared__ __align__(16) float Cs[kSrcT * kSrcStride];  // [k][jr] C columns
+    const int Q = ns * M;
+    const int q0 = blockIdx.x * kSrcT, k0 = blockIdx.y * kSrcT;
+    const int t = threadIdx.x, tq = t / 16, tk = t % 16;
+    float acc[4][4][4];
 #pragma unroll
-    for (int c = 0; c < 4; ++c)
+    for (int i = 0; i < 4; ++i)
 #pragma unroll
-        for (int e = 0; e < 4; ++e) acc[c][e] = 0.f;
-    for (int u = 0; u < R4; ++u) {
-        float cv[4];
+        for (int j = 0; j < 4; ++j)
 #pragma unroll
-        for (int e = 0; e < 4; ++e) cv[e] = 4 * u + e < R ? C_rm[(size_t)(4 * u + e) * Kp + k] : 0.f;
+            for (int e = 0; e < 4; ++e) acc[i][j][e] = 0.f;
+    for (int j0 = 0; j0 < R; j0 += kSrcJ) {
+        __syncthreads();  // the previous chunk's reads are done
+        for (int idx = t; idx < kSrcT * kSrcJ; idx += blockDim.x) {
+            const int r = idx / kSrcJ, jj = idx % kSrcJ, jr = j0 + jj, q = q0 + r;
+            float v = 0.f;
+            if (q < Q && jr < R) {
+                const int sq = q / M, m = q - sq * M, n = n_lo + sq;
+                v = traces[((size_t)(n + 1 - rec_base) * M + m) * R + jr] - ystar[((size_t)n * M + m) * R + jr];
+            }
+            Rs[r * kSrcStride + jj] = v;
+        }
+        for (int idx = t; idx < kSrcJ * kSrcT; idx += blockDim.x) {
+            const int jj = idx / kSrcT, kk = idx % kSrcT, jr = j0 + jj;
+            Cs[kk * kSrcStride + jj] = jr < R ? C_rm[(size_t)jr * Kp + k0 + kk] : 0.f;
+        }
+        __syncthreads();
+        const int nu = min(kSrcJ, R - j0 + 3) / 4;  // receiver quads of the chunk below R
+        for (int u = 0; u < nu; ++u) {
+            float4 rv[4], cv[4];
 #pragma unroll
-        for (int c = 0; c < 4; ++c) {
-            const float4 r4 = res4[(cg4 + c) * R4 + u];
-            acc[c][0] = __fmaf_rn(cv[0], r4.x, acc[c][0]);
-            acc[c][1] = __fmaf_rn(cv[1], r4.y, acc[c][1]);
-            acc[c][2] = __fmaf_rn(cv[2], r4.z, acc[c][2]);
-            acc[c][3] = __fmaf_rn(cv[3], r4.w, acc[c][3]);
+            for (int i = 0; i < 4; ++i) rv[i] = *reinterpret_cast<const float4*>(Rs + (4 * tq + i) * kSrcStride + 4 * u);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) cv[j] = *reinterpret_cast<const float4*>(Cs + (tk + 16 * j) * kSrcStride + 4 * u);
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    acc[i][j][0] = __fmaf_rn(cv[j].x, rv[i].x, acc[i][j][0]);
+                    acc[i][j][1] = __fmaf_rn(cv[j].y, rv[i].y, acc[i][j][1]);
+                    acc[i][j][2] = __fmaf_rn(cv[j].z, rv[i].z, acc[i][j][2]);
+                    acc[i][j][3] = __fmaf_rn(cv[j].w, rv[i].w, acc[i][j][3]);
+                }
         }
     }
 #pragma unroll
-    for (int c = 0; c < 4; ++c) {
-        const int m = m0 + cg4 + c;
-        if (m < M) src[((size_t)s * M + m) * Kp + k] = (acc[c][0] + acc[c][1]) + (acc[c][2] + acc[c][3]);
+    for (int i = 0; i < 4; ++i) {
+        const int q = q0 + 4 * tq + i;
+        if (q < Q) {
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+                src[(size_t)q * Kp + k0 + tk + 16 * j] =
+                    (acc[i][j][0] + acc[i][j][1]) + (acc[i][j][2] + acc[i][j][3]);
+        }
     }
 }
 
 cudaError_t launch_adj_source(const float* C_rm, const float* traces, const float* ystar, int n_lo, int ns,
                               int rec_base, int M, int R, int Kp, float* src, cudaStream_t st) {
-    if (ns < 1 || M < 1 || R < 1 || Kp < kSrcRows || Kp % kSrcRows != 0) return cudaErrorInvalidValue;
-    const size_t smem = (size_t)kSrcCols * ((R + 3) / 4) * sizeof(float4);
-    if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(adj_source_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)smem);
-        if (e != cudaSuccess) return e;
-    }
-    const dim3 grid(Kp / kSrcRows, (M + kSrcCols - 1) / kSrcCols, ns);
-    adj_source_kernel<<<grid, 256, smem, st>>>(C_rm, traces, ystar, n_lo, rec_base, M, R, Kp, src);
+    if (ns < 1 || M < 1 || R < 1 || Kp < kSrcT || Kp % kSrcT != 0) return cudaErrorInvalidValue;
+    const long long Q = (long long)ns * M;
+    const dim3 grid((unsigned)((Q + kSrcT - 1) / kSrcT), Kp / kSrcT);
+    adj_source_kernel<<<grid, 256, 0, st>>>(C_rm, traces, ystar, n_lo, ns, rec_base, M, R, Kp, src);
     return cudaGetLastError();
 }
 
