@@ -208,6 +208,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) rank2_tc_kernel(const TcArgs a)
     const uint32_t chunk_bytes = NA * kATileBytes + NX * xtile;
 
     long long it_prod = 0, it_mma = 0, it_rd = 0;  // chunk counters of producer / MMA / readers
+    // producer / MMA counters also as (ring stage, uses of that stage),
+    // advanced by one so that the per-chunk loops do no 64-bit division
+    int s_prod = 0, s_mma = 0;
+    uint32_t u_prod = 0, u_mma = 0;
     const int N = a.nsteps;
     for (int n = 0; n < N && !*abort_all; ++n) {
 #pragma unroll 1
@@ -222,9 +226,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) rank2_tc_kernel(const TcArgs a)
             if (warp == 0) {
                 if (lane == 0 && !*abort_flag) {
                     // ---- producer: stream every k-chunk's terms into the stage ring
-                    for (int kc = 0; kc < NKC; ++kc, ++it_prod) {
-                        const int s = (int)(it_prod % STAGES);
-                        const uint32_t use = (uint32_t)(it_prod / STAGES);
+                    for (int kc = 0; kc < NKC; ++kc) {
+                        const int s = s_prod;
+                        const uint32_t use = u_prod;
                         if (use > 0 && !mbarrier_wait(&empty[s], (use - 1) & 1, limit, abort_flag)) break;
                         unsigned char* st = smem + (size_t)s * stage_bytes;
                         mbarrier_arrive_expect_tx(&full[s], chunk_bytes);
@@ -234,15 +238,17 @@ __global__ void __launch_bounds__(kTcThreads, 1) rank2_tc_kernel(const TcArgs a)
                         for (int t = 0; t < NX; ++t)
                             bulk_g2s(st + NA * kATileBytes + t * xtile,
                                      Xsrc + (size_t)t * xterm + (size_t)kc * xtile, xtile, &full[s]);
+                        ++it_prod;
+                        if (++s_prod == STAGES) { s_prod = 0; ++u_prod; }
                     }
                 }
                 __syncwarp();
             } else if (warp == 1) {
                 if (lane == 0 && !*abort_flag) {
                     // ---- MMA issue: each chunk's split products into accumulator (chunk & 1)
-                    for (int kc = 0; kc < NKC; ++kc, ++it_mma) {
-                        const int s = (int)(it_mma % STAGES);
-                        const uint32_t use = (uint32_t)(it_mma / STAGES);
+                    for (int kc = 0; kc < NKC; ++kc) {
+                        const int s = s_mma;
+                        const uint32_t use = u_mma;
                         const int b = (int)(it_mma & 1);
                         const uint32_t ub = (uint32_t)(it_mma >> 1);
                         if (!mbarrier_wait(&full[s], use & 1, limit, abort_flag)) break;
@@ -262,6 +268,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) rank2_tc_kernel(const TcArgs a)
                         }
                         mma_commit(&empty[s]);
                         mma_commit(&dready[b]);
+                        ++it_mma;
+                        if (++s_mma == STAGES) { s_mma = 0; ++u_mma; }
                     }
                 }
                 __syncwarp();

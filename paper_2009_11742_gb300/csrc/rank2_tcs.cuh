@@ -159,6 +159,30 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, float (&v)[8]) {
     for (int q = 0; q < 8; ++q) v[q] = __uint_as_float(r[q]);
 }
 
+// The six digit products of one 16-deep k-step, issued from one asm block:
+// d0 += a0 x0, d1 += a0 x1 + a1 x0, d2 += a0 x2 + a1 x1 + a2 x0.  The
+// operands are given as the low words of their SW128 descriptors (the high
+// word, hi, is the same for every tile); acc0 / acc1 = 0 start d0 and d2 /
+// d1 afresh.
+__device__ __forceinline__ void tcs_mma6(uint32_t d0, uint32_t d1, uint32_t d2, uint32_t hi, uint32_t a0,
+                                         uint32_t a1, uint32_t a2, uint32_t x0, uint32_t x1, uint32_t x2,
+                                         uint32_t idesc, uint32_t acc0, uint32_t acc1) {
+    asm volatile(
+        "{\n\t.reg .pred p0, p1;\n\t.reg .b64 da0, da1, da2, dx0, dx1, dx2;\n\t"
+        "setp.ne.b32 p0, %11, 0;\n\tsetp.ne.b32 p1, %12, 0;\n\t"
+        "mov.b64 da0, {%4, %3};\n\tmov.b64 da1, {%5, %3};\n\tmov.b64 da2, {%6, %3};\n\t"
+        "mov.b64 dx0, {%7, %3};\n\tmov.b64 dx1, {%8, %3};\n\tmov.b64 dx2, {%9, %3};\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], da0, dx0, %10, p0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%1], da0, dx1, %10, p1;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%1], da1, dx0, %10, 1;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%2], da0, dx2, %10, p0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%2], da1, dx1, %10, 1;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%2], da2, dx0, %10, 1;\n\t}"
+        ::"r"(d0), "r"(d1), "r"(d2), "r"(hi), "r"(a0), "r"(a1), "r"(a2), "r"(x0), "r"(x1), "r"(x2),
+          "r"(idesc), "r"(acc0), "r"(acc1)
+        : "memory");
+}
+
 // Old state and carries of 8 columns of one row (zero outside the valid range).
 __device__ __forceinline__ void load_group8(const float* __restrict__ Y, const float* __restrict__ Cy,
                                             int Kown, int col_first, int ncol_left, bool rowok,
@@ -334,6 +358,10 @@ __global__ void __launch_bounds__(kTcsThreads, 1) rank2_tcs_kernel(const TcArgs 
     const uint32_t chunk_bytes = kTcsTerms * kATileBytes + kTcsTerms * xtile;
 
     long long it_prod = 0, it_mma = 0;  // chunk counters of producer / MMA
+    // the same counters as (ring stage, uses of that stage), advanced by one
+    // so that the per-chunk loops do no 64-bit division
+    int s_prod = 0, s_mma = 0;
+    uint32_t u_prod = 0, u_mma = 0;
     int hs = 0;                         // half-steps done (parity of dready)
     const int N = a.nsteps;
     for (int n = 0; n < N && !*abort_all; ++n) {
@@ -371,9 +399,9 @@ __global__ void __launch_bounds__(kTcsThreads, 1) rank2_tcs_kernel(const TcArgs 
             if (warp == 0) {
                 if (lane == 0 && !*abort_flag) {
                     // ---- producer: stream every k-chunk's digit tiles into the stage ring
-                    for (int kc = 0; kc < NKC; ++kc, ++it_prod) {
-                        const int s = (int)(it_prod % STAGES);
-                        const uint32_t use = (uint32_t)(it_prod / STAGES);
+                    for (int kc = 0; kc < NKC; ++kc) {
+                        const int s = s_prod;
+                        const uint32_t use = u_prod;
                         if (use > 0 && !mbarrier_wait(&empty[s], (use - 1) & 1, limit, abort_flag)) break;
                         unsigned char* st = smem + (size_t)s * stage_bytes;
                         mbarrier_arrive_expect_tx(&full[s], chunk_bytes);
@@ -383,45 +411,45 @@ __global__ void __launch_bounds__(kTcsThreads, 1) rank2_tcs_kernel(const TcArgs 
                         for (int t = 0; t < kTcsTerms; ++t)
                             bulk_g2s(st + kTcsTerms * kATileBytes + t * xtile,
                                      Xsrc + (size_t)t * xterm + (size_t)kc * xtile, xtile, &full[s]);
+                        ++it_prod;
+                        if (++s_prod == STAGES) { s_prod = 0; ++u_prod; }
                     }
                 }
                 __syncwarp();
             } else if (warp == 1) {
                 if (lane == 0 && !*abort_flag) {
-                    // ---- MMA issue: the six digit products of every chunk
+                    // ---- MMA issue: the six digit products of every chunk.  The
+                    //      descriptors differ only in their start-address field, so
+                    //      their low words are formed by adding tile offsets (in
+                    //      16-byte units) to that of the ring's first tile.
                     bool ok = true;
-                    for (int kc = 0; kc < NKC; ++kc, ++it_mma) {
-                        const int s = (int)(it_mma % STAGES);
-                        const uint32_t use = (uint32_t)(it_mma / STAGES);
+                    const uint64_t dring = sw128_desc(cvta_shared(smem));
+                    const uint32_t dhi = (uint32_t)(dring >> 32), dlo = (uint32_t)dring;
+                    const uint32_t ta = kATileBytes >> 4, tx = xtile >> 4;
+                    const uint32_t tstage = (uint32_t)(stage_bytes >> 4);
+                    for (int kc = 0; kc < NKC; ++kc) {
+                        const int s = s_mma;
+                        const uint32_t use = u_mma;
                         if (!mbarrier_wait(&full[s], use & 1, limit, abort_flag)) { ok = false; break; }
                         tc_fence_after();
-                        const uint32_t sA = cvta_shared(smem + (size_t)s * stage_bytes);
-                        const uint32_t sX = sA + kTcsTerms * kATileBytes;
+                        const uint32_t la = dlo + (uint32_t)s * tstage;
+                        const uint32_t lx = la + kTcsTerms * ta;
                         const bool t1b = two_t1 && kc >= KC_T1B;
                         const uint32_t d0 = tbase;
                         const uint32_t d1 = tbase + (uint32_t)((t1b ? 2 : 1) * AST);
                         const uint32_t d2 = tbase + (uint32_t)(3 * AST);
                         const bool first0 = kc == 0;
                         const bool first1 = kc == (t1b ? KC_T1B : 0);
-#pragma unroll 1
+#pragma unroll
                         for (int ks = 0; ks < 4; ++ks) {  // four 16-deep K steps per 128-byte chunk
-                            const uint32_t ko = 32u * ks;
-                            const uint64_t a0 = sw128_desc(sA + ko);
-                            const uint64_t a1 = sw128_desc(sA + kATileBytes + ko);
-                            const uint64_t a2 = sw128_desc(sA + 2 * kATileBytes + ko);
-                            const uint64_t x0 = sw128_desc(sX + ko);
-                            const uint64_t x1 = sw128_desc(sX + xtile + ko);
-                            const uint64_t x2 = sw128_desc(sX + 2 * xtile + ko);
-                            const uint32_t acc0 = (first0 && ks == 0) ? 0u : 1u;
-                            const uint32_t acc1 = (first1 && ks == 0) ? 0u : 1u;
-                            mma_issue<false>(d0, a0, x0, idesc, acc0);
-                            mma_issue<false>(d1, a0, x1, idesc, acc1);
-                            mma_issue<false>(d1, a1, x0, idesc, 1u);
-                            mma_issue<false>(d2, a0, x2, idesc, acc0);
-                            mma_issue<false>(d2, a1, x1, idesc, 1u);
-                            mma_issue<false>(d2, a2, x0, idesc, 1u);
+                            const uint32_t o = 2u * ks;     // 32 bytes
+                            tcs_mma6(d0, d1, d2, dhi, la + o, la + ta + o, la + 2 * ta + o, lx + o, lx + tx + o,
+                                     lx + 2 * tx + o, idesc, (first0 && ks == 0) ? 0u : 1u,
+                                     (first1 && ks == 0) ? 0u : 1u);
                         }
                         mma_commit(&empty[s]);
+                        ++it_mma;
+                        if (++s_mma == STAGES) { s_mma = 0; ++u_mma; }
                     }
                     if (ok) mma_commit(dready);
                 }
