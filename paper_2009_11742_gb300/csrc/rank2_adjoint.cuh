@@ -18,10 +18,12 @@
 // kernel does there; the adjoint state is Kahan-compensated.  FP64 (the
 // check path, Kp <= 512, one tile per CTA): resident up to Kp = 256 and
 // read from L2 per half-step above, plain sums, as the FP64 forward kernel.
-// Half A's epilogue adds the rank-R source 2 C^T r^{n+1} (C columns of the
-// CTA's rows and the step's residuals staged in shared memory), and a
-// deterministic per-CTA column reduction accumulates the period gradient.
-// The split-role kernel below (FP32, Kp <= 512) is the faster form there.
+// Half A's epilogue adds the rank-R source 2 C^T r^{n+1}: in FP32 read
+// precomputed for the launch's range of steps (adj_source_kernel) and copied
+// one step ahead; in FP64 formed from C's columns of the CTA's rows and the
+// step's residual staged in shared memory.  A deterministic per-CTA column
+// reduction accumulates the period gradient.  The split-role kernel below
+// (FP32, Kp <= 512) is the faster form there.
 #pragma once
 
 #include <cooperative_groups.h>
@@ -38,25 +40,30 @@ namespace romk {
 constexpr int kAdjTab = 64;
 
 struct AdjSmem {
-    size_t Vf, Sf, cV, cS, Ccol, rbuf, trS, ysS, g, T, gT, dfT, total;
+    size_t Vf, Sf, cV, cS, Ccol, rbuf, trS, ysS, src, g, T, gT, dfT, total;
 };
 
 // nrt: 32-row tiles owned per CTA (1 for Kp <= 512, 2 above); T the element
-// type (the carries are FP32 and only the FP32 path has them).
+// type (the carries are FP32 and only the FP32 path has them).  FP32 reads
+// the source term precomputed (src: two step buffers of Wa x own rows); FP64
+// forms it from C's columns and the staged residual (Ccol .. ysS).
 template <typename T>
 __host__ __device__ inline AdjSmem adj_smem_layout(int Wa, int Kp, int R, int nrt = 1) {
+    constexpr bool F32 = sizeof(T) == 4;
     AdjSmem s{};
     const size_t own = (size_t)nrt * kRowsPerCta;
-    const size_t ncarry = sizeof(T) == 4 ? (size_t)Wa * own : 0;
+    const size_t ncarry = F32 ? (size_t)Wa * own : 0;
+    const size_t nres = F32 ? 0 : (size_t)R;
     size_t o = 0;
     s.Vf = o;   o += align16((size_t)Wa * Kp * sizeof(T));
     s.Sf = o;   o += align16((size_t)Wa * Kp * sizeof(T));
     s.cV = o;   o += align16(ncarry * sizeof(float));
     s.cS = o;   o += align16(ncarry * sizeof(float));
-    s.Ccol = o; o += align16((size_t)R * own * sizeof(T));
-    s.rbuf = o; o += align16((size_t)R * Wa * sizeof(T));
-    s.trS = o;  o += align16((size_t)R * Wa * sizeof(T));   // next step's traces, in flight
-    s.ysS = o;  o += align16((size_t)R * Wa * sizeof(T));   // and targets
+    s.Ccol = o; o += align16(nres * own * sizeof(T));
+    s.rbuf = o; o += align16(nres * Wa * sizeof(T));
+    s.trS = o;  o += align16(nres * Wa * sizeof(T));   // next step's traces, in flight
+    s.ysS = o;  o += align16(nres * Wa * sizeof(T));   // and targets
+    s.src = o;  o += align16((F32 ? 2 * (size_t)Wa * own : 0) * sizeof(float));
     s.g = o;    o += align16(own * sizeof(T));
     s.T = o;    o += align16((size_t)Wa * sizeof(T));
     s.gT = o;   o += align16((size_t)Wa * sizeof(T));
@@ -118,14 +125,13 @@ __device__ __forceinline__ void adj_half_a(const T (&op)[2][4 * KI], const T* __
 // Half A in the 4-row, 32-lane form of the work-list kernel (FP32 with the
 // operators streamed from L2): warp w holds rows 4w .. 4w + 3 of the tile,
 // lane l the k values 128 i + 4 l + q (k < Kp); the epilogue adds
-// 2 C_own^T r as above.
+// 2 C_own^T r, read precomputed from asrc ([Wa][sstride], the tile's rows).
 template <int KQ>
 __device__ __forceinline__ void wl_adj_half_a(const float (&op)[4][4 * KQ], const float* __restrict__ X,
                                               float* __restrict__ Y, float* __restrict__ comp,
-                                              const float* __restrict__ Ccol, const int cstride,
-                                              const float* __restrict__ rbuf, const int R, const float dt,
-                                              const int Wa, const int Kp, const int row0, const int warp,
-                                              const int lane) {
+                                              const float* __restrict__ asrc, const int sstride,
+                                              const float dt, const int Wa, const int Kp, const int row0,
+                                              const int warp, const int lane) {
     constexpr int CB = 8;
     for (int c0 = 0; c0 < Wa; c0 += CB) {
         float acc[4][CB];
@@ -155,9 +161,7 @@ __device__ __forceinline__ void wl_adj_half_a(const float (&op)[4][4 * KQ], cons
         const float tot = reduce_scatter32(v, lane, vi);
         const int rl = 4 * warp + vi / CB;
         const int c = c0 + vi % CB;
-        float src = 0.f;
-        for (int jr = 0; jr < R; ++jr) src = __fmaf_rn(Ccol[jr * cstride + rl], rbuf[jr * Wa + c], src);
-        const float inc = __fmaf_rn(tot, dt, 2.f * src);
+        const float inc = __fmaf_rn(tot, dt, 2.f * asrc[c * sstride + rl]);
         float* yp = Y + (size_t)c * Kp + row0 + rl;
         *yp = kahan_add(*yp, inc, comp[c * kRowsPerCta + rl]);
     }
@@ -209,6 +213,7 @@ __global__ void __launch_bounds__(kThreads, 1) rank2_adjoint_kernel(const AdjArg
     T* rbuf = reinterpret_cast<T*>(smem + L.rbuf);  // [R][Wa]: residual of the step
     T* trS = reinterpret_cast<T*>(smem + L.trS);    // [R][Wa]: C V^{n+1} of the next step
     T* ysS = reinterpret_cast<T*>(smem + L.ysS);    // [R][Wa]: its target
+    float* srcS = reinterpret_cast<float*>(smem + L.src);  // FP32: [2][Wa][OWN] C^T r, by step parity
     T* gown = reinterpret_cast<T*>(smem + L.g);
     T* Tcol = reinterpret_cast<T*>(smem + L.T);
     T* gTacc = reinterpret_cast<T*>(smem + L.gT);
@@ -227,7 +232,7 @@ __global__ void __launch_bounds__(kThreads, 1) rank2_adjoint_kernel(const AdjArg
         cV[idx] = (c < ncol && row < a.Kv) ? a.compV[(size_t)(col0 + c) * a.Kv + row] : 0.f;
         cS[idx] = (c < ncol && row < a.Ks) ? a.compS[(size_t)(col0 + c) * a.Ks + row] : 0.f;
     }
-    for (int idx = tid; idx < R * OWN; idx += kThreads) {
+    for (int idx = tid; idx < (F32 ? 0 : R * OWN); idx += kThreads) {
         const int jr = idx / OWN, ro = idx % OWN;
         Ccol[idx] = ro < own_rows ? a.C_rm[(size_t)jr * Kp + row0 + ro] : T(0);
     }
@@ -259,7 +264,22 @@ __global__ void __launch_bounds__(kThreads, 1) rank2_adjoint_kernel(const AdjArg
             cp_async_elem<T>(ysS + idx, a.ystar + ((size_t)n * a.M + col0 + cc) * R + jr, ok);
         }
     };
-    if (a.n_hi > a.n_lo) prefetch_residual(a.n_hi - 1);
+    // FP32: the own rows' C^T r of reverse step n (precomputed for the range)
+    // into step buffer pb, 16 bytes per copy, zero for absent columns and rows
+    auto prefetch_src = [&](int n, int pb) {
+        float* dst = srcS + (size_t)pb * Wa * OWN;
+        for (int idx = tid; idx < Wa * (OWN / 4); idx += kThreads) {
+            const int c = idx / (OWN / 4), ro = 4 * (idx % (OWN / 4));
+            const bool ok = c < ncol && ro < own_rows;
+            const float* gsrc = ok ? a.src + ((size_t)(n - a.n_lo) * a.M + col0 + c) * Kp + row0 + ro
+                                   : a.src;  // a valid address for the zero fill
+            cp_async16(dst + (size_t)c * OWN + ro, gsrc, ok ? 16 : 0);
+        }
+    };
+    if (a.n_hi > a.n_lo) {
+        if constexpr (F32) prefetch_src(a.n_hi - 1, 0);
+        else prefetch_residual(a.n_hi - 1);
+    }
     cluster.sync();
 
     for (int n = a.n_hi - 1; n >= a.n_lo; --n) {
@@ -277,21 +297,28 @@ __global__ void __launch_bounds__(kThreads, 1) rank2_adjoint_kernel(const AdjArg
             }
         }
         const T* dfn = dfT + (done % kAdjTab) * Wa;
+        // FP32: this step's C^T r, copied one step earlier into buffer done & 1;
+        // the next step's copies go to the other buffer, whose last readers
+        // passed the cluster barriers of the previous step.  FP64: the
         // residual r^{n+1} = C V^{n+1} - ystar^{n+1} of this block's columns
-        // (zero past ncol), from the copies issued one step earlier; then the
-        // next step's copies start
+        // (zero past ncol) from the copies issued one step earlier.
         cp_async_wait_all();
         __syncthreads();
-        for (int idx = tid; idx < R * Wa; idx += kThreads) rbuf[idx] = trS[idx] - ysS[idx];
-        __syncthreads();
-        if (n > a.n_lo) prefetch_residual(n - 1);
+        if constexpr (F32) {
+            if (n > a.n_lo) prefetch_src(n - 1, (done + 1) & 1);
+        } else {
+            for (int idx = tid; idx < R * Wa; idx += kThreads) rbuf[idx] = trS[idx] - ysS[idx];
+            __syncthreads();
+            if (n > a.n_lo) prefetch_residual(n - 1);
+        }
         // ---- half A: lamV <- lamV + 2 C^T r^{n+1} + dt Asv^T lamS
         for (int rt = 0; rt < nrt_own; ++rt) {
             const int rowt = row0 + rt * kRowsPerCta;
             if constexpr (GEN) {
                 if (!RES) wl_load_op<KQ>(opQA, a.opA_rm, Kp, rowt + 4 * warp, lane);
-                wl_adj_half_a<KQ>(opQA, Sf, Vf, cV + rt * Wa * kRowsPerCta, Ccol + rt * kRowsPerCta, OWN,
-                                  rbuf, R, dt, Wa, Kp, rowt, warp, lane);
+                wl_adj_half_a<KQ>(opQA, Sf, Vf, cV + rt * Wa * kRowsPerCta,
+                                  srcS + (size_t)(done & 1) * Wa * OWN + rt * kRowsPerCta, OWN, dt, Wa, Kp,
+                                  rowt, warp, lane);
             } else {
                 if (!RES) load_op_rows<T, KI>(opA, a.opA_rm, Kp, rowt + 2 * rp, j);
                 adj_half_a<T, KI, CB>(opA, Sf, Vf, cV + rt * Wa * kRowsPerCta, Ccol + rt * kRowsPerCta, OWN,
@@ -453,7 +480,8 @@ __global__ void __launch_bounds__(kThreads, 1) rank2_adjoint_split_kernel(const 
         for (int idx = tid; idx < Wa * (kSplitRows / 4); idx += kThreads) {
             const int c = idx / (kSplitRows / 4), piece = idx % (kSplitRows / 4);
             const bool ok = c < ncol(b);
-            const float* gsrc = a.src + ((size_t)(n - a.n_lo) * M + gc0(b) + (ok ? c : 0)) * Kp + row0 + 4 * piece;
+            const float* gsrc = ok ? a.src + ((size_t)(n - a.n_lo) * M + gc0(b) + c) * Kp + row0 + 4 * piece
+                                   : a.src;  // a valid address for the zero fill
             cp_async16(dst + (size_t)c * kOwnStride + 4 * piece, gsrc, ok ? 16 : 0);
         }
     };

@@ -1864,11 +1864,9 @@ AdjLayout adjoint_layout(const rom_s* h, int M, int nsteps, int ckpt_every, size
     L.acomp = o;  o += al(sizeof(float) * kvm);
     L.gtp = o;    o += al(es * 16 * (size_t)M);
     L.acc = o;    o += al(sizeof(double) * 2);
-    // FP32 up to Kp = 512 (the split-role reverse kernel): the source term of
-    // up to kAdjSrcSteps reverse steps
+    // FP32: the source term of one launch range of reverse steps
     L.src = o;
-    if (es == 4 && h->Kp <= 512)
-        o += al(sizeof(float) * (size_t)(L.seg < kAdjSrcSteps ? L.seg : kAdjSrcSteps) * M * h->Kp);
+    if (es == 4) o += al(sizeof(float) * (size_t)adj_src_steps(M, h->Kp, L.seg) * M * h->Kp);
     L.total = o;
     return L;
 }
@@ -1968,11 +1966,12 @@ rom_status adjoint_run(rom_s* h, const void* V0, const void* S0, const void* Tp,
         aa.Kp = h->Kp;
         aa.R = h->R;
         aa.M = M;
-        if (F32 && ap.split) {
-            // the split-role kernel reads the source term precomputed for at
-            // most kAdjSrcSteps steps: the segment's latest steps first
+        if (F32) {
+            // the FP32 reverse kernels read the source term precomputed for a
+            // range of steps: the segment's latest steps first
+            const int nsrc = adj_src_steps(M, h->Kp, L.seg);
             for (int hi = n_start + len; hi > n_start && e == cudaSuccess;) {
-                const int lo = hi - kAdjSrcSteps > n_start ? hi - kAdjSrcSteps : n_start;
+                const int lo = hi - nsrc > n_start ? hi - nsrc : n_start;
                 e = launch_adj_source(static_cast<const float*>(h->C_rm[1]), reinterpret_cast<const float*>(traces),
                                       reinterpret_cast<const float*>(ys), lo, hi - lo, aa.rec_base, M, h->R,
                                       h->Kp, asrc, st);

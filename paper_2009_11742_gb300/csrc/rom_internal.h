@@ -204,7 +204,7 @@ struct AdjArgsT {
     const T* traces;  // forward records: record k = C V^{rec_base + k}, [k][m][j]
     const T* ystar;   // targets: record n = ystar^{n+1}, [n][m][j]
     T* gTpart;        // cs x M per-CTA partial dL/dT (in/out)
-    const float* src; // split-role kernel: C^T r of the range's steps, [n - n_lo][m][Kp]
+    const float* src; // FP32: C^T r of the range's steps, [n - n_lo][m][Kp] (adj_source_kernel)
     int* status;
     double dt;
     long long n0;
@@ -228,7 +228,17 @@ cudaError_t launch_adjoint(const AdjArgsT<double>& a, const AdjPlan& p, cudaStre
 // The reverse step's source term, hoisted out of the recurrence for the
 // split-role kernel: src[s][m][k] = sum_jr C[jr][k] r[jr] with r = traces of
 // record n + 1 - rec_base minus ystar of step n, n = n_lo + s, s < ns.
-constexpr int kAdjSrcSteps = 64;  // reverse steps per launch of the split-role kernel
+constexpr int kAdjSrcSteps = 64;  // most reverse steps per launch of the FP32 reverse kernels
+// Reverse steps per launch range for M columns of Kp rows within a segment of
+// seg steps: at most kAdjSrcSteps, and the source buffer (steps x M x Kp
+// floats) within about 64 MB.
+inline int adj_src_steps(int M, int Kp, int seg) {
+    const long long per = (long long)M * Kp * 4;
+    long long s = per > 0 ? (64ll << 20) / per : kAdjSrcSteps;
+    if (s > kAdjSrcSteps) s = kAdjSrcSteps;
+    if (s > seg) s = seg;
+    return s < 1 ? 1 : (int)s;
+}
 cudaError_t launch_adj_source(const float* C_rm, const float* traces, const float* ystar, int n_lo, int ns,
                               int rec_base, int M, int R, int Kp, float* src, cudaStream_t st);
 cudaError_t launch_sum_partials(const float* part, int cs, int M, float* out, cudaStream_t st);
