@@ -63,9 +63,10 @@ def gpu_adjoint(R, h, p, V0, S0, ystar, N, ckpt):
 
 @pytest.mark.parametrize("Kv,Ks,M,R,N,ckpt", [(64, 64, 7, 3, 60, 0), (64, 64, 7, 3, 60, 16),
                                                (200, 180, 20, 5, 100, 32), (512, 512, 9, 8, 40, 7),
-                                               # one receiver, and more receivers than rows per CTA
-                                               # (receiver-contiguous buffers of stride 4 and 100)
+                                               # one receiver, more receivers than rows per CTA, and
+                                               # more than K (the source term in chunks of 64)
                                                (128, 96, 5, 1, 30, 0), (256, 256, 10, 100, 30, 8),
+                                               (128, 128, 6, 300, 20, 0),
                                                # above K = 512: two 32-row tiles per CTA, the
                                                # transposed operators read from L2
                                                (640, 600, 11, 5, 36, 0), (1024, 1000, 6, 8, 40, 16),
@@ -90,6 +91,25 @@ def test_checkpointed_equals_stored_traces_bitwise(rom):
     h = rom.Rom.from_problem(p)
     a = gpu_adjoint(rom, h, p, V0, S0, ystar, 90, 0)
     b = gpu_adjoint(rom, h, p, V0, S0, ystar, 90, 20)
+    assert abs(a[0] - b[0]) <= 1e-13 * abs(a[0])
+    for x, y in zip(a[1:], b[1:]):
+        np.testing.assert_array_equal(x, y)
+
+
+def test_source_ranges_do_not_change_the_gradients(rom):
+    """K = 1024, M = 300: the precomputed source term of one launch range is
+    capped at 64 MB, so every trace kept (c = 0) runs ranges of 54, 54 and 12
+    steps while c = 40 runs ranges of 40; the gradients are bitwise equal."""
+    Kv = Ks = 1024
+    M, R, N = 300, 8, 120
+    p = inputs.make_problem(Kv, Ks, M, R, seed=13)
+    V0 = inputs.random_state(Kv, M, seed=14, scale=0.2)
+    S0 = inputs.random_state(Ks, M, seed=15, scale=0.2)
+    ystar = inputs.random_state(N * R, M, seed=16, scale=0.1).reshape(N, R, M)
+    h = rom.Rom.from_problem(p)
+    a = gpu_adjoint(rom, h, p, V0, S0, ystar, N, 0)
+    b = gpu_adjoint(rom, h, p, V0, S0, ystar, N, 40)
+    assert np.isfinite(a[0]) and a[0] > 0
     assert abs(a[0] - b[0]) <= 1e-13 * abs(a[0])
     for x, y in zip(a[1:], b[1:]):
         np.testing.assert_array_equal(x, y)
