@@ -93,7 +93,8 @@ def test_tc_small_vs_oracle(rom, prec, Kv, Ks, M, R, N, r):
 @pytest.mark.parametrize("prec", ["tf32x3", "bf16x3", "bf16", "bf16s"])
 @pytest.mark.parametrize("Kv,Ks,M,R,N,r", [(1, 1, 1, 1, 100, 1),       # K = 1, M = 1: one padded tile, one column
                                            (256, 130, 33, 0, 90, 0),   # no receivers, Ks < Kv
-                                           (130, 256, 129, 3, 60, 60)])  # Kv < Ks, one column past two blocks, one record
+                                           (130, 256, 129, 3, 60, 60),  # Kv < Ks, one column past two blocks, one record
+                                           (256, 256, 48, 100, 40, 5)])  # R > 64: traces from global V
 def test_tc_edge_shapes_vs_oracle(rom, prec, Kv, Ks, M, R, N, r):
     p = inputs.make_problem(Kv, Ks, M, R, seed=Kv + 2 * M + 5)
     h = rom.Rom.from_problem(p)
