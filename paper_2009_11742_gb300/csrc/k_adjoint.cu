@@ -173,67 +173,68 @@ cudaError_t launch_adjoint(const AdjArgsT<double>& a, const AdjPlan& p, cudaStre
 // misfit's derivative enters the adjoint of V through C^T):
 //   src[q][k] = sum_jr C[jr][k] (traces[n + 1 - rec_base][m][jr] - ystar[n][m][jr]),
 // q = s M + m, n = n_lo + s.  It does not depend on the adjoint state, so the
-// split-role kernel reads it instead of forming it on its critical path.
-// Four chains over jr = 4 u + e, summed as (c0 + c1) + (c2 + c3): the order
-// the reverse kernels use.  It is a (ns M) x Kp x R product, tiled as one:
-// a block takes 64 rows q x 64 columns k, stages 64 receivers at a time of
-// the residual rows and of C (k-major) in shared memory, and thread
-// (tq, tk) = (t / 16, t % 16) accumulates rows 4 tq + i and columns
-// tk + 16 j (i, j < 4), so that one 16-byte read of each operand feeds 16
-// multiply-adds and the C reads of a quarter warp fall in distinct banks.
-constexpr int kSrcT = 64;                // rows q and columns k per block
-constexpr int kSrcJ = 64;                // receivers per shared-memory chunk
-constexpr int kSrcStride = kSrcJ + 4;    // 17 16-byte groups per row (odd)
+// reverse kernels read it instead of forming it on their critical path.
+// Four chains over jr = 4 u + e, summed as (c0 + c1) + (c2 + c3).  It is a
+// (ns M) x Kp x R product, tiled as one: a block takes 64 rows q x 64
+// columns k, stages J receivers at a time of the residual rows and of C
+// (k-major) in shared memory, and thread (tq, tk) = (t / 16, t % 16)
+// accumulates rows 4 tq + i and columns tk + 16 j (i, j < 4), so that one
+// read of four receivers of each operand feeds 16 multiply-adds.  FP32: J =
+// 64 and a row stride of 17 16-byte groups (odd), so that the C reads of a
+// quarter warp fall in distinct banks; FP64: J = 32 (static shared memory).
+constexpr int kSrcT = 64;  // rows q and columns k per block
+template <typename T>
+struct AdjSrcTile {
+    static constexpr int J = sizeof(T) == 4 ? 64 : 32;  // receivers per chunk
+    static constexpr int S = J + 4;                     // row stride (elements)
+};
 
-__global__ void __launch_bounds__(256) adj_source_kernel(const float* __restrict__ C_rm,
-                                                         const float* __restrict__ traces,
-                                                         const float* __restrict__ ystar, int n_lo, int ns,
-                                                         int rec_base, int M, int R, int Kp,
-                                                         float* __restrict__ src) {
-    __shared__ __align__(16) float Rs[kSrcT * kSrcStride];  // [q][jr] residual rows
-    __shared__ __align__(16) float Cs[kSrcT * kSrcStride];  // [k][jr] C columns
+template <typename T>
+__global__ void __launch_bounds__(256) adj_source_kernel(const T* __restrict__ C_rm, const T* __restrict__ traces,
+                                                         const T* __restrict__ ystar, int n_lo, int ns,
+                                                         int rec_base, int M, int R, int Kp, T* __restrict__ src) {
+    constexpr int J = AdjSrcTile<T>::J, ST = AdjSrcTile<T>::S;
+    __shared__ __align__(16) T Rs[kSrcT * ST];  // [q][jr] residual rows
+    __shared__ __align__(16) T Cs[kSrcT * ST];  // [k][jr] C columns
     const int Q = ns * M;
     const int q0 = blockIdx.x * kSrcT, k0 = blockIdx.y * kSrcT;
     const int t = threadIdx.x, tq = t / 16, tk = t % 16;
-    float acc[4][4][4];
+    T acc[4][4][4];
 #pragma unroll
     for (int i = 0; i < 4; ++i)
 #pragma unroll
         for (int j = 0; j < 4; ++j)
 #pragma unroll
-            for (int e = 0; e < 4; ++e) acc[i][j][e] = 0.f;
-    for (int j0 = 0; j0 < R; j0 += kSrcJ) {
+            for (int e = 0; e < 4; ++e) acc[i][j][e] = T(0);
+    for (int j0 = 0; j0 < R; j0 += J) {
         __syncthreads();  // the previous chunk's reads are done
-        for (int idx = t; idx < kSrcT * kSrcJ; idx += blockDim.x) {
-            const int r = idx / kSrcJ, jj = idx % kSrcJ, jr = j0 + jj, q = q0 + r;
-            float v = 0.f;
+        for (int idx = t; idx < kSrcT * J; idx += blockDim.x) {
+            const int r = idx / J, jj = idx % J, jr = j0 + jj, q = q0 + r;
+            T v = T(0);
             if (q < Q && jr < R) {
                 const int sq = q / M, m = q - sq * M, n = n_lo + sq;
                 v = traces[((size_t)(n + 1 - rec_base) * M + m) * R + jr] - ystar[((size_t)n * M + m) * R + jr];
             }
-            Rs[r * kSrcStride + jj] = v;
+            Rs[r * ST + jj] = v;
         }
-        for (int idx = t; idx < kSrcJ * kSrcT; idx += blockDim.x) {
+        for (int idx = t; idx < J * kSrcT; idx += blockDim.x) {
             const int jj = idx / kSrcT, kk = idx % kSrcT, jr = j0 + jj;
-            Cs[kk * kSrcStride + jj] = jr < R ? C_rm[(size_t)jr * Kp + k0 + kk] : 0.f;
+            Cs[kk * ST + jj] = jr < R ? C_rm[(size_t)jr * Kp + k0 + kk] : T(0);
         }
         __syncthreads();
-        const int nu = min(kSrcJ, R - j0 + 3) / 4;  // receiver quads of the chunk below R
+        const int nu = min(J, R - j0 + 3) / 4;  // receiver quads of the chunk below R
         for (int u = 0; u < nu; ++u) {
-            float4 rv[4], cv[4];
+            T rv[4][4], cv[4][4];
 #pragma unroll
-            for (int i = 0; i < 4; ++i) rv[i] = *reinterpret_cast<const float4*>(Rs + (4 * tq + i) * kSrcStride + 4 * u);
+            for (int i = 0; i < 4; ++i) load4(Rs + (4 * tq + i) * ST + 4 * u, rv[i]);
 #pragma unroll
-            for (int j = 0; j < 4; ++j) cv[j] = *reinterpret_cast<const float4*>(Cs + (tk + 16 * j) * kSrcStride + 4 * u);
+            for (int j = 0; j < 4; ++j) load4(Cs + (tk + 16 * j) * ST + 4 * u, cv[j]);
 #pragma unroll
             for (int i = 0; i < 4; ++i)
 #pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    acc[i][j][0] = __fmaf_rn(cv[j].x, rv[i].x, acc[i][j][0]);
-                    acc[i][j][1] = __fmaf_rn(cv[j].y, rv[i].y, acc[i][j][1]);
-                    acc[i][j][2] = __fmaf_rn(cv[j].z, rv[i].z, acc[i][j][2]);
-                    acc[i][j][3] = __fmaf_rn(cv[j].w, rv[i].w, acc[i][j][3]);
-                }
+                for (int j = 0; j < 4; ++j)
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) acc[i][j][e] = fmadd(cv[j][e], rv[i][e], acc[i][j][e]);
         }
     }
 #pragma unroll
@@ -248,13 +249,22 @@ __global__ void __launch_bounds__(256) adj_source_kernel(const float* __restrict
     }
 }
 
-cudaError_t launch_adj_source(const float* C_rm, const float* traces, const float* ystar, int n_lo, int ns,
-                              int rec_base, int M, int R, int Kp, float* src, cudaStream_t st) {
+template <typename T>
+static cudaError_t launch_adj_source_t(const T* C_rm, const T* traces, const T* ystar, int n_lo, int ns,
+                                       int rec_base, int M, int R, int Kp, T* src, cudaStream_t st) {
     if (ns < 1 || M < 1 || R < 1 || Kp < kSrcT || Kp % kSrcT != 0) return cudaErrorInvalidValue;
     const long long Q = (long long)ns * M;
     const dim3 grid((unsigned)((Q + kSrcT - 1) / kSrcT), Kp / kSrcT);
-    adj_source_kernel<<<grid, 256, 0, st>>>(C_rm, traces, ystar, n_lo, ns, rec_base, M, R, Kp, src);
+    adj_source_kernel<T><<<grid, 256, 0, st>>>(C_rm, traces, ystar, n_lo, ns, rec_base, M, R, Kp, src);
     return cudaGetLastError();
+}
+cudaError_t launch_adj_source(const float* C_rm, const float* traces, const float* ystar, int n_lo, int ns,
+                              int rec_base, int M, int R, int Kp, float* src, cudaStream_t st) {
+    return launch_adj_source_t<float>(C_rm, traces, ystar, n_lo, ns, rec_base, M, R, Kp, src, st);
+}
+cudaError_t launch_adj_source(const double* C_rm, const double* traces, const double* ystar, int n_lo, int ns,
+                              int rec_base, int M, int R, int Kp, double* src, cudaStream_t st) {
+    return launch_adj_source_t<double>(C_rm, traces, ystar, n_lo, ns, rec_base, M, R, Kp, src, st);
 }
 
 // out[m] = sum over CTAs (in rank order) of part[rank][m].

@@ -18,12 +18,11 @@
 // kernel does there; the adjoint state is Kahan-compensated.  FP64 (the
 // check path, Kp <= 512, one tile per CTA): resident up to Kp = 256 and
 // read from L2 per half-step above, plain sums, as the FP64 forward kernel.
-// Half A's epilogue adds the rank-R source 2 C^T r^{n+1}: in FP32 read
-// precomputed for the launch's range of steps (adj_source_kernel) and copied
-// one step ahead; in FP64 formed from C's columns of the CTA's rows and the
-// step's residual staged in shared memory.  A deterministic per-CTA column
-// reduction accumulates the period gradient.  The split-role kernel below
-// (FP32, Kp <= 512) is the faster form there.
+// Half A's epilogue adds the rank-R source 2 C^T r^{n+1}, read precomputed
+// for the launch's range of steps (adj_source_kernel) and copied one step
+// ahead.  A deterministic per-CTA column reduction accumulates the period
+// gradient.  The split-role kernel below (FP32, Kp <= 512) is the faster
+// form there.
 #pragma once
 
 #include <cooperative_groups.h>
@@ -40,30 +39,25 @@ namespace romk {
 constexpr int kAdjTab = 64;
 
 struct AdjSmem {
-    size_t Vf, Sf, cV, cS, Ccol, rbuf, trS, ysS, src, g, T, gT, dfT, total;
+    size_t Vf, Sf, cV, cS, src, g, T, gT, dfT, total;
 };
 
 // nrt: 32-row tiles owned per CTA (1 for Kp <= 512, 2 above); T the element
-// type (the carries are FP32 and only the FP32 path has them).  FP32 reads
-// the source term precomputed (src: two step buffers of Wa x own rows); FP64
-// forms it from C's columns and the staged residual (Ccol .. ysS).
+// type (the carries are FP32 and only the FP32 path has them).  The source
+// term arrives precomputed (src: two step buffers of Wa x own rows), so the
+// layout does not depend on R.
 template <typename T>
 __host__ __device__ inline AdjSmem adj_smem_layout(int Wa, int Kp, int R, int nrt = 1) {
-    constexpr bool F32 = sizeof(T) == 4;
+    (void)R;
     AdjSmem s{};
     const size_t own = (size_t)nrt * kRowsPerCta;
-    const size_t ncarry = F32 ? (size_t)Wa * own : 0;
-    const size_t nres = F32 ? 0 : (size_t)R;
+    const size_t ncarry = sizeof(T) == 4 ? (size_t)Wa * own : 0;
     size_t o = 0;
     s.Vf = o;   o += align16((size_t)Wa * Kp * sizeof(T));
     s.Sf = o;   o += align16((size_t)Wa * Kp * sizeof(T));
     s.cV = o;   o += align16(ncarry * sizeof(float));
     s.cS = o;   o += align16(ncarry * sizeof(float));
-    s.Ccol = o; o += align16(nres * own * sizeof(T));
-    s.rbuf = o; o += align16(nres * Wa * sizeof(T));
-    s.trS = o;  o += align16(nres * Wa * sizeof(T));   // next step's traces, in flight
-    s.ysS = o;  o += align16(nres * Wa * sizeof(T));   // and targets
-    s.src = o;  o += align16((F32 ? 2 * (size_t)Wa * own : 0) * sizeof(float));
+    s.src = o;  o += align16(2 * (size_t)Wa * own * sizeof(T));
     s.g = o;    o += align16(own * sizeof(T));
     s.T = o;    o += align16((size_t)Wa * sizeof(T));
     s.gT = o;   o += align16((size_t)Wa * sizeof(T));
@@ -73,16 +67,14 @@ __host__ __device__ inline AdjSmem adj_smem_layout(int Wa, int Kp, int R, int nr
 }
 
 // Half A of a reverse step on one 32-row tile of the CTA (rows row0 ..):
-//   Y_own += dt (op . X) + 2 C_own^T r   (Kahan-compensated in FP32).
-// Ccol points at the tile's first row of the CTA's C columns (row stride
-// cstride values).
+//   Y_own += dt (op . X) + 2 C_own^T r   (Kahan-compensated in FP32),
+// with C_own^T r read precomputed from asrc ([Wa][sstride], the tile's rows).
 template <typename T, int KI, int CB>
 __device__ __forceinline__ void adj_half_a(const T (&op)[2][4 * KI], const T* __restrict__ X,
                                            T* __restrict__ Y, float* __restrict__ comp,
-                                           const T* __restrict__ Ccol, const int cstride,
-                                           const T* __restrict__ rbuf,
-                                           const int R, const T dt, const int Wa, const int Kp,
-                                           const int row0, const int rp, const int j) {
+                                           const T* __restrict__ asrc, const int sstride, const T dt,
+                                           const int Wa, const int Kp, const int row0, const int rp,
+                                           const int j) {
     for (int c0 = 0; c0 < Wa; c0 += CB) {
         T acc[2][CB];
 #pragma unroll
@@ -109,9 +101,7 @@ __device__ __forceinline__ void adj_half_a(const T (&op)[2][4 * KI], const T* __
         if (active) {
             const int rl = 2 * rp + vi / CB;
             const int c = c0 + vi % CB;
-            T src = T(0);
-            for (int jr = 0; jr < R; ++jr) src = fmadd(Ccol[jr * cstride + rl], rbuf[jr * Wa + c], src);
-            const T inc = fmadd(tot, dt, T(2) * src);
+            const T inc = fmadd(tot, dt, T(2) * asrc[c * sstride + rl]);
             T* yp = Y + (size_t)c * Kp + row0 + rl;
             if constexpr (sizeof(T) == 4) {
                 *yp = kahan_add(*yp, inc, comp[c * kRowsPerCta + rl]);
@@ -209,11 +199,7 @@ __global__ void __launch_bounds__(kThreads, 1) rank2_adjoint_kernel(const AdjArg
     T* Sf = reinterpret_cast<T*>(smem + L.Sf);
     float* cV = reinterpret_cast<float*>(smem + L.cV);
     float* cS = reinterpret_cast<float*>(smem + L.cS);
-    T* Ccol = reinterpret_cast<T*>(smem + L.Ccol);  // [R][OWN]: C[j][row0 + ro]
-    T* rbuf = reinterpret_cast<T*>(smem + L.rbuf);  // [R][Wa]: residual of the step
-    T* trS = reinterpret_cast<T*>(smem + L.trS);    // [R][Wa]: C V^{n+1} of the next step
-    T* ysS = reinterpret_cast<T*>(smem + L.ysS);    // [R][Wa]: its target
-    float* srcS = reinterpret_cast<float*>(smem + L.src);  // FP32: [2][Wa][OWN] C^T r, by step parity
+    T* srcS = reinterpret_cast<T*>(smem + L.src);   // [2][Wa][OWN]: C^T r, by step parity
     T* gown = reinterpret_cast<T*>(smem + L.g);
     T* Tcol = reinterpret_cast<T*>(smem + L.T);
     T* gTacc = reinterpret_cast<T*>(smem + L.gT);
@@ -232,10 +218,6 @@ __global__ void __launch_bounds__(kThreads, 1) rank2_adjoint_kernel(const AdjArg
         cV[idx] = (c < ncol && row < a.Kv) ? a.compV[(size_t)(col0 + c) * a.Kv + row] : 0.f;
         cS[idx] = (c < ncol && row < a.Ks) ? a.compS[(size_t)(col0 + c) * a.Ks + row] : 0.f;
     }
-    for (int idx = tid; idx < (F32 ? 0 : R * OWN); idx += kThreads) {
-        const int jr = idx / OWN, ro = idx % OWN;
-        Ccol[idx] = ro < own_rows ? a.C_rm[(size_t)jr * Kp + row0 + ro] : T(0);
-    }
     for (int ro = tid; ro < OWN; ro += kThreads) gown[ro] = ro < own_rows ? a.g_p[row0 + ro] : T(0);
     for (int c = tid; c < Wa; c += kThreads) {
         Tcol[c] = (c < ncol) ? a.Tper[col0 + c] : T(1);
@@ -252,34 +234,20 @@ __global__ void __launch_bounds__(kThreads, 1) rank2_adjoint_kernel(const AdjArg
         load_op_rows<T, KI>(opA, a.opA_rm, Kp, row0 + 2 * rp, j);
         load_op_rows<T, KI>(opB, a.opB_rm, Kp, row0 + 2 * rp, j);
     }
-    // the trace record C V^{n+1} and target y*^{n+1} of reverse step n, copied
-    // asynchronously into trS / ysS while the step before it computes
-    auto prefetch_residual = [&](int n) {
-        const int rec = n + 1 - a.rec_base;  // trace record holding C V^{n+1}
-        for (int idx = tid; idx < R * Wa; idx += kThreads) {
-            const int jr = idx / Wa, c = idx % Wa;
-            const bool ok = c < ncol;
-            const int cc = ok ? c : 0;  // a valid address for the zero fill
-            cp_async_elem<T>(trS + idx, a.traces + ((size_t)rec * a.M + col0 + cc) * R + jr, ok);
-            cp_async_elem<T>(ysS + idx, a.ystar + ((size_t)n * a.M + col0 + cc) * R + jr, ok);
-        }
-    };
-    // FP32: the own rows' C^T r of reverse step n (precomputed for the range)
-    // into step buffer pb, 16 bytes per copy, zero for absent columns and rows
+    // the own rows' C^T r of reverse step n (precomputed for the range) into
+    // step buffer pb, 16 bytes (E rows) per copy, zero for absent columns and rows
+    constexpr int E = 16 / (int)sizeof(T);
     auto prefetch_src = [&](int n, int pb) {
-        float* dst = srcS + (size_t)pb * Wa * OWN;
-        for (int idx = tid; idx < Wa * (OWN / 4); idx += kThreads) {
-            const int c = idx / (OWN / 4), ro = 4 * (idx % (OWN / 4));
+        T* dst = srcS + (size_t)pb * Wa * OWN;
+        for (int idx = tid; idx < Wa * (OWN / E); idx += kThreads) {
+            const int c = idx / (OWN / E), ro = E * (idx % (OWN / E));
             const bool ok = c < ncol && ro < own_rows;
-            const float* gsrc = ok ? a.src + ((size_t)(n - a.n_lo) * a.M + col0 + c) * Kp + row0 + ro
-                                   : a.src;  // a valid address for the zero fill
+            const T* gsrc = ok ? a.src + ((size_t)(n - a.n_lo) * a.M + col0 + c) * Kp + row0 + ro
+                               : a.src;  // a valid address for the zero fill
             cp_async16(dst + (size_t)c * OWN + ro, gsrc, ok ? 16 : 0);
         }
     };
-    if (a.n_hi > a.n_lo) {
-        if constexpr (F32) prefetch_src(a.n_hi - 1, 0);
-        else prefetch_residual(a.n_hi - 1);
-    }
+    if (a.n_hi > a.n_lo) prefetch_src(a.n_hi - 1, 0);
     cluster.sync();
 
     for (int n = a.n_hi - 1; n >= a.n_lo; --n) {
@@ -297,20 +265,12 @@ __global__ void __launch_bounds__(kThreads, 1) rank2_adjoint_kernel(const AdjArg
             }
         }
         const T* dfn = dfT + (done % kAdjTab) * Wa;
-        // FP32: this step's C^T r, copied one step earlier into buffer done & 1;
-        // the next step's copies go to the other buffer, whose last readers
-        // passed the cluster barriers of the previous step.  FP64: the
-        // residual r^{n+1} = C V^{n+1} - ystar^{n+1} of this block's columns
-        // (zero past ncol) from the copies issued one step earlier.
+        // this step's C^T r, copied one step earlier into buffer done & 1; the
+        // next step's copies go to the other buffer, whose last readers passed
+        // the cluster barriers of the previous step
         cp_async_wait_all();
         __syncthreads();
-        if constexpr (F32) {
-            if (n > a.n_lo) prefetch_src(n - 1, (done + 1) & 1);
-        } else {
-            for (int idx = tid; idx < R * Wa; idx += kThreads) rbuf[idx] = trS[idx] - ysS[idx];
-            __syncthreads();
-            if (n > a.n_lo) prefetch_residual(n - 1);
-        }
+        if (n > a.n_lo) prefetch_src(n - 1, (done + 1) & 1);
         // ---- half A: lamV <- lamV + 2 C^T r^{n+1} + dt Asv^T lamS
         for (int rt = 0; rt < nrt_own; ++rt) {
             const int rowt = row0 + rt * kRowsPerCta;
@@ -321,8 +281,9 @@ __global__ void __launch_bounds__(kThreads, 1) rank2_adjoint_kernel(const AdjArg
                                   rowt, warp, lane);
             } else {
                 if (!RES) load_op_rows<T, KI>(opA, a.opA_rm, Kp, rowt + 2 * rp, j);
-                adj_half_a<T, KI, CB>(opA, Sf, Vf, cV + rt * Wa * kRowsPerCta, Ccol + rt * kRowsPerCta, OWN,
-                                      rbuf, R, dt, Wa, Kp, rowt, rp, j);
+                adj_half_a<T, KI, CB>(opA, Sf, Vf, cV + rt * Wa * kRowsPerCta,
+                                      srcS + (size_t)(done & 1) * Wa * OWN + rt * kRowsPerCta, OWN, dt, Wa, Kp,
+                                      rowt, rp, j);
             }
         }
         __syncthreads();

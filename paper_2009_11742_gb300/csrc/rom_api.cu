@@ -1864,9 +1864,8 @@ AdjLayout adjoint_layout(const rom_s* h, int M, int nsteps, int ckpt_every, size
     L.acomp = o;  o += al(sizeof(float) * kvm);
     L.gtp = o;    o += al(es * 16 * (size_t)M);
     L.acc = o;    o += al(sizeof(double) * 2);
-    // FP32: the source term of one launch range of reverse steps
-    L.src = o;
-    if (es == 4) o += al(sizeof(float) * (size_t)adj_src_steps(M, h->Kp, L.seg) * M * h->Kp);
+    // the source term of one launch range of reverse steps
+    L.src = o;  o += al(es * (size_t)adj_src_steps(M, h->Kp, L.seg, (int)es) * M * h->Kp);
     L.total = o;
     return L;
 }
@@ -1895,7 +1894,7 @@ rom_status adjoint_run(rom_s* h, const void* V0, const void* S0, const void* Tp,
     float* acomp = reinterpret_cast<float*>(ws + L.acomp);
     T* gtp = reinterpret_cast<T*>(ws + L.gtp);
     double* acc = reinterpret_cast<double*>(ws + L.acc);
-    float* asrc = reinterpret_cast<float*>(ws + L.src);
+    T* asrc = reinterpret_cast<T*>(ws + L.src);
     const size_t nv = (size_t)h->Kv * M, ns = (size_t)h->Ks * M, kvm = nv + ns;
     T* wV = work;
     T* wS = work + nv;
@@ -1966,23 +1965,20 @@ rom_status adjoint_run(rom_s* h, const void* V0, const void* S0, const void* Tp,
         aa.Kp = h->Kp;
         aa.R = h->R;
         aa.M = M;
-        if (F32) {
-            // the FP32 reverse kernels read the source term precomputed for a
-            // range of steps: the segment's latest steps first
-            const int nsrc = adj_src_steps(M, h->Kp, L.seg);
+        {
+            // the reverse kernels read the source term precomputed for a range
+            // of steps: the segment's latest steps first
+            const int nsrc = adj_src_steps(M, h->Kp, L.seg, (int)sizeof(T));
             for (int hi = n_start + len; hi > n_start && e == cudaSuccess;) {
                 const int lo = hi - nsrc > n_start ? hi - nsrc : n_start;
-                e = launch_adj_source(static_cast<const float*>(h->C_rm[1]), reinterpret_cast<const float*>(traces),
-                                      reinterpret_cast<const float*>(ys), lo, hi - lo, aa.rec_base, M, h->R,
-                                      h->Kp, asrc, st);
+                e = launch_adj_source(static_cast<const T*>(h->C_rm[t]), traces, ys, lo, hi - lo, aa.rec_base, M,
+                                      h->R, h->Kp, asrc, st);
                 aa.src = asrc;
                 aa.n_lo = lo;
                 aa.n_hi = hi;
                 if (e == cudaSuccess) e = launch_adjoint(aa, ap, st);
                 hi = lo;
             }
-        } else {
-            e = launch_adjoint(aa, ap, st);
         }
     }
     if (e == cudaSuccess && s == ROM_OK) e = launch_sum_partials(gtp, ap.cs, M, static_cast<T*>(gT), st);

@@ -204,7 +204,7 @@ struct AdjArgsT {
     const T* traces;  // forward records: record k = C V^{rec_base + k}, [k][m][j]
     const T* ystar;   // targets: record n = ystar^{n+1}, [n][m][j]
     T* gTpart;        // cs x M per-CTA partial dL/dT (in/out)
-    const float* src; // FP32: C^T r of the range's steps, [n - n_lo][m][Kp] (adj_source_kernel)
+    const T* src;     // C^T r of the range's steps, [n - n_lo][m][Kp] (adj_source_kernel)
     int* status;
     double dt;
     long long n0;
@@ -225,15 +225,15 @@ struct AdjPlan {
 bool plan_adjoint(int Kp, int M, int R, AdjPlan* p, bool f64 = false);
 cudaError_t launch_adjoint(const AdjArgsT<float>& a, const AdjPlan& p, cudaStream_t st);
 cudaError_t launch_adjoint(const AdjArgsT<double>& a, const AdjPlan& p, cudaStream_t st);
-// The reverse step's source term, hoisted out of the recurrence for the
-// split-role kernel: src[s][m][k] = sum_jr C[jr][k] r[jr] with r = traces of
+// The reverse step's source term, hoisted out of the recurrence of the
+// reverse kernels: src[s][m][k] = sum_jr C[jr][k] r[jr] with r = traces of
 // record n + 1 - rec_base minus ystar of step n, n = n_lo + s, s < ns.
-constexpr int kAdjSrcSteps = 64;  // most reverse steps per launch of the FP32 reverse kernels
+constexpr int kAdjSrcSteps = 64;  // most reverse steps per launch of the reverse kernels
 // Reverse steps per launch range for M columns of Kp rows within a segment of
 // seg steps: at most kAdjSrcSteps, and the source buffer (steps x M x Kp
-// floats) within about 64 MB.
-inline int adj_src_steps(int M, int Kp, int seg) {
-    const long long per = (long long)M * Kp * 4;
+// elements of es bytes) within about 64 MB.
+inline int adj_src_steps(int M, int Kp, int seg, int es) {
+    const long long per = (long long)M * Kp * es;
     long long s = per > 0 ? (64ll << 20) / per : kAdjSrcSteps;
     if (s > kAdjSrcSteps) s = kAdjSrcSteps;
     if (s > seg) s = seg;
@@ -241,6 +241,8 @@ inline int adj_src_steps(int M, int Kp, int seg) {
 }
 cudaError_t launch_adj_source(const float* C_rm, const float* traces, const float* ystar, int n_lo, int ns,
                               int rec_base, int M, int R, int Kp, float* src, cudaStream_t st);
+cudaError_t launch_adj_source(const double* C_rm, const double* traces, const double* ystar, int n_lo, int ns,
+                              int rec_base, int M, int R, int Kp, double* src, cudaStream_t st);
 cudaError_t launch_sum_partials(const float* part, int cs, int M, float* out, cudaStream_t st);
 cudaError_t launch_sum_partials(const double* part, int cs, int M, double* out, cudaStream_t st);
 
