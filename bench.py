@@ -564,8 +564,8 @@ def bench_uq(args, torch, dev, inputs, rom):
     steps, 64 receivers every 10 steps), then the per-receiver ensemble mean
     and 5/50/95 % bands on the device.  Reports both times, the rank-2 vs
     rank-1 ensemble throughput ratio and sampled accuracy."""
-    c = inputs.CONFIGS[5]
-    p = inputs.config(5)
+    c = inputs.WORKLOADS[5]
+    p = inputs.workload(5)
     N = args.nsteps or c["steps"]
     r, M, R, Kv, Ks = c["r"], p.M, p.R, p.Kv, p.Ks
     h = rom.Rom.from_problem(p)
@@ -642,7 +642,7 @@ def bench_fp64(args, torch, dev, inputs, rom):
     microbenchmark (and the 1.25 TFLOP/s nominal), the FP64
     rank-1 paths on the same operator, and the error against the FP64
     oracle."""
-    p = inputs.config(0)
+    p = inputs.workload(0)
     K, M, N = 128, 16, args.nsteps or 1000
     h = rom.Rom.from_problem(p)
     V = rom.Rom.new_state(K, M, "fp64", device=dev)
@@ -708,7 +708,7 @@ def bench_adjoint(args, torch, dev, inputs, rom):
     """Workload 4: gradients of the trace misfit (K = 512, M = 128, 4000 steps,
     R = 64, checkpoints every 64 steps) against the forward run with every
     trace recorded; reports the time ratio adjoint / forward."""
-    p = inputs.config(4)
+    p = inputs.workload(4)
     K, M, R = 512, 128, 64
     N = args.nsteps or 4000
     h = rom.Rom.from_problem(p)

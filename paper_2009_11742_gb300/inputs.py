@@ -39,9 +39,9 @@ __all__ = [
     "RomProblem",
     "make_problem",
     "random_state",
-    "config",
+    "workload",
     "batched_problems",
-    "CONFIGS",
+    "WORKLOADS",
 ]
 
 
@@ -107,9 +107,9 @@ def random_state(K: int, M: int, seed: int, scale: float = 1.0) -> np.ndarray:
     return _f32(scale * rng.standard_normal((K, M)))
 
 
-# The five workloads.  ``steps`` and ``r`` (trace interval) are part of the
-# workload, not of the drawn arrays.
-CONFIGS = {
+# The single-problem workloads 0-5 (3 is a batch).  ``steps`` and ``r``
+# (trace interval) are part of the workload, not of the drawn arrays.
+WORKLOADS = {
     0: dict(name="rank2-fp64-K128-M16-N1000", K=128, M=16, R=0, steps=1000,
             r=0, seed=0, prec="fp64"),
     1: dict(name="rank2-fp32-K512-M256-N10000-R64-r10", K=512, M=256, R=64,
@@ -130,9 +130,9 @@ CONFIGS = {
 }
 
 
-def config(i: int) -> RomProblem:
+def workload(i: int) -> RomProblem:
     """The problem of workload i (0, 1, 2, 4 or 5)."""
-    c = CONFIGS[i]
+    c = WORKLOADS[i]
     if i == 3:
         raise ValueError("workload 3 is a batch; use batched_problems()")
     if i == 5:
@@ -171,6 +171,6 @@ def batched_problems(nroms: int = 64, seed: int = 0, pow2_m: bool = False):
     out = []
     for i, (K, M) in enumerate(batched_sizes(nroms, seed, pow2_m)):
         p = make_problem(K, K, M, 0, seed=i + 1)
-        p.meta.update(name=f"rom{i}", steps=CONFIGS[3]["steps"])
+        p.meta.update(name=f"rom{i}", steps=WORKLOADS[3]["steps"])
         out.append(p)
     return out

@@ -140,7 +140,7 @@ def test_gradients_vs_fp64_finite_differences_workload4_shape(rom):
     forward run gives.  The misfit is quadratic in (V0, S0), so those
     differences are exact up to rounding; for T the difference quotient's own
     error is O(h^2), far below the bar."""
-    p = inputs.config(4)
+    p = inputs.workload(4)
     N, K = 300, 512
     cols = np.array([0, 41, 77, 127])
     M = len(cols)
@@ -223,7 +223,7 @@ def test_adjoint_workload4_full_size_sampled(rom):
     steps.  Targets come from the oracle at T* = 1.05 T for a sample of
     columns (zero elsewhere; the misfit is a sum over columns, so each
     column's gradient depends on its own target only)."""
-    p = inputs.config(4)
+    p = inputs.workload(4)
     N = 4000
     cols = np.array([0, 77, 127])
     Z = np.zeros((512, len(cols)))

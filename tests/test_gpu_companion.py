@@ -152,7 +152,7 @@ def test_companion_headline_workload_sampled(rom):
     """The benchmark's workload (K = 512, M = 256, 10000 steps, R = 64,
     r = 10) in the automatic plan; 24 sampled columns, among them every
     column the companion owns when the plan has one, each held to the bar."""
-    p = inputs.config(1)
+    p = inputs.workload(1)
     h = rom.Rom.from_problem(p)
     plan = h.plan(256)
     Z = np.zeros((512, 256), np.float32)

@@ -94,7 +94,7 @@ def test_unconverged_power_iteration_refused(rom):
 
 def test_config0_fp64(rom):
     """Workload 0: K = 128, M = 16, 1000 steps, FP64 check path, zero X0."""
-    p = inputs.config(0)
+    p = inputs.workload(0)
     h = rom.Rom.from_problem(p)
     Z = np.zeros((128, 16))
     V, S, _ = gpu_run(rom, h, p, Z, Z, 1000, "fp64")
@@ -129,7 +129,7 @@ def test_config1_fp32_sampled_columns(rom):
     """Workload 1 at full size on the GPU (K = 512, M = 256, 10000 steps,
     R = 64, r = 10) in the bench's launch configuration; the oracle recomputes
     a sample of columns (columns are independent, Sec. 2.4)."""
-    p = inputs.config(1)
+    p = inputs.workload(1)
     h = rom.Rom.from_problem(p)
     Z = np.zeros((512, 256))
     V, S, tr = gpu_run(rom, h, p, Z, Z, 10000, "fp32", r=10)
@@ -307,7 +307,7 @@ def test_host_buffers_match_device_buffers(rom):
 
 def test_energy_conserved_fp64_gpu(rom):
     """Unforced skew system: the discrete energy stays at its initial value."""
-    p = inputs.config(0)
+    p = inputs.workload(0)
     h = rom.Rom.from_problem(p)
     V0 = inputs.random_state(128, 4, seed=1).astype(np.float64)
     S0 = inputs.random_state(128, 4, seed=2).astype(np.float64)

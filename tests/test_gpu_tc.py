@@ -203,7 +203,7 @@ def test_bf16s_scales_span_many_binades(rom):
 def test_bf16s_config2_full_size_sampled(rom):
     """Workload 2 at full size with the exact sliced-integer scheme: the
     FP32 bar (relative L2 <= 1e-4) over all 20000 steps."""
-    p = inputs.config(2)
+    p = inputs.workload(2)
     h = rom.Rom.from_problem(p)
     Z = np.zeros((1024, 1024))
     V, S, tr = run_tc(rom, h, p, Z, Z, 20000, "bf16s", r=10)

@@ -220,7 +220,7 @@ def test_closed_form_svd_k32():
 def test_energy_exactly_conserved():
     """Unforced skew leapfrog conserves ||V||^2 + ||S||^2 - dt <S, Asv V>
     to roundoff over 1000 steps at K = 128 (workload-0 operator)."""
-    p = inputs.config(0)
+    p = inputs.workload(0)
     V0 = inputs.random_state(128, 4, seed=1).astype(np.float64)
     S0 = inputs.random_state(128, 4, seed=2).astype(np.float64)
     E0 = oracle.energy(p.Asv, p.dt, V0, S0)
