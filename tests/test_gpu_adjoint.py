@@ -340,6 +340,42 @@ def test_adjoint_fp64_checkpoints_and_autograd(rom):
     np.testing.assert_array_equal(Tt.grad.cpu().numpy(), a[3])
 
 
+@pytest.mark.parametrize("dtype", ["fp32", "fp64"])
+def test_adjoint_caller_workspace(rom, dtype):
+    """A caller-owned workspace of exactly rom_adjoint_workspace_size bytes
+    (checkpoints, traces and one launch range's source term) gives the same
+    gradients, bit for bit, as the library's own allocation (the loss to its
+    last bits); one byte less is refused with ROM_E_INVAL."""
+    Kv, Ks, M, R, N, ckpt = 192, 160, 9, 5, 150, 40
+    p, V0, S0, ystar = case(Kv, Ks, M, R, N, seed=61)
+    h = rom.Rom.from_problem(p)
+    f64 = dtype == "fp64"
+    tdt = torch.float64 if f64 else torch.float32
+    ndt = np.float64 if f64 else np.float32
+    V0t = rom.Rom.new_state(Kv, M, dtype, fill=V0.astype(ndt))
+    S0t = rom.Rom.new_state(Ks, M, dtype, fill=S0.astype(ndt))
+    T = torch.as_tensor(p.T.astype(ndt), device="cuda")
+    ys = torch.as_tensor(np.ascontiguousarray(np.transpose(ystar.astype(ndt), (0, 2, 1))), device="cuda")
+    ref = rom.adjoint(h, V0t, S0t, T, ys, N, ckpt_every=ckpt)
+    prec = rom.ROM_FP64 if f64 else rom.ROM_FP32
+    need = rom.rom_adjoint_workspace_size(h.h, M, N, ckpt, prec)
+    assert need > 0
+    ws = torch.empty(need, dtype=torch.uint8, device="cuda")
+    gV = rom.Rom.new_state(Kv, M, dtype)
+    gS = rom.Rom.new_state(Ks, M, dtype)
+    gT = torch.zeros(M, dtype=tdt, device="cuda")
+    args = (h.h, V0t.data_ptr(), S0t.data_ptr(), T.data_ptr(), M, N, ys.data_ptr(), ckpt, gV.data_ptr(),
+            gS.data_ptr(), gT.data_ptr())
+    st, loss = rom.rom_adjoint(*args, ws.data_ptr(), need, prec, None)
+    torch.cuda.synchronize()
+    assert st == rom.ROM_OK and h.sync_status() == 0
+    assert abs(loss - ref[0]) <= 1e-13 * abs(ref[0])  # the misfit's atomic sums
+    for x, y in zip((gV, gS, gT), ref[1:]):
+        np.testing.assert_array_equal(x.cpu().numpy(), y.cpu().numpy())
+    st, _ = rom.rom_adjoint(*args, ws.data_ptr(), need - 1, prec, None)
+    assert st == rom.ROM_E_INVAL
+
+
 def test_adjoint_fp64_refuses_above_512(rom):
     p, V0, S0, ystar = case(576, 576, 2, 2, 5, seed=3)
     h = rom.Rom.from_problem(p)
